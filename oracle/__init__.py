@@ -1,0 +1,216 @@
+"""ctypes binding of the FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg import this
+package.  It shares no code with the CUDA library (paper_2007_15405_gb300).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from .build import build
+
+_lib = None
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+_up = C.POINTER(C.c_uint32)
+_bp = C.POINTER(C.c_uint8)
+
+
+def _ptr(a, t=_dp):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = C.CDLL(path)
+        L.or_create.restype = C.c_void_p
+        L.or_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                C.c_double, C.c_double]
+        L.or_destroy.argtypes = [C.c_void_p]
+        L.or_add_capsule.restype = C.c_int
+        L.or_add_capsule.argtypes = [C.c_void_p, C.c_int, _dp, C.c_int, _ip, C.c_double,
+                                     C.c_double, C.c_double, C.c_double, C.c_double, C.c_int]
+        L.or_set_film.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, _dp]
+        L.or_set_populations.argtypes = [C.c_void_p, _dp]
+        L.or_get_populations.argtypes = [C.c_void_p, _dp]
+        L.or_step.argtypes = [C.c_void_p, C.c_int]
+        L.or_fields.argtypes = [C.c_void_p, _dp, _dp]
+        L.or_capsule_state.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp, _dp]
+        L.or_momentum.argtypes = [C.c_void_p, _dp, _dp, _dp]
+        L.or_total_mass.argtypes = [C.c_void_p, _dp]
+        L.or_cuts.argtypes = [C.c_void_p, _up, _ip, _bp]
+        L.or_cuts_bruteforce.argtypes = [C.c_void_p, _up, _ip]
+        L.or_meniscus_field.argtypes = [C.c_void_p, _dp, _dp]
+        L.or_set_capsule_velocity.argtypes = [C.c_void_p, C.c_int, _dp]
+        L.or_tables.argtypes = [_ip, _dp, _ip]
+        L.or_equilibrium.argtypes = [C.c_double, _dp, _dp]
+        L.or_sc_forces.argtypes = [C.c_void_p, _dp]
+        L.or_membrane.argtypes = [C.c_int, _dp, _dp, C.c_int, _ip, C.c_double, C.c_double,
+                                  C.c_double, C.c_double, _dp, _dp, C.c_int]
+        L.or_mesh_volume.restype = C.c_double
+        L.or_mesh_volume.argtypes = [_dp, _ip, C.c_int]
+        L.or_mesh_area.restype = C.c_double
+        L.or_mesh_area.argtypes = [_dp, _ip, C.c_int]
+        L.or_hertz.restype = C.c_double
+        L.or_hertz.argtypes = [C.c_double, C.c_double, C.c_double]
+        _lib = L
+    return _lib
+
+
+def tables():
+    e = np.zeros((19, 3), np.int32)
+    w = np.zeros(19)
+    op = np.zeros(19, np.int32)
+    lib().or_tables(_ptr(e, _ip), _ptr(w), _ptr(op, _ip))
+    return e, w, op
+
+
+def equilibrium(rho, u):
+    f = np.zeros(19)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    lib().or_equilibrium(float(rho), _ptr(u), _ptr(f))
+    return f
+
+
+def membrane(X, Xref, F, kS=0.0, C=0.0, kB=0.0, kV=0.0, which=7):
+    """Energies [skalak, helfrich, volume] and elastic node forces [nv,3]."""
+    X = np.ascontiguousarray(X, np.float64)
+    Xref = np.ascontiguousarray(Xref, np.float64)
+    F = np.ascontiguousarray(F, np.int32)
+    E = np.zeros(3)
+    Fo = np.zeros_like(X)
+    lib().or_membrane(X.shape[0], _ptr(X), _ptr(Xref), F.shape[0], _ptr(F, _ip), kS, C, kB, kV,
+                      _ptr(E), _ptr(Fo), which)
+    return E, Fo
+
+
+def mesh_volume(X, F):
+    X = np.ascontiguousarray(X, np.float64)
+    F = np.ascontiguousarray(F, np.int32)
+    return lib().or_mesh_volume(_ptr(X), _ptr(F, _ip), F.shape[0])
+
+
+def mesh_area(X, F):
+    X = np.ascontiguousarray(X, np.float64)
+    F = np.ascontiguousarray(F, np.int32)
+    return lib().or_mesh_area(_ptr(X), _ptr(F, _ip), F.shape[0])
+
+
+def hertz(d, xi=1.5, delta0=1.5):
+    return lib().or_hertz(xi, delta0, d)
+
+
+class Oracle:
+    """One lattice with its capsules, stepped by the FP64 oracle."""
+
+    def __init__(self, nx, ny, nz, wall=1, tau=(1.0, 1.0), G=3.6, rep_dz=10.0):
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.N = nx * ny * nz
+        self._h = lib().or_create(nx, ny, nz, wall, tau[0], tau[1], G, rep_dz)
+        self.nv = []
+
+    def close(self):
+        if self._h:
+            lib().or_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @classmethod
+    def from_workload(cls, wl, set_film=True):
+        o = cls(wl.nx, wl.ny, wl.nz, wall=wl.wall, tau=wl.tau, G=wl.G, rep_dz=wl.rep_dz)
+        for cap in wl.capsules:
+            X, F = cap.mesh()
+            o.add_capsule(X, F, cap.kS, cap.C, cap.kB, cap.kV, cap.mass, cap.mode)
+        if set_film:
+            from paper_2007_15405_gb300.inputs import RHO_MAJ, RHO_MIN, RHO_MIX
+            o.set_film(wl.h_top, RHO_MAJ, RHO_MIN, RHO_MIX, wl.jitter())
+        return o
+
+    def add_capsule(self, X, F, kS, C, kB, kV, mass, mode):
+        X = np.ascontiguousarray(X, np.float64)
+        F = np.ascontiguousarray(F, np.int32)
+        cid = lib().or_add_capsule(self._h, X.shape[0], _ptr(X), F.shape[0], _ptr(F, _ip), kS, C,
+                                   kB, kV, mass, mode)
+        self.nv.append(X.shape[0])
+        return cid
+
+    def set_film(self, h_top, rho_maj, rho_min, rho_mix, jit=None):
+        j = None if jit is None else np.ascontiguousarray(jit, np.float64).reshape(-1)
+        lib().or_set_film(self._h, h_top, rho_maj, rho_min, rho_mix, _ptr(j))
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(f, np.float64).reshape(-1)
+        assert f.size == 38 * self.N
+        lib().or_set_populations(self._h, _ptr(f))
+
+    def populations(self):
+        f = np.zeros((2, 19, self.nz, self.ny, self.nx))
+        lib().or_get_populations(self._h, _ptr(f))
+        return f
+
+    def step(self, n=1):
+        lib().or_step(self._h, int(n))
+
+    def fields(self):
+        rho = np.zeros((2, self.nz, self.ny, self.nx))
+        u = np.zeros((3, self.nz, self.ny, self.nx))
+        lib().or_fields(self._h, _ptr(rho), _ptr(u))
+        return rho, u
+
+    def capsule_state(self, cid):
+        nv = self.nv[cid]
+        X = np.zeros((nv, 3)); V = np.zeros((nv, 3)); Fc = np.zeros((nv, 3)); Ft = np.zeros((nv, 3))
+        o = np.zeros(8)
+        lib().or_capsule_state(self._h, cid, _ptr(X), _ptr(V), _ptr(Fc), _ptr(Ft), _ptr(o))
+        return dict(X=X, V=V, Fcpl=Fc, Ftot=Ft, force=o[0:3].copy(), torque=o[3:6].copy(),
+                    area=o[6], volume=o[7])
+
+    def momentum(self):
+        a, b, c = np.zeros(3), np.zeros(3), np.zeros(3)
+        lib().or_momentum(self._h, _ptr(a), _ptr(b), _ptr(c))
+        return a, b, c
+
+    def total_mass(self):
+        m = np.zeros(2)
+        lib().or_total_mass(self._h, _ptr(m))
+        return m
+
+    def cuts(self):
+        mask = np.zeros((self.nz, self.ny, self.nx), np.uint32)
+        tri = np.zeros((self.nz, self.ny, self.nx, 18), np.int32)
+        inside = np.zeros((self.nz, self.ny, self.nx), np.uint8)
+        lib().or_cuts(self._h, _ptr(mask, _up), _ptr(tri, _ip), _ptr(inside, _bp))
+        return mask, tri, inside
+
+    def cuts_bruteforce(self):
+        mask = np.zeros((self.nz, self.ny, self.nx), np.uint32)
+        tri = np.zeros((self.nz, self.ny, self.nx, 18), np.int32)
+        lib().or_cuts_bruteforce(self._h, _ptr(mask, _up), _ptr(tri, _ip))
+        return mask, tri
+
+    def meniscus_field(self, rho=None):
+        h = np.zeros((self.ny, self.nx))
+        r = None if rho is None else np.ascontiguousarray(rho, np.float64)
+        lib().or_meniscus_field(self._h, _ptr(r), _ptr(h))
+        return h
+
+    def set_capsule_velocity(self, cid, V):
+        V = np.ascontiguousarray(V, np.float64)
+        lib().or_set_capsule_velocity(self._h, cid, _ptr(V))
+
+    def sc_forces(self):
+        F = np.zeros((2, 3, self.nz, self.ny, self.nx))
+        lib().or_sc_forces(self._h, _ptr(F))
+        return F

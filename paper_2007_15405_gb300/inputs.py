@@ -1,0 +1,173 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle's tests.
+
+This module holds no arithmetic of the method itself: it only builds meshes, random
+density jitter and the workload descriptions (lattice sizes, film heights, capsule
+placements and moduli) that both sides receive as plain arrays.
+
+Workloads follow the simulation set-up of the paper (Sec. 3.2 "Simulation setup"):
+two equal-density components with initial majority/minority densities 0.7/0.04 and
+one mixed layer at 0.3, G = 3.6, node mass 25, Hertz range 1.5 and a repulsive plane
+10 lattice units above the substrate.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+# Physical constants of the set-up (Sec. 3.2).
+RHO_MAJ = 0.7
+RHO_MIN = 0.04
+RHO_MIX = 0.3
+G_SC = 3.6
+NODE_MASS = 25.0
+REP_DZ = 10.0  # repulsive plane offset above the substrate (Delta_z)
+DELTA0 = 1.5   # Hertz cut-off
+XI = 1.5       # Hertz strength
+
+MODE_FREE = 0
+MODE_FROZEN = 1
+MODE_FIXED = 2
+
+
+def icosphere(level: int, radius: float = 1.0,
+              centre: Tuple[float, float, float] = (0.0, 0.0, 0.0)) -> Tuple[np.ndarray, np.ndarray]:
+    """Subdivided icosahedron projected on a sphere.
+
+    Returns (nodes float64 [nv,3], faces int32 [nf,3]) with faces oriented
+    counter-clockwise seen from outside (outward normals).  nv = 10*4**level + 2,
+    nf = 20*4**level (level 3: 642/1280, level 4: 2562/5120).
+    """
+    t = (1.0 + math.sqrt(5.0)) / 2.0
+    verts = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0),
+             (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
+             (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    verts = [np.array(v, dtype=np.float64) / np.linalg.norm(v) for v in verts]
+    faces = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11),
+             (1, 5, 9), (5, 11, 4), (11, 10, 2), (10, 7, 6), (7, 1, 8),
+             (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9),
+             (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(level):
+        cache = {}
+        new_faces = []
+
+        def mid(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in cache:
+                m = verts[a] + verts[b]
+                verts.append(m / np.linalg.norm(m))
+                cache[key] = len(verts) - 1
+            return cache[key]
+
+        for (a, b, c) in faces:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            new_faces += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = new_faces
+    X = np.array(verts, dtype=np.float64) * radius + np.asarray(centre, dtype=np.float64)
+    F = np.array(faces, dtype=np.int32)
+    # orient outward: the icosahedron list above is counter-clockwise from outside
+    c = np.asarray(centre, dtype=np.float64)
+    n = np.cross(X[F[:, 1]] - X[F[:, 0]], X[F[:, 2]] - X[F[:, 0]])
+    flip = np.einsum("ij,ij->i", n, X[F[:, 0]] - c) < 0
+    F[flip] = F[flip][:, [0, 2, 1]]
+    return X, F
+
+
+def jitter(shape_zyx: Tuple[int, int, int], amplitude: float, seed: int) -> np.ndarray:
+    """Uniform density jitter U(-a, a) for both components, float64 [2, nz, ny, nx]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nz, ny, nx = shape_zyx
+    return rng.uniform(-amplitude, amplitude, size=(2, nz, ny, nx))
+
+
+@dataclasses.dataclass
+class CapsuleSpec:
+    centre: Tuple[float, float, float]
+    radius: float
+    level: int
+    kS: float = 5e-3
+    C: float = 0.0
+    kB: float = 1e-3
+    kV: float = 1.0
+    mass: float = NODE_MASS
+    mode: int = MODE_FREE
+
+    def mesh(self):
+        return icosphere(self.level, self.radius, self.centre)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    h_top: float
+    capsules: List[CapsuleSpec]
+    steps: int
+    tau: Tuple[float, float] = (1.0, 1.0)
+    G: float = G_SC
+    wall: int = 1
+    jitter_amp: float = 1e-3
+    seed: int = 1234
+    rep_dz: float = REP_DZ
+
+    @property
+    def nodes(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def jitter(self) -> Optional[np.ndarray]:
+        if self.jitter_amp == 0.0:
+            return None
+        return jitter((self.nz, self.ny, self.nx), self.jitter_amp, self.seed)
+
+
+def z_rest(radius: float) -> float:
+    """Capsule centre height with its bottom where the substrate repulsion starts
+    (Sec. 4.2: the lower part of the particle sits at the boundary of the interaction)."""
+    return 0.5 + REP_DZ + DELTA0 + radius
+
+
+# Small generic offsets keep icosphere vertices off lattice links so that no
+# link-triangle test is an exact tie.
+_OFF = (0.3, 0.4, 0.17)
+
+
+def single_capsule_film(mode: int = MODE_FREE, steps: int = 1000) -> Workload:
+    """32x32x48 lattice, tau=1, substrate at z=0, A film 12 cells thick under B,
+    one R=8 level-3 icosphere (642 nodes / 1280 faces), kS=5e-3, area-dilation
+    ratio 1 (C=0), kB=1e-3, jitter +-1e-3, 1000 steps."""
+    cap = CapsuleSpec(centre=(16 + _OFF[0], 16 + _OFF[1], z_rest(8.0) + _OFF[2]), radius=8.0,
+                      level=3, kS=5e-3, C=0.0, kB=1e-3, mode=mode)
+    return Workload("single-capsule film 32x32x48 R=8", 32, 32, 48, h_top=12.5,
+                    capsules=[cap], steps=steps)
+
+
+def capsule_pair(steps: int = 20000, mode: int = MODE_FREE, nx: int = 128, ny: int = 64,
+                 nz: int = 64, radius: float = 12.0, level: int = 4) -> Workload:
+    """Two R=12 level-4 capsules (2562 nodes each) at centre distance 3R in a
+    128x64x64 lattice, film height 0.6R above the repulsive plane."""
+    d = 3.0 * radius
+    zc = z_rest(radius) + _OFF[2]
+    cx = nx / 2 + _OFF[0]
+    cy = ny / 2 + _OFF[1]
+    caps = [CapsuleSpec(centre=(cx - d / 2, cy, zc), radius=radius, level=level, mode=mode),
+            CapsuleSpec(centre=(cx + d / 2, cy, zc), radius=radius, level=level, mode=mode)]
+    h_top = 0.5 + REP_DZ + 0.6 * radius
+    return Workload(f"capsule pair {nx}x{ny}x{nz} R={radius:g} d=3R", nx, ny, nz, h_top=h_top,
+                    capsules=caps, steps=steps)
+
+
+def tiny_film(nx=16, ny=12, nz=20, radius=4.0, level=2, mode=MODE_FREE, steps=20,
+              h_top=None, seed=99, rep_dz=2.0) -> Workload:
+    """Small ragged lattice for oracle-vs-kernel element-wise parity (repulsive
+    plane lowered to 2 lattice units so that the capsule fits)."""
+    zc = 0.5 + rep_dz + DELTA0 + radius + _OFF[2]
+    cap = CapsuleSpec(centre=(nx / 2 + _OFF[0], ny / 2 + _OFF[1], zc), radius=radius,
+                      level=level, kS=5e-3, C=1.0, kB=1e-3, mode=mode)
+    if h_top is None:
+        h_top = zc - 0.3 * radius
+    return Workload(f"tiny film {nx}x{ny}x{nz}", nx, ny, nz, h_top=h_top, capsules=[cap],
+                    steps=steps, seed=seed, rep_dz=rep_dz)
