@@ -1,0 +1,171 @@
+/*
+ * capfilm -- C ABI of the GB300 coupled lattice Boltzmann / FEM capsule step.
+ *
+ * The method is the one of Wouters, Aouane, Sega & Harting, "Capillary
+ * interactions between soft capsules protruding through thin fluid films":
+ * a two-component Shan-Chen D3Q19 lattice Boltzmann fluid (Sec. 3.1, Eqs. 4,
+ * 5, 10) on a substrate, coupled by half-way bounce-back with Ladd's
+ * moving-wall term to triangulated elastic capsules (Sec. 3.1, Eqs. 6-9, 11).
+ *
+ * Conventions
+ *  - Lattice units: dx = dt = rho_0 = 1.  Nodes (x, y, z), 0 <= x < nx, ...,
+ *    node index n = (z*ny + y)*nx + x.  Periodic in x, y and z; with `wall` set
+ *    the plane z = 0 is solid (the substrate, wall at z = 1/2).
+ *  - Populations are ordered [component][direction][z][y][x]; component 0 is
+ *    the film fluid A, component 1 the covering fluid B.  Direction order:
+ *    0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = (1,1,0),(-1,-1,0),(1,-1,0),
+ *    (-1,1,0),(1,0,1),(-1,0,-1),(1,0,-1),(-1,0,1),(0,1,1),(0,-1,-1),(0,1,-1),
+ *    (0,-1,1): opposite directions are adjacent pairs (1,2), (3,4), ...
+ *  - Every call returns a cf_status; nothing throws across the ABI.  On error
+ *    cf_last_error() returns a thread-local description.
+ *  - Host arrays passed in are copied; the caller keeps ownership.  Output
+ *    arrays are caller-allocated host buffers of the stated size.
+ *  - Device memory is owned by the context.  It is taken from the caller's
+ *    allocator when one is given (e.g. PyTorch's caching allocator), otherwise
+ *    from cudaMallocAsync on the context's stream.
+ *  - All work is queued on the context's stream (desc.stream, or a stream the
+ *    context creates).  Readout calls synchronise that stream.
+ */
+#ifndef CAPFILM_H
+#define CAPFILM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CF_OK = 0,
+    CF_EINVAL = 1,     /* bad argument or size                               */
+    CF_ENOMEM = 2,     /* device allocation failed                           */
+    CF_ECUDA = 3,      /* a CUDA call failed (text in cf_last_error)          */
+    CF_ESTATE = 4,     /* call not valid in the current state                */
+    CF_ENOTFOUND = 5,  /* unknown capsule id                                 */
+    CF_EDIVERGED = 6,  /* non-finite density detected                        */
+    CF_EOVERFLOW = 7   /* an internal list (cut-link nodes) exceeded capacity */
+} cf_status;
+
+typedef enum { CF_FP32 = 0 } cf_precision;
+
+/* Capsule modes: FREE moves and deforms (Eq. 9); FROZEN keeps its shape and
+ * translates rigidly with the summed force (the frozen-shape protocol of
+ * Sec. 4.3); FIXED does not move (the rigid particles of Sec. 4.1). */
+typedef enum { CF_FREE = 0, CF_FROZEN = 1, CF_FIXED = 2 } cf_mode;
+
+typedef struct {
+    /* returns a device pointer of at least `bytes` bytes usable on `stream`,
+     * or NULL on failure */
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, void *stream, void *user);
+    void *user;
+} cf_allocator;
+
+typedef struct {
+    int nx, ny, nz;          /* lattice size, each >= 3                        */
+    int wall;                /* 1: substrate plane z = 0; 0: fully periodic    */
+    double tau[2];           /* BGK relaxation times of A and B (Eq. 4), > 1/2 */
+    double G;                /* Shan-Chen coupling G^{AB} = G^{BA} (Eq. 10)    */
+    double rep_dz;           /* repulsive plane at z = 1/2 + rep_dz (Sec. 3.2) */
+    double xi, delta0;       /* Hertz strength and range (Eq. 11)              */
+    int precision;           /* cf_precision                                   */
+    const cf_allocator *allocator; /* may be NULL                              */
+    void *stream;            /* cudaStream_t or NULL                           */
+} cf_lattice_desc;
+
+typedef struct {
+    int nv, nf;              /* nodes and triangular elements                 */
+    const double *nodes;     /* host [nv*3], reference (stress-free) shape   */
+    const int *faces;        /* host [nf*3], counter-clockwise seen from out */
+    double kS;               /* Skalak shear modulus kappa_S (Eq. 6)          */
+    double C;                /* Skalak area constant, kappa_A/kappa_S = 1+2C  */
+    double kB;               /* Helfrich bending modulus kappa_B (Eq. 7), H0=0 */
+    double kV;               /* volume penalty kappa_V (Eq. 8)                */
+    double mass;             /* mass per node m_i (Sec. 3.2: 25)              */
+    int mode;                /* cf_mode                                       */
+} cf_capsule_desc;
+
+typedef struct cf_ctx cf_ctx;
+
+/* Thread-local text of the last error of this thread ("" if none). */
+const char *cf_last_error(void);
+
+/* Lattice and film set-up (Sec. 3.2).  Allocates the populations and the
+ * coupling structures; populations start at zero until cf_set_film. */
+cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out);
+cf_status cf_destroy(cf_ctx *ctx);
+
+/* Capsule insertion with its elastic moduli (Sec. 3.1, Eqs. 6-8).  The given
+ * mesh is the stress-free reference state; *id receives the capsule index
+ * (0, 1, ... in insertion order).  Capsules must be added before cf_set_film,
+ * which fills their interior with the B-majority fluid. */
+cf_status cf_add_capsule(cf_ctx *ctx, const cf_capsule_desc *desc, int *id);
+cf_status cf_set_capsule_mode(cf_ctx *ctx, int id, int mode);
+
+/* Film initialisation (Sec. 3.2): A-majority (rho_maj / rho_min) below the
+ * film top h_top, B-majority above, the plane floor(h_top + 1/2) mixed at
+ * rho_mix for both, capsule interiors B-majority, all at rest (f_i = w_i rho).
+ * jitter: NULL or host [2][nz][ny][nx] added to the densities of A and B. */
+cf_status cf_set_film(cf_ctx *ctx, double h_top, double rho_maj, double rho_min,
+                      double rho_mix, const double *jitter);
+
+/* Advance n coupled time steps (Sec. 3.1): streaming with bounce-back and
+ * Ladd momentum exchange, Shan-Chen forces with interior/exterior
+ * decoupling, BGK collision, element forces averaged over two steps, Skalak,
+ * Helfrich, volume and Hertz forces, node update, new cut links.  Asynchronous
+ * on the context stream; returns CF_EOVERFLOW / CF_EDIVERGED detected by the
+ * previous readout or sync. */
+cf_status cf_step(cf_ctx *ctx, long long n);
+
+/* Wait for queued work; reports device-side error flags. */
+cf_status cf_sync(cf_ctx *ctx);
+
+/* Readouts (Sec. 4.1, 4.3).  Sum over the capsule's nodes of the fluid
+ * coupling force of the last step (F) and its torque about the node centroid
+ * (T); lateral capillary force between capsules a and b,
+ * F = 1/2 (F_b - F_a) . e_ab with e_ab the unit xy vector from a to b
+ * (negative = attraction, as in Eq. 3). */
+cf_status cf_capsule_force(cf_ctx *ctx, int id, double F[3], double T[3]);
+cf_status cf_lateral_force(cf_ctx *ctx, int a, int b, double *F);
+
+/* Node positions (host [nv*3]), surface area and enclosed volume of the mesh
+ * the last step's forces were computed on.  Any output may be NULL. */
+cf_status cf_capsule_state(cf_ctx *ctx, int id, double *nodes, double *area, double *volume);
+
+/* Densities [2][N] and barycentric velocity u = (j_A + j_B + F/2)/rho [3][N]
+ * of the last step (N = nx*ny*nz; solid nodes read 0).  Either may be NULL. */
+cf_status cf_fields(cf_ctx *ctx, double *rho, double *u);
+
+/* Post-collision populations [2][19][N] as stored (float). */
+cf_status cf_populations(cf_ctx *ctx, float *f);
+
+/* Total mass of each component (FP64 sum over the lattice). */
+cf_status cf_total_mass(cf_ctx *ctx, double m[2]);
+
+/* Film height per column h[ny][nx]: the first zero of rho_A - rho_B above the
+ * substrate, linearly interpolated; NaN where it touches a capsule interior. */
+cf_status cf_meniscus_field(cf_ctx *ctx, double *h);
+
+/* Meniscus profile around capsule id (Sec. 4.1): zeta(r) = h - h_inf along the
+ * four principal directions from the capsule centroid column, averaged; h_inf
+ * is the mean height of the valid columns farthest from every capsule.
+ * r and zeta have capacity *inout_n (in) and receive *inout_n entries (out);
+ * too small returns CF_EINVAL with the needed size.  Z receives the largest
+ * zeta (the capillary rise) and may be NULL. */
+cf_status cf_meniscus_profile(cf_ctx *ctx, int id, double *r, double *zeta, size_t *inout_n,
+                              double *Z);
+
+/* Cut-link structure for the current membrane positions (diagnostics):
+ * mask[N] bit (k-1) set when link n -> n + e_k crosses a membrane an odd number
+ * of times; tri[N*18] the crossed element (global index) or -1; inside[N]
+ * 1 for capsule-interior nodes.  Any output may be NULL. */
+cf_status cf_cuts(cf_ctx *ctx, uint32_t *mask, int *tri, uint8_t *inside);
+
+/* Number of kernel launches issued by the last cf_step call. */
+cf_status cf_launch_count(cf_ctx *ctx, long long *n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

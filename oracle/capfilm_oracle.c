@@ -793,6 +793,9 @@ static void membrane_update(or_ctx *c) {
         }
         memcpy(p->force, sF, sizeof(sF));
         memcpy(p->torque, sT, sizeof(sT));
+        /* area and volume of the mesh this step's forces were computed on */
+        p->area = mesh_area(p->X, p->F, p->nf);
+        p->volume = mesh_volume(p->X, p->F, p->nf);
         if (p->mode == 0) {          /* free: x += F/m, v = F/m (Eq. 9, dt = 1) */
             for (int k = 0; k < 3 * p->nv; ++k) {
                 p->V[k] = p->Ftot[k] / p->mass;
@@ -806,8 +809,6 @@ static void membrane_update(or_ctx *c) {
         } else {                     /* fixed */
             memset(p->V, 0, sizeof(double) * 3 * p->nv);
         }
-        p->area = mesh_area(p->X, p->F, p->nf);
-        p->volume = mesh_volume(p->X, p->F, p->nf);
     }
 }
 

@@ -1,0 +1,264 @@
+"""Thin Python binding of the capfilm C ABI (include/capfilm.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+libcapfilm.so built next to this file.  PyTorch supplies device memory (its
+caching allocator, through the ABI's allocator callbacks) and the CUDA stream.
+There is no CPU fallback: if the library is missing, loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcapfilm.so")
+
+CF_OK = 0
+STATUS_NAMES = {0: "CF_OK", 1: "CF_EINVAL", 2: "CF_ENOMEM", 3: "CF_ECUDA", 4: "CF_ESTATE",
+                5: "CF_ENOTFOUND", 6: "CF_EDIVERGED", 7: "CF_EOVERFLOW"}
+
+FREE, FROZEN, FIXED = 0, 1, 2
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+class LatticeDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("wall", C.c_int),
+                ("tau", C.c_double * 2), ("G", C.c_double), ("rep_dz", C.c_double),
+                ("xi", C.c_double), ("delta0", C.c_double), ("precision", C.c_int),
+                ("allocator", C.POINTER(Allocator)), ("stream", C.c_void_p)]
+
+
+class CapsuleDesc(C.Structure):
+    _fields_ = [("nv", C.c_int), ("nf", C.c_int), ("nodes", C.POINTER(C.c_double)),
+                ("faces", C.POINTER(C.c_int)), ("kS", C.c_double), ("C", C.c_double),
+                ("kB", C.c_double), ("kV", C.c_double), ("mass", C.c_double), ("mode", C.c_int)]
+
+
+class CapfilmError(RuntimeError):
+    pass
+
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+_fp = C.POINTER(C.c_float)
+
+
+def load_library(path: Optional[str] = None):
+    """Load libcapfilm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise CapfilmError(f"CUDA library not built: {path} is missing (run build())")
+    L = C.CDLL(path)
+    L.cf_last_error.restype = C.c_char_p
+    sig = {
+        "cf_create": [C.POINTER(LatticeDesc), C.POINTER(C.c_void_p)],
+        "cf_destroy": [C.c_void_p],
+        "cf_add_capsule": [C.c_void_p, C.POINTER(CapsuleDesc), C.POINTER(C.c_int)],
+        "cf_set_capsule_mode": [C.c_void_p, C.c_int, C.c_int],
+        "cf_set_film": [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, _dp],
+        "cf_step": [C.c_void_p, C.c_longlong],
+        "cf_sync": [C.c_void_p],
+        "cf_capsule_force": [C.c_void_p, C.c_int, _dp, _dp],
+        "cf_lateral_force": [C.c_void_p, C.c_int, C.c_int, _dp],
+        "cf_capsule_state": [C.c_void_p, C.c_int, _dp, _dp, _dp],
+        "cf_fields": [C.c_void_p, _dp, _dp],
+        "cf_populations": [C.c_void_p, _fp],
+        "cf_total_mass": [C.c_void_p, _dp],
+        "cf_meniscus_field": [C.c_void_p, _dp],
+        "cf_meniscus_profile": [C.c_void_p, C.c_int, _dp, _dp, C.POINTER(C.c_size_t), _dp],
+        "cf_cuts": [C.c_void_p, C.POINTER(C.c_uint32), C.POINTER(C.c_int), C.POINTER(C.c_uint8)],
+        "cf_launch_count": [C.c_void_p, C.POINTER(C.c_longlong)],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    return ["cf_last_error", "cf_create", "cf_destroy", "cf_add_capsule", "cf_set_capsule_mode",
+            "cf_set_film", "cf_step", "cf_sync", "cf_capsule_force", "cf_lateral_force",
+            "cf_capsule_state", "cf_fields", "cf_populations", "cf_total_mass",
+            "cf_meniscus_field", "cf_meniscus_profile", "cf_cuts", "cf_launch_count"]
+
+
+def _check(rc):
+    if rc != CF_OK:
+        msg = _lib.cf_last_error().decode()
+        raise CapfilmError(f"{STATUS_NAMES.get(rc, rc)}: {msg}")
+
+
+def _ptr(a, t=_dp):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+class _TorchAllocator:
+    """Device memory from PyTorch's caching allocator, exposed as C callbacks."""
+
+    def __init__(self, device):
+        import torch
+        self.torch = torch
+        self.device = device
+
+        def _alloc(size, stream, user):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(size), self.device, stream))
+            except Exception:
+                return None
+
+        def _free(ptr, stream, user):
+            try:
+                torch.cuda.caching_allocator_delete(int(ptr))
+            except Exception:
+                pass
+
+        self._alloc = ALLOC_FN(_alloc)
+        self._free = FREE_FN(_free)
+        self.struct = Allocator(self._alloc, self._free, None)
+
+
+class Simulation:
+    """One lattice with its capsules, stepped on the GPU by the CUDA library."""
+
+    def __init__(self, nx, ny, nz, wall=1, tau=(1.0, 1.0), G=3.6, rep_dz=10.0, xi=1.5,
+                 delta0=1.5, stream=None, use_torch_allocator=True):
+        L = load_library()
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.N = nx * ny * nz
+        self._alloc = None
+        alloc_ptr = None
+        stream_handle = None
+        if use_torch_allocator:
+            import torch
+            dev = torch.cuda.current_device()
+            self._alloc = _TorchAllocator(dev)
+            alloc_ptr = C.pointer(self._alloc.struct)
+            s = stream if stream is not None else torch.cuda.current_stream()
+            stream_handle = s.cuda_stream
+            self._stream = s
+        elif stream is not None:
+            stream_handle = stream.cuda_stream
+            self._stream = stream
+        desc = LatticeDesc(nx, ny, nz, wall, (C.c_double * 2)(*tau), G, rep_dz, xi, delta0, 0,
+                           alloc_ptr, stream_handle)
+        self._desc = desc
+        h = C.c_void_p()
+        _check(L.cf_create(C.byref(desc), C.byref(h)))
+        self._h = h
+        self.nv = []
+
+    @classmethod
+    def from_workload(cls, wl, set_film=True, **kw):
+        s = cls(wl.nx, wl.ny, wl.nz, wall=wl.wall, tau=wl.tau, G=wl.G, rep_dz=wl.rep_dz, **kw)
+        for cap in wl.capsules:
+            X, F = cap.mesh()
+            s.add_capsule(X, F, cap.kS, cap.C, cap.kB, cap.kV, cap.mass, cap.mode)
+        if set_film:
+            from .inputs import RHO_MAJ, RHO_MIN, RHO_MIX
+            s.set_film(wl.h_top, RHO_MAJ, RHO_MIN, RHO_MIX, wl.jitter())
+        return s
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.cf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_capsule(self, X, F, kS, C_, kB, kV, mass, mode):
+        X = np.ascontiguousarray(X, np.float64)
+        F = np.ascontiguousarray(F, np.int32)
+        d = CapsuleDesc(X.shape[0], F.shape[0], _ptr(X), F.ctypes.data_as(C.POINTER(C.c_int)),
+                        kS, C_, kB, kV, mass, mode)
+        cid = C.c_int()
+        _check(_lib.cf_add_capsule(self._h, C.byref(d), C.byref(cid)))
+        self.nv.append(X.shape[0])
+        return cid.value
+
+    def set_capsule_mode(self, cid, mode):
+        _check(_lib.cf_set_capsule_mode(self._h, cid, mode))
+
+    def set_film(self, h_top, rho_maj, rho_min, rho_mix, jit=None):
+        j = None if jit is None else np.ascontiguousarray(jit, np.float64).reshape(-1)
+        _check(_lib.cf_set_film(self._h, h_top, rho_maj, rho_min, rho_mix, _ptr(j)))
+
+    def step(self, n=1):
+        _check(_lib.cf_step(self._h, int(n)))
+
+    def sync(self):
+        _check(_lib.cf_sync(self._h))
+
+    def launches(self):
+        n = C.c_longlong()
+        _check(_lib.cf_launch_count(self._h, C.byref(n)))
+        return n.value
+
+    def capsule_force(self, cid):
+        F = np.zeros(3); T = np.zeros(3)
+        _check(_lib.cf_capsule_force(self._h, cid, _ptr(F), _ptr(T)))
+        return F, T
+
+    def lateral_force(self, a, b):
+        F = np.zeros(1)
+        _check(_lib.cf_lateral_force(self._h, a, b, _ptr(F)))
+        return float(F[0])
+
+    def capsule_state(self, cid):
+        X = np.zeros((self.nv[cid], 3)); A = np.zeros(1); V = np.zeros(1)
+        _check(_lib.cf_capsule_state(self._h, cid, _ptr(X), _ptr(A), _ptr(V)))
+        return dict(X=X, area=float(A[0]), volume=float(V[0]))
+
+    def fields(self):
+        rho = np.zeros((2, self.nz, self.ny, self.nx))
+        u = np.zeros((3, self.nz, self.ny, self.nx))
+        _check(_lib.cf_fields(self._h, _ptr(rho), _ptr(u)))
+        return rho, u
+
+    def populations(self):
+        f = np.zeros((2, 19, self.nz, self.ny, self.nx), np.float32)
+        _check(_lib.cf_populations(self._h, _ptr(f, _fp)))
+        return f
+
+    def total_mass(self):
+        m = np.zeros(2)
+        _check(_lib.cf_total_mass(self._h, _ptr(m)))
+        return m
+
+    def meniscus_field(self):
+        h = np.zeros((self.ny, self.nx))
+        _check(_lib.cf_meniscus_field(self._h, _ptr(h)))
+        return h
+
+    def meniscus_profile(self, cid):
+        n = C.c_size_t(0)
+        rc = _lib.cf_meniscus_profile(self._h, cid, None, None, C.byref(n), None)
+        r = np.zeros(n.value); z = np.zeros(n.value); Z = np.zeros(1)
+        _check(_lib.cf_meniscus_profile(self._h, cid, _ptr(r), _ptr(z), C.byref(n), _ptr(Z)))
+        return r, z, float(Z[0])
+
+    def cuts(self):
+        mask = np.zeros((self.nz, self.ny, self.nx), np.uint32)
+        tri = np.zeros((self.nz, self.ny, self.nx, 18), np.int32)
+        ins = np.zeros((self.nz, self.ny, self.nx), np.uint8)
+        _check(_lib.cf_cuts(self._h, mask.ctypes.data_as(C.POINTER(C.c_uint32)),
+                            tri.ctypes.data_as(C.POINTER(C.c_int)),
+                            ins.ctypes.data_as(C.POINTER(C.c_uint8))))
+        return mask, tri, ins

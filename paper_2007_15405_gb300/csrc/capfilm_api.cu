@@ -1,0 +1,743 @@
+// Host runtime of the capfilm C ABI (include/capfilm.h).
+//
+// Owns the device state of one lattice with its capsules, queues the kernels
+// of a coupled step on the context stream and replays pairs of steps from a
+// captured CUDA graph (a pair returns every double buffer to its starting
+// parity, so one graph serves any even number of steps).
+#include "../../include/capfilm.h"
+#include "cf_common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace cf;
+
+namespace {
+
+thread_local std::string g_err;
+
+cf_status fail(cf_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+#define CF_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(CF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+    } while (0)
+
+struct HostCapsule {
+    int nv, nf, mode;
+    double kS, C, kB, kV, mass;
+    std::vector<float> X;      // reference positions (float)
+    std::vector<int> F;        // local faces
+};
+
+}  // namespace
+
+struct cf_ctx {
+    cf_lattice_desc d{};
+    long long N = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cf_allocator alloc{};
+    bool has_alloc = false;
+    std::vector<void *> allocations;
+
+    float *f[2] = {nullptr, nullptr};
+    int fpar = 0;
+    float *out = nullptr;
+    uint32_t *mask = nullptr;
+    int *tri = nullptr;
+    uint32_t *touched = nullptr;
+    uint8_t *inside = nullptr;
+    int *list[2] = {nullptr, nullptr};
+    int *counts = nullptr;  // [2]
+    int lpar = 0;
+    int capacity = 0;
+    unsigned *status = nullptr;
+    double *dscratch = nullptr;  // small FP64 scratch (mass)
+    float *hscratch = nullptr;   // meniscus field [nx*ny]
+    double *jit = nullptr;
+
+    // membrane (all capsules concatenated)
+    std::vector<HostCapsule> caps;
+    int nnodes = 0, nfaces = 0;
+    bool any_frozen = false, all_fixed = true;
+    float *X[2] = {nullptr, nullptr};
+    int xpar = 0;
+    float *V = nullptr, *FT = nullptr, *FTprev = nullptr, *fscr = nullptr, *vscr = nullptr,
+          *Fcpl = nullptr, *refM = nullptr, *refA = nullptr, *refDet = nullptr;
+    int *faces = nullptr, *face_cap = nullptr, *node_cap = nullptr, *vf_off = nullptr,
+        *vf_ent = nullptr, *bbox = nullptr;
+    CapDev *capdev = nullptr;
+    double *acc = nullptr;
+    std::vector<void *> mem_allocs;
+
+    bool film_set = false;
+    long long steps_done = 0;
+    long long launches_last = 0;
+    int lb_variant = 0;
+    int zchunk = 0;
+
+    cudaGraphExec_t graph = nullptr;
+    int graph_key = -1;
+};
+
+namespace {
+
+void *dalloc(cf_ctx *c, size_t bytes, bool membrane = false) {
+    void *p = nullptr;
+    bytes = std::max<size_t>(bytes, 256);
+    if (c->has_alloc) {
+        p = c->alloc.alloc(bytes, c->stream, c->alloc.user);
+    } else {
+        if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) p = nullptr;
+    }
+    if (p) (membrane ? c->mem_allocs : c->allocations).push_back(p);
+    return p;
+}
+
+void dfree(cf_ctx *c, void *p) {
+    if (!p) return;
+    if (c->has_alloc) c->alloc.free(p, c->stream, c->alloc.user);
+    else cudaFreeAsync(p, c->stream);
+}
+
+cf_status check_status(cf_ctx *c) {
+    unsigned st = 0;
+    CF_CUDA(cudaMemcpyAsync(&st, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CF_CUDA(cudaStreamSynchronize(c->stream));
+    if (st) {
+        CF_CUDA(cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
+        if (st & ST_NAN) return fail(CF_EDIVERGED, "non-finite density in the lattice");
+        if (st & ST_OVERFLOW) return fail(CF_EOVERFLOW, "cut-link node list exceeded its capacity");
+    }
+    return CF_OK;
+}
+
+LBParams lb_params(cf_ctx *c, bool with_out) {
+    LBParams p{};
+    p.nx = c->d.nx; p.ny = c->d.ny; p.nz = c->d.nz; p.wall = c->d.wall;
+    p.N = c->N;
+    p.zlo = c->d.wall ? 1 : 0;
+    p.zhi = c->d.nz;
+    p.zchunk = c->zchunk;
+    for (int k = 0; k < 2; ++k) {
+        p.tau[k] = (float)c->d.tau[k];
+        p.itau[k] = (float)(1.0 / c->d.tau[k]);
+    }
+    p.G = (float)c->d.G;
+    p.src = c->f[c->fpar];
+    p.dst = c->f[1 - c->fpar];
+    p.mask = c->mask;
+    p.tri = c->tri;
+    p.faces = c->faces;
+    p.V = c->V;
+    p.FT = c->FT;
+    p.out = with_out ? c->out : nullptr;
+    p.status = c->status;
+    return p;
+}
+
+MemParams mem_params(cf_ctx *c) {
+    MemParams p{};
+    p.nx = c->d.nx; p.ny = c->d.ny; p.nz = c->d.nz; p.wall = c->d.wall;
+    p.ncaps = (int)c->caps.size();
+    p.nfaces = c->nfaces;
+    p.nnodes = c->nnodes;
+    p.zrep = (float)(0.5 + c->d.rep_dz);
+    p.xi = (float)c->d.xi;
+    p.delta0 = (float)c->d.delta0;
+    p.caps = c->capdev;
+    p.faces = c->faces;
+    p.face_cap = c->face_cap;
+    p.node_cap = c->node_cap;
+    p.refM = c->refM; p.refA = c->refA; p.refDet = c->refDet;
+    p.vf_off = c->vf_off; p.vf_ent = c->vf_ent;
+    p.X = c->X[c->xpar];
+    p.Xn = c->X[1 - c->xpar];
+    p.V = c->V;
+    p.FT = c->FT;
+    p.FTprev = c->FTprev;
+    p.fscr = c->fscr;
+    p.vscr = c->vscr;
+    p.Fcpl = c->Fcpl;
+    p.acc = c->acc;
+    p.bbox = c->bbox;
+    return p;
+}
+
+// Cut links for positions X (cur list lpar, clears the other list's nodes).
+cf_status enqueue_cuts(cf_ctx *c, const float *X, int *nl) {
+    if (c->nfaces == 0) return CF_OK;
+    const int cur = 1 - c->lpar;
+    CutParams q{};
+    q.nx = c->d.nx; q.ny = c->d.ny; q.nz = c->d.nz; q.wall = c->d.wall;
+    q.nfaces = c->nfaces;
+    q.faces = c->faces;
+    q.X = X;
+    q.mask = c->mask;
+    q.tri = c->tri;
+    q.touched = c->touched;
+    q.list = c->list[cur];
+    q.count = c->counts + cur;
+    q.prev_count = c->counts + c->lpar;
+    q.prev_list = c->list[c->lpar];
+    q.capacity = c->capacity;
+    q.status = c->status;
+    CF_CUDA(cudaMemsetAsync(c->counts + cur, 0, sizeof(int), c->stream));
+    CF_CUDA(launch_cuts(q, 0, c->stream, nl));
+    c->lpar = cur;
+    return CF_OK;
+}
+
+// One coupled step on the stream (also used under graph capture).
+cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl) {
+    CF_CUDA(launch_lb_step(lb_params(c, with_out), c->lb_variant, c->stream));
+    *nl += 1;
+    c->fpar = 1 - c->fpar;
+    if (c->nnodes) {
+        const int nc = (int)c->caps.size();
+        CF_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(double) * A_NACC * nc, c->stream));
+        CF_CUDA(cudaMemsetAsync(c->bbox, 0x7f, sizeof(int) * 3 * nc, c->stream));
+        CF_CUDA(cudaMemsetAsync(c->bbox + 3 * nc, 0x80, sizeof(int) * 3 * nc, c->stream));
+        CF_CUDA(launch_membrane(mem_params(c), c->any_frozen, c->stream, nl));
+        c->xpar = 1 - c->xpar;
+        if (!c->all_fixed) {
+            cf_status s = enqueue_cuts(c, c->X[c->xpar], nl);
+            if (s != CF_OK) return s;
+        }
+    }
+    return CF_OK;
+}
+
+void choose_launch(cf_ctx *c) {
+    // tiles of 32 x 4 columns; split z so that the grid covers the GPU several
+    // times over (152 SMs, 2+ CTAs each)
+    const int tiles = ((c->d.nx + 31) / 32) * ((c->d.ny + 3) / 4);
+    const int nzf = c->d.nz - (c->d.wall ? 1 : 0);
+    const int target = 152 * 4;
+    int chunks = std::max(1, std::min(nzf / 4, (target + tiles - 1) / tiles));
+    c->zchunk = std::max(1, (nzf + chunks - 1) / chunks);
+    c->lb_variant = 0;
+}
+
+cf_status build_membrane(cf_ctx *c) {
+    for (void *p : c->mem_allocs) dfree(c, p);
+    c->mem_allocs.clear();
+    const int nc = (int)c->caps.size();
+    int nv = 0, nf = 0;
+    for (auto &h : c->caps) { nv += h.nv; nf += h.nf; }
+    c->nnodes = nv;
+    c->nfaces = nf;
+    c->any_frozen = false;
+    c->all_fixed = true;
+    for (auto &h : c->caps) {
+        c->any_frozen |= h.mode == CF_FROZEN;
+        c->all_fixed &= h.mode == CF_FIXED;
+    }
+    std::vector<float> X(3 * (size_t)nv), refM(3 * (size_t)nf), refA(nf), refDet(nf);
+    std::vector<int> faces(3 * (size_t)nf), face_cap(nf), node_cap(nv);
+    std::vector<CapDev> cd(nc);
+    std::vector<std::vector<int>> vf(nv);
+    int v0 = 0, f0 = 0;
+    for (int k = 0; k < nc; ++k) {
+        const HostCapsule &h = c->caps[k];
+        CapDev &d = cd[k];
+        d.kS = (float)h.kS; d.C = (float)h.C; d.kB = (float)h.kB; d.kV = (float)h.kV;
+        d.mass = (float)h.mass; d.mode = h.mode;
+        d.v0 = v0; d.nv = h.nv; d.f0 = f0; d.nf = h.nf;
+        double V0 = 0.0;
+        for (int i = 0; i < h.nv; ++i) {
+            for (int a = 0; a < 3; ++a) X[3 * (size_t)(v0 + i) + a] = h.X[3 * i + a];
+            node_cap[v0 + i] = k;
+        }
+        for (int f = 0; f < h.nf; ++f) {
+            const int ia = h.F[3 * f], ib = h.F[3 * f + 1], ic = h.F[3 * f + 2];
+            faces[3 * (size_t)(f0 + f)] = v0 + ia;
+            faces[3 * (size_t)(f0 + f) + 1] = v0 + ib;
+            faces[3 * (size_t)(f0 + f) + 2] = v0 + ic;
+            face_cap[f0 + f] = k;
+            vf[v0 + ia].push_back(3 * (f0 + f) + 0);
+            vf[v0 + ib].push_back(3 * (f0 + f) + 1);
+            vf[v0 + ic].push_back(3 * (f0 + f) + 2);
+            double a[3], b[3], cc[3], u[3], w[3];
+            for (int q = 0; q < 3; ++q) {
+                a[q] = h.X[3 * ia + q]; b[q] = h.X[3 * ib + q]; cc[q] = h.X[3 * ic + q];
+                u[q] = b[q] - a[q]; w[q] = cc[q] - a[q];
+            }
+            const double g11 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+            const double g12 = u[0] * w[0] + u[1] * w[1] + u[2] * w[2];
+            const double g22 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+            const double det = g11 * g22 - g12 * g12;
+            refM[3 * (size_t)(f0 + f)] = (float)(g22 / det);
+            refM[3 * (size_t)(f0 + f) + 1] = (float)(-g12 / det);
+            refM[3 * (size_t)(f0 + f) + 2] = (float)(g11 / det);
+            refDet[f0 + f] = (float)det;
+            refA[f0 + f] = (float)(0.5 * std::sqrt(det));
+            const double n0 = b[1] * cc[2] - b[2] * cc[1], n1 = b[2] * cc[0] - b[0] * cc[2],
+                         n2 = b[0] * cc[1] - b[1] * cc[0];
+            V0 += (a[0] * n0 + a[1] * n1 + a[2] * n2) / 6.0;
+        }
+        d.V0 = V0;
+        v0 += h.nv;
+        f0 += h.nf;
+    }
+    std::vector<int> vf_off(nv + 1, 0), vf_ent;
+    for (int v = 0; v < nv; ++v) {
+        vf_off[v + 1] = vf_off[v] + (int)vf[v].size();
+        for (int e : vf[v]) vf_ent.push_back(e);
+    }
+    auto up = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream);
+    };
+#define MALLOC_M(ptr, T, n)                                                          \
+    do {                                                                             \
+        ptr = (T *)dalloc(c, sizeof(T) * (size_t)(n), true);                         \
+        if (!ptr) return fail(CF_ENOMEM, "device allocation failed (membrane)");     \
+    } while (0)
+    MALLOC_M(c->X[0], float, 3 * nv);
+    MALLOC_M(c->X[1], float, 3 * nv);
+    MALLOC_M(c->V, float, 3 * nv);
+    MALLOC_M(c->Fcpl, float, 3 * nv);
+    MALLOC_M(c->vscr, float, 4 * nv);
+    MALLOC_M(c->FT, float, 3 * nf);
+    MALLOC_M(c->FTprev, float, 3 * nf);
+    MALLOC_M(c->fscr, float, (size_t)FS_N * nf);
+    MALLOC_M(c->refM, float, 3 * nf);
+    MALLOC_M(c->refA, float, nf);
+    MALLOC_M(c->refDet, float, nf);
+    MALLOC_M(c->faces, int, 3 * nf);
+    MALLOC_M(c->face_cap, int, nf);
+    MALLOC_M(c->node_cap, int, nv);
+    MALLOC_M(c->vf_off, int, nv + 1);
+    MALLOC_M(c->vf_ent, int, vf_ent.size());
+    MALLOC_M(c->bbox, int, 6 * nc);
+    MALLOC_M(c->capdev, CapDev, nc);
+    MALLOC_M(c->acc, double, A_NACC * nc);
+#undef MALLOC_M
+    c->xpar = 0;
+    CF_CUDA(up(c->X[0], X.data(), sizeof(float) * X.size()));
+    CF_CUDA(up(c->X[1], X.data(), sizeof(float) * X.size()));
+    CF_CUDA(cudaMemsetAsync(c->V, 0, sizeof(float) * 3 * nv, c->stream));
+    CF_CUDA(cudaMemsetAsync(c->Fcpl, 0, sizeof(float) * 3 * nv, c->stream));
+    CF_CUDA(cudaMemsetAsync(c->FT, 0, sizeof(float) * 3 * nf, c->stream));
+    CF_CUDA(cudaMemsetAsync(c->FTprev, 0, sizeof(float) * 3 * nf, c->stream));
+    CF_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(double) * A_NACC * nc, c->stream));
+    CF_CUDA(up(c->refM, refM.data(), sizeof(float) * refM.size()));
+    CF_CUDA(up(c->refA, refA.data(), sizeof(float) * refA.size()));
+    CF_CUDA(up(c->refDet, refDet.data(), sizeof(float) * refDet.size()));
+    CF_CUDA(up(c->faces, faces.data(), sizeof(int) * faces.size()));
+    CF_CUDA(up(c->face_cap, face_cap.data(), sizeof(int) * face_cap.size()));
+    CF_CUDA(up(c->node_cap, node_cap.data(), sizeof(int) * node_cap.size()));
+    CF_CUDA(up(c->vf_off, vf_off.data(), sizeof(int) * vf_off.size()));
+    CF_CUDA(up(c->vf_ent, vf_ent.data(), sizeof(int) * vf_ent.size()));
+    CF_CUDA(up(c->capdev, cd.data(), sizeof(CapDev) * cd.size()));
+    // cut-link node lists: nodes within one link of any element
+    c->capacity = (int)std::min<long long>(c->N, 24LL * nf + 4096);
+    for (int k = 0; k < 2; ++k) {
+        c->list[k] = (int *)dalloc(c, sizeof(int) * (size_t)c->capacity, true);
+        if (!c->list[k]) return fail(CF_ENOMEM, "device allocation failed (cut lists)");
+    }
+    // start from a clean cut structure
+    CF_CUDA(cudaMemsetAsync(c->mask, 0, sizeof(uint32_t) * c->N, c->stream));
+    CF_CUDA(cudaMemsetAsync(c->touched, 0, sizeof(uint32_t) * c->N, c->stream));
+    CF_CUDA(cudaMemsetAsync(c->tri, 0x7f, sizeof(int) * 18 * (size_t)c->N, c->stream));
+    CF_CUDA(cudaMemsetAsync(c->counts, 0, sizeof(int) * 2, c->stream));
+    // 0x7f7f7f7f is not INT_MAX but any value above every element index works
+    int nl = 0;
+    cf_status s = enqueue_cuts(c, c->X[c->xpar], &nl);
+    if (s != CF_OK) return s;
+    CF_CUDA(launch_inside(c->mask, c->inside, c->d.nx, c->d.ny, c->d.nz, c->stream));
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_key = -1; }
+    return CF_OK;
+}
+
+cf_status sync_ok(cf_ctx *c) {
+    CF_CUDA(cudaStreamSynchronize(c->stream));
+    return check_status(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cf_last_error(void) { return g_err.c_str(); }
+
+cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
+    if (!desc || !out) return fail(CF_EINVAL, "null argument");
+    if (desc->nx < 3 || desc->ny < 3 || desc->nz < 3) return fail(CF_EINVAL, "lattice dimensions must be >= 3");
+    if ((long long)desc->nx * desc->ny * desc->nz > (1LL << 30)) return fail(CF_EINVAL, "lattice too large");
+    if (!(desc->tau[0] > 0.5) || !(desc->tau[1] > 0.5)) return fail(CF_EINVAL, "tau must exceed 1/2");
+    if (desc->precision != CF_FP32) return fail(CF_EINVAL, "unsupported precision");
+    cf_ctx *c = new cf_ctx();
+    c->d = *desc;
+    c->N = (long long)desc->nx * desc->ny * desc->nz;
+    if (desc->allocator) {
+        c->alloc = *desc->allocator;
+        c->has_alloc = c->alloc.alloc && c->alloc.free;
+    }
+    if (desc->stream) c->stream = (cudaStream_t)desc->stream;
+    else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return fail(CF_ECUDA, "cudaStreamCreate failed");
+        }
+        c->own_stream = true;
+    }
+    const long long N = c->N;
+    c->f[0] = (float *)dalloc(c, sizeof(float) * 38 * N);
+    c->f[1] = (float *)dalloc(c, sizeof(float) * 38 * N);
+    c->out = (float *)dalloc(c, sizeof(float) * 5 * N);
+    c->mask = (uint32_t *)dalloc(c, sizeof(uint32_t) * N);
+    c->tri = (int *)dalloc(c, sizeof(int) * 18 * N);
+    c->touched = (uint32_t *)dalloc(c, sizeof(uint32_t) * N);
+    c->inside = (uint8_t *)dalloc(c, N);
+    c->counts = (int *)dalloc(c, sizeof(int) * 2);
+    c->status = (unsigned *)dalloc(c, sizeof(unsigned));
+    c->dscratch = (double *)dalloc(c, sizeof(double) * 8);
+    c->hscratch = (float *)dalloc(c, sizeof(float) * desc->nx * desc->ny);
+    if (!c->f[0] || !c->f[1] || !c->out || !c->mask || !c->tri || !c->touched || !c->inside ||
+        !c->counts || !c->status || !c->dscratch || !c->hscratch) {
+        cf_destroy(c);
+        return fail(CF_ENOMEM, "device allocation failed");
+    }
+    cudaMemsetAsync(c->f[0], 0, sizeof(float) * 38 * N, c->stream);
+    cudaMemsetAsync(c->f[1], 0, sizeof(float) * 38 * N, c->stream);
+    cudaMemsetAsync(c->out, 0, sizeof(float) * 5 * N, c->stream);
+    cudaMemsetAsync(c->mask, 0, sizeof(uint32_t) * N, c->stream);
+    cudaMemsetAsync(c->tri, 0x7f, sizeof(int) * 18 * N, c->stream);
+    cudaMemsetAsync(c->touched, 0, sizeof(uint32_t) * N, c->stream);
+    cudaMemsetAsync(c->inside, 0, N, c->stream);
+    cudaMemsetAsync(c->counts, 0, sizeof(int) * 2, c->stream);
+    cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cf_destroy(c);
+        return fail(CF_ECUDA, std::string("set-up: ") + cudaGetErrorString(e));
+    }
+    choose_launch(c);
+    *out = c;
+    return CF_OK;
+}
+
+cf_status cf_destroy(cf_ctx *c) {
+    if (!c) return CF_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (void *p : c->mem_allocs) dfree(c, p);
+    for (void *p : c->allocations) dfree(c, p);
+    if (c->jit) dfree(c, c->jit);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return CF_OK;
+}
+
+cf_status cf_add_capsule(cf_ctx *c, const cf_capsule_desc *d, int *id) {
+    if (!c || !d || !d->nodes || !d->faces) return fail(CF_EINVAL, "null argument");
+    if (d->nv < 4 || d->nf < 4) return fail(CF_EINVAL, "capsule mesh too small");
+    if (d->mode < 0 || d->mode > 2) return fail(CF_EINVAL, "bad capsule mode");
+    if (!(d->mass > 0)) return fail(CF_EINVAL, "node mass must be positive");
+    if (c->film_set) return fail(CF_ESTATE, "capsules must be added before cf_set_film");
+    HostCapsule h;
+    h.nv = d->nv; h.nf = d->nf; h.mode = d->mode;
+    h.kS = d->kS; h.C = d->C; h.kB = d->kB; h.kV = d->kV; h.mass = d->mass;
+    h.X.resize(3 * (size_t)d->nv);
+    for (size_t i = 0; i < h.X.size(); ++i) h.X[i] = (float)d->nodes[i];
+    h.F.assign(d->faces, d->faces + 3 * (size_t)d->nf);
+    for (int v : h.F)
+        if (v < 0 || v >= d->nv) return fail(CF_EINVAL, "face index out of range");
+    c->caps.push_back(h);
+    cf_status s = build_membrane(c);
+    if (s != CF_OK) { c->caps.pop_back(); return s; }
+    if (id) *id = (int)c->caps.size() - 1;
+    return sync_ok(c);
+}
+
+cf_status cf_set_capsule_mode(cf_ctx *c, int id, int mode) {
+    if (!c) return fail(CF_EINVAL, "null context");
+    if (id < 0 || id >= (int)c->caps.size()) return fail(CF_ENOTFOUND, "unknown capsule");
+    if (mode < 0 || mode > 2) return fail(CF_EINVAL, "bad capsule mode");
+    CF_CUDA(cudaStreamSynchronize(c->stream));
+    c->caps[id].mode = mode;
+    CapDev d;
+    CF_CUDA(cudaMemcpy(&d, c->capdev + id, sizeof(CapDev), cudaMemcpyDeviceToHost));
+    d.mode = mode;
+    CF_CUDA(cudaMemcpy(c->capdev + id, &d, sizeof(CapDev), cudaMemcpyHostToDevice));
+    c->any_frozen = false;
+    c->all_fixed = true;
+    for (auto &h : c->caps) {
+        c->any_frozen |= h.mode == CF_FROZEN;
+        c->all_fixed &= h.mode == CF_FIXED;
+    }
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_key = -1; }
+    return CF_OK;
+}
+
+cf_status cf_set_film(cf_ctx *c, double h_top, double rmaj, double rmin, double rmix,
+                      const double *jitter) {
+    if (!c) return fail(CF_EINVAL, "null context");
+    const long long N = c->N;
+    const double *djit = nullptr;
+    if (jitter) {
+        if (!c->jit) {
+            c->jit = (double *)dalloc(c, sizeof(double) * 2 * N);
+            if (!c->jit) return fail(CF_ENOMEM, "device allocation failed (jitter)");
+            c->allocations.pop_back();  // freed explicitly
+        }
+        CF_CUDA(cudaMemcpyAsync(c->jit, jitter, sizeof(double) * 2 * N, cudaMemcpyHostToDevice, c->stream));
+        djit = c->jit;
+    }
+    if (c->nfaces) CF_CUDA(launch_inside(c->mask, c->inside, c->d.nx, c->d.ny, c->d.nz, c->stream));
+    CF_CUDA(launch_init_film(c->f[c->fpar], N, c->d.nx, c->d.ny, c->d.nz, c->d.wall, (float)h_top,
+                             (float)rmaj, (float)rmin, (float)rmix, djit, c->inside, c->stream));
+    c->film_set = true;
+    return sync_ok(c);
+}
+
+cf_status cf_step(cf_ctx *c, long long n) {
+    if (!c) return fail(CF_EINVAL, "null context");
+    if (!c->film_set) return fail(CF_ESTATE, "cf_set_film must come before cf_step");
+    if (n < 0) return fail(CF_EINVAL, "negative step count");
+    if (n == 0) return CF_OK;
+    int nl = 0;
+    long long left = n - 1;  // the last step records the fields
+    if (left >= 2) {
+        const int key = c->fpar | (c->xpar << 1) | (c->lpar << 2);
+        if (!c->graph || c->graph_key != key) {
+            if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+            cudaGraph_t g;
+            CF_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            int nlg = 0;
+            cf_status s1 = enqueue_step(c, false, &nlg);
+            cf_status s2 = s1 == CF_OK ? enqueue_step(c, false, &nlg) : s1;
+            cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+            if (s2 != CF_OK) return s2;
+            if (e != cudaSuccess) return fail(CF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&c->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fail(CF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+            c->graph_key = key;
+        }
+        int per_pair = 0;
+        {
+            // count the launches of one step pair (for reporting)
+            const bool fx = c->all_fixed;
+            per_pair = 2 * (1 + (c->nnodes ? 4 + (c->any_frozen ? 1 : 0) + (fx ? 0 : 2) : 0));
+        }
+        while (left >= 2) {
+            CF_CUDA(cudaGraphLaunch(c->graph, c->stream));
+            left -= 2;
+            nl += per_pair;
+        }
+    }
+    while (left > 0) {
+        cf_status s = enqueue_step(c, false, &nl);
+        if (s != CF_OK) return s;
+        --left;
+    }
+    cf_status s = enqueue_step(c, true, &nl);
+    if (s != CF_OK) return s;
+    c->steps_done += n;
+    c->launches_last = nl;
+    return CF_OK;
+}
+
+cf_status cf_sync(cf_ctx *c) {
+    if (!c) return fail(CF_EINVAL, "null context");
+    return sync_ok(c);
+}
+
+cf_status cf_launch_count(cf_ctx *c, long long *n) {
+    if (!c || !n) return fail(CF_EINVAL, "null argument");
+    *n = c->launches_last;
+    return CF_OK;
+}
+
+static cf_status read_acc(cf_ctx *c, std::vector<double> &acc) {
+    const int nc = (int)c->caps.size();
+    acc.assign((size_t)A_NACC * nc, 0.0);
+    if (!nc) return CF_OK;
+    CF_CUDA(cudaMemcpyAsync(acc.data(), c->acc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost, c->stream));
+    return sync_ok(c);
+}
+
+cf_status cf_capsule_force(cf_ctx *c, int id, double F[3], double T[3]) {
+    if (!c) return fail(CF_EINVAL, "null context");
+    if (id < 0 || id >= (int)c->caps.size()) return fail(CF_ENOTFOUND, "unknown capsule");
+    std::vector<double> acc;
+    cf_status s = read_acc(c, acc);
+    if (s != CF_OK) return s;
+    for (int a = 0; a < 3; ++a) {
+        if (F) F[a] = acc[(size_t)id * A_NACC + A_FX + a];
+        if (T) T[a] = acc[(size_t)id * A_NACC + A_TX + a];
+    }
+    return CF_OK;
+}
+
+cf_status cf_lateral_force(cf_ctx *c, int a, int b, double *F) {
+    if (!c || !F) return fail(CF_EINVAL, "null argument");
+    const int nc = (int)c->caps.size();
+    if (a < 0 || a >= nc || b < 0 || b >= nc || a == b) return fail(CF_ENOTFOUND, "unknown capsule pair");
+    std::vector<double> acc;
+    cf_status s = read_acc(c, acc);
+    if (s != CF_OK) return s;
+    const double *A = &acc[(size_t)a * A_NACC], *B = &acc[(size_t)b * A_NACC];
+    double dx = B[A_CX] / c->caps[b].nv - A[A_CX] / c->caps[a].nv;
+    double dy = B[A_CY] / c->caps[b].nv - A[A_CY] / c->caps[a].nv;
+    dx -= c->d.nx * std::floor(dx / c->d.nx + 0.5);
+    dy -= c->d.ny * std::floor(dy / c->d.ny + 0.5);
+    const double L = std::sqrt(dx * dx + dy * dy);
+    if (!(L > 0)) return fail(CF_EINVAL, "capsule centroids coincide in the xy plane");
+    *F = 0.5 * ((B[A_FX] - A[A_FX]) * dx + (B[A_FY] - A[A_FY]) * dy) / L;
+    return CF_OK;
+}
+
+cf_status cf_capsule_state(cf_ctx *c, int id, double *nodes, double *area, double *volume) {
+    if (!c) return fail(CF_EINVAL, "null context");
+    if (id < 0 || id >= (int)c->caps.size()) return fail(CF_ENOTFOUND, "unknown capsule");
+    int v0 = 0;
+    for (int k = 0; k < id; ++k) v0 += c->caps[k].nv;
+    const int nv = c->caps[id].nv;
+    if (nodes) {
+        std::vector<float> X(3 * (size_t)nv);
+        CF_CUDA(cudaMemcpyAsync(X.data(), c->X[c->xpar] + 3 * (size_t)v0, sizeof(float) * X.size(),
+                                cudaMemcpyDeviceToHost, c->stream));
+        cf_status s = sync_ok(c);
+        if (s != CF_OK) return s;
+        for (size_t i = 0; i < X.size(); ++i) nodes[i] = X[i];
+    }
+    if (area || volume) {
+        std::vector<double> acc;
+        cf_status s = read_acc(c, acc);
+        if (s != CF_OK) return s;
+        if (area) *area = acc[(size_t)id * A_NACC + A_AREA];
+        if (volume) *volume = acc[(size_t)id * A_NACC + A_VOL];
+    }
+    return CF_OK;
+}
+
+cf_status cf_fields(cf_ctx *c, double *rho, double *u) {
+    if (!c) return fail(CF_EINVAL, "null context");
+    const long long N = c->N;
+    std::vector<float> h(5 * (size_t)N);
+    CF_CUDA(cudaMemcpyAsync(h.data(), c->out, sizeof(float) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+    cf_status s = sync_ok(c);
+    if (s != CF_OK) return s;
+    if (rho) for (long long i = 0; i < 2 * N; ++i) rho[i] = h[i];
+    if (u) for (long long i = 0; i < 3 * N; ++i) u[i] = h[2 * N + i];
+    return CF_OK;
+}
+
+cf_status cf_populations(cf_ctx *c, float *f) {
+    if (!c || !f) return fail(CF_EINVAL, "null argument");
+    CF_CUDA(cudaMemcpyAsync(f, c->f[c->fpar], sizeof(float) * 38 * c->N, cudaMemcpyDeviceToHost, c->stream));
+    return sync_ok(c);
+}
+
+cf_status cf_total_mass(cf_ctx *c, double m[2]) {
+    if (!c || !m) return fail(CF_EINVAL, "null argument");
+    CF_CUDA(cudaMemsetAsync(c->dscratch, 0, sizeof(double) * 2, c->stream));
+    CF_CUDA(launch_mass(c->f[c->fpar], c->N, c->dscratch, c->stream));
+    CF_CUDA(cudaMemcpyAsync(m, c->dscratch, sizeof(double) * 2, cudaMemcpyDeviceToHost, c->stream));
+    return sync_ok(c);
+}
+
+cf_status cf_meniscus_field(cf_ctx *c, double *h) {
+    if (!c || !h) return fail(CF_EINVAL, "null argument");
+    const int nxy = c->d.nx * c->d.ny;
+    CF_CUDA(launch_inside(c->mask, c->inside, c->d.nx, c->d.ny, c->d.nz, c->stream));
+    CF_CUDA(launch_meniscus(c->out, c->inside, c->hscratch, c->d.nx, c->d.ny, c->d.nz, c->d.wall, c->stream));
+    std::vector<float> hf(nxy);
+    CF_CUDA(cudaMemcpyAsync(hf.data(), c->hscratch, sizeof(float) * nxy, cudaMemcpyDeviceToHost, c->stream));
+    cf_status s = sync_ok(c);
+    if (s != CF_OK) return s;
+    for (int i = 0; i < nxy; ++i) h[i] = hf[i];
+    return CF_OK;
+}
+
+cf_status cf_meniscus_profile(cf_ctx *c, int id, double *r, double *zeta, size_t *inout_n, double *Z) {
+    if (!c || !inout_n) return fail(CF_EINVAL, "null argument");
+    const int nc = (int)c->caps.size();
+    if (id < 0 || id >= nc) return fail(CF_ENOTFOUND, "unknown capsule");
+    const int nx = c->d.nx, ny = c->d.ny;
+    const size_t nr = (size_t)(std::min(nx, ny) / 2);
+    if (*inout_n < nr || !r || !zeta) { *inout_n = nr; return fail(CF_EINVAL, "profile buffer too small"); }
+    std::vector<double> h((size_t)nx * ny), acc;
+    cf_status s = cf_meniscus_field(c, h.data());
+    if (s != CF_OK) return s;
+    s = read_acc(c, acc);
+    if (s != CF_OK) return s;
+    std::vector<double> cx(nc), cy(nc);
+    for (int k = 0; k < nc; ++k) {
+        cx[k] = acc[(size_t)k * A_NACC + A_CX] / c->caps[k].nv;
+        cy[k] = acc[(size_t)k * A_NACC + A_CY] / c->caps[k].nv;
+    }
+    // far-field height: valid columns whose distance to the nearest capsule
+    // is at least 90 % of the largest such distance
+    std::vector<double> dmin((size_t)nx * ny);
+    double dmax = 0.0;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double best = 1e300;
+            for (int k = 0; k < nc; ++k) {
+                double dx = x - cx[k], dy = y - cy[k];
+                dx -= nx * std::floor(dx / nx + 0.5);
+                dy -= ny * std::floor(dy / ny + 0.5);
+                best = std::min(best, std::sqrt(dx * dx + dy * dy));
+            }
+            dmin[(size_t)y * nx + x] = best;
+            if (!std::isnan(h[(size_t)y * nx + x])) dmax = std::max(dmax, best);
+        }
+    double hs = 0.0;
+    int hc = 0;
+    for (size_t i = 0; i < h.size(); ++i)
+        if (!std::isnan(h[i]) && dmin[i] >= 0.9 * dmax) { hs += h[i]; ++hc; }
+    const double hinf = hc ? hs / hc : NAN;
+    const int x0 = (int)std::lround(cx[id]), y0 = (int)std::lround(cy[id]);
+    double zmax = -1e300;
+    for (size_t k = 0; k < nr; ++k) {
+        double s2 = 0.0;
+        int cnt = 0;
+        const int dxs[4] = {1, -1, 0, 0}, dys[4] = {0, 0, 1, -1};
+        for (int q = 0; q < 4; ++q) {
+            const int x = ((x0 + dxs[q] * (int)k) % nx + nx) % nx;
+            const int y = ((y0 + dys[q] * (int)k) % ny + ny) % ny;
+            const double v = h[(size_t)y * nx + x];
+            if (!std::isnan(v)) { s2 += v; ++cnt; }
+        }
+        r[k] = (double)k;
+        zeta[k] = cnt ? s2 / cnt - hinf : NAN;
+        if (cnt && zeta[k] > zmax) zmax = zeta[k];
+    }
+    *inout_n = nr;
+    if (Z) *Z = zmax;
+    return CF_OK;
+}
+
+cf_status cf_cuts(cf_ctx *c, uint32_t *mask, int *tri, uint8_t *inside) {
+    if (!c) return fail(CF_EINVAL, "null context");
+    const long long N = c->N;
+    if (mask) CF_CUDA(cudaMemcpyAsync(mask, c->mask, sizeof(uint32_t) * N, cudaMemcpyDeviceToHost, c->stream));
+    if (tri) CF_CUDA(cudaMemcpyAsync(tri, c->tri, sizeof(int) * 18 * N, cudaMemcpyDeviceToHost, c->stream));
+    if (inside) {
+        CF_CUDA(launch_inside(c->mask, c->inside, c->d.nx, c->d.ny, c->d.nz, c->stream));
+        CF_CUDA(cudaMemcpyAsync(inside, c->inside, N, cudaMemcpyDeviceToHost, c->stream));
+    }
+    cf_status s = sync_ok(c);
+    if (s != CF_OK) return s;
+    if (tri)
+        for (long long i = 0; i < 18 * N; ++i)
+            if (tri[i] >= c->nfaces || tri[i] < 0) tri[i] = -1;
+    return CF_OK;
+}
+
+}  // extern "C"

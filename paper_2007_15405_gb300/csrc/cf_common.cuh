@@ -1,0 +1,126 @@
+// Shared device definitions of the capfilm CUDA library (sm_103a).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cf {
+
+// D3Q19 (Sec. 3.1): rest, six face neighbours (w = 1/18), twelve edge
+// neighbours (w = 1/36); opposite directions are adjacent pairs.
+__host__ __device__ constexpr int ex(int i) {
+    return i == 1 ? 1 : i == 2 ? -1 : i == 7 ? 1 : i == 8 ? -1 : i == 9 ? 1 : i == 10 ? -1
+         : i == 11 ? 1 : i == 12 ? -1 : i == 13 ? 1 : i == 14 ? -1 : 0;
+}
+__host__ __device__ constexpr int ey(int i) {
+    return i == 3 ? 1 : i == 4 ? -1 : i == 7 ? 1 : i == 8 ? -1 : i == 9 ? -1 : i == 10 ? 1
+         : i == 15 ? 1 : i == 16 ? -1 : i == 17 ? 1 : i == 18 ? -1 : 0;
+}
+__host__ __device__ constexpr int ez(int i) {
+    return i == 5 ? 1 : i == 6 ? -1 : i == 11 ? 1 : i == 12 ? -1 : i == 13 ? -1 : i == 14 ? 1
+         : i == 15 ? 1 : i == 16 ? -1 : i == 17 ? -1 : i == 18 ? 1 : 0;
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr float wgt(int i) {
+    return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+}
+constexpr int Q = 19;
+
+// Parameters of the fused lattice kernel.
+struct LBParams {
+    int nx, ny, nz, wall;
+    long long N;            // nodes
+    int zlo, zhi;           // fluid planes [zlo, zhi)
+    int zchunk;             // planes per CTA
+    float itau[2], tau[2];  // 1/tau and tau per component
+    float G;
+    const float *__restrict__ src;   // post-collision populations of the last step
+    float *__restrict__ dst;         // post-collision populations of this step
+    const uint32_t *__restrict__ mask;  // cut bits per node
+    const int *__restrict__ tri;        // crossed element per node and link [N*18]
+    const int *__restrict__ faces;      // element nodes [3*nfaces]
+    const float *__restrict__ V;        // node velocities [3*nnodes]
+    float *__restrict__ FT;             // element momentum exchange accumulators [3*nfaces]
+    float *__restrict__ out;            // optional [5][N]: rhoA, rhoB, ux, uy, uz
+    unsigned *__restrict__ status;      // device error flags
+};
+
+enum StatusBits : unsigned { ST_OVERFLOW = 1u, ST_NAN = 2u };
+
+// Capsule description on the device.
+struct CapDev {
+    float kS, C, kB, kV, mass;
+    int mode;               // 0 free, 1 frozen, 2 fixed
+    int v0, nv, f0, nf;     // global offsets and counts
+    double V0;              // reference volume
+};
+
+// Per-capsule FP64 accumulators (reset each step).
+enum CapAcc { A_FX = 0, A_FY, A_FZ, A_TX, A_TY, A_TZ, A_AREA, A_VOL, A_CX, A_CY, A_CZ,
+              A_FTX, A_FTY, A_FTZ, A_NACC = 16 };
+
+struct MemParams {
+    int nx, ny, nz, wall;
+    int ncaps, nfaces, nnodes;
+    float zrep, xi, delta0;
+    const CapDev *caps;
+    const int *faces;        // [3*nf] global node ids
+    const int *face_cap;     // [nf]
+    const int *node_cap;     // [nv]
+    const float *refM;       // [3*nf] inverse reference metric
+    const float *refA;       // [nf]
+    const float *refDet;     // [nf]
+    const int *vf_off;       // [nv+1] vertex -> (face*3+slot) CSR
+    const int *vf_ent;
+    const float *X;          // [3*nv] positions of this step
+    float *Xn;               // [3*nv] positions of the next step
+    float *V;                // [3*nv] node velocities (written)
+    float *FT;               // [3*nf] exchange accumulated by the lattice kernel (zeroed here)
+    float *FTprev;           // [3*nf] exchange of the previous step
+    float *fscr;             // [nf*FS_N] per-element scratch
+    float *vscr;             // [nv*4] per-node scratch (gL, gA)
+    float *Fcpl;             // [3*nv] coupling force on nodes (readout)
+    double *acc;             // [ncaps*A_NACC]
+    int *bbox;               // [ncaps*3] mins then [ncaps*3] maxs (integer bounding boxes)
+};
+
+// per-element scratch layout (floats)
+enum FaceScr { FS_FBAR = 0, FS_SK = 3, FS_DV = 12, FS_L = 21, FS_AF3 = 30, FS_COT = 31,
+               FS_BEND = 34, FS_N = 43 };
+
+struct CutParams {
+    int nx, ny, nz, wall;
+    int nfaces;
+    const int *faces;
+    const float *X;          // positions the cut links are computed for
+    uint32_t *mask;
+    int *tri;
+    uint32_t *touched;       // [N] node listed flag
+    int *list;               // touched-node list
+    int *count;              // entries appended to `list` (zeroed before)
+    const int *prev_count;   // entries of `prev_list`
+    int *prev_list;          // list of the previous computation (cleared first)
+    int capacity;
+    unsigned *status;
+};
+
+__host__ __device__ inline int wrapi(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+}  // namespace cf
+
+// Host-side launchers (defined in the kernel translation units).
+namespace cf {
+cudaError_t launch_lb_step(const LBParams &p, int tx_variant, cudaStream_t s);
+cudaError_t launch_init_film(float *f, long long N, int nx, int ny, int nz, int wall,
+                             float h_top, float rmaj, float rmin, float rmix,
+                             const double *jit, const uint8_t *inside, cudaStream_t s);
+cudaError_t launch_inside(const uint32_t *mask, uint8_t *inside, int nx, int ny, int nz,
+                          cudaStream_t s);
+cudaError_t launch_meniscus(const float *out, const uint8_t *inside, float *h, int nx, int ny,
+                            int nz, int wall, cudaStream_t s);
+cudaError_t launch_mass(const float *f, long long N, double *m2, cudaStream_t s);
+cudaError_t launch_membrane(const MemParams &p, bool any_frozen, cudaStream_t s, int *nlaunch);
+cudaError_t launch_cuts(const CutParams &p, int prev_count_hint, cudaStream_t s, int *nlaunch);
+}  // namespace cf

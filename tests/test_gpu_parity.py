@@ -1,0 +1,164 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (float32 storage and arithmetic against float64):
+  densities      max |rho_gpu - rho_or| / max |rho_or|            < 1e-5
+  velocities     max |u_gpu - u_or| / max |u_or|                    < TOL_U
+  populations    max |f_gpu - f_or| / max |f_or|                    < 1e-5
+  cut links      bit-exact masks, elements and interior flags
+  capsule force  |F_gpu - F_or| / max(|F_or|)                       < 1e-3
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2007_15405_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL_RHO = 1e-5
+TOL_U = 2e-4
+
+
+@pytest.fixture(scope="module")
+def cfm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2007_15405_gb300 import build
+    build.build()
+    from paper_2007_15405_gb300 import capfilm
+    capfilm.load_library()
+    return capfilm
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def compare_state(sim, orc, tol_u=TOL_U, check_pops=True):
+    rg, ug = sim.fields()
+    ro, uo = orc.fields()
+    e_rho = rel(rg, ro)
+    e_u = rel(ug, uo)
+    assert e_rho < TOL_RHO, f"rho rel err {e_rho:.3e}"
+    assert e_u < tol_u, f"u rel err {e_u:.3e}"
+    if check_pops:
+        fg = sim.populations().astype(np.float64)
+        fo = orc.populations()
+        assert rel(fg, fo) < TOL_RHO, f"population rel err {rel(fg, fo):.3e}"
+    return e_rho, e_u
+
+
+def compare_cuts(sim, orc):
+    mg, tg, ig = sim.cuts()
+    mo, to, io = orc.cuts()
+    assert (mg == mo).all(), f"{(mg != mo).sum()} nodes differ in cut masks"
+    bits = ((mo[..., None] >> np.arange(18, dtype=np.uint32)) & 1).astype(bool)
+    assert (tg[bits] == to[bits]).all()
+    assert (ig == io).all()
+
+
+def test_rest_state_and_mass_no_capsule(cfm):
+    wl = I.Workload("rest", 40, 12, 10, h_top=4.5, capsules=[], steps=30)
+    sim = cfm.Simulation.from_workload(wl)
+    orc = O.Oracle.from_workload(wl)
+    m0 = sim.total_mass()
+    sim.step(30); orc.step(30)
+    compare_state(sim, orc)
+    assert np.allclose(sim.total_mass(), m0, rtol=1e-6)
+
+
+def test_cut_links_match_oracle(cfm):
+    for mode in (I.MODE_FIXED, I.MODE_FREE):
+        wl = I.tiny_film(mode=mode)
+        sim = cfm.Simulation.from_workload(wl)
+        orc = O.Oracle.from_workload(wl)
+        compare_cuts(sim, orc)
+
+
+@pytest.mark.parametrize("mode", [I.MODE_FIXED, I.MODE_FREE, I.MODE_FROZEN])
+def test_tiny_film_parity(cfm, mode):
+    wl = I.tiny_film(mode=mode, steps=40)
+    sim = cfm.Simulation.from_workload(wl)
+    orc = O.Oracle.from_workload(wl)
+    sim.step(wl.steps); orc.step(wl.steps)
+    compare_state(sim, orc)
+    sg = sim.capsule_state(0); so = orc.capsule_state(0)
+    assert np.abs(sg["X"] - so["X"]).max() < 1e-5
+    Fg, Tg = sim.capsule_force(0)
+    assert np.abs(Fg - so["force"]).max() < 1e-3 * np.abs(so["force"]).max() + 1e-7
+    assert abs(sg["area"] / so["area"] - 1) < 1e-6 and abs(sg["volume"] / so["volume"] - 1) < 1e-6
+    if mode != I.MODE_FIXED:
+        compare_cuts(sim, orc)
+
+
+def test_ragged_periodic_no_wall(cfm):
+    """Lattice not a multiple of the tile, fully periodic (no substrate),
+    capsule crossing the periodic x boundary."""
+    nx, ny, nz = 37, 13, 15
+    X, F = I.icosphere(2, 4.0, (nx - 1.3, 6.4, 7.17))
+    wl = I.Workload("ragged", nx, ny, nz, h_top=6.5, steps=25, wall=0, seed=5,
+                    capsules=[I.CapsuleSpec(centre=(nx - 1.3, 6.4, 7.17), radius=4.0, level=2,
+                                            kS=5e-3, C=1.0, kB=1e-3, mode=I.MODE_FREE)])
+    sim = cfm.Simulation.from_workload(wl)
+    orc = O.Oracle.from_workload(wl)
+    compare_cuts(sim, orc)
+    sim.step(wl.steps); orc.step(wl.steps)
+    compare_state(sim, orc)
+
+
+def test_two_capsules_hertz_contact(cfm):
+    """Two capsules closer than the Hertz range interact (Eq. 11)."""
+    nx, ny, nz = 32, 16, 20
+    caps = [I.CapsuleSpec(centre=(10.3, 8.4, 10.17), radius=4.0, level=2, C=1.0, mode=I.MODE_FREE),
+            I.CapsuleSpec(centre=(19.1, 8.4, 10.17), radius=4.0, level=2, C=1.0, mode=I.MODE_FREE)]
+    wl = I.Workload("contact", nx, ny, nz, h_top=8.5, capsules=caps, steps=20, rep_dz=2.0)
+    sim = cfm.Simulation.from_workload(wl)
+    orc = O.Oracle.from_workload(wl)
+    sim.step(wl.steps); orc.step(wl.steps)
+    compare_state(sim, orc)
+    for k in range(2):
+        assert np.abs(sim.capsule_state(k)["X"] - orc.capsule_state(k)["X"]).max() < 1e-5
+
+
+def test_meniscus_field_matches_oracle(cfm):
+    wl = I.tiny_film(mode=I.MODE_FIXED, steps=30)
+    sim = cfm.Simulation.from_workload(wl)
+    orc = O.Oracle.from_workload(wl)
+    sim.step(wl.steps); orc.step(wl.steps)
+    hg = sim.meniscus_field(); ho = orc.meniscus_field()
+    assert (np.isnan(hg) == np.isnan(ho)).all()
+    ok = ~np.isnan(ho)
+    assert np.abs(hg[ok] - ho[ok]).max() < 1e-3
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mode", [I.MODE_FIXED, I.MODE_FREE])
+def test_single_capsule_film_1000_steps(cfm, mode):
+    """32x32x48 lattice, R=8 capsule through a 12-cell film, 1000 steps."""
+    wl = I.single_capsule_film(mode=mode, steps=1000)
+    sim = cfm.Simulation.from_workload(wl)
+    orc = O.Oracle.from_workload(wl)
+    sim.step(wl.steps); orc.step(wl.steps)
+    e_rho, e_u = compare_state(sim, orc)
+    print(f"mode {mode}: rho {e_rho:.2e} u {e_u:.2e}")
+    Fg, _ = sim.capsule_force(0)
+    Fo = orc.capsule_state(0)["force"]
+    assert np.abs(Fg - Fo).max() < 1e-2 * np.abs(Fo).max()
+
+
+@pytest.mark.slow
+def test_capsule_pair_full_size_lateral_force(cfm):
+    """128x64x64 with two R=12 capsules at d = 3R, the benchmark workload's
+    launch configuration, 60 steps: fields and the lateral force vs oracle."""
+    wl = I.capsule_pair(steps=60)
+    sim = cfm.Simulation.from_workload(wl)
+    orc = O.Oracle.from_workload(wl)
+    sim.step(wl.steps); orc.step(wl.steps)
+    compare_state(sim, orc, check_pops=False)
+    Fg = sim.lateral_force(0, 1)
+    Fa = orc.capsule_state(0)["force"]; Fb = orc.capsule_state(1)["force"]
+    ca = orc.capsule_state(0)["X"].mean(0); cb = orc.capsule_state(1)["X"].mean(0)
+    e = (cb - ca)[:2]; e /= np.linalg.norm(e)
+    Fo = 0.5 * np.dot((Fb - Fa)[:2], e)
+    assert abs(Fg - Fo) <= 1e-2 * abs(Fo) + 1e-7, (Fg, Fo)
