@@ -80,6 +80,7 @@ def load_library(path: Optional[str] = None):
         "cf_meniscus_profile": [C.c_void_p, C.c_int, _dp, _dp, C.POINTER(C.c_size_t), _dp],
         "cf_cuts": [C.c_void_p, C.POINTER(C.c_uint32), C.POINTER(C.c_int), C.POINTER(C.c_uint8)],
         "cf_launch_count": [C.c_void_p, C.POINTER(C.c_longlong)],
+        "cf_time_phases": [C.c_void_p, C.c_longlong, _dp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -93,7 +94,8 @@ def exported_symbols():
     return ["cf_last_error", "cf_create", "cf_destroy", "cf_add_capsule", "cf_set_capsule_mode",
             "cf_set_film", "cf_step", "cf_sync", "cf_capsule_force", "cf_lateral_force",
             "cf_capsule_state", "cf_fields", "cf_populations", "cf_total_mass",
-            "cf_meniscus_field", "cf_meniscus_profile", "cf_cuts", "cf_launch_count"]
+            "cf_meniscus_field", "cf_meniscus_profile", "cf_cuts", "cf_launch_count",
+            "cf_time_phases"]
 
 
 def _check(rc):
@@ -205,6 +207,12 @@ class Simulation:
 
     def sync(self):
         _check(_lib.cf_sync(self._h))
+
+    def time_phases(self, n):
+        """Mean device ms per step of (lattice, membrane, cut links) over n steps."""
+        ms = np.zeros(3)
+        _check(_lib.cf_time_phases(self._h, int(n), _ptr(ms)))
+        return ms
 
     def launches(self):
         n = C.c_longlong()

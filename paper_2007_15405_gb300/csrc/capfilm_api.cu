@@ -70,7 +70,7 @@ struct cf_ctx {
     std::vector<HostCapsule> caps;
     int nnodes = 0, nfaces = 0;
     bool any_frozen = false, all_fixed = true;
-    float *X[2] = {nullptr, nullptr};
+    double *X[2] = {nullptr, nullptr};
     int xpar = 0;
     float *V = nullptr, *FT = nullptr, *FTprev = nullptr, *fscr = nullptr, *vscr = nullptr,
           *Fcpl = nullptr, *refM = nullptr, *refA = nullptr, *refDet = nullptr;
@@ -175,7 +175,7 @@ MemParams mem_params(cf_ctx *c) {
 }
 
 // Cut links for positions X (cur list lpar, clears the other list's nodes).
-cf_status enqueue_cuts(cf_ctx *c, const float *X, int *nl) {
+cf_status enqueue_cuts(cf_ctx *c, const double *X, int *nl) {
     if (c->nfaces == 0) return CF_OK;
     const int cur = 1 - c->lpar;
     CutParams q{};
@@ -198,11 +198,14 @@ cf_status enqueue_cuts(cf_ctx *c, const float *X, int *nl) {
     return CF_OK;
 }
 
-// One coupled step on the stream (also used under graph capture).
-cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl) {
+// One coupled step on the stream (also used under graph capture).  ev, when
+// given, receives four events bracketing the lattice, membrane and cut phases.
+cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev = nullptr) {
+    if (ev) CF_CUDA(cudaEventRecord(ev[0], c->stream));
     CF_CUDA(launch_lb_step(lb_params(c, with_out), c->lb_variant, c->stream));
     *nl += 1;
     c->fpar = 1 - c->fpar;
+    if (ev) CF_CUDA(cudaEventRecord(ev[1], c->stream));
     if (c->nnodes) {
         const int nc = (int)c->caps.size();
         CF_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(double) * A_NACC * nc, c->stream));
@@ -210,11 +213,13 @@ cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl) {
         CF_CUDA(cudaMemsetAsync(c->bbox + 3 * nc, 0x80, sizeof(int) * 3 * nc, c->stream));
         CF_CUDA(launch_membrane(mem_params(c), c->any_frozen, c->stream, nl));
         c->xpar = 1 - c->xpar;
-        if (!c->all_fixed) {
-            cf_status s = enqueue_cuts(c, c->X[c->xpar], nl);
-            if (s != CF_OK) return s;
-        }
     }
+    if (ev) CF_CUDA(cudaEventRecord(ev[2], c->stream));
+    if (c->nnodes && !c->all_fixed) {
+        cf_status s = enqueue_cuts(c, c->X[c->xpar], nl);
+        if (s != CF_OK) return s;
+    }
+    if (ev) CF_CUDA(cudaEventRecord(ev[3], c->stream));
     return CF_OK;
 }
 
@@ -243,7 +248,8 @@ cf_status build_membrane(cf_ctx *c) {
         c->any_frozen |= h.mode == CF_FROZEN;
         c->all_fixed &= h.mode == CF_FIXED;
     }
-    std::vector<float> X(3 * (size_t)nv), refM(3 * (size_t)nf), refA(nf), refDet(nf);
+    std::vector<double> X(3 * (size_t)nv);
+    std::vector<float> refM(3 * (size_t)nf), refA(nf), refDet(nf);
     std::vector<int> faces(3 * (size_t)nf), face_cap(nf), node_cap(nv);
     std::vector<CapDev> cd(nc);
     std::vector<std::vector<int>> vf(nv);
@@ -303,8 +309,8 @@ cf_status build_membrane(cf_ctx *c) {
         ptr = (T *)dalloc(c, sizeof(T) * (size_t)(n), true);                         \
         if (!ptr) return fail(CF_ENOMEM, "device allocation failed (membrane)");     \
     } while (0)
-    MALLOC_M(c->X[0], float, 3 * nv);
-    MALLOC_M(c->X[1], float, 3 * nv);
+    MALLOC_M(c->X[0], double, 3 * nv);
+    MALLOC_M(c->X[1], double, 3 * nv);
     MALLOC_M(c->V, float, 3 * nv);
     MALLOC_M(c->Fcpl, float, 3 * nv);
     MALLOC_M(c->vscr, float, 4 * nv);
@@ -324,8 +330,8 @@ cf_status build_membrane(cf_ctx *c) {
     MALLOC_M(c->acc, double, A_NACC * nc);
 #undef MALLOC_M
     c->xpar = 0;
-    CF_CUDA(up(c->X[0], X.data(), sizeof(float) * X.size()));
-    CF_CUDA(up(c->X[1], X.data(), sizeof(float) * X.size()));
+    CF_CUDA(up(c->X[0], X.data(), sizeof(double) * X.size()));
+    CF_CUDA(up(c->X[1], X.data(), sizeof(double) * X.size()));
     CF_CUDA(cudaMemsetAsync(c->V, 0, sizeof(float) * 3 * nv, c->stream));
     CF_CUDA(cudaMemsetAsync(c->Fcpl, 0, sizeof(float) * 3 * nv, c->stream));
     CF_CUDA(cudaMemsetAsync(c->FT, 0, sizeof(float) * 3 * nf, c->stream));
@@ -551,6 +557,29 @@ cf_status cf_step(cf_ctx *c, long long n) {
     return CF_OK;
 }
 
+cf_status cf_time_phases(cf_ctx *c, long long n, double ms[3]) {
+    if (!c || !ms || n <= 0) return fail(CF_EINVAL, "bad argument");
+    if (!c->film_set) return fail(CF_ESTATE, "cf_set_film must come before cf_time_phases");
+    std::vector<cudaEvent_t> ev(4 * (size_t)n);
+    for (auto &e : ev) CF_CUDA(cudaEventCreate(&e));
+    int nl = 0;
+    cf_status st = CF_OK;
+    for (long long k = 0; k < n && st == CF_OK; ++k) st = enqueue_step(c, k == n - 1, &nl, &ev[4 * k]);
+    CF_CUDA(cudaStreamSynchronize(c->stream));
+    ms[0] = ms[1] = ms[2] = 0.0;
+    for (long long k = 0; k < n && st == CF_OK; ++k)
+        for (int q = 0; q < 3; ++q) {
+            float t = 0.f;
+            CF_CUDA(cudaEventElapsedTime(&t, ev[4 * k + q], ev[4 * k + q + 1]));
+            ms[q] += t / n;
+        }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (st != CF_OK) return st;
+    c->steps_done += n;
+    c->launches_last = nl;
+    return check_status(c);
+}
+
 cf_status cf_sync(cf_ctx *c) {
     if (!c) return fail(CF_EINVAL, "null context");
     return sync_ok(c);
@@ -608,12 +637,10 @@ cf_status cf_capsule_state(cf_ctx *c, int id, double *nodes, double *area, doubl
     for (int k = 0; k < id; ++k) v0 += c->caps[k].nv;
     const int nv = c->caps[id].nv;
     if (nodes) {
-        std::vector<float> X(3 * (size_t)nv);
-        CF_CUDA(cudaMemcpyAsync(X.data(), c->X[c->xpar] + 3 * (size_t)v0, sizeof(float) * X.size(),
+        CF_CUDA(cudaMemcpyAsync(nodes, c->X[c->xpar] + 3 * (size_t)v0, sizeof(double) * 3 * (size_t)nv,
                                 cudaMemcpyDeviceToHost, c->stream));
         cf_status s = sync_ok(c);
         if (s != CF_OK) return s;
-        for (size_t i = 0; i < X.size(); ++i) nodes[i] = X[i];
     }
     if (area || volume) {
         std::vector<double> acc;

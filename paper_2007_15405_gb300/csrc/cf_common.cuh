@@ -71,8 +71,9 @@ struct MemParams {
     const float *refDet;     // [nf]
     const int *vf_off;       // [nv+1] vertex -> (face*3+slot) CSR
     const int *vf_ent;
-    const float *X;          // [3*nv] positions of this step
-    float *Xn;               // [3*nv] positions of the next step
+    const double *X;         // [3*nv] positions of this step (FP64: per-step
+                             // displacements are far below a float ulp at x ~ 100)
+    double *Xn;              // [3*nv] positions of the next step
     float *V;                // [3*nv] node velocities (written)
     float *FT;               // [3*nf] exchange accumulated by the lattice kernel (zeroed here)
     float *FTprev;           // [3*nf] exchange of the previous step
@@ -91,7 +92,7 @@ struct CutParams {
     int nx, ny, nz, wall;
     int nfaces;
     const int *faces;
-    const float *X;          // positions the cut links are computed for
+    const double *X;         // positions the cut links are computed for (rounded to float)
     uint32_t *mask;
     int *tri;
     uint32_t *touched;       // [N] node listed flag

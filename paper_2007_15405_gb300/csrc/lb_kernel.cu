@@ -228,15 +228,22 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Ring<TX, T
     const float uub = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
     float *__restrict__ dA = p.dst;
     float *__restrict__ dB = p.dst + (long long)Q * p.N;
+    // Eq. 5; the rest population takes the mass balance (sum_i f^eq_i = rho)
+    // so that the float32 weights (which sum to 1 + 1.5e-8) create no mass
+    float qa0 = ra, qb0 = rb;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int i = 1; i < Q; ++i) {
         const float eua = ex(i) * ua[0] + ey(i) * ua[1] + ez(i) * ua[2];
         const float eub = ex(i) * ub[0] + ey(i) * ub[1] + ez(i) * ub[2];
         const float qa = wgt(i) * ra * (1.0f + 3.0f * eua + 4.5f * eua * eua - 1.5f * uua);
         const float qb = wgt(i) * rb * (1.0f + 3.0f * eub + 4.5f * eub * eub - 1.5f * uub);
+        qa0 -= qa;
+        qb0 -= qb;
         dA[(long long)i * p.N + n] = fa[i] - (fa[i] - qa) * p.itau[0];
         dB[(long long)i * p.N + n] = fb[i] - (fb[i] - qb) * p.itau[1];
     }
+    dA[n] = fa[0] - (fa[0] - qa0) * p.itau[0];
+    dB[n] = fb[0] - (fb[0] - qb0) * p.itau[1];
 }
 
 template <int TX, int TY>

@@ -31,6 +31,12 @@ __device__ __forceinline__ f3 cross(f3 a, f3 b) {
     return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
 __device__ __forceinline__ void st3(float *p, f3 v) { p[0] = v.x; p[1] = v.y; p[2] = v.z; }
+struct d3 { double x, y, z; };
+__device__ __forceinline__ d3 ld3d(const double *p, int i) { return {p[3 * i], p[3 * i + 1], p[3 * i + 2]}; }
+__device__ __forceinline__ f3 fdiff(d3 a, d3 b) {  // float(a - b), exact difference first
+    return {(float)(a.x - b.x), (float)(a.y - b.y), (float)(a.z - b.z)};
+}
+__device__ __forceinline__ f3 tof(d3 a) { return {(float)a.x, (float)a.y, (float)a.z}; }
 
 // Warp-aggregated FP64 add into per-capsule accumulators: lanes sharing the
 // capsule id combine first, one atomic per group.
@@ -74,7 +80,9 @@ __global__ void k_faces(const MemParams p) {
     const int cap = p.face_cap[ff];
     const CapDev cp = p.caps[cap];
     const int ia = p.faces[3 * ff], ib = p.faces[3 * ff + 1], ic = p.faces[3 * ff + 2];
-    const f3 a = ld3(p.X, ia), b = ld3(p.X, ib), c = ld3(p.X, ic);
+    const d3 da = ld3d(p.X, ia), db = ld3d(p.X, ib), dc = ld3d(p.X, ic);
+    // element geometry in coordinates local to its first node (translation invariant)
+    const f3 a{0.f, 0.f, 0.f}, b = fdiff(db, da), c = fdiff(dc, da);
     float *S = p.fscr + (long long)ff * FS_N;
     double area = 0.0, vol = 0.0;
     if (valid) {
@@ -90,7 +98,7 @@ __global__ void k_faces(const MemParams p) {
         // volume term in FP64 relative to the first node (translation invariant)
         {
             const double ux = u.x, uy = u.y, uz = u.z, wx = w.x, wy = w.y, wz = w.z;
-            const double ax = a.x, ay = a.y, az = a.z;
+            const double ax = da.x, ay = da.y, az = da.z;
             // x_a . (x_b x x_c) = x_a . (u x w) + ... ; use (a, a+u, a+w):
             // a.(b x c) = a.((a+u) x (a+w)) = a.(u x w) (a.(a x .) = 0)
             const double cx = uy * wz - uz * wy, cy = uz * wx - ux * wz, cz = ux * wy - uy * wx;
@@ -114,8 +122,8 @@ __global__ void k_faces(const MemParams p) {
             // volume gradient terms (x_b x x_c etc.); their per-node sums are
             // translation invariant on a closed mesh, so positions are taken
             // relative to the capsule's first node to avoid cancellation
-            const f3 o = ld3(p.X, cp.v0);
-            const f3 ra = a - o, rb = b - o, rc = c - o;
+            const d3 o = ld3d(p.X, cp.v0);
+            const f3 ra = fdiff(da, o), rb = fdiff(db, o), rc = fdiff(dc, o);
             st3(S + FS_DV + 0, cross(rb, rc));
             st3(S + FS_DV + 3, cross(rc, ra));
             st3(S + FS_DV + 6, cross(ra, rb));
@@ -138,7 +146,7 @@ __global__ void k_vert1(const MemParams p) {
     const int vv = valid ? v : 0;
     const int cap = p.node_cap[vv];
     const CapDev cp = p.caps[cap];
-    const f3 x = ld3(p.X, vv);
+    const d3 x = ld3d(p.X, vv);
     if (valid && cp.mode == 0) {
         f3 L{0.f, 0.f, 0.f};
         float A = 0.f;
@@ -158,12 +166,12 @@ __global__ void k_vert1(const MemParams p) {
     acc_add(p.acc, cap, A_CY, x.y, valid);
     acc_add(p.acc, cap, A_CZ, x.z, valid);
     if (valid) {  // bbox: mins [3*ncaps] then maxs [3*ncaps]
-        atomicMin(p.bbox + 3 * cap + 0, (int)floorf(x.x));
-        atomicMin(p.bbox + 3 * cap + 1, (int)floorf(x.y));
-        atomicMin(p.bbox + 3 * cap + 2, (int)floorf(x.z));
-        atomicMax(p.bbox + 3 * p.ncaps + 3 * cap + 0, (int)ceilf(x.x));
-        atomicMax(p.bbox + 3 * p.ncaps + 3 * cap + 1, (int)ceilf(x.y));
-        atomicMax(p.bbox + 3 * p.ncaps + 3 * cap + 2, (int)ceilf(x.z));
+        atomicMin(p.bbox + 3 * cap + 0, (int)floor(x.x));
+        atomicMin(p.bbox + 3 * cap + 1, (int)floor(x.y));
+        atomicMin(p.bbox + 3 * cap + 2, (int)floor(x.z));
+        atomicMax(p.bbox + 3 * p.ncaps + 3 * cap + 0, (int)ceil(x.x));
+        atomicMax(p.bbox + 3 * p.ncaps + 3 * cap + 1, (int)ceil(x.y));
+        atomicMax(p.bbox + 3 * p.ncaps + 3 * cap + 2, (int)ceil(x.z));
     }
 }
 
@@ -173,7 +181,8 @@ __global__ void k_bend(const MemParams p) {
     const int cap = p.face_cap[f];
     if (p.caps[cap].mode != 0) return;
     const int ia = p.faces[3 * f], ib = p.faces[3 * f + 1], ic = p.faces[3 * f + 2];
-    const f3 a = ld3(p.X, ia), b = ld3(p.X, ib), c = ld3(p.X, ic);
+    const d3 pa = ld3d(p.X, ia);
+    const f3 a{0.f, 0.f, 0.f}, b = fdiff(ld3d(p.X, ib), pa), c = fdiff(ld3d(p.X, ic), pa);
     float *S = p.fscr + (long long)f * FS_N;
     f3 da_p, da_q, db_p, db_q, dc_p, dc_q;
     const float cta = cot_grad(a, b, c, da_p, da_q);  // p=b, q=c
@@ -214,7 +223,7 @@ __global__ void k_vert2(const MemParams p) {
     const int vv = valid ? v : 0;
     const int cap = p.node_cap[vv];
     const CapDev cp = p.caps[cap];
-    const f3 x = ld3(p.X, vv);
+    const d3 x = ld3d(p.X, vv);
     f3 Fc{0.f, 0.f, 0.f}, Fe{0.f, 0.f, 0.f}, Fi{0.f, 0.f, 0.f};
     if (valid) {
         const bool el = cp.mode == 0;
@@ -237,7 +246,7 @@ __global__ void k_vert2(const MemParams p) {
         }
         // Hertz (Eq. 11): substrate plane
         if (p.wall) {
-            const float d = x.z - p.zrep;
+            const float d = (float)(x.z - (double)p.zrep);
             if (d < p.delta0) Fi.z += hertz(p.xi, p.delta0, d);
         }
         // Hertz: nodes of other capsules (bounding boxes prefilter)
@@ -247,13 +256,13 @@ __global__ void k_vert2(const MemParams p) {
             if (x.z < lo[2] - p.delta0 || x.z > hi[2] + p.delta0) continue;
             for (int sy = -1; sy <= 1; ++sy)
                 for (int sx = -1; sx <= 1; ++sx) {
-                    const float ox = sx * p.nx, oy = sy * p.ny;
+                    const double ox = sx * p.nx, oy = sy * p.ny;
                     if (x.x + ox < lo[0] - p.delta0 || x.x + ox > hi[0] + p.delta0) continue;
                     if (x.y + oy < lo[1] - p.delta0 || x.y + oy > hi[1] + p.delta0) continue;
                     const CapDev c2d = p.caps[c2];
                     for (int w = c2d.v0; w < c2d.v0 + c2d.nv; ++w) {
-                        const f3 y = ld3(p.X, w);
-                        f3 dd = x - y;
+                        const d3 y = ld3d(p.X, w);
+                        f3 dd = fdiff(x, y);
                         dd.x -= p.nx * floorf(dd.x / p.nx + 0.5f);
                         dd.y -= p.ny * floorf(dd.y / p.ny + 0.5f);
                         const float d = sqrtf(dot(dd, dd));
@@ -268,10 +277,14 @@ __global__ void k_vert2(const MemParams p) {
         if (cp.mode == 0) {
             const f3 vel = (1.f / cp.mass) * Ft;
             st3(p.V + 3 * vv, vel);
-            st3(p.Xn + 3 * vv, x + vel);
+            p.Xn[3 * vv] = x.x + vel.x;
+            p.Xn[3 * vv + 1] = x.y + vel.y;
+            p.Xn[3 * vv + 2] = x.z + vel.z;
         } else if (cp.mode == 2) {
             st3(p.V + 3 * vv, f3{0.f, 0.f, 0.f});
-            st3(p.Xn + 3 * vv, x);
+            p.Xn[3 * vv] = x.x;
+            p.Xn[3 * vv + 1] = x.y;
+            p.Xn[3 * vv + 2] = x.z;
         }
     }
     // per-capsule FP64 sums: coupling force, its torque about the centroid, total force
@@ -300,7 +313,10 @@ __global__ void k_frozen(const MemParams p) {
     const f3 vel{(float)(p.acc[cap * A_NACC + A_FTX] * s), (float)(p.acc[cap * A_NACC + A_FTY] * s),
                  (float)(p.acc[cap * A_NACC + A_FTZ] * s)};
     st3(p.V + 3 * v, vel);
-    st3(p.Xn + 3 * v, ld3(p.X, v) + vel);
+    const d3 x = ld3d(p.X, v);
+    p.Xn[3 * v] = x.x + vel.x;
+    p.Xn[3 * v + 1] = x.y + vel.y;
+    p.Xn[3 * v + 2] = x.z + vel.z;
 }
 
 cudaError_t launch_membrane(const MemParams &p, bool any_frozen, cudaStream_t s, int *nl) {
@@ -376,8 +392,8 @@ __global__ void k_cut_faces(const CutParams p) {
     const int lane = threadIdx.x & 31;
     if (warp >= p.nfaces) return;
     const int T = warp;
-    const f3 A = ld3(p.X, p.faces[3 * T]), B = ld3(p.X, p.faces[3 * T + 1]),
-             C = ld3(p.X, p.faces[3 * T + 2]);
+    const f3 A = tof(ld3d(p.X, p.faces[3 * T])), B = tof(ld3d(p.X, p.faces[3 * T + 1])),
+             C = tof(ld3d(p.X, p.faces[3 * T + 2]));
     const int lx = (int)ceilf(fminf(A.x, fminf(B.x, C.x)) - 1.f), hx = (int)floorf(fmaxf(A.x, fmaxf(B.x, C.x)) + 1.f);
     const int ly = (int)ceilf(fminf(A.y, fminf(B.y, C.y)) - 1.f), hy = (int)floorf(fmaxf(A.y, fmaxf(B.y, C.y)) + 1.f);
     const int lz = (int)ceilf(fminf(A.z, fminf(B.z, C.z)) - 1.f), hz = (int)floorf(fmaxf(A.z, fmaxf(B.z, C.z)) + 1.f);
