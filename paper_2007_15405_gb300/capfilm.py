@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libcapfilm.so")
 
 CF_OK = 0
 STATUS_NAMES = {0: "CF_OK", 1: "CF_EINVAL", 2: "CF_ENOMEM", 3: "CF_ECUDA", 4: "CF_ESTATE",
-                5: "CF_ENOTFOUND", 6: "CF_EDIVERGED", 7: "CF_EOVERFLOW"}
+                5: "CF_ENOTFOUND", 6: "CF_EDIVERGED", 7: "CF_EOVERFLOW", 8: "CF_ETIMEOUT"}
 
 FREE, FROZEN, FIXED = 0, 1, 2
 

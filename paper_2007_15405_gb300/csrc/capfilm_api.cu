@@ -8,8 +8,10 @@
 #include "cf_common.cuh"
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -53,6 +55,7 @@ struct cf_ctx {
     float *f[2] = {nullptr, nullptr};
     int fpar = 0;
     float *out = nullptr;
+    float4 *dens = nullptr;
     uint32_t *mask = nullptr;
     int *tri = nullptr;
     uint32_t *touched = nullptr;
@@ -62,6 +65,7 @@ struct cf_ctx {
     int lpar = 0;
     int capacity = 0;
     unsigned *status = nullptr;
+    unsigned *bar = nullptr;     // grid barrier of the membrane kernel
     double *dscratch = nullptr;  // small FP64 scratch (mass)
     float *hscratch = nullptr;   // meniscus field [nx*ny]
     double *jit = nullptr;
@@ -70,12 +74,12 @@ struct cf_ctx {
     std::vector<HostCapsule> caps;
     int nnodes = 0, nfaces = 0;
     bool any_frozen = false, all_fixed = true;
-    double *X[2] = {nullptr, nullptr};
+    float *X[2] = {nullptr, nullptr};  // [hi 3*nv | lo 3*nv] per buffer
     int xpar = 0;
     float *V = nullptr, *FT = nullptr, *FTprev = nullptr, *fscr = nullptr, *vscr = nullptr,
           *Fcpl = nullptr, *refM = nullptr, *refA = nullptr, *refDet = nullptr;
     int *faces = nullptr, *face_cap = nullptr, *node_cap = nullptr, *vf_off = nullptr,
-        *vf_ent = nullptr, *bbox = nullptr;
+        *vf_ent = nullptr, *bbox[2] = {nullptr, nullptr};
     CapDev *capdev = nullptr;
     double *acc = nullptr;
     std::vector<void *> mem_allocs;
@@ -117,7 +121,8 @@ cf_status check_status(cf_ctx *c) {
     if (st) {
         CF_CUDA(cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
         if (st & ST_NAN) return fail(CF_EDIVERGED, "non-finite density in the lattice");
-        if (st & ST_OVERFLOW) return fail(CF_EOVERFLOW, "cut-link node list exceeded its capacity");
+        if (st & ST_OVERFLOW) return fail(CF_EOVERFLOW, "cut-link node list or element box exceeded its capacity");
+        if (st & ST_TIMEOUT) return fail(CF_ETIMEOUT, "grid barrier of the membrane kernel timed out");
     }
     return CF_OK;
 }
@@ -142,6 +147,7 @@ LBParams lb_params(cf_ctx *c, bool with_out) {
     p.V = c->V;
     p.FT = c->FT;
     p.out = with_out ? c->out : nullptr;
+    p.dens = c->dens;
     p.status = c->status;
     return p;
 }
@@ -161,8 +167,10 @@ MemParams mem_params(cf_ctx *c) {
     p.node_cap = c->node_cap;
     p.refM = c->refM; p.refA = c->refA; p.refDet = c->refDet;
     p.vf_off = c->vf_off; p.vf_ent = c->vf_ent;
-    p.X = c->X[c->xpar];
-    p.Xn = c->X[1 - c->xpar];
+    p.Xh = c->X[c->xpar];
+    p.Xl = c->X[c->xpar] + 3 * (size_t)c->nnodes;
+    p.Xnh = c->X[1 - c->xpar];
+    p.Xnl = c->X[1 - c->xpar] + 3 * (size_t)c->nnodes;
     p.V = c->V;
     p.FT = c->FT;
     p.FTprev = c->FTprev;
@@ -170,12 +178,16 @@ MemParams mem_params(cf_ctx *c) {
     p.vscr = c->vscr;
     p.Fcpl = c->Fcpl;
     p.acc = c->acc;
-    p.bbox = c->bbox;
+    p.bbox = c->bbox[c->xpar];
+    p.bbox_prev = c->bbox[1 - c->xpar];
+    p.bar = c->bar;
+    p.status = c->status;
+    p.any_frozen = c->any_frozen ? 1 : 0;
     return p;
 }
 
 // Cut links for positions X (cur list lpar, clears the other list's nodes).
-cf_status enqueue_cuts(cf_ctx *c, const double *X, int *nl) {
+cf_status enqueue_cuts(cf_ctx *c, const float *X, int *nl) {
     if (c->nfaces == 0) return CF_OK;
     const int cur = 1 - c->lpar;
     CutParams q{};
@@ -203,14 +215,16 @@ cf_status enqueue_cuts(cf_ctx *c, const double *X, int *nl) {
 cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev = nullptr) {
     if (ev) CF_CUDA(cudaEventRecord(ev[0], c->stream));
     CF_CUDA(launch_lb_step(lb_params(c, with_out), c->lb_variant, c->stream));
-    *nl += 1;
+    *nl += 2;
     c->fpar = 1 - c->fpar;
     if (ev) CF_CUDA(cudaEventRecord(ev[1], c->stream));
     if (c->nnodes) {
         const int nc = (int)c->caps.size();
+        int *bb = c->bbox[c->xpar];
         CF_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(double) * A_NACC * nc, c->stream));
-        CF_CUDA(cudaMemsetAsync(c->bbox, 0x7f, sizeof(int) * 3 * nc, c->stream));
-        CF_CUDA(cudaMemsetAsync(c->bbox + 3 * nc, 0x80, sizeof(int) * 3 * nc, c->stream));
+        CF_CUDA(cudaMemsetAsync(bb, 0x7f, sizeof(int) * 3 * nc, c->stream));
+        CF_CUDA(cudaMemsetAsync(bb + 3 * nc, 0x80, sizeof(int) * 3 * nc, c->stream));
+        CF_CUDA(cudaMemsetAsync(c->bar, 0, sizeof(unsigned) * 2, c->stream));
         CF_CUDA(launch_membrane(mem_params(c), c->any_frozen, c->stream, nl));
         c->xpar = 1 - c->xpar;
     }
@@ -224,13 +238,17 @@ cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev = null
 }
 
 void choose_launch(cf_ctx *c) {
-    // tiles of 32 x 4 columns; split z so that the grid covers the GPU several
-    // times over (152 SMs, 2+ CTAs each)
-    const int tiles = ((c->d.nx + 31) / 32) * ((c->d.ny + 3) / 4);
+    // blocks of 32 x 4 columns; each thread walks zchunk planes (strided), so
+    // the grid holds about 16 resident blocks per SM on 152 SMs
+    const int cols = ((c->d.nx + 31) / 32) * ((c->d.ny + 3) / 4);
     const int nzf = c->d.nz - (c->d.wall ? 1 : 0);
-    const int target = 152 * 4;
-    int chunks = std::max(1, std::min(nzf / 4, (target + tiles - 1) / tiles));
-    c->zchunk = std::max(1, (nzf + chunks - 1) / chunks);
+    const int target = 152 * 16;
+    const int gz = std::max(1, std::min(nzf, (target + cols - 1) / cols));
+    c->zchunk = std::max(1, (nzf + gz - 1) / gz);
+    if (const char *e = std::getenv("CAPFILM_ZCHUNK")) {  // manual override for launch sweeps
+        const int v = std::atoi(e);
+        if (v > 0) c->zchunk = std::min(v, nzf);
+    }
     c->lb_variant = 0;
 }
 
@@ -309,8 +327,8 @@ cf_status build_membrane(cf_ctx *c) {
         ptr = (T *)dalloc(c, sizeof(T) * (size_t)(n), true);                         \
         if (!ptr) return fail(CF_ENOMEM, "device allocation failed (membrane)");     \
     } while (0)
-    MALLOC_M(c->X[0], double, 3 * nv);
-    MALLOC_M(c->X[1], double, 3 * nv);
+    MALLOC_M(c->X[0], float, 6 * nv);
+    MALLOC_M(c->X[1], float, 6 * nv);
     MALLOC_M(c->V, float, 3 * nv);
     MALLOC_M(c->Fcpl, float, 3 * nv);
     MALLOC_M(c->vscr, float, 4 * nv);
@@ -325,13 +343,34 @@ cf_status build_membrane(cf_ctx *c) {
     MALLOC_M(c->node_cap, int, nv);
     MALLOC_M(c->vf_off, int, nv + 1);
     MALLOC_M(c->vf_ent, int, vf_ent.size());
-    MALLOC_M(c->bbox, int, 6 * nc);
+    MALLOC_M(c->bbox[0], int, 6 * nc);
+    MALLOC_M(c->bbox[1], int, 6 * nc);
     MALLOC_M(c->capdev, CapDev, nc);
     MALLOC_M(c->acc, double, A_NACC * nc);
 #undef MALLOC_M
     c->xpar = 0;
-    CF_CUDA(up(c->X[0], X.data(), sizeof(double) * X.size()));
-    CF_CUDA(up(c->X[1], X.data(), sizeof(double) * X.size()));
+    {   // bounding boxes of the initial shapes (read as the previous step's)
+        std::vector<int> bb(6 * (size_t)nc);
+        for (int k = 0; k < nc; ++k) {
+            for (int a = 0; a < 3; ++a) { bb[3 * k + a] = INT_MAX; bb[3 * nc + 3 * k + a] = INT_MIN; }
+            for (int i = cd[k].v0; i < cd[k].v0 + cd[k].nv; ++i)
+                for (int a = 0; a < 3; ++a) {
+                    bb[3 * k + a] = std::min(bb[3 * k + a], (int)std::floor(X[3 * (size_t)i + a]));
+                    bb[3 * nc + 3 * k + a] = std::max(bb[3 * nc + 3 * k + a], (int)std::ceil(X[3 * (size_t)i + a]));
+                }
+        }
+        CF_CUDA(up(c->bbox[0], bb.data(), sizeof(int) * bb.size()));
+        CF_CUDA(up(c->bbox[1], bb.data(), sizeof(int) * bb.size()));
+    }
+    {   // hi + lo float pairs (the inputs are float-rounded, so lo starts at 0)
+        std::vector<float> hl(6 * (size_t)nv, 0.f);
+        for (size_t i = 0; i < X.size(); ++i) {
+            hl[i] = (float)X[i];
+            hl[X.size() + i] = (float)(X[i] - (double)hl[i]);
+        }
+        CF_CUDA(up(c->X[0], hl.data(), sizeof(float) * hl.size()));
+        CF_CUDA(up(c->X[1], hl.data(), sizeof(float) * hl.size()));
+    }
     CF_CUDA(cudaMemsetAsync(c->V, 0, sizeof(float) * 3 * nv, c->stream));
     CF_CUDA(cudaMemsetAsync(c->Fcpl, 0, sizeof(float) * 3 * nv, c->stream));
     CF_CUDA(cudaMemsetAsync(c->FT, 0, sizeof(float) * 3 * nf, c->stream));
@@ -380,7 +419,8 @@ const char *cf_last_error(void) { return g_err.c_str(); }
 cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     if (!desc || !out) return fail(CF_EINVAL, "null argument");
     if (desc->nx < 3 || desc->ny < 3 || desc->nz < 3) return fail(CF_EINVAL, "lattice dimensions must be >= 3");
-    if ((long long)desc->nx * desc->ny * desc->nz > (1LL << 30)) return fail(CF_EINVAL, "lattice too large");
+    // population offsets are 32-bit: 38 * N must stay below 2^31
+    if (38LL * desc->nx * desc->ny * desc->nz >= (1LL << 31)) return fail(CF_EINVAL, "lattice too large (38*N >= 2^31)");
     if (!(desc->tau[0] > 0.5) || !(desc->tau[1] > 0.5)) return fail(CF_EINVAL, "tau must exceed 1/2");
     if (desc->precision != CF_FP32) return fail(CF_EINVAL, "unsupported precision");
     cf_ctx *c = new cf_ctx();
@@ -402,16 +442,18 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     c->f[0] = (float *)dalloc(c, sizeof(float) * 38 * N);
     c->f[1] = (float *)dalloc(c, sizeof(float) * 38 * N);
     c->out = (float *)dalloc(c, sizeof(float) * 5 * N);
+    c->dens = (float4 *)dalloc(c, sizeof(float4) * N);
     c->mask = (uint32_t *)dalloc(c, sizeof(uint32_t) * N);
     c->tri = (int *)dalloc(c, sizeof(int) * 18 * N);
     c->touched = (uint32_t *)dalloc(c, sizeof(uint32_t) * N);
     c->inside = (uint8_t *)dalloc(c, N);
     c->counts = (int *)dalloc(c, sizeof(int) * 2);
     c->status = (unsigned *)dalloc(c, sizeof(unsigned));
+    c->bar = (unsigned *)dalloc(c, sizeof(unsigned) * 2);
     c->dscratch = (double *)dalloc(c, sizeof(double) * 8);
     c->hscratch = (float *)dalloc(c, sizeof(float) * desc->nx * desc->ny);
-    if (!c->f[0] || !c->f[1] || !c->out || !c->mask || !c->tri || !c->touched || !c->inside ||
-        !c->counts || !c->status || !c->dscratch || !c->hscratch) {
+    if (!c->f[0] || !c->f[1] || !c->out || !c->dens || !c->mask || !c->tri || !c->touched || !c->inside ||
+        !c->counts || !c->status || !c->bar || !c->dscratch || !c->hscratch) {
         cf_destroy(c);
         return fail(CF_ENOMEM, "device allocation failed");
     }
@@ -537,7 +579,7 @@ cf_status cf_step(cf_ctx *c, long long n) {
         {
             // count the launches of one step pair (for reporting)
             const bool fx = c->all_fixed;
-            per_pair = 2 * (1 + (c->nnodes ? 4 + (c->any_frozen ? 1 : 0) + (fx ? 0 : 2) : 0));
+            per_pair = 2 * (2 + (c->nnodes ? 1 + (fx ? 0 : 2) : 0));
         }
         while (left >= 2) {
             CF_CUDA(cudaGraphLaunch(c->graph, c->stream));
@@ -620,8 +662,8 @@ cf_status cf_lateral_force(cf_ctx *c, int a, int b, double *F) {
     cf_status s = read_acc(c, acc);
     if (s != CF_OK) return s;
     const double *A = &acc[(size_t)a * A_NACC], *B = &acc[(size_t)b * A_NACC];
-    double dx = B[A_CX] / c->caps[b].nv - A[A_CX] / c->caps[a].nv;
-    double dy = B[A_CY] / c->caps[b].nv - A[A_CY] / c->caps[a].nv;
+    double dx = (B[A_OX] + B[A_CX] / c->caps[b].nv) - (A[A_OX] + A[A_CX] / c->caps[a].nv);
+    double dy = (B[A_OY] + B[A_CY] / c->caps[b].nv) - (A[A_OY] + A[A_CY] / c->caps[a].nv);
     dx -= c->d.nx * std::floor(dx / c->d.nx + 0.5);
     dy -= c->d.ny * std::floor(dy / c->d.ny + 0.5);
     const double L = std::sqrt(dx * dx + dy * dy);
@@ -637,10 +679,14 @@ cf_status cf_capsule_state(cf_ctx *c, int id, double *nodes, double *area, doubl
     for (int k = 0; k < id; ++k) v0 += c->caps[k].nv;
     const int nv = c->caps[id].nv;
     if (nodes) {
-        CF_CUDA(cudaMemcpyAsync(nodes, c->X[c->xpar] + 3 * (size_t)v0, sizeof(double) * 3 * (size_t)nv,
+        std::vector<float> h(3 * (size_t)nv), l(3 * (size_t)nv);
+        CF_CUDA(cudaMemcpyAsync(h.data(), c->X[c->xpar] + 3 * (size_t)v0, sizeof(float) * h.size(),
                                 cudaMemcpyDeviceToHost, c->stream));
+        CF_CUDA(cudaMemcpyAsync(l.data(), c->X[c->xpar] + 3 * (size_t)c->nnodes + 3 * (size_t)v0,
+                                sizeof(float) * l.size(), cudaMemcpyDeviceToHost, c->stream));
         cf_status s = sync_ok(c);
         if (s != CF_OK) return s;
+        for (size_t i = 0; i < h.size(); ++i) nodes[i] = (double)h[i] + (double)l[i];
     }
     if (area || volume) {
         std::vector<double> acc;
@@ -705,8 +751,8 @@ cf_status cf_meniscus_profile(cf_ctx *c, int id, double *r, double *zeta, size_t
     if (s != CF_OK) return s;
     std::vector<double> cx(nc), cy(nc);
     for (int k = 0; k < nc; ++k) {
-        cx[k] = acc[(size_t)k * A_NACC + A_CX] / c->caps[k].nv;
-        cy[k] = acc[(size_t)k * A_NACC + A_CY] / c->caps[k].nv;
+        cx[k] = acc[(size_t)k * A_NACC + A_OX] + acc[(size_t)k * A_NACC + A_CX] / c->caps[k].nv;
+        cy[k] = acc[(size_t)k * A_NACC + A_OY] + acc[(size_t)k * A_NACC + A_CY] / c->caps[k].nv;
     }
     // far-field height: valid columns whose distance to the nearest capsule
     // is at least 90 % of the largest such distance

@@ -30,7 +30,7 @@ struct LBParams {
     int nx, ny, nz, wall;
     long long N;            // nodes
     int zlo, zhi;           // fluid planes [zlo, zhi)
-    int zchunk;             // planes per CTA
+    int zchunk;             // planes walked per thread (grid.z = fluid planes / zchunk)
     float itau[2], tau[2];  // 1/tau and tau per component
     float G;
     const float *__restrict__ src;   // post-collision populations of the last step
@@ -41,10 +41,11 @@ struct LBParams {
     const float *__restrict__ V;        // node velocities [3*nnodes]
     float *__restrict__ FT;             // element momentum exchange accumulators [3*nfaces]
     float *__restrict__ out;            // optional [5][N]: rhoA, rhoB, ux, uy, uz
+    float4 *__restrict__ dens;          // [N] (rhoA, rhoB, psiA, psiB) of this step
     unsigned *__restrict__ status;      // device error flags
 };
 
-enum StatusBits : unsigned { ST_OVERFLOW = 1u, ST_NAN = 2u };
+enum StatusBits : unsigned { ST_OVERFLOW = 1u, ST_NAN = 2u, ST_TIMEOUT = 4u };
 
 // Capsule description on the device.
 struct CapDev {
@@ -55,8 +56,10 @@ struct CapDev {
 };
 
 // Per-capsule FP64 accumulators (reset each step).
+// A_CX..A_CZ hold the node sum relative to the capsule's first node, whose
+// position is A_OX..A_OZ; A_VOL the enclosed volume.
 enum CapAcc { A_FX = 0, A_FY, A_FZ, A_TX, A_TY, A_TZ, A_AREA, A_VOL, A_CX, A_CY, A_CZ,
-              A_FTX, A_FTY, A_FTZ, A_NACC = 16 };
+              A_FTX, A_FTY, A_FTZ, A_OX, A_OY, A_OZ, A_NACC = 20 };
 
 struct MemParams {
     int nx, ny, nz, wall;
@@ -71,9 +74,9 @@ struct MemParams {
     const float *refDet;     // [nf]
     const int *vf_off;       // [nv+1] vertex -> (face*3+slot) CSR
     const int *vf_ent;
-    const double *X;         // [3*nv] positions of this step (FP64: per-step
-                             // displacements are far below a float ulp at x ~ 100)
-    double *Xn;              // [3*nv] positions of the next step
+    const float *Xh, *Xl;    // [3*nv] positions of this step as float pairs hi + lo
+                             // (per-step displacements are below a float ulp at x ~ 100)
+    float *Xnh, *Xnl;        // [3*nv] positions of the next step
     float *V;                // [3*nv] node velocities (written)
     float *FT;               // [3*nf] exchange accumulated by the lattice kernel (zeroed here)
     float *FTprev;           // [3*nf] exchange of the previous step
@@ -81,7 +84,11 @@ struct MemParams {
     float *vscr;             // [nv*4] per-node scratch (gL, gA)
     float *Fcpl;             // [3*nv] coupling force on nodes (readout)
     double *acc;             // [ncaps*A_NACC]
-    int *bbox;               // [ncaps*3] mins then [ncaps*3] maxs (integer bounding boxes)
+    int *bbox;               // [ncaps*3] mins then [ncaps*3] maxs of this step (written)
+    const int *bbox_prev;    // same, of the previous step (Hertz prefilter)
+    unsigned *bar;           // [2] grid barrier (count, generation)
+    unsigned *status;        // device error flags
+    int any_frozen;
 };
 
 // per-element scratch layout (floats)
@@ -92,7 +99,7 @@ struct CutParams {
     int nx, ny, nz, wall;
     int nfaces;
     const int *faces;
-    const double *X;         // positions the cut links are computed for (rounded to float)
+    const float *X;          // positions (float, hi part) the cut links are computed for
     uint32_t *mask;
     int *tri;
     uint32_t *touched;       // [N] node listed flag

@@ -1,161 +1,174 @@
-// Fused two-component Shan-Chen lattice Boltzmann step (sm_103a).
+// Two-component Shan-Chen lattice Boltzmann step (sm_103a), two passes.
 //
-// One launch performs, for every fluid node, the whole lattice part of a time
-// step of the coupled method (Sec. 3.1): pull-streaming of both components
-// with half-way bounce-back on the substrate and on membrane-cut links (Ladd's
-// moving-wall term), the momentum those bounces exchange with the membrane
-// elements, the densities and pseudopotentials psi = 1 - exp(-rho), the
-// Shan-Chen force (Eq. 10) with the interior/exterior decoupling, and the BGK
-// collision (Eqs. 4-5) with the velocity-shift forcing.
+// The lattice part of a coupled time step (Sec. 3.1): pull-streaming of both
+// components with half-way bounce-back on the substrate and on membrane-cut
+// links (Ladd's moving-wall term), the momentum those bounces exchange with
+// the membrane elements, the densities and pseudopotentials
+// psi = 1 - exp(-rho), the Shan-Chen force (Eq. 10) with the interior/exterior
+// decoupling, and the BGK collision (Eqs. 4-5) with the velocity-shift forcing.
 //
-// Layout: populations f[c][i][z][y][x] (float), two buffers (src -> dst).
-// Each CTA owns a TX x TY column tile and marches through a chunk of z planes.
-// The densities and pseudopotentials of three consecutive planes (tile plus a
-// one-node halo) live in a shared-memory ring, so the Shan-Chen stencil needs
-// no second pass over the populations: each population is read once and
-// written once per step (304 bytes per node update), plus the halo recomputes
-// which neighbouring tiles/chunks fetch concurrently (L2 hits).  Alternate z
-// chunks march in opposite directions so that the planes two chunks share are
-// loaded at the same time.
+//   k_density   per node: gather the 38 streamed populations, write
+//               (rho_A, rho_B, psi_A, psi_B) as one float4
+//   k_collide   per node: gather the 38 streamed populations again, read the
+//               pseudopotentials of the 18 neighbours (float4, L1/L2 resident),
+//               Shan-Chen force, velocity shift, BGK, store
+//
+// Layout: populations f[c][i][z][y][x] (float), two buffers (src -> dst);
+// threads map to x so every gather is a coalesced row.  Both passes are
+// barrier-free and run at high occupancy; DRAM traffic per node update is
+// 2 x 152 B of population reads + 152 B of writes + 16 B of density writes.
+// Gather addresses are the node index plus per-direction offsets with the
+// periodic wrap folded into per-node deltas.
 #include "cf_common.cuh"
 
 namespace cf {
 
-template <int TX, int TY>
-struct Ring {
-    float rho[3][2][TY + 2][TX + 2];
-    float psi[3][2][TY + 2][TX + 2];
-};
+constexpr int BX = 32, BY = 4;  // thread block: one row segment of 32 x 4 rows
 
-__device__ __forceinline__ int slot3(int z) { return ((z % 3) + 3) % 3; }
 __device__ __forceinline__ float psi_of(float r) { return -expm1f(-r); }
 
-// plane zu (unwrapped) is solid when the substrate is on
-__device__ __forceinline__ bool solid_plane(const LBParams &p, int zu) {
-    return p.wall && (wrapi(zu, p.nz) == 0);
+// Offsets from node n to its neighbour at -e in each axis (periodic).
+struct Deltas {
+    int n;                 // node index
+    int dxm, dxp;          // to x-1, x+1
+    int dym, dyp;          // to y-1, y+1 (in nodes)
+    int dzm, dzp;          // to z-1, z+1 (in nodes)
+    bool wlo, whi;         // z-1 / z+1 is the substrate
+};
+
+__device__ __forceinline__ Deltas deltas(const LBParams &p, int x, int y, int z) {
+    Deltas d;
+    const int nx = p.nx, ny = p.ny, nxy = p.nx * p.ny;
+    d.n = (z * ny + y) * nx + x;
+    d.dxm = x == 0 ? nx - 1 : -1;
+    d.dxp = x == nx - 1 ? -(nx - 1) : 1;
+    d.dym = y == 0 ? (ny - 1) * nx : -nx;
+    d.dyp = y == ny - 1 ? -(ny - 1) * nx : nx;
+    d.dzm = z == 0 ? (p.nz - 1) * nxy : -nxy;
+    d.dzp = z == p.nz - 1 ? -(p.nz - 1) * nxy : nxy;
+    d.wlo = p.wall && z == 1;
+    d.whi = p.wall && z == p.nz - 1;
+    return d;
 }
 
-// Pull the 2 x 19 post-streaming populations of node (x, y, z) (z wrapped,
-// fluid).  OWNER: this thread owns the node and books the momentum exchange.
+// offset of node x + s (s in {-1,0,1}^3) relative to n
+__device__ __forceinline__ int nb_off(const Deltas &d, int sx, int sy, int sz) {
+    int o = 0;
+    o += sx == -1 ? d.dxm : sx == 1 ? d.dxp : 0;
+    o += sy == -1 ? d.dym : sy == 1 ? d.dyp : 0;
+    o += sz == -1 ? d.dzm : sz == 1 ? d.dzp : 0;
+    return o;
+}
+
+// offset of the source of pulled direction i (node x - e_i, or the node's own
+// opposite population where x - e_i is the substrate), relative to src + n
+__device__ __forceinline__ int src_off(const Deltas &d, int N, int i) {
+    if ((ez(i) == 1 && d.wlo) || (ez(i) == -1 && d.whi)) return opp(i) * N;
+    return i * N + nb_off(d, -ex(i), -ey(i), -ez(i));
+}
+
+// Membrane-cut links of node n: the population the node sent towards the
+// membrane comes back with Ladd's term -2 w_k rho (e_k . u_T)/c_s^2, where rho
+// is the node's density (= sum of its post-collision populations) and u_T the
+// mean velocity of the crossed element's three nodes.  OWNER books the
+// exchanged momentum on the element.  Only nodes next to a membrane get here;
+// the path is kept out of line and returns the bounced populations through
+// patch[2][Q] (entries of uncut directions are left untouched).
 template <bool OWNER>
-__device__ __forceinline__ void pull_node(const LBParams &p, int x, int y, int z, float (&fa)[Q],
-                                          float (&fb)[Q], uint32_t &m) {
-    const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const long long N = p.N;
-    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-    const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-    const long long n = ((long long)z * ny + y) * nx + x;
-    const float *__restrict__ sA = p.src;
-    const float *__restrict__ sB = p.src + (long long)Q * N;
-    m = p.mask[n];
-    const bool wall_below = p.wall && zm == 0;  // pulling from z-1 hits the substrate
-    const bool wall_above = p.wall && zp == 0;
+__device__ __noinline__ void bounce_cut(const LBParams p, int n, uint32_t m, float *patch) {
+    const int N = (int)p.N;
+    const float *sA = p.src + n, *sB = p.src + (long long)Q * N + n;
+    float rwa = 0.f, rwb = 0.f;
+    for (int j = 0; j < Q; ++j) {
+        rwa += __ldg(sA + j * N);
+        rwb += __ldg(sB + j * N);
+    }
+    for (int k = 1; k < Q; ++k) {
+        if (!((m >> (k - 1)) & 1u)) continue;
+        const int kx = ex(k), ky = ey(k), kz = ez(k);
+        const int T = __ldg(p.tri + (long long)n * 18 + (k - 1));
+        const int a = __ldg(p.faces + 3 * T), b = __ldg(p.faces + 3 * T + 1),
+                  c = __ldg(p.faces + 3 * T + 2);
+        const float ux = (p.V[3 * a] + p.V[3 * b] + p.V[3 * c]) * (1.0f / 3.0f);
+        const float uy = (p.V[3 * a + 1] + p.V[3 * b + 1] + p.V[3 * c + 1]) * (1.0f / 3.0f);
+        const float uz = (p.V[3 * a + 2] + p.V[3 * b + 2] + p.V[3 * c + 2]) * (1.0f / 3.0f);
+        const float eu = kx * ux + ky * uy + kz * uz;
+        const float foa = __ldg(sA + k * N), fob = __ldg(sB + k * N);
+        const float w6 = 6.0f * wgt(k);
+        const float ca = w6 * rwa * eu, cb = w6 * rwb * eu;
+        patch[opp(k)] = foa - ca;
+        patch[Q + opp(k)] = fob - cb;
+        if (OWNER) {
+            const float sx = (2.0f * foa - ca) + (2.0f * fob - cb);
+            if (kx) atomicAdd(p.FT + 3 * T + 0, kx * sx);
+            if (ky) atomicAdd(p.FT + 3 * T + 1, ky * sx);
+            if (kz) atomicAdd(p.FT + 3 * T + 2, kz * sx);
+        }
+    }
+}
+
+// Post-streaming populations of the node: coalesced gathers, then the rare
+// cut-link patch.
+template <bool OWNER>
+__device__ __forceinline__ uint32_t pull(const LBParams &p, const Deltas &d, float (&fa)[Q],
+                                         float (&fb)[Q]) {
+    const int N = (int)p.N;
+    const float *sA = p.src + d.n;
+    const float *sB = p.src + (long long)Q * N + d.n;
+    const uint32_t m = __ldg(p.mask + d.n);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        // source node x - e_i
-        const int sx = ex(i) == 1 ? xm : ex(i) == -1 ? xp : x;
-        const int sy = ey(i) == 1 ? ym : ey(i) == -1 ? yp : y;
-        const int sz = ez(i) == 1 ? zm : ez(i) == -1 ? zp : z;
-        const bool wb = (ez(i) == 1 && wall_below) || (ez(i) == -1 && wall_above);
-        long long s;
-        int d;
-        if (wb) { s = n; d = opp(i); }
-        else { s = ((long long)sz * ny + sy) * nx + sx; d = i; }
-        fa[i] = __ldg(sA + (long long)d * N + s);
-        fb[i] = __ldg(sB + (long long)d * N + s);
+        const int o = src_off(d, N, i);
+        fa[i] = __ldg(sA + o);
+        fb[i] = __ldg(sB + o);
     }
     if (m) {
-        // membrane-cut links: bounce back what this node sent towards the
-        // membrane, with Ladd's term -2 w_k rho (e_k . u_T)/c_s^2, where rho
-        // is this node's density (= sum of its post-collision populations)
-        // and u_T the mean velocity of the crossed element's three nodes.
-        float rwa = 0.f, rwb = 0.f;
+        float patch[2 * Q];
 #pragma unroll
-        for (int j = 0; j < Q; ++j) {
-            rwa += __ldg(sA + (long long)j * N + n);
-            rwb += __ldg(sB + (long long)j * N + n);
-        }
+        for (int i = 0; i < Q; ++i) { patch[i] = fa[i]; patch[Q + i] = fb[i]; }
+        bounce_cut<OWNER>(p, d.n, m, patch);
 #pragma unroll
-        for (int k = 1; k < Q; ++k) {
-            if ((m >> (k - 1)) & 1u) {
-                const int T = __ldg(p.tri + n * 18 + (k - 1));
-                const int a = __ldg(p.faces + 3 * T), b = __ldg(p.faces + 3 * T + 1),
-                          c = __ldg(p.faces + 3 * T + 2);
-                const float ux = (p.V[3 * a] + p.V[3 * b] + p.V[3 * c]) * (1.0f / 3.0f);
-                const float uy = (p.V[3 * a + 1] + p.V[3 * b + 1] + p.V[3 * c + 1]) * (1.0f / 3.0f);
-                const float uz = (p.V[3 * a + 2] + p.V[3 * b + 2] + p.V[3 * c + 2]) * (1.0f / 3.0f);
-                const float eu = ex(k) * ux + ey(k) * uy + ez(k) * uz;
-                const float foa = __ldg(sA + (long long)k * N + n);
-                const float fob = __ldg(sB + (long long)k * N + n);
-                const float ca = 6.0f * wgt(k) * rwa * eu;
-                const float cb = 6.0f * wgt(k) * rwb * eu;
-                fa[opp(k)] = foa - ca;
-                fb[opp(k)] = fob - cb;
-                if (OWNER) {
-                    const float sx = (2.0f * foa - ca) + (2.0f * fob - cb);
-                    if (ex(k)) atomicAdd(p.FT + 3 * T + 0, ex(k) * sx);
-                    if (ey(k)) atomicAdd(p.FT + 3 * T + 1, ey(k) * sx);
-                    if (ez(k)) atomicAdd(p.FT + 3 * T + 2, ez(k) * sx);
-                }
-            }
-        }
+        for (int i = 0; i < Q; ++i) { fa[i] = patch[i]; fb[i] = patch[Q + i]; }
     }
+    return m;
 }
 
-template <int TX, int TY>
-__device__ __forceinline__ void store_ring(Ring<TX, TY> &R, int sl, int cy, int cx, float ra, float rb) {
-    R.rho[sl][0][cy][cx] = ra;
-    R.rho[sl][1][cy][cx] = rb;
-    R.psi[sl][0][cy][cx] = psi_of(ra);
-    R.psi[sl][1][cy][cx] = psi_of(rb);
+// z range of the fluid planes a thread walks (grid.z splits the column)
+__device__ __forceinline__ bool node_of(const LBParams &p, int &x, int &y, int &z) {
+    x = blockIdx.x * BX + threadIdx.x;
+    y = blockIdx.y * BY + threadIdx.y;
+    z = p.zlo + blockIdx.z;
+    return x < p.nx && y < p.ny;
 }
 
-// Densities of the halo ring of plane zu (unwrapped) into the shared ring.
-template <int TX, int TY>
-__device__ __forceinline__ void load_halo(const LBParams &p, Ring<TX, TY> &R, int zu, int x0, int y0) {
-    constexpr int NH = 2 * (TX + 2) + 2 * TY;
-    const int t = threadIdx.y * TX + threadIdx.x;
-    const int z = wrapi(zu, p.nz);
-    const int sl = slot3(zu);
-    for (int h = t; h < NH; h += TX * TY) {
-        int cx, cy;
-        if (h < TX + 2) { cx = h; cy = 0; }
-        else if (h < 2 * (TX + 2)) { cx = h - (TX + 2); cy = TY + 1; }
-        else if (h < 2 * (TX + 2) + TY) { cx = 0; cy = 1 + h - 2 * (TX + 2); }
-        else { cx = TX + 1; cy = 1 + h - 2 * (TX + 2) - TY; }
-        const int x = wrapi(x0 - 1 + cx, p.nx), y = wrapi(y0 - 1 + cy, p.ny);
+__global__ void __launch_bounds__(BX *BY, 6) k_density(const LBParams p) {
+    int x, y, z;
+    if (!node_of(p, x, y, z)) return;
+    for (; z < p.zhi; z += gridDim.z) {
+        const Deltas d = deltas(p, x, y, z);
         float fa[Q], fb[Q];
-        uint32_t m;
-        pull_node<false>(p, x, y, z, fa, fb, m);
+        pull<false>(p, d, fa, fb);
         float ra = 0.f, rb = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) { ra += fa[i]; rb += fb[i]; }
-        store_ring(R, sl, cy, cx, ra, rb);
+        p.dens[d.n] = make_float4(ra, rb, psi_of(ra), psi_of(rb));
     }
 }
 
 // Shan-Chen force with decoupling, velocity shift, BGK, store.
-template <int TX, int TY>
-__device__ __forceinline__ void collide_node(const LBParams &p, const Ring<TX, TY> &R, int zu, int x,
-                                             int y, const float (&fa)[Q], const float (&fb)[Q],
-                                             uint32_t m) {
-    const int cx = threadIdx.x + 1, cy = threadIdx.y + 1;
-    const int z = wrapi(zu, p.nz);
-    const int s0 = slot3(zu), sm = slot3(zu - 1), sp = slot3(zu + 1);
-    const float ra = R.rho[s0][0][cy][cx], rb = R.rho[s0][1][cy][cx];
-    const float pa = R.psi[s0][0][cy][cx], pb = R.psi[s0][1][cy][cx];
-    const bool wall_lo = solid_plane(p, zu - 1), wall_hi = solid_plane(p, zu + 1);
+__device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d) {
+    float fa[Q], fb[Q];
+    const uint32_t m = pull<true>(p, d, fa, fb);
+    const int n = d.n;
+    const float4 me = __ldg(p.dens + n);
+    const float ra = me.x, rb = me.y, pa = me.z, pb = me.w;
     float sa[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};  // sum_k w_k psi'(x+e_k) e_k
-    const long long n = ((long long)z * p.ny + y) * p.nx + x;
-    if (!m && !wall_lo && !wall_hi) {
+    if (!m && !d.wlo && !d.whi) {
 #pragma unroll
         for (int k = 1; k < Q; ++k) {
-            const int sl = ez(k) == 1 ? sp : ez(k) == -1 ? sm : s0;
-            const float qa = R.psi[sl][0][cy + ey(k)][cx + ex(k)];
-            const float qb = R.psi[sl][1][cy + ey(k)][cx + ex(k)];
-            sa[0] += wgt(k) * ex(k) * qa; sa[1] += wgt(k) * ey(k) * qa; sa[2] += wgt(k) * ez(k) * qa;
-            sb[0] += wgt(k) * ex(k) * qb; sb[1] += wgt(k) * ey(k) * qb; sb[2] += wgt(k) * ez(k) * qb;
+            const float4 q = __ldg(p.dens + n + nb_off(d, ex(k), ey(k), ez(k)));
+            sa[0] += wgt(k) * ex(k) * q.z; sa[1] += wgt(k) * ey(k) * q.z; sa[2] += wgt(k) * ez(k) * q.z;
+            sb[0] += wgt(k) * ex(k) * q.w; sb[1] += wgt(k) * ey(k) * q.w; sb[2] += wgt(k) * ez(k) * q.w;
         }
     } else {
         // partner densities across a cut or substrate link: mean over this
@@ -163,35 +176,32 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Ring<TX, T
         float ia = ra, ib = rb, cnt = 1.f;
 #pragma unroll
         for (int k = 1; k < Q; ++k) {
-            const bool solid = (ez(k) == 1 && wall_hi) || (ez(k) == -1 && wall_lo);
+            const bool solid = (ez(k) == 1 && d.whi) || (ez(k) == -1 && d.wlo);
             const bool cut = (m >> (k - 1)) & 1u;
             if (!solid && !cut) {
-                const int sl = ez(k) == 1 ? sp : ez(k) == -1 ? sm : s0;
-                ia += R.rho[sl][0][cy + ey(k)][cx + ex(k)];
-                ib += R.rho[sl][1][cy + ey(k)][cx + ex(k)];
-                cnt += 1.f;
+                const float4 q = __ldg(p.dens + n + nb_off(d, ex(k), ey(k), ez(k)));
+                ia += q.x; ib += q.y; cnt += 1.f;
             }
         }
         const float qa_eff = psi_of(ia / cnt), qb_eff = psi_of(ib / cnt);
 #pragma unroll
         for (int k = 1; k < Q; ++k) {
-            const bool solid = (ez(k) == 1 && wall_hi) || (ez(k) == -1 && wall_lo);
+            const bool solid = (ez(k) == 1 && d.whi) || (ez(k) == -1 && d.wlo);
             const bool cut = (m >> (k - 1)) & 1u;
             float qa, qb;
             if (solid || cut) {
                 qa = qa_eff; qb = qb_eff;
                 if (cut && !solid) {
                     // reaction of the decoupled interaction on the crossed element
-                    const int T = __ldg(p.tri + n * 18 + (k - 1));
+                    const int T = __ldg(p.tri + (long long)n * 18 + (k - 1));
                     const float r = p.G * wgt(k) * (pa * qb_eff + pb * qa_eff);
                     if (ex(k)) atomicAdd(p.FT + 3 * T + 0, ex(k) * r);
                     if (ey(k)) atomicAdd(p.FT + 3 * T + 1, ey(k) * r);
                     if (ez(k)) atomicAdd(p.FT + 3 * T + 2, ez(k) * r);
                 }
             } else {
-                const int sl = ez(k) == 1 ? sp : ez(k) == -1 ? sm : s0;
-                qa = R.psi[sl][0][cy + ey(k)][cx + ex(k)];
-                qb = R.psi[sl][1][cy + ey(k)][cx + ex(k)];
+                const float4 q = __ldg(p.dens + n + nb_off(d, ex(k), ey(k), ez(k)));
+                qa = q.z; qb = q.w;
             }
             sa[0] += wgt(k) * ex(k) * qa; sa[1] += wgt(k) * ey(k) * qa; sa[2] += wgt(k) * ez(k) * qa;
             sb[0] += wgt(k) * ex(k) * qb; sb[1] += wgt(k) * ey(k) * qb; sb[2] += wgt(k) * ez(k) * qb;
@@ -202,9 +212,10 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Ring<TX, T
     const float FB[3] = {-p.G * pb * sa[0], -p.G * pb * sa[1], -p.G * pb * sa[2]};
     float ja[3] = {0.f, 0.f, 0.f}, jb[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        ja[0] += ex(i) * fa[i]; ja[1] += ey(i) * fa[i]; ja[2] += ez(i) * fa[i];
-        jb[0] += ex(i) * fb[i]; jb[1] += ey(i) * fb[i]; jb[2] += ez(i) * fb[i];
+    for (int i = 1; i < Q; i += 2) {  // opposite pairs (i, i+1)
+        const float da = fa[i] - fa[i + 1], db = fb[i] - fb[i + 1];
+        ja[0] += ex(i) * da; ja[1] += ey(i) * da; ja[2] += ez(i) * da;
+        jb[0] += ex(i) * db; jb[1] += ey(i) * db; jb[2] += ez(i) * db;
     }
     // velocity shift: common velocity weighted by 1/tau, u^{c,eq} = u' + tau^c F^c / rho^c
     const float den = ra * p.itau[0] + rb * p.itau[1];
@@ -224,100 +235,48 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Ring<TX, T
         p.out[4 * p.N + n] = (ja[2] + jb[2] + 0.5f * (FA[2] + FB[2])) / rt;
     }
     if (!(ra + rb < 1e30f)) atomicOr(p.status, ST_NAN);
-    const float uua = ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2];
-    const float uub = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
-    float *__restrict__ dA = p.dst;
-    float *__restrict__ dB = p.dst + (long long)Q * p.N;
-    // Eq. 5; the rest population takes the mass balance (sum_i f^eq_i = rho)
-    // so that the float32 weights (which sum to 1 + 1.5e-8) create no mass
+    const float ka = 1.0f - 1.5f * (ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2]);
+    const float kb = 1.0f - 1.5f * (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
+    const int N = (int)p.N;
+    float *__restrict__ dA = p.dst + n;
+    float *__restrict__ dB = p.dst + (long long)Q * N + n;
+    const float ta = p.itau[0], tb = p.itau[1];
+    // Eq. 5 for opposite pairs: f^eq_{i,i+1} = w rho (ka + 4.5 eu^2 +- 3 eu); the
+    // rest population takes the mass balance (sum_i f^eq_i = rho) so that the
+    // float32 weights (which sum to 1 + 1.5e-8) create no mass
     float qa0 = ra, qb0 = rb;
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
+    for (int i = 1; i < Q; i += 2) {
         const float eua = ex(i) * ua[0] + ey(i) * ua[1] + ez(i) * ua[2];
         const float eub = ex(i) * ub[0] + ey(i) * ub[1] + ez(i) * ub[2];
-        const float qa = wgt(i) * ra * (1.0f + 3.0f * eua + 4.5f * eua * eua - 1.5f * uua);
-        const float qb = wgt(i) * rb * (1.0f + 3.0f * eub + 4.5f * eub * eub - 1.5f * uub);
-        qa0 -= qa;
-        qb0 -= qb;
-        dA[(long long)i * p.N + n] = fa[i] - (fa[i] - qa) * p.itau[0];
-        dB[(long long)i * p.N + n] = fb[i] - (fb[i] - qb) * p.itau[1];
+        const float wa = wgt(i) * ra, wb = wgt(i) * rb;
+        const float sa_ = wa * (ka + 4.5f * eua * eua), sb_ = wb * (kb + 4.5f * eub * eub);
+        const float qa1 = sa_ + 3.0f * wa * eua, qa2 = sa_ - 3.0f * wa * eua;
+        const float qb1 = sb_ + 3.0f * wb * eub, qb2 = sb_ - 3.0f * wb * eub;
+        qa0 -= qa1 + qa2;
+        qb0 -= qb1 + qb2;
+        dA[i * N] = fa[i] - (fa[i] - qa1) * ta;
+        dA[(i + 1) * N] = fa[i + 1] - (fa[i + 1] - qa2) * ta;
+        dB[i * N] = fb[i] - (fb[i] - qb1) * tb;
+        dB[(i + 1) * N] = fb[i + 1] - (fb[i + 1] - qb2) * tb;
     }
-    dA[n] = fa[0] - (fa[0] - qa0) * p.itau[0];
-    dB[n] = fb[0] - (fb[0] - qb0) * p.itau[1];
+    dA[0] = fa[0] - (fa[0] - qa0) * ta;
+    dB[0] = fb[0] - (fb[0] - qb0) * tb;
 }
 
-template <int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, 2) k_lb_fused(const LBParams p) {
-    __shared__ Ring<TX, TY> R;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int chunk = blockIdx.z;
-    const int z0 = p.zlo + chunk * p.zchunk;
-    const int z1 = min(z0 + p.zchunk, p.zhi);
-    if (z0 >= z1) return;
-    const int dir = (chunk & 1) ? -1 : 1;
-    const int zs = dir > 0 ? z0 : z1 - 1;
-    const int cnt = z1 - z0;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x = wrapi(x0 + tx, p.nx), y = wrapi(y0 + ty, p.ny);
-    const bool active = (x0 + tx < p.nx) && (y0 + ty < p.ny);
-
-    float ca[Q], cb[Q], na[Q], nb[Q];
-    uint32_t cm = 0, nm = 0;
-
-    // plane before the chunk (densities only)
-    {
-        const int zu = zs - dir;
-        if (!solid_plane(p, zu)) {
-            pull_node<false>(p, x, y, wrapi(zu, p.nz), na, nb, nm);
-            float ra = 0.f, rb = 0.f;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) { ra += na[i]; rb += nb[i]; }
-            store_ring(R, slot3(zu), ty + 1, tx + 1, ra, rb);
-            load_halo(p, R, zu, x0, y0);
-        }
-    }
-    // first plane of the chunk
-    {
-        if (active) pull_node<true>(p, x, y, wrapi(zs, p.nz), ca, cb, cm);
-        else pull_node<false>(p, x, y, wrapi(zs, p.nz), ca, cb, cm);
-        float ra = 0.f, rb = 0.f;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) { ra += ca[i]; rb += cb[i]; }
-        store_ring(R, slot3(zs), ty + 1, tx + 1, ra, rb);
-        load_halo(p, R, zs, x0, y0);
-    }
-    for (int s = 0; s < cnt; ++s) {
-        const int zu = zs + s * dir;
-        const int zn = zu + dir;
-        if (s + 1 < cnt || !solid_plane(p, zn)) {
-            const bool keep = s + 1 < cnt;
-            if (keep && active) pull_node<true>(p, x, y, wrapi(zn, p.nz), na, nb, nm);
-            else pull_node<false>(p, x, y, wrapi(zn, p.nz), na, nb, nm);
-            float ra = 0.f, rb = 0.f;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) { ra += na[i]; rb += nb[i]; }
-            store_ring(R, slot3(zn), ty + 1, tx + 1, ra, rb);
-            load_halo(p, R, zn, x0, y0);
-        }
-        __syncthreads();
-        if (active) collide_node<TX, TY>(p, R, zu, x, y, ca, cb, cm);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) { ca[i] = na[i]; cb[i] = nb[i]; }
-        cm = nm;
-        __syncthreads();
-    }
+__global__ void __launch_bounds__(BX *BY, 6) k_collide(const LBParams p) {
+    int x, y, z;
+    if (!node_of(p, x, y, z)) return;
+    for (; z < p.zhi; z += gridDim.z) collide_node(p, deltas(p, x, y, z));
 }
 
 cudaError_t launch_lb_step(const LBParams &p, int variant, cudaStream_t s) {
+    (void)variant;
     const int nzf = p.zhi - p.zlo;
-    const int nch = (nzf + p.zchunk - 1) / p.zchunk;
-    if (variant == 1) {
-        dim3 grid((p.nx + 31) / 32, (p.ny + 7) / 8, nch), block(32, 8);
-        k_lb_fused<32, 8><<<grid, block, 0, s>>>(p);
-    } else {
-        dim3 grid((p.nx + 31) / 32, (p.ny + 3) / 4, nch), block(32, 4);
-        k_lb_fused<32, 4><<<grid, block, 0, s>>>(p);
-    }
+    const int gz = p.zchunk > 0 ? (nzf + p.zchunk - 1) / p.zchunk : nzf;
+    dim3 grid((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, gz), block(BX, BY);
+    k_density<<<grid, block, 0, s>>>(p);
+    k_collide<<<grid, block, 0, s>>>(p);
     return cudaGetLastError();
 }
 

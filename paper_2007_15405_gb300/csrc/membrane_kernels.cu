@@ -1,23 +1,27 @@
 // Membrane phase of the coupled step and cut-link geometry (sm_103a).
 //
 // All capsules are concatenated: global node and element indices, with the
-// owning capsule per element and per node.  One step of the membrane phase
-// (Sec. 3.1, Eqs. 6-9, 11) is four short kernels:
-//   k_faces     per element: two-step average of the exchanged momentum,
-//               Skalak strain forces (Eq. 6), volume gradient terms (Eq. 8),
-//               cotangent-Laplacian contributions for the bending energy,
-//               FP64 per-capsule area and volume
-//   k_vert1     per node: mean-curvature vector and node area, gradients of
-//               the bending energy with respect to them; FP64 centroid and
-//               integer bounding box per capsule
-//   k_bend      per element: back-propagation of the bending energy (Eq. 7)
-//   k_vert2     per node: gathers of all element contributions (vertex->element
-//               CSR, no atomics), Hertz forces (Eq. 11), node update (Eq. 9),
-//               FP64 per-capsule force/torque sums
-// plus k_frozen for rigidly translated capsules.  The cut links for the moved
-// membrane are then rebuilt by k_cut_clear and k_cut_faces.
+// owning capsule per element and per node.  The membrane phase of one step
+// (Sec. 3.1, Eqs. 6-9, 11) is ONE cooperative kernel, k_membrane, whose
+// blocks stride over all elements / nodes of all capsules and meet at grid
+// barriers between four phases:
+//   1. per element: two-step average of the exchanged momentum, Skalak strain
+//      forces (Eq. 6), volume gradient terms (Eq. 8), cotangent-Laplacian
+//      contributions of the bending energy; FP64 area and volume
+//   2. per node: mean-curvature vector and node area, gradients of the
+//      bending energy with respect to them; FP64 centroid, bounding box
+//   3. per element: back-propagation of the bending energy (Eq. 7)
+//   4. per node: gathers of all element contributions (node -> element CSR,
+//      no atomics), Hertz forces (Eq. 11), node update (Eq. 9); FP64 sums of
+//      force, torque and total force
+//   5. (frozen capsules only) rigid translation with the summed force.
+// The grid barrier spins a bounded number of times; on timeout it raises a
+// status flag and the kernel returns.  The cut links for the moved membrane
+// are rebuilt by k_cut_clear and k_cut_faces.
 #include "cf_common.cuh"
 #include <cfloat>
+#include <climits>
+#include <algorithm>
 
 namespace cf {
 
@@ -31,28 +35,111 @@ __device__ __forceinline__ f3 cross(f3 a, f3 b) {
     return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
 __device__ __forceinline__ void st3(float *p, f3 v) { p[0] = v.x; p[1] = v.y; p[2] = v.z; }
-struct d3 { double x, y, z; };
-__device__ __forceinline__ d3 ld3d(const double *p, int i) { return {p[3 * i], p[3 * i + 1], p[3 * i + 2]}; }
-__device__ __forceinline__ f3 fdiff(d3 a, d3 b) {  // float(a - b), exact difference first
-    return {(float)(a.x - b.x), (float)(a.y - b.y), (float)(a.z - b.z)};
+// Node positions are float pairs hi + lo (|lo| <= ulp(hi)/2, ~48-bit
+// precision): per-step displacements (~1e-5) are below the float ulp at
+// x ~ 100, and GB300's FP64 pipe runs at a small fraction of the FP32 rate, so
+// positions are advanced with an exact two-sum and all geometry uses
+// differences (hi_a - hi_b) + (lo_a - lo_b) in float.
+struct pf { f3 h, l; };
+__device__ __forceinline__ pf ldp(const float *H, const float *L, int i) { return {ld3(H, i), ld3(L, i)}; }
+__device__ __forceinline__ f3 pdiff(const pf &a, const pf &b) {
+    return {(a.h.x - b.h.x) + (a.l.x - b.l.x), (a.h.y - b.h.y) + (a.l.y - b.l.y),
+            (a.h.z - b.h.z) + (a.l.z - b.l.z)};
 }
-__device__ __forceinline__ f3 tof(d3 a) { return {(float)a.x, (float)a.y, (float)a.z}; }
+// (h, l) += v exactly up to the pair's precision (Knuth two-sum, renormalised)
+__device__ __forceinline__ void pf_add(float &h, float &l, float v) {
+    const float s = h + v;
+    const float bb = s - h;
+    const float err = (h - (s - bb)) + (v - bb);
+    const float t = l + err;
+    const float h2 = s + t;
+    l = t - (h2 - s);
+    h = h2;
+}
+__device__ __forceinline__ void st_pos(float *H, float *L, int i, const pf &x, f3 v) {
+    float hx = x.h.x, hy = x.h.y, hz = x.h.z, lx = x.l.x, ly = x.l.y, lz = x.l.z;
+    pf_add(hx, lx, v.x); pf_add(hy, ly, v.y); pf_add(hz, lz, v.z);
+    st3(H + 3 * i, f3{hx, hy, hz});
+    st3(L + 3 * i, f3{lx, ly, lz});
+}
 
-// Warp-aggregated FP64 add into per-capsule accumulators: lanes sharing the
-// capsule id combine first, one atomic per group.
-__device__ __forceinline__ void acc_add(double *acc, int cap, int slot, double v, bool valid) {
+// Per-capsule sums: a warp that holds one capsule (the usual case, capsules
+// are contiguous) adds its 32 terms in float by shuffles and books the partial
+// with one FP64 atomic; mixed warps book per lane.  The accumulators are FP64.
+__device__ __forceinline__ void acc_add(double *acc, int cap, int slot, float v, bool valid) {
     const unsigned full = 0xffffffffu;
     const int key = valid ? cap : -1;
-    const unsigned grp = __match_any_sync(full, key);
-    const int leader = __ffs(grp) - 1;
-    const int lane = threadIdx.x & 31;
-    double s = 0.0;
-#pragma unroll 4
-    for (int src = 0; src < 32; ++src) {  // all lanes shuffle together
-        const double o = __shfl_sync(full, v, src);
-        if ((grp >> src) & 1u) s += o;
+    const int k0 = __shfl_sync(full, key, 0);
+    if (__all_sync(full, key == k0)) {
+        float s = valid ? v : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(full, s, o);
+        if ((threadIdx.x & 31) == 0 && k0 >= 0) atomicAdd(acc + k0 * A_NACC + slot, (double)s);
+    } else if (valid) {
+        atomicAdd(acc + cap * A_NACC + slot, (double)v);
     }
-    if (lane == leader && valid) atomicAdd(acc + cap * A_NACC + slot, s);
+}
+
+__device__ __forceinline__ void acc_minmax(int *bbox, int ncaps, int cap, f3 x, bool valid) {
+    const unsigned full = 0xffffffffu;
+    const int key = valid ? cap : -1;
+    const int k0 = __shfl_sync(full, key, 0);
+    const float lo[3] = {valid ? x.x : 3.0e38f, valid ? x.y : 3.0e38f, valid ? x.z : 3.0e38f};
+    const float hi[3] = {valid ? x.x : -3.0e38f, valid ? x.y : -3.0e38f, valid ? x.z : -3.0e38f};
+    if (__all_sync(full, key == k0)) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float mn = lo[a], mx = hi[a];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                mn = fminf(mn, __shfl_xor_sync(full, mn, o));
+                mx = fmaxf(mx, __shfl_xor_sync(full, mx, o));
+            }
+            if ((threadIdx.x & 31) == 0 && k0 >= 0) {
+                atomicMin(bbox + 3 * k0 + a, (int)floorf(mn));
+                atomicMax(bbox + 3 * ncaps + 3 * k0 + a, (int)ceilf(mx));
+            }
+        }
+    } else if (valid) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(bbox + 3 * cap + a, (int)floorf(lo[a]));
+            atomicMax(bbox + 3 * ncaps + 3 * cap + a, (int)ceilf(hi[a]));
+        }
+    }
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).
+// bar[0] counts arrivals, bar[1] is the generation.  Bounded spin: after
+// ~0.5 s without progress it raises ST_TIMEOUT and returns false.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned *status) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        ok = 1;
+        if (arrived == gridDim.x - 1) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned long long it = 0;
+            while (*gen == g) {
+                if (++it > (1ull << 24)) {
+                    atomicOr(status, ST_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
 }
 
 // cot of the angle at o between o->p and o->q, with gradients w.r.t. p, q
@@ -73,116 +160,87 @@ __device__ __forceinline__ float cot_only(f3 o, f3 p, f3 q) {
     return dot(u, w) / sqrtf(dot(n, n));
 }
 
-__global__ void k_faces(const MemParams p) {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = f < p.nfaces;
-    const int ff = valid ? f : 0;
-    const int cap = p.face_cap[ff];
-    const CapDev cp = p.caps[cap];
-    const int ia = p.faces[3 * ff], ib = p.faces[3 * ff + 1], ic = p.faces[3 * ff + 2];
-    const d3 da = ld3d(p.X, ia), db = ld3d(p.X, ib), dc = ld3d(p.X, ic);
+// Phase 1 for element f (global index): area and volume terms returned.
+__device__ __forceinline__ void face_pass(const MemParams &p, const CapDev &cp, int f, float &area,
+                                          float &vol) {
+    const int ia = p.faces[3 * f], ib = p.faces[3 * f + 1], ic = p.faces[3 * f + 2];
+    const pf pa = ldp(p.Xh, p.Xl, ia), pb = ldp(p.Xh, p.Xl, ib), pc = ldp(p.Xh, p.Xl, ic);
+    const pf po = ldp(p.Xh, p.Xl, cp.v0);  // capsule origin: its first node
     // element geometry in coordinates local to its first node (translation invariant)
-    const f3 a{0.f, 0.f, 0.f}, b = fdiff(db, da), c = fdiff(dc, da);
-    float *S = p.fscr + (long long)ff * FS_N;
-    double area = 0.0, vol = 0.0;
-    if (valid) {
-        // two-step average of the momentum exchanged with this element
-        const f3 ft = ld3(p.FT, ff), fp = ld3(p.FTprev, ff);
-        st3(S + FS_FBAR, 0.5f * (ft + fp));
-        st3(p.FTprev + 3 * ff, ft);
-        st3(p.FT + 3 * ff, f3{0.f, 0.f, 0.f});
-        const f3 u = b - a, w = c - a;
-        const f3 nrm = cross(u, w);
-        const float Af = 0.5f * sqrtf(dot(nrm, nrm));
-        area = Af;
-        // volume term in FP64 relative to the first node (translation invariant)
-        {
-            const double ux = u.x, uy = u.y, uz = u.z, wx = w.x, wy = w.y, wz = w.z;
-            const double ax = da.x, ay = da.y, az = da.z;
-            // x_a . (x_b x x_c) = x_a . (u x w) + ... ; use (a, a+u, a+w):
-            // a.(b x c) = a.((a+u) x (a+w)) = a.(u x w) (a.(a x .) = 0)
-            const double cx = uy * wz - uz * wy, cy = uz * wx - ux * wz, cz = ux * wy - uy * wx;
-            vol = (ax * cx + ay * cy + az * cz) / 6.0;
-        }
-        if (cp.mode == 0) {
-            // Skalak (Eq. 6): I1 = tr(G0^-1 g) - 2, I2 = det g / det G0 - 1
-            const float g11 = dot(u, u), g12 = dot(u, w), g22 = dot(w, w);
-            const float m11 = p.refM[3 * ff], m12 = p.refM[3 * ff + 1], m22 = p.refM[3 * ff + 2];
-            const float idet = 1.0f / p.refDet[ff];
-            const float I1 = m11 * g11 + 2.f * m12 * g12 + m22 * g22 - 2.f;
-            const float I2 = (g11 * g22 - g12 * g12) * idet - 1.f;
-            const float A0 = p.refA[ff];
-            const float dW1 = 0.25f * cp.kS * (2.f * I1 + 2.f);
-            const float dW2 = 0.25f * cp.kS * (-2.f + 2.f * cp.C * I2);
-            const f3 gb = A0 * (dW1 * (2.f * (m11 * u + m12 * w)) + dW2 * (2.f * idet * (g22 * u - g12 * w)));
-            const f3 gc = A0 * (dW1 * (2.f * (m12 * u + m22 * w)) + dW2 * (2.f * idet * (g11 * w - g12 * u)));
-            st3(S + FS_SK + 0, gb + gc);
-            st3(S + FS_SK + 3, -1.f * gb);
-            st3(S + FS_SK + 6, -1.f * gc);
-            // volume gradient terms (x_b x x_c etc.); their per-node sums are
-            // translation invariant on a closed mesh, so positions are taken
-            // relative to the capsule's first node to avoid cancellation
-            const d3 o = ld3d(p.X, cp.v0);
-            const f3 ra = fdiff(da, o), rb = fdiff(db, o), rc = fdiff(dc, o);
-            st3(S + FS_DV + 0, cross(rb, rc));
-            st3(S + FS_DV + 3, cross(rc, ra));
-            st3(S + FS_DV + 6, cross(ra, rb));
-            // bending, first pass: cotangents, Laplacian contributions, A_f/3
-            const float cta = cot_only(a, b, c), ctb = cot_only(b, c, a), ctc = cot_only(c, a, b);
-            st3(S + FS_L + 0, ctc * (b - a) + ctb * (c - a));
-            st3(S + FS_L + 3, cta * (c - b) + ctc * (a - b));
-            st3(S + FS_L + 6, ctb * (a - c) + cta * (b - c));
-            S[FS_AF3] = Af / 3.f;
-            S[FS_COT] = cta; S[FS_COT + 1] = ctb; S[FS_COT + 2] = ctc;
-        }
-    }
-    acc_add(p.acc, cap, A_AREA, area, valid);
-    acc_add(p.acc, cap, A_VOL, vol, valid);
+    const f3 a{0.f, 0.f, 0.f}, b = pdiff(pb, pa), c = pdiff(pc, pa);
+    const f3 ra = pdiff(pa, po);
+    float *S = p.fscr + (long long)f * FS_N;
+    // two-step average of the momentum exchanged with this element
+    const f3 ft = ld3(p.FT, f), fp = ld3(p.FTprev, f);
+    st3(S + FS_FBAR, 0.5f * (ft + fp));
+    st3(p.FTprev + 3 * f, ft);
+    st3(p.FT + 3 * f, f3{0.f, 0.f, 0.f});
+    const f3 u = b - a, w = c - a;
+    const f3 nrm = cross(u, w);
+    const float Af = 0.5f * sqrtf(dot(nrm, nrm));
+    area = Af;
+    vol = dot(ra, nrm) * (1.f / 6.f);  // (x_a - o) . (u x w) / 6, summed in FP64
+    if (cp.mode != 0) return;
+    // Skalak (Eq. 6): I1 = tr(G0^-1 g) - 2, I2 = det g / det G0 - 1
+    const float g11 = dot(u, u), g12 = dot(u, w), g22 = dot(w, w);
+    const float m11 = p.refM[3 * f], m12 = p.refM[3 * f + 1], m22 = p.refM[3 * f + 2];
+    const float idet = 1.0f / p.refDet[f];
+    const float I1 = m11 * g11 + 2.f * m12 * g12 + m22 * g22 - 2.f;
+    const float I2 = (g11 * g22 - g12 * g12) * idet - 1.f;
+    const float A0 = p.refA[f];
+    const float dW1 = 0.25f * cp.kS * (2.f * I1 + 2.f);
+    const float dW2 = 0.25f * cp.kS * (-2.f + 2.f * cp.C * I2);
+    const f3 gb = A0 * (dW1 * (2.f * (m11 * u + m12 * w)) + dW2 * (2.f * idet * (g22 * u - g12 * w)));
+    const f3 gc = A0 * (dW1 * (2.f * (m12 * u + m22 * w)) + dW2 * (2.f * idet * (g11 * w - g12 * u)));
+    st3(S + FS_SK + 0, gb + gc);
+    st3(S + FS_SK + 3, -1.f * gb);
+    st3(S + FS_SK + 6, -1.f * gc);
+    // volume gradient terms (x_b x x_c etc.); their per-node sums are
+    // translation invariant on a closed mesh, so positions are taken relative
+    // to the capsule's first node to avoid cancellation
+    const f3 rb = ra + b, rc = ra + c;
+    st3(S + FS_DV + 0, cross(rb, rc));
+    st3(S + FS_DV + 3, cross(rc, ra));
+    st3(S + FS_DV + 6, cross(ra, rb));
+    // bending, first pass: cotangents, Laplacian contributions, A_f/3
+    const float cta = cot_only(a, b, c), ctb = cot_only(b, c, a), ctc = cot_only(c, a, b);
+    st3(S + FS_L + 0, ctc * (b - a) + ctb * (c - a));
+    st3(S + FS_L + 3, cta * (c - b) + ctc * (a - b));
+    st3(S + FS_L + 6, ctb * (a - c) + cta * (b - c));
+    S[FS_AF3] = Af / 3.f;
 }
 
-__global__ void k_vert1(const MemParams p) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = v < p.nnodes;
-    const int vv = valid ? v : 0;
-    const int cap = p.node_cap[vv];
-    const CapDev cp = p.caps[cap];
-    const d3 x = ld3d(p.X, vv);
-    if (valid && cp.mode == 0) {
-        f3 L{0.f, 0.f, 0.f};
-        float A = 0.f;
-        for (int e = p.vf_off[vv]; e < p.vf_off[vv + 1]; ++e) {
-            const int ent = p.vf_ent[e];
-            const int f = ent / 3, sl = ent % 3;
+// Node -> element entries are visited eight at a time with all loads issued
+// before use (the gather is latency-bound).
+constexpr int VU = 8;
+
+__device__ __forceinline__ void node_bending_grad(const MemParams &p, const CapDev &cp, int v) {
+    f3 L{0.f, 0.f, 0.f};
+    float A = 0.f;
+    const int e0 = p.vf_off[v], e1 = p.vf_off[v + 1];
+    for (int eb = e0; eb < e1; eb += VU) {
+        int ent[VU];
+#pragma unroll
+        for (int j = 0; j < VU; ++j) ent[j] = eb + j < e1 ? __ldg(p.vf_ent + eb + j) : -1;
+#pragma unroll
+        for (int j = 0; j < VU; ++j) {
+            if (ent[j] < 0) continue;
+            const int f = ent[j] / 3, sl = ent[j] - 3 * f;
             const float *S = p.fscr + (long long)f * FS_N;
             L = L + ld3(S + FS_L, sl);
             A += S[FS_AF3];
         }
-        // E = kB/8 |L|^2 / A (Eq. 7, H0 = 0): dE/dL and dE/dA
-        const float iA = 1.f / A;
-        st3(p.vscr + 4 * vv, (0.25f * cp.kB * iA) * L);
-        p.vscr[4 * vv + 3] = -0.125f * cp.kB * dot(L, L) * iA * iA;
     }
-    acc_add(p.acc, cap, A_CX, x.x, valid);
-    acc_add(p.acc, cap, A_CY, x.y, valid);
-    acc_add(p.acc, cap, A_CZ, x.z, valid);
-    if (valid) {  // bbox: mins [3*ncaps] then maxs [3*ncaps]
-        atomicMin(p.bbox + 3 * cap + 0, (int)floor(x.x));
-        atomicMin(p.bbox + 3 * cap + 1, (int)floor(x.y));
-        atomicMin(p.bbox + 3 * cap + 2, (int)floor(x.z));
-        atomicMax(p.bbox + 3 * p.ncaps + 3 * cap + 0, (int)ceil(x.x));
-        atomicMax(p.bbox + 3 * p.ncaps + 3 * cap + 1, (int)ceil(x.y));
-        atomicMax(p.bbox + 3 * p.ncaps + 3 * cap + 2, (int)ceil(x.z));
-    }
+    const float iA = 1.f / A;
+    st3(p.vscr + 4 * v, (0.25f * cp.kB * iA) * L);
+    p.vscr[4 * v + 3] = -0.125f * cp.kB * dot(L, L) * iA * iA;
 }
 
-__global__ void k_bend(const MemParams p) {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= p.nfaces) return;
-    const int cap = p.face_cap[f];
-    if (p.caps[cap].mode != 0) return;
+// Phase 3 for element f: back-propagation of the bending energy.
+__device__ __forceinline__ void face_bending(const MemParams &p, int f) {
     const int ia = p.faces[3 * f], ib = p.faces[3 * f + 1], ic = p.faces[3 * f + 2];
-    const d3 pa = ld3d(p.X, ia);
-    const f3 a{0.f, 0.f, 0.f}, b = fdiff(ld3d(p.X, ib), pa), c = fdiff(ld3d(p.X, ic), pa);
+    const pf pa = ldp(p.Xh, p.Xl, ia);
+    const f3 a{0.f, 0.f, 0.f}, b = pdiff(ldp(p.Xh, p.Xl, ib), pa), c = pdiff(ldp(p.Xh, p.Xl, ic), pa);
     float *S = p.fscr + (long long)f * FS_N;
     f3 da_p, da_q, db_p, db_q, dc_p, dc_q;
     const float cta = cot_grad(a, b, c, da_p, da_q);  // p=b, q=c
@@ -209,7 +267,6 @@ __global__ void k_bend(const MemParams p) {
     st3(S + FS_BEND + 0, -1.f * ga);
     st3(S + FS_BEND + 3, -1.f * gb);
     st3(S + FS_BEND + 6, -1.f * gc);
-    (void)cta; (void)ctb; (void)ctc;
 }
 
 __device__ __forceinline__ float hertz(float xi, float d0, float d) {
@@ -217,20 +274,21 @@ __device__ __forceinline__ float hertz(float xi, float d0, float d) {
     return xi * o * sqrtf(o);
 }
 
-__global__ void k_vert2(const MemParams p) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = v < p.nnodes;
-    const int vv = valid ? v : 0;
-    const int cap = p.node_cap[vv];
-    const CapDev cp = p.caps[cap];
-    const d3 x = ld3d(p.X, vv);
-    f3 Fc{0.f, 0.f, 0.f}, Fe{0.f, 0.f, 0.f}, Fi{0.f, 0.f, 0.f};
-    if (valid) {
-        const bool el = cp.mode == 0;
-        f3 dv{0.f, 0.f, 0.f};
-        for (int e = p.vf_off[vv]; e < p.vf_off[vv + 1]; ++e) {
-            const int ent = p.vf_ent[e];
-            const int f = ent / 3, sl = ent % 3;
+// Phase 4 for node v: coupling, elastic and Hertz forces.
+__device__ __forceinline__ void node_forces(const MemParams &p, const CapDev &cp, int cap, int v,
+                                            float pre, const pf &x, f3 &Fc, f3 &Ft) {
+    Fc = f3{0.f, 0.f, 0.f};
+    f3 Fe{0.f, 0.f, 0.f}, Fi{0.f, 0.f, 0.f}, dv{0.f, 0.f, 0.f};
+    const bool el = cp.mode == 0;
+    const int e0 = p.vf_off[v], e1 = p.vf_off[v + 1];
+    for (int eb = e0; eb < e1; eb += VU) {
+        int ent[VU];
+#pragma unroll
+        for (int j = 0; j < VU; ++j) ent[j] = eb + j < e1 ? __ldg(p.vf_ent + eb + j) : -1;
+#pragma unroll
+        for (int j = 0; j < VU; ++j) {
+            if (ent[j] < 0) continue;
+            const int f = ent[j] / 3, sl = ent[j] - 3 * f;
             const float *S = p.fscr + (long long)f * FS_N;
             Fc = Fc + ld3(S + FS_FBAR, 0);
             if (el) {
@@ -238,97 +296,163 @@ __global__ void k_vert2(const MemParams p) {
                 dv = dv + ld3(S + FS_DV, sl);
             }
         }
-        Fc = (1.f / 3.f) * Fc;
-        if (el) {
-            const double V = p.acc[cap * A_NACC + A_VOL];
-            const float pre = (float)(-(double)cp.kV * (V - cp.V0) / cp.V0 / 6.0);
-            Fe = Fe + pre * dv;
-        }
-        // Hertz (Eq. 11): substrate plane
-        if (p.wall) {
-            const float d = (float)(x.z - (double)p.zrep);
-            if (d < p.delta0) Fi.z += hertz(p.xi, p.delta0, d);
-        }
-        // Hertz: nodes of other capsules (bounding boxes prefilter)
-        for (int c2 = 0; c2 < p.ncaps; ++c2) {
-            if (c2 == cap) continue;
-            const int *lo = p.bbox + 3 * c2, *hi = p.bbox + 3 * p.ncaps + 3 * c2;
-            if (x.z < lo[2] - p.delta0 || x.z > hi[2] + p.delta0) continue;
-            for (int sy = -1; sy <= 1; ++sy)
-                for (int sx = -1; sx <= 1; ++sx) {
-                    const double ox = sx * p.nx, oy = sy * p.ny;
-                    if (x.x + ox < lo[0] - p.delta0 || x.x + ox > hi[0] + p.delta0) continue;
-                    if (x.y + oy < lo[1] - p.delta0 || x.y + oy > hi[1] + p.delta0) continue;
-                    const CapDev c2d = p.caps[c2];
-                    for (int w = c2d.v0; w < c2d.v0 + c2d.nv; ++w) {
-                        const d3 y = ld3d(p.X, w);
-                        f3 dd = fdiff(x, y);
-                        dd.x -= p.nx * floorf(dd.x / p.nx + 0.5f);
-                        dd.y -= p.ny * floorf(dd.y / p.ny + 0.5f);
-                        const float d = sqrtf(dot(dd, dd));
-                        if (d < p.delta0 && d > 0.f) Fi = Fi + (hertz(p.xi, p.delta0, d) / d) * dd;
-                    }
+    }
+    Fc = (1.f / 3.f) * Fc;
+    if (el) Fe = Fe + pre * dv;
+    // Hertz (Eq. 11): substrate plane
+    if (p.wall) {
+        const float d = (x.h.z - p.zrep) + x.l.z;
+        if (d < p.delta0) Fi.z += hertz(p.xi, p.delta0, d);
+    }
+    // Hertz: nodes of other capsules, prefiltered by their bounding boxes of
+    // the previous step widened by one lattice unit (nodes move far less per step)
+    const float pad = p.delta0 + 1.0f;
+    for (int c2 = 0; c2 < p.ncaps; ++c2) {
+        if (c2 == cap) continue;
+        const int *lo = p.bbox_prev + 3 * c2, *hi = p.bbox_prev + 3 * p.ncaps + 3 * c2;
+        if (x.h.z < lo[2] - pad || x.h.z > hi[2] + pad) continue;
+        for (int sy = -1; sy <= 1; ++sy)
+            for (int sx = -1; sx <= 1; ++sx) {
+                const float ox = (float)(sx * p.nx), oy = (float)(sy * p.ny);
+                if (x.h.x + ox < lo[0] - pad || x.h.x + ox > hi[0] + pad) continue;
+                if (x.h.y + oy < lo[1] - pad || x.h.y + oy > hi[1] + pad) continue;
+                const CapDev c2d = p.caps[c2];
+                for (int w = c2d.v0; w < c2d.v0 + c2d.nv; ++w) {
+                    f3 dd = pdiff(x, ldp(p.Xh, p.Xl, w));
+                    dd.x -= p.nx * floorf(dd.x / p.nx + 0.5f);
+                    dd.y -= p.ny * floorf(dd.y / p.ny + 0.5f);
+                    const float d = sqrtf(dot(dd, dd));
+                    if (d < p.delta0 && d > 0.f) Fi = Fi + (hertz(p.xi, p.delta0, d) / d) * dd;
                 }
-        }
+            }
     }
-    const f3 Ft = Fc + Fe + Fi;
-    if (valid) {
-        st3(p.Fcpl + 3 * vv, Fc);
-        if (cp.mode == 0) {
-            const f3 vel = (1.f / cp.mass) * Ft;
-            st3(p.V + 3 * vv, vel);
-            p.Xn[3 * vv] = x.x + vel.x;
-            p.Xn[3 * vv + 1] = x.y + vel.y;
-            p.Xn[3 * vv + 2] = x.z + vel.z;
-        } else if (cp.mode == 2) {
-            st3(p.V + 3 * vv, f3{0.f, 0.f, 0.f});
-            p.Xn[3 * vv] = x.x;
-            p.Xn[3 * vv + 1] = x.y;
-            p.Xn[3 * vv + 2] = x.z;
-        }
-    }
-    // per-capsule FP64 sums: coupling force, its torque about the centroid, total force
-    const double icnt = 1.0 / cp.nv;
-    const double rx = x.x - p.acc[cap * A_NACC + A_CX] * icnt;
-    const double ry = x.y - p.acc[cap * A_NACC + A_CY] * icnt;
-    const double rz = x.z - p.acc[cap * A_NACC + A_CZ] * icnt;
-    acc_add(p.acc, cap, A_FX, Fc.x, valid);
-    acc_add(p.acc, cap, A_FY, Fc.y, valid);
-    acc_add(p.acc, cap, A_FZ, Fc.z, valid);
-    acc_add(p.acc, cap, A_TX, ry * Fc.z - rz * Fc.y, valid);
-    acc_add(p.acc, cap, A_TY, rz * Fc.x - rx * Fc.z, valid);
-    acc_add(p.acc, cap, A_TZ, rx * Fc.y - ry * Fc.x, valid);
-    acc_add(p.acc, cap, A_FTX, Ft.x, valid);
-    acc_add(p.acc, cap, A_FTY, Ft.y, valid);
-    acc_add(p.acc, cap, A_FTZ, Ft.z, valid);
+    Ft = Fc + Fe + Fi;
 }
 
-__global__ void k_frozen(const MemParams p) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= p.nnodes) return;
-    const int cap = p.node_cap[v];
-    const CapDev cp = p.caps[cap];
-    if (cp.mode != 1) return;
-    const double s = 1.0 / ((double)cp.mass * cp.nv);
-    const f3 vel{(float)(p.acc[cap * A_NACC + A_FTX] * s), (float)(p.acc[cap * A_NACC + A_FTY] * s),
-                 (float)(p.acc[cap * A_NACC + A_FTZ] * s)};
-    st3(p.V + 3 * v, vel);
-    const d3 x = ld3d(p.X, v);
-    p.Xn[3 * v] = x.x + vel.x;
-    p.Xn[3 * v + 1] = x.y + vel.y;
-    p.Xn[3 * v + 2] = x.z + vel.z;
+constexpr int MT = 256;  // threads per block of the membrane kernel
+
+__global__ void __launch_bounds__(MT) k_membrane(const MemParams p) {
+    const int gt = blockIdx.x * MT + threadIdx.x, gs = gridDim.x * MT;
+    // 1. elements
+    for (int base = 0; base < p.nfaces; base += gs) {
+        const int f = base + gt;
+        const bool valid = f < p.nfaces;
+        const int cap = p.face_cap[valid ? f : 0];
+        float area = 0.f, vol = 0.f;
+        if (valid) face_pass(p, p.caps[cap], f, area, vol);
+        acc_add(p.acc, cap, A_AREA, area, valid);
+        acc_add(p.acc, cap, A_VOL, vol, valid);
+    }
+    if (!grid_barrier(p.bar, p.status)) return;
+    // 2. nodes: bending gradients, centroid (relative to the capsule's first
+    //    node), bounding box
+    for (int base = 0; base < p.nnodes; base += gs) {
+        const int v = base + gt;
+        const bool valid = v < p.nnodes;
+        const int vv = valid ? v : 0;
+        const int cap = p.node_cap[vv];
+        const CapDev cp = p.caps[cap];
+        if (valid && cp.mode == 0) node_bending_grad(p, cp, vv);
+        const pf x = ldp(p.Xh, p.Xl, vv);
+        const f3 r = pdiff(x, ldp(p.Xh, p.Xl, cp.v0));
+        if (valid && vv == cp.v0) {
+            double *A = p.acc + cap * A_NACC;
+            A[A_OX] = (double)x.h.x + x.l.x;
+            A[A_OY] = (double)x.h.y + x.l.y;
+            A[A_OZ] = (double)x.h.z + x.l.z;
+        }
+        acc_add(p.acc, cap, A_CX, r.x, valid);
+        acc_add(p.acc, cap, A_CY, r.y, valid);
+        acc_add(p.acc, cap, A_CZ, r.z, valid);
+        acc_minmax(p.bbox, p.ncaps, cap, x.h, valid);
+    }
+    if (!grid_barrier(p.bar, p.status)) return;
+    // 3. elements: bending back-propagation
+    for (int f = gt; f < p.nfaces; f += gs)
+        if (p.caps[p.face_cap[f]].mode == 0) face_bending(p, f);
+    if (!grid_barrier(p.bar, p.status)) return;
+    // 4. nodes: forces, node update, sums
+    for (int base = 0; base < p.nnodes; base += gs) {
+        const int v = base + gt;
+        const bool valid = v < p.nnodes;
+        const int vv = valid ? v : 0;
+        const int cap = p.node_cap[vv];
+        const CapDev cp = p.caps[cap];
+        const double *A = p.acc + cap * A_NACC;
+        f3 Fc{0.f, 0.f, 0.f}, Ft{0.f, 0.f, 0.f}, r{0.f, 0.f, 0.f};
+        if (valid) {
+            const pf x = ldp(p.Xh, p.Xl, vv);
+            // volume penalty prefactor -kV (V - V0) / V0 / 6 (Eq. 8); V is the
+            // FP64 sum of the element terms relative to the first node
+            const float pre = (float)(-(double)cp.kV * (A[A_VOL] - cp.V0) / cp.V0 / 6.0);
+            node_forces(p, cp, cap, vv, pre, x, Fc, Ft);
+            st3(p.Fcpl + 3 * vv, Fc);
+            if (cp.mode == 0) {
+                const f3 vel = (1.f / cp.mass) * Ft;
+                st3(p.V + 3 * vv, vel);
+                st_pos(p.Xnh, p.Xnl, vv, x, vel);
+            } else if (cp.mode == 2) {
+                st3(p.V + 3 * vv, f3{0.f, 0.f, 0.f});
+                st_pos(p.Xnh, p.Xnl, vv, x, f3{0.f, 0.f, 0.f});
+            }
+            const float ic = 1.f / cp.nv;
+            const f3 cen{(float)A[A_CX] * ic, (float)A[A_CY] * ic, (float)A[A_CZ] * ic};
+            r = pdiff(x, ldp(p.Xh, p.Xl, cp.v0)) - cen;
+        }
+        const f3 tq = cross(r, Fc);
+        acc_add(p.acc, cap, A_FX, Fc.x, valid);
+        acc_add(p.acc, cap, A_FY, Fc.y, valid);
+        acc_add(p.acc, cap, A_FZ, Fc.z, valid);
+        acc_add(p.acc, cap, A_TX, tq.x, valid);
+        acc_add(p.acc, cap, A_TY, tq.y, valid);
+        acc_add(p.acc, cap, A_TZ, tq.z, valid);
+        acc_add(p.acc, cap, A_FTX, Ft.x, valid);
+        acc_add(p.acc, cap, A_FTY, Ft.y, valid);
+        acc_add(p.acc, cap, A_FTZ, Ft.z, valid);
+    }
+    if (!p.any_frozen) return;
+    if (!grid_barrier(p.bar, p.status)) return;
+    // 5. frozen shapes: rigid translation with the summed force
+    for (int v = gt; v < p.nnodes; v += gs) {
+        const int cap = p.node_cap[v];
+        const CapDev cp = p.caps[cap];
+        if (cp.mode != 1) continue;
+        const double *A = p.acc + cap * A_NACC;
+        const double sc = 1.0 / ((double)cp.mass * cp.nv);
+        const f3 vel{(float)(A[A_FTX] * sc), (float)(A[A_FTY] * sc), (float)(A[A_FTZ] * sc)};
+        st3(p.V + 3 * v, vel);
+        st_pos(p.Xnh, p.Xnl, v, ldp(p.Xh, p.Xl, v), vel);
+    }
+}
+
+int membrane_grid(int nfaces, int nnodes) {
+    static int max_blocks = -1;
+    if (max_blocks < 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_membrane, MT, 0);
+        max_blocks = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int want = (std::max(nfaces, nnodes) + MT - 1) / MT;
+    return std::max(1, std::min(want, std::min(max_blocks, 152)));
 }
 
 cudaError_t launch_membrane(const MemParams &p, bool any_frozen, cudaStream_t s, int *nl) {
-    const int bt = 128;
-    const int gf = (p.nfaces + bt - 1) / bt, gv = (p.nnodes + bt - 1) / bt;
-    k_faces<<<gf, bt, 0, s>>>(p);
-    k_vert1<<<gv, bt, 0, s>>>(p);
-    k_bend<<<gf, bt, 0, s>>>(p);
-    k_vert2<<<gv, bt, 0, s>>>(p);
-    *nl += 4;
-    if (any_frozen) { k_frozen<<<gv, bt, 0, s>>>(p); *nl += 1; }
-    return cudaGetLastError();
+    (void)any_frozen;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(membrane_grid(p.nfaces, p.nnodes));
+    cfg.blockDim = dim3(MT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_membrane, p);
+    *nl += 1;
+    return e;
 }
 
 // ---------------------------------------------------------------- cut links
@@ -345,19 +469,26 @@ __device__ __forceinline__ double orient_d(f3 a, f3 b, f3 c, f3 d) {
     const double nx = r2y * r3z - r2z * r3y, ny = r2z * r3x - r2x * r3z, nz = r2x * r3y - r2y * r3x;
     return r1x * nx + r1y * ny + r1z * nz;
 }
+constexpr float OEPS = 1e-4f;
 
-// segment P->Q crosses triangle ABC (sign(0) = + convention)
-__device__ bool seg_tri(f3 P, f3 Qp, f3 A, f3 B, f3 C) {
-    const float EPS = 1e-4f;
-    const float dp = orient_f(A, B, C, P), dq = orient_f(A, B, C, Qp);
-    if (fabsf(dp) > EPS && fabsf(dq) > EPS) {
-        if ((dp >= 0.f) == (dq >= 0.f)) return false;
-        const float s1 = orient_f(P, Qp, A, B), s2 = orient_f(P, Qp, B, C), s3 = orient_f(P, Qp, C, A);
-        if (fabsf(s1) > EPS && fabsf(s2) > EPS && fabsf(s3) > EPS)
-            return ((s1 >= 0.f) == (s2 >= 0.f)) && ((s2 >= 0.f) == (s3 >= 0.f));
-    }
-    const double Dp = orient_d(A, B, C, P), Dq = orient_d(A, B, C, Qp);
-    if ((Dp >= 0.0) == (Dq >= 0.0)) return false;
+// FP64 decisions are rare and kept out of line: GB300's FP64 pipe is a small
+// fraction of its FP32 rate, and an inlined fallback may be if-converted.
+__device__ __noinline__ bool side_of_d(f3 A, f3 B, f3 C, f3 P) { return orient_d(A, B, C, P) >= 0.0; }
+
+// sign (sign(0) = +) of the orientation of P relative to the plane ABC, decided
+// in FP32 when clear and in FP64 otherwise
+__device__ __forceinline__ bool side_of(f3 A, f3 B, f3 C, f3 P) {
+    const float d = orient_f(A, B, C, P);
+    if (fabsf(d) > OEPS) return d >= 0.f;
+    return side_of_d(A, B, C, P);
+}
+
+// segment P->Q, already known to have its end points on opposite sides of the
+// plane, crosses triangle ABC (sign(0) = + convention on the edge tests)
+__device__ __noinline__ bool edges_pass(f3 P, f3 Qp, f3 A, f3 B, f3 C) {
+    const float s1 = orient_f(P, Qp, A, B), s2 = orient_f(P, Qp, B, C), s3 = orient_f(P, Qp, C, A);
+    if (fabsf(s1) > OEPS && fabsf(s2) > OEPS && fabsf(s3) > OEPS)
+        return ((s1 >= 0.f) == (s2 >= 0.f)) && ((s2 >= 0.f) == (s3 >= 0.f));
     const double S1 = orient_d(P, Qp, A, B), S2 = orient_d(P, Qp, B, C), S3 = orient_d(P, Qp, C, A);
     return ((S1 >= 0.0) == (S2 >= 0.0)) && ((S2 >= 0.0) == (S3 >= 0.0));
 }
@@ -369,8 +500,9 @@ __global__ void k_cut_clear(const CutParams p) {
         const int n = p.prev_list[i];
         p.mask[n] = 0u;
         p.touched[n] = 0u;
+        int2 *t2 = reinterpret_cast<int2 *>(p.tri + (long long)n * 18);  // 72 B rows, 8-byte aligned
 #pragma unroll
-        for (int k = 0; k < 18; ++k) p.tri[(long long)n * 18 + k] = 0x7fffffff;
+        for (int k = 0; k < 9; ++k) t2[k] = make_int2(0x7fffffff, 0x7fffffff);
     }
 }
 
@@ -378,51 +510,115 @@ __device__ __forceinline__ void mark(const CutParams &p, int x, int y, int z, in
     const long long n = ((long long)wrapi(z, p.nz) * p.ny + wrapi(y, p.ny)) * p.nx + wrapi(x, p.nx);
     atomicXor(p.mask + n, 1u << (k - 1));
     atomicMin(p.tri + n * 18 + (k - 1), T);
-    if (atomicExch(p.touched + n, 1u) == 0u) {
-        const int idx = atomicAdd(p.count, 1);
-        if (idx < p.capacity) p.list[idx] = (int)n;
-        else atomicOr(p.status, ST_OVERFLOW);
+    const bool fresh = atomicExch(p.touched + n, 1u) == 0u;
+    // warp-aggregated append of newly touched nodes to the list
+    const unsigned act = __activemask();
+    const unsigned want = __ballot_sync(act, fresh);
+    if (want) {
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(want) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(p.count, __popc(want));
+        base = __shfl_sync(act, base, leader);
+        if (fresh) {
+            const int idx = base + __popc(want & ((1u << lane) - 1u));
+            if (idx < p.capacity) p.list[idx] = (int)n;
+            else atomicOr(p.status, ST_OVERFLOW);
+        }
     }
 }
 
-// one warp per element: all links (x, x+e_k), k in the nine positive
-// directions, starting within one unit of the element's bounding box
-__global__ void k_cut_faces(const CutParams p) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= p.nfaces) return;
-    const int T = warp;
-    const f3 A = tof(ld3d(p.X, p.faces[3 * T])), B = tof(ld3d(p.X, p.faces[3 * T + 1])),
-             C = tof(ld3d(p.X, p.faces[3 * T + 2]));
-    const int lx = (int)ceilf(fminf(A.x, fminf(B.x, C.x)) - 1.f), hx = (int)floorf(fmaxf(A.x, fmaxf(B.x, C.x)) + 1.f);
-    const int ly = (int)ceilf(fminf(A.y, fminf(B.y, C.y)) - 1.f), hy = (int)floorf(fmaxf(A.y, fmaxf(B.y, C.y)) + 1.f);
-    const int lz = (int)ceilf(fminf(A.z, fminf(B.z, C.z)) - 1.f), hz = (int)floorf(fmaxf(A.z, fmaxf(B.z, C.z)) + 1.f);
-    const int sx = hx - lx + 1, sy = hy - ly + 1, sz = hz - lz + 1;
-    const int total = sx * sy * sz * 9;
+// Edge tests and marks for the links of start node (x, y, z) whose end points
+// lie on opposite sides of the element's plane (rare, out of line).
+__device__ __noinline__ void crossing_links(const CutParams p, unsigned dirs, int x, int y, int z,
+                                            f3 A, f3 B, f3 C, int T) {
     constexpr int POS[9] = {1, 3, 5, 7, 9, 11, 13, 15, 17};
-    for (int t = lane; t < total; t += 32) {
-        const int d = t % 9;
-        const int node = t / 9;
-        const int x = lx + node % sx, y = ly + (node / sx) % sy, z = lz + node / (sx * sy);
-        int k = 1, kx = 0, ky = 0, kz = 0;
-#pragma unroll
-        for (int j = 0; j < 9; ++j)
-            if (j == d) { k = POS[j]; kx = ex(POS[j]); ky = ey(POS[j]); kz = ez(POS[j]); }
+    for (; dirs; dirs &= dirs - 1u) {
+        const int k = POS[__ffs(dirs) - 1];
+        const int kx = ex(k), ky = ey(k), kz = ez(k);
         if (p.wall && (wrapi(z, p.nz) == 0 || wrapi(z + kz, p.nz) == 0)) continue;
         const f3 P{(float)x, (float)y, (float)z};
         const f3 Qp{(float)(x + kx), (float)(y + ky), (float)(z + kz)};
-        if (seg_tri(P, Qp, A, B, C)) {
+        if (edges_pass(P, Qp, A, B, C)) {
             mark(p, x, y, z, k, T);
             mark(p, x + kx, y + ky, z + kz, opp(k), T);
         }
     }
 }
 
+// One warp per element.  The links (x, x+e_k), k in the nine positive
+// directions, that can touch the element start within one unit of its
+// bounding box (the start box, at most 4 nodes per axis for elements shorter
+// than two lattice units); their end points lie in the start box widened by
+// one unit (at most 6 per axis).  The warp first decides the plane side of
+// every node of the widened box (one orientation each, a bit per node), then
+// each lane takes start nodes and checks their nine links, running the three
+// edge tests only where the end points lie on opposite sides.  Box indices use
+// constant strides, so no division by a run-time value is needed.
+constexpr int CUT_WARPS = 8;
+constexpr int SB = 4, WB = 6, WB3 = WB * WB * WB;  // start / widened box capacity
+constexpr int SIDE_WORDS = (WB3 + 31) / 32;
+
+__global__ void __launch_bounds__(CUT_WARPS * 32) k_cut_faces(const CutParams p) {
+    __shared__ unsigned side[CUT_WARPS][SIDE_WORDS];
+    __shared__ float wq[SIDE_WORDS * 32][3];  // widened-box offsets of q (x, y, z)
+    for (int q = threadIdx.x; q < SIDE_WORDS * 32; q += blockDim.x) {
+        const int z = q / (WB * WB), r = q - z * (WB * WB), y = r / WB, x = r - y * WB;
+        wq[q][0] = (float)x; wq[q][1] = (float)y; wq[q][2] = (float)z;
+    }
+    __syncthreads();
+    const int wib = threadIdx.x >> 5;
+    const int T = blockIdx.x * CUT_WARPS + wib;
+    const int lane = threadIdx.x & 31;
+    if (T >= p.nfaces) return;
+    // the decision is taken on the float (hi) positions
+    const f3 A = ld3(p.X, p.faces[3 * T]), B = ld3(p.X, p.faces[3 * T + 1]),
+             C = ld3(p.X, p.faces[3 * T + 2]);
+    // start box: [ceil(min-1), floor(max+1)] per axis
+    const float flx = ceilf(fminf(A.x, fminf(B.x, C.x)) - 1.f), fhx = floorf(fmaxf(A.x, fmaxf(B.x, C.x)) + 1.f);
+    const float fly = ceilf(fminf(A.y, fminf(B.y, C.y)) - 1.f), fhy = floorf(fmaxf(A.y, fmaxf(B.y, C.y)) + 1.f);
+    const float flz = ceilf(fminf(A.z, fminf(B.z, C.z)) - 1.f), fhz = floorf(fmaxf(A.z, fmaxf(B.z, C.z)) + 1.f);
+    const int sx = (int)(fhx - flx) + 1, sy = (int)(fhy - fly) + 1, sz = (int)(fhz - flz) + 1;
+    if (sx > SB || sy > SB || sz > SB) {  // element longer than the boxes allow
+        if (lane == 0) atomicOr(p.status, ST_OVERFLOW);
+        return;
+    }
+    // plane side of each widened-box node q = x + WB*y + WB*WB*z (origin start - 1)
+    const float wxl = (float)(sx + 2), wyl = (float)(sy + 2), wzl = (float)(sz + 2);
+    for (int base = 0; base < SIDE_WORDS * 32; base += 32) {
+        const int q = base + lane;
+        const float x = wq[q][0], y = wq[q][1], z = wq[q][2];
+        bool s = false;
+        if (q < WB3 && x < wxl && y < wyl && z < wzl)
+            s = side_of(A, B, C, f3{flx - 1.f + x, fly - 1.f + y, flz - 1.f + z});
+        const unsigned b = __ballot_sync(0xffffffffu, s);
+        if (lane == 0) side[wib][base >> 5] = b;
+    }
+    __syncwarp();
+    // links: lane owns start nodes s = x + SB*y + SB*SB*z
+    for (int sidx = lane; sidx < SB * SB * SB; sidx += 32) {
+        const int xi = sidx & (SB - 1), yi = (sidx >> 2) & (SB - 1), zi = sidx >> 4;
+        if (xi >= sx || yi >= sy || zi >= sz) continue;
+        const int qa = (xi + 1) + WB * (yi + 1) + WB * WB * (zi + 1);
+        const bool sa = (side[wib][qa >> 5] >> (qa & 31)) & 1u;
+        unsigned cross_dirs = 0u;  // bit d: link d has end points on both sides
+#pragma unroll
+        for (int d = 0; d < 9; ++d) {
+            constexpr int POS[9] = {1, 3, 5, 7, 9, 11, 13, 15, 17};
+            const int k = POS[d];
+            const int qb = qa + ex(k) + WB * ey(k) + WB * WB * ez(k);
+            const bool sb = (side[wib][qb >> 5] >> (qb & 31)) & 1u;
+            cross_dirs |= (sa != sb ? 1u : 0u) << d;
+        }
+        if (cross_dirs)
+            crossing_links(p, cross_dirs, (int)flx + xi, (int)fly + yi, (int)flz + zi, A, B, C, T);
+    }
+}
+
 cudaError_t launch_cuts(const CutParams &p, int prev_hint, cudaStream_t s, int *nl) {
     (void)prev_hint;
     k_cut_clear<<<152, 256, 0, s>>>(p);
-    const long long threads = (long long)p.nfaces * 32;
-    k_cut_faces<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(p);
+    k_cut_faces<<<(p.nfaces + CUT_WARPS - 1) / CUT_WARPS, CUT_WARPS * 32, 0, s>>>(p);
     *nl += 2;
     return cudaGetLastError();
 }
