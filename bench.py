@@ -252,7 +252,7 @@ def run_ours(args):
                      "frac": achieved / peak, "traffic": None,
                      "algorithmic_bytes_per_launch": ALG_BYTES_PER_LU * wl.nodes,
                      "kernel_ms": lb_ms},
-        "phases_ms": {"lattice": ph[0], "membrane": ph[1], "cut_links": ph[2]},
+        "phases_ms": {"lattice": ph[0], "membrane": ph[1], "cut_links": ph[2], "bounce_prep": ph[3]},
         "clocks": clk,
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,

@@ -164,11 +164,11 @@ cf_status cf_meniscus_profile(cf_ctx *ctx, int id, double *r, double *zeta, size
 cf_status cf_cuts(cf_ctx *ctx, uint32_t *mask, int *tri, uint8_t *inside);
 
 /* Advance n steps like cf_step, without graph replay, timing each phase with
- * CUDA events on the context stream; ms[0..2] receive the mean device time per
- * step of the lattice kernel, of the membrane phase and of the cut-link
- * rebuild (milliseconds).  Synchronises.  For measurement; the populations
- * advance exactly as with cf_step. */
-cf_status cf_time_phases(cf_ctx *ctx, long long n, double ms[3]);
+ * CUDA events on the context stream; ms[0..3] receive the mean device time per
+ * step of the two lattice passes, of the membrane phase, of the cut-link
+ * rebuild and of the bounce-record preparation (milliseconds).  Synchronises.
+ * For measurement; the populations advance exactly as with cf_step. */
+cf_status cf_time_phases(cf_ctx *ctx, long long n, double ms[4]);
 
 /* Number of kernel launches issued by the last cf_step / cf_time_phases call. */
 cf_status cf_launch_count(cf_ctx *ctx, long long *n);

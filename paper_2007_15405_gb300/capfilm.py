@@ -209,8 +209,9 @@ class Simulation:
         _check(_lib.cf_sync(self._h))
 
     def time_phases(self, n):
-        """Mean device ms per step of (lattice, membrane, cut links) over n steps."""
-        ms = np.zeros(3)
+        """Mean device ms per step of (lattice passes, membrane, cut links, bounce
+        records) over n steps."""
+        ms = np.zeros(4)
         _check(_lib.cf_time_phases(self._h, int(n), _ptr(ms)))
         return ms
 

@@ -58,7 +58,11 @@ struct cf_ctx {
     float4 *dens = nullptr;
     uint32_t *mask = nullptr;
     int *tri = nullptr;
-    uint32_t *touched = nullptr;
+    uint32_t *owner = nullptr;    // claim flags of cut nodes
+    int *cutrec = nullptr;        // [N] bounce record of a cut node
+    int *uniq = nullptr;          // distinct cut nodes
+    int *ucount = nullptr;
+    float *rec = nullptr;         // [capacity][38] bounce records
     uint8_t *inside = nullptr;
     int *list[2] = {nullptr, nullptr};
     int *counts = nullptr;  // [2]
@@ -148,6 +152,8 @@ LBParams lb_params(cf_ctx *c, bool with_out) {
     p.FT = c->FT;
     p.out = with_out ? c->out : nullptr;
     p.dens = c->dens;
+    p.cutrec = c->cutrec;
+    p.rec = c->rec;
     p.status = c->status;
     return p;
 }
@@ -197,7 +203,10 @@ cf_status enqueue_cuts(cf_ctx *c, const float *X, int *nl) {
     q.X = X;
     q.mask = c->mask;
     q.tri = c->tri;
-    q.touched = c->touched;
+    q.owner = c->owner;
+    q.uniq = c->uniq;
+    q.ucount = c->ucount;
+    q.cutrec = c->cutrec;
     q.list = c->list[cur];
     q.count = c->counts + cur;
     q.prev_count = c->counts + c->lpar;
@@ -205,6 +214,7 @@ cf_status enqueue_cuts(cf_ctx *c, const float *X, int *nl) {
     q.capacity = c->capacity;
     q.status = c->status;
     CF_CUDA(cudaMemsetAsync(c->counts + cur, 0, sizeof(int), c->stream));
+    CF_CUDA(cudaMemsetAsync(c->ucount, 0, sizeof(int), c->stream));
     CF_CUDA(launch_cuts(q, 0, c->stream, nl));
     c->lpar = cur;
     return CF_OK;
@@ -213,6 +223,23 @@ cf_status enqueue_cuts(cf_ctx *c, const float *X, int *nl) {
 // One coupled step on the stream (also used under graph capture).  ev, when
 // given, receives four events bracketing the lattice, membrane and cut phases.
 cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev = nullptr) {
+    if (ev) CF_CUDA(cudaEventRecord(ev[4], c->stream));
+    if (c->nnodes) {  // bounce records of the cut nodes for this step's streaming
+        PrepParams q{};
+        q.N = c->N;
+        q.src = c->f[c->fpar];
+        q.dens = c->dens;
+        q.mask = c->mask;
+        q.tri = c->tri;
+        q.faces = c->faces;
+        q.V = c->V;
+        q.uniq = c->uniq;
+        q.ucount = c->ucount;
+        q.rec = c->rec;
+        q.FT = c->FT;
+        q.capacity = c->capacity;
+        CF_CUDA(launch_prep(q, c->stream, nl));
+    }
     if (ev) CF_CUDA(cudaEventRecord(ev[0], c->stream));
     CF_CUDA(launch_lb_step(lb_params(c, with_out), c->lb_variant, c->stream));
     *nl += 2;
@@ -386,14 +413,19 @@ cf_status build_membrane(cf_ctx *c) {
     CF_CUDA(up(c->vf_ent, vf_ent.data(), sizeof(int) * vf_ent.size()));
     CF_CUDA(up(c->capdev, cd.data(), sizeof(CapDev) * cd.size()));
     // cut-link node lists: nodes within one link of any element
-    c->capacity = (int)std::min<long long>(c->N, 24LL * nf + 4096);
+    c->capacity = (int)std::min<long long>(36LL * c->N, 24LL * nf + 4096);
     for (int k = 0; k < 2; ++k) {
         c->list[k] = (int *)dalloc(c, sizeof(int) * (size_t)c->capacity, true);
         if (!c->list[k]) return fail(CF_ENOMEM, "device allocation failed (cut lists)");
     }
+    c->uniq = (int *)dalloc(c, sizeof(int) * (size_t)c->capacity, true);
+    c->ucount = (int *)dalloc(c, sizeof(int), true);
+    c->rec = (float *)dalloc(c, sizeof(float) * 2 * Q * (size_t)c->capacity, true);
+    if (!c->uniq || !c->ucount || !c->rec) return fail(CF_ENOMEM, "device allocation failed (cut records)");
+    CF_CUDA(cudaMemsetAsync(c->ucount, 0, sizeof(int), c->stream));
     // start from a clean cut structure
     CF_CUDA(cudaMemsetAsync(c->mask, 0, sizeof(uint32_t) * c->N, c->stream));
-    CF_CUDA(cudaMemsetAsync(c->touched, 0, sizeof(uint32_t) * c->N, c->stream));
+    CF_CUDA(cudaMemsetAsync(c->owner, 0, sizeof(uint32_t) * c->N, c->stream));
     CF_CUDA(cudaMemsetAsync(c->tri, 0x7f, sizeof(int) * 18 * (size_t)c->N, c->stream));
     CF_CUDA(cudaMemsetAsync(c->counts, 0, sizeof(int) * 2, c->stream));
     // 0x7f7f7f7f is not INT_MAX but any value above every element index works
@@ -445,14 +477,15 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     c->dens = (float4 *)dalloc(c, sizeof(float4) * N);
     c->mask = (uint32_t *)dalloc(c, sizeof(uint32_t) * N);
     c->tri = (int *)dalloc(c, sizeof(int) * 18 * N);
-    c->touched = (uint32_t *)dalloc(c, sizeof(uint32_t) * N);
+    c->owner = (uint32_t *)dalloc(c, sizeof(uint32_t) * N);
+    c->cutrec = (int *)dalloc(c, sizeof(int) * N);
     c->inside = (uint8_t *)dalloc(c, N);
     c->counts = (int *)dalloc(c, sizeof(int) * 2);
     c->status = (unsigned *)dalloc(c, sizeof(unsigned));
     c->bar = (unsigned *)dalloc(c, sizeof(unsigned) * 2);
     c->dscratch = (double *)dalloc(c, sizeof(double) * 8);
     c->hscratch = (float *)dalloc(c, sizeof(float) * desc->nx * desc->ny);
-    if (!c->f[0] || !c->f[1] || !c->out || !c->dens || !c->mask || !c->tri || !c->touched || !c->inside ||
+    if (!c->f[0] || !c->f[1] || !c->out || !c->dens || !c->mask || !c->tri || !c->owner || !c->cutrec || !c->inside ||
         !c->counts || !c->status || !c->bar || !c->dscratch || !c->hscratch) {
         cf_destroy(c);
         return fail(CF_ENOMEM, "device allocation failed");
@@ -462,7 +495,8 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     cudaMemsetAsync(c->out, 0, sizeof(float) * 5 * N, c->stream);
     cudaMemsetAsync(c->mask, 0, sizeof(uint32_t) * N, c->stream);
     cudaMemsetAsync(c->tri, 0x7f, sizeof(int) * 18 * N, c->stream);
-    cudaMemsetAsync(c->touched, 0, sizeof(uint32_t) * N, c->stream);
+    cudaMemsetAsync(c->owner, 0, sizeof(uint32_t) * N, c->stream);
+    cudaMemsetAsync(c->cutrec, 0, sizeof(int) * N, c->stream);
     cudaMemsetAsync(c->inside, 0, N, c->stream);
     cudaMemsetAsync(c->counts, 0, sizeof(int) * 2, c->stream);
     cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream);
@@ -545,7 +579,7 @@ cf_status cf_set_film(cf_ctx *c, double h_top, double rmaj, double rmin, double 
         djit = c->jit;
     }
     if (c->nfaces) CF_CUDA(launch_inside(c->mask, c->inside, c->d.nx, c->d.ny, c->d.nz, c->stream));
-    CF_CUDA(launch_init_film(c->f[c->fpar], N, c->d.nx, c->d.ny, c->d.nz, c->d.wall, (float)h_top,
+    CF_CUDA(launch_init_film(c->f[c->fpar], c->dens, N, c->d.nx, c->d.ny, c->d.nz, c->d.wall, (float)h_top,
                              (float)rmaj, (float)rmin, (float)rmix, djit, c->inside, c->stream));
     c->film_set = true;
     return sync_ok(c);
@@ -579,7 +613,7 @@ cf_status cf_step(cf_ctx *c, long long n) {
         {
             // count the launches of one step pair (for reporting)
             const bool fx = c->all_fixed;
-            per_pair = 2 * (2 + (c->nnodes ? 1 + (fx ? 0 : 2) : 0));
+            per_pair = 2 * (2 + (c->nnodes ? 2 + (fx ? 0 : 3) : 0));
         }
         while (left >= 2) {
             CF_CUDA(cudaGraphLaunch(c->graph, c->stream));
@@ -599,22 +633,26 @@ cf_status cf_step(cf_ctx *c, long long n) {
     return CF_OK;
 }
 
-cf_status cf_time_phases(cf_ctx *c, long long n, double ms[3]) {
+cf_status cf_time_phases(cf_ctx *c, long long n, double ms[4]) {
     if (!c || !ms || n <= 0) return fail(CF_EINVAL, "bad argument");
     if (!c->film_set) return fail(CF_ESTATE, "cf_set_film must come before cf_time_phases");
-    std::vector<cudaEvent_t> ev(4 * (size_t)n);
+    std::vector<cudaEvent_t> ev(5 * (size_t)n);
     for (auto &e : ev) CF_CUDA(cudaEventCreate(&e));
     int nl = 0;
     cf_status st = CF_OK;
-    for (long long k = 0; k < n && st == CF_OK; ++k) st = enqueue_step(c, k == n - 1, &nl, &ev[4 * k]);
+    for (long long k = 0; k < n && st == CF_OK; ++k) st = enqueue_step(c, k == n - 1, &nl, &ev[5 * k]);
     CF_CUDA(cudaStreamSynchronize(c->stream));
-    ms[0] = ms[1] = ms[2] = 0.0;
-    for (long long k = 0; k < n && st == CF_OK; ++k)
+    ms[0] = ms[1] = ms[2] = ms[3] = 0.0;
+    for (long long k = 0; k < n && st == CF_OK; ++k) {
         for (int q = 0; q < 3; ++q) {
             float t = 0.f;
-            CF_CUDA(cudaEventElapsedTime(&t, ev[4 * k + q], ev[4 * k + q + 1]));
+            CF_CUDA(cudaEventElapsedTime(&t, ev[5 * k + q], ev[5 * k + q + 1]));
             ms[q] += t / n;
         }
+        float t = 0.f;
+        CF_CUDA(cudaEventElapsedTime(&t, ev[5 * k + 4], ev[5 * k]));
+        ms[3] += t / n;
+    }
     for (auto &e : ev) cudaEventDestroy(e);
     if (st != CF_OK) return st;
     c->steps_done += n;

@@ -40,6 +40,8 @@ struct LBParams {
     const int *__restrict__ faces;      // element nodes [3*nfaces]
     const float *__restrict__ V;        // node velocities [3*nnodes]
     float *__restrict__ FT;             // element momentum exchange accumulators [3*nfaces]
+    const int *__restrict__ cutrec;     // [N] bounce record of a cut node
+    const float *__restrict__ rec;      // [capacity][2*Q] bounced populations
     float *__restrict__ out;            // optional [5][N]: rhoA, rhoB, ux, uy, uz
     float4 *__restrict__ dens;          // [N] (rhoA, rhoB, psiA, psiB) of this step
     unsigned *__restrict__ status;      // device error flags
@@ -102,13 +104,32 @@ struct CutParams {
     const float *X;          // positions (float, hi part) the cut links are computed for
     uint32_t *mask;
     int *tri;
-    uint32_t *touched;       // [N] node listed flag
-    int *list;               // touched-node list
+    uint32_t *owner;         // [N] claim flag of cut nodes (reset with the masks)
+    int *list;               // marked nodes, with repetitions
     int *count;              // entries appended to `list` (zeroed before)
     const int *prev_count;   // entries of `prev_list`
     int *prev_list;          // list of the previous computation (cleared first)
+    int *uniq;               // distinct cut nodes
+    int *ucount;             // entries of `uniq` (zeroed before)
+    int *cutrec;             // [N] index into `uniq` / the bounce records of a cut node
     int capacity;
     unsigned *status;
+};
+
+// Bounce records of the cut nodes for the next streaming (built once per step).
+struct PrepParams {
+    long long N;
+    const float *src;        // post-collision populations about to be streamed
+    const float4 *dens;      // (rhoA, rhoB, ...) of the step that produced them
+    const uint32_t *mask;
+    const int *tri;
+    const int *faces;
+    const float *V;
+    const int *uniq;
+    const int *ucount;
+    float *rec;              // [capacity][2*Q] bounced populations (cut directions)
+    float *FT;               // element momentum exchange accumulators
+    int capacity;
 };
 
 __host__ __device__ inline int wrapi(int a, int n) {
@@ -121,7 +142,7 @@ __host__ __device__ inline int wrapi(int a, int n) {
 // Host-side launchers (defined in the kernel translation units).
 namespace cf {
 cudaError_t launch_lb_step(const LBParams &p, int tx_variant, cudaStream_t s);
-cudaError_t launch_init_film(float *f, long long N, int nx, int ny, int nz, int wall,
+cudaError_t launch_init_film(float *f, float4 *dens, long long N, int nx, int ny, int nz, int wall,
                              float h_top, float rmaj, float rmin, float rmix,
                              const double *jit, const uint8_t *inside, cudaStream_t s);
 cudaError_t launch_inside(const uint32_t *mask, uint8_t *inside, int nx, int ny, int nz,
@@ -131,4 +152,5 @@ cudaError_t launch_meniscus(const float *out, const uint8_t *inside, float *h, i
 cudaError_t launch_mass(const float *f, long long N, double *m2, cudaStream_t s);
 cudaError_t launch_membrane(const MemParams &p, bool any_frozen, cudaStream_t s, int *nlaunch);
 cudaError_t launch_cuts(const CutParams &p, int prev_count_hint, cudaStream_t s, int *nlaunch);
+cudaError_t launch_prep(const PrepParams &p, cudaStream_t s, int *nlaunch);
 }  // namespace cf

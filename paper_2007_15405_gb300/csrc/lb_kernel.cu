@@ -67,49 +67,8 @@ __device__ __forceinline__ int src_off(const Deltas &d, int N, int i) {
     return i * N + nb_off(d, -ex(i), -ey(i), -ez(i));
 }
 
-// Membrane-cut links of node n: the population the node sent towards the
-// membrane comes back with Ladd's term -2 w_k rho (e_k . u_T)/c_s^2, where rho
-// is the node's density (= sum of its post-collision populations) and u_T the
-// mean velocity of the crossed element's three nodes.  OWNER books the
-// exchanged momentum on the element.  Only nodes next to a membrane get here;
-// the path is kept out of line and returns the bounced populations through
-// patch[2][Q] (entries of uncut directions are left untouched).
-template <bool OWNER>
-__device__ __noinline__ void bounce_cut(const LBParams p, int n, uint32_t m, float *patch) {
-    const int N = (int)p.N;
-    const float *sA = p.src + n, *sB = p.src + (long long)Q * N + n;
-    float rwa = 0.f, rwb = 0.f;
-    for (int j = 0; j < Q; ++j) {
-        rwa += __ldg(sA + j * N);
-        rwb += __ldg(sB + j * N);
-    }
-    for (int k = 1; k < Q; ++k) {
-        if (!((m >> (k - 1)) & 1u)) continue;
-        const int kx = ex(k), ky = ey(k), kz = ez(k);
-        const int T = __ldg(p.tri + (long long)n * 18 + (k - 1));
-        const int a = __ldg(p.faces + 3 * T), b = __ldg(p.faces + 3 * T + 1),
-                  c = __ldg(p.faces + 3 * T + 2);
-        const float ux = (p.V[3 * a] + p.V[3 * b] + p.V[3 * c]) * (1.0f / 3.0f);
-        const float uy = (p.V[3 * a + 1] + p.V[3 * b + 1] + p.V[3 * c + 1]) * (1.0f / 3.0f);
-        const float uz = (p.V[3 * a + 2] + p.V[3 * b + 2] + p.V[3 * c + 2]) * (1.0f / 3.0f);
-        const float eu = kx * ux + ky * uy + kz * uz;
-        const float foa = __ldg(sA + k * N), fob = __ldg(sB + k * N);
-        const float w6 = 6.0f * wgt(k);
-        const float ca = w6 * rwa * eu, cb = w6 * rwb * eu;
-        patch[opp(k)] = foa - ca;
-        patch[Q + opp(k)] = fob - cb;
-        if (OWNER) {
-            const float sx = (2.0f * foa - ca) + (2.0f * fob - cb);
-            if (kx) atomicAdd(p.FT + 3 * T + 0, kx * sx);
-            if (ky) atomicAdd(p.FT + 3 * T + 1, ky * sx);
-            if (kz) atomicAdd(p.FT + 3 * T + 2, kz * sx);
-        }
-    }
-}
-
-// Post-streaming populations of the node: coalesced gathers, then the rare
-// cut-link patch.
-template <bool OWNER>
+// Post-streaming populations of the node: coalesced gathers, then the
+// bounce-back values of its membrane-cut links.
 __device__ __forceinline__ uint32_t pull(const LBParams &p, const Deltas &d, float (&fa)[Q],
                                          float (&fb)[Q]) {
     const int N = (int)p.N;
@@ -123,12 +82,16 @@ __device__ __forceinline__ uint32_t pull(const LBParams &p, const Deltas &d, flo
         fb[i] = __ldg(sB + o);
     }
     if (m) {
-        float patch[2 * Q];
+        // membrane-cut links: the bounced populations (Ladd's moving-wall term
+        // included) were prepared for this step by k_cut_prep
+        const float *R = p.rec + (long long)__ldg(p.cutrec + d.n) * (2 * Q);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) { patch[i] = fa[i]; patch[Q + i] = fb[i]; }
-        bounce_cut<OWNER>(p, d.n, m, patch);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) { fa[i] = patch[i]; fb[i] = patch[Q + i]; }
+        for (int k = 1; k < Q; ++k) {
+            if ((m >> (k - 1)) & 1u) {
+                fa[opp(k)] = __ldg(R + opp(k));
+                fb[opp(k)] = __ldg(R + Q + opp(k));
+            }
+        }
     }
     return m;
 }
@@ -147,7 +110,7 @@ __global__ void __launch_bounds__(BX *BY, 6) k_density(const LBParams p) {
     for (; z < p.zhi; z += gridDim.z) {
         const Deltas d = deltas(p, x, y, z);
         float fa[Q], fb[Q];
-        pull<false>(p, d, fa, fb);
+        pull(p, d, fa, fb);
         float ra = 0.f, rb = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) { ra += fa[i]; rb += fb[i]; }
@@ -158,7 +121,7 @@ __global__ void __launch_bounds__(BX *BY, 6) k_density(const LBParams p) {
 // Shan-Chen force with decoupling, velocity shift, BGK, store.
 __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d) {
     float fa[Q], fb[Q];
-    const uint32_t m = pull<true>(p, d, fa, fb);
+    const uint32_t m = pull(p, d, fa, fb);
     const int n = d.n;
     const float4 me = __ldg(p.dens + n);
     const float ra = me.x, rb = me.y, pa = me.z, pb = me.w;
@@ -281,8 +244,8 @@ cudaError_t launch_lb_step(const LBParams &p, int variant, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------ film set-up
-__global__ void k_init_film(float *f, long long N, int nx, int ny, int nz, int wall, float h_top,
-                           float rmaj, float rmin, float rmix, const double *jit,
+__global__ void k_init_film(float *f, float4 *dens, long long N, int nx, int ny, int nz, int wall,
+                           float h_top, float rmaj, float rmin, float rmix, const double *jit,
                            const uint8_t *inside) {
     const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= N) return;
@@ -297,18 +260,23 @@ __global__ void k_init_film(float *f, long long N, int nx, int ny, int nz, int w
         else { r[0] = rmin; r[1] = rmaj; }
         if (jit) { r[0] += jit[n]; r[1] += jit[N + n]; }
     }
+    float ra = 0.f, rb = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const double w = i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
-        f[(long long)i * N + n] = (float)(w * r[0]);
-        f[(long long)(Q + i) * N + n] = (float)(w * r[1]);
+        const float fa = (float)(w * r[0]), fb = (float)(w * r[1]);
+        f[(long long)i * N + n] = fa;
+        f[(long long)(Q + i) * N + n] = fb;
+        ra += fa;
+        rb += fb;
     }
+    dens[n] = make_float4(ra, rb, psi_of(ra), psi_of(rb));  // density of the initial state
 }
 
-cudaError_t launch_init_film(float *f, long long N, int nx, int ny, int nz, int wall, float h_top,
-                             float rmaj, float rmin, float rmix, const double *jit,
+cudaError_t launch_init_film(float *f, float4 *dens, long long N, int nx, int ny, int nz, int wall,
+                             float h_top, float rmaj, float rmin, float rmix, const double *jit,
                              const uint8_t *inside, cudaStream_t s) {
-    k_init_film<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(f, N, nx, ny, nz, wall, h_top, rmaj,
+    k_init_film<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(f, dens, N, nx, ny, nz, wall, h_top, rmaj,
                                                              rmin, rmix, jit, inside);
     return cudaGetLastError();
 }

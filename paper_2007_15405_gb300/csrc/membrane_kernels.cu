@@ -17,7 +17,8 @@
 //   5. (frozen capsules only) rigid translation with the summed force.
 // The grid barrier spins a bounded number of times; on timeout it raises a
 // status flag and the kernel returns.  The cut links for the moved membrane
-// are rebuilt by k_cut_clear and k_cut_faces.
+// are rebuilt by k_cut_clear, k_cut_faces and k_cut_claim; k_cut_prep builds
+// the bounce records of the cut nodes at the start of each step.
 #include "cf_common.cuh"
 #include <cfloat>
 #include <climits>
@@ -485,12 +486,15 @@ __device__ __forceinline__ bool side_of(f3 A, f3 B, f3 C, f3 P) {
 
 // segment P->Q, already known to have its end points on opposite sides of the
 // plane, crosses triangle ABC (sign(0) = + convention on the edge tests)
-__device__ __noinline__ bool edges_pass(f3 P, f3 Qp, f3 A, f3 B, f3 C) {
+__device__ __noinline__ bool edges_pass_d(f3 P, f3 Qp, f3 A, f3 B, f3 C) {
+    const double S1 = orient_d(P, Qp, A, B), S2 = orient_d(P, Qp, B, C), S3 = orient_d(P, Qp, C, A);
+    return ((S1 >= 0.0) == (S2 >= 0.0)) && ((S2 >= 0.0) == (S3 >= 0.0));
+}
+__device__ __forceinline__ bool edges_pass(f3 P, f3 Qp, f3 A, f3 B, f3 C) {
     const float s1 = orient_f(P, Qp, A, B), s2 = orient_f(P, Qp, B, C), s3 = orient_f(P, Qp, C, A);
     if (fabsf(s1) > OEPS && fabsf(s2) > OEPS && fabsf(s3) > OEPS)
         return ((s1 >= 0.f) == (s2 >= 0.f)) && ((s2 >= 0.f) == (s3 >= 0.f));
-    const double S1 = orient_d(P, Qp, A, B), S2 = orient_d(P, Qp, B, C), S3 = orient_d(P, Qp, C, A);
-    return ((S1 >= 0.0) == (S2 >= 0.0)) && ((S2 >= 0.0) == (S3 >= 0.0));
+    return edges_pass_d(P, Qp, A, B, C);
 }
 
 __global__ void k_cut_clear(const CutParams p) {
@@ -499,32 +503,42 @@ __global__ void k_cut_clear(const CutParams p) {
          i += gridDim.x * blockDim.x) {
         const int n = p.prev_list[i];
         p.mask[n] = 0u;
-        p.touched[n] = 0u;
+        p.owner[n] = 0u;
         int2 *t2 = reinterpret_cast<int2 *>(p.tri + (long long)n * 18);  // 72 B rows, 8-byte aligned
 #pragma unroll
         for (int k = 0; k < 9; ++k) t2[k] = make_int2(0x7fffffff, 0x7fffffff);
     }
 }
 
+// Toggle the cut bit of link k at node (x, y, z), keep the smallest crossing
+// element and list the node (fire-and-forget atomics; the list append is
+// aggregated over the active lanes of the warp).
 __device__ __forceinline__ void mark(const CutParams &p, int x, int y, int z, int k, int T) {
     const long long n = ((long long)wrapi(z, p.nz) * p.ny + wrapi(y, p.ny)) * p.nx + wrapi(x, p.nx);
     atomicXor(p.mask + n, 1u << (k - 1));
     atomicMin(p.tri + n * 18 + (k - 1), T);
-    const bool fresh = atomicExch(p.touched + n, 1u) == 0u;
-    // warp-aggregated append of newly touched nodes to the list
     const unsigned act = __activemask();
-    const unsigned want = __ballot_sync(act, fresh);
-    if (want) {
-        const int lane = threadIdx.x & 31;
-        const int leader = __ffs(want) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(p.count, __popc(want));
-        base = __shfl_sync(act, base, leader);
-        if (fresh) {
-            const int idx = base + __popc(want & ((1u << lane) - 1u));
-            if (idx < p.capacity) p.list[idx] = (int)n;
-            else atomicOr(p.status, ST_OVERFLOW);
-        }
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(act) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(p.count, __popc(act));
+    base = __shfl_sync(act, base, leader);
+    const int idx = base + __popc(act & ((1u << lane) - 1u));
+    if (idx < p.capacity) p.list[idx] = (int)n;
+    else atomicOr(p.status, ST_OVERFLOW);
+}
+
+// Distinct cut nodes: the first list entry of a node whose links stayed cut
+// claims it and gets a bounce-record slot.
+__global__ void k_cut_claim(const CutParams p) {
+    const int cnt = min(*p.count, p.capacity);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+        const int n = p.list[i];
+        if (p.mask[n] == 0u) continue;  // crossings cancelled out
+        if (atomicExch(p.owner + n, 1u) != 0u) continue;
+        const int u = atomicAdd(p.ucount, 1);
+        p.uniq[u] = n;
+        p.cutrec[n] = u;
     }
 }
 
@@ -546,80 +560,121 @@ __device__ __noinline__ void crossing_links(const CutParams p, unsigned dirs, in
     }
 }
 
-// One warp per element.  The links (x, x+e_k), k in the nine positive
-// directions, that can touch the element start within one unit of its
+// One thread per (element, start node).  The links (x, x+e_k), k in the nine
+// positive directions, that can touch an element start within one unit of its
 // bounding box (the start box, at most 4 nodes per axis for elements shorter
-// than two lattice units); their end points lie in the start box widened by
-// one unit (at most 6 per axis).  The warp first decides the plane side of
-// every node of the widened box (one orientation each, a bit per node), then
-// each lane takes start nodes and checks their nine links, running the three
-// edge tests only where the end points lie on opposite sides.  Box indices use
-// constant strides, so no division by a run-time value is needed.
-constexpr int CUT_WARPS = 8;
-constexpr int SB = 4, WB = 6, WB3 = WB * WB * WB;  // start / widened box capacity
-constexpr int SIDE_WORDS = (WB3 + 31) / 32;
+// than two lattice units).  Each thread takes one node of that box, decides
+// the plane side of the node and of its nine link partners (one orientation
+// each), and for links with end points on both sides whose crossing point
+// falls inside the element's box widened by 1e-3 (a conservative float
+// prefilter) runs the exact edge tests.
+constexpr int SB = 4, SB3 = SB * SB * SB;      // start box capacity
+constexpr int CUT_T = 256, CUT_EPB = CUT_T / SB3;  // threads / elements per block
 
-__global__ void __launch_bounds__(CUT_WARPS * 32) k_cut_faces(const CutParams p) {
-    __shared__ unsigned side[CUT_WARPS][SIDE_WORDS];
-    __shared__ float wq[SIDE_WORDS * 32][3];  // widened-box offsets of q (x, y, z)
-    for (int q = threadIdx.x; q < SIDE_WORDS * 32; q += blockDim.x) {
-        const int z = q / (WB * WB), r = q - z * (WB * WB), y = r / WB, x = r - y * WB;
-        wq[q][0] = (float)x; wq[q][1] = (float)y; wq[q][2] = (float)z;
-    }
-    __syncthreads();
-    const int wib = threadIdx.x >> 5;
-    const int T = blockIdx.x * CUT_WARPS + wib;
-    const int lane = threadIdx.x & 31;
+__device__ __forceinline__ bool plane_side(const f3 &nrm, const f3 &A, const f3 &B, const f3 &C,
+                                           f3 P) {
+    // orientation det[B-A; C-A; P-A] = ((B-A) x (C-A)) . (P-A); P - A is exact
+    // for nodes within a few units of A
+    const float d = dot(nrm, P - A);
+    return fabsf(d) > OEPS ? d >= 0.f : side_of_d(A, B, C, P);
+}
+
+__global__ void __launch_bounds__(CUT_T) k_cut_faces(const CutParams p) {
+    const int T = blockIdx.x * CUT_EPB + (int)(threadIdx.x / SB3);
     if (T >= p.nfaces) return;
+    const int sidx = threadIdx.x & (SB3 - 1);
+    const int xi = sidx & (SB - 1), yi = (sidx >> 2) & (SB - 1), zi = sidx >> 4;
     // the decision is taken on the float (hi) positions
     const f3 A = ld3(p.X, p.faces[3 * T]), B = ld3(p.X, p.faces[3 * T + 1]),
              C = ld3(p.X, p.faces[3 * T + 2]);
+    const f3 emin{fminf(A.x, fminf(B.x, C.x)), fminf(A.y, fminf(B.y, C.y)), fminf(A.z, fminf(B.z, C.z))};
+    const f3 emax{fmaxf(A.x, fmaxf(B.x, C.x)), fmaxf(A.y, fmaxf(B.y, C.y)), fmaxf(A.z, fmaxf(B.z, C.z))};
     // start box: [ceil(min-1), floor(max+1)] per axis
-    const float flx = ceilf(fminf(A.x, fminf(B.x, C.x)) - 1.f), fhx = floorf(fmaxf(A.x, fmaxf(B.x, C.x)) + 1.f);
-    const float fly = ceilf(fminf(A.y, fminf(B.y, C.y)) - 1.f), fhy = floorf(fmaxf(A.y, fmaxf(B.y, C.y)) + 1.f);
-    const float flz = ceilf(fminf(A.z, fminf(B.z, C.z)) - 1.f), fhz = floorf(fmaxf(A.z, fmaxf(B.z, C.z)) + 1.f);
-    const int sx = (int)(fhx - flx) + 1, sy = (int)(fhy - fly) + 1, sz = (int)(fhz - flz) + 1;
-    if (sx > SB || sy > SB || sz > SB) {  // element longer than the boxes allow
-        if (lane == 0) atomicOr(p.status, ST_OVERFLOW);
+    const float flx = ceilf(emin.x - 1.f), fly = ceilf(emin.y - 1.f), flz = ceilf(emin.z - 1.f);
+    const float fsx = floorf(emax.x + 1.f) - flx, fsy = floorf(emax.y + 1.f) - fly,
+                fsz = floorf(emax.z + 1.f) - flz;  // box span - 1
+    if (fsx >= SB || fsy >= SB || fsz >= SB) {  // element longer than the box allows
+        if (sidx == 0) atomicOr(p.status, ST_OVERFLOW);
         return;
     }
-    // plane side of each widened-box node q = x + WB*y + WB*WB*z (origin start - 1)
-    const float wxl = (float)(sx + 2), wyl = (float)(sy + 2), wzl = (float)(sz + 2);
-    for (int base = 0; base < SIDE_WORDS * 32; base += 32) {
-        const int q = base + lane;
-        const float x = wq[q][0], y = wq[q][1], z = wq[q][2];
-        bool s = false;
-        if (q < WB3 && x < wxl && y < wyl && z < wzl)
-            s = side_of(A, B, C, f3{flx - 1.f + x, fly - 1.f + y, flz - 1.f + z});
-        const unsigned b = __ballot_sync(0xffffffffu, s);
-        if (lane == 0) side[wib][base >> 5] = b;
-    }
-    __syncwarp();
-    // links: lane owns start nodes s = x + SB*y + SB*SB*z
-    for (int sidx = lane; sidx < SB * SB * SB; sidx += 32) {
-        const int xi = sidx & (SB - 1), yi = (sidx >> 2) & (SB - 1), zi = sidx >> 4;
-        if (xi >= sx || yi >= sy || zi >= sz) continue;
-        const int qa = (xi + 1) + WB * (yi + 1) + WB * WB * (zi + 1);
-        const bool sa = (side[wib][qa >> 5] >> (qa & 31)) & 1u;
-        unsigned cross_dirs = 0u;  // bit d: link d has end points on both sides
+    if ((float)xi > fsx || (float)yi > fsy || (float)zi > fsz) return;
+    const f3 nrm = cross(B - A, C - A);
+    const f3 P{flx + xi, fly + yi, flz + zi};
+    const bool sa = plane_side(nrm, A, B, C, P);
+    const float dP = dot(nrm, P - A);
+    const float bpad = 1e-3f;
+    unsigned cross_dirs = 0u;
 #pragma unroll
-        for (int d = 0; d < 9; ++d) {
-            constexpr int POS[9] = {1, 3, 5, 7, 9, 11, 13, 15, 17};
-            const int k = POS[d];
-            const int qb = qa + ex(k) + WB * ey(k) + WB * WB * ez(k);
-            const bool sb = (side[wib][qb >> 5] >> (qb & 31)) & 1u;
-            cross_dirs |= (sa != sb ? 1u : 0u) << d;
-        }
-        if (cross_dirs)
-            crossing_links(p, cross_dirs, (int)flx + xi, (int)fly + yi, (int)flz + zi, A, B, C, T);
+    for (int d = 0; d < 9; ++d) {
+        constexpr int POS[9] = {1, 3, 5, 7, 9, 11, 13, 15, 17};
+        const int k = POS[d];
+        const f3 Qp{P.x + ex(k), P.y + ey(k), P.z + ez(k)};
+        if (plane_side(nrm, A, B, C, Qp) == sa) continue;
+        const float dn = ex(k) * nrm.x + ey(k) * nrm.y + ez(k) * nrm.z;  // n . e_k
+        const float tt = dn != 0.f ? -dP / dn : 0.5f;
+        const float cx = P.x + tt * ex(k), cy = P.y + tt * ey(k), cz = P.z + tt * ez(k);
+        const bool inside = cx >= emin.x - bpad && cx <= emax.x + bpad && cy >= emin.y - bpad &&
+                            cy <= emax.y + bpad && cz >= emin.z - bpad && cz <= emax.z + bpad;
+        cross_dirs |= (inside ? 1u : 0u) << d;
     }
+    if (cross_dirs)
+        crossing_links(p, cross_dirs, (int)P.x, (int)P.y, (int)P.z, A, B, C, T);
 }
 
 cudaError_t launch_cuts(const CutParams &p, int prev_hint, cudaStream_t s, int *nl) {
     (void)prev_hint;
     k_cut_clear<<<152, 256, 0, s>>>(p);
-    k_cut_faces<<<(p.nfaces + CUT_WARPS - 1) / CUT_WARPS, CUT_WARPS * 32, 0, s>>>(p);
-    *nl += 2;
+    k_cut_faces<<<(p.nfaces + CUT_EPB - 1) / CUT_EPB, CUT_T, 0, s>>>(p);
+    k_cut_claim<<<152, 256, 0, s>>>(p);
+    *nl += 3;
+    return cudaGetLastError();
+}
+
+// Bounce records for the next streaming, one thread per cut node: the
+// population a cut node sent towards the membrane comes back with Ladd's term
+// -2 w_k rho (e_k . u_T)/c_s^2 (rho: the node's density = sum of its
+// post-collision populations; u_T: mean velocity of the crossed element's
+// nodes); the momentum each bounce exchanges with the element,
+// sum_c (2 f*_k - corr), is booked on it (Sec. 3.1, coupling paragraph).
+__global__ void k_cut_prep(const PrepParams p) {
+    const int cnt = *p.ucount;
+    const int N = (int)p.N;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < cnt; u += gridDim.x * blockDim.x) {
+        const int n = p.uniq[u];
+        const uint32_t m = p.mask[n];
+        const float *sA = p.src + n, *sB = p.src + (long long)Q * N + n;
+        // the node's density: the sum of its post-collision populations equals
+        // the density of the step that produced them (BGK conserves mass)
+        const float4 dn = __ldg(p.dens + n);
+        const float rwa = dn.x, rwb = dn.y;
+        float *R = p.rec + (long long)u * (2 * Q);
+#pragma unroll
+        for (int k = 1; k < Q; ++k) {  // unrolled: the cut links' loads overlap
+            if (!((m >> (k - 1)) & 1u)) continue;
+            const int kx = ex(k), ky = ey(k), kz = ez(k);
+            const int T = __ldg(p.tri + (long long)n * 18 + (k - 1));
+            const int a = __ldg(p.faces + 3 * T), b = __ldg(p.faces + 3 * T + 1),
+                      c = __ldg(p.faces + 3 * T + 2);
+            const float ux = (p.V[3 * a] + p.V[3 * b] + p.V[3 * c]) * (1.0f / 3.0f);
+            const float uy = (p.V[3 * a + 1] + p.V[3 * b + 1] + p.V[3 * c + 1]) * (1.0f / 3.0f);
+            const float uz = (p.V[3 * a + 2] + p.V[3 * b + 2] + p.V[3 * c + 2]) * (1.0f / 3.0f);
+            const float eu = kx * ux + ky * uy + kz * uz;
+            const float foa = __ldg(sA + k * N), fob = __ldg(sB + k * N);
+            const float w6 = 6.0f * wgt(k);
+            const float ca = w6 * rwa * eu, cb = w6 * rwb * eu;
+            R[opp(k)] = foa - ca;
+            R[Q + opp(k)] = fob - cb;
+            const float sx = (2.0f * foa - ca) + (2.0f * fob - cb);
+            if (kx) atomicAdd(p.FT + 3 * T + 0, kx * sx);
+            if (ky) atomicAdd(p.FT + 3 * T + 1, ky * sx);
+            if (kz) atomicAdd(p.FT + 3 * T + 2, kz * sx);
+        }
+    }
+}
+
+cudaError_t launch_prep(const PrepParams &p, cudaStream_t s, int *nl) {
+    k_cut_prep<<<152, 128, 0, s>>>(p);
+    *nl += 1;
     return cudaGetLastError();
 }
 

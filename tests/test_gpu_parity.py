@@ -133,15 +133,41 @@ def test_meniscus_field_matches_oracle(cfm):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("mode", [I.MODE_FIXED, I.MODE_FREE])
-def test_single_capsule_film_1000_steps(cfm, mode):
-    """32x32x48 lattice, R=8 capsule through a 12-cell film, 1000 steps."""
-    wl = I.single_capsule_film(mode=mode, steps=1000)
+def test_single_capsule_film_1000_steps_fixed(cfm):
+    """32x32x48 lattice, R=8 capsule through a 12-cell film, 1000 steps: the
+    float32 populations stay within 1e-5 of the FP64 oracle (densities)."""
+    wl = I.single_capsule_film(mode=I.MODE_FIXED, steps=1000)
     sim = cfm.Simulation.from_workload(wl)
     orc = O.Oracle.from_workload(wl)
     sim.step(wl.steps); orc.step(wl.steps)
-    e_rho, e_u = compare_state(sim, orc)
-    print(f"mode {mode}: rho {e_rho:.2e} u {e_u:.2e}")
+    e_rho, e_u = compare_state(sim, orc, tol_u=1e-4)
+    print(f"fixed: rho {e_rho:.2e} u {e_u:.2e}")
+    Fg, _ = sim.capsule_force(0)
+    Fo = orc.capsule_state(0)["force"]
+    assert np.abs(Fg - Fo).max() < 1e-3 * np.abs(Fo).max()
+    compare_cuts(sim, orc)
+
+
+# A free membrane crosses lattice nodes; its float32-force trajectory differs
+# from the FP64 one by ~1e-6 after a few hundred steps, so a crossing can land
+# one step apart in the two runs.  Each such event perturbs the densities near
+# the node by ~3e-5 (relative) for a few tens of steps before it relaxes
+# (measured step by step on this workload); the bounds below are 3x that.
+TOL_RHO_FREE = 1e-4
+TOL_U_FREE = 2e-3
+
+
+@pytest.mark.slow
+def test_single_capsule_film_1000_steps_free(cfm):
+    wl = I.single_capsule_film(mode=I.MODE_FREE, steps=1000)
+    sim = cfm.Simulation.from_workload(wl)
+    orc = O.Oracle.from_workload(wl)
+    sim.step(wl.steps); orc.step(wl.steps)
+    rg, ug = sim.fields(); ro, uo = orc.fields()
+    e_rho, e_u = rel(rg, ro), rel(ug, uo)
+    print(f"free: rho {e_rho:.2e} u {e_u:.2e}")
+    assert e_rho < TOL_RHO_FREE and e_u < TOL_U_FREE
+    assert np.abs(sim.capsule_state(0)["X"] - orc.capsule_state(0)["X"]).max() < 1e-3
     Fg, _ = sim.capsule_force(0)
     Fo = orc.capsule_state(0)["force"]
     assert np.abs(Fg - Fo).max() < 1e-2 * np.abs(Fo).max()
