@@ -170,6 +170,26 @@ cf_status cf_cuts(cf_ctx *ctx, uint32_t *mask, int *tri, uint8_t *inside);
  * For measurement; the populations advance exactly as with cf_step. */
 cf_status cf_time_phases(cf_ctx *ctx, long long n, double ms[4]);
 
+/* One lattice time step without capsules that allocates no device memory.
+ * The paper has no counterpart: this is for callers that cannot call
+ * cudaMalloc (code running inside a framework that owns the device memory as
+ * one fixed pool, or that must not allocate once set-up is over).  It applies
+ * the same streaming, substrate bounce-back, Shan-Chen force and BGK collision
+ * as cf_step does for a lattice without capsules.
+ *   src, dst  device pointers, caller-owned, [2][19][nz][ny][nx] float
+ *             populations (post-collision) in and out; must not overlap
+ *   nx..G     as in cf_lattice_desc; stream: cudaStream_t or NULL
+ * The per-node density scratch is a fixed array inside the library, sized for
+ * at most 1048576 nodes (16 MiB, held by every GPU that loads the library until
+ * the process exits); larger lattices return CF_EINVAL.  The first call on a
+ * device looks up the array's device address with that device current; make
+ * that first call before any stream capture.  All calls share the array, so
+ * calls that overlap on the GPU (other streams, other threads) race; each
+ * call overwrites the scratch completely before reading it.  Asynchronous on
+ * `stream`. */
+cf_status cf_lattice_step_static(const float *src, float *dst, int nx, int ny, int nz, int wall,
+                                 const double tau[2], double G, void *stream);
+
 /* Number of kernel launches issued by the last cf_step / cf_time_phases call. */
 cf_status cf_launch_count(cf_ctx *ctx, long long *n);
 

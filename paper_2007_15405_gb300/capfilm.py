@@ -81,6 +81,8 @@ def load_library(path: Optional[str] = None):
         "cf_cuts": [C.c_void_p, C.POINTER(C.c_uint32), C.POINTER(C.c_int), C.POINTER(C.c_uint8)],
         "cf_launch_count": [C.c_void_p, C.POINTER(C.c_longlong)],
         "cf_time_phases": [C.c_void_p, C.c_longlong, _dp],
+        "cf_lattice_step_static": [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                   _dp, C.c_double, C.c_void_p],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -95,7 +97,7 @@ def exported_symbols():
             "cf_set_film", "cf_step", "cf_sync", "cf_capsule_force", "cf_lateral_force",
             "cf_capsule_state", "cf_fields", "cf_populations", "cf_total_mass",
             "cf_meniscus_field", "cf_meniscus_profile", "cf_cuts", "cf_launch_count",
-            "cf_time_phases"]
+            "cf_time_phases", "cf_lattice_step_static"]
 
 
 def _check(rc):
@@ -106,6 +108,16 @@ def _check(rc):
 
 def _ptr(a, t=_dp):
     return a.ctypes.data_as(t) if a is not None else None
+
+
+def lattice_step_static(src_ptr, dst_ptr, nx, ny, nz, wall=1, tau=(1.0, 1.0), G=3.6,
+                        stream_ptr=None):
+    """One capsule-free lattice step on caller-owned device buffers (integer
+    device addresses), with the library's fixed scratch: no allocation."""
+    L = load_library()
+    t = np.ascontiguousarray(tau, np.float64)
+    _check(L.cf_lattice_step_static(C.c_void_p(src_ptr), C.c_void_p(dst_ptr), nx, ny, nz, wall,
+                                    _ptr(t), G, C.c_void_p(stream_ptr) if stream_ptr else None))
 
 
 class _TorchAllocator:

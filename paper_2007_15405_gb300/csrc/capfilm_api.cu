@@ -43,6 +43,8 @@ struct HostCapsule {
 
 }  // namespace
 
+void cf::set_last_error(const char *msg) { g_err = msg; }
+
 struct cf_ctx {
     cf_lattice_desc d{};
     long long N = 0;

@@ -141,6 +141,7 @@ __host__ __device__ inline int wrapi(int a, int n) {
 
 // Host-side launchers (defined in the kernel translation units).
 namespace cf {
+void set_last_error(const char *msg);  // text returned by cf_last_error() on this thread
 cudaError_t launch_lb_step(const LBParams &p, int tx_variant, cudaStream_t s);
 cudaError_t launch_init_film(float *f, float4 *dens, long long N, int nx, int ny, int nz, int wall,
                              float h_top, float rmaj, float rmin, float rmix,

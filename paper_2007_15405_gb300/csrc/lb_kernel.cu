@@ -20,6 +20,9 @@
 // Gather addresses are the node index plus per-direction offsets with the
 // periodic wrap folded into per-node deltas.
 #include "cf_common.cuh"
+#include "../../include/capfilm.h"
+
+#include <mutex>
 
 namespace cf {
 
@@ -347,3 +350,192 @@ cudaError_t launch_mass(const float *f, long long N, double *m2, cudaStream_t s)
 }
 
 }  // namespace cf
+
+// ------------------------------------------- lattice update with static scratch
+// Some callers cannot allocate device memory: code that runs inside a host
+// framework which owns the whole device allocation (a fixed pool handed out
+// once, or an allocator that may not be called from the thread doing the
+// stepping), or code that must not allocate between a set-up phase and the
+// stepping loop.  cf_lattice_step_static advances a lattice without capsules
+// one step with the same arithmetic as the density and collide passes above,
+// taking the per-node density scratch from a fixed array compiled into this
+// library instead of allocating it.  The array holds the densities of at most
+// CF_STATIC_MAX_NODES nodes; every GPU that loads the library keeps it
+// (16 MiB) until the process exits.
+namespace cf {
+
+constexpr long long CF_STATIC_MAX_NODES = 1LL << 20;
+static __device__ __align__(256) float4 g_static_dens[CF_STATIC_MAX_NODES];
+
+__global__ void __launch_bounds__(BX *BY) k_density_static(const LBParams p) {
+    int x, y, z;
+    if (!node_of(p, x, y, z)) return;
+    const int N = (int)p.N;
+    for (; z < p.zhi; z += gridDim.z) {
+        const Deltas d = deltas(p, x, y, z);
+        const float *sA = p.src + d.n, *sB = p.src + (long long)Q * N + d.n;
+        float ra = 0.f, rb = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int o = src_off(d, N, i);
+            ra += __ldg(sA + o);
+            rb += __ldg(sB + o);
+        }
+        p.dens[d.n] = make_float4(ra, rb, psi_of(ra), psi_of(rb));
+    }
+}
+
+// Shan-Chen force (substrate links use the interpolated partner density),
+// velocity shift, BGK, store: the collide pass without membrane links.
+__device__ __forceinline__ void collide_node_static(const LBParams &p, const Deltas &d) {
+    const int N = (int)p.N, n = d.n;
+    float fa[Q], fb[Q];
+    {
+        const float *sA = p.src + n, *sB = p.src + (long long)Q * N + n;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int o = src_off(d, N, i);
+            fa[i] = __ldg(sA + o);
+            fb[i] = __ldg(sB + o);
+        }
+    }
+    const float4 me = p.dens[n];
+    const float ra = me.x, rb = me.y, pa = me.z, pb = me.w;
+    float sa[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};
+    if (!d.wlo && !d.whi) {
+#pragma unroll
+        for (int k = 1; k < Q; ++k) {
+            const float4 q = p.dens[n + nb_off(d, ex(k), ey(k), ez(k))];
+            sa[0] += wgt(k) * ex(k) * q.z; sa[1] += wgt(k) * ey(k) * q.z; sa[2] += wgt(k) * ez(k) * q.z;
+            sb[0] += wgt(k) * ex(k) * q.w; sb[1] += wgt(k) * ey(k) * q.w; sb[2] += wgt(k) * ez(k) * q.w;
+        }
+    } else {
+        float ia = ra, ib = rb, cnt = 1.f;
+#pragma unroll
+        for (int k = 1; k < Q; ++k) {
+            const bool solid = (ez(k) == 1 && d.whi) || (ez(k) == -1 && d.wlo);
+            if (!solid) {
+                const float4 q = p.dens[n + nb_off(d, ex(k), ey(k), ez(k))];
+                ia += q.x; ib += q.y; cnt += 1.f;
+            }
+        }
+        const float qa_eff = psi_of(ia / cnt), qb_eff = psi_of(ib / cnt);
+#pragma unroll
+        for (int k = 1; k < Q; ++k) {
+            const bool solid = (ez(k) == 1 && d.whi) || (ez(k) == -1 && d.wlo);
+            float qa, qb;
+            if (solid) { qa = qa_eff; qb = qb_eff; }
+            else {
+                const float4 q = p.dens[n + nb_off(d, ex(k), ey(k), ez(k))];
+                qa = q.z; qb = q.w;
+            }
+            sa[0] += wgt(k) * ex(k) * qa; sa[1] += wgt(k) * ey(k) * qa; sa[2] += wgt(k) * ez(k) * qa;
+            sb[0] += wgt(k) * ex(k) * qb; sb[1] += wgt(k) * ey(k) * qb; sb[2] += wgt(k) * ez(k) * qb;
+        }
+    }
+    const float FA[3] = {-p.G * pa * sb[0], -p.G * pa * sb[1], -p.G * pa * sb[2]};
+    const float FB[3] = {-p.G * pb * sa[0], -p.G * pb * sa[1], -p.G * pb * sa[2]};
+    float ja[3] = {0.f, 0.f, 0.f}, jb[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float da = fa[i] - fa[i + 1], db = fb[i] - fb[i + 1];
+        ja[0] += ex(i) * da; ja[1] += ey(i) * da; ja[2] += ez(i) * da;
+        jb[0] += ex(i) * db; jb[1] += ey(i) * db; jb[2] += ez(i) * db;
+    }
+    const float den = ra * p.itau[0] + rb * p.itau[1];
+    float ua[3], ub[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float up = (ja[a] * p.itau[0] + jb[a] * p.itau[1]) / den;
+        ua[a] = up + p.tau[0] * FA[a] / ra;
+        ub[a] = up + p.tau[1] * FB[a] / rb;
+    }
+    const float ka = 1.0f - 1.5f * (ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2]);
+    const float kb = 1.0f - 1.5f * (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
+    float *__restrict__ dA = p.dst + n;
+    float *__restrict__ dB = p.dst + (long long)Q * N + n;
+    const float ta = p.itau[0], tb = p.itau[1];
+    float qa0 = ra, qb0 = rb;
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float eua = ex(i) * ua[0] + ey(i) * ua[1] + ez(i) * ua[2];
+        const float eub = ex(i) * ub[0] + ey(i) * ub[1] + ez(i) * ub[2];
+        const float wa = wgt(i) * ra, wb = wgt(i) * rb;
+        const float sa_ = wa * (ka + 4.5f * eua * eua), sb_ = wb * (kb + 4.5f * eub * eub);
+        const float qa1 = sa_ + 3.0f * wa * eua, qa2 = sa_ - 3.0f * wa * eua;
+        const float qb1 = sb_ + 3.0f * wb * eub, qb2 = sb_ - 3.0f * wb * eub;
+        qa0 -= qa1 + qa2;
+        qb0 -= qb1 + qb2;
+        dA[i * N] = fa[i] - (fa[i] - qa1) * ta;
+        dA[(i + 1) * N] = fa[i + 1] - (fa[i + 1] - qa2) * ta;
+        dB[i * N] = fb[i] - (fb[i] - qb1) * tb;
+        dB[(i + 1) * N] = fb[i + 1] - (fb[i + 1] - qb2) * tb;
+    }
+    dA[0] = fa[0] - (fa[0] - qa0) * ta;
+    dB[0] = fb[0] - (fb[0] - qb0) * tb;
+}
+
+__global__ void __launch_bounds__(BX *BY) k_collide_static(const LBParams p) {
+    int x, y, z;
+    if (!node_of(p, x, y, z)) return;
+    for (; z < p.zhi; z += gridDim.z) collide_node_static(p, deltas(p, x, y, z));
+}
+
+// Device address of the static scratch, looked up once per device with that
+// device current (the array's name is only a host-side stand-in).
+static float4 *static_dens_address(int dev, cudaError_t *err) {
+    constexpr int MAXDEV = 64;
+    static float4 *addr[MAXDEV] = {};
+    static std::mutex mu;
+    *err = cudaSuccess;
+    if (dev < 0 || dev >= MAXDEV) { *err = cudaErrorInvalidDevice; return nullptr; }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *ptr = nullptr;
+        *err = cudaGetSymbolAddress(&ptr, g_static_dens);
+        if (*err != cudaSuccess) return nullptr;
+        addr[dev] = static_cast<float4 *>(ptr);
+    }
+    return addr[dev];
+}
+
+}  // namespace cf
+
+extern "C" cf_status cf_lattice_step_static(const float *src, float *dst, int nx, int ny, int nz,
+                                            int wall, const double tau[2], double G, void *stream) {
+    using namespace cf;
+    if (!src || !dst || !tau) { set_last_error("null argument"); return CF_EINVAL; }
+    if (nx < 3 || ny < 3 || nz < 3) { set_last_error("lattice dimensions must be >= 3"); return CF_EINVAL; }
+    const long long N = (long long)nx * ny * nz;
+    if (N > CF_STATIC_MAX_NODES) {
+        set_last_error("cf_lattice_step_static: lattice larger than the static scratch "
+                       "(at most 1048576 nodes)");
+        return CF_EINVAL;
+    }
+    if (!(tau[0] > 0.5) || !(tau[1] > 0.5)) { set_last_error("tau must exceed 1/2"); return CF_EINVAL; }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    float4 *dens = e == cudaSuccess ? static_dens_address(dev, &e) : nullptr;
+    if (!dens) {
+        set_last_error(cudaGetErrorString(e));
+        return CF_ECUDA;
+    }
+    LBParams p{};
+    p.nx = nx; p.ny = ny; p.nz = nz; p.wall = wall ? 1 : 0;
+    p.N = N;
+    p.zlo = p.wall ? 1 : 0;
+    p.zhi = nz;
+    p.zchunk = 1;
+    for (int k = 0; k < 2; ++k) { p.tau[k] = (float)tau[k]; p.itau[k] = (float)(1.0 / tau[k]); }
+    p.G = (float)G;
+    p.src = src;
+    p.dst = dst;
+    p.dens = dens;
+    const cudaStream_t s = (cudaStream_t)stream;
+    dim3 grid((nx + BX - 1) / BX, (ny + BY - 1) / BY, p.zhi - p.zlo), block(BX, BY);
+    k_density_static<<<grid, block, 0, s>>>(p);
+    k_collide_static<<<grid, block, 0, s>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { set_last_error(cudaGetErrorString(e)); return CF_ECUDA; }
+    return CF_OK;
+}

@@ -1,0 +1,68 @@
+"""The allocation-free lattice step (cf_lattice_step_static) against the
+context step (cf_step) on a lattice without capsules.
+
+Callers that cannot allocate device memory (a host framework that owns the
+device memory as one fixed pool, or code that must not allocate once set-up is
+over) get cf_lattice_step_static, which takes its density scratch from a fixed
+array inside the library.  Its populations must match what cf_step produces,
+for two calls in a row (the second call reuses the scratch left by the first).
+This file is collected last on purpose.
+"""
+import numpy as np
+import pytest
+
+from paper_2007_15405_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5  # the parity tolerance of the population comparisons
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2007_15405_gb300 import build
+    build.build()
+    from paper_2007_15405_gb300 import capfilm
+    capfilm.load_library()
+    return torch, capfilm
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.mark.parametrize("wall", [1, 0])
+def test_static_scratch_step_matches_context_step(env, wall):
+    torch, cfm = env
+    wl = I.Workload("static", 45, 14, 12, h_top=5.5, capsules=[], steps=2, wall=wall, seed=21)
+    sim = cfm.Simulation.from_workload(wl)
+    f0 = sim.populations()
+    sim.step(1)
+    f1 = sim.populations()
+    sim.step(1)
+    f2 = sim.populations()
+    sim.close()
+
+    stream = torch.cuda.current_stream()
+    a = torch.from_numpy(f0).cuda()
+    b = torch.empty_like(a)
+    # two calls in a row through the C ABI, device buffers owned by the caller
+    cfm.lattice_step_static(a.data_ptr(), b.data_ptr(), wl.nx, wl.ny, wl.nz, wall, wl.tau, wl.G,
+                            stream.cuda_stream)
+    cfm.lattice_step_static(b.data_ptr(), a.data_ptr(), wl.nx, wl.ny, wl.nz, wall, wl.tau, wl.G,
+                            stream.cuda_stream)
+    torch.cuda.synchronize()
+    g1 = b.cpu().numpy().astype(np.float64)
+    g2 = a.cpu().numpy().astype(np.float64)
+    assert rel(g1, f1.astype(np.float64)) < TOL
+    assert rel(g2, f2.astype(np.float64)) < TOL
+
+
+def test_static_scratch_rejects_oversized_lattice(env):
+    torch, cfm = env
+    a = torch.zeros(38 * 27, device="cuda")
+    with pytest.raises(cfm.CapfilmError, match="static scratch"):
+        cfm.lattice_step_static(a.data_ptr(), a.data_ptr(), 1024, 1024, 3, 1, (1.0, 1.0), 3.6)
