@@ -111,7 +111,7 @@ def profiled_traffic():
         if line.startswith("traffic_bytes_per_step:"):
             t = int(line.split(":")[1])
         if line.startswith("lb_kernel.cu sha256[:16]:"):
-            h = line.split(":")[1].strip()
+            h = line.rsplit(":", 1)[1].strip()
     return t if (t is not None and h == sha) else None
 
 
