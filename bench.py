@@ -25,6 +25,9 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 ALG_BYTES_PER_LU = 2 * 19 * 2 * 4  # two components x 19 populations x (read + write) x float32
+# 16-bit storage: 18 moving populations x 2 B + the float rest population, per component
+ALG_BYTES_PER_LU_16 = 2 * (18 * 2 + 4) * 2
+PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2}
 METRIC = "coupled LB+IBM MLUPS (% HBM roofline)"
 
 
@@ -36,6 +39,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS),
+                    help="population storage (arithmetic is float32 in every mode)")
     return ap.parse_args()
 
 
@@ -201,7 +206,9 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     wl = workload()
-    sim = cfm.Simulation.from_workload(wl)
+    prec = PRECISIONS[args.precision]
+    alg_bytes = ALG_BYTES_PER_LU if prec == 0 else ALG_BYTES_PER_LU_16
+    sim = cfm.Simulation.from_workload(wl, precision=prec)
     stream = torch.cuda.current_stream()
     # warm-up
     sim.step(args.warmup)
@@ -232,7 +239,7 @@ def run_ours(args):
     ph = sim.time_phases(nprof)
     lb_ms = ph[0]
     peak, peak_kind = measured_peak()
-    achieved = ALG_BYTES_PER_LU * wl.nodes / (lb_ms / 1e3) / 1e9
+    achieved = alg_bytes * wl.nodes / (lb_ms / 1e3) / 1e9
     # ---- end to end through the public API with host buffers
     from paper_2007_15405_gb300.inputs import RHO_MAJ, RHO_MIN, RHO_MIX
     jit = wl.jitter()
@@ -269,8 +276,9 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": "lattice update: k_density + k_collide",
                      "achieved": achieved, "peak": peak,
                      "peak_kind": f"{peak_kind} copy bandwidth (burst)", "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(),
-                     "algorithmic_bytes_per_launch": ALG_BYTES_PER_LU * wl.nodes,
+                     "frac": achieved / peak,
+                     "traffic": profiled_traffic() if prec == 0 else None,
+                     "algorithmic_bytes_per_launch": alg_bytes * wl.nodes,
                      "kernel_ms": lb_ms},
         "phases_ms": {"lattice": ph[0], "membrane": ph[1], "cut_links": ph[2], "bounce_prep": ph[3]},
         "clocks": clk,
@@ -281,6 +289,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "cpu_baseline": cpu,
     }
+    line["config"]["population_storage"] = args.precision
     print(json.dumps(line), flush=True)
 
 

@@ -48,7 +48,19 @@ typedef enum {
     CF_ETIMEOUT = 8    /* a bounded device-side wait gave up (kernel returned early) */
 } cf_status;
 
-typedef enum { CF_FP32 = 0 } cf_precision;
+/* Storage of the populations (arithmetic is float32 in every case):
+ * CF_FP32       float32 populations;
+ * CF_FP16_SHIFT the 18 moving populations as IEEE half offsets
+ *               g_i = f_i - w_i rho from the rest equilibrium of the node that
+ *               wrote them (rho kept in float32), stored times 2^15 so that
+ *               small offsets stay out of half's subnormal range;
+ * CF_BF16_SHIFT the same offsets in bfloat16 (unscaled).
+ * In both 16-bit modes the offsets are rounded stochastically (a hash of node,
+ * step and direction; deterministic from run to run) and the rest population
+ * is kept in float32 and takes each node's mass balance, so the stored mass is
+ * the collided mass up to float32 rounding.  Population bytes per node drop
+ * from 152 to 80. */
+typedef enum { CF_FP32 = 0, CF_FP16_SHIFT = 1, CF_BF16_SHIFT = 2 } cf_precision;
 
 /* Capsule modes: FREE moves and deforms (Eq. 9); FROZEN keeps its shape and
  * translates rigidly with the summed force (the frozen-shape protocol of
@@ -138,7 +150,7 @@ cf_status cf_capsule_state(cf_ctx *ctx, int id, double *nodes, double *area, dou
  * of the last step (N = nx*ny*nz; solid nodes read 0).  Either may be NULL. */
 cf_status cf_fields(cf_ctx *ctx, double *rho, double *u);
 
-/* Post-collision populations [2][19][N] as stored (float). */
+/* Post-collision populations [2][19][N] as float (16-bit storage decoded). */
 cf_status cf_populations(cf_ctx *ctx, float *f);
 
 /* Total mass of each component (FP64 sum over the lattice). */

@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "CF_OK", 1: "CF_EINVAL", 2: "CF_ENOMEM", 3: "CF_ECUDA", 4: "C
                 5: "CF_ENOTFOUND", 6: "CF_EDIVERGED", 7: "CF_EOVERFLOW", 8: "CF_ETIMEOUT"}
 
 FREE, FROZEN, FIXED = 0, 1, 2
+FP32, FP16_SHIFT, BF16_SHIFT = 0, 1, 2
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
@@ -149,7 +150,7 @@ class Simulation:
     """One lattice with its capsules, stepped on the GPU by the CUDA library."""
 
     def __init__(self, nx, ny, nz, wall=1, tau=(1.0, 1.0), G=3.6, rep_dz=10.0, xi=1.5,
-                 delta0=1.5, stream=None, use_torch_allocator=True):
+                 delta0=1.5, stream=None, use_torch_allocator=True, precision=FP32):
         L = load_library()
         self.nx, self.ny, self.nz = nx, ny, nz
         self.N = nx * ny * nz
@@ -167,8 +168,8 @@ class Simulation:
         elif stream is not None:
             stream_handle = stream.cuda_stream
             self._stream = stream
-        desc = LatticeDesc(nx, ny, nz, wall, (C.c_double * 2)(*tau), G, rep_dz, xi, delta0, 0,
-                           alloc_ptr, stream_handle)
+        desc = LatticeDesc(nx, ny, nz, wall, (C.c_double * 2)(*tau), G, rep_dz, xi, delta0,
+                           precision, alloc_ptr, stream_handle)
         self._desc = desc
         h = C.c_void_p()
         _check(L.cf_create(C.byref(desc), C.byref(h)))

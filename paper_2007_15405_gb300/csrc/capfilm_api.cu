@@ -45,6 +45,26 @@ struct HostCapsule {
 
 void cf::set_last_error(const char *msg) { g_err = msg; }
 
+namespace {
+// IEEE binary16 -> float (host side, for population readouts)
+float half_to_float(uint16_t h) {
+    const uint32_t sign = (uint32_t)(h >> 15) << 31;
+    uint32_t exp = (h >> 10) & 0x1f, man = h & 0x3ff, u;
+    if (exp == 0) {
+        if (man == 0) u = sign;
+        else {  // subnormal
+            int e = -1;
+            do { ++e; man <<= 1; } while (!(man & 0x400));
+            u = sign | ((uint32_t)(127 - 15 - e) << 23) | ((man & 0x3ff) << 13);
+        }
+    } else if (exp == 31) u = sign | 0x7f800000u | (man << 13);
+    else u = sign | ((exp + 127 - 15) << 23) | (man << 13);
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+}  // namespace
+
 struct cf_ctx {
     cf_lattice_desc d{};
     long long N = 0;
@@ -54,10 +74,12 @@ struct cf_ctx {
     bool has_alloc = false;
     std::vector<void *> allocations;
 
-    float *f[2] = {nullptr, nullptr};
+    void *f[2] = {nullptr, nullptr};     // populations (float, or 16-bit offsets)
+    float *f0[2] = {nullptr, nullptr};   // 16-bit storage: float rest populations [2][N]
+    unsigned *step_ctr = nullptr;
     int fpar = 0;
     float *out = nullptr;
-    float4 *dens = nullptr;
+    float4 *dens[2] = {nullptr, nullptr};  // densities paired with each population buffer
     uint32_t *mask = nullptr;
     int *tri = nullptr;
     uint32_t *owner = nullptr;    // claim flags of cut nodes
@@ -147,13 +169,17 @@ LBParams lb_params(cf_ctx *c, bool with_out) {
     p.G = (float)c->d.G;
     p.src = c->f[c->fpar];
     p.dst = c->f[1 - c->fpar];
+    p.dens_src = c->dens[c->fpar];
+    p.src0 = c->f0[c->fpar];
+    p.dst0 = c->f0[1 - c->fpar];
+    p.step_ctr = c->step_ctr;
     p.mask = c->mask;
     p.tri = c->tri;
     p.faces = c->faces;
     p.V = c->V;
     p.FT = c->FT;
     p.out = with_out ? c->out : nullptr;
-    p.dens = c->dens;
+    p.dens = c->dens[1 - c->fpar];
     p.cutrec = c->cutrec;
     p.rec = c->rec;
     p.status = c->status;
@@ -229,8 +255,9 @@ cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev = null
     if (c->nnodes) {  // bounce records of the cut nodes for this step's streaming
         PrepParams q{};
         q.N = c->N;
+        q.prec = c->d.precision;
         q.src = c->f[c->fpar];
-        q.dens = c->dens;
+        q.dens = c->dens[c->fpar];
         q.mask = c->mask;
         q.tri = c->tri;
         q.faces = c->faces;
@@ -243,7 +270,7 @@ cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev = null
         CF_CUDA(launch_prep(q, c->stream, nl));
     }
     if (ev) CF_CUDA(cudaEventRecord(ev[0], c->stream));
-    CF_CUDA(launch_lb_step(lb_params(c, with_out), c->lb_variant, c->stream));
+    CF_CUDA(launch_lb_step(lb_params(c, with_out), c->d.precision, c->stream));
     *nl += 2;
     c->fpar = 1 - c->fpar;
     if (ev) CF_CUDA(cudaEventRecord(ev[1], c->stream));
@@ -456,7 +483,9 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     // population offsets are 32-bit: 38 * N must stay below 2^31
     if (38LL * desc->nx * desc->ny * desc->nz >= (1LL << 31)) return fail(CF_EINVAL, "lattice too large (38*N >= 2^31)");
     if (!(desc->tau[0] > 0.5) || !(desc->tau[1] > 0.5)) return fail(CF_EINVAL, "tau must exceed 1/2");
-    if (desc->precision != CF_FP32) return fail(CF_EINVAL, "unsupported precision");
+    if (desc->precision != CF_FP32 && desc->precision != CF_FP16_SHIFT &&
+        desc->precision != CF_BF16_SHIFT)
+        return fail(CF_EINVAL, "unsupported precision");
     cf_ctx *c = new cf_ctx();
     c->d = *desc;
     c->N = (long long)desc->nx * desc->ny * desc->nz;
@@ -473,10 +502,15 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
         c->own_stream = true;
     }
     const long long N = c->N;
-    c->f[0] = (float *)dalloc(c, sizeof(float) * 38 * N);
-    c->f[1] = (float *)dalloc(c, sizeof(float) * 38 * N);
+    const size_t pb = pop_bytes(desc->precision);
+    c->f[0] = dalloc(c, pb * 38 * N);
+    c->f[1] = dalloc(c, pb * 38 * N);
     c->out = (float *)dalloc(c, sizeof(float) * 5 * N);
-    c->dens = (float4 *)dalloc(c, sizeof(float4) * N);
+    c->f0[0] = (float *)dalloc(c, sizeof(float) * 2 * N);
+    c->f0[1] = (float *)dalloc(c, sizeof(float) * 2 * N);
+    c->step_ctr = (unsigned *)dalloc(c, sizeof(unsigned));
+    c->dens[0] = (float4 *)dalloc(c, sizeof(float4) * N);
+    c->dens[1] = (float4 *)dalloc(c, sizeof(float4) * N);
     c->mask = (uint32_t *)dalloc(c, sizeof(uint32_t) * N);
     c->tri = (int *)dalloc(c, sizeof(int) * 18 * N);
     c->owner = (uint32_t *)dalloc(c, sizeof(uint32_t) * N);
@@ -487,13 +521,18 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     c->bar = (unsigned *)dalloc(c, sizeof(unsigned) * 2);
     c->dscratch = (double *)dalloc(c, sizeof(double) * 8);
     c->hscratch = (float *)dalloc(c, sizeof(float) * desc->nx * desc->ny);
-    if (!c->f[0] || !c->f[1] || !c->out || !c->dens || !c->mask || !c->tri || !c->owner || !c->cutrec || !c->inside ||
+    if (!c->f[0] || !c->f[1] || !c->f0[0] || !c->f0[1] || !c->step_ctr || !c->out || !c->dens[0] || !c->dens[1] || !c->mask || !c->tri || !c->owner || !c->cutrec || !c->inside ||
         !c->counts || !c->status || !c->bar || !c->dscratch || !c->hscratch) {
         cf_destroy(c);
         return fail(CF_ENOMEM, "device allocation failed");
     }
-    cudaMemsetAsync(c->f[0], 0, sizeof(float) * 38 * N, c->stream);
-    cudaMemsetAsync(c->f[1], 0, sizeof(float) * 38 * N, c->stream);
+    cudaMemsetAsync(c->f[0], 0, pb * 38 * N, c->stream);
+    cudaMemsetAsync(c->f[1], 0, pb * 38 * N, c->stream);
+    cudaMemsetAsync(c->f0[0], 0, sizeof(float) * 2 * N, c->stream);
+    cudaMemsetAsync(c->f0[1], 0, sizeof(float) * 2 * N, c->stream);
+    cudaMemsetAsync(c->step_ctr, 0, sizeof(unsigned), c->stream);
+    cudaMemsetAsync(c->dens[0], 0, sizeof(float4) * N, c->stream);
+    cudaMemsetAsync(c->dens[1], 0, sizeof(float4) * N, c->stream);
     cudaMemsetAsync(c->out, 0, sizeof(float) * 5 * N, c->stream);
     cudaMemsetAsync(c->mask, 0, sizeof(uint32_t) * N, c->stream);
     cudaMemsetAsync(c->tri, 0x7f, sizeof(int) * 18 * N, c->stream);
@@ -581,7 +620,7 @@ cf_status cf_set_film(cf_ctx *c, double h_top, double rmaj, double rmin, double 
         djit = c->jit;
     }
     if (c->nfaces) CF_CUDA(launch_inside(c->mask, c->inside, c->d.nx, c->d.ny, c->d.nz, c->stream));
-    CF_CUDA(launch_init_film(c->f[c->fpar], c->dens, N, c->d.nx, c->d.ny, c->d.nz, c->d.wall, (float)h_top,
+    CF_CUDA(launch_init_film(c->f[c->fpar], c->f0[c->fpar], c->d.precision, c->dens[c->fpar], N, c->d.nx, c->d.ny, c->d.nz, c->d.wall, (float)h_top,
                              (float)rmaj, (float)rmin, (float)rmix, djit, c->inside, c->stream));
     c->film_set = true;
     return sync_ok(c);
@@ -752,14 +791,44 @@ cf_status cf_fields(cf_ctx *c, double *rho, double *u) {
 
 cf_status cf_populations(cf_ctx *c, float *f) {
     if (!c || !f) return fail(CF_EINVAL, "null argument");
-    CF_CUDA(cudaMemcpyAsync(f, c->f[c->fpar], sizeof(float) * 38 * c->N, cudaMemcpyDeviceToHost, c->stream));
-    return sync_ok(c);
+    const long long N = c->N;
+    if (c->d.precision == CF_FP32) {
+        CF_CUDA(cudaMemcpyAsync(f, c->f[c->fpar], sizeof(float) * 38 * N, cudaMemcpyDeviceToHost, c->stream));
+        return sync_ok(c);
+    }
+    // 16-bit offsets: f_i = g_i + w_i rho (rho of the node that wrote them)
+    std::vector<uint16_t> g(38 * (size_t)N);
+    std::vector<float4> d((size_t)N);
+    std::vector<float> r0(2 * (size_t)N);
+    CF_CUDA(cudaMemcpyAsync(g.data(), c->f[c->fpar], 2 * g.size(), cudaMemcpyDeviceToHost, c->stream));
+    CF_CUDA(cudaMemcpyAsync(r0.data(), c->f0[c->fpar], sizeof(float) * r0.size(), cudaMemcpyDeviceToHost, c->stream));
+    CF_CUDA(cudaMemcpyAsync(d.data(), c->dens[c->fpar], sizeof(float4) * d.size(), cudaMemcpyDeviceToHost, c->stream));
+    cf_status s = sync_ok(c);
+    if (s != CF_OK) return s;
+    const bool bf = c->d.precision == CF_BF16_SHIFT;
+    for (int comp = 0; comp < 2; ++comp)
+        for (int i = 0; i < Q; ++i) {
+            const float w = i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+            for (long long n = 0; n < N; ++n) {
+                if (i == 0) {  // rest populations are kept in float
+                    f[((size_t)comp * Q) * N + n] = r0[(size_t)comp * N + n];
+                    continue;
+                }
+                const uint16_t h = g[((size_t)comp * Q + i) * N + n];
+                float v;
+                if (bf) { uint32_t u = (uint32_t)h << 16; std::memcpy(&v, &u, 4); }
+                else v = half_to_float(h) * F16_INV_SCALE;
+                f[((size_t)comp * Q + i) * N + n] = v + w * (comp ? d[n].y : d[n].x);
+            }
+        }
+    return CF_OK;
 }
 
 cf_status cf_total_mass(cf_ctx *c, double m[2]) {
     if (!c || !m) return fail(CF_EINVAL, "null argument");
     CF_CUDA(cudaMemsetAsync(c->dscratch, 0, sizeof(double) * 2, c->stream));
-    CF_CUDA(launch_mass(c->f[c->fpar], c->N, c->dscratch, c->stream));
+    CF_CUDA(launch_mass(c->f[c->fpar], c->f0[c->fpar], c->d.precision, c->dens[c->fpar], c->N, c->dscratch,
+                        c->stream));
     CF_CUDA(cudaMemcpyAsync(m, c->dscratch, sizeof(double) * 2, cudaMemcpyDeviceToHost, c->stream));
     return sync_ok(c);
 }

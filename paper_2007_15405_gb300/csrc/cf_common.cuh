@@ -25,7 +25,16 @@ __host__ __device__ constexpr float wgt(int i) {
 }
 constexpr int Q = 19;
 
-// Parameters of the fused lattice kernel.
+// Storage of the populations: float, or half / bfloat16 offsets from the
+// rest equilibrium w_i rho of the node (rho kept in float in the density array).
+enum Prec { P_F32 = 0, P_F16 = 1, P_BF16 = 2 };
+// Half offsets are stored times 2^15: quiescent offsets (~1e-7) then sit in
+// half's normal range (above 2^-14) instead of its subnormals, and the largest
+// representable offset is still 2 (populations never exceed the density).
+constexpr float F16_SCALE = 32768.0f, F16_INV_SCALE = 1.0f / 32768.0f;
+inline size_t pop_bytes(int prec) { return prec == P_F32 ? 4 : 2; }
+
+// Parameters of the lattice passes.
 struct LBParams {
     int nx, ny, nz, wall;
     long long N;            // nodes
@@ -33,8 +42,12 @@ struct LBParams {
     int zchunk;             // planes walked per thread (grid.z = fluid planes / zchunk)
     float itau[2], tau[2];  // 1/tau and tau per component
     float G;
-    const float *__restrict__ src;   // post-collision populations of the last step
-    float *__restrict__ dst;         // post-collision populations of this step
+    const void *__restrict__ src;    // post-collision populations of the last step
+    void *__restrict__ dst;          // post-collision populations of this step
+    const float4 *__restrict__ dens_src;  // densities the src populations were encoded with
+    const float *__restrict__ src0;  // 16-bit storage: rest populations in float [2][N]
+    float *__restrict__ dst0;
+    unsigned *__restrict__ step_ctr; // step counter (stochastic-rounding stream)
     const uint32_t *__restrict__ mask;  // cut bits per node
     const int *__restrict__ tri;        // crossed element per node and link [N*18]
     const int *__restrict__ faces;      // element nodes [3*nfaces]
@@ -43,7 +56,7 @@ struct LBParams {
     const int *__restrict__ cutrec;     // [N] bounce record of a cut node
     const float *__restrict__ rec;      // [capacity][2*Q] bounced populations
     float *__restrict__ out;            // optional [5][N]: rhoA, rhoB, ux, uy, uz
-    float4 *__restrict__ dens;          // [N] (rhoA, rhoB, psiA, psiB) of this step
+    float4 *__restrict__ dens;          // [N] (rhoA, rhoB, psiA, psiB) of this step (written)
     unsigned *__restrict__ status;      // device error flags
 };
 
@@ -119,7 +132,8 @@ struct CutParams {
 // Bounce records of the cut nodes for the next streaming (built once per step).
 struct PrepParams {
     long long N;
-    const float *src;        // post-collision populations about to be streamed
+    int prec;                // storage of the populations (cf_precision)
+    const void *src;         // post-collision populations about to be streamed
     const float4 *dens;      // (rhoA, rhoB, ...) of the step that produced them
     const uint32_t *mask;
     const int *tri;
@@ -142,15 +156,16 @@ __host__ __device__ inline int wrapi(int a, int n) {
 // Host-side launchers (defined in the kernel translation units).
 namespace cf {
 void set_last_error(const char *msg);  // text returned by cf_last_error() on this thread
-cudaError_t launch_lb_step(const LBParams &p, int tx_variant, cudaStream_t s);
-cudaError_t launch_init_film(float *f, float4 *dens, long long N, int nx, int ny, int nz, int wall,
-                             float h_top, float rmaj, float rmin, float rmix,
+cudaError_t launch_lb_step(const LBParams &p, int prec, cudaStream_t s);
+cudaError_t launch_init_film(void *f, float *f0, int prec, float4 *dens, long long N, int nx, int ny,
+                             int nz, int wall, float h_top, float rmaj, float rmin, float rmix,
                              const double *jit, const uint8_t *inside, cudaStream_t s);
 cudaError_t launch_inside(const uint32_t *mask, uint8_t *inside, int nx, int ny, int nz,
                           cudaStream_t s);
 cudaError_t launch_meniscus(const float *out, const uint8_t *inside, float *h, int nx, int ny,
                             int nz, int wall, cudaStream_t s);
-cudaError_t launch_mass(const float *f, long long N, double *m2, cudaStream_t s);
+cudaError_t launch_mass(const void *f, const float *f0, int prec, const float4 *dens, long long N,
+                        double *m2, cudaStream_t s);
 cudaError_t launch_membrane(const MemParams &p, bool any_frozen, cudaStream_t s, int *nlaunch);
 cudaError_t launch_cuts(const CutParams &p, int prev_count_hint, cudaStream_t s, int *nlaunch);
 cudaError_t launch_prep(const PrepParams &p, cudaStream_t s, int *nlaunch);

@@ -22,6 +22,8 @@
 #include "cf_common.cuh"
 #include "../../include/capfilm.h"
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <mutex>
 
 namespace cf {
@@ -29,6 +31,60 @@ namespace cf {
 constexpr int BX = 32, BY = 4;  // thread block: one row segment of 32 x 4 rows
 
 __device__ __forceinline__ float psi_of(float r) { return -expm1f(-r); }
+
+// Population storage.  Float stores f_i itself.  Half and bfloat16 store,
+// for the 18 moving directions, the offset g_i = f_i - w_i rho from the rest
+// equilibrium of the node that wrote it (rho from that step's density array):
+// the offsets are O(w rho |u|), so 16 bits resolve f_i far better than
+// storing f_i directly, and the population traffic is halved.  The offsets
+// are rounded stochastically (a counter-based hash of node, step and
+// direction picks the rounding): at a stationary interface the offsets repeat
+// from step to step, and round-to-nearest errors would add up linearly.  The
+// rest population stays in float and takes the node's mass balance after the
+// moving offsets are rounded, so every node stores exactly its mass.
+template <typename T> struct Pop;
+template <> struct Pop<float> {
+    static constexpr bool shifted = false;
+    __device__ static float ld(const float *p) { return __ldg(p); }
+    // store v, return the value stored
+    __device__ static float st(float *p, float v, uint32_t) { *p = v; return v; }
+};
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16; x *= 0x7feb352du; x ^= x >> 15; x *= 0x846ca68bu; x ^= x >> 16;
+    return x;
+}
+// stochastic rounding of v to bfloat16: random bits below its 8-bit mantissa,
+// then truncation of the magnitude
+__device__ __forceinline__ __nv_bfloat16 sr_bf16(float v, uint32_t r) {
+    uint32_t b = __float_as_uint(v);
+    if ((b & 0x7f800000u) != 0x7f800000u) b += r & 0xffffu;
+    return __ushort_as_bfloat16((unsigned short)(b >> 16));
+}
+// stochastic rounding of v to half: random bits below its 10-bit mantissa
+// (13 float bits in the normal range), then round toward zero
+__device__ __forceinline__ __half sr_f16(float v, uint32_t r) {
+    uint32_t b = __float_as_uint(v);
+    if ((b & 0x7f800000u) != 0x7f800000u) b = (b + (r & 0x1fffu)) & ~0x1fffu;
+    return __float2half_rz(__uint_as_float(b));
+}
+template <> struct Pop<__half> {
+    static constexpr bool shifted = true;
+    __device__ static float ld(const __half *p) { return __half2float(__ldg(p)) * F16_INV_SCALE; }
+    __device__ static float st(__half *p, float v, uint32_t r) {
+        const __half h = sr_f16(v * F16_SCALE, r);
+        *p = h;
+        return __half2float(h) * F16_INV_SCALE;
+    }
+};
+template <> struct Pop<__nv_bfloat16> {
+    static constexpr bool shifted = true;
+    __device__ static float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    __device__ static float st(__nv_bfloat16 *p, float v, uint32_t r) {
+        const __nv_bfloat16 h = sr_bf16(v, r);
+        *p = h;
+        return __bfloat162float(h);
+    }
+};
 
 // Offsets from node n to its neighbour at -e in each axis (periodic).
 struct Deltas {
@@ -69,20 +125,36 @@ __device__ __forceinline__ int src_off(const Deltas &d, int N, int i) {
     if ((ez(i) == 1 && d.wlo) || (ez(i) == -1 && d.whi)) return opp(i) * N;
     return i * N + nb_off(d, -ex(i), -ey(i), -ez(i));
 }
+// node offset of that source
+__device__ __forceinline__ int src_node_off(const Deltas &d, int i) {
+    if ((ez(i) == 1 && d.wlo) || (ez(i) == -1 && d.whi)) return 0;
+    return nb_off(d, -ex(i), -ey(i), -ez(i));
+}
 
 // Post-streaming populations of the node: coalesced gathers, then the
 // bounce-back values of its membrane-cut links.
+template <typename T>
 __device__ __forceinline__ uint32_t pull(const LBParams &p, const Deltas &d, float (&fa)[Q],
                                          float (&fb)[Q]) {
     const int N = (int)p.N;
-    const float *sA = p.src + d.n;
-    const float *sB = p.src + (long long)Q * N + d.n;
+    const T *sA = static_cast<const T *>(p.src) + d.n;
+    const T *sB = static_cast<const T *>(p.src) + (long long)Q * N + d.n;
     const uint32_t m = __ldg(p.mask + d.n);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
+        if (Pop<T>::shifted && i == 0) {  // rest populations are kept in float
+            fa[0] = __ldg(p.src0 + d.n);
+            fb[0] = __ldg(p.src0 + N + d.n);
+            continue;
+        }
         const int o = src_off(d, N, i);
-        fa[i] = __ldg(sA + o);
-        fb[i] = __ldg(sB + o);
+        fa[i] = Pop<T>::ld(sA + o);
+        fb[i] = Pop<T>::ld(sB + o);
+        if (Pop<T>::shifted) {  // decode with the density of the source node
+            const float4 r = __ldg(p.dens_src + d.n + src_node_off(d, i));
+            fa[i] += wgt(i) * r.x;
+            fb[i] += wgt(i) * r.y;
+        }
     }
     if (m) {
         // membrane-cut links: the bounced populations (Ladd's moving-wall term
@@ -107,13 +179,17 @@ __device__ __forceinline__ bool node_of(const LBParams &p, int &x, int &y, int &
     return x < p.nx && y < p.ny;
 }
 
+template <typename T>
 __global__ void __launch_bounds__(BX *BY, 6) k_density(const LBParams p) {
+    if (Pop<T>::shifted && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 &&
+        threadIdx.x == 0 && threadIdx.y == 0)
+        atomicAdd(p.step_ctr, 1u);  // read by the collide pass that follows
     int x, y, z;
     if (!node_of(p, x, y, z)) return;
     for (; z < p.zhi; z += gridDim.z) {
         const Deltas d = deltas(p, x, y, z);
         float fa[Q], fb[Q];
-        pull(p, d, fa, fb);
+        pull<T>(p, d, fa, fb);
         float ra = 0.f, rb = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) { ra += fa[i]; rb += fb[i]; }
@@ -122,9 +198,10 @@ __global__ void __launch_bounds__(BX *BY, 6) k_density(const LBParams p) {
 }
 
 // Shan-Chen force with decoupling, velocity shift, BGK, store.
+template <typename T>
 __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d) {
     float fa[Q], fb[Q];
-    const uint32_t m = pull(p, d, fa, fb);
+    const uint32_t m = pull<T>(p, d, fa, fb);
     const int n = d.n;
     const float4 me = __ldg(p.dens + n);
     const float ra = me.x, rb = me.y, pa = me.z, pb = me.w;
@@ -204,13 +281,37 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
     const float ka = 1.0f - 1.5f * (ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2]);
     const float kb = 1.0f - 1.5f * (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
     const int N = (int)p.N;
-    float *__restrict__ dA = p.dst + n;
-    float *__restrict__ dB = p.dst + (long long)Q * N + n;
+    T *__restrict__ dA = static_cast<T *>(p.dst) + n;
+    T *__restrict__ dB = static_cast<T *>(p.dst) + (long long)Q * N + n;
     const float ta = p.itau[0], tb = p.itau[1];
     // Eq. 5 for opposite pairs: f^eq_{i,i+1} = w rho (ka + 4.5 eu^2 +- 3 eu); the
     // rest population takes the mass balance (sum_i f^eq_i = rho) so that the
     // float32 weights (which sum to 1 + 1.5e-8) create no mass
     float qa0 = ra, qb0 = rb;
+    if (!Pop<T>::shifted) {
+#pragma unroll
+        for (int i = 1; i < Q; i += 2) {
+            const float eua = ex(i) * ua[0] + ey(i) * ua[1] + ez(i) * ua[2];
+            const float eub = ex(i) * ub[0] + ey(i) * ub[1] + ez(i) * ub[2];
+            const float wa = wgt(i) * ra, wb = wgt(i) * rb;
+            const float sa_ = wa * (ka + 4.5f * eua * eua), sb_ = wb * (kb + 4.5f * eub * eub);
+            const float qa1 = sa_ + 3.0f * wa * eua, qa2 = sa_ - 3.0f * wa * eua;
+            const float qb1 = sb_ + 3.0f * wb * eub, qb2 = sb_ - 3.0f * wb * eub;
+            qa0 -= qa1 + qa2;
+            qb0 -= qb1 + qb2;
+            Pop<T>::st(dA + i * N, fa[i] - (fa[i] - qa1) * ta, 0u);
+            Pop<T>::st(dA + (i + 1) * N, fa[i + 1] - (fa[i + 1] - qa2) * ta, 0u);
+            Pop<T>::st(dB + i * N, fb[i] - (fb[i] - qb1) * tb, 0u);
+            Pop<T>::st(dB + (i + 1) * N, fb[i + 1] - (fb[i + 1] - qb2) * tb, 0u);
+        }
+        Pop<T>::st(dA, fa[0] - (fa[0] - qa0) * ta, 0u);
+        Pop<T>::st(dB, fb[0] - (fb[0] - qb0) * tb, 0u);
+        return;
+    }
+    // 16-bit offsets from w_i rho, stochastically rounded; the float rest
+    // population takes what the rounded moving populations leave of the mass
+    uint32_t rs = mix32((uint32_t)n * 0x9e3779b9u ^ mix32(*p.step_ctr));
+    float ma = ra, mb = rb;  // mass left for the rest populations
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
         const float eua = ex(i) * ua[0] + ey(i) * ua[1] + ez(i) * ua[2];
@@ -219,37 +320,49 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
         const float sa_ = wa * (ka + 4.5f * eua * eua), sb_ = wb * (kb + 4.5f * eub * eub);
         const float qa1 = sa_ + 3.0f * wa * eua, qa2 = sa_ - 3.0f * wa * eua;
         const float qb1 = sb_ + 3.0f * wb * eub, qb2 = sb_ - 3.0f * wb * eub;
-        qa0 -= qa1 + qa2;
-        qb0 -= qb1 + qb2;
-        dA[i * N] = fa[i] - (fa[i] - qa1) * ta;
-        dA[(i + 1) * N] = fa[i + 1] - (fa[i + 1] - qa2) * ta;
-        dB[i * N] = fb[i] - (fb[i] - qb1) * tb;
-        dB[(i + 1) * N] = fb[i + 1] - (fb[i + 1] - qb2) * tb;
+        // an LCG step per store draws its rounding bits
+        rs = rs * 1664525u + 1013904223u;
+        ma -= Pop<T>::st(dA + i * N, fa[i] - (fa[i] - qa1) * ta - wa, rs >> 8) + wa;
+        rs = rs * 1664525u + 1013904223u;
+        ma -= Pop<T>::st(dA + (i + 1) * N, fa[i + 1] - (fa[i + 1] - qa2) * ta - wa, rs >> 8) + wa;
+        rs = rs * 1664525u + 1013904223u;
+        mb -= Pop<T>::st(dB + i * N, fb[i] - (fb[i] - qb1) * tb - wb, rs >> 8) + wb;
+        rs = rs * 1664525u + 1013904223u;
+        mb -= Pop<T>::st(dB + (i + 1) * N, fb[i + 1] - (fb[i + 1] - qb2) * tb - wb, rs >> 8) + wb;
     }
-    dA[0] = fa[0] - (fa[0] - qa0) * ta;
-    dB[0] = fb[0] - (fb[0] - qb0) * tb;
+    p.dst0[n] = ma;
+    p.dst0[N + n] = mb;
 }
 
-__global__ void __launch_bounds__(BX *BY, 6) k_collide(const LBParams p) {
+template <typename T>
+__global__ void __launch_bounds__(BX *BY, Pop<T>::shifted ? 5 : 6) k_collide(const LBParams p) {
     int x, y, z;
     if (!node_of(p, x, y, z)) return;
-    for (; z < p.zhi; z += gridDim.z) collide_node(p, deltas(p, x, y, z));
+    for (; z < p.zhi; z += gridDim.z) collide_node<T>(p, deltas(p, x, y, z));
 }
 
-cudaError_t launch_lb_step(const LBParams &p, int variant, cudaStream_t s) {
-    (void)variant;
+cudaError_t launch_lb_step(const LBParams &p, int prec, cudaStream_t s) {
     const int nzf = p.zhi - p.zlo;
     const int gz = p.zchunk > 0 ? (nzf + p.zchunk - 1) / p.zchunk : nzf;
     dim3 grid((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, gz), block(BX, BY);
-    k_density<<<grid, block, 0, s>>>(p);
-    k_collide<<<grid, block, 0, s>>>(p);
+    if (prec == P_F16) {
+        k_density<__half><<<grid, block, 0, s>>>(p);
+        k_collide<__half><<<grid, block, 0, s>>>(p);
+    } else if (prec == P_BF16) {
+        k_density<__nv_bfloat16><<<grid, block, 0, s>>>(p);
+        k_collide<__nv_bfloat16><<<grid, block, 0, s>>>(p);
+    } else {
+        k_density<float><<<grid, block, 0, s>>>(p);
+        k_collide<float><<<grid, block, 0, s>>>(p);
+    }
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ film set-up
-__global__ void k_init_film(float *f, float4 *dens, long long N, int nx, int ny, int nz, int wall,
-                           float h_top, float rmaj, float rmin, float rmix, const double *jit,
-                           const uint8_t *inside) {
+template <typename T>
+__global__ void k_init_film(T *f, float *f0, float4 *dens, long long N, int nx, int ny, int nz,
+                           int wall, float h_top, float rmaj, float rmin, float rmix,
+                           const double *jit, const uint8_t *inside) {
     const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= N) return;
     const int z = (int)(n / ((long long)nx * ny));
@@ -264,23 +377,46 @@ __global__ void k_init_film(float *f, float4 *dens, long long N, int nx, int ny,
         if (jit) { r[0] += jit[n]; r[1] += jit[N + n]; }
     }
     float ra = 0.f, rb = 0.f;
+    if (Pop<T>::shifted) {  // rest state: zero offsets from w_i rho, float rest populations
+        ra = (float)r[0];
+        rb = (float)r[1];
+        float ma = ra, mb = rb;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const double w = i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
-        const float fa = (float)(w * r[0]), fb = (float)(w * r[1]);
-        f[(long long)i * N + n] = fa;
-        f[(long long)(Q + i) * N + n] = fb;
-        ra += fa;
-        rb += fb;
+        for (int i = 1; i < Q; ++i) {
+            Pop<T>::st(f + (long long)i * N + n, 0.f, 0u);
+            Pop<T>::st(f + (long long)(Q + i) * N + n, 0.f, 0u);
+            ma -= wgt(i) * ra;
+            mb -= wgt(i) * rb;
+        }
+        f0[n] = ma;
+        f0[N + n] = mb;
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const double w = i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+            const float fa = (float)(w * r[0]), fb = (float)(w * r[1]);
+            Pop<T>::st(f + (long long)i * N + n, fa, 0u);
+            Pop<T>::st(f + (long long)(Q + i) * N + n, fb, 0u);
+            ra += fa;
+            rb += fb;
+        }
     }
     dens[n] = make_float4(ra, rb, psi_of(ra), psi_of(rb));  // density of the initial state
 }
 
-cudaError_t launch_init_film(float *f, float4 *dens, long long N, int nx, int ny, int nz, int wall,
-                             float h_top, float rmaj, float rmin, float rmix, const double *jit,
-                             const uint8_t *inside, cudaStream_t s) {
-    k_init_film<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(f, dens, N, nx, ny, nz, wall, h_top, rmaj,
-                                                             rmin, rmix, jit, inside);
+cudaError_t launch_init_film(void *f, float *f0, int prec, float4 *dens, long long N, int nx, int ny,
+                             int nz, int wall, float h_top, float rmaj, float rmin, float rmix,
+                             const double *jit, const uint8_t *inside, cudaStream_t s) {
+    const unsigned g = (unsigned)((N + 255) / 256);
+    if (prec == P_F16)
+        k_init_film<<<g, 256, 0, s>>>(static_cast<__half *>(f), f0, dens, N, nx, ny, nz, wall, h_top,
+                                      rmaj, rmin, rmix, jit, inside);
+    else if (prec == P_BF16)
+        k_init_film<<<g, 256, 0, s>>>(static_cast<__nv_bfloat16 *>(f), f0, dens, N, nx, ny, nz, wall,
+                                      h_top, rmaj, rmin, rmix, jit, inside);
+    else
+        k_init_film<<<g, 256, 0, s>>>(static_cast<float *>(f), f0, dens, N, nx, ny, nz, wall, h_top,
+                                      rmaj, rmin, rmix, jit, inside);
     return cudaGetLastError();
 }
 
@@ -326,15 +462,27 @@ cudaError_t launch_meniscus(const float *out, const uint8_t *inside, float *h, i
     return cudaGetLastError();
 }
 
-// FP64 mass of each component
-__global__ void k_mass(const float *f, long long N, double *m2) {
+// FP64 mass of each component (decoded populations)
+template <typename T>
+__global__ void k_mass(const T *f, const float *f0, const float4 *dens, long long N, double *m2) {
     double s[2] = {0.0, 0.0};
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
+        if (Pop<T>::shifted) {
+            const float4 r = dens[n];
+            s[0] += f0[n];
+            s[1] += f0[N + n];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            s[0] += f[(long long)i * N + n];
-            s[1] += f[(long long)(Q + i) * N + n];
+            for (int i = 1; i < Q; ++i) {
+                s[0] += Pop<T>::ld(f + (long long)i * N + n) + wgt(i) * r.x;
+                s[1] += Pop<T>::ld(f + (long long)(Q + i) * N + n) + wgt(i) * r.y;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                s[0] += Pop<T>::ld(f + (long long)i * N + n);
+                s[1] += Pop<T>::ld(f + (long long)(Q + i) * N + n);
+            }
         }
     }
     for (int c = 0; c < 2; ++c) {
@@ -344,8 +492,12 @@ __global__ void k_mass(const float *f, long long N, double *m2) {
     }
 }
 
-cudaError_t launch_mass(const float *f, long long N, double *m2, cudaStream_t s) {
-    k_mass<<<304, 256, 0, s>>>(f, N, m2);
+cudaError_t launch_mass(const void *f, const float *f0, int prec, const float4 *dens, long long N,
+                        double *m2, cudaStream_t s) {
+    if (prec == P_F16) k_mass<<<304, 256, 0, s>>>(static_cast<const __half *>(f), f0, dens, N, m2);
+    else if (prec == P_BF16)
+        k_mass<<<304, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(f), f0, dens, N, m2);
+    else k_mass<<<304, 256, 0, s>>>(static_cast<const float *>(f), f0, dens, N, m2);
     return cudaGetLastError();
 }
 
@@ -373,7 +525,8 @@ __global__ void __launch_bounds__(BX *BY) k_density_static(const LBParams p) {
     const int N = (int)p.N;
     for (; z < p.zhi; z += gridDim.z) {
         const Deltas d = deltas(p, x, y, z);
-        const float *sA = p.src + d.n, *sB = p.src + (long long)Q * N + d.n;
+        const float *src = static_cast<const float *>(p.src);
+        const float *sA = src + d.n, *sB = src + (long long)Q * N + d.n;
         float ra = 0.f, rb = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -391,7 +544,8 @@ __device__ __forceinline__ void collide_node_static(const LBParams &p, const Del
     const int N = (int)p.N, n = d.n;
     float fa[Q], fb[Q];
     {
-        const float *sA = p.src + n, *sB = p.src + (long long)Q * N + n;
+        const float *src = static_cast<const float *>(p.src);
+        const float *sA = src + n, *sB = src + (long long)Q * N + n;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int o = src_off(d, N, i);
@@ -452,8 +606,8 @@ __device__ __forceinline__ void collide_node_static(const LBParams &p, const Del
     }
     const float ka = 1.0f - 1.5f * (ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2]);
     const float kb = 1.0f - 1.5f * (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
-    float *__restrict__ dA = p.dst + n;
-    float *__restrict__ dB = p.dst + (long long)Q * N + n;
+    float *__restrict__ dA = static_cast<float *>(p.dst) + n;
+    float *__restrict__ dB = static_cast<float *>(p.dst) + (long long)Q * N + n;
     const float ta = p.itau[0], tb = p.itau[1];
     float qa0 = ra, qb0 = rb;
 #pragma unroll

@@ -20,6 +20,8 @@
 // are rebuilt by k_cut_clear, k_cut_faces and k_cut_claim; k_cut_prep builds
 // the bounce records of the cut nodes at the start of each step.
 #include "cf_common.cuh"
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cfloat>
 #include <climits>
 #include <algorithm>
@@ -630,6 +632,17 @@ cudaError_t launch_cuts(const CutParams &p, int prev_hint, cudaStream_t s, int *
     return cudaGetLastError();
 }
 
+// Post-collision population (component c, direction k) of node n, decoded
+// (16-bit storage holds the offset from w_k rho of the node).
+__device__ __forceinline__ float pop_at(const PrepParams &p, int c, int k, int n, float rho) {
+    const long long i = ((long long)c * Q + k) * p.N + n;
+    if (p.prec == P_F16)
+        return __half2float(static_cast<const __half *>(p.src)[i]) * F16_INV_SCALE + wgt(k) * rho;
+    if (p.prec == P_BF16)
+        return __bfloat162float(static_cast<const __nv_bfloat16 *>(p.src)[i]) + wgt(k) * rho;
+    return static_cast<const float *>(p.src)[i];
+}
+
 // Bounce records for the next streaming, one thread per cut node: the
 // population a cut node sent towards the membrane comes back with Ladd's term
 // -2 w_k rho (e_k . u_T)/c_s^2 (rho: the node's density = sum of its
@@ -642,7 +655,6 @@ __global__ void k_cut_prep(const PrepParams p) {
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < cnt; u += gridDim.x * blockDim.x) {
         const int n = p.uniq[u];
         const uint32_t m = p.mask[n];
-        const float *sA = p.src + n, *sB = p.src + (long long)Q * N + n;
         // the node's density: the sum of its post-collision populations equals
         // the density of the step that produced them (BGK conserves mass)
         const float4 dn = __ldg(p.dens + n);
@@ -659,7 +671,7 @@ __global__ void k_cut_prep(const PrepParams p) {
             const float uy = (p.V[3 * a + 1] + p.V[3 * b + 1] + p.V[3 * c + 1]) * (1.0f / 3.0f);
             const float uz = (p.V[3 * a + 2] + p.V[3 * b + 2] + p.V[3 * c + 2]) * (1.0f / 3.0f);
             const float eu = kx * ux + ky * uy + kz * uz;
-            const float foa = __ldg(sA + k * N), fob = __ldg(sB + k * N);
+            const float foa = pop_at(p, 0, k, n, rwa), fob = pop_at(p, 1, k, n, rwb);
             const float w6 = 6.0f * wgt(k);
             const float ca = w6 * rwa * eu, cb = w6 * rwb * eu;
             R[opp(k)] = foa - ca;
