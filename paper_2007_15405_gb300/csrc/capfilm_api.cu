@@ -70,6 +70,10 @@ struct cf_ctx {
     long long N = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // second stream for the membrane's position-only kernels, forked from and
+    // joined back into `stream` every step
+    cudaStream_t stream2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cf_allocator alloc{};
     bool has_alloc = false;
     std::vector<void *> allocations;
@@ -82,13 +86,9 @@ struct cf_ctx {
     float4 *dens[2] = {nullptr, nullptr};  // densities paired with each population buffer
     uint32_t *mask = nullptr;
     int *tri = nullptr;
-    uint32_t *owner = nullptr;    // claim flags of cut nodes
-    int *cutrec = nullptr;        // [N] bounce record of a cut node
-    int *uniq = nullptr;          // distinct cut nodes
-    int *ucount = nullptr;
-    float *rec = nullptr;         // [capacity][38] bounce records
+    float2 *rec = nullptr;        // [N][18] bounce records (A, B) by arriving direction
     uint8_t *inside = nullptr;
-    int *list[2] = {nullptr, nullptr};
+    int2 *list[2] = {nullptr, nullptr};  // cut-link entries (node << 5 | k - 1, element)
     int *counts = nullptr;  // [2]
     int lpar = 0;
     int capacity = 0;
@@ -104,7 +104,11 @@ struct cf_ctx {
     bool any_frozen = false, all_fixed = true;
     float *X[2] = {nullptr, nullptr};  // [hi 3*nv | lo 3*nv] per buffer
     int xpar = 0;
-    float *V = nullptr, *FT = nullptr, *FTprev = nullptr, *fscr = nullptr, *vscr = nullptr,
+    // momentum exchanged with each element: FT[ftpar] accumulates this step's,
+    // FT[1 - ftpar] holds the previous step's (two-step average)
+    float *FT[2] = {nullptr, nullptr};
+    int ftpar = 0;
+    float *V = nullptr, *fscr = nullptr, *vscr = nullptr,
           *Fcpl = nullptr, *refM = nullptr, *refA = nullptr, *refDet = nullptr;
     int *faces = nullptr, *face_cap = nullptr, *node_cap = nullptr, *vf_off = nullptr,
         *vf_ent = nullptr, *bbox[2] = {nullptr, nullptr};
@@ -120,6 +124,7 @@ struct cf_ctx {
 
     cudaGraphExec_t graph = nullptr;
     int graph_key = -1;
+    int graph_launches = 0;  // kernel launches of one graph replay (two steps)
 };
 
 namespace {
@@ -177,10 +182,9 @@ LBParams lb_params(cf_ctx *c, bool with_out) {
     p.tri = c->tri;
     p.faces = c->faces;
     p.V = c->V;
-    p.FT = c->FT;
+    p.FT = c->FT[c->ftpar];
     p.out = with_out ? c->out : nullptr;
     p.dens = c->dens[1 - c->fpar];
-    p.cutrec = c->cutrec;
     p.rec = c->rec;
     p.status = c->status;
     return p;
@@ -206,15 +210,14 @@ MemParams mem_params(cf_ctx *c) {
     p.Xnh = c->X[1 - c->xpar];
     p.Xnl = c->X[1 - c->xpar] + 3 * (size_t)c->nnodes;
     p.V = c->V;
-    p.FT = c->FT;
-    p.FTprev = c->FTprev;
+    p.FT = c->FT[c->ftpar];
+    p.FTprev = c->FT[1 - c->ftpar];
     p.fscr = c->fscr;
     p.vscr = c->vscr;
     p.Fcpl = c->Fcpl;
     p.acc = c->acc;
     p.bbox = c->bbox[c->xpar];
     p.bbox_prev = c->bbox[1 - c->xpar];
-    p.bar = c->bar;
     p.status = c->status;
     p.any_frozen = c->any_frozen ? 1 : 0;
     return p;
@@ -231,28 +234,44 @@ cf_status enqueue_cuts(cf_ctx *c, const float *X, int *nl) {
     q.X = X;
     q.mask = c->mask;
     q.tri = c->tri;
-    q.owner = c->owner;
-    q.uniq = c->uniq;
-    q.ucount = c->ucount;
-    q.cutrec = c->cutrec;
     q.list = c->list[cur];
     q.count = c->counts + cur;
     q.prev_count = c->counts + c->lpar;
     q.prev_list = c->list[c->lpar];
+    q.FTnext = c->FT[1 - c->ftpar];
     q.capacity = c->capacity;
     q.status = c->status;
     CF_CUDA(cudaMemsetAsync(c->counts + cur, 0, sizeof(int), c->stream));
-    CF_CUDA(cudaMemsetAsync(c->ucount, 0, sizeof(int), c->stream));
     CF_CUDA(launch_cuts(q, 0, c->stream, nl));
     c->lpar = cur;
     return CF_OK;
 }
 
 // One coupled step on the stream (also used under graph capture).  ev, when
-// given, receives four events bracketing the lattice, membrane and cut phases.
+// given, receives five events: ev[4] step start, ev[0] after the bounce
+// records, ev[1] after the lattice update, ev[2] after the node update, ev[3]
+// after the cut links.
+//
+//   stream   prep -> density -> collide -----join-> update [-> frozen] -> cuts
+//   stream2        \-> memsets -> elements -> nodes -> bending -/
+//
+// The membrane's position-only kernels run beside the lattice update; the
+// node update waits for both.
 cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev = nullptr) {
     if (ev) CF_CUDA(cudaEventRecord(ev[4], c->stream));
-    if (c->nnodes) {  // bounce records of the cut nodes for this step's streaming
+    const bool mem = c->nnodes > 0;
+    if (mem) {
+        // fork: elastic, volume and bending forces of the current positions
+        CF_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+        CF_CUDA(cudaStreamWaitEvent(c->stream2, c->ev_fork, 0));
+        const int nc = (int)c->caps.size();
+        int *bb = c->bbox[c->xpar];
+        CF_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(double) * A_NACC * nc, c->stream2));
+        CF_CUDA(cudaMemsetAsync(bb, 0x7f, sizeof(int) * 3 * nc, c->stream2));
+        CF_CUDA(cudaMemsetAsync(bb + 3 * nc, 0x80, sizeof(int) * 3 * nc, c->stream2));
+        CF_CUDA(launch_membrane_forces(mem_params(c), c->stream2, nl));
+        CF_CUDA(cudaEventRecord(c->ev_join, c->stream2));
+        // bounce records of the cut links for this step's streaming
         PrepParams q{};
         q.N = c->N;
         q.prec = c->d.precision;
@@ -262,10 +281,10 @@ cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev = null
         q.tri = c->tri;
         q.faces = c->faces;
         q.V = c->V;
-        q.uniq = c->uniq;
-        q.ucount = c->ucount;
+        q.list = c->list[c->lpar];
+        q.count = c->counts + c->lpar;
         q.rec = c->rec;
-        q.FT = c->FT;
+        q.FT = c->FT[c->ftpar];
         q.capacity = c->capacity;
         CF_CUDA(launch_prep(q, c->stream, nl));
     }
@@ -274,20 +293,22 @@ cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev = null
     *nl += 2;
     c->fpar = 1 - c->fpar;
     if (ev) CF_CUDA(cudaEventRecord(ev[1], c->stream));
-    if (c->nnodes) {
-        const int nc = (int)c->caps.size();
-        int *bb = c->bbox[c->xpar];
-        CF_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(double) * A_NACC * nc, c->stream));
-        CF_CUDA(cudaMemsetAsync(bb, 0x7f, sizeof(int) * 3 * nc, c->stream));
-        CF_CUDA(cudaMemsetAsync(bb + 3 * nc, 0x80, sizeof(int) * 3 * nc, c->stream));
-        CF_CUDA(cudaMemsetAsync(c->bar, 0, sizeof(unsigned) * 2, c->stream));
-        CF_CUDA(launch_membrane(mem_params(c), c->any_frozen, c->stream, nl));
+    if (mem) {
+        CF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+        CF_CUDA(launch_membrane_update(mem_params(c), c->any_frozen, c->stream, nl));
         c->xpar = 1 - c->xpar;
     }
     if (ev) CF_CUDA(cudaEventRecord(ev[2], c->stream));
-    if (c->nnodes && !c->all_fixed) {
-        cf_status s = enqueue_cuts(c, c->X[c->xpar], nl);
-        if (s != CF_OK) return s;
+    if (mem) {
+        if (!c->all_fixed) {
+            // also zeroes the exchange accumulator of the next step
+            cf_status s = enqueue_cuts(c, c->X[c->xpar], nl);
+            if (s != CF_OK) return s;
+        } else {
+            CF_CUDA(cudaMemsetAsync(c->FT[1 - c->ftpar], 0, sizeof(float) * 3 * (size_t)c->nfaces,
+                                    c->stream));
+        }
+        c->ftpar = 1 - c->ftpar;
     }
     if (ev) CF_CUDA(cudaEventRecord(ev[3], c->stream));
     return CF_OK;
@@ -388,8 +409,8 @@ cf_status build_membrane(cf_ctx *c) {
     MALLOC_M(c->V, float, 3 * nv);
     MALLOC_M(c->Fcpl, float, 3 * nv);
     MALLOC_M(c->vscr, float, 4 * nv);
-    MALLOC_M(c->FT, float, 3 * nf);
-    MALLOC_M(c->FTprev, float, 3 * nf);
+    MALLOC_M(c->FT[0], float, 3 * nf);
+    MALLOC_M(c->FT[1], float, 3 * nf);
     MALLOC_M(c->fscr, float, (size_t)FS_N * nf);
     MALLOC_M(c->refM, float, 3 * nf);
     MALLOC_M(c->refA, float, nf);
@@ -429,8 +450,9 @@ cf_status build_membrane(cf_ctx *c) {
     }
     CF_CUDA(cudaMemsetAsync(c->V, 0, sizeof(float) * 3 * nv, c->stream));
     CF_CUDA(cudaMemsetAsync(c->Fcpl, 0, sizeof(float) * 3 * nv, c->stream));
-    CF_CUDA(cudaMemsetAsync(c->FT, 0, sizeof(float) * 3 * nf, c->stream));
-    CF_CUDA(cudaMemsetAsync(c->FTprev, 0, sizeof(float) * 3 * nf, c->stream));
+    CF_CUDA(cudaMemsetAsync(c->FT[0], 0, sizeof(float) * 3 * nf, c->stream));
+    CF_CUDA(cudaMemsetAsync(c->FT[1], 0, sizeof(float) * 3 * nf, c->stream));
+    c->ftpar = 0;
     CF_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(double) * A_NACC * nc, c->stream));
     CF_CUDA(up(c->refM, refM.data(), sizeof(float) * refM.size()));
     CF_CUDA(up(c->refA, refA.data(), sizeof(float) * refA.size()));
@@ -441,20 +463,19 @@ cf_status build_membrane(cf_ctx *c) {
     CF_CUDA(up(c->vf_off, vf_off.data(), sizeof(int) * vf_off.size()));
     CF_CUDA(up(c->vf_ent, vf_ent.data(), sizeof(int) * vf_ent.size()));
     CF_CUDA(up(c->capdev, cd.data(), sizeof(CapDev) * cd.size()));
-    // cut-link node lists: nodes within one link of any element
+    // cut-link lists: one entry per end node of each crossing (link, element);
+    // an element of edge < 1 crosses a few links, 24 entries per element is a
+    // wide bound (overflow raises CF_EOVERFLOW)
     c->capacity = (int)std::min<long long>(36LL * c->N, 24LL * nf + 4096);
     for (int k = 0; k < 2; ++k) {
-        c->list[k] = (int *)dalloc(c, sizeof(int) * (size_t)c->capacity, true);
+        c->list[k] = (int2 *)dalloc(c, sizeof(int2) * (size_t)c->capacity, true);
         if (!c->list[k]) return fail(CF_ENOMEM, "device allocation failed (cut lists)");
     }
-    c->uniq = (int *)dalloc(c, sizeof(int) * (size_t)c->capacity, true);
-    c->ucount = (int *)dalloc(c, sizeof(int), true);
-    c->rec = (float *)dalloc(c, sizeof(float) * 2 * Q * (size_t)c->capacity, true);
-    if (!c->uniq || !c->ucount || !c->rec) return fail(CF_ENOMEM, "device allocation failed (cut records)");
-    CF_CUDA(cudaMemsetAsync(c->ucount, 0, sizeof(int), c->stream));
+    // bounce records, dense per node: written and read only at cut links
+    c->rec = (float2 *)dalloc(c, sizeof(float2) * 18 * (size_t)c->N, true);
+    if (!c->rec) return fail(CF_ENOMEM, "device allocation failed (cut records)");
     // start from a clean cut structure
     CF_CUDA(cudaMemsetAsync(c->mask, 0, sizeof(uint32_t) * c->N, c->stream));
-    CF_CUDA(cudaMemsetAsync(c->owner, 0, sizeof(uint32_t) * c->N, c->stream));
     CF_CUDA(cudaMemsetAsync(c->tri, 0x7f, sizeof(int) * 18 * (size_t)c->N, c->stream));
     CF_CUDA(cudaMemsetAsync(c->counts, 0, sizeof(int) * 2, c->stream));
     // 0x7f7f7f7f is not INT_MAX but any value above every element index works
@@ -501,6 +522,12 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
         }
         c->own_stream = true;
     }
+    if (cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cf_destroy(c);
+        return fail(CF_ECUDA, "stream / event creation failed");
+    }
     const long long N = c->N;
     const size_t pb = pop_bytes(desc->precision);
     c->f[0] = dalloc(c, pb * 38 * N);
@@ -513,16 +540,13 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     c->dens[1] = (float4 *)dalloc(c, sizeof(float4) * N);
     c->mask = (uint32_t *)dalloc(c, sizeof(uint32_t) * N);
     c->tri = (int *)dalloc(c, sizeof(int) * 18 * N);
-    c->owner = (uint32_t *)dalloc(c, sizeof(uint32_t) * N);
-    c->cutrec = (int *)dalloc(c, sizeof(int) * N);
     c->inside = (uint8_t *)dalloc(c, N);
     c->counts = (int *)dalloc(c, sizeof(int) * 2);
     c->status = (unsigned *)dalloc(c, sizeof(unsigned));
-    c->bar = (unsigned *)dalloc(c, sizeof(unsigned) * 2);
     c->dscratch = (double *)dalloc(c, sizeof(double) * 8);
     c->hscratch = (float *)dalloc(c, sizeof(float) * desc->nx * desc->ny);
-    if (!c->f[0] || !c->f[1] || !c->f0[0] || !c->f0[1] || !c->step_ctr || !c->out || !c->dens[0] || !c->dens[1] || !c->mask || !c->tri || !c->owner || !c->cutrec || !c->inside ||
-        !c->counts || !c->status || !c->bar || !c->dscratch || !c->hscratch) {
+    if (!c->f[0] || !c->f[1] || !c->f0[0] || !c->f0[1] || !c->step_ctr || !c->out || !c->dens[0] || !c->dens[1] || !c->mask || !c->tri || !c->inside ||
+        !c->counts || !c->status || !c->dscratch || !c->hscratch) {
         cf_destroy(c);
         return fail(CF_ENOMEM, "device allocation failed");
     }
@@ -536,8 +560,6 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     cudaMemsetAsync(c->out, 0, sizeof(float) * 5 * N, c->stream);
     cudaMemsetAsync(c->mask, 0, sizeof(uint32_t) * N, c->stream);
     cudaMemsetAsync(c->tri, 0x7f, sizeof(int) * 18 * N, c->stream);
-    cudaMemsetAsync(c->owner, 0, sizeof(uint32_t) * N, c->stream);
-    cudaMemsetAsync(c->cutrec, 0, sizeof(int) * N, c->stream);
     cudaMemsetAsync(c->inside, 0, N, c->stream);
     cudaMemsetAsync(c->counts, 0, sizeof(int) * 2, c->stream);
     cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream);
@@ -559,6 +581,9 @@ cf_status cf_destroy(cf_ctx *c) {
     for (void *p : c->allocations) dfree(c, p);
     if (c->jit) dfree(c, c->jit);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->stream2) { cudaStreamSynchronize(c->stream2); cudaStreamDestroy(c->stream2); }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return CF_OK;
@@ -634,7 +659,7 @@ cf_status cf_step(cf_ctx *c, long long n) {
     int nl = 0;
     long long left = n - 1;  // the last step records the fields
     if (left >= 2) {
-        const int key = c->fpar | (c->xpar << 1) | (c->lpar << 2);
+        const int key = c->fpar | (c->xpar << 1) | (c->lpar << 2) | (c->ftpar << 3);
         if (!c->graph || c->graph_key != key) {
             if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
             cudaGraph_t g;
@@ -649,17 +674,12 @@ cf_status cf_step(cf_ctx *c, long long n) {
             cudaGraphDestroy(g);
             if (e != cudaSuccess) return fail(CF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
             c->graph_key = key;
-        }
-        int per_pair = 0;
-        {
-            // count the launches of one step pair (for reporting)
-            const bool fx = c->all_fixed;
-            per_pair = 2 * (2 + (c->nnodes ? 2 + (fx ? 0 : 3) : 0));
+            c->graph_launches = nlg;
         }
         while (left >= 2) {
             CF_CUDA(cudaGraphLaunch(c->graph, c->stream));
             left -= 2;
-            nl += per_pair;
+            nl += c->graph_launches;
         }
     }
     while (left > 0) {

@@ -25,6 +25,28 @@ __host__ __device__ constexpr float wgt(int i) {
 }
 constexpr int Q = 19;
 
+// Directions 0..18 packed 6 bits each ((ex+1) | (ey+1) << 2 | (ez+1) << 4),
+// for code that selects a direction at run time (ek below).
+constexpr unsigned long long pack_dirs(int lo) {
+    unsigned long long v = 0;
+    for (int j = 0; j < 10 && lo + j < Q; ++j) {
+        const int k = lo + j;
+        v |= (unsigned long long)((ex(k) + 1) | ((ey(k) + 1) << 2) | ((ez(k) + 1) << 4)) << (6 * j);
+    }
+    return v;
+}
+constexpr unsigned long long DIRS_LO = pack_dirs(0), DIRS_HI = pack_dirs(10);
+__host__ __device__ __forceinline__ void ek(int k, int &x, int &y, int &z) {
+    const unsigned c = (unsigned)((k < 10 ? DIRS_LO : DIRS_HI) >> (6 * (k < 10 ? k : k - 10))) & 63u;
+    x = (int)(c & 3u) - 1;
+    y = (int)((c >> 2) & 3u) - 1;
+    z = (int)((c >> 4) & 3u) - 1;
+}
+
+// One entry of the cut-link list: link k (1..18) of node n, marked by element T.
+// code = n << 5 | (k - 1); n < 2^26 for every lattice cf_create accepts.
+__host__ __device__ __forceinline__ int cut_code(long long n, int k) { return (int)(n << 5) | (k - 1); }
+
 // Storage of the populations: float, or half / bfloat16 offsets from the
 // rest equilibrium w_i rho of the node (rho kept in float in the density array).
 enum Prec { P_F32 = 0, P_F16 = 1, P_BF16 = 2 };
@@ -53,8 +75,7 @@ struct LBParams {
     const int *__restrict__ faces;      // element nodes [3*nfaces]
     const float *__restrict__ V;        // node velocities [3*nnodes]
     float *__restrict__ FT;             // element momentum exchange accumulators [3*nfaces]
-    const int *__restrict__ cutrec;     // [N] bounce record of a cut node
-    const float *__restrict__ rec;      // [capacity][2*Q] bounced populations
+    const float2 *__restrict__ rec;     // [N][18] bounced (A, B) populations by arriving direction - 1
     float *__restrict__ out;            // optional [5][N]: rhoA, rhoB, ux, uy, uz
     float4 *__restrict__ dens;          // [N] (rhoA, rhoB, psiA, psiB) of this step (written)
     unsigned *__restrict__ status;      // device error flags
@@ -93,22 +114,20 @@ struct MemParams {
                              // (per-step displacements are below a float ulp at x ~ 100)
     float *Xnh, *Xnl;        // [3*nv] positions of the next step
     float *V;                // [3*nv] node velocities (written)
-    float *FT;               // [3*nf] exchange accumulated by the lattice kernel (zeroed here)
-    float *FTprev;           // [3*nf] exchange of the previous step
+    const float *FT;         // [3*nf] momentum exchanged with the fluid in this step
+    const float *FTprev;     // [3*nf] the same, of the previous step
     float *fscr;             // [nf*FS_N] per-element scratch
     float *vscr;             // [nv*4] per-node scratch (gL, gA)
     float *Fcpl;             // [3*nv] coupling force on nodes (readout)
     double *acc;             // [ncaps*A_NACC]
     int *bbox;               // [ncaps*3] mins then [ncaps*3] maxs of this step (written)
     const int *bbox_prev;    // same, of the previous step (Hertz prefilter)
-    unsigned *bar;           // [2] grid barrier (count, generation)
     unsigned *status;        // device error flags
     int any_frozen;
 };
 
 // per-element scratch layout (floats)
-enum FaceScr { FS_FBAR = 0, FS_SK = 3, FS_DV = 12, FS_L = 21, FS_AF3 = 30, FS_COT = 31,
-               FS_BEND = 34, FS_N = 43 };
+enum FaceScr { FS_SK = 0, FS_DV = 9, FS_L = 18, FS_AF3 = 27, FS_BEND = 28, FS_N = 37 };
 
 struct CutParams {
     int nx, ny, nz, wall;
@@ -117,14 +136,11 @@ struct CutParams {
     const float *X;          // positions (float, hi part) the cut links are computed for
     uint32_t *mask;
     int *tri;
-    uint32_t *owner;         // [N] claim flag of cut nodes (reset with the masks)
-    int *list;               // marked nodes, with repetitions
+    int2 *list;              // one entry per marked link: (cut_code(n, k), T)
     int *count;              // entries appended to `list` (zeroed before)
     const int *prev_count;   // entries of `prev_list`
-    int *prev_list;          // list of the previous computation (cleared first)
-    int *uniq;               // distinct cut nodes
-    int *ucount;             // entries of `uniq` (zeroed before)
-    int *cutrec;             // [N] index into `uniq` / the bounce records of a cut node
+    const int2 *prev_list;   // list of the previous computation (cleared first)
+    float *FTnext;           // [3*nfaces] exchange accumulator of the next step (zeroed first)
     int capacity;
     unsigned *status;
 };
@@ -139,9 +155,9 @@ struct PrepParams {
     const int *tri;
     const int *faces;
     const float *V;
-    const int *uniq;
-    const int *ucount;
-    float *rec;              // [capacity][2*Q] bounced populations (cut directions)
+    const int2 *list;        // cut-link entries (cut_code(n, k), T), with repetitions
+    const int *count;
+    float2 *rec;             // [N][18] bounced (A, B) populations by arriving direction - 1
     float *FT;               // element momentum exchange accumulators
     int capacity;
 };
@@ -166,7 +182,9 @@ cudaError_t launch_meniscus(const float *out, const uint8_t *inside, float *h, i
                             int nz, int wall, cudaStream_t s);
 cudaError_t launch_mass(const void *f, const float *f0, int prec, const float4 *dens, long long N,
                         double *m2, cudaStream_t s);
-cudaError_t launch_membrane(const MemParams &p, bool any_frozen, cudaStream_t s, int *nlaunch);
+// membrane kernels 1-3 (positions only) and 4-5 (after the lattice update)
+cudaError_t launch_membrane_forces(const MemParams &p, cudaStream_t s, int *nlaunch);
+cudaError_t launch_membrane_update(const MemParams &p, bool any_frozen, cudaStream_t s, int *nlaunch);
 cudaError_t launch_cuts(const CutParams &p, int prev_count_hint, cudaStream_t s, int *nlaunch);
 cudaError_t launch_prep(const PrepParams &p, cudaStream_t s, int *nlaunch);
 }  // namespace cf

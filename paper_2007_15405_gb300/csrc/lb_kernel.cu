@@ -159,12 +159,13 @@ __device__ __forceinline__ uint32_t pull(const LBParams &p, const Deltas &d, flo
     if (m) {
         // membrane-cut links: the bounced populations (Ladd's moving-wall term
         // included) were prepared for this step by k_cut_prep
-        const float *R = p.rec + (long long)__ldg(p.cutrec + d.n) * (2 * Q);
+        const float2 *R = p.rec + (long long)d.n * 18;
 #pragma unroll
         for (int k = 1; k < Q; ++k) {
             if ((m >> (k - 1)) & 1u) {
-                fa[opp(k)] = __ldg(R + opp(k));
-                fb[opp(k)] = __ldg(R + Q + opp(k));
+                const float2 v = __ldg(R + opp(k) - 1);
+                fa[opp(k)] = v.x;
+                fb[opp(k)] = v.y;
             }
         }
     }
@@ -236,11 +237,11 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
                 qa = qa_eff; qb = qb_eff;
                 if (cut && !solid) {
                     // reaction of the decoupled interaction on the crossed element
-                    const int T = __ldg(p.tri + (long long)n * 18 + (k - 1));
+                    const int el = __ldg(p.tri + (long long)n * 18 + (k - 1));
                     const float r = p.G * wgt(k) * (pa * qb_eff + pb * qa_eff);
-                    if (ex(k)) atomicAdd(p.FT + 3 * T + 0, ex(k) * r);
-                    if (ey(k)) atomicAdd(p.FT + 3 * T + 1, ey(k) * r);
-                    if (ez(k)) atomicAdd(p.FT + 3 * T + 2, ez(k) * r);
+                    if (ex(k)) atomicAdd(p.FT + 3 * el + 0, ex(k) * r);
+                    if (ey(k)) atomicAdd(p.FT + 3 * el + 1, ey(k) * r);
+                    if (ez(k)) atomicAdd(p.FT + 3 * el + 2, ez(k) * r);
                 }
             } else {
                 const float4 q = __ldg(p.dens + n + nb_off(d, ex(k), ey(k), ez(k)));

@@ -2,23 +2,25 @@
 //
 // All capsules are concatenated: global node and element indices, with the
 // owning capsule per element and per node.  The membrane phase of one step
-// (Sec. 3.1, Eqs. 6-9, 11) is ONE cooperative kernel, k_membrane, whose
-// blocks stride over all elements / nodes of all capsules and meet at grid
-// barriers between four phases:
-//   1. per element: two-step average of the exchanged momentum, Skalak strain
-//      forces (Eq. 6), volume gradient terms (Eq. 8), cotangent-Laplacian
-//      contributions of the bending energy; FP64 area and volume
-//   2. per node: mean-curvature vector and node area, gradients of the
-//      bending energy with respect to them; FP64 centroid, bounding box
-//   3. per element: back-propagation of the bending energy (Eq. 7)
-//   4. per node: gathers of all element contributions (node -> element CSR,
-//      no atomics), Hertz forces (Eq. 11), node update (Eq. 9); FP64 sums of
-//      force, torque and total force
-//   5. (frozen capsules only) rigid translation with the summed force.
-// The grid barrier spins a bounded number of times; on timeout it raises a
-// status flag and the kernel returns.  The cut links for the moved membrane
-// are rebuilt by k_cut_clear, k_cut_faces and k_cut_claim; k_cut_prep builds
-// the bounce records of the cut nodes at the start of each step.
+// (Sec. 3.1, Eqs. 6-9, 11) is five kernels, one thread per element or node of
+// all capsules:
+//   1. k_mem_elements  per element: Skalak strain forces (Eq. 6), volume
+//      gradient terms (Eq. 8), cotangent-Laplacian contributions of the
+//      bending energy; FP64 area and volume
+//   2. k_mem_nodes     per node: mean-curvature vector and node area, gradients
+//      of the bending energy with respect to them; FP64 centroid, bounding box
+//   3. k_mem_bending   per element: back-propagation of the bending energy (Eq. 7)
+//   4. k_mem_update    per node: gathers of all element contributions (node ->
+//      element CSR, no atomics) including the two-step average of the momentum
+//      exchanged with the fluid, Hertz forces (Eq. 11), node update (Eq. 9);
+//      FP64 sums of force, torque and total force
+//   5. k_mem_frozen    (frozen capsules only) rigid translation with the
+//      summed force.
+// Kernels 1-3 depend on the positions only, so they run on a second stream
+// while the lattice update of the same step runs; kernel 4 joins both.  The
+// cut links for the moved membrane are rebuilt by k_cut_clear and
+// k_cut_faces; k_cut_prep builds the bounce records of the cut links at the
+// start of each step.
 #include "cf_common.cuh"
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -112,39 +114,6 @@ __device__ __forceinline__ void acc_minmax(int *bbox, int ncaps, int cap, f3 x, 
     }
 }
 
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).
-// bar[0] counts arrivals, bar[1] is the generation.  Bounded spin: after
-// ~0.5 s without progress it raises ST_TIMEOUT and returns false.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned *status) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned *gen = bar + 1;
-        const unsigned g = *gen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(bar, 1u);
-        ok = 1;
-        if (arrived == gridDim.x - 1) {
-            bar[0] = 0u;
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            unsigned long long it = 0;
-            while (*gen == g) {
-                if (++it > (1ull << 24)) {
-                    atomicOr(status, ST_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
 // cot of the angle at o between o->p and o->q, with gradients w.r.t. p, q
 __device__ __forceinline__ float cot_grad(f3 o, f3 p, f3 q, f3 &dp, f3 &dq) {
     const f3 u = p - o, w = q - o;
@@ -173,11 +142,6 @@ __device__ __forceinline__ void face_pass(const MemParams &p, const CapDev &cp, 
     const f3 a{0.f, 0.f, 0.f}, b = pdiff(pb, pa), c = pdiff(pc, pa);
     const f3 ra = pdiff(pa, po);
     float *S = p.fscr + (long long)f * FS_N;
-    // two-step average of the momentum exchanged with this element
-    const f3 ft = ld3(p.FT, f), fp = ld3(p.FTprev, f);
-    st3(S + FS_FBAR, 0.5f * (ft + fp));
-    st3(p.FTprev + 3 * f, ft);
-    st3(p.FT + 3 * f, f3{0.f, 0.f, 0.f});
     const f3 u = b - a, w = c - a;
     const f3 nrm = cross(u, w);
     const float Af = 0.5f * sqrtf(dot(nrm, nrm));
@@ -293,14 +257,15 @@ __device__ __forceinline__ void node_forces(const MemParams &p, const CapDev &cp
             if (ent[j] < 0) continue;
             const int f = ent[j] / 3, sl = ent[j] - 3 * f;
             const float *S = p.fscr + (long long)f * FS_N;
-            Fc = Fc + ld3(S + FS_FBAR, 0);
+            // momentum exchanged with the element in this step and the previous one
+            Fc = Fc + ld3(p.FT, f) + ld3(p.FTprev, f);
             if (el) {
                 Fe = Fe + ld3(S + FS_SK, sl) + ld3(S + FS_BEND, sl);
                 dv = dv + ld3(S + FS_DV, sl);
             }
         }
     }
-    Fc = (1.f / 3.f) * Fc;
+    Fc = (0.5f / 3.f) * Fc;  // two-step average, a third to each node of the element
     if (el) Fe = Fe + pre * dv;
     // Hertz (Eq. 11): substrate plane
     if (p.wall) {
@@ -332,130 +297,122 @@ __device__ __forceinline__ void node_forces(const MemParams &p, const CapDev &cp
     Ft = Fc + Fe + Fi;
 }
 
-constexpr int MT = 256;  // threads per block of the membrane kernel
+constexpr int MT = 128;  // threads per block of the membrane kernels
 
-__global__ void __launch_bounds__(MT) k_membrane(const MemParams p) {
-    const int gt = blockIdx.x * MT + threadIdx.x, gs = gridDim.x * MT;
-    // 1. elements
-    for (int base = 0; base < p.nfaces; base += gs) {
-        const int f = base + gt;
-        const bool valid = f < p.nfaces;
-        const int cap = p.face_cap[valid ? f : 0];
-        float area = 0.f, vol = 0.f;
-        if (valid) face_pass(p, p.caps[cap], f, area, vol);
-        acc_add(p.acc, cap, A_AREA, area, valid);
-        acc_add(p.acc, cap, A_VOL, vol, valid);
+// 1. elements: Skalak, volume and first bending terms, FP64 area and volume
+__global__ void __launch_bounds__(MT) k_mem_elements(const MemParams p) {
+    const int f = blockIdx.x * MT + threadIdx.x;
+    const bool valid = f < p.nfaces;
+    const int cap = p.face_cap[valid ? f : 0];
+    float area = 0.f, vol = 0.f;
+    if (valid) face_pass(p, p.caps[cap], f, area, vol);
+    acc_add(p.acc, cap, A_AREA, area, valid);
+    acc_add(p.acc, cap, A_VOL, vol, valid);
+}
+
+// 2. nodes: bending gradients, centroid (relative to the capsule's first
+//    node), bounding box
+__global__ void __launch_bounds__(MT) k_mem_nodes(const MemParams p) {
+    const int v = blockIdx.x * MT + threadIdx.x;
+    const bool valid = v < p.nnodes;
+    const int vv = valid ? v : 0;
+    const int cap = p.node_cap[vv];
+    const CapDev cp = p.caps[cap];
+    if (valid && cp.mode == 0) node_bending_grad(p, cp, vv);
+    const pf x = ldp(p.Xh, p.Xl, vv);
+    const f3 r = pdiff(x, ldp(p.Xh, p.Xl, cp.v0));
+    if (valid && vv == cp.v0) {
+        double *A = p.acc + cap * A_NACC;
+        A[A_OX] = (double)x.h.x + x.l.x;
+        A[A_OY] = (double)x.h.y + x.l.y;
+        A[A_OZ] = (double)x.h.z + x.l.z;
     }
-    if (!grid_barrier(p.bar, p.status)) return;
-    // 2. nodes: bending gradients, centroid (relative to the capsule's first
-    //    node), bounding box
-    for (int base = 0; base < p.nnodes; base += gs) {
-        const int v = base + gt;
-        const bool valid = v < p.nnodes;
-        const int vv = valid ? v : 0;
-        const int cap = p.node_cap[vv];
-        const CapDev cp = p.caps[cap];
-        if (valid && cp.mode == 0) node_bending_grad(p, cp, vv);
+    acc_add(p.acc, cap, A_CX, r.x, valid);
+    acc_add(p.acc, cap, A_CY, r.y, valid);
+    acc_add(p.acc, cap, A_CZ, r.z, valid);
+    acc_minmax(p.bbox, p.ncaps, cap, x.h, valid);
+}
+
+// 3. elements: bending back-propagation
+__global__ void __launch_bounds__(MT) k_mem_bending(const MemParams p) {
+    const int f = blockIdx.x * MT + threadIdx.x;
+    if (f < p.nfaces && p.caps[p.face_cap[f]].mode == 0) face_bending(p, f);
+}
+
+// 4. nodes: coupling, elastic and Hertz forces, node update (Eq. 9), FP64
+//    sums of force, torque and total force
+__global__ void __launch_bounds__(MT) k_mem_update(const MemParams p) {
+    const int v = blockIdx.x * MT + threadIdx.x;
+    const bool valid = v < p.nnodes;
+    const int vv = valid ? v : 0;
+    const int cap = p.node_cap[vv];
+    const CapDev cp = p.caps[cap];
+    const double *A = p.acc + cap * A_NACC;
+    f3 Fc{0.f, 0.f, 0.f}, Ft{0.f, 0.f, 0.f}, r{0.f, 0.f, 0.f};
+    if (valid) {
         const pf x = ldp(p.Xh, p.Xl, vv);
-        const f3 r = pdiff(x, ldp(p.Xh, p.Xl, cp.v0));
-        if (valid && vv == cp.v0) {
-            double *A = p.acc + cap * A_NACC;
-            A[A_OX] = (double)x.h.x + x.l.x;
-            A[A_OY] = (double)x.h.y + x.l.y;
-            A[A_OZ] = (double)x.h.z + x.l.z;
+        // volume penalty prefactor -kV (V - V0) / V0 / 6 (Eq. 8); V is the
+        // FP64 sum of the element terms relative to the first node
+        const float pre = (float)(-(double)cp.kV * (A[A_VOL] - cp.V0) / cp.V0 / 6.0);
+        node_forces(p, cp, cap, vv, pre, x, Fc, Ft);
+        st3(p.Fcpl + 3 * vv, Fc);
+        if (cp.mode == 0) {
+            const f3 vel = (1.f / cp.mass) * Ft;
+            st3(p.V + 3 * vv, vel);
+            st_pos(p.Xnh, p.Xnl, vv, x, vel);
+        } else if (cp.mode == 2) {
+            st3(p.V + 3 * vv, f3{0.f, 0.f, 0.f});
+            st_pos(p.Xnh, p.Xnl, vv, x, f3{0.f, 0.f, 0.f});
         }
-        acc_add(p.acc, cap, A_CX, r.x, valid);
-        acc_add(p.acc, cap, A_CY, r.y, valid);
-        acc_add(p.acc, cap, A_CZ, r.z, valid);
-        acc_minmax(p.bbox, p.ncaps, cap, x.h, valid);
+        const float ic = 1.f / cp.nv;
+        const f3 cen{(float)A[A_CX] * ic, (float)A[A_CY] * ic, (float)A[A_CZ] * ic};
+        r = pdiff(x, ldp(p.Xh, p.Xl, cp.v0)) - cen;
     }
-    if (!grid_barrier(p.bar, p.status)) return;
-    // 3. elements: bending back-propagation
-    for (int f = gt; f < p.nfaces; f += gs)
-        if (p.caps[p.face_cap[f]].mode == 0) face_bending(p, f);
-    if (!grid_barrier(p.bar, p.status)) return;
-    // 4. nodes: forces, node update, sums
-    for (int base = 0; base < p.nnodes; base += gs) {
-        const int v = base + gt;
-        const bool valid = v < p.nnodes;
-        const int vv = valid ? v : 0;
-        const int cap = p.node_cap[vv];
-        const CapDev cp = p.caps[cap];
-        const double *A = p.acc + cap * A_NACC;
-        f3 Fc{0.f, 0.f, 0.f}, Ft{0.f, 0.f, 0.f}, r{0.f, 0.f, 0.f};
-        if (valid) {
-            const pf x = ldp(p.Xh, p.Xl, vv);
-            // volume penalty prefactor -kV (V - V0) / V0 / 6 (Eq. 8); V is the
-            // FP64 sum of the element terms relative to the first node
-            const float pre = (float)(-(double)cp.kV * (A[A_VOL] - cp.V0) / cp.V0 / 6.0);
-            node_forces(p, cp, cap, vv, pre, x, Fc, Ft);
-            st3(p.Fcpl + 3 * vv, Fc);
-            if (cp.mode == 0) {
-                const f3 vel = (1.f / cp.mass) * Ft;
-                st3(p.V + 3 * vv, vel);
-                st_pos(p.Xnh, p.Xnl, vv, x, vel);
-            } else if (cp.mode == 2) {
-                st3(p.V + 3 * vv, f3{0.f, 0.f, 0.f});
-                st_pos(p.Xnh, p.Xnl, vv, x, f3{0.f, 0.f, 0.f});
-            }
-            const float ic = 1.f / cp.nv;
-            const f3 cen{(float)A[A_CX] * ic, (float)A[A_CY] * ic, (float)A[A_CZ] * ic};
-            r = pdiff(x, ldp(p.Xh, p.Xl, cp.v0)) - cen;
-        }
-        const f3 tq = cross(r, Fc);
-        acc_add(p.acc, cap, A_FX, Fc.x, valid);
-        acc_add(p.acc, cap, A_FY, Fc.y, valid);
-        acc_add(p.acc, cap, A_FZ, Fc.z, valid);
-        acc_add(p.acc, cap, A_TX, tq.x, valid);
-        acc_add(p.acc, cap, A_TY, tq.y, valid);
-        acc_add(p.acc, cap, A_TZ, tq.z, valid);
-        acc_add(p.acc, cap, A_FTX, Ft.x, valid);
-        acc_add(p.acc, cap, A_FTY, Ft.y, valid);
-        acc_add(p.acc, cap, A_FTZ, Ft.z, valid);
-    }
-    if (!p.any_frozen) return;
-    if (!grid_barrier(p.bar, p.status)) return;
-    // 5. frozen shapes: rigid translation with the summed force
-    for (int v = gt; v < p.nnodes; v += gs) {
-        const int cap = p.node_cap[v];
-        const CapDev cp = p.caps[cap];
-        if (cp.mode != 1) continue;
-        const double *A = p.acc + cap * A_NACC;
-        const double sc = 1.0 / ((double)cp.mass * cp.nv);
-        const f3 vel{(float)(A[A_FTX] * sc), (float)(A[A_FTY] * sc), (float)(A[A_FTZ] * sc)};
-        st3(p.V + 3 * v, vel);
-        st_pos(p.Xnh, p.Xnl, v, ldp(p.Xh, p.Xl, v), vel);
-    }
+    const f3 tq = cross(r, Fc);
+    double *Aw = p.acc;
+    acc_add(Aw, cap, A_FX, Fc.x, valid);
+    acc_add(Aw, cap, A_FY, Fc.y, valid);
+    acc_add(Aw, cap, A_FZ, Fc.z, valid);
+    acc_add(Aw, cap, A_TX, tq.x, valid);
+    acc_add(Aw, cap, A_TY, tq.y, valid);
+    acc_add(Aw, cap, A_TZ, tq.z, valid);
+    acc_add(Aw, cap, A_FTX, Ft.x, valid);
+    acc_add(Aw, cap, A_FTY, Ft.y, valid);
+    acc_add(Aw, cap, A_FTZ, Ft.z, valid);
 }
 
-int membrane_grid(int nfaces, int nnodes) {
-    static int max_blocks = -1;
-    if (max_blocks < 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_membrane, MT, 0);
-        max_blocks = sms * (per_sm > 0 ? per_sm : 1);
-    }
-    const int want = (std::max(nfaces, nnodes) + MT - 1) / MT;
-    return std::max(1, std::min(want, std::min(max_blocks, 152)));
+// 5. frozen shapes: rigid translation with the summed force
+__global__ void __launch_bounds__(MT) k_mem_frozen(const MemParams p) {
+    const int v = blockIdx.x * MT + threadIdx.x;
+    if (v >= p.nnodes) return;
+    const int cap = p.node_cap[v];
+    const CapDev cp = p.caps[cap];
+    if (cp.mode != 1) return;
+    const double *A = p.acc + cap * A_NACC;
+    const double sc = 1.0 / ((double)cp.mass * cp.nv);
+    const f3 vel{(float)(A[A_FTX] * sc), (float)(A[A_FTY] * sc), (float)(A[A_FTZ] * sc)};
+    st3(p.V + 3 * v, vel);
+    st_pos(p.Xnh, p.Xnl, v, ldp(p.Xh, p.Xl, v), vel);
 }
 
-cudaError_t launch_membrane(const MemParams &p, bool any_frozen, cudaStream_t s, int *nl) {
-    (void)any_frozen;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(membrane_grid(p.nfaces, p.nnodes));
-    cfg.blockDim = dim3(MT);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_membrane, p);
+cudaError_t launch_membrane_forces(const MemParams &p, cudaStream_t s, int *nl) {
+    const unsigned gf = (unsigned)((p.nfaces + MT - 1) / MT), gv = (unsigned)((p.nnodes + MT - 1) / MT);
+    k_mem_elements<<<gf, MT, 0, s>>>(p);
+    k_mem_nodes<<<gv, MT, 0, s>>>(p);
+    k_mem_bending<<<gf, MT, 0, s>>>(p);
+    *nl += 3;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_membrane_update(const MemParams &p, bool any_frozen, cudaStream_t s, int *nl) {
+    const unsigned gv = (unsigned)((p.nnodes + MT - 1) / MT);
+    k_mem_update<<<gv, MT, 0, s>>>(p);
     *nl += 1;
-    return e;
+    if (any_frozen) {
+        k_mem_frozen<<<gv, MT, 0, s>>>(p);
+        *nl += 1;
+    }
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- cut links
@@ -478,14 +435,6 @@ constexpr float OEPS = 1e-4f;
 // fraction of its FP32 rate, and an inlined fallback may be if-converted.
 __device__ __noinline__ bool side_of_d(f3 A, f3 B, f3 C, f3 P) { return orient_d(A, B, C, P) >= 0.0; }
 
-// sign (sign(0) = +) of the orientation of P relative to the plane ABC, decided
-// in FP32 when clear and in FP64 otherwise
-__device__ __forceinline__ bool side_of(f3 A, f3 B, f3 C, f3 P) {
-    const float d = orient_f(A, B, C, P);
-    if (fabsf(d) > OEPS) return d >= 0.f;
-    return side_of_d(A, B, C, P);
-}
-
 // segment P->Q, already known to have its end points on opposite sides of the
 // plane, crosses triangle ABC (sign(0) = + convention on the edge tests)
 __device__ __noinline__ bool edges_pass_d(f3 P, f3 Qp, f3 A, f3 B, f3 C) {
@@ -499,93 +448,60 @@ __device__ __forceinline__ bool edges_pass(f3 P, f3 Qp, f3 A, f3 B, f3 C) {
     return edges_pass_d(P, Qp, A, B, C);
 }
 
+// Undo the previous cut structure: each entry of the previous list names one
+// marked link (node, direction); its mask word and crossed element are reset.
+// The exchange accumulator of the next step is zeroed here as well.
 __global__ void k_cut_clear(const CutParams p) {
-    const int prev = *p.prev_count;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < prev && i < p.capacity;
-         i += gridDim.x * blockDim.x) {
-        const int n = p.prev_list[i];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * p.nfaces; i += gridDim.x * blockDim.x)
+        p.FTnext[i] = 0.f;
+    const int prev = min(*p.prev_count, p.capacity);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < prev; i += gridDim.x * blockDim.x) {
+        const int2 e = p.prev_list[i];
+        const long long n = (long long)((unsigned)e.x >> 5);
         p.mask[n] = 0u;
-        p.owner[n] = 0u;
-        int2 *t2 = reinterpret_cast<int2 *>(p.tri + (long long)n * 18);  // 72 B rows, 8-byte aligned
-#pragma unroll
-        for (int k = 0; k < 9; ++k) t2[k] = make_int2(0x7fffffff, 0x7fffffff);
+        p.tri[n * 18 + (e.x & 31)] = 0x7fffffff;
     }
 }
 
-// Toggle the cut bit of link k at node (x, y, z), keep the smallest crossing
-// element and list the node (fire-and-forget atomics; the list append is
-// aggregated over the active lanes of the warp).
-__device__ __forceinline__ void mark(const CutParams &p, int x, int y, int z, int k, int T) {
-    const long long n = ((long long)wrapi(z, p.nz) * p.ny + wrapi(y, p.ny)) * p.nx + wrapi(x, p.nx);
-    atomicXor(p.mask + n, 1u << (k - 1));
-    atomicMin(p.tri + n * 18 + (k - 1), T);
-    const unsigned act = __activemask();
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(act) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(p.count, __popc(act));
-    base = __shfl_sync(act, base, leader);
-    const int idx = base + __popc(act & ((1u << lane) - 1u));
-    if (idx < p.capacity) p.list[idx] = (int)n;
-    else atomicOr(p.status, ST_OVERFLOW);
-}
-
-// Distinct cut nodes: the first list entry of a node whose links stayed cut
-// claims it and gets a bounce-record slot.
-__global__ void k_cut_claim(const CutParams p) {
-    const int cnt = min(*p.count, p.capacity);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
-        const int n = p.list[i];
-        if (p.mask[n] == 0u) continue;  // crossings cancelled out
-        if (atomicExch(p.owner + n, 1u) != 0u) continue;
-        const int u = atomicAdd(p.ucount, 1);
-        p.uniq[u] = n;
-        p.cutrec[n] = u;
-    }
-}
-
-// Edge tests and marks for the links of start node (x, y, z) whose end points
-// lie on opposite sides of the element's plane (rare, out of line).
-__device__ __noinline__ void crossing_links(const CutParams p, unsigned dirs, int x, int y, int z,
-                                            f3 A, f3 B, f3 C, int T) {
-    constexpr int POS[9] = {1, 3, 5, 7, 9, 11, 13, 15, 17};
-    for (; dirs; dirs &= dirs - 1u) {
-        const int k = POS[__ffs(dirs) - 1];
-        const int kx = ex(k), ky = ey(k), kz = ez(k);
-        if (p.wall && (wrapi(z, p.nz) == 0 || wrapi(z + kz, p.nz) == 0)) continue;
-        const f3 P{(float)x, (float)y, (float)z};
-        const f3 Qp{(float)(x + kx), (float)(y + ky), (float)(z + kz)};
-        if (edges_pass(P, Qp, A, B, C)) {
-            mark(p, x, y, z, k, T);
-            mark(p, x + kx, y + ky, z + kz, opp(k), T);
-        }
-    }
-}
-
-// One thread per (element, start node).  The links (x, x+e_k), k in the nine
-// positive directions, that can touch an element start within one unit of its
-// bounding box (the start box, at most 4 nodes per axis for elements shorter
-// than two lattice units).  Each thread takes one node of that box, decides
-// the plane side of the node and of its nine link partners (one orientation
-// each), and for links with end points on both sides whose crossing point
+// One warp per element.  The links (x, x+e_k), k in the nine positive
+// directions, that can touch an element start within one unit of its bounding
+// box (the start box, at most 4 nodes per axis for elements shorter than two
+// lattice units).  The lanes take the nodes of that box, decide the plane side
+// of each node and of its nine link partners (one orientation each), and keep
+// as candidates the links with end points on both sides whose crossing point
 // falls inside the element's box widened by 1e-3 (a conservative float
-// prefilter) runs the exact edge tests.
-constexpr int SB = 4, SB3 = SB * SB * SB;      // start box capacity
-constexpr int CUT_T = 256, CUT_EPB = CUT_T / SB3;  // threads / elements per block
+// prefilter).  The warp gathers its candidates in shared memory and runs the
+// exact edge tests on them 32 at a time, so that the tests and the marks run
+// on full warps.  A crossing toggles the cut bit of the link at both of its end
+// nodes, keeps the smallest crossing element there, and appends one list entry
+// per end node (one counter update per warp and pass).
+constexpr int SB = 4, SB3 = SB * SB * SB;  // start box capacity
+constexpr int CUT_WPB = 8;                 // elements (warps) per block
+constexpr int CAND_MAX = SB3 * 9;          // candidate links of one element, at most
 
-__device__ __forceinline__ bool plane_side(const f3 &nrm, const f3 &A, const f3 &B, const f3 &C,
-                                           f3 P) {
-    // orientation det[B-A; C-A; P-A] = ((B-A) x (C-A)) . (P-A); P - A is exact
-    // for nodes within a few units of A
-    const float d = dot(nrm, P - A);
-    return fabsf(d) > OEPS ? d >= 0.f : side_of_d(A, B, C, P);
+
+// periodic index, with the common in-range case first
+__device__ __forceinline__ int wrap_fast(int a, int n) { return (unsigned)a < (unsigned)n ? a : wrapi(a, n); }
+__device__ __forceinline__ long long node_at(const CutParams &p, int x, int y, int z) {
+    return ((long long)wrap_fast(z, p.nz) * p.ny + wrap_fast(y, p.ny)) * p.nx + wrap_fast(x, p.nx);
+}
+// box node s -> offsets (xi, yi, zi) in a box of nbx x nby x nbz nodes (s < 64):
+// (s + 1/2) / nbxy is at least 1/32 away from an integer, so the float
+// quotient truncates exactly
+__device__ __forceinline__ void box_of(int s, int nbx, int nbxy, float rnbx, float rnbxy, int &xi,
+                                       int &yi, int &zi) {
+    zi = (int)(((float)s + 0.5f) * rnbxy);
+    const int r = s - zi * nbxy;
+    yi = (int)(((float)r + 0.5f) * rnbx);
+    xi = r - yi * nbx;
 }
 
-__global__ void __launch_bounds__(CUT_T) k_cut_faces(const CutParams p) {
-    const int T = blockIdx.x * CUT_EPB + (int)(threadIdx.x / SB3);
-    if (T >= p.nfaces) return;
-    const int sidx = threadIdx.x & (SB3 - 1);
-    const int xi = sidx & (SB - 1), yi = (sidx >> 2) & (SB - 1), zi = sidx >> 4;
+__global__ void __launch_bounds__(32 * CUT_WPB) k_cut_faces(const CutParams p) {
+    __shared__ unsigned short cand[CUT_WPB][CAND_MAX];  // (box node << 4) | positive direction
+    const unsigned full = 0xffffffffu;
+    const int w = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+    const int T = blockIdx.x * CUT_WPB + w;
+    if (T >= p.nfaces) return;  // the whole warp
     // the decision is taken on the float (hi) positions
     const f3 A = ld3(p.X, p.faces[3 * T]), B = ld3(p.X, p.faces[3 * T + 1]),
              C = ld3(p.X, p.faces[3 * T + 2]);
@@ -596,45 +512,120 @@ __global__ void __launch_bounds__(CUT_T) k_cut_faces(const CutParams p) {
     const float fsx = floorf(emax.x + 1.f) - flx, fsy = floorf(emax.y + 1.f) - fly,
                 fsz = floorf(emax.z + 1.f) - flz;  // box span - 1
     if (fsx >= SB || fsy >= SB || fsz >= SB) {  // element longer than the box allows
-        if (sidx == 0) atomicOr(p.status, ST_OVERFLOW);
+        if (lane == 0) atomicOr(p.status, ST_OVERFLOW);
         return;
     }
-    if ((float)xi > fsx || (float)yi > fsy || (float)zi > fsz) return;
+    const int nbx = (int)fsx + 1, nbxy = nbx * ((int)fsy + 1), nb = nbxy * ((int)fsz + 1);
+    const float rnbx = 1.0f / (float)nbx, rnbxy = 1.0f / (float)nbxy;
+    const int x0 = (int)flx, y0 = (int)fly, z0 = (int)flz;
     const f3 nrm = cross(B - A, C - A);
-    const f3 P{flx + xi, fly + yi, flz + zi};
-    const bool sa = plane_side(nrm, A, B, C, P);
-    const float dP = dot(nrm, P - A);
     const float bpad = 1e-3f;
-    unsigned cross_dirs = 0u;
+    unsigned short *cw = cand[w];
+    int ncand = 0;  // warp-uniform
+    for (int s0 = 0; s0 < nb; s0 += 32) {
+        const int s = s0 + lane;
+        unsigned dirs = 0u;
+        if (s < nb) {
+            int xi, yi, zi;
+            box_of(s, nbx, nbxy, rnbx, rnbxy, xi, yi, zi);
+            const f3 P{(float)(x0 + xi), (float)(y0 + yi), (float)(z0 + zi)};
+            // orientation det[B-A; C-A; P-A] = ((B-A) x (C-A)) . (P-A); P - A is
+            // exact for nodes within a few units of A
+            const float dP = dot(nrm, P - A);
+            const bool sa = fabsf(dP) > OEPS ? dP >= 0.f : side_of_d(A, B, C, P);
 #pragma unroll
-    for (int d = 0; d < 9; ++d) {
-        constexpr int POS[9] = {1, 3, 5, 7, 9, 11, 13, 15, 17};
-        const int k = POS[d];
-        const f3 Qp{P.x + ex(k), P.y + ey(k), P.z + ez(k)};
-        if (plane_side(nrm, A, B, C, Qp) == sa) continue;
-        const float dn = ex(k) * nrm.x + ey(k) * nrm.y + ez(k) * nrm.z;  // n . e_k
-        const float tt = dn != 0.f ? -dP / dn : 0.5f;
-        const float cx = P.x + tt * ex(k), cy = P.y + tt * ey(k), cz = P.z + tt * ez(k);
-        const bool inside = cx >= emin.x - bpad && cx <= emax.x + bpad && cy >= emin.y - bpad &&
-                            cy <= emax.y + bpad && cz >= emin.z - bpad && cz <= emax.z + bpad;
-        cross_dirs |= (inside ? 1u : 0u) << d;
+            for (int d = 0; d < 9; ++d) {
+                const int k = 2 * d + 1;  // the positive member of each opposite pair
+                const float dn = ex(k) * nrm.x + ey(k) * nrm.y + ez(k) * nrm.z;  // n . e_k
+                // n . (P + e_k - A), within ~1e-6 of the direct product; the
+                // margin sends the close cases to the FP64 test
+                const float dQ = dP + dn;
+                const bool sq = fabsf(dQ) > OEPS
+                                    ? dQ >= 0.f
+                                    : side_of_d(A, B, C, f3{P.x + ex(k), P.y + ey(k), P.z + ez(k)});
+                if (sq == sa) continue;
+                // crossing point for the box prefilter (a fast quotient is
+                // ample against the 1e-3 pad)
+                const float tt = dn != 0.f ? __fdividef(-dP, dn) : 0.5f;
+                const float cx = P.x + tt * ex(k), cy = P.y + tt * ey(k), cz = P.z + tt * ez(k);
+                const bool inside = cx >= emin.x - bpad && cx <= emax.x + bpad &&
+                                    cy >= emin.y - bpad && cy <= emax.y + bpad &&
+                                    cz >= emin.z - bpad && cz <= emax.z + bpad;
+                dirs |= (inside ? 1u : 0u) << d;
+            }
+        }
+        // warp prefix sum of the candidate counts, then the lanes' slots
+        const int c = __popc(dirs);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(full, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int j = ncand + incl - c;
+        for (unsigned b = dirs; b; b &= b - 1u) cw[j++] = (unsigned short)((s << 4) | (__ffs(b) - 1));
+        ncand += __shfl_sync(full, incl, 31);
     }
-    if (cross_dirs)
-        crossing_links(p, cross_dirs, (int)P.x, (int)P.y, (int)P.z, A, B, C, T);
+    __syncwarp();
+    for (int j0 = 0; j0 < ncand; j0 += 32) {
+        const int j = j0 + lane;
+        bool hit = false;
+        long long n0 = 0, n1 = 0;
+        int k = 1;
+        if (j < ncand) {
+            const unsigned cv = cw[j];
+            const int s = (int)(cv >> 4);
+            k = 2 * (int)(cv & 15u) + 1;
+            int kx, ky, kz;
+            ek(k, kx, ky, kz);
+            int xi, yi, zi;
+            box_of(s, nbx, nbxy, rnbx, rnbxy, xi, yi, zi);
+            const int x = x0 + xi, y = y0 + yi, z = z0 + zi;
+            // links touching the substrate plane z = 0 are not fluid links
+            if (!(p.wall && (wrap_fast(z, p.nz) == 0 || wrap_fast(z + kz, p.nz) == 0))) {
+                const f3 P{(float)x, (float)y, (float)z};
+                const f3 Qp{(float)(x + kx), (float)(y + ky), (float)(z + kz)};
+                hit = edges_pass(P, Qp, A, B, C);
+            }
+            if (hit) {
+                n0 = node_at(p, x, y, z);
+                n1 = node_at(p, x + kx, y + ky, z + kz);
+            }
+        }
+        const unsigned hits = __ballot_sync(full, hit);
+        if (!hits) continue;
+        const int leader = __ffs(hits) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(p.count, 2 * __popc(hits));
+        base = __shfl_sync(full, base, leader);
+        if (hit) {
+            const int k2 = opp(k);
+            atomicXor(p.mask + n0, 1u << (k - 1));
+            atomicMin(p.tri + n0 * 18 + (k - 1), T);
+            atomicXor(p.mask + n1, 1u << (k2 - 1));
+            atomicMin(p.tri + n1 * 18 + (k2 - 1), T);
+            const int idx = base + 2 * __popc(hits & ((1u << lane) - 1u));
+            if (idx + 1 < p.capacity) {
+                p.list[idx] = make_int2(cut_code(n0, k), T);
+                p.list[idx + 1] = make_int2(cut_code(n1, k2), T);
+            } else {
+                atomicOr(p.status, ST_OVERFLOW);
+            }
+        }
+    }
 }
 
 cudaError_t launch_cuts(const CutParams &p, int prev_hint, cudaStream_t s, int *nl) {
     (void)prev_hint;
     k_cut_clear<<<152, 256, 0, s>>>(p);
-    k_cut_faces<<<(p.nfaces + CUT_EPB - 1) / CUT_EPB, CUT_T, 0, s>>>(p);
-    k_cut_claim<<<152, 256, 0, s>>>(p);
-    *nl += 3;
+    k_cut_faces<<<(p.nfaces + CUT_WPB - 1) / CUT_WPB, 32 * CUT_WPB, 0, s>>>(p);
+    *nl += 2;
     return cudaGetLastError();
 }
 
 // Post-collision population (component c, direction k) of node n, decoded
 // (16-bit storage holds the offset from w_k rho of the node).
-__device__ __forceinline__ float pop_at(const PrepParams &p, int c, int k, int n, float rho) {
+__device__ __forceinline__ float pop_at(const PrepParams &p, int c, int k, long long n, float rho) {
     const long long i = ((long long)c * Q + k) * p.N + n;
     if (p.prec == P_F16)
         return __half2float(static_cast<const __half *>(p.src)[i]) * F16_INV_SCALE + wgt(k) * rho;
@@ -643,49 +634,46 @@ __device__ __forceinline__ float pop_at(const PrepParams &p, int c, int k, int n
     return static_cast<const float *>(p.src)[i];
 }
 
-// Bounce records for the next streaming, one thread per cut node: the
-// population a cut node sent towards the membrane comes back with Ladd's term
-// -2 w_k rho (e_k . u_T)/c_s^2 (rho: the node's density = sum of its
-// post-collision populations; u_T: mean velocity of the crossed element's
+// Bounce records for the next streaming, one thread per entry of the cut-link
+// list: the population a cut node sent towards the membrane comes back with
+// Ladd's term -2 w_k rho (e_k . u_T)/c_s^2 (rho: the node's density = sum of
+// its post-collision populations; u_T: mean velocity of the crossed element's
 // nodes); the momentum each bounce exchanges with the element,
-// sum_c (2 f*_k - corr), is booked on it (Sec. 3.1, coupling paragraph).
+// sum_c (2 f*_k - corr), is booked on it (Sec. 3.1, coupling paragraph).  A link
+// crossed by several elements has one entry per element: the entry of the
+// smallest one (the element kept in tri) writes the record, and a link whose
+// crossings cancelled out (even count, cut bit clear) writes none.
 __global__ void k_cut_prep(const PrepParams p) {
-    const int cnt = *p.ucount;
-    const int N = (int)p.N;
-    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < cnt; u += gridDim.x * blockDim.x) {
-        const int n = p.uniq[u];
-        const uint32_t m = p.mask[n];
+    const int cnt = min(*p.count, p.capacity);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+        const int2 e = __ldg(p.list + i);
+        const long long n = (long long)((unsigned)e.x >> 5);
+        const int k1 = e.x & 31, k = k1 + 1, T = e.y;
+        if (!((__ldg(p.mask + n) >> k1) & 1u)) continue;
+        if (__ldg(p.tri + n * 18 + k1) != T) continue;
         // the node's density: the sum of its post-collision populations equals
         // the density of the step that produced them (BGK conserves mass)
         const float4 dn = __ldg(p.dens + n);
-        const float rwa = dn.x, rwb = dn.y;
-        float *R = p.rec + (long long)u * (2 * Q);
-#pragma unroll
-        for (int k = 1; k < Q; ++k) {  // unrolled: the cut links' loads overlap
-            if (!((m >> (k - 1)) & 1u)) continue;
-            const int kx = ex(k), ky = ey(k), kz = ez(k);
-            const int T = __ldg(p.tri + (long long)n * 18 + (k - 1));
-            const int a = __ldg(p.faces + 3 * T), b = __ldg(p.faces + 3 * T + 1),
-                      c = __ldg(p.faces + 3 * T + 2);
-            const float ux = (p.V[3 * a] + p.V[3 * b] + p.V[3 * c]) * (1.0f / 3.0f);
-            const float uy = (p.V[3 * a + 1] + p.V[3 * b + 1] + p.V[3 * c + 1]) * (1.0f / 3.0f);
-            const float uz = (p.V[3 * a + 2] + p.V[3 * b + 2] + p.V[3 * c + 2]) * (1.0f / 3.0f);
-            const float eu = kx * ux + ky * uy + kz * uz;
-            const float foa = pop_at(p, 0, k, n, rwa), fob = pop_at(p, 1, k, n, rwb);
-            const float w6 = 6.0f * wgt(k);
-            const float ca = w6 * rwa * eu, cb = w6 * rwb * eu;
-            R[opp(k)] = foa - ca;
-            R[Q + opp(k)] = fob - cb;
-            const float sx = (2.0f * foa - ca) + (2.0f * fob - cb);
-            if (kx) atomicAdd(p.FT + 3 * T + 0, kx * sx);
-            if (ky) atomicAdd(p.FT + 3 * T + 1, ky * sx);
-            if (kz) atomicAdd(p.FT + 3 * T + 2, kz * sx);
-        }
+        int kx, ky, kz;
+        ek(k, kx, ky, kz);
+        const int a = __ldg(p.faces + 3 * T), b = __ldg(p.faces + 3 * T + 1), c = __ldg(p.faces + 3 * T + 2);
+        const float ux = (p.V[3 * a] + p.V[3 * b] + p.V[3 * c]) * (1.0f / 3.0f);
+        const float uy = (p.V[3 * a + 1] + p.V[3 * b + 1] + p.V[3 * c + 1]) * (1.0f / 3.0f);
+        const float uz = (p.V[3 * a + 2] + p.V[3 * b + 2] + p.V[3 * c + 2]) * (1.0f / 3.0f);
+        const float eu = kx * ux + ky * uy + kz * uz;
+        const float foa = pop_at(p, 0, k, n, dn.x), fob = pop_at(p, 1, k, n, dn.y);
+        const float w6 = 6.0f * wgt(k);
+        const float ca = w6 * dn.x * eu, cb = w6 * dn.y * eu;
+        p.rec[n * 18 + (opp(k) - 1)] = make_float2(foa - ca, fob - cb);
+        const float sx = (2.0f * foa - ca) + (2.0f * fob - cb);
+        if (kx) atomicAdd(p.FT + 3 * T + 0, kx * sx);
+        if (ky) atomicAdd(p.FT + 3 * T + 1, ky * sx);
+        if (kz) atomicAdd(p.FT + 3 * T + 2, kz * sx);
     }
 }
 
 cudaError_t launch_prep(const PrepParams &p, cudaStream_t s, int *nl) {
-    k_cut_prep<<<152, 128, 0, s>>>(p);
+    k_cut_prep<<<2 * 152, 256, 0, s>>>(p);
     *nl += 1;
     return cudaGetLastError();
 }
