@@ -44,7 +44,8 @@ typedef enum {
     CF_ESTATE = 4,     /* call not valid in the current state                */
     CF_ENOTFOUND = 5,  /* unknown capsule id                                 */
     CF_EDIVERGED = 6,  /* non-finite density detected                        */
-    CF_EOVERFLOW = 7,  /* an internal list (cut-link nodes) exceeded capacity */
+    CF_EOVERFLOW = 7,  /* the cut-link list exceeded its capacity, or an element
+                          spans more than 16 lattice units */
     CF_ETIMEOUT = 8    /* a bounded device-side wait gave up (kernel returned early) */
 } cf_status;
 

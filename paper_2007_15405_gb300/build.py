@@ -16,6 +16,14 @@ LIB = os.path.join(HERE, "libcapfilm.so")
 SOURCES = ["lb_kernel.cu", "membrane_kernels.cu", "capfilm_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+# extra nvcc flags for tuning builds (e.g. "-DCF_COLLIDE_MINB=6"); a change of
+# them rebuilds the library
+EXTRA_ENV = "CAPFILM_NVCC_FLAGS"
+STAMP = os.path.join(BUILD, "flags.txt")
+
+
+def _extra_flags() -> list:
+    return os.environ.get(EXTRA_ENV, "").split()
 
 
 def nvcc() -> str:
@@ -31,7 +39,10 @@ def _stale() -> bool:
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     deps.append(os.path.join(os.path.dirname(HERE), "include", "capfilm.h"))
-    return any(os.path.getmtime(d) > t for d in deps)
+    if any(os.path.getmtime(d) > t for d in deps):
+        return True
+    old = open(STAMP).read() if os.path.exists(STAMP) else ""
+    return old != " ".join(_extra_flags())
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
@@ -39,7 +50,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nv = nvcc()
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + _extra_flags()
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
@@ -60,6 +71,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as fh:
+        fh.write(" ".join(_extra_flags()))
     return LIB
 
 

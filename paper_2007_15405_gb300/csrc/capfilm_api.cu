@@ -83,7 +83,8 @@ struct cf_ctx {
     unsigned *step_ctr = nullptr;
     int fpar = 0;
     float *out = nullptr;
-    float4 *dens[2] = {nullptr, nullptr};  // densities paired with each population buffer
+    float2 *rho[2] = {nullptr, nullptr};   // densities paired with each population buffer
+    float2 *psi = nullptr;                 // pseudopotentials of the current step
     uint32_t *mask = nullptr;
     int *tri = nullptr;
     float2 *rec = nullptr;        // [N][18] bounce records (A, B) by arriving direction
@@ -93,7 +94,6 @@ struct cf_ctx {
     int lpar = 0;
     int capacity = 0;
     unsigned *status = nullptr;
-    unsigned *bar = nullptr;     // grid barrier of the membrane kernel
     double *dscratch = nullptr;  // small FP64 scratch (mass)
     float *hscratch = nullptr;   // meniscus field [nx*ny]
     double *jit = nullptr;
@@ -154,8 +154,10 @@ cf_status check_status(cf_ctx *c) {
     if (st) {
         CF_CUDA(cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
         if (st & ST_NAN) return fail(CF_EDIVERGED, "non-finite density in the lattice");
-        if (st & ST_OVERFLOW) return fail(CF_EOVERFLOW, "cut-link node list or element box exceeded its capacity");
-        if (st & ST_TIMEOUT) return fail(CF_ETIMEOUT, "grid barrier of the membrane kernel timed out");
+        if (st & ST_OVERFLOW)
+            return fail(CF_EOVERFLOW, "cut-link list exceeded its capacity, or an element spans more "
+                                      "than 16 lattice units (or has a non-finite position)");
+        if (st & ST_TIMEOUT) return fail(CF_ETIMEOUT, "a bounded device-side wait timed out");
     }
     return CF_OK;
 }
@@ -174,7 +176,7 @@ LBParams lb_params(cf_ctx *c, bool with_out) {
     p.G = (float)c->d.G;
     p.src = c->f[c->fpar];
     p.dst = c->f[1 - c->fpar];
-    p.dens_src = c->dens[c->fpar];
+    p.rho_src = c->rho[c->fpar];
     p.src0 = c->f0[c->fpar];
     p.dst0 = c->f0[1 - c->fpar];
     p.step_ctr = c->step_ctr;
@@ -184,7 +186,8 @@ LBParams lb_params(cf_ctx *c, bool with_out) {
     p.V = c->V;
     p.FT = c->FT[c->ftpar];
     p.out = with_out ? c->out : nullptr;
-    p.dens = c->dens[1 - c->fpar];
+    p.rho = c->rho[1 - c->fpar];
+    p.psi = c->psi;
     p.rec = c->rec;
     p.status = c->status;
     return p;
@@ -276,7 +279,7 @@ cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev = null
         q.N = c->N;
         q.prec = c->d.precision;
         q.src = c->f[c->fpar];
-        q.dens = c->dens[c->fpar];
+        q.rho = c->rho[c->fpar];
         q.mask = c->mask;
         q.tri = c->tri;
         q.faces = c->faces;
@@ -536,8 +539,9 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     c->f0[0] = (float *)dalloc(c, sizeof(float) * 2 * N);
     c->f0[1] = (float *)dalloc(c, sizeof(float) * 2 * N);
     c->step_ctr = (unsigned *)dalloc(c, sizeof(unsigned));
-    c->dens[0] = (float4 *)dalloc(c, sizeof(float4) * N);
-    c->dens[1] = (float4 *)dalloc(c, sizeof(float4) * N);
+    c->rho[0] = (float2 *)dalloc(c, sizeof(float2) * N);
+    c->rho[1] = (float2 *)dalloc(c, sizeof(float2) * N);
+    c->psi = (float2 *)dalloc(c, sizeof(float2) * N);
     c->mask = (uint32_t *)dalloc(c, sizeof(uint32_t) * N);
     c->tri = (int *)dalloc(c, sizeof(int) * 18 * N);
     c->inside = (uint8_t *)dalloc(c, N);
@@ -545,7 +549,7 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     c->status = (unsigned *)dalloc(c, sizeof(unsigned));
     c->dscratch = (double *)dalloc(c, sizeof(double) * 8);
     c->hscratch = (float *)dalloc(c, sizeof(float) * desc->nx * desc->ny);
-    if (!c->f[0] || !c->f[1] || !c->f0[0] || !c->f0[1] || !c->step_ctr || !c->out || !c->dens[0] || !c->dens[1] || !c->mask || !c->tri || !c->inside ||
+    if (!c->f[0] || !c->f[1] || !c->f0[0] || !c->f0[1] || !c->step_ctr || !c->out || !c->rho[0] || !c->rho[1] || !c->psi || !c->mask || !c->tri || !c->inside ||
         !c->counts || !c->status || !c->dscratch || !c->hscratch) {
         cf_destroy(c);
         return fail(CF_ENOMEM, "device allocation failed");
@@ -555,8 +559,9 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     cudaMemsetAsync(c->f0[0], 0, sizeof(float) * 2 * N, c->stream);
     cudaMemsetAsync(c->f0[1], 0, sizeof(float) * 2 * N, c->stream);
     cudaMemsetAsync(c->step_ctr, 0, sizeof(unsigned), c->stream);
-    cudaMemsetAsync(c->dens[0], 0, sizeof(float4) * N, c->stream);
-    cudaMemsetAsync(c->dens[1], 0, sizeof(float4) * N, c->stream);
+    cudaMemsetAsync(c->rho[0], 0, sizeof(float2) * N, c->stream);
+    cudaMemsetAsync(c->rho[1], 0, sizeof(float2) * N, c->stream);
+    cudaMemsetAsync(c->psi, 0, sizeof(float2) * N, c->stream);
     cudaMemsetAsync(c->out, 0, sizeof(float) * 5 * N, c->stream);
     cudaMemsetAsync(c->mask, 0, sizeof(uint32_t) * N, c->stream);
     cudaMemsetAsync(c->tri, 0x7f, sizeof(int) * 18 * N, c->stream);
@@ -645,7 +650,7 @@ cf_status cf_set_film(cf_ctx *c, double h_top, double rmaj, double rmin, double 
         djit = c->jit;
     }
     if (c->nfaces) CF_CUDA(launch_inside(c->mask, c->inside, c->d.nx, c->d.ny, c->d.nz, c->stream));
-    CF_CUDA(launch_init_film(c->f[c->fpar], c->f0[c->fpar], c->d.precision, c->dens[c->fpar], N, c->d.nx, c->d.ny, c->d.nz, c->d.wall, (float)h_top,
+    CF_CUDA(launch_init_film(c->f[c->fpar], c->f0[c->fpar], c->d.precision, c->rho[c->fpar], N, c->d.nx, c->d.ny, c->d.nz, c->d.wall, (float)h_top,
                              (float)rmaj, (float)rmin, (float)rmix, djit, c->inside, c->stream));
     c->film_set = true;
     return sync_ok(c);
@@ -818,11 +823,11 @@ cf_status cf_populations(cf_ctx *c, float *f) {
     }
     // 16-bit offsets: f_i = g_i + w_i rho (rho of the node that wrote them)
     std::vector<uint16_t> g(38 * (size_t)N);
-    std::vector<float4> d((size_t)N);
+    std::vector<float2> d((size_t)N);
     std::vector<float> r0(2 * (size_t)N);
     CF_CUDA(cudaMemcpyAsync(g.data(), c->f[c->fpar], 2 * g.size(), cudaMemcpyDeviceToHost, c->stream));
     CF_CUDA(cudaMemcpyAsync(r0.data(), c->f0[c->fpar], sizeof(float) * r0.size(), cudaMemcpyDeviceToHost, c->stream));
-    CF_CUDA(cudaMemcpyAsync(d.data(), c->dens[c->fpar], sizeof(float4) * d.size(), cudaMemcpyDeviceToHost, c->stream));
+    CF_CUDA(cudaMemcpyAsync(d.data(), c->rho[c->fpar], sizeof(float2) * d.size(), cudaMemcpyDeviceToHost, c->stream));
     cf_status s = sync_ok(c);
     if (s != CF_OK) return s;
     const bool bf = c->d.precision == CF_BF16_SHIFT;
@@ -847,7 +852,7 @@ cf_status cf_populations(cf_ctx *c, float *f) {
 cf_status cf_total_mass(cf_ctx *c, double m[2]) {
     if (!c || !m) return fail(CF_EINVAL, "null argument");
     CF_CUDA(cudaMemsetAsync(c->dscratch, 0, sizeof(double) * 2, c->stream));
-    CF_CUDA(launch_mass(c->f[c->fpar], c->f0[c->fpar], c->d.precision, c->dens[c->fpar], c->N, c->dscratch,
+    CF_CUDA(launch_mass(c->f[c->fpar], c->f0[c->fpar], c->d.precision, c->rho[c->fpar], c->N, c->dscratch,
                         c->stream));
     CF_CUDA(cudaMemcpyAsync(m, c->dscratch, sizeof(double) * 2, cudaMemcpyDeviceToHost, c->stream));
     return sync_ok(c);

@@ -66,7 +66,7 @@ struct LBParams {
     float G;
     const void *__restrict__ src;    // post-collision populations of the last step
     void *__restrict__ dst;          // post-collision populations of this step
-    const float4 *__restrict__ dens_src;  // densities the src populations were encoded with
+    const float2 *__restrict__ rho_src;  // densities the src populations were encoded with
     const float *__restrict__ src0;  // 16-bit storage: rest populations in float [2][N]
     float *__restrict__ dst0;
     unsigned *__restrict__ step_ctr; // step counter (stochastic-rounding stream)
@@ -77,7 +77,9 @@ struct LBParams {
     float *__restrict__ FT;             // element momentum exchange accumulators [3*nfaces]
     const float2 *__restrict__ rec;     // [N][18] bounced (A, B) populations by arriving direction - 1
     float *__restrict__ out;            // optional [5][N]: rhoA, rhoB, ux, uy, uz
-    float4 *__restrict__ dens;          // [N] (rhoA, rhoB, psiA, psiB) of this step (written)
+    float2 *__restrict__ rho;           // [N] (rhoA, rhoB) of this step (written by the density pass)
+    float2 *__restrict__ psi;           // [N] (psiA, psiB) of this step (written by the density pass)
+    float4 *__restrict__ sdens;         // allocation-free step: (rho, psi) scratch of the library
     unsigned *__restrict__ status;      // device error flags
 };
 
@@ -93,9 +95,10 @@ struct CapDev {
 
 // Per-capsule FP64 accumulators (reset each step).
 // A_CX..A_CZ hold the node sum relative to the capsule's first node, whose
-// position is A_OX..A_OZ; A_VOL the enclosed volume.
+// position is A_OX..A_OZ; A_VOL the enclosed volume; A_PRE the volume-penalty
+// prefactor of Eq. 8 for this step.
 enum CapAcc { A_FX = 0, A_FY, A_FZ, A_TX, A_TY, A_TZ, A_AREA, A_VOL, A_CX, A_CY, A_CZ,
-              A_FTX, A_FTY, A_FTZ, A_OX, A_OY, A_OZ, A_NACC = 20 };
+              A_FTX, A_FTY, A_FTZ, A_OX, A_OY, A_OZ, A_PRE, A_NACC = 20 };
 
 struct MemParams {
     int nx, ny, nz, wall;
@@ -150,7 +153,7 @@ struct PrepParams {
     long long N;
     int prec;                // storage of the populations (cf_precision)
     const void *src;         // post-collision populations about to be streamed
-    const float4 *dens;      // (rhoA, rhoB, ...) of the step that produced them
+    const float2 *rho;       // (rhoA, rhoB) of the step that produced them
     const uint32_t *mask;
     const int *tri;
     const int *faces;
@@ -173,14 +176,14 @@ __host__ __device__ inline int wrapi(int a, int n) {
 namespace cf {
 void set_last_error(const char *msg);  // text returned by cf_last_error() on this thread
 cudaError_t launch_lb_step(const LBParams &p, int prec, cudaStream_t s);
-cudaError_t launch_init_film(void *f, float *f0, int prec, float4 *dens, long long N, int nx, int ny,
+cudaError_t launch_init_film(void *f, float *f0, int prec, float2 *rho, long long N, int nx, int ny,
                              int nz, int wall, float h_top, float rmaj, float rmin, float rmix,
                              const double *jit, const uint8_t *inside, cudaStream_t s);
 cudaError_t launch_inside(const uint32_t *mask, uint8_t *inside, int nx, int ny, int nz,
                           cudaStream_t s);
 cudaError_t launch_meniscus(const float *out, const uint8_t *inside, float *h, int nx, int ny,
                             int nz, int wall, cudaStream_t s);
-cudaError_t launch_mass(const void *f, const float *f0, int prec, const float4 *dens, long long N,
+cudaError_t launch_mass(const void *f, const float *f0, int prec, const float2 *rho, long long N,
                         double *m2, cudaStream_t s);
 // membrane kernels 1-3 (positions only) and 4-5 (after the lattice update)
 cudaError_t launch_membrane_forces(const MemParams &p, cudaStream_t s, int *nlaunch);

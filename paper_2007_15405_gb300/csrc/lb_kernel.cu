@@ -7,10 +7,10 @@
 // psi = 1 - exp(-rho), the Shan-Chen force (Eq. 10) with the interior/exterior
 // decoupling, and the BGK collision (Eqs. 4-5) with the velocity-shift forcing.
 //
-//   k_density   per node: gather the 38 streamed populations, write
-//               (rho_A, rho_B, psi_A, psi_B) as one float4
+//   k_density   per node: sum the 38 streamed populations, write
+//               (rho_A, rho_B) and (psi_A, psi_B) as two float2
 //   k_collide   per node: gather the 38 streamed populations again, read the
-//               pseudopotentials of the 18 neighbours (float4, L1/L2 resident),
+//               pseudopotentials of the 18 neighbours (float2, L1/L2 resident),
 //               Shan-Chen force, velocity shift, BGK, store
 //
 // Layout: populations f[c][i][z][y][x] (float), two buffers (src -> dst);
@@ -29,6 +29,10 @@
 namespace cf {
 
 constexpr int BX = 32, BY = 4;  // thread block: one row segment of 32 x 4 rows
+// resident blocks per SM the collide pass is compiled for (its register cap)
+#ifndef CF_COLLIDE_MINB
+#define CF_COLLIDE_MINB 5
+#endif
 
 __device__ __forceinline__ float psi_of(float r) { return -expm1f(-r); }
 
@@ -151,7 +155,7 @@ __device__ __forceinline__ uint32_t pull(const LBParams &p, const Deltas &d, flo
         fa[i] = Pop<T>::ld(sA + o);
         fb[i] = Pop<T>::ld(sB + o);
         if (Pop<T>::shifted) {  // decode with the density of the source node
-            const float4 r = __ldg(p.dens_src + d.n + src_node_off(d, i));
+            const float2 r = __ldg(p.rho_src + d.n + src_node_off(d, i));
             fa[i] += wgt(i) * r.x;
             fb[i] += wgt(i) * r.y;
         }
@@ -180,8 +184,14 @@ __device__ __forceinline__ bool node_of(const LBParams &p, int &x, int &y, int &
     return x < p.nx && y < p.ny;
 }
 
+// resident blocks per SM the density pass is compiled for: its 38 gathers are
+// issued back to back, so the register cap sets how many nodes are in flight
+#ifndef CF_DENSITY_MINB
+#define CF_DENSITY_MINB 8
+#endif
+
 template <typename T>
-__global__ void __launch_bounds__(BX *BY, 6) k_density(const LBParams p) {
+__global__ void __launch_bounds__(BX *BY, CF_DENSITY_MINB) k_density(const LBParams p) {
     if (Pop<T>::shifted && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 &&
         threadIdx.x == 0 && threadIdx.y == 0)
         atomicAdd(p.step_ctr, 1u);  // read by the collide pass that follows
@@ -194,7 +204,8 @@ __global__ void __launch_bounds__(BX *BY, 6) k_density(const LBParams p) {
         float ra = 0.f, rb = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) { ra += fa[i]; rb += fb[i]; }
-        p.dens[d.n] = make_float4(ra, rb, psi_of(ra), psi_of(rb));
+        p.rho[d.n] = make_float2(ra, rb);
+        p.psi[d.n] = make_float2(psi_of(ra), psi_of(rb));
     }
 }
 
@@ -204,15 +215,15 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
     float fa[Q], fb[Q];
     const uint32_t m = pull<T>(p, d, fa, fb);
     const int n = d.n;
-    const float4 me = __ldg(p.dens + n);
-    const float ra = me.x, rb = me.y, pa = me.z, pb = me.w;
+    const float2 mr = __ldg(p.rho + n), mp = __ldg(p.psi + n);
+    const float ra = mr.x, rb = mr.y, pa = mp.x, pb = mp.y;
     float sa[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};  // sum_k w_k psi'(x+e_k) e_k
     if (!m && !d.wlo && !d.whi) {
 #pragma unroll
         for (int k = 1; k < Q; ++k) {
-            const float4 q = __ldg(p.dens + n + nb_off(d, ex(k), ey(k), ez(k)));
-            sa[0] += wgt(k) * ex(k) * q.z; sa[1] += wgt(k) * ey(k) * q.z; sa[2] += wgt(k) * ez(k) * q.z;
-            sb[0] += wgt(k) * ex(k) * q.w; sb[1] += wgt(k) * ey(k) * q.w; sb[2] += wgt(k) * ez(k) * q.w;
+            const float2 q = __ldg(p.psi + n + nb_off(d, ex(k), ey(k), ez(k)));
+            sa[0] += wgt(k) * ex(k) * q.x; sa[1] += wgt(k) * ey(k) * q.x; sa[2] += wgt(k) * ez(k) * q.x;
+            sb[0] += wgt(k) * ex(k) * q.y; sb[1] += wgt(k) * ey(k) * q.y; sb[2] += wgt(k) * ez(k) * q.y;
         }
     } else {
         // partner densities across a cut or substrate link: mean over this
@@ -223,7 +234,7 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
             const bool solid = (ez(k) == 1 && d.whi) || (ez(k) == -1 && d.wlo);
             const bool cut = (m >> (k - 1)) & 1u;
             if (!solid && !cut) {
-                const float4 q = __ldg(p.dens + n + nb_off(d, ex(k), ey(k), ez(k)));
+                const float2 q = __ldg(p.rho + n + nb_off(d, ex(k), ey(k), ez(k)));
                 ia += q.x; ib += q.y; cnt += 1.f;
             }
         }
@@ -244,8 +255,8 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
                     if (ez(k)) atomicAdd(p.FT + 3 * el + 2, ez(k) * r);
                 }
             } else {
-                const float4 q = __ldg(p.dens + n + nb_off(d, ex(k), ey(k), ez(k)));
-                qa = q.z; qb = q.w;
+                const float2 q = __ldg(p.psi + n + nb_off(d, ex(k), ey(k), ez(k)));
+                qa = q.x; qb = q.y;
             }
             sa[0] += wgt(k) * ex(k) * qa; sa[1] += wgt(k) * ey(k) * qa; sa[2] += wgt(k) * ez(k) * qa;
             sb[0] += wgt(k) * ex(k) * qb; sb[1] += wgt(k) * ey(k) * qb; sb[2] += wgt(k) * ez(k) * qb;
@@ -262,13 +273,14 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
         jb[0] += ex(i) * db; jb[1] += ey(i) * db; jb[2] += ez(i) * db;
     }
     // velocity shift: common velocity weighted by 1/tau, u^{c,eq} = u' + tau^c F^c / rho^c
-    const float den = ra * p.itau[0] + rb * p.itau[1];
+    const float iden = 1.0f / (ra * p.itau[0] + rb * p.itau[1]);
+    const float sfa = p.tau[0] / ra, sfb = p.tau[1] / rb;
     float ua[3], ub[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float up = (ja[a] * p.itau[0] + jb[a] * p.itau[1]) / den;
-        ua[a] = up + p.tau[0] * FA[a] / ra;
-        ub[a] = up + p.tau[1] * FB[a] / rb;
+        const float up = (ja[a] * p.itau[0] + jb[a] * p.itau[1]) * iden;
+        ua[a] = up + sfa * FA[a];
+        ub[a] = up + sfb * FB[a];
     }
     if (p.out) {
         const float rt = ra + rb;
@@ -336,7 +348,7 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BX *BY, Pop<T>::shifted ? 5 : 6) k_collide(const LBParams p) {
+__global__ void __launch_bounds__(BX *BY, CF_COLLIDE_MINB) k_collide(const LBParams p) {
     int x, y, z;
     if (!node_of(p, x, y, z)) return;
     for (; z < p.zhi; z += gridDim.z) collide_node<T>(p, deltas(p, x, y, z));
@@ -361,7 +373,7 @@ cudaError_t launch_lb_step(const LBParams &p, int prec, cudaStream_t s) {
 
 // ------------------------------------------------------------ film set-up
 template <typename T>
-__global__ void k_init_film(T *f, float *f0, float4 *dens, long long N, int nx, int ny, int nz,
+__global__ void k_init_film(T *f, float *f0, float2 *rho, long long N, int nx, int ny, int nz,
                            int wall, float h_top, float rmaj, float rmin, float rmix,
                            const double *jit, const uint8_t *inside) {
     const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -402,21 +414,21 @@ __global__ void k_init_film(T *f, float *f0, float4 *dens, long long N, int nx, 
             rb += fb;
         }
     }
-    dens[n] = make_float4(ra, rb, psi_of(ra), psi_of(rb));  // density of the initial state
+    rho[n] = make_float2(ra, rb);  // density of the initial state
 }
 
-cudaError_t launch_init_film(void *f, float *f0, int prec, float4 *dens, long long N, int nx, int ny,
+cudaError_t launch_init_film(void *f, float *f0, int prec, float2 *rho, long long N, int nx, int ny,
                              int nz, int wall, float h_top, float rmaj, float rmin, float rmix,
                              const double *jit, const uint8_t *inside, cudaStream_t s) {
     const unsigned g = (unsigned)((N + 255) / 256);
     if (prec == P_F16)
-        k_init_film<<<g, 256, 0, s>>>(static_cast<__half *>(f), f0, dens, N, nx, ny, nz, wall, h_top,
+        k_init_film<<<g, 256, 0, s>>>(static_cast<__half *>(f), f0, rho, N, nx, ny, nz, wall, h_top,
                                       rmaj, rmin, rmix, jit, inside);
     else if (prec == P_BF16)
-        k_init_film<<<g, 256, 0, s>>>(static_cast<__nv_bfloat16 *>(f), f0, dens, N, nx, ny, nz, wall,
+        k_init_film<<<g, 256, 0, s>>>(static_cast<__nv_bfloat16 *>(f), f0, rho, N, nx, ny, nz, wall,
                                       h_top, rmaj, rmin, rmix, jit, inside);
     else
-        k_init_film<<<g, 256, 0, s>>>(static_cast<float *>(f), f0, dens, N, nx, ny, nz, wall, h_top,
+        k_init_film<<<g, 256, 0, s>>>(static_cast<float *>(f), f0, rho, N, nx, ny, nz, wall, h_top,
                                       rmaj, rmin, rmix, jit, inside);
     return cudaGetLastError();
 }
@@ -465,12 +477,12 @@ cudaError_t launch_meniscus(const float *out, const uint8_t *inside, float *h, i
 
 // FP64 mass of each component (decoded populations)
 template <typename T>
-__global__ void k_mass(const T *f, const float *f0, const float4 *dens, long long N, double *m2) {
+__global__ void k_mass(const T *f, const float *f0, const float2 *rho, long long N, double *m2) {
     double s[2] = {0.0, 0.0};
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
         if (Pop<T>::shifted) {
-            const float4 r = dens[n];
+            const float2 r = rho[n];
             s[0] += f0[n];
             s[1] += f0[N + n];
 #pragma unroll
@@ -493,12 +505,12 @@ __global__ void k_mass(const T *f, const float *f0, const float4 *dens, long lon
     }
 }
 
-cudaError_t launch_mass(const void *f, const float *f0, int prec, const float4 *dens, long long N,
+cudaError_t launch_mass(const void *f, const float *f0, int prec, const float2 *rho, long long N,
                         double *m2, cudaStream_t s) {
-    if (prec == P_F16) k_mass<<<304, 256, 0, s>>>(static_cast<const __half *>(f), f0, dens, N, m2);
+    if (prec == P_F16) k_mass<<<304, 256, 0, s>>>(static_cast<const __half *>(f), f0, rho, N, m2);
     else if (prec == P_BF16)
-        k_mass<<<304, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(f), f0, dens, N, m2);
-    else k_mass<<<304, 256, 0, s>>>(static_cast<const float *>(f), f0, dens, N, m2);
+        k_mass<<<304, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(f), f0, rho, N, m2);
+    else k_mass<<<304, 256, 0, s>>>(static_cast<const float *>(f), f0, rho, N, m2);
     return cudaGetLastError();
 }
 
@@ -535,7 +547,7 @@ __global__ void __launch_bounds__(BX *BY) k_density_static(const LBParams p) {
             ra += __ldg(sA + o);
             rb += __ldg(sB + o);
         }
-        p.dens[d.n] = make_float4(ra, rb, psi_of(ra), psi_of(rb));
+        p.sdens[d.n] = make_float4(ra, rb, psi_of(ra), psi_of(rb));
     }
 }
 
@@ -554,13 +566,13 @@ __device__ __forceinline__ void collide_node_static(const LBParams &p, const Del
             fb[i] = __ldg(sB + o);
         }
     }
-    const float4 me = p.dens[n];
+    const float4 me = p.sdens[n];
     const float ra = me.x, rb = me.y, pa = me.z, pb = me.w;
     float sa[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};
     if (!d.wlo && !d.whi) {
 #pragma unroll
         for (int k = 1; k < Q; ++k) {
-            const float4 q = p.dens[n + nb_off(d, ex(k), ey(k), ez(k))];
+            const float4 q = p.sdens[n + nb_off(d, ex(k), ey(k), ez(k))];
             sa[0] += wgt(k) * ex(k) * q.z; sa[1] += wgt(k) * ey(k) * q.z; sa[2] += wgt(k) * ez(k) * q.z;
             sb[0] += wgt(k) * ex(k) * q.w; sb[1] += wgt(k) * ey(k) * q.w; sb[2] += wgt(k) * ez(k) * q.w;
         }
@@ -570,7 +582,7 @@ __device__ __forceinline__ void collide_node_static(const LBParams &p, const Del
         for (int k = 1; k < Q; ++k) {
             const bool solid = (ez(k) == 1 && d.whi) || (ez(k) == -1 && d.wlo);
             if (!solid) {
-                const float4 q = p.dens[n + nb_off(d, ex(k), ey(k), ez(k))];
+                const float4 q = p.sdens[n + nb_off(d, ex(k), ey(k), ez(k))];
                 ia += q.x; ib += q.y; cnt += 1.f;
             }
         }
@@ -581,7 +593,7 @@ __device__ __forceinline__ void collide_node_static(const LBParams &p, const Del
             float qa, qb;
             if (solid) { qa = qa_eff; qb = qb_eff; }
             else {
-                const float4 q = p.dens[n + nb_off(d, ex(k), ey(k), ez(k))];
+                const float4 q = p.sdens[n + nb_off(d, ex(k), ey(k), ez(k))];
                 qa = q.z; qb = q.w;
             }
             sa[0] += wgt(k) * ex(k) * qa; sa[1] += wgt(k) * ey(k) * qa; sa[2] += wgt(k) * ez(k) * qa;
@@ -685,7 +697,7 @@ extern "C" cf_status cf_lattice_step_static(const float *src, float *dst, int nx
     p.G = (float)G;
     p.src = src;
     p.dst = dst;
-    p.dens = dens;
+    p.sdens = dens;
     const cudaStream_t s = (cudaStream_t)stream;
     dim3 grid((nx + BX - 1) / BX, (ny + BY - 1) / BY, p.zhi - p.zlo), block(BX, BY);
     k_density_static<<<grid, block, 0, s>>>(p);

@@ -297,7 +297,10 @@ __device__ __forceinline__ void node_forces(const MemParams &p, const CapDev &cp
     Ft = Fc + Fe + Fi;
 }
 
-constexpr int MT = 128;  // threads per block of the membrane kernels
+// Threads per block of the membrane kernels: small blocks spread the few
+// thousand latency-bound threads over all SMs.
+constexpr int MT = 64;   // element kernels
+constexpr int MV = 32;   // node kernels
 
 // 1. elements: Skalak, volume and first bending terms, FP64 area and volume
 __global__ void __launch_bounds__(MT) k_mem_elements(const MemParams p) {
@@ -312,8 +315,8 @@ __global__ void __launch_bounds__(MT) k_mem_elements(const MemParams p) {
 
 // 2. nodes: bending gradients, centroid (relative to the capsule's first
 //    node), bounding box
-__global__ void __launch_bounds__(MT) k_mem_nodes(const MemParams p) {
-    const int v = blockIdx.x * MT + threadIdx.x;
+__global__ void __launch_bounds__(MV) k_mem_nodes(const MemParams p) {
+    const int v = blockIdx.x * MV + threadIdx.x;
     const bool valid = v < p.nnodes;
     const int vv = valid ? v : 0;
     const int cap = p.node_cap[vv];
@@ -326,6 +329,10 @@ __global__ void __launch_bounds__(MT) k_mem_nodes(const MemParams p) {
         A[A_OX] = (double)x.h.x + x.l.x;
         A[A_OY] = (double)x.h.y + x.l.y;
         A[A_OZ] = (double)x.h.z + x.l.z;
+        // volume penalty prefactor -kV (V - V0) / V0 / 6 (Eq. 8); V is the
+        // FP64 sum of the element terms (relative to the first node), complete
+        // since the element kernel ran
+        A[A_PRE] = -(double)cp.kV * (A[A_VOL] - cp.V0) / cp.V0 / 6.0;
     }
     acc_add(p.acc, cap, A_CX, r.x, valid);
     acc_add(p.acc, cap, A_CY, r.y, valid);
@@ -341,8 +348,8 @@ __global__ void __launch_bounds__(MT) k_mem_bending(const MemParams p) {
 
 // 4. nodes: coupling, elastic and Hertz forces, node update (Eq. 9), FP64
 //    sums of force, torque and total force
-__global__ void __launch_bounds__(MT) k_mem_update(const MemParams p) {
-    const int v = blockIdx.x * MT + threadIdx.x;
+__global__ void __launch_bounds__(MV) k_mem_update(const MemParams p) {
+    const int v = blockIdx.x * MV + threadIdx.x;
     const bool valid = v < p.nnodes;
     const int vv = valid ? v : 0;
     const int cap = p.node_cap[vv];
@@ -351,9 +358,7 @@ __global__ void __launch_bounds__(MT) k_mem_update(const MemParams p) {
     f3 Fc{0.f, 0.f, 0.f}, Ft{0.f, 0.f, 0.f}, r{0.f, 0.f, 0.f};
     if (valid) {
         const pf x = ldp(p.Xh, p.Xl, vv);
-        // volume penalty prefactor -kV (V - V0) / V0 / 6 (Eq. 8); V is the
-        // FP64 sum of the element terms relative to the first node
-        const float pre = (float)(-(double)cp.kV * (A[A_VOL] - cp.V0) / cp.V0 / 6.0);
+        const float pre = (float)A[A_PRE];
         node_forces(p, cp, cap, vv, pre, x, Fc, Ft);
         st3(p.Fcpl + 3 * vv, Fc);
         if (cp.mode == 0) {
@@ -382,8 +387,8 @@ __global__ void __launch_bounds__(MT) k_mem_update(const MemParams p) {
 }
 
 // 5. frozen shapes: rigid translation with the summed force
-__global__ void __launch_bounds__(MT) k_mem_frozen(const MemParams p) {
-    const int v = blockIdx.x * MT + threadIdx.x;
+__global__ void __launch_bounds__(MV) k_mem_frozen(const MemParams p) {
+    const int v = blockIdx.x * MV + threadIdx.x;
     if (v >= p.nnodes) return;
     const int cap = p.node_cap[v];
     const CapDev cp = p.caps[cap];
@@ -396,20 +401,20 @@ __global__ void __launch_bounds__(MT) k_mem_frozen(const MemParams p) {
 }
 
 cudaError_t launch_membrane_forces(const MemParams &p, cudaStream_t s, int *nl) {
-    const unsigned gf = (unsigned)((p.nfaces + MT - 1) / MT), gv = (unsigned)((p.nnodes + MT - 1) / MT);
+    const unsigned gf = (unsigned)((p.nfaces + MT - 1) / MT), gv = (unsigned)((p.nnodes + MV - 1) / MV);
     k_mem_elements<<<gf, MT, 0, s>>>(p);
-    k_mem_nodes<<<gv, MT, 0, s>>>(p);
+    k_mem_nodes<<<gv, MV, 0, s>>>(p);
     k_mem_bending<<<gf, MT, 0, s>>>(p);
     *nl += 3;
     return cudaGetLastError();
 }
 
 cudaError_t launch_membrane_update(const MemParams &p, bool any_frozen, cudaStream_t s, int *nl) {
-    const unsigned gv = (unsigned)((p.nnodes + MT - 1) / MT);
-    k_mem_update<<<gv, MT, 0, s>>>(p);
+    const unsigned gv = (unsigned)((p.nnodes + MV - 1) / MV);
+    k_mem_update<<<gv, MV, 0, s>>>(p);
     *nl += 1;
     if (any_frozen) {
-        k_mem_frozen<<<gv, MT, 0, s>>>(p);
+        k_mem_frozen<<<gv, MV, 0, s>>>(p);
         *nl += 1;
     }
     return cudaGetLastError();
@@ -463,129 +468,113 @@ __global__ void k_cut_clear(const CutParams p) {
     }
 }
 
-// One warp per element.  The links (x, x+e_k), k in the nine positive
-// directions, that can touch an element start within one unit of its bounding
-// box (the start box, at most 4 nodes per axis for elements shorter than two
-// lattice units).  The lanes take the nodes of that box, decide the plane side
-// of each node and of its nine link partners (one orientation each), and keep
-// as candidates the links with end points on both sides whose crossing point
-// falls inside the element's box widened by 1e-3 (a conservative float
-// prefilter).  The warp gathers its candidates in shared memory and runs the
-// exact edge tests on them 32 at a time, so that the tests and the marks run
-// on full warps.  A crossing toggles the cut bit of the link at both of its end
-// nodes, keeps the smallest crossing element there, and appends one list entry
-// per end node (one counter update per warp and pass).
-constexpr int SB = 4, SB3 = SB * SB * SB;  // start box capacity
-constexpr int CUT_WPB = 8;                 // elements (warps) per block
-constexpr int CAND_MAX = SB3 * 9;          // candidate links of one element, at most
-
+// One warp per element.  A link (P, P+e_k), k in the nine positive directions,
+// can cross the element only where its crossing point lies in the element's
+// bounding box: along an axis a with e_a = 0 the start node lies in the box,
+// along an axis with e_a = +1 (-1) in the box widened by one unit below
+// (above).  Lanes 0-8 take one direction each and compute that range of
+// start nodes (widened by 1e-3, so the candidates cover every crossing the
+// exact tests can find); a warp prefix sum then hands every lane one
+// (direction, start node) candidate, 32 per pass.  Each candidate gets the
+// exact tests: plane sides of both end points (orientation against the
+// element, sign(0) = +, FP32 with a margin and FP64 otherwise) and, where they
+// differ, the three edge orientations.  A crossing toggles the cut bit of the
+// link at both of its end nodes, keeps the smallest crossing element there,
+// and appends one list entry per end node (one counter update per warp and
+// pass).
+constexpr int CUT_WPB = 8;  // elements (warps) per block
 
 // periodic index, with the common in-range case first
 __device__ __forceinline__ int wrap_fast(int a, int n) { return (unsigned)a < (unsigned)n ? a : wrapi(a, n); }
 __device__ __forceinline__ long long node_at(const CutParams &p, int x, int y, int z) {
     return ((long long)wrap_fast(z, p.nz) * p.ny + wrap_fast(y, p.ny)) * p.nx + wrap_fast(x, p.nx);
 }
-// box node s -> offsets (xi, yi, zi) in a box of nbx x nby x nbz nodes (s < 64):
-// (s + 1/2) / nbxy is at least 1/32 away from an integer, so the float
-// quotient truncates exactly
-__device__ __forceinline__ void box_of(int s, int nbx, int nbxy, float rnbx, float rnbxy, int &xi,
-                                       int &yi, int &zi) {
-    zi = (int)(((float)s + 0.5f) * rnbxy);
-    const int r = s - zi * nbxy;
-    yi = (int)(((float)r + 0.5f) * rnbx);
-    xi = r - yi * nbx;
+
+// plane side (sign(0) = +) of P against the element ABC with normal nrm =
+// (B-A) x (C-A): the orientation det[B-A; C-A; P-A] = nrm . (P-A), in float
+// within ~1e-6 of its exact value for nodes within a few units of A, so the
+// margin sends every close case to the FP64 test
+__device__ __forceinline__ bool plane_side(const f3 &nrm, const f3 &A, const f3 &B, const f3 &C,
+                                           const f3 &P) {
+    const float d = dot(nrm, P - A);
+    return fabsf(d) > OEPS ? d >= 0.f : side_of_d(A, B, C, P);
 }
 
 __global__ void __launch_bounds__(32 * CUT_WPB) k_cut_faces(const CutParams p) {
-    __shared__ unsigned short cand[CUT_WPB][CAND_MAX];  // (box node << 4) | positive direction
     const unsigned full = 0xffffffffu;
-    const int w = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
-    const int T = blockIdx.x * CUT_WPB + w;
+    const int lane = (int)(threadIdx.x & 31);
+    const int T = blockIdx.x * CUT_WPB + (int)(threadIdx.x >> 5);
     if (T >= p.nfaces) return;  // the whole warp
     // the decision is taken on the float (hi) positions
     const f3 A = ld3(p.X, p.faces[3 * T]), B = ld3(p.X, p.faces[3 * T + 1]),
              C = ld3(p.X, p.faces[3 * T + 2]);
-    const f3 emin{fminf(A.x, fminf(B.x, C.x)), fminf(A.y, fminf(B.y, C.y)), fminf(A.z, fminf(B.z, C.z))};
-    const f3 emax{fmaxf(A.x, fmaxf(B.x, C.x)), fmaxf(A.y, fmaxf(B.y, C.y)), fmaxf(A.z, fmaxf(B.z, C.z))};
-    // start box: [ceil(min-1), floor(max+1)] per axis
-    const float flx = ceilf(emin.x - 1.f), fly = ceilf(emin.y - 1.f), flz = ceilf(emin.z - 1.f);
-    const float fsx = floorf(emax.x + 1.f) - flx, fsy = floorf(emax.y + 1.f) - fly,
-                fsz = floorf(emax.z + 1.f) - flz;  // box span - 1
-    if (fsx >= SB || fsy >= SB || fsz >= SB) {  // element longer than the box allows
+    const float emin[3] = {fminf(A.x, fminf(B.x, C.x)), fminf(A.y, fminf(B.y, C.y)),
+                           fminf(A.z, fminf(B.z, C.z))};
+    const float emax[3] = {fmaxf(A.x, fmaxf(B.x, C.x)), fmaxf(A.y, fmaxf(B.y, C.y)),
+                           fmaxf(A.z, fmaxf(B.z, C.z))};
+    // an element spanning more than 16 units (or with a non-finite position)
+    // is an error, not a workload: it would hand the warp unbounded candidates
+    if (!(emax[0] - emin[0] <= 16.f && emax[1] - emin[1] <= 16.f && emax[2] - emin[2] <= 16.f)) {
         if (lane == 0) atomicOr(p.status, ST_OVERFLOW);
         return;
     }
-    const int nbx = (int)fsx + 1, nbxy = nbx * ((int)fsy + 1), nb = nbxy * ((int)fsz + 1);
-    const float rnbx = 1.0f / (float)nbx, rnbxy = 1.0f / (float)nbxy;
-    const int x0 = (int)flx, y0 = (int)fly, z0 = (int)flz;
-    const f3 nrm = cross(B - A, C - A);
-    const float bpad = 1e-3f;
-    unsigned short *cw = cand[w];
-    int ncand = 0;  // warp-uniform
-    for (int s0 = 0; s0 < nb; s0 += 32) {
-        const int s = s0 + lane;
-        unsigned dirs = 0u;
-        if (s < nb) {
-            int xi, yi, zi;
-            box_of(s, nbx, nbxy, rnbx, rnbxy, xi, yi, zi);
-            const f3 P{(float)(x0 + xi), (float)(y0 + yi), (float)(z0 + zi)};
-            // orientation det[B-A; C-A; P-A] = ((B-A) x (C-A)) . (P-A); P - A is
-            // exact for nodes within a few units of A
-            const float dP = dot(nrm, P - A);
-            const bool sa = fabsf(dP) > OEPS ? dP >= 0.f : side_of_d(A, B, C, P);
+    // lane d < 9: start-node range of direction k = 2d + 1
+    const float pad = 1e-3f;
+    int rlo[3] = {0, 0, 0}, rn[3] = {0, 0, 0};
+    int cnt = 0;
+    if (lane < 9) {
+        int e[3];
+        ek(2 * lane + 1, e[0], e[1], e[2]);
 #pragma unroll
-            for (int d = 0; d < 9; ++d) {
-                const int k = 2 * d + 1;  // the positive member of each opposite pair
-                const float dn = ex(k) * nrm.x + ey(k) * nrm.y + ez(k) * nrm.z;  // n . e_k
-                // n . (P + e_k - A), within ~1e-6 of the direct product; the
-                // margin sends the close cases to the FP64 test
-                const float dQ = dP + dn;
-                const bool sq = fabsf(dQ) > OEPS
-                                    ? dQ >= 0.f
-                                    : side_of_d(A, B, C, f3{P.x + ex(k), P.y + ey(k), P.z + ez(k)});
-                if (sq == sa) continue;
-                // crossing point for the box prefilter (a fast quotient is
-                // ample against the 1e-3 pad)
-                const float tt = dn != 0.f ? __fdividef(-dP, dn) : 0.5f;
-                const float cx = P.x + tt * ex(k), cy = P.y + tt * ey(k), cz = P.z + tt * ez(k);
-                const bool inside = cx >= emin.x - bpad && cx <= emax.x + bpad &&
-                                    cy >= emin.y - bpad && cy <= emax.y + bpad &&
-                                    cz >= emin.z - bpad && cz <= emax.z + bpad;
-                dirs |= (inside ? 1u : 0u) << d;
-            }
+        for (int a = 0; a < 3; ++a) {
+            const float lo = (e[a] > 0 ? emin[a] - 1.f : emin[a]) - pad;
+            const float hi = (e[a] < 0 ? emax[a] + 1.f : emax[a]) + pad;
+            rlo[a] = (int)ceilf(lo);
+            rn[a] = max(0, (int)floorf(hi) - rlo[a] + 1);
         }
-        // warp prefix sum of the candidate counts, then the lanes' slots
-        const int c = __popc(dirs);
-        int incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(full, incl, o);
-            if (lane >= o) incl += t;
-        }
-        int j = ncand + incl - c;
-        for (unsigned b = dirs; b; b &= b - 1u) cw[j++] = (unsigned short)((s << 4) | (__ffs(b) - 1));
-        ncand += __shfl_sync(full, incl, 31);
+        cnt = rn[0] * rn[1] * rn[2];
     }
-    __syncwarp();
-    for (int j0 = 0; j0 < ncand; j0 += 32) {
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        const int t = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(full, incl, 8);
+    const f3 nrm = cross(B - A, C - A);
+    for (int j0 = 0; j0 < total; j0 += 32) {
         const int j = j0 + lane;
+        // direction of candidate j: the number of directions whose inclusive
+        // prefix is at most j
+        int dsel = 0;
+#pragma unroll
+        for (int d = 0; d < 9; ++d) dsel += __shfl_sync(full, incl, d) <= j ? 1 : 0;
+        const int src = min(dsel, 8);
+        const int base = __shfl_sync(full, incl - cnt, src);
+        const int lx = __shfl_sync(full, rlo[0], src), ly = __shfl_sync(full, rlo[1], src),
+                  lz = __shfl_sync(full, rlo[2], src);
+        const int nx_ = __shfl_sync(full, rn[0], src), ny_ = __shfl_sync(full, rn[1], src);
         bool hit = false;
         long long n0 = 0, n1 = 0;
-        int k = 1;
-        if (j < ncand) {
-            const unsigned cv = cw[j];
-            const int s = (int)(cv >> 4);
-            k = 2 * (int)(cv & 15u) + 1;
+        const int k = 2 * src + 1;
+        if (j < total) {
+            // start node idx of the direction's range, x fastest
+            const int idx = j - base;
+            const int nxy = nx_ * ny_;
+            // (idx + 1/2) / nxy lies at least 1/(2 nxy) from an integer, far
+            // above the error of the fast quotient, so truncation is exact
+            const int iz = (int)__fdividef((float)idx + 0.5f, (float)nxy);
+            const int r = idx - iz * nxy;
+            const int iy = (int)__fdividef((float)r + 0.5f, (float)nx_);
+            const int x = lx + r - iy * nx_, y = ly + iy, z = lz + iz;
             int kx, ky, kz;
             ek(k, kx, ky, kz);
-            int xi, yi, zi;
-            box_of(s, nbx, nbxy, rnbx, rnbxy, xi, yi, zi);
-            const int x = x0 + xi, y = y0 + yi, z = z0 + zi;
             // links touching the substrate plane z = 0 are not fluid links
             if (!(p.wall && (wrap_fast(z, p.nz) == 0 || wrap_fast(z + kz, p.nz) == 0))) {
                 const f3 P{(float)x, (float)y, (float)z};
                 const f3 Qp{(float)(x + kx), (float)(y + ky), (float)(z + kz)};
-                hit = edges_pass(P, Qp, A, B, C);
+                hit = plane_side(nrm, A, B, C, P) != plane_side(nrm, A, B, C, Qp) &&
+                      edges_pass(P, Qp, A, B, C);
             }
             if (hit) {
                 n0 = node_at(p, x, y, z);
@@ -595,16 +584,16 @@ __global__ void __launch_bounds__(32 * CUT_WPB) k_cut_faces(const CutParams p) {
         const unsigned hits = __ballot_sync(full, hit);
         if (!hits) continue;
         const int leader = __ffs(hits) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(p.count, 2 * __popc(hits));
-        base = __shfl_sync(full, base, leader);
+        int at = 0;
+        if (lane == leader) at = atomicAdd(p.count, 2 * __popc(hits));
+        at = __shfl_sync(full, at, leader);
         if (hit) {
             const int k2 = opp(k);
             atomicXor(p.mask + n0, 1u << (k - 1));
             atomicMin(p.tri + n0 * 18 + (k - 1), T);
             atomicXor(p.mask + n1, 1u << (k2 - 1));
             atomicMin(p.tri + n1 * 18 + (k2 - 1), T);
-            const int idx = base + 2 * __popc(hits & ((1u << lane) - 1u));
+            const int idx = at + 2 * __popc(hits & ((1u << lane) - 1u));
             if (idx + 1 < p.capacity) {
                 p.list[idx] = make_int2(cut_code(n0, k), T);
                 p.list[idx + 1] = make_int2(cut_code(n1, k2), T);
@@ -653,7 +642,7 @@ __global__ void k_cut_prep(const PrepParams p) {
         if (__ldg(p.tri + n * 18 + k1) != T) continue;
         // the node's density: the sum of its post-collision populations equals
         // the density of the step that produced them (BGK conserves mass)
-        const float4 dn = __ldg(p.dens + n);
+        const float2 dn = __ldg(p.rho + n);
         int kx, ky, kz;
         ek(k, kx, ky, kz);
         const int a = __ldg(p.faces + 3 * T), b = __ldg(p.faces + 3 * T + 1), c = __ldg(p.faces + 3 * T + 2);

@@ -188,3 +188,30 @@ def test_capsule_pair_full_size_lateral_force(cfm):
     e = (cb - ca)[:2]; e /= np.linalg.norm(e)
     Fo = 0.5 * np.dot((Fb - Fa)[:2], e)
     assert abs(Fg - Fo) <= 1e-2 * abs(Fo) + 1e-7, (Fg, Fo)
+
+
+@pytest.mark.parametrize("level,radius", [(1, 6.0), (0, 5.0)])
+def test_cut_links_coarse_mesh(cfm, level, radius):
+    """Elements several lattice units long (level-1 and level-0 icospheres):
+    the cut links match the oracle at set-up and after free motion."""
+    c = (12.3, 11.6, 12.17)
+    wl = I.Workload("coarse", 24, 24, 24, h_top=12.5, steps=10, seed=8,
+                    capsules=[I.CapsuleSpec(centre=c, radius=radius, level=level, kS=5e-3, C=1.0,
+                                            kB=1e-3, mode=I.MODE_FREE)], rep_dz=2.0)
+    sim = cfm.Simulation.from_workload(wl)
+    orc = O.Oracle.from_workload(wl)
+    compare_cuts(sim, orc)
+    sim.step(wl.steps); orc.step(wl.steps)
+    compare_cuts(sim, orc)
+    compare_state(sim, orc)
+
+
+def test_element_longer_than_16_units_is_rejected(cfm):
+    """An element spanning more than 16 lattice units is reported as
+    CF_EOVERFLOW instead of being searched."""
+    c = (32.3, 32.4, 32.17)
+    wl = I.Workload("huge", 64, 64, 64, h_top=30.5, steps=1,
+                    capsules=[I.CapsuleSpec(centre=c, radius=20.0, level=0, mode=I.MODE_FIXED)])
+    with pytest.raises(cfm.CapfilmError, match="16 lattice units"):
+        sim = cfm.Simulation.from_workload(wl)
+        sim.step(1)
