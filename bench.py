@@ -209,7 +209,7 @@ def run_ours(args):
     prec = PRECISIONS[args.precision]
     alg_bytes = ALG_BYTES_PER_LU if prec == 0 else ALG_BYTES_PER_LU_16
     sim = cfm.Simulation.from_workload(wl, precision=prec)
-    stream = torch.cuda.current_stream()
+    stream = sim.stream  # the events must be recorded on the stream the steps run on
     # warm-up
     sim.step(args.warmup)
     sim.sync()

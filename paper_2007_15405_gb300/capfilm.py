@@ -157,12 +157,17 @@ class Simulation:
         self._alloc = None
         alloc_ptr = None
         stream_handle = None
+        self._stream = None
         if use_torch_allocator:
             import torch
             dev = torch.cuda.current_device()
             self._alloc = _TorchAllocator(dev)
             alloc_ptr = C.pointer(self._alloc.struct)
             s = stream if stream is not None else torch.cuda.current_stream()
+            if s.cuda_stream == 0:
+                # the library runs on a stream of its own; make it a torch
+                # stream so that callers can order work and events after it
+                s = torch.cuda.Stream()
             stream_handle = s.cuda_stream
             self._stream = s
         elif stream is not None:
@@ -217,6 +222,12 @@ class Simulation:
 
     def step(self, n=1):
         _check(_lib.cf_step(self._h, int(n)))
+
+    @property
+    def stream(self):
+        """The torch stream every call of this simulation is enqueued on (None
+        when the library created its own stream)."""
+        return self._stream
 
     def sync(self):
         _check(_lib.cf_sync(self._h))
