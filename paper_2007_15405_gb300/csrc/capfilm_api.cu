@@ -108,6 +108,7 @@ struct cf_ctx {
     // FT[1 - ftpar] holds the previous step's (two-step average)
     float *FT[2] = {nullptr, nullptr};
     int ftpar = 0;
+    float4 *uT = nullptr;  // element velocities, recorded with the cut links
     float *V = nullptr, *fscr = nullptr, *vscr = nullptr,
           *Fcpl = nullptr, *refM = nullptr, *refA = nullptr, *refDet = nullptr;
     int *faces = nullptr, *face_cap = nullptr, *node_cap = nullptr, *vf_off = nullptr,
@@ -239,13 +240,13 @@ cf_status enqueue_cuts(cf_ctx *c, const float *X, int *nl) {
     q.tri = c->tri;
     q.list = c->list[cur];
     q.count = c->counts + cur;
-    q.prev_count = c->counts + c->lpar;
-    q.prev_list = c->list[c->lpar];
     q.FTnext = c->FT[1 - c->ftpar];
+    q.V = c->V;
+    q.uT = c->uT;
     q.capacity = c->capacity;
     q.status = c->status;
     CF_CUDA(cudaMemsetAsync(c->counts + cur, 0, sizeof(int), c->stream));
-    CF_CUDA(launch_cuts(q, 0, c->stream, nl));
+    CF_CUDA(launch_cuts(q, c->stream, nl));
     c->lpar = cur;
     return CF_OK;
 }
@@ -255,8 +256,8 @@ cf_status enqueue_cuts(cf_ctx *c, const float *X, int *nl) {
 // records, ev[1] after the lattice update, ev[2] after the node update, ev[3]
 // after the cut links.
 //
-//   stream   prep -> density -> collide -----join-> update [-> frozen] -> cuts
-//   stream2        \-> memsets -> elements -> nodes -> bending -/
+//   stream   prep -> density -> collide ----join-> update (+ cut reset) [-> frozen] -> cut links
+//   stream2       \-> memsets -> elements -> nodes -> bending -/
 //
 // The membrane's position-only kernels run beside the lattice update; the
 // node update waits for both.
@@ -282,8 +283,7 @@ cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev = null
         q.rho = c->rho[c->fpar];
         q.mask = c->mask;
         q.tri = c->tri;
-        q.faces = c->faces;
-        q.V = c->V;
+        q.uT = c->uT;
         q.list = c->list[c->lpar];
         q.count = c->counts + c->lpar;
         q.rec = c->rec;
@@ -298,7 +298,17 @@ cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev = null
     if (ev) CF_CUDA(cudaEventRecord(ev[1], c->stream));
     if (mem) {
         CF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
-        CF_CUDA(launch_membrane_update(mem_params(c), c->any_frozen, c->stream, nl));
+        // extra blocks of the update reset the cut structure about to be rebuilt
+        ClearParams cl{};
+        if (!c->all_fixed) {
+            cl.list = c->list[c->lpar];
+            cl.count = c->counts + c->lpar;
+            cl.capacity = c->capacity;
+            cl.mask = c->mask;
+            cl.tri = c->tri;
+            cl.blocks = 304;
+        }
+        CF_CUDA(launch_membrane_update(mem_params(c), cl, c->any_frozen, c->stream, nl));
         c->xpar = 1 - c->xpar;
     }
     if (ev) CF_CUDA(cudaEventRecord(ev[2], c->stream));
@@ -414,6 +424,7 @@ cf_status build_membrane(cf_ctx *c) {
     MALLOC_M(c->vscr, float, 4 * nv);
     MALLOC_M(c->FT[0], float, 3 * nf);
     MALLOC_M(c->FT[1], float, 3 * nf);
+    MALLOC_M(c->uT, float4, nf);
     MALLOC_M(c->fscr, float, (size_t)FS_N * nf);
     MALLOC_M(c->refM, float, 3 * nf);
     MALLOC_M(c->refA, float, nf);

@@ -141,14 +141,25 @@ struct CutParams {
     int *tri;
     int2 *list;              // one entry per marked link: (cut_code(n, k), T)
     int *count;              // entries appended to `list` (zeroed before)
-    const int *prev_count;   // entries of `prev_list`
-    const int2 *prev_list;   // list of the previous computation (cleared first)
-    float *FTnext;           // [3*nfaces] exchange accumulator of the next step (zeroed first)
+    float *FTnext;           // [3*nfaces] exchange accumulator of the next step (zeroed here)
+    const float *V;          // [3*nnodes] node velocities
+    float4 *uT;              // [nfaces] element velocities (written here)
     int capacity;
     unsigned *status;
 };
 
-// Bounce records of the cut nodes for the next streaming (built once per step).
+// Reset of the previous cut structure, run by extra blocks of the node-update
+// kernel (which touches neither masks nor crossed elements).
+struct ClearParams {
+    const int2 *list;        // entries of the previous computation
+    const int *count;
+    int capacity;
+    uint32_t *mask;
+    int *tri;
+    int blocks;              // blocks of the update kernel given to the reset (0: none)
+};
+
+// Bounce records of the cut links for the next streaming (built once per step).
 struct PrepParams {
     long long N;
     int prec;                // storage of the populations (cf_precision)
@@ -156,8 +167,7 @@ struct PrepParams {
     const float2 *rho;       // (rhoA, rhoB) of the step that produced them
     const uint32_t *mask;
     const int *tri;
-    const int *faces;
-    const float *V;
+    const float4 *uT;        // element velocities (mean of their nodes')
     const int2 *list;        // cut-link entries (cut_code(n, k), T), with repetitions
     const int *count;
     float2 *rec;             // [N][18] bounced (A, B) populations by arriving direction - 1
@@ -187,7 +197,8 @@ cudaError_t launch_mass(const void *f, const float *f0, int prec, const float2 *
                         double *m2, cudaStream_t s);
 // membrane kernels 1-3 (positions only) and 4-5 (after the lattice update)
 cudaError_t launch_membrane_forces(const MemParams &p, cudaStream_t s, int *nlaunch);
-cudaError_t launch_membrane_update(const MemParams &p, bool any_frozen, cudaStream_t s, int *nlaunch);
-cudaError_t launch_cuts(const CutParams &p, int prev_count_hint, cudaStream_t s, int *nlaunch);
+cudaError_t launch_membrane_update(const MemParams &p, const ClearParams &cl, bool any_frozen,
+                                   cudaStream_t s, int *nlaunch);
+cudaError_t launch_cuts(const CutParams &p, cudaStream_t s, int *nlaunch);
 cudaError_t launch_prep(const PrepParams &p, cudaStream_t s, int *nlaunch);
 }  // namespace cf

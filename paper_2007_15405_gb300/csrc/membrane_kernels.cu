@@ -18,9 +18,9 @@
 //      summed force.
 // Kernels 1-3 depend on the positions only, so they run on a second stream
 // while the lattice update of the same step runs; kernel 4 joins both.  The
-// cut links for the moved membrane are rebuilt by k_cut_clear and
-// k_cut_faces; k_cut_prep builds the bounce records of the cut links at the
-// start of each step.
+// cut links of the moved membrane are rebuilt by k_cut_faces after
+// k_mem_update has reset the previous ones; the density pass of the next step
+// prepares the bounce records of the cut links.
 #include "cf_common.cuh"
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -248,22 +248,40 @@ __device__ __forceinline__ void node_forces(const MemParams &p, const CapDev &cp
     f3 Fe{0.f, 0.f, 0.f}, Fi{0.f, 0.f, 0.f}, dv{0.f, 0.f, 0.f};
     const bool el = cp.mode == 0;
     const int e0 = p.vf_off[v], e1 = p.vf_off[v + 1];
-    for (int eb = e0; eb < e1; eb += VU) {
-        int ent[VU];
+    // entries GU at a time, every load unconditional (entries past the end
+    // repeat the first one with weight 0), so that they are all in flight at once
+    constexpr int GU = 4;
+    for (int eb = e0; eb < e1; eb += GU) {
+        int f[GU], sl[GU];
+        float w[GU];
 #pragma unroll
-        for (int j = 0; j < VU; ++j) ent[j] = eb + j < e1 ? __ldg(p.vf_ent + eb + j) : -1;
+        for (int j = 0; j < GU; ++j) {
+            const bool ok = eb + j < e1;
+            const int e = __ldg(p.vf_ent + (ok ? eb + j : e0));
+            f[j] = e / 3;
+            sl[j] = e - 3 * f[j];
+            w[j] = ok ? 1.f : 0.f;
+        }
+        f3 ft[GU];
 #pragma unroll
-        for (int j = 0; j < VU; ++j) {
-            if (ent[j] < 0) continue;
-            const int f = ent[j] / 3, sl = ent[j] - 3 * f;
-            const float *S = p.fscr + (long long)f * FS_N;
-            // momentum exchanged with the element in this step and the previous one
-            Fc = Fc + ld3(p.FT, f) + ld3(p.FTprev, f);
-            if (el) {
-                Fe = Fe + ld3(S + FS_SK, sl) + ld3(S + FS_BEND, sl);
-                dv = dv + ld3(S + FS_DV, sl);
+        for (int j = 0; j < GU; ++j)  // exchange of this step and the previous one
+            ft[j] = ld3(p.FT, f[j]) + ld3(p.FTprev, f[j]);
+        if (el) {
+            f3 fe[GU], fd[GU];
+#pragma unroll
+            for (int j = 0; j < GU; ++j) {
+                const float *S = p.fscr + (long long)f[j] * FS_N;
+                fe[j] = ld3(S + FS_SK, sl[j]) + ld3(S + FS_BEND, sl[j]);
+                fd[j] = ld3(S + FS_DV, sl[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < GU; ++j) {
+                Fe = Fe + w[j] * fe[j];
+                dv = dv + w[j] * fd[j];
             }
         }
+#pragma unroll
+        for (int j = 0; j < GU; ++j) Fc = Fc + w[j] * ft[j];
     }
     Fc = (0.5f / 3.f) * Fc;  // two-step average, a third to each node of the element
     if (el) Fe = Fe + pre * dv;
@@ -347,8 +365,22 @@ __global__ void __launch_bounds__(MT) k_mem_bending(const MemParams p) {
 }
 
 // 4. nodes: coupling, elastic and Hertz forces, node update (Eq. 9), FP64
-//    sums of force, torque and total force
-__global__ void __launch_bounds__(MV) k_mem_update(const MemParams p) {
+//    sums of force, torque and total force.  Blocks past the nodes undo the
+//    previous cut structure (each entry of the previous list names one marked
+//    link: its mask word and crossed element are reset) before the cut links
+//    of the new positions are marked.
+__global__ void __launch_bounds__(MV) k_mem_update(const MemParams p, const ClearParams cl) {
+    const int node_blocks = (p.nnodes + MV - 1) / MV;
+    if ((int)blockIdx.x >= node_blocks) {
+        const int cnt = min(*cl.count, cl.capacity);
+        for (int i = ((int)blockIdx.x - node_blocks) * MV + threadIdx.x; i < cnt; i += cl.blocks * MV) {
+            const int2 e = cl.list[i];
+            const long long n = (long long)((unsigned)e.x >> 5);
+            cl.mask[n] = 0u;
+            cl.tri[n * 18 + (e.x & 31)] = 0x7fffffff;
+        }
+        return;
+    }
     const int v = blockIdx.x * MV + threadIdx.x;
     const bool valid = v < p.nnodes;
     const int vv = valid ? v : 0;
@@ -409,9 +441,10 @@ cudaError_t launch_membrane_forces(const MemParams &p, cudaStream_t s, int *nl) 
     return cudaGetLastError();
 }
 
-cudaError_t launch_membrane_update(const MemParams &p, bool any_frozen, cudaStream_t s, int *nl) {
+cudaError_t launch_membrane_update(const MemParams &p, const ClearParams &cl, bool any_frozen,
+                                   cudaStream_t s, int *nl) {
     const unsigned gv = (unsigned)((p.nnodes + MV - 1) / MV);
-    k_mem_update<<<gv, MV, 0, s>>>(p);
+    k_mem_update<<<gv + (unsigned)cl.blocks, MV, 0, s>>>(p, cl);
     *nl += 1;
     if (any_frozen) {
         k_mem_frozen<<<gv, MV, 0, s>>>(p);
@@ -453,21 +486,6 @@ __device__ __forceinline__ bool edges_pass(f3 P, f3 Qp, f3 A, f3 B, f3 C) {
     return edges_pass_d(P, Qp, A, B, C);
 }
 
-// Undo the previous cut structure: each entry of the previous list names one
-// marked link (node, direction); its mask word and crossed element are reset.
-// The exchange accumulator of the next step is zeroed here as well.
-__global__ void k_cut_clear(const CutParams p) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * p.nfaces; i += gridDim.x * blockDim.x)
-        p.FTnext[i] = 0.f;
-    const int prev = min(*p.prev_count, p.capacity);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < prev; i += gridDim.x * blockDim.x) {
-        const int2 e = p.prev_list[i];
-        const long long n = (long long)((unsigned)e.x >> 5);
-        p.mask[n] = 0u;
-        p.tri[n * 18 + (e.x & 31)] = 0x7fffffff;
-    }
-}
-
 // One warp per element.  A link (P, P+e_k), k in the nine positive directions,
 // can cross the element only where its crossing point lies in the element's
 // bounding box: along an axis a with e_a = 0 the start node lies in the box,
@@ -481,7 +499,9 @@ __global__ void k_cut_clear(const CutParams p) {
 // differ, the three edge orientations.  A crossing toggles the cut bit of the
 // link at both of its end nodes, keeps the smallest crossing element there,
 // and appends one list entry per end node (one counter update per warp and
-// pass).
+// pass).  The warp also records the element's velocity (the mean of its
+// nodes', for Ladd's term of the next streaming) and zeroes the element's
+// momentum-exchange accumulator of the next step.
 constexpr int CUT_WPB = 8;  // elements (warps) per block
 
 // periodic index, with the common in-range case first
@@ -505,9 +525,17 @@ __global__ void __launch_bounds__(32 * CUT_WPB) k_cut_faces(const CutParams p) {
     const int lane = (int)(threadIdx.x & 31);
     const int T = blockIdx.x * CUT_WPB + (int)(threadIdx.x >> 5);
     if (T >= p.nfaces) return;  // the whole warp
+    const int ia = p.faces[3 * T], ib = p.faces[3 * T + 1], ic = p.faces[3 * T + 2];
+    if (lane == 0) {
+        const float ux = (p.V[3 * ia] + p.V[3 * ib] + p.V[3 * ic]) * (1.0f / 3.0f);
+        const float uy = (p.V[3 * ia + 1] + p.V[3 * ib + 1] + p.V[3 * ic + 1]) * (1.0f / 3.0f);
+        const float uz = (p.V[3 * ia + 2] + p.V[3 * ib + 2] + p.V[3 * ic + 2]) * (1.0f / 3.0f);
+        p.uT[T] = make_float4(ux, uy, uz, 0.f);
+    } else if (lane < 4) {
+        p.FTnext[3 * T + lane - 1] = 0.f;
+    }
     // the decision is taken on the float (hi) positions
-    const f3 A = ld3(p.X, p.faces[3 * T]), B = ld3(p.X, p.faces[3 * T + 1]),
-             C = ld3(p.X, p.faces[3 * T + 2]);
+    const f3 A = ld3(p.X, ia), B = ld3(p.X, ib), C = ld3(p.X, ic);
     const float emin[3] = {fminf(A.x, fminf(B.x, C.x)), fminf(A.y, fminf(B.y, C.y)),
                            fminf(A.z, fminf(B.z, C.z))};
     const float emax[3] = {fmaxf(A.x, fmaxf(B.x, C.x)), fmaxf(A.y, fmaxf(B.y, C.y)),
@@ -604,11 +632,9 @@ __global__ void __launch_bounds__(32 * CUT_WPB) k_cut_faces(const CutParams p) {
     }
 }
 
-cudaError_t launch_cuts(const CutParams &p, int prev_hint, cudaStream_t s, int *nl) {
-    (void)prev_hint;
-    k_cut_clear<<<152, 256, 0, s>>>(p);
+cudaError_t launch_cuts(const CutParams &p, cudaStream_t s, int *nl) {
     k_cut_faces<<<(p.nfaces + CUT_WPB - 1) / CUT_WPB, 32 * CUT_WPB, 0, s>>>(p);
-    *nl += 2;
+    *nl += 1;
     return cudaGetLastError();
 }
 
@@ -626,8 +652,8 @@ __device__ __forceinline__ float pop_at(const PrepParams &p, int c, int k, long 
 // Bounce records for the next streaming, one thread per entry of the cut-link
 // list: the population a cut node sent towards the membrane comes back with
 // Ladd's term -2 w_k rho (e_k . u_T)/c_s^2 (rho: the node's density = sum of
-// its post-collision populations; u_T: mean velocity of the crossed element's
-// nodes); the momentum each bounce exchanges with the element,
+// its post-collision populations; u_T: velocity of the crossed element, the
+// mean of its nodes' velocities); the momentum each bounce exchanges with the element,
 // sum_c (2 f*_k - corr), is booked on it (Sec. 3.1, coupling paragraph).  A link
 // crossed by several elements has one entry per element: the entry of the
 // smallest one (the element kept in tri) writes the record, and a link whose
@@ -645,11 +671,8 @@ __global__ void k_cut_prep(const PrepParams p) {
         const float2 dn = __ldg(p.rho + n);
         int kx, ky, kz;
         ek(k, kx, ky, kz);
-        const int a = __ldg(p.faces + 3 * T), b = __ldg(p.faces + 3 * T + 1), c = __ldg(p.faces + 3 * T + 2);
-        const float ux = (p.V[3 * a] + p.V[3 * b] + p.V[3 * c]) * (1.0f / 3.0f);
-        const float uy = (p.V[3 * a + 1] + p.V[3 * b + 1] + p.V[3 * c + 1]) * (1.0f / 3.0f);
-        const float uz = (p.V[3 * a + 2] + p.V[3 * b + 2] + p.V[3 * c + 2]) * (1.0f / 3.0f);
-        const float eu = kx * ux + ky * uy + kz * uz;
+        const float4 u = __ldg(p.uT + T);  // recorded by k_cut_faces
+        const float eu = kx * u.x + ky * u.y + kz * u.z;
         const float foa = pop_at(p, 0, k, n, dn.x), fob = pop_at(p, 1, k, n, dn.y);
         const float w6 = 6.0f * wgt(k);
         const float ca = w6 * dn.x * eu, cb = w6 * dn.y * eu;
