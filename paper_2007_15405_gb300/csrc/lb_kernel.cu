@@ -176,11 +176,18 @@ __device__ __forceinline__ uint32_t pull(const LBParams &p, const Deltas &d, flo
     return m;
 }
 
-// z range of the fluid planes a thread walks (grid.z splits the column)
+// z range of the fluid planes a thread walks (grid.z splits the column).
+// REV maps the blocks in reverse order: the collide pass then starts on the
+// tiles the density pass touched last (still in L2), and the next density pass
+// starts on the tiles the collide pass wrote last.
+template <bool REV = false>
 __device__ __forceinline__ bool node_of(const LBParams &p, int &x, int &y, int &z) {
-    x = blockIdx.x * BX + threadIdx.x;
-    y = blockIdx.y * BY + threadIdx.y;
-    z = p.zlo + blockIdx.z;
+    const int bx = REV ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+    const int by = REV ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y;
+    const int bz = REV ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z;
+    x = bx * BX + threadIdx.x;
+    y = by * BY + threadIdx.y;
+    z = p.zlo + bz;
     return x < p.nx && y < p.ny;
 }
 
@@ -350,7 +357,7 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
 template <typename T>
 __global__ void __launch_bounds__(BX *BY, CF_COLLIDE_MINB) k_collide(const LBParams p) {
     int x, y, z;
-    if (!node_of(p, x, y, z)) return;
+    if (!node_of<true>(p, x, y, z)) return;
     for (; z < p.zhi; z += gridDim.z) collide_node<T>(p, deltas(p, x, y, z));
 }
 

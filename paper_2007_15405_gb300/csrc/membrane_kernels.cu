@@ -520,7 +520,7 @@ __device__ __forceinline__ bool plane_side(const f3 &nrm, const f3 &A, const f3 
     return fabsf(d) > OEPS ? d >= 0.f : side_of_d(A, B, C, P);
 }
 
-__global__ void __launch_bounds__(32 * CUT_WPB) k_cut_faces(const CutParams p) {
+__global__ void __launch_bounds__(32 * CUT_WPB, 4) k_cut_faces(const CutParams p) {
     const unsigned full = 0xffffffffu;
     const int lane = (int)(threadIdx.x & 31);
     const int T = blockIdx.x * CUT_WPB + (int)(threadIdx.x >> 5);
