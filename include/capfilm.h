@@ -206,6 +206,48 @@ cf_status cf_lattice_step_static(const float *src, float *dst, int nx, int ny, i
 /* Number of kernel launches issued by the last cf_step / cf_time_phases call. */
 cf_status cf_launch_count(cf_ctx *ctx, long long *n);
 
+/* ---------------------------------------------------------------- batches
+ * A batch steps many independent contexts together, for parameter sweeps such
+ * as the paper's series over capsule distance and elastic modulus (Sec. 4):
+ * the lattice passes of all of them run as one persistent launch per pass over
+ * a work list of (lattice, tile) items, their membrane and cut-link phases as
+ * parallel branches, and pairs of steps are replayed from a captured CUDA
+ * graph.  Each context advances exactly as cf_step would advance it alone
+ * (same arithmetic per node); it stays usable for all readouts, and may also
+ * be stepped alone between batch steps.  The batch keeps pointers to the
+ * contexts: destroy the batch before any of its contexts. */
+typedef struct cf_batch cf_batch;
+
+/* n (1..128) distinct contexts, all after cf_set_film and with the same
+ * precision.  Starts with tile shape 1 (32 x 4) and 2 planes per thread.
+ * Errors: CF_EINVAL (bad or repeated context, mixed precision), CF_ESTATE. */
+cf_status cf_batch_create(cf_ctx *const *ctxs, int n, cf_batch **batch);
+cf_status cf_batch_destroy(cf_batch *batch);
+
+/* n steps of every context; returns after they have completed (device errors
+ * of any context are reported as by cf_step). */
+cf_status cf_batch_step(cf_batch *batch, long long n);
+
+/* As cf_batch_step, and the device time of the n steps in *ms (CUDA events on
+ * the batch's own stream). */
+cf_status cf_batch_time(cf_batch *batch, long long n, double *ms);
+
+/* Launch shape of the batched lattice passes: tile in 0..5 selects the block
+ * (x width, y depth) = (32,2), (32,4), (32,8), (64,2), (64,4), (128,2);
+ * zchunk >= 1 is the number of planes each thread walks.  Results do not
+ * depend on the shape. */
+cf_status cf_batch_set_config(cf_batch *batch, int tile, int zchunk);
+cf_status cf_batch_config(const cf_batch *batch, int *tile, int *tile_x, int *tile_y, int *zchunk);
+
+/* Autotuner: times `steps` (>= 2) steps of the batch for every tile shape and
+ * zchunk in {1, 2, 4}, keeps the fastest and returns it with its time per
+ * step.  The trials are real steps: every context advances by 18 * (steps + 3)
+ * steps. */
+cf_status cf_batch_autotune(cf_batch *batch, int steps, int *tile, int *zchunk, double *ms_per_step);
+
+/* Number of kernel launches issued by the last cf_batch_step / cf_batch_time. */
+cf_status cf_batch_launch_count(const cf_batch *batch, long long *n);
+
 #ifdef __cplusplus
 }
 #endif

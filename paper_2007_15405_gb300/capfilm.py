@@ -84,6 +84,15 @@ def load_library(path: Optional[str] = None):
         "cf_time_phases": [C.c_void_p, C.c_longlong, _dp],
         "cf_lattice_step_static": [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
                                    _dp, C.c_double, C.c_void_p],
+        "cf_batch_create": [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)],
+        "cf_batch_destroy": [C.c_void_p],
+        "cf_batch_step": [C.c_void_p, C.c_longlong],
+        "cf_batch_time": [C.c_void_p, C.c_longlong, _dp],
+        "cf_batch_set_config": [C.c_void_p, C.c_int, C.c_int],
+        "cf_batch_config": [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                            C.POINTER(C.c_int)],
+        "cf_batch_autotune": [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp],
+        "cf_batch_launch_count": [C.c_void_p, C.POINTER(C.c_longlong)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -98,7 +107,9 @@ def exported_symbols():
             "cf_set_film", "cf_step", "cf_sync", "cf_capsule_force", "cf_lateral_force",
             "cf_capsule_state", "cf_fields", "cf_populations", "cf_total_mass",
             "cf_meniscus_field", "cf_meniscus_profile", "cf_cuts", "cf_launch_count",
-            "cf_time_phases", "cf_lattice_step_static"]
+            "cf_time_phases", "cf_lattice_step_static", "cf_batch_create", "cf_batch_destroy",
+            "cf_batch_step", "cf_batch_time", "cf_batch_set_config", "cf_batch_config",
+            "cf_batch_autotune", "cf_batch_launch_count"]
 
 
 def _check(rc):
@@ -295,3 +306,60 @@ class Simulation:
                             tri.ctypes.data_as(C.POINTER(C.c_int)),
                             ins.ctypes.data_as(C.POINTER(C.c_uint8))))
         return mask, tri, ins
+
+
+class Batch:
+    """Many simulations stepped together (cf_batch): one persistent launch per
+    lattice pass over all of them, their membrane phases as parallel branches.
+    The simulations stay usable for readouts; close the batch before them."""
+
+    def __init__(self, sims):
+        L = load_library()
+        self.sims = list(sims)
+        arr = (C.c_void_p * len(self.sims))(*[s._h.value for s in self.sims])
+        h = C.c_void_p()
+        _check(L.cf_batch_create(arr, len(self.sims), C.byref(h)))
+        self._h = h
+
+    def step(self, n):
+        _check(_lib.cf_batch_step(self._h, int(n)))
+
+    def time(self, n):
+        """Device time (ms) of n steps."""
+        ms = C.c_double()
+        _check(_lib.cf_batch_time(self._h, int(n), C.byref(ms)))
+        return ms.value
+
+    def set_config(self, tile, zchunk):
+        _check(_lib.cf_batch_set_config(self._h, int(tile), int(zchunk)))
+
+    def config(self):
+        t, tx, ty, zc = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(_lib.cf_batch_config(self._h, C.byref(t), C.byref(tx), C.byref(ty), C.byref(zc)))
+        return dict(tile=t.value, tile_x=tx.value, tile_y=ty.value, zchunk=zc.value)
+
+    def autotune(self, steps=6):
+        """Time every launch shape for `steps` steps (real steps) and keep the
+        fastest; returns the chosen shape and its ms per step."""
+        t, zc, ms = C.c_int(), C.c_int(), C.c_double()
+        _check(_lib.cf_batch_autotune(self._h, int(steps), C.byref(t), C.byref(zc), C.byref(ms)))
+        d = self.config()
+        d["ms_per_step"] = ms.value
+        return d
+
+    def launches(self):
+        n = C.c_longlong()
+        _check(_lib.cf_batch_launch_count(self._h, C.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.cf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

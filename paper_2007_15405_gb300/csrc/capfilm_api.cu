@@ -74,6 +74,7 @@ struct cf_ctx {
     // joined back into `stream` every step
     cudaStream_t stream2 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_batch = nullptr;  // joins this context's work into a batch step
     cf_allocator alloc{};
     bool has_alloc = false;
     std::vector<void *> allocations;
@@ -261,41 +262,43 @@ cf_status enqueue_cuts(cf_ctx *c, const float *X, int *nl) {
 //
 // The membrane's position-only kernels run beside the lattice update; the
 // node update waits for both.
-cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev = nullptr) {
-    if (ev) CF_CUDA(cudaEventRecord(ev[4], c->stream));
+// The membrane half before the lattice update: fork the position-only
+// membrane kernels onto stream2 and prepare the bounce records on the stream.
+cf_status enqueue_pre(cf_ctx *c, int *nl) {
+    if (c->nnodes == 0) return CF_OK;
+    // fork: elastic, volume and bending forces of the current positions
+    CF_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+    CF_CUDA(cudaStreamWaitEvent(c->stream2, c->ev_fork, 0));
+    const int nc = (int)c->caps.size();
+    int *bb = c->bbox[c->xpar];
+    CF_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(double) * A_NACC * nc, c->stream2));
+    CF_CUDA(cudaMemsetAsync(bb, 0x7f, sizeof(int) * 3 * nc, c->stream2));
+    CF_CUDA(cudaMemsetAsync(bb + 3 * nc, 0x80, sizeof(int) * 3 * nc, c->stream2));
+    CF_CUDA(launch_membrane_forces(mem_params(c), c->stream2, nl));
+    CF_CUDA(cudaEventRecord(c->ev_join, c->stream2));
+    // bounce records of the cut links for this step's streaming
+    PrepParams q{};
+    q.N = c->N;
+    q.prec = c->d.precision;
+    q.src = c->f[c->fpar];
+    q.rho = c->rho[c->fpar];
+    q.mask = c->mask;
+    q.tri = c->tri;
+    q.uT = c->uT;
+    q.list = c->list[c->lpar];
+    q.count = c->counts + c->lpar;
+    q.rec = c->rec;
+    q.FT = c->FT[c->ftpar];
+    q.capacity = c->capacity;
+    CF_CUDA(launch_prep(q, c->stream, nl));
+    return CF_OK;
+}
+
+// The membrane half after the lattice update (whose populations are now in
+// f[fpar]): join stream2, node update with the reset of the old cut
+// structure, new cut links; ev2 (optional) is recorded after the node update.
+cf_status enqueue_post(cf_ctx *c, int *nl, cudaEvent_t ev2 = nullptr) {
     const bool mem = c->nnodes > 0;
-    if (mem) {
-        // fork: elastic, volume and bending forces of the current positions
-        CF_CUDA(cudaEventRecord(c->ev_fork, c->stream));
-        CF_CUDA(cudaStreamWaitEvent(c->stream2, c->ev_fork, 0));
-        const int nc = (int)c->caps.size();
-        int *bb = c->bbox[c->xpar];
-        CF_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(double) * A_NACC * nc, c->stream2));
-        CF_CUDA(cudaMemsetAsync(bb, 0x7f, sizeof(int) * 3 * nc, c->stream2));
-        CF_CUDA(cudaMemsetAsync(bb + 3 * nc, 0x80, sizeof(int) * 3 * nc, c->stream2));
-        CF_CUDA(launch_membrane_forces(mem_params(c), c->stream2, nl));
-        CF_CUDA(cudaEventRecord(c->ev_join, c->stream2));
-        // bounce records of the cut links for this step's streaming
-        PrepParams q{};
-        q.N = c->N;
-        q.prec = c->d.precision;
-        q.src = c->f[c->fpar];
-        q.rho = c->rho[c->fpar];
-        q.mask = c->mask;
-        q.tri = c->tri;
-        q.uT = c->uT;
-        q.list = c->list[c->lpar];
-        q.count = c->counts + c->lpar;
-        q.rec = c->rec;
-        q.FT = c->FT[c->ftpar];
-        q.capacity = c->capacity;
-        CF_CUDA(launch_prep(q, c->stream, nl));
-    }
-    if (ev) CF_CUDA(cudaEventRecord(ev[0], c->stream));
-    CF_CUDA(launch_lb_step(lb_params(c, with_out), c->d.precision, c->stream));
-    *nl += 2;
-    c->fpar = 1 - c->fpar;
-    if (ev) CF_CUDA(cudaEventRecord(ev[1], c->stream));
     if (mem) {
         CF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
         // extra blocks of the update reset the cut structure about to be rebuilt
@@ -311,7 +314,7 @@ cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev = null
         CF_CUDA(launch_membrane_update(mem_params(c), cl, c->any_frozen, c->stream, nl));
         c->xpar = 1 - c->xpar;
     }
-    if (ev) CF_CUDA(cudaEventRecord(ev[2], c->stream));
+    if (ev2) CF_CUDA(cudaEventRecord(ev2, c->stream));
     if (mem) {
         if (!c->all_fixed) {
             // also zeroes the exchange accumulator of the next step
@@ -323,6 +326,20 @@ cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev = null
         }
         c->ftpar = 1 - c->ftpar;
     }
+    return CF_OK;
+}
+
+cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev = nullptr) {
+    if (ev) CF_CUDA(cudaEventRecord(ev[4], c->stream));
+    cf_status s = enqueue_pre(c, nl);
+    if (s != CF_OK) return s;
+    if (ev) CF_CUDA(cudaEventRecord(ev[0], c->stream));
+    CF_CUDA(launch_lb_step(lb_params(c, with_out), c->d.precision, c->stream));
+    *nl += 2;
+    c->fpar = 1 - c->fpar;
+    if (ev) CF_CUDA(cudaEventRecord(ev[1], c->stream));
+    s = enqueue_post(c, nl, ev ? ev[2] : nullptr);
+    if (s != CF_OK) return s;
     if (ev) CF_CUDA(cudaEventRecord(ev[3], c->stream));
     return CF_OK;
 }
@@ -538,7 +555,8 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     }
     if (cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_batch, cudaEventDisableTiming) != cudaSuccess) {
         cf_destroy(c);
         return fail(CF_ECUDA, "stream / event creation failed");
     }
@@ -600,6 +618,7 @@ cf_status cf_destroy(cf_ctx *c) {
     if (c->stream2) { cudaStreamSynchronize(c->stream2); cudaStreamDestroy(c->stream2); }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_batch) cudaEventDestroy(c->ev_batch);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return CF_OK;
@@ -955,6 +974,258 @@ cf_status cf_cuts(cf_ctx *c, uint32_t *mask, int *tri, uint8_t *inside) {
     if (tri)
         for (long long i = 0; i < 18 * N; ++i)
             if (tri[i] >= c->nfaces || tri[i] < 0) tri[i] = -1;
+    return CF_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------- batches
+// A batch steps many contexts together: their membrane halves run as
+// parallel branches, their lattice passes as one persistent launch per pass.
+struct cf_batch {
+    std::vector<cf_ctx *> ctx;
+    int prec = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_lat = nullptr;
+    int tile = 1, zchunk = 2;     // tile shape index and planes per thread
+    int4 *work = nullptr;          // device work list
+    int nwork = 0;
+    std::vector<int> zstride;      // per lattice
+    cudaGraphExec_t graph = nullptr;
+    std::vector<int> graph_key;    // parities of all contexts at capture
+    int graph_launches = 0;
+    long long launches_last = 0;
+};
+
+namespace {
+
+cf_status batch_build_work(cf_batch *b) {
+    int tx, ty;
+    lb_batch_tile(b->tile, &tx, &ty);
+    std::vector<int4> w;
+    b->zstride.assign(b->ctx.size(), 1);
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        const cf_ctx *c = b->ctx[i];
+        const int nzf = c->d.nz - (c->d.wall ? 1 : 0);
+        const int gz = std::max(1, (nzf + b->zchunk - 1) / b->zchunk);
+        b->zstride[i] = gz;
+        for (int zs = 0; zs < gz; ++zs)
+            for (int ty_ = 0; ty_ < (c->d.ny + ty - 1) / ty; ++ty_)
+                for (int tx_ = 0; tx_ < (c->d.nx + tx - 1) / tx; ++tx_)
+                    w.push_back(make_int4((int)i, tx_, ty_, zs));
+    }
+    if (b->work) cudaFree(b->work);
+    b->work = nullptr;
+    CF_CUDA(cudaMalloc(&b->work, sizeof(int4) * w.size()));
+    CF_CUDA(cudaMemcpy(b->work, w.data(), sizeof(int4) * w.size(), cudaMemcpyHostToDevice));
+    b->nwork = (int)w.size();
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    return CF_OK;
+}
+
+// one step of every context of the batch, enqueued on the batch stream
+cf_status batch_enqueue_step(cf_batch *b, bool with_out, int *nl) {
+    CF_CUDA(cudaEventRecord(b->ev_fork, b->stream));
+    for (cf_ctx *c : b->ctx) {
+        CF_CUDA(cudaStreamWaitEvent(c->stream, b->ev_fork, 0));
+        cf_status s = enqueue_pre(c, nl);
+        if (s != CF_OK) return s;
+        CF_CUDA(cudaEventRecord(c->ev_batch, c->stream));
+        CF_CUDA(cudaStreamWaitEvent(b->stream, c->ev_batch, 0));
+    }
+    static BatchTab tab;  // copied into the launch
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        tab.lat[i] = lb_params(b->ctx[i], with_out);
+        tab.lat[i].zstride = b->zstride[i];
+    }
+    CF_CUDA(launch_lb_batch(tab, b->work, b->nwork, b->prec, b->tile, b->stream));
+    *nl += 2;
+    CF_CUDA(cudaEventRecord(b->ev_lat, b->stream));
+    for (cf_ctx *c : b->ctx) {
+        c->fpar = 1 - c->fpar;
+        CF_CUDA(cudaStreamWaitEvent(c->stream, b->ev_lat, 0));
+        cf_status s = enqueue_post(c, nl);
+        if (s != CF_OK) return s;
+        CF_CUDA(cudaEventRecord(c->ev_batch, c->stream));
+        CF_CUDA(cudaStreamWaitEvent(b->stream, c->ev_batch, 0));
+    }
+    return CF_OK;
+}
+
+std::vector<int> batch_key(const cf_batch *b) {
+    std::vector<int> k;
+    for (const cf_ctx *c : b->ctx) k.push_back(c->fpar | (c->xpar << 1) | (c->lpar << 2) | (c->ftpar << 3));
+    return k;
+}
+
+cf_status batch_run(cf_batch *b, long long n) {
+    int nl = 0;
+    long long left = n - 1;  // the last step records the fields
+    if (left >= 2) {
+        const std::vector<int> key = batch_key(b);
+        if (!b->graph || b->graph_key != key) {
+            if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+            cudaGraph_t g;
+            CF_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            int nlg = 0;
+            cf_status s1 = batch_enqueue_step(b, false, &nlg);
+            cf_status s2 = s1 == CF_OK ? batch_enqueue_step(b, false, &nlg) : s1;
+            cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+            if (s2 != CF_OK) return s2;
+            if (e != cudaSuccess) return fail(CF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&b->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fail(CF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+            b->graph_key = key;
+            b->graph_launches = nlg;
+        }
+        while (left >= 2) {
+            CF_CUDA(cudaGraphLaunch(b->graph, b->stream));
+            left -= 2;
+            nl += b->graph_launches;
+        }
+    }
+    while (left > 0) {
+        cf_status s = batch_enqueue_step(b, false, &nl);
+        if (s != CF_OK) return s;
+        --left;
+    }
+    cf_status s = batch_enqueue_step(b, true, &nl);
+    if (s != CF_OK) return s;
+    for (cf_ctx *c : b->ctx) c->steps_done += n;
+    b->launches_last = nl;
+    return CF_OK;
+}
+
+cf_status batch_sync(cf_batch *b) {
+    CF_CUDA(cudaStreamSynchronize(b->stream));
+    for (cf_ctx *c : b->ctx) {
+        cf_status s = sync_ok(c);
+        if (s != CF_OK) return s;
+    }
+    return CF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cf_status cf_batch_create(cf_ctx *const *ctxs, int n, cf_batch **out) {
+    if (!ctxs || !out || n <= 0) return fail(CF_EINVAL, "bad argument");
+    if (n > CF_BATCH_MAX) return fail(CF_EINVAL, "at most 128 contexts per batch");
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return fail(CF_EINVAL, "null context in batch");
+        if (!ctxs[i]->film_set) return fail(CF_ESTATE, "cf_set_film must come before cf_batch_create");
+        if (ctxs[i]->d.precision != ctxs[0]->d.precision)
+            return fail(CF_EINVAL, "all contexts of a batch need the same precision");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return fail(CF_EINVAL, "a context appears twice in the batch");
+    }
+    cf_batch *b = new cf_batch();
+    b->ctx.assign(ctxs, ctxs + n);
+    b->prec = ctxs[0]->d.precision;
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_lat, cudaEventDisableTiming) != cudaSuccess) {
+        cf_batch_destroy(b);
+        return fail(CF_ECUDA, "stream / event creation failed");
+    }
+    // every context's pending work completes before the first batch step
+    for (cf_ctx *c : b->ctx) {
+        cf_status s = sync_ok(c);
+        if (s != CF_OK) { cf_batch_destroy(b); return s; }
+    }
+    cf_status s = batch_build_work(b);
+    if (s != CF_OK) { cf_batch_destroy(b); return s; }
+    *out = b;
+    return CF_OK;
+}
+
+cf_status cf_batch_destroy(cf_batch *b) {
+    if (!b) return CF_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->work) cudaFree(b->work);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_lat) cudaEventDestroy(b->ev_lat);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return CF_OK;
+}
+
+cf_status cf_batch_set_config(cf_batch *b, int tile, int zchunk) {
+    if (!b || tile < 0 || tile >= CF_NTILES || zchunk < 1) return fail(CF_EINVAL, "bad argument");
+    CF_CUDA(cudaStreamSynchronize(b->stream));
+    b->tile = tile;
+    b->zchunk = zchunk;
+    return batch_build_work(b);
+}
+
+cf_status cf_batch_config(const cf_batch *b, int *tile, int *tile_x, int *tile_y, int *zchunk) {
+    if (!b) return fail(CF_EINVAL, "null batch");
+    int tx, ty;
+    lb_batch_tile(b->tile, &tx, &ty);
+    if (tile) *tile = b->tile;
+    if (tile_x) *tile_x = tx;
+    if (tile_y) *tile_y = ty;
+    if (zchunk) *zchunk = b->zchunk;
+    return CF_OK;
+}
+
+cf_status cf_batch_step(cf_batch *b, long long n) {
+    if (!b) return fail(CF_EINVAL, "null batch");
+    if (n < 0) return fail(CF_EINVAL, "negative step count");
+    if (n == 0) return CF_OK;
+    cf_status s = batch_run(b, n);
+    if (s != CF_OK) return s;
+    return batch_sync(b);
+}
+
+cf_status cf_batch_time(cf_batch *b, long long n, double *ms) {
+    if (!b || !ms || n <= 0) return fail(CF_EINVAL, "bad argument");
+    cudaEvent_t e0, e1;
+    CF_CUDA(cudaEventCreate(&e0));
+    CF_CUDA(cudaEventCreate(&e1));
+    CF_CUDA(cudaEventRecord(e0, b->stream));
+    cf_status s = batch_run(b, n);
+    CF_CUDA(cudaEventRecord(e1, b->stream));
+    CF_CUDA(cudaEventSynchronize(e1));
+    float t = 0.f;
+    CF_CUDA(cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != CF_OK) return s;
+    *ms = t;
+    return batch_sync(b);
+}
+
+cf_status cf_batch_autotune(cf_batch *b, int steps, int *tile_out, int *zchunk_out, double *ms_out) {
+    if (!b || steps < 2) return fail(CF_EINVAL, "bad argument");
+    const int zcs[3] = {1, 2, 4};
+    double best = 1e300;
+    int bt = b->tile, bz = b->zchunk;
+    for (int t = 0; t < CF_NTILES; ++t)
+        for (int zc : zcs) {
+            cf_status s = cf_batch_set_config(b, t, zc);
+            if (s != CF_OK) return s;
+            s = batch_run(b, 3);  // warm-up, graph capture
+            if (s != CF_OK) return s;
+            double ms = 0.0;
+            s = cf_batch_time(b, steps, &ms);
+            if (s != CF_OK) return s;
+            if (ms < best) { best = ms; bt = t; bz = zc; }
+        }
+    cf_status s = cf_batch_set_config(b, bt, bz);
+    if (s != CF_OK) return s;
+    if (tile_out) *tile_out = bt;
+    if (zchunk_out) *zchunk_out = bz;
+    if (ms_out) *ms_out = best / steps;
+    return CF_OK;
+}
+
+cf_status cf_batch_launch_count(const cf_batch *b, long long *n) {
+    if (!b || !n) return fail(CF_EINVAL, "null argument");
+    *n = b->launches_last;
     return CF_OK;
 }
 

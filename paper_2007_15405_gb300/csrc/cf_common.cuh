@@ -62,6 +62,7 @@ struct LBParams {
     long long N;            // nodes
     int zlo, zhi;           // fluid planes [zlo, zhi)
     int zchunk;             // planes walked per thread (grid.z = fluid planes / zchunk)
+    int zstride;            // batched passes: z slices of this lattice (a thread's plane stride)
     float itau[2], tau[2];  // 1/tau and tau per component
     float G;
     const void *__restrict__ src;    // post-collision populations of the last step
@@ -186,6 +187,20 @@ __host__ __device__ inline int wrapi(int a, int n) {
 namespace cf {
 void set_last_error(const char *msg);  // text returned by cf_last_error() on this thread
 cudaError_t launch_lb_step(const LBParams &p, int prec, cudaStream_t s);
+
+// Batched lattice passes: many independent lattices in one persistent launch
+// per pass.  The per-lattice parameters travel by value in the launch (one
+// table per step parity of a captured step pair); the work list holds
+// (lattice, x tile, y tile, z slice) items of the chosen tile shape.
+constexpr int CF_BATCH_MAX = 128;
+struct BatchTab {
+    LBParams lat[CF_BATCH_MAX];
+};
+constexpr int CF_NTILES = 6;  // tile shapes (x width, y depth) of the batched passes
+void lb_batch_tile(int tile, int *tx, int *ty);
+int lb_batch_resident(int tile, int prec);  // blocks of one pass resident on the device
+cudaError_t launch_lb_batch(const BatchTab &tab, const int4 *work, int nwork, int prec, int tile,
+                            cudaStream_t s);
 cudaError_t launch_init_film(void *f, float *f0, int prec, float2 *rho, long long N, int nx, int ny,
                              int nz, int wall, float h_top, float rmaj, float rmin, float rmix,
                              const double *jit, const uint8_t *inside, cudaStream_t s);

@@ -191,6 +191,18 @@ __device__ __forceinline__ bool node_of(const LBParams &p, int &x, int &y, int &
     return x < p.nx && y < p.ny;
 }
 
+// Density pass of one node: streamed populations -> rho, psi.
+template <typename T>
+__device__ __forceinline__ void density_node(const LBParams &p, const Deltas &d) {
+    float fa[Q], fb[Q];
+    pull<T>(p, d, fa, fb);
+    float ra = 0.f, rb = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) { ra += fa[i]; rb += fb[i]; }
+    p.rho[d.n] = make_float2(ra, rb);
+    p.psi[d.n] = make_float2(psi_of(ra), psi_of(rb));
+}
+
 // resident blocks per SM the density pass is compiled for: its 38 gathers are
 // issued back to back, so the register cap sets how many nodes are in flight
 #ifndef CF_DENSITY_MINB
@@ -204,16 +216,7 @@ __global__ void __launch_bounds__(BX *BY, CF_DENSITY_MINB) k_density(const LBPar
         atomicAdd(p.step_ctr, 1u);  // read by the collide pass that follows
     int x, y, z;
     if (!node_of(p, x, y, z)) return;
-    for (; z < p.zhi; z += gridDim.z) {
-        const Deltas d = deltas(p, x, y, z);
-        float fa[Q], fb[Q];
-        pull<T>(p, d, fa, fb);
-        float ra = 0.f, rb = 0.f;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) { ra += fa[i]; rb += fb[i]; }
-        p.rho[d.n] = make_float2(ra, rb);
-        p.psi[d.n] = make_float2(psi_of(ra), psi_of(rb));
-    }
+    for (; z < p.zhi; z += gridDim.z) density_node<T>(p, deltas(p, x, y, z));
 }
 
 // Shan-Chen force with decoupling, velocity shift, BGK, store.
@@ -376,6 +379,107 @@ cudaError_t launch_lb_step(const LBParams &p, int prec, cudaStream_t s) {
         k_collide<float><<<grid, block, 0, s>>>(p);
     }
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ batched passes
+// One persistent launch per pass for many independent lattices (a parameter
+// sweep).  Blocks stride over the work list of (lattice, x tile, y tile,
+// z slice) items; a thread walks the planes z0, z0 + zstride, ... of its
+// column.  The per-node arithmetic is that of the single-lattice passes, so
+// a lattice stepped in a batch follows the same trajectory as alone.  The
+// collide pass walks the list backwards (the tiles the density pass read last
+// are still in L2).  Tile shapes (x width x y depth, the block shape) are
+// compiled in and chosen by the autotuner of the batch.
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) k_density_batch(const __grid_constant__ BatchTab tab,
+                                                          const int4 *__restrict__ work, int nwork) {
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        const int4 it = __ldg(work + w);
+        const LBParams &p = tab.lat[it.x];
+        if (Pop<T>::shifted && it.y == 0 && it.z == 0 && it.w == 0 && threadIdx.x == 0 &&
+            threadIdx.y == 0)
+            atomicAdd(p.step_ctr, 1u);  // read by the collide pass that follows
+        const int x = it.y * TX + (int)threadIdx.x, y = it.z * TY + (int)threadIdx.y;
+        if (x >= p.nx || y >= p.ny) continue;
+        for (int z = p.zlo + it.w; z < p.zhi; z += p.zstride) density_node<T>(p, deltas(p, x, y, z));
+    }
+}
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY, (TX * TY >= 256 ? 2 : 5)) k_collide_batch(
+    const __grid_constant__ BatchTab tab, const int4 *__restrict__ work, int nwork) {
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        const int4 it = __ldg(work + (nwork - 1 - w));
+        const LBParams &p = tab.lat[it.x];
+        const int x = it.y * TX + (int)threadIdx.x, y = it.z * TY + (int)threadIdx.y;
+        if (x >= p.nx || y >= p.ny) continue;
+        for (int z = p.zlo + it.w; z < p.zhi; z += p.zstride) collide_node<T>(p, deltas(p, x, y, z));
+    }
+}
+
+namespace {
+constexpr int TILE_X[CF_NTILES] = {32, 32, 32, 64, 64, 128};
+constexpr int TILE_Y[CF_NTILES] = {2, 4, 8, 2, 4, 2};
+
+template <typename T, int TX, int TY>
+void batch_kernels(const void *&kd, const void *&kc) {
+    kd = reinterpret_cast<const void *>(&k_density_batch<T, TX, TY>);
+    kc = reinterpret_cast<const void *>(&k_collide_batch<T, TX, TY>);
+}
+
+template <typename T>
+void batch_kernels_t(int tile, const void *&kd, const void *&kc) {
+    switch (tile) {
+    case 0: batch_kernels<T, 32, 2>(kd, kc); break;
+    case 1: batch_kernels<T, 32, 4>(kd, kc); break;
+    case 2: batch_kernels<T, 32, 8>(kd, kc); break;
+    case 3: batch_kernels<T, 64, 2>(kd, kc); break;
+    case 4: batch_kernels<T, 64, 4>(kd, kc); break;
+    default: batch_kernels<T, 128, 2>(kd, kc); break;
+    }
+}
+
+void batch_kernel_ptrs(int tile, int prec, const void *&kd, const void *&kc) {
+    if (prec == P_F16) batch_kernels_t<__half>(tile, kd, kc);
+    else if (prec == P_BF16) batch_kernels_t<__nv_bfloat16>(tile, kd, kc);
+    else batch_kernels_t<float>(tile, kd, kc);
+}
+}  // namespace
+
+void lb_batch_tile(int tile, int *tx, int *ty) {
+    tile = std::min(std::max(tile, 0), CF_NTILES - 1);
+    *tx = TILE_X[tile];
+    *ty = TILE_Y[tile];
+}
+
+int lb_batch_resident(int tile, int prec) {
+    static int cache[3][CF_NTILES] = {};
+    tile = std::min(std::max(tile, 0), CF_NTILES - 1);
+    prec = std::min(std::max(prec, 0), 2);
+    if (cache[prec][tile] == 0) {
+        const void *kd, *kc;
+        batch_kernel_ptrs(tile, prec, kd, kc);
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kc, TILE_X[tile] * TILE_Y[tile], 0);
+        cache[prec][tile] = sms * std::max(per_sm, 1);
+    }
+    return cache[prec][tile];
+}
+
+cudaError_t launch_lb_batch(const BatchTab &tab, const int4 *work, int nwork, int prec, int tile,
+                            cudaStream_t s) {
+    tile = std::min(std::max(tile, 0), CF_NTILES - 1);
+    const void *kd, *kc;
+    batch_kernel_ptrs(tile, prec, kd, kc);
+    const dim3 block(TILE_X[tile], TILE_Y[tile]);
+    // enough blocks to cover the list, at most a few waves of resident blocks
+    const unsigned grid = (unsigned)std::max(1, std::min(nwork, 4 * lb_batch_resident(tile, prec)));
+    void *args[] = {const_cast<BatchTab *>(&tab), &work, &nwork};
+    cudaError_t e = cudaLaunchKernel(kd, dim3(grid), block, args, 0, s);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernel(kc, dim3(grid), block, args, 0, s);
 }
 
 // ------------------------------------------------------------ film set-up

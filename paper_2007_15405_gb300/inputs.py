@@ -171,3 +171,44 @@ def tiny_film(nx=16, ny=12, nz=20, radius=4.0, level=2, mode=MODE_FREE, steps=20
         h_top = zc - 0.3 * radius
     return Workload(f"tiny film {nx}x{ny}x{nz}", nx, ny, nz, h_top=h_top, capsules=[cap],
                     steps=steps, seed=seed, rep_dz=rep_dz)
+
+
+def sweep_point(d_over_R: float, kS: Optional[float], nx: int, ny: int, nz: int,
+                radius: float = 8.0, level: int = 3, steps: int = 20000, seed: int = 1234) -> Workload:
+    """One lattice of a distance x softness sweep: two capsules of radius R at
+    centre distance d = d_over_R * R along x, film 0.6R above the repulsive
+    plane; kS None is the rigid limit (frozen shape)."""
+    d = d_over_R * radius
+    zc = z_rest(radius) + _OFF[2]
+    cx, cy = nx / 2 + _OFF[0], ny / 2 + _OFF[1]
+    mode = MODE_FROZEN if kS is None else MODE_FREE
+    k = 5e-3 if kS is None else kS
+    caps = [CapsuleSpec(centre=(cx - d / 2, cy, zc), radius=radius, level=level, kS=k, mode=mode),
+            CapsuleSpec(centre=(cx + d / 2, cy, zc), radius=radius, level=level, kS=k, mode=mode)]
+    h_top = 0.5 + REP_DZ + 0.6 * radius
+    soft = "rigid" if kS is None else f"kS={kS:g}"
+    return Workload(f"sweep {nx}x{ny}x{nz} d={d_over_R:.2f}R {soft}", nx, ny, nz, h_top=h_top,
+                    capsules=caps, steps=steps, seed=seed)
+
+
+SWEEP_MODULI = (1e-3, 1e-2, 1e-1, None)  # shear moduli and the rigid limit
+
+
+def batched_sweep(n_dist: int = 16, moduli=SWEEP_MODULI, radius: float = 8.0, level: int = 3,
+                  steps: int = 20000) -> List[Workload]:
+    """Distance x softness sweep of independent lattices of uneven size: n_dist
+    distances in [2.2R, 6R] times the moduli (64 lattices by default).  The
+    lattice grows with the distance (x: 64..160) and with the modulus index
+    (y: 48..80, z: 48..64), from 147k to 819k nodes."""
+    out = []
+    for i in range(n_dist):
+        f = i / max(1, n_dist - 1)
+        d_over_R = 2.2 + f * (6.0 - 2.2)
+        nx = 64 + 8 * int(round(f * 12))
+        for j, kS in enumerate(moduli):
+            g = j / max(1, len(moduli) - 1)
+            ny = 48 + 8 * int(round(g * 4))
+            nz = 48 + 8 * int(round(g * 2))
+            out.append(sweep_point(d_over_R, kS, nx, ny, nz, radius=radius, level=level,
+                                   steps=steps, seed=1234 + 97 * i + j))
+    return out
