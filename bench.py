@@ -49,7 +49,9 @@ def parse():
                     help="population storage (arithmetic is float32 in every mode)")
     ap.add_argument("--sweep", action="store_true",
                     help="batched 64-lattice sweep instead of the capsule pair")
-    ap.add_argument("--tune-steps", type=int, default=4)
+    ap.add_argument("--tune-steps", type=int, default=8)
+    ap.add_argument("--sweep-n", type=int, default=16,
+                    help="distances of the sweep (x 4 moduli lattices)")
     return ap.parse_args()
 
 
@@ -310,7 +312,7 @@ def run_sweep(args):
     from paper_2007_15405_gb300 import inputs as I
     torch.cuda.set_device(0)
     prec = PRECISIONS[args.precision]
-    wls = I.batched_sweep()
+    wls = I.batched_sweep(n_dist=args.sweep_n)
     nodes = sum(w.nodes for w in wls)
     sims = [cfm.Simulation.from_workload(w, precision=prec) for w in wls]
     batch = cfm.Batch(sims)
@@ -347,7 +349,8 @@ def run_sweep(args):
         "config": {"workload": f"{len(wls)} lattices 64x48x48..160x80x64 ({nodes} nodes), two R=8 "
                                "level-3 capsules each, d in [2.2R, 6R] x kS in {1e-3, 1e-2, 1e-1, rigid}",
                    "population_storage": args.precision,
-                   "l2": "no flush: per-step working set of the 64 lattices ~8 GB exceeds the L2"},
+                   "l2": f"no flush: per-step working set {nodes * 304 / 1e9:.1f} GB of populations "
+                         "exceeds the 129 MB L2"},
         "autotune": dict(cfg, seconds=t_tune),
         "one_by_one": {"value": seq_value, "unit": "MLUPS", "steps": k},
         "speedup_vs_one_by_one": value / seq_value,

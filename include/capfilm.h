@@ -239,10 +239,12 @@ cf_status cf_batch_time(cf_batch *batch, long long n, double *ms);
 cf_status cf_batch_set_config(cf_batch *batch, int tile, int zchunk);
 cf_status cf_batch_config(const cf_batch *batch, int *tile, int *tile_x, int *tile_y, int *zchunk);
 
-/* Autotuner: times `steps` (>= 2) steps of the batch for every tile shape and
- * zchunk in {1, 2, 4}, keeps the fastest and returns it with its time per
- * step.  The trials are real steps: every context advances by 18 * (steps + 3)
- * steps. */
+/* Autotuner: for every tile shape and zchunk in {1, 2, 4} it replays the
+ * captured two-step graph once untimed and then ceil(steps/2) times timed
+ * (steps >= 2), keeps the fastest shape and returns it with its time per step.
+ * The trials are real steps: every context advances by
+ * 18 * (2 + 2 * ceil(steps / 2)) steps; the fields readout (cf_fields) is
+ * refreshed only by the next cf_batch_step. */
 cf_status cf_batch_autotune(cf_batch *batch, int steps, int *tile, int *zchunk, double *ms_per_step);
 
 /* Number of kernel launches issued by the last cf_batch_step / cf_batch_time. */

@@ -1058,27 +1058,44 @@ std::vector<int> batch_key(const cf_batch *b) {
     return k;
 }
 
+// the captured two-step graph for the contexts' current parities
+cf_status batch_graph(cf_batch *b) {
+    const std::vector<int> key = batch_key(b);
+    if (!b->graph || b->graph_key != key) {
+        if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+        cudaGraph_t g;
+        CF_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        int nlg = 0;
+        cf_status s1 = batch_enqueue_step(b, false, &nlg);
+        cf_status s2 = s1 == CF_OK ? batch_enqueue_step(b, false, &nlg) : s1;
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (s2 != CF_OK) return s2;
+        if (e != cudaSuccess) return fail(CF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(CF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        b->graph_key = key;
+        b->graph_launches = nlg;
+    }
+    return CF_OK;
+}
+
+// pairs graph replays (2 * pairs steps; the fields readout is not refreshed)
+cf_status batch_replay(cf_batch *b, int pairs) {
+    cf_status s = batch_graph(b);
+    if (s != CF_OK) return s;
+    for (int k = 0; k < pairs; ++k) CF_CUDA(cudaGraphLaunch(b->graph, b->stream));
+    for (cf_ctx *c : b->ctx) c->steps_done += 2 * pairs;
+    b->launches_last = (long long)pairs * b->graph_launches;
+    return CF_OK;
+}
+
 cf_status batch_run(cf_batch *b, long long n) {
     int nl = 0;
     long long left = n - 1;  // the last step records the fields
     if (left >= 2) {
-        const std::vector<int> key = batch_key(b);
-        if (!b->graph || b->graph_key != key) {
-            if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
-            cudaGraph_t g;
-            CF_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-            int nlg = 0;
-            cf_status s1 = batch_enqueue_step(b, false, &nlg);
-            cf_status s2 = s1 == CF_OK ? batch_enqueue_step(b, false, &nlg) : s1;
-            cudaError_t e = cudaStreamEndCapture(b->stream, &g);
-            if (s2 != CF_OK) return s2;
-            if (e != cudaSuccess) return fail(CF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-            e = cudaGraphInstantiate(&b->graph, g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) return fail(CF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-            b->graph_key = key;
-            b->graph_launches = nlg;
-        }
+        cf_status s = batch_graph(b);
+        if (s != CF_OK) return s;
         while (left >= 2) {
             CF_CUDA(cudaGraphLaunch(b->graph, b->stream));
             left -= 2;
@@ -1112,7 +1129,8 @@ extern "C" {
 
 cf_status cf_batch_create(cf_ctx *const *ctxs, int n, cf_batch **out) {
     if (!ctxs || !out || n <= 0) return fail(CF_EINVAL, "bad argument");
-    if (n > CF_BATCH_MAX) return fail(CF_EINVAL, "at most 128 contexts per batch");
+    if (n > CF_BATCH_MAX)
+        return fail(CF_EINVAL, "at most " + std::to_string(CF_BATCH_MAX) + " contexts per batch");
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i]) return fail(CF_EINVAL, "null context in batch");
         if (!ctxs[i]->film_set) return fail(CF_ESTATE, "cf_set_film must come before cf_batch_create");
@@ -1202,24 +1220,36 @@ cf_status cf_batch_time(cf_batch *b, long long n, double *ms) {
 cf_status cf_batch_autotune(cf_batch *b, int steps, int *tile_out, int *zchunk_out, double *ms_out) {
     if (!b || steps < 2) return fail(CF_EINVAL, "bad argument");
     const int zcs[3] = {1, 2, 4};
+    const int pairs = (steps + 1) / 2;
     double best = 1e300;
     int bt = b->tile, bz = b->zchunk;
-    for (int t = 0; t < CF_NTILES; ++t)
+    cudaEvent_t e0, e1;
+    CF_CUDA(cudaEventCreate(&e0));
+    CF_CUDA(cudaEventCreate(&e1));
+    cf_status s = CF_OK;
+    for (int t = 0; t < CF_NTILES && s == CF_OK; ++t)
         for (int zc : zcs) {
-            cf_status s = cf_batch_set_config(b, t, zc);
-            if (s != CF_OK) return s;
-            s = batch_run(b, 3);  // warm-up, graph capture
-            if (s != CF_OK) return s;
-            double ms = 0.0;
-            s = cf_batch_time(b, steps, &ms);
-            if (s != CF_OK) return s;
+            s = cf_batch_set_config(b, t, zc);
+            if (s == CF_OK) s = batch_replay(b, 1);  // capture and one untimed replay
+            if (s != CF_OK) break;
+            CF_CUDA(cudaEventRecord(e0, b->stream));
+            s = batch_replay(b, pairs);
+            if (s != CF_OK) break;
+            CF_CUDA(cudaEventRecord(e1, b->stream));
+            CF_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
             if (ms < best) { best = ms; bt = t; bz = zc; }
         }
-    cf_status s = cf_batch_set_config(b, bt, bz);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s == CF_OK) s = batch_sync(b);
+    if (s != CF_OK) return s;
+    s = cf_batch_set_config(b, bt, bz);
     if (s != CF_OK) return s;
     if (tile_out) *tile_out = bt;
     if (zchunk_out) *zchunk_out = bz;
-    if (ms_out) *ms_out = best / steps;
+    if (ms_out) *ms_out = best / (2 * pairs);
     return CF_OK;
 }
 

@@ -192,7 +192,11 @@ cudaError_t launch_lb_step(const LBParams &p, int prec, cudaStream_t s);
 // per pass.  The per-lattice parameters travel by value in the launch (one
 // table per step parity of a captured step pair); the work list holds
 // (lattice, x tile, y tile, z slice) items of the chosen tile shape.
-constexpr int CF_BATCH_MAX = 128;
+// (128 x 200 B fits the 32 KB launch-parameter limit; a build with a table of
+// at most 16 lattices keeps the launch parameters under 4 KB)
+#ifndef CF_BATCH_MAX
+#define CF_BATCH_MAX 128
+#endif
 struct BatchTab {
     LBParams lat[CF_BATCH_MAX];
 };

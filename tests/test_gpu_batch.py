@@ -117,7 +117,7 @@ def test_batch_autotune(cfm):
     cfg = b.autotune(steps=2)
     assert 0 <= cfg["tile"] < 6 and cfg["zchunk"] in (1, 2, 4) and cfg["ms_per_step"] > 0
     assert cfg["tile_x"] in (32, 64, 128) and cfg["tile_y"] in (2, 4, 8)
-    done = 18 * (2 + 3)
+    done = 18 * (2 + 2)
     ref = run_alone(cfm, wls, done)
     for s, a in zip(sims, ref):
         assert rel(s.populations().astype(np.float64), a.populations().astype(np.float64)) < TOL_SAME
@@ -153,8 +153,9 @@ def test_batch_rejects_bad_input(cfm):
 @pytest.mark.slow
 def test_sweep_of_64_lattices_sampled(cfm):
     """The full distance x softness sweep (64 lattices, 147k-819k nodes) in one
-    batch, 10 steps after autotuning: sampled lattices against their lone runs
-    (free capsules: within the free-run tolerances of the parity tests)."""
+    batch, 10 steps: sampled lattices against their lone runs (free capsules:
+    atomics sum the membrane forces in another order, so the comparison is at
+    the free-run tolerances of the parity tests)."""
     wls = I.batched_sweep()
     sims = [cfm.Simulation.from_workload(w) for w in wls]
     b = cfm.Batch(sims)
