@@ -190,7 +190,8 @@ cf_status cf_time_phases(cf_ctx *ctx, long long n, double ms[4]);
  * the same streaming, substrate bounce-back, Shan-Chen force and BGK collision
  * as cf_step does for a lattice without capsules.
  *   src, dst  device pointers, caller-owned, [2][19][nz][ny][nx] float
- *             populations (post-collision) in and out; must not overlap
+ *             populations (post-collision) in and out; must not overlap; with
+ *             a substrate (wall != 0) the plane z = 0 of dst is not written
  *   nx..G     as in cf_lattice_desc; stream: cudaStream_t or NULL
  * The per-node density scratch is a fixed array inside the library, sized for
  * at most 1048576 nodes (16 MiB, held by every GPU that loads the library until
@@ -205,6 +206,13 @@ cf_status cf_lattice_step_static(const float *src, float *dst, int nx, int ny, i
 
 /* Number of kernel launches issued by the last cf_step / cf_time_phases call. */
 cf_status cf_launch_count(cf_ctx *ctx, long long *n);
+
+/* Initial state from given densities: rhoA, rhoB host arrays [nz][ny][nx]
+ * (copied), populations at rest f_i = w_i rho (Eq. 5 with u = 0); the substrate
+ * plane stays empty.  An alternative to cf_set_film for states such as a
+ * predicted equilibrium (the learned warm start below); capsules must be added
+ * before.  Synchronous. */
+cf_status cf_set_densities(cf_ctx *ctx, const double *rhoA, const double *rhoB);
 
 /* ---------------------------------------------------------------- batches
  * A batch steps many independent contexts together, for parameter sweeps such
@@ -249,6 +257,44 @@ cf_status cf_batch_autotune(cf_batch *batch, int steps, int *tile, int *zchunk, 
 
 /* Number of kernel launches issued by the last cf_batch_step / cf_batch_time. */
 cf_status cf_batch_launch_count(const cf_batch *batch, long long *n);
+
+/* ------------------------------------------------------- learned warm start
+ * Kernels of a small 3-D convolutional network that predicts an equilibrated
+ * density field from the set-up (the paper has no counterpart; its long
+ * equilibration runs, Sec. 4, are what the prediction shortens).  All pointers
+ * are device pointers owned by the caller; calls are asynchronous on `stream`
+ * (cudaStream_t or NULL); bad arguments return CF_EINVAL.
+ *   activations  [n][c][nz][ny][nx] bfloat16 (x, y) or float (gradients)
+ *   weights      [cout][cin][27] bfloat16, tap = (dz+1)*9 + (dy+1)*3 + (dx+1)
+ *   bias         [cout] float
+ * A layer is a 3x3x3 convolution with zero padding and dilation dil,
+ * 1 <= cin, cout <= 16, followed by a ReLU when relu != 0; products are
+ * accumulated in float. */
+cf_status cf_conv3d_forward(const void *x, int n, int cin, int nz, int ny, int nx, const void *w,
+                            const float *b, int cout, int dil, int relu, void *y, void *stream);
+
+/* Backward of the same layer: gy = dL/dy (float, with respect to the layer's
+ * output after its ReLU), y = the forward output (for the ReLU mask; may be NULL
+ * when relu == 0).  Writes gx = dL/dx (float; skipped when gx is NULL) and ADDS
+ * dL/dw to gw [cout][cin][27] and dL/db to gb [cout] (float, caller zeroes). */
+cf_status cf_conv3d_backward(const void *x, int n, int cin, int nz, int ny, int nx, const void *w,
+                             int cout, int dil, const void *y, int relu, const float *gy, float *gx,
+                             float *gw, float *gb, void *stream);
+
+/* Masked mean squared error of m bfloat16 predictions against float targets:
+ * ADDS sum_i mask_i (p_i - t_i)^2 / msum to *loss (device double) and writes
+ * grad_i = 2 mask_i (p_i - t_i) / msum (float).  mask may be NULL (all ones). */
+cf_status cf_mse(const void *pred, const float *target, const float *mask, long long m, double msum,
+                 float *grad, double *loss, void *stream);
+
+/* Adam step t (>= 1) on float master weights w with moments m1, m2 (float, n
+ * each), bias-corrected; writes the bfloat16 copy w_bf16 when not NULL. */
+cf_status cf_adam(float *w, void *w_bf16, const float *g, float *m1, float *m2, long long n, double lr,
+                  double b1, double b2, double eps, int t, void *stream);
+
+/* Conversions float <-> bfloat16 (round to nearest even), n elements. */
+cf_status cf_to_bf16(const float *x, void *y, long long n, void *stream);
+cf_status cf_from_bf16(const void *x, float *y, long long n, void *stream);
 
 #ifdef __cplusplus
 }

@@ -48,17 +48,20 @@ def test_static_scratch_step_matches_context_step(env, wall):
 
     stream = torch.cuda.current_stream()
     a = torch.from_numpy(f0).cuda()
-    b = torch.empty_like(a)
+    # the substrate plane z = 0 of the output is never written: start it from
+    # zeros like the context's own buffers, and compare the fluid planes
+    b = torch.zeros_like(a)
     # two calls in a row through the C ABI, device buffers owned by the caller
     cfm.lattice_step_static(a.data_ptr(), b.data_ptr(), wl.nx, wl.ny, wl.nz, wall, wl.tau, wl.G,
                             stream.cuda_stream)
     cfm.lattice_step_static(b.data_ptr(), a.data_ptr(), wl.nx, wl.ny, wl.nz, wall, wl.tau, wl.G,
                             stream.cuda_stream)
     torch.cuda.synchronize()
-    g1 = b.cpu().numpy().astype(np.float64)
-    g2 = a.cpu().numpy().astype(np.float64)
-    assert rel(g1, f1.astype(np.float64)) < TOL
-    assert rel(g2, f2.astype(np.float64)) < TOL
+    z0 = 1 if wall else 0
+    g1 = b.cpu().numpy().astype(np.float64)[:, :, z0:]
+    g2 = a.cpu().numpy().astype(np.float64)[:, :, z0:]
+    assert rel(g1, f1.astype(np.float64)[:, :, z0:]) < TOL
+    assert rel(g2, f2.astype(np.float64)[:, :, z0:]) < TOL
 
 
 def test_static_scratch_rejects_oversized_lattice(env):
