@@ -84,6 +84,18 @@ def load_library(path: Optional[str] = None):
         "cf_time_phases": [C.c_void_p, C.c_longlong, _dp],
         "cf_lattice_step_static": [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
                                    _dp, C.c_double, C.c_void_p],
+        "cf_set_densities": [C.c_void_p, _dp, _dp],
+        "cf_conv3d_forward": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                              C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+        "cf_conv3d_backward": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                               C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                               C.c_void_p, C.c_void_p, C.c_void_p],
+        "cf_mse": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_double, C.c_void_p,
+                   C.c_void_p, C.c_void_p],
+        "cf_adam": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong,
+                    C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_void_p],
+        "cf_to_bf16": [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p],
+        "cf_from_bf16": [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p],
         "cf_batch_create": [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)],
         "cf_batch_destroy": [C.c_void_p],
         "cf_batch_step": [C.c_void_p, C.c_longlong],
@@ -109,7 +121,8 @@ def exported_symbols():
             "cf_meniscus_field", "cf_meniscus_profile", "cf_cuts", "cf_launch_count",
             "cf_time_phases", "cf_lattice_step_static", "cf_batch_create", "cf_batch_destroy",
             "cf_batch_step", "cf_batch_time", "cf_batch_set_config", "cf_batch_config",
-            "cf_batch_autotune", "cf_batch_launch_count"]
+            "cf_batch_autotune", "cf_batch_launch_count", "cf_set_densities", "cf_conv3d_forward",
+            "cf_conv3d_backward", "cf_mse", "cf_adam", "cf_to_bf16", "cf_from_bf16"]
 
 
 def _check(rc):
@@ -233,6 +246,13 @@ class Simulation:
 
     def step(self, n=1):
         _check(_lib.cf_step(self._h, int(n)))
+
+    def set_densities(self, rhoA, rhoB):
+        """Initial state at rest from density fields [nz][ny][nx] (cf_set_densities)."""
+        a = np.ascontiguousarray(rhoA, dtype=np.float64).reshape(-1)
+        b = np.ascontiguousarray(rhoB, dtype=np.float64).reshape(-1)
+        assert a.size == self.N and b.size == self.N
+        _check(_lib.cf_set_densities(self._h, _ptr(a), _ptr(b)))
 
     @property
     def stream(self):

@@ -686,6 +686,22 @@ cf_status cf_set_film(cf_ctx *c, double h_top, double rmaj, double rmin, double 
     return sync_ok(c);
 }
 
+cf_status cf_set_densities(cf_ctx *c, const double *rhoA, const double *rhoB) {
+    if (!c || !rhoA || !rhoB) return fail(CF_EINVAL, "null argument");
+    const long long N = c->N;
+    if (!c->jit) {
+        c->jit = (double *)dalloc(c, sizeof(double) * 2 * N);
+        if (!c->jit) return fail(CF_ENOMEM, "device allocation failed (densities)");
+        c->allocations.pop_back();  // freed explicitly
+    }
+    CF_CUDA(cudaMemcpyAsync(c->jit, rhoA, sizeof(double) * N, cudaMemcpyHostToDevice, c->stream));
+    CF_CUDA(cudaMemcpyAsync(c->jit + N, rhoB, sizeof(double) * N, cudaMemcpyHostToDevice, c->stream));
+    CF_CUDA(launch_init_dens(c->f[c->fpar], c->f0[c->fpar], c->d.precision, c->rho[c->fpar], N, c->d.nx,
+                             c->d.ny, c->d.wall, c->jit, c->stream));
+    c->film_set = true;
+    return sync_ok(c);
+}
+
 cf_status cf_step(cf_ctx *c, long long n) {
     if (!c) return fail(CF_EINVAL, "null context");
     if (!c->film_set) return fail(CF_ESTATE, "cf_set_film must come before cf_step");

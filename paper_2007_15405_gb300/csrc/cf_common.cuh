@@ -212,6 +212,8 @@ cudaError_t launch_inside(const uint32_t *mask, uint8_t *inside, int nx, int ny,
                           cudaStream_t s);
 cudaError_t launch_meniscus(const float *out, const uint8_t *inside, float *h, int nx, int ny,
                             int nz, int wall, cudaStream_t s);
+cudaError_t launch_init_dens(void *f, float *f0, int prec, float2 *rho, long long N, int nx, int ny,
+                             int wall, const double *rAB, cudaStream_t s);
 cudaError_t launch_mass(const void *f, const float *f0, int prec, const float2 *rho, long long N,
                         double *m2, cudaStream_t s);
 // membrane kernels 1-3 (positions only) and 4-5 (after the lattice update)

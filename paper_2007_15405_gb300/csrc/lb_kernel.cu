@@ -484,6 +484,10 @@ cudaError_t launch_lb_batch(const BatchTab &tab, const int4 *work, int nwork, in
 
 // ------------------------------------------------------------ film set-up
 template <typename T>
+__device__ __forceinline__ void init_rest(T *f, float *f0, float2 *rho, long long N, long long n,
+                                          const double (&r)[2]);
+
+template <typename T>
 __global__ void k_init_film(T *f, float *f0, float2 *rho, long long N, int nx, int ny, int nz,
                            int wall, float h_top, float rmaj, float rmin, float rmix,
                            const double *jit, const uint8_t *inside) {
@@ -500,6 +504,14 @@ __global__ void k_init_film(T *f, float *f0, float2 *rho, long long N, int nx, i
         else { r[0] = rmin; r[1] = rmaj; }
         if (jit) { r[0] += jit[n]; r[1] += jit[N + n]; }
     }
+    init_rest<T>(f, f0, rho, N, n, r);
+}
+
+// Rest state f_i = w_i rho of node n for the densities r[2] (16-bit storage:
+// zero offsets and the float rest population from the mass balance).
+template <typename T>
+__device__ __forceinline__ void init_rest(T *f, float *f0, float2 *rho, long long N, long long n,
+                                          const double (&r)[2]) {
     float ra = 0.f, rb = 0.f;
     if (Pop<T>::shifted) {  // rest state: zero offsets from w_i rho, float rest populations
         ra = (float)r[0];
@@ -526,6 +538,30 @@ __global__ void k_init_film(T *f, float *f0, float2 *rho, long long N, int nx, i
         }
     }
     rho[n] = make_float2(ra, rb);  // density of the initial state
+}
+
+// Rest state from given densities rAB [2][N] (the substrate plane empty).
+template <typename T>
+__global__ void k_init_dens(T *f, float *f0, float2 *rho, long long N, int nx, int ny, int wall,
+                            const double *rAB) {
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int z = (int)(n / ((long long)nx * ny));
+    double r[2] = {rAB[n], rAB[N + n]};
+    if (wall && z == 0) r[0] = r[1] = 0.0;
+    init_rest<T>(f, f0, rho, N, n, r);
+}
+
+cudaError_t launch_init_dens(void *f, float *f0, int prec, float2 *rho, long long N, int nx, int ny,
+                             int wall, const double *rAB, cudaStream_t s) {
+    const unsigned g = (unsigned)((N + 255) / 256);
+    if (prec == P_F16)
+        k_init_dens<<<g, 256, 0, s>>>(static_cast<__half *>(f), f0, rho, N, nx, ny, wall, rAB);
+    else if (prec == P_BF16)
+        k_init_dens<<<g, 256, 0, s>>>(static_cast<__nv_bfloat16 *>(f), f0, rho, N, nx, ny, wall, rAB);
+    else
+        k_init_dens<<<g, 256, 0, s>>>(static_cast<float *>(f), f0, rho, N, nx, ny, wall, rAB);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_init_film(void *f, float *f0, int prec, float2 *rho, long long N, int nx, int ny,

@@ -1,0 +1,254 @@
+"""Learned warm start: a small 3-D convolutional network that predicts the
+equilibrated density field of a film with capsules from its set-up, so that
+the coupled run starts near equilibrium instead of from the flat film.
+
+Every layer, gradient and optimiser step runs in the library's CUDA kernels
+(cf_conv3d_forward / cf_conv3d_backward / cf_mse / cf_adam, bfloat16
+activations and weights, float32 accumulation and master weights); this
+module only holds the device buffers (torch tensors) and orders the calls.
+
+Network: five 3x3x3 convolutions 4 -> 16 -> 16 -> 16 -> 16 -> 1 with
+dilations 1, 2, 4, 8, 1 (receptive field 33 nodes), ReLU between them.
+Inputs per lattice node:
+  0  capsule interior (1 inside a membrane, from the cut links)
+  1  phi of the flat initial film, phi = (rho_A - rho_B) / (rho_maj - rho_min)
+  2  z / nz
+  3  log10(kS) + 2 (shear modulus of the capsule)
+Output: the equilibrium correction d phi = phi_eq - phi_film on fluid nodes.
+The predicted state is phi_film + d phi outside the capsules (clipped to
+[-1, 1]), the film values inside, turned into densities with the bulk sum
+rho_A + rho_B = rho_maj + rho_min.
+
+The warm-started run judges its own start: it advances two short windows and
+falls back to the flat film when densities turn non-finite or negative, a
+velocity exceeds a low-Mach limit, or the density change of the second window
+exceeds 1.5 times that of the first (the residual grows instead of decaying).
+"""
+import ctypes as C
+import math
+
+import numpy as np
+
+from . import capfilm as cfm
+from . import inputs as I
+
+LAYERS = [(4, 16, 1, True), (16, 16, 2, True), (16, 16, 4, True), (16, 16, 8, True), (16, 1, 1, False)]
+N_IN = 4
+
+
+def _p(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def features(sim, wl):
+    """Network inputs [4][nz][ny][nx] (float32) and the fluid mask for lattice wl."""
+    nz, ny, nx = wl.nz, wl.ny, wl.nx
+    _, _, inside = sim.cuts()
+    ins = inside.reshape(nz, ny, nx).astype(np.float32)
+    z = np.arange(nz, dtype=np.float32)[:, None, None] * np.ones((1, ny, nx), np.float32)
+    zm = math.floor(wl.h_top + 0.5)
+    phi = np.where(z < zm, 1.0, np.where(z == zm, 0.0, -1.0)).astype(np.float32)
+    phi = np.where(ins > 0, -1.0, phi)
+    if wl.wall:
+        phi[0] = 0.0
+    ks = wl.capsules[0].kS if wl.capsules else 1e-2
+    soft = np.full((nz, ny, nx), math.log10(ks) + 2.0, np.float32)
+    x = np.stack([ins, phi, z / nz, soft]).astype(np.float32)
+    mask = ((ins == 0) & (z >= (1 if wl.wall else 0))).astype(np.float32)
+    return x, mask
+
+
+def phi_of(sim):
+    """phi = (rho_A - rho_B) / (rho_maj - rho_min) of the current state."""
+    rho, _ = sim.fields()
+    return ((rho[0] - rho[1]) / (I.RHO_MAJ - I.RHO_MIN)).astype(np.float32)
+
+
+def densities_from_phi(phi, x, wl):
+    """rho_A, rho_B [nz][ny][nx] for a phi field: the film state inside the
+    capsules, empty substrate, phi clipped to [-1, 1] elsewhere with the bulk
+    sum rho_A + rho_B = rho_maj + rho_min."""
+    S, D = I.RHO_MAJ + I.RHO_MIN, I.RHO_MAJ - I.RHO_MIN
+    p = np.clip(phi, -1.0, 1.0).astype(np.float64)
+    p = np.where(x[0] > 0, -1.0, p)
+    ra, rb = 0.5 * (S + p * D), 0.5 * (S - p * D)
+    if wl.wall:
+        ra[0] = rb[0] = 0.0
+    return ra, rb
+
+
+class WarmNet:
+    """The network's parameters and buffers on the GPU (torch tensors)."""
+
+    def __init__(self, seed=0, device="cuda"):
+        import torch
+        self.torch = torch
+        self.dev = device
+        rng = np.random.default_rng(seed)
+        self.w, self.b, self.wb = [], [], []
+        for cin, cout, dil, relu in LAYERS:
+            std = math.sqrt(2.0 / (27 * cin)) if relu else math.sqrt(1.0 / (27 * cin))
+            w = rng.standard_normal((cout, cin, 27)).astype(np.float32) * std
+            if not relu:
+                w *= 0.1
+            self.w.append(torch.from_numpy(w).to(device))
+            self.b.append(torch.zeros(cout, dtype=torch.float32, device=device))
+            self.wb.append(torch.empty(cout * cin * 27, dtype=torch.bfloat16, device=device))
+        self.stream = torch.cuda.current_stream().cuda_stream
+        self._sync_bf16()
+        self.mw = [torch.zeros_like(w) for w in self.w]
+        self.vw = [torch.zeros_like(w) for w in self.w]
+        self.mb = [torch.zeros_like(b) for b in self.b]
+        self.vb = [torch.zeros_like(b) for b in self.b]
+        self.t = 0
+
+    @property
+    def n_params(self):
+        return sum(w.numel() + b.numel() for w, b in zip(self.w, self.b))
+
+    def _sync_bf16(self):
+        L = cfm.load_library()
+        for w, wb in zip(self.w, self.wb):
+            cfm._check(L.cf_to_bf16(_p(w), _p(wb), w.numel(), C.c_void_p(self.stream)))
+
+    def to_bf16(self, a):
+        torch = self.torch
+        t = torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(self.dev)
+        out = torch.empty(t.numel(), dtype=torch.bfloat16, device=self.dev)
+        cfm._check(cfm._lib.cf_to_bf16(_p(t), _p(out), t.numel(), C.c_void_p(self.stream)))
+        return out
+
+    def forward(self, xb, shape):
+        """xb: bfloat16 device tensor [n][4][nz][ny][nx] (flat); returns the
+        activations of every layer (bfloat16, flat) with the input first."""
+        torch = self.torch
+        n, nz, ny, nx = shape
+        acts = [xb]
+        for (cin, cout, dil, relu), wb, b in zip(LAYERS, self.wb, self.b):
+            y = torch.empty(n * cout * nz * ny * nx, dtype=torch.bfloat16, device=self.dev)
+            cfm._check(cfm._lib.cf_conv3d_forward(_p(acts[-1]), n, cin, nz, ny, nx, _p(wb), _p(b), cout,
+                                                  dil, int(relu), _p(y), C.c_void_p(self.stream)))
+            acts.append(y)
+        return acts
+
+    def predict(self, x):
+        """d phi for one lattice: x [4][nz][ny][nx] -> [nz][ny][nx] float32."""
+        torch = self.torch
+        nz, ny, nx = x.shape[1:]
+        acts = self.forward(self.to_bf16(x), (1, nz, ny, nx))
+        out = torch.empty(nz * ny * nx, dtype=torch.float32, device=self.dev)
+        cfm._check(cfm._lib.cf_from_bf16(_p(acts[-1]), _p(out), out.numel(), C.c_void_p(self.stream)))
+        return out.cpu().numpy().reshape(nz, ny, nx)
+
+    def train_step(self, xb, target, mask, shape, lr):
+        """One Adam step on a batch: xb bfloat16 inputs, target / mask float
+        device tensors [n][1][nz][ny][nx]; returns the loss (masked MSE).  Each
+        layer's input gradient is taken with its weights before they move."""
+        torch = self.torch
+        L = cfm._lib
+        st = C.c_void_p(self.stream)
+        n, nz, ny, nx = shape
+        acts = self.forward(xb, shape)
+        m = n * nz * ny * nx
+        g = torch.empty(m, dtype=torch.float32, device=self.dev)
+        loss = torch.zeros(1, dtype=torch.float64, device=self.dev)
+        msum = float(mask.sum().item())
+        cfm._check(L.cf_mse(_p(acts[-1]), _p(target), _p(mask), m, msum, _p(g), _p(loss), st))
+        self.t += 1
+        for k in reversed(range(len(LAYERS))):
+            cin, cout, dil, relu = LAYERS[k]
+            gw = torch.zeros_like(self.w[k])
+            gb = torch.zeros_like(self.b[k])
+            gx = torch.empty(n * cin * nz * ny * nx, dtype=torch.float32, device=self.dev) if k > 0 else None
+            cfm._check(L.cf_conv3d_backward(_p(acts[k]), n, cin, nz, ny, nx, _p(self.wb[k]), cout, dil,
+                                            _p(acts[k + 1]), int(relu), _p(g), _p(gx), _p(gw), _p(gb), st))
+            cfm._check(L.cf_adam(_p(self.w[k]), _p(self.wb[k]), _p(gw), _p(self.mw[k]), _p(self.vw[k]),
+                                 self.w[k].numel(), lr, 0.9, 0.999, 1e-8, self.t, st))
+            cfm._check(L.cf_adam(_p(self.b[k]), None, _p(gb), _p(self.mb[k]), _p(self.vb[k]),
+                                 self.b[k].numel(), lr, 0.9, 0.999, 1e-8, self.t, st))
+            g = gx
+        return float(loss.item())
+
+    def state(self):
+        out = {f"w{k}": w.cpu().numpy() for k, w in enumerate(self.w)}
+        out.update({f"b{k}": b.cpu().numpy() for k, b in enumerate(self.b)})
+        return out
+
+    def load(self, st):
+        torch = self.torch
+        for k in range(len(LAYERS)):
+            self.w[k].copy_(torch.from_numpy(st[f"w{k}"]))
+            self.b[k].copy_(torch.from_numpy(st[f"b{k}"]))
+        self._sync_bf16()
+
+
+def equilibrate(wls, steps, tile=1, zchunk=1):
+    """Plain runs of the lattices (one batch) for `steps` steps; returns the
+    simulations (with their final state)."""
+    sims = [cfm.Simulation.from_workload(w) for w in wls]
+    batch = cfm.Batch(sims)
+    batch.set_config(tile, zchunk)
+    batch.step(steps)
+    batch.close()
+    return sims
+
+
+def dataset(wls, steps):
+    """(inputs, targets, masks) of equilibrated lattices generated by the method."""
+    sims = equilibrate(wls, steps)
+    xs, ts, ms = [], [], []
+    for s, w in zip(sims, wls):
+        x, mask = features(s, w)
+        t = (phi_of(s) - x[1]) * mask
+        xs.append(x)
+        ts.append(t[None])
+        ms.append(mask[None])
+        s.close()
+    return np.stack(xs), np.stack(ts), np.stack(ms)
+
+
+def train(net, X, T, M, steps=300, batch=8, lr=2e-3, seed=0, log=None):
+    """Adam on mini-batches drawn from the training arrays; returns the losses."""
+    torch = net.torch
+    rng = np.random.default_rng(seed)
+    n = X.shape[0]
+    shape_v = X.shape[2:]
+    losses = []
+    for it in range(steps):
+        idx = rng.choice(n, size=min(batch, n), replace=False)
+        xb = net.to_bf16(X[idx])
+        t = torch.from_numpy(np.ascontiguousarray(T[idx], np.float32)).to(net.dev).reshape(-1)
+        m = torch.from_numpy(np.ascontiguousarray(M[idx], np.float32)).to(net.dev).reshape(-1)
+        loss = net.train_step(xb, t, m, (len(idx),) + shape_v, lr)
+        losses.append(loss)
+        if log and it % 50 == 0:
+            log(f"step {it}: loss {loss:.4e}")
+    return losses
+
+
+def warm_start(sim, wl, net, window=25, u_limit=0.1, grow=1.5):
+    """Set the predicted state and judge it over two windows of `window`
+    steps; falls back to the flat film when the residual misbehaves.
+    Returns (used_warm, steps_taken)."""
+    x, _ = features(sim, wl)
+    phi = x[1] + net.predict(x)
+    ra, rb = densities_from_phi(phi, x, wl)
+    sim.set_densities(ra, rb)
+    ok = True
+    sim.step(1)
+    r0, _ = sim.fields()
+    sim.step(window)
+    r1, u1 = sim.fields()
+    sim.step(window)
+    r2, u2 = sim.fields()
+    for r, u in ((r1, u1), (r2, u2)):
+        if not (np.isfinite(r).all() and np.isfinite(u).all()) or (r < 0).any() or np.abs(u).max() > u_limit:
+            ok = False
+    if ok:
+        d1 = np.abs(r1 - r0).mean()
+        d2 = np.abs(r2 - r1).mean()
+        ok = d2 <= grow * d1
+    if ok:
+        return True, 2 * window + 1
+    sim.set_film(wl.h_top, I.RHO_MAJ, I.RHO_MIN, I.RHO_MIX, wl.jitter())
+    return False, 2 * window + 1

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_symbols():
     hdr = open(os.path.join(ROOT, "include", "capfilm.h")).read()
     hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
-    return sorted(set(re.findall(r"\b(cf_[a-z_]+)\s*\(", hdr)))
+    return sorted(set(re.findall(r"\b(cf_[a-z0-9_]+)\s*\(", hdr)))
 
 
 @pytest.fixture(scope="module")
