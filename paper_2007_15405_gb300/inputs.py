@@ -214,11 +214,12 @@ def batched_sweep(n_dist: int = 16, moduli=SWEEP_MODULI, radius: float = 8.0, le
     return out
 
 
-def warm_dataset(n: int, seed: int = 0, nx: int = 48, ny: int = 32, nz: int = 32) -> List[Workload]:
-    """Set-ups for the learned warm start: one free capsule (R in [5, 7],
-    level-2 icosphere) at a random position protruding through a film of random
-    height (0.3R..0.9R above the repulsive plane), shear modulus log-uniform in
-    [1e-3, 1e-1]."""
+def warm_dataset(n: int, seed: int = 0, nx: int = 48, ny: int = 32, nz: int = 32,
+                 mode: int = MODE_FREE) -> List[Workload]:
+    """Set-ups for the learned warm start: one capsule (R in [5, 7], level-3
+    icosphere; free by default, or fixed: the rigid particles of Sec. 4.1) at a
+    random position protruding through a film of random height (0.3R..0.9R
+    above the repulsive plane), shear modulus log-uniform in [3e-3, 1e-1]."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n):
@@ -226,9 +227,9 @@ def warm_dataset(n: int, seed: int = 0, nx: int = 48, ny: int = 32, nz: int = 32
         cx = float(rng.uniform(R + 4, nx - R - 4)) + _OFF[0]
         cy = float(rng.uniform(R + 4, ny - R - 4)) + _OFF[1]
         zc = z_rest(R) + _OFF[2]
-        kS = float(10 ** rng.uniform(-3, -1))
+        kS = float(10 ** rng.uniform(math.log10(3e-3), -1))
         h_top = 0.5 + REP_DZ + float(rng.uniform(0.3, 0.9)) * R
-        cap = CapsuleSpec(centre=(cx, cy, zc), radius=R, level=2, kS=kS, mode=MODE_FREE)
+        cap = CapsuleSpec(centre=(cx, cy, zc), radius=R, level=3, kS=kS, mode=mode)
         out.append(Workload(f"warm {i} R={R:.2f} kS={kS:.1e} h={h_top:.2f}", nx, ny, nz, h_top=h_top,
                             capsules=[cap], steps=1, seed=5000 + i))
     return out

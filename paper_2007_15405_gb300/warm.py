@@ -7,17 +7,19 @@ Every layer, gradient and optimiser step runs in the library's CUDA kernels
 activations and weights, float32 accumulation and master weights); this
 module only holds the device buffers (torch tensors) and orders the calls.
 
-Network: five 3x3x3 convolutions 4 -> 16 -> 16 -> 16 -> 16 -> 1 with
+Network: five 3x3x3 convolutions 4 -> 16 -> 16 -> 16 -> 16 -> 2 with
 dilations 1, 2, 4, 8, 1 (receptive field 33 nodes), ReLU between them.
 Inputs per lattice node:
   0  capsule interior (1 inside a membrane, from the cut links)
   1  phi of the flat initial film, phi = (rho_A - rho_B) / (rho_maj - rho_min)
   2  z / nz
   3  log10(kS) + 2 (shear modulus of the capsule)
-Output: the equilibrium correction d phi = phi_eq - phi_film on fluid nodes.
-The predicted state is phi_film + d phi outside the capsules (clipped to
-[-1, 1]), the film values inside, turned into densities with the bulk sum
-rho_A + rho_B = rho_maj + rho_min.
+Outputs: the equilibrium corrections of both densities on fluid nodes,
+(rho_c,eq - rho_c,film) / (rho_maj - rho_min) for c = A, B (the bulk
+composition relaxes too, not only the interface).  The predicted state is the
+film plus these corrections outside the capsules (at least 1e-3), the film
+values inside; each component is then scaled on the fluid outside the
+capsules to the flat film's mass, which the run conserves.
 
 The warm-started run judges its own start: it advances two short windows and
 falls back to the flat film when densities turn non-finite or negative, a
@@ -32,8 +34,9 @@ import numpy as np
 from . import capfilm as cfm
 from . import inputs as I
 
-LAYERS = [(4, 16, 1, True), (16, 16, 2, True), (16, 16, 4, True), (16, 16, 8, True), (16, 1, 1, False)]
-N_IN = 4
+LAYERS = [(4, 16, 1, True), (16, 16, 2, True), (16, 16, 4, True), (16, 16, 8, True), (16, 2, 1, False)]
+N_IN, N_OUT = 4, 2
+D_RHO = I.RHO_MAJ - I.RHO_MIN  # scale of the outputs
 
 
 def _p(t):
@@ -64,16 +67,42 @@ def phi_of(sim):
     return ((rho[0] - rho[1]) / (I.RHO_MAJ - I.RHO_MIN)).astype(np.float32)
 
 
-def densities_from_phi(phi, x, wl):
-    """rho_A, rho_B [nz][ny][nx] for a phi field: the film state inside the
-    capsules, empty substrate, phi clipped to [-1, 1] elsewhere with the bulk
-    sum rho_A + rho_B = rho_maj + rho_min."""
-    S, D = I.RHO_MAJ + I.RHO_MIN, I.RHO_MAJ - I.RHO_MIN
-    p = np.clip(phi, -1.0, 1.0).astype(np.float64)
-    p = np.where(x[0] > 0, -1.0, p)
-    ra, rb = 0.5 * (S + p * D), 0.5 * (S - p * D)
+def target_of(sim, x, wl):
+    """Network target [2][nz][ny][nx]: density corrections from the film state."""
+    rho, _ = sim.fields()
+    fa, fb = film_densities(x, wl)
+    return np.stack([(rho[0] - fa) / D_RHO, (rho[1] - fb) / D_RHO]).astype(np.float32)
+
+
+def film_densities(x, wl):
+    """The flat film's densities (without jitter) from its phi channel:
+    majority / minority away from the interface, the mixed value in its plane."""
+    phi = x[1]
+    ra = np.where(phi > 0.5, I.RHO_MAJ, np.where(phi < -0.5, I.RHO_MIN, I.RHO_MIX)).astype(np.float64)
+    rb = np.where(phi > 0.5, I.RHO_MIN, np.where(phi < -0.5, I.RHO_MAJ, I.RHO_MIX)).astype(np.float64)
     if wl.wall:
         ra[0] = rb[0] = 0.0
+    return ra, rb
+
+
+def densities_from_prediction(d, x, wl):
+    """rho_A, rho_B [nz][ny][nx] from predicted corrections d [2][...]: the
+    film plus the corrections on the fluid outside the capsules (at least
+    1e-3), the film inside and on the substrate; then each component is scaled
+    on the fluid outside the capsules so that its total mass equals the flat
+    film's (masses are conserved, so a start with other masses relaxes to
+    another equilibrium)."""
+    fa, fb = film_densities(x, wl)
+    free = x[0] == 0
+    if wl.wall:
+        free[0] = False
+    ra = np.where(free, np.maximum(fa + D_RHO * d[0], 1e-3), fa)
+    rb = np.where(free, np.maximum(fb + D_RHO * d[1], 1e-3), fb)
+    for r, f in ((ra, fa), (rb, fb)):
+        target = f[free].sum()
+        have = r[free].sum()
+        if have > 0:
+            r[free] *= target / have
     return ra, rb
 
 
@@ -132,24 +161,25 @@ class WarmNet:
         return acts
 
     def predict(self, x):
-        """d phi for one lattice: x [4][nz][ny][nx] -> [nz][ny][nx] float32."""
+        """Density corrections for one lattice: x [4][nz][ny][nx] -> [2][nz][ny][nx] float32."""
         torch = self.torch
         nz, ny, nx = x.shape[1:]
         acts = self.forward(self.to_bf16(x), (1, nz, ny, nx))
-        out = torch.empty(nz * ny * nx, dtype=torch.float32, device=self.dev)
+        out = torch.empty(N_OUT * nz * ny * nx, dtype=torch.float32, device=self.dev)
         cfm._check(cfm._lib.cf_from_bf16(_p(acts[-1]), _p(out), out.numel(), C.c_void_p(self.stream)))
-        return out.cpu().numpy().reshape(nz, ny, nx)
+        return out.cpu().numpy().reshape(N_OUT, nz, ny, nx)
 
     def train_step(self, xb, target, mask, shape, lr):
         """One Adam step on a batch: xb bfloat16 inputs, target / mask float
-        device tensors [n][1][nz][ny][nx]; returns the loss (masked MSE).  Each
+        device tensors [n][2][nz][ny][nx]; returns the loss (masked MSE).  Each
         layer's input gradient is taken with its weights before they move."""
         torch = self.torch
         L = cfm._lib
         st = C.c_void_p(self.stream)
         n, nz, ny, nx = shape
         acts = self.forward(xb, shape)
-        m = n * nz * ny * nx
+        m = n * LAYERS[-1][1] * nz * ny * nx  # every output of the last layer
+        assert target.numel() == m and mask.numel() == m
         g = torch.empty(m, dtype=torch.float32, device=self.dev)
         loss = torch.zeros(1, dtype=torch.float64, device=self.dev)
         msum = float(mask.sum().item())
@@ -199,10 +229,10 @@ def dataset(wls, steps):
     xs, ts, ms = [], [], []
     for s, w in zip(sims, wls):
         x, mask = features(s, w)
-        t = (phi_of(s) - x[1]) * mask
+        t = target_of(s, x, w) * mask[None]
         xs.append(x)
-        ts.append(t[None])
-        ms.append(mask[None])
+        ts.append(t)
+        ms.append(np.stack([mask] * N_OUT))
         s.close()
     return np.stack(xs), np.stack(ts), np.stack(ms)
 
@@ -231,8 +261,7 @@ def warm_start(sim, wl, net, window=25, u_limit=0.1, grow=1.5):
     steps; falls back to the flat film when the residual misbehaves.
     Returns (used_warm, steps_taken)."""
     x, _ = features(sim, wl)
-    phi = x[1] + net.predict(x)
-    ra, rb = densities_from_phi(phi, x, wl)
+    ra, rb = densities_from_prediction(net.predict(x), x, wl)
     sim.set_densities(ra, rb)
     ok = True
     sim.step(1)
@@ -252,3 +281,47 @@ def warm_start(sim, wl, net, window=25, u_limit=0.1, grow=1.5):
         return True, 2 * window + 1
     sim.set_film(wl.h_top, I.RHO_MAJ, I.RHO_MIN, I.RHO_MIX, wl.jitter())
     return False, 2 * window + 1
+
+
+def force_traces(sims, total, every):
+    """Capsule force z-component of every simulation every `every` steps
+    (one batch); returns [len(sims)][total // every]."""
+    batch = cfm.Batch(sims)
+    out = []
+    for _ in range(total // every):
+        batch.step(every)
+        out.append([s.capsule_force(0)[0][2] for s in sims])
+    batch.close()
+    return np.array(out).T
+
+
+def settle_step(trace, every, f_eq, tol=0.01):
+    """First sample step after which the trace stays within tol of f_eq
+    (None when it never does)."""
+    ok = np.abs(trace - f_eq) <= tol * abs(f_eq)
+    for k in range(len(ok)):
+        if ok[k:].all():
+            return (k + 1) * every
+    return None
+
+
+def convergence(net, wls, total=8000, every=50, tol=0.01):
+    """Flat-film and warm-started runs of the set-ups wls: steps until the
+    capsule force settles within tol of its equilibrium (the mean of the last
+    five samples of the flat-film run), and the warm starts that fell back."""
+    plain = [cfm.Simulation.from_workload(w) for w in wls]
+    warmed, used = [], []
+    for w in wls:
+        s = cfm.Simulation.from_workload(w)
+        u, _ = warm_start(s, w, net)
+        warmed.append(s)
+        used.append(u)
+    fp = force_traces(plain, total, every)
+    fw = force_traces(warmed, total, every)
+    res = []
+    for k in range(len(wls)):
+        f_eq = fp[k, -5:].mean()
+        res.append((settle_step(fp[k], every, f_eq, tol), settle_step(fw[k], every, f_eq, tol), used[k]))
+    for s in plain + warmed:
+        s.close()
+    return res

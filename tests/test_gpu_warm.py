@@ -102,8 +102,9 @@ def test_mse_and_adam_match_reference(env):
 
 
 def test_training_learns_a_known_convolution(env):
-    """The network trained with the project's kernels fits a target made by a
-    fixed random convolution of its input: the loss falls by 10x or more."""
+    """The network trained with the project's kernels fits a two-channel target
+    made by fixed random convolutions of its input: the loss falls by 10x or
+    more."""
     torch, cfm = env
     from paper_2007_15405_gb300 import warm
     net = warm.WarmNet(seed=1)
@@ -111,7 +112,8 @@ def test_training_learns_a_known_convolution(env):
     n, nz, ny, nx = 4, 12, 10, 14
     X = rng.standard_normal((n, 4, nz, ny, nx)).astype(np.float32)
     wt = rng.standard_normal((1, 4, 27)) / np.sqrt(27 * 4)
-    T = W.conv3d(X.astype(np.float64), wt, np.zeros(1), 1, False).astype(np.float32) * 0.5
+    wt = np.concatenate([wt, -wt])  # two output channels
+    T = W.conv3d(X.astype(np.float64), wt, np.zeros(2), 1, False).astype(np.float32) * 0.5
     M = np.ones_like(T)
     losses = warm.train(net, X, T, M, steps=150, batch=4, lr=3e-3)
     assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
@@ -160,8 +162,8 @@ def test_trained_network_gains_over_the_flat_film(env):
     err_plain, err_warm = [], []
     for k in range(24, 28):
         pred = net.predict(X[k])
-        err_plain.append(np.sqrt((T[k, 0] ** 2 * M[k, 0]).sum() / M[k, 0].sum()))
-        err_warm.append(np.sqrt(((pred - T[k, 0]) ** 2 * M[k, 0]).sum() / M[k, 0].sum()))
+        err_plain.append(np.sqrt((T[k] ** 2 * M[k]).sum() / M[k].sum()))
+        err_warm.append(np.sqrt(((pred - T[k]) ** 2 * M[k]).sum() / M[k].sum()))
     assert np.mean(err_warm) < 0.7 * np.mean(err_plain), (err_plain, err_warm)
     sim = cfm.Simulation.from_workload(wls[24])
     used, _ = warm.warm_start(sim, wls[24], net)
