@@ -41,6 +41,7 @@ def lib():
         L.or_set_populations.argtypes = [C.c_void_p, _dp]
         L.or_get_populations.argtypes = [C.c_void_p, _dp]
         L.or_step.argtypes = [C.c_void_p, C.c_int]
+        L.or_remove_mass.argtypes = [C.c_void_p, C.c_double]
         L.or_fields.argtypes = [C.c_void_p, _dp, _dp]
         L.or_capsule_state.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp, _dp]
         L.or_momentum.argtypes = [C.c_void_p, _dp, _dp, _dp]
@@ -162,6 +163,10 @@ class Oracle:
 
     def step(self, n=1):
         lib().or_step(self._h, int(n))
+
+    def remove_mass(self, dmA):
+        """Drying: turn dmA of component A into B each step (0 turns it off)."""
+        lib().or_remove_mass(self._h, float(dmA))
 
     def fields(self):
         rho = np.zeros((2, self.nz, self.ny, self.nx))

@@ -26,6 +26,8 @@
  *      volume penalty (Eq. 8), Hertz repulsion (Eq. 11); node update
  *      x(t+1) = x(t) + F_tot/m (Eq. 9)
  *   7. new cut links for the moved membrane.
+ * An optional drying step (a reading: the paper fixes each film height per
+ * run and lowers none) follows the collision, see remove_mass below.
  * Points where the paper is silent are resolved the same way as in the CUDA
  * library and are listed as readings c1..c25 in the design notes.
  *
@@ -93,6 +95,7 @@ typedef struct or_ctx {
     int ncaps, ntri;
     or_capsule caps[MAXCAPS];
     long step;
+    double dmA;                 /* drying: A mass turned into B per step (0: off) */
     double mom_to_membrane[3];  /* cumulative momentum given to membranes  */
     double mom_to_wall[3];      /* cumulative momentum given to substrate  */
 } or_ctx;
@@ -812,10 +815,41 @@ static void membrane_update(or_ctx *c) {
     }
 }
 
+/* Drying by species conversion.  The film is lowered by turning a mass dmA
+ * of component A into component B each step, so the total mass stays put.
+ * The nodes where A is the majority (rho^A > rho^B, this step's densities)
+ * each give up the same fraction eps = dmA / (sum of their rho^A), at most 1,
+ * of their post-collision A populations; the mass eps rho^A(x) a node gives
+ * up joins its B populations in the rest-state proportions w_i.  The total A
+ * inventory then falls by exactly dmA per step (by all of it once eps = 1). */
+static void remove_mass(or_ctx *c) {
+    const long N = c->N;
+    double S = 0.0;
+    for (long n = 0; n < N; ++n) {
+        int z = (int)(n / ((long)c->nx * c->ny));
+        if (!is_solid(c, z) && c->rho[n] > c->rho[N + n]) S += c->rho[n];
+    }
+    if (S <= 0.0) return;
+    double eps = c->dmA / S;
+    if (eps > 1.0) eps = 1.0;
+    for (long n = 0; n < N; ++n) {
+        int z = (int)(n / ((long)c->nx * c->ny));
+        if (is_solid(c, z) || !(c->rho[n] > c->rho[N + n])) continue;
+        const double dm = eps * c->rho[n];
+        for (int i = 0; i < NQ; ++i) {
+            *F_(c, c->fpost, 0, i, n) *= 1.0 - eps;
+            *F_(c, c->fpost, 1, i, n) += WV[i] * dm;
+        }
+    }
+}
+
+void or_remove_mass(or_ctx *c, double dmA) { c->dmA = dmA; }
+
 int or_step(or_ctx *c, int nsteps) {
     for (int s = 0; s < nsteps; ++s) {
         stream(c);
         collide(c, NULL);
+        if (c->dmA > 0.0) remove_mass(c);
         membrane_update(c);
         int moving = 0;
         for (int ci = 0; ci < c->ncaps; ++ci) moving |= c->caps[ci].mode != 2;
