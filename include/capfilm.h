@@ -214,6 +214,18 @@ cf_status cf_launch_count(cf_ctx *ctx, long long *n);
  * before.  Synchronous. */
 cf_status cf_set_densities(cf_ctx *ctx, const double *rhoA, const double *rhoB);
 
+/* Drying: lower the film by turning a mass dmA of component A into component
+ * B every step (0 turns it off; the paper keeps each film height fixed, so
+ * this rule is a reading of "lowering the film", not a passage of it).  After
+ * each collision, every node where A is the majority (rho^A > rho^B, that
+ * step's densities) keeps 1 - eps of its A populations and adds eps rho^A w_i
+ * to its B populations, eps = dmA / (sum of rho^A over those nodes), at most
+ * 1.  The A inventory thus falls by dmA per step and every node keeps its
+ * total mass.  The sum is reduced on the device in a fixed order (runs are
+ * reproducible).  Not available in a batch (cf_batch_step returns CF_ESTATE).
+ * Synchronous.  Errors: CF_EINVAL (dmA negative or not finite), CF_ENOMEM. */
+cf_status cf_remove_mass(cf_ctx *ctx, double dmA);
+
 /* ---------------------------------------------------------------- batches
  * A batch steps many independent contexts together, for parameter sweeps such
  * as the paper's series over capsule distance and elastic modulus (Sec. 4):

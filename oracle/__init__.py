@@ -137,6 +137,8 @@ class Oracle:
         if set_film:
             from paper_2007_15405_gb300.inputs import RHO_MAJ, RHO_MIN, RHO_MIX
             o.set_film(wl.h_top, RHO_MAJ, RHO_MIN, RHO_MIX, wl.jitter())
+        if getattr(wl, "dry_dm", 0.0) > 0.0:
+            o.remove_mass(wl.dry_dm)
         return o
 
     def add_capsule(self, X, F, kS, C, kB, kV, mass, mode):
@@ -198,6 +200,11 @@ class Oracle:
         inside = np.zeros((self.nz, self.ny, self.nx), np.uint8)
         lib().or_cuts(self._h, _ptr(mask, _up), _ptr(tri, _ip), _ptr(inside, _bp))
         return mask, tri, inside
+
+    def cut_mask(self):
+        mask = np.zeros((self.nz, self.ny, self.nx), np.uint32)
+        lib().or_cuts(self._h, _ptr(mask, _up), None, None)
+        return mask
 
     def cuts_bruteforce(self):
         mask = np.zeros((self.nz, self.ny, self.nx), np.uint32)

@@ -85,6 +85,7 @@ def load_library(path: Optional[str] = None):
         "cf_lattice_step_static": [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
                                    _dp, C.c_double, C.c_void_p],
         "cf_set_densities": [C.c_void_p, _dp, _dp],
+        "cf_remove_mass": [C.c_void_p, C.c_double],
         "cf_conv3d_forward": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
                               C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
         "cf_conv3d_backward": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
@@ -121,7 +122,7 @@ def exported_symbols():
             "cf_meniscus_field", "cf_meniscus_profile", "cf_cuts", "cf_launch_count",
             "cf_time_phases", "cf_lattice_step_static", "cf_batch_create", "cf_batch_destroy",
             "cf_batch_step", "cf_batch_time", "cf_batch_set_config", "cf_batch_config",
-            "cf_batch_autotune", "cf_batch_launch_count", "cf_set_densities", "cf_conv3d_forward",
+            "cf_batch_autotune", "cf_batch_launch_count", "cf_set_densities", "cf_remove_mass", "cf_conv3d_forward",
             "cf_conv3d_backward", "cf_mse", "cf_adam", "cf_to_bf16", "cf_from_bf16"]
 
 
@@ -214,6 +215,8 @@ class Simulation:
         if set_film:
             from .inputs import RHO_MAJ, RHO_MIN, RHO_MIX
             s.set_film(wl.h_top, RHO_MAJ, RHO_MIN, RHO_MIX, wl.jitter())
+        if wl.dry_dm > 0.0:
+            s.remove_mass(wl.dry_dm)
         return s
 
     def close(self):
@@ -253,6 +256,11 @@ class Simulation:
         b = np.ascontiguousarray(rhoB, dtype=np.float64).reshape(-1)
         assert a.size == self.N and b.size == self.N
         _check(_lib.cf_set_densities(self._h, _ptr(a), _ptr(b)))
+
+    def remove_mass(self, dmA):
+        """Drying: turn dmA of component A into B each step, 0 turns it off
+        (cf_remove_mass)."""
+        _check(_lib.cf_remove_mass(self._h, float(dmA)))
 
     @property
     def stream(self):
@@ -326,6 +334,12 @@ class Simulation:
                             tri.ctypes.data_as(C.POINTER(C.c_int)),
                             ins.ctypes.data_as(C.POINTER(C.c_uint8))))
         return mask, tri, ins
+
+    def cut_mask(self):
+        """Cut bits per node [nz][ny][nx] (bit k-1: link to x + e_k cut) alone."""
+        mask = np.zeros((self.nz, self.ny, self.nx), np.uint32)
+        _check(_lib.cf_cuts(self._h, mask.ctypes.data_as(C.POINTER(C.c_uint32)), None, None))
+        return mask
 
 
 class Batch:

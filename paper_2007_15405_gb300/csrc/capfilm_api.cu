@@ -127,6 +127,12 @@ struct cf_ctx {
     cudaGraphExec_t graph = nullptr;
     int graph_key = -1;
     int graph_launches = 0;  // kernel launches of one graph replay (two steps)
+
+    // drying: A mass turned into B per step, and the reduction scratch
+    double dry_dm = 0.0;
+    double *dry_part = nullptr;
+    unsigned *dry_ctr = nullptr;
+    float *dry_eps = nullptr;
 };
 
 namespace {
@@ -192,6 +198,10 @@ LBParams lb_params(cf_ctx *c, bool with_out) {
     p.psi = c->psi;
     p.rec = c->rec;
     p.status = c->status;
+    p.dry_dm = c->dry_dm;
+    p.dry_part = c->dry_part;
+    p.dry_ctr = c->dry_ctr;
+    p.dry_eps = c->dry_eps;
     return p;
 }
 
@@ -665,6 +675,25 @@ cf_status cf_set_capsule_mode(cf_ctx *c, int id, int mode) {
     return CF_OK;
 }
 
+cf_status cf_remove_mass(cf_ctx *c, double dm) {
+    if (!c) return fail(CF_EINVAL, "null context");
+    if (!(dm >= 0.0) || !std::isfinite(dm)) return fail(CF_EINVAL, "the mass per step must be finite and >= 0");
+    if (dm > 0.0 && !c->dry_part) {
+        // one partial sum per density-pass block
+        const size_t nb = density_blocks_max(c->d.nx, c->d.ny, c->d.nz);
+        c->dry_part = (double *)dalloc(c, sizeof(double) * nb);
+        c->dry_ctr = (unsigned *)dalloc(c, sizeof(unsigned));
+        c->dry_eps = (float *)dalloc(c, sizeof(float));
+        if (!c->dry_part || !c->dry_ctr || !c->dry_eps) return fail(CF_ENOMEM, "device allocation failed (drying)");
+        CF_CUDA(cudaMemsetAsync(c->dry_ctr, 0, sizeof(unsigned), c->stream));
+        CF_CUDA(cudaMemsetAsync(c->dry_eps, 0, sizeof(float), c->stream));
+    }
+    CF_CUDA(cudaStreamSynchronize(c->stream));
+    c->dry_dm = dm;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_key = -1; }
+    return CF_OK;
+}
+
 cf_status cf_set_film(cf_ctx *c, double h_top, double rmaj, double rmin, double rmix,
                       const double *jitter) {
     if (!c) return fail(CF_EINVAL, "null context");
@@ -1107,6 +1136,8 @@ cf_status batch_replay(cf_batch *b, int pairs) {
 }
 
 cf_status batch_run(cf_batch *b, long long n) {
+    for (cf_ctx *c : b->ctx)
+        if (c->dry_dm > 0.0) return fail(CF_ESTATE, "drying (cf_remove_mass) is not available in a batch");
     int nl = 0;
     long long left = n - 1;  // the last step records the fields
     if (left >= 2) {

@@ -82,6 +82,13 @@ struct LBParams {
     float2 *__restrict__ psi;           // [N] (psiA, psiB) of this step (written by the density pass)
     float4 *__restrict__ sdens;         // allocation-free step: (rho, psi) scratch of the library
     unsigned *__restrict__ status;      // device error flags
+    // drying (A turned into B): the density pass sums rho_A over the
+    // A-majority nodes into block partials, its last block turns them into the
+    // fraction the collide pass converts
+    double dry_dm;                      // A mass converted per step (0: off)
+    double *__restrict__ dry_part;      // [density-pass blocks] partial sums
+    unsigned *__restrict__ dry_ctr;     // density-pass blocks finished
+    float *__restrict__ dry_eps;        // fraction of this step
 };
 
 enum StatusBits : unsigned { ST_OVERFLOW = 1u, ST_NAN = 2u, ST_TIMEOUT = 4u };
@@ -186,6 +193,8 @@ __host__ __device__ inline int wrapi(int a, int n) {
 // Host-side launchers (defined in the kernel translation units).
 namespace cf {
 void set_last_error(const char *msg);  // text returned by cf_last_error() on this thread
+// most blocks a density pass of an nx x ny x nz lattice launches
+size_t density_blocks_max(int nx, int ny, int nz);
 cudaError_t launch_lb_step(const LBParams &p, int prec, cudaStream_t s);
 
 // Batched lattice passes: many independent lattices in one persistent launch

@@ -191,9 +191,10 @@ __device__ __forceinline__ bool node_of(const LBParams &p, int &x, int &y, int &
     return x < p.nx && y < p.ny;
 }
 
-// Density pass of one node: streamed populations -> rho, psi.
+// Density pass of one node: streamed populations -> rho, psi.  Returns rho_A
+// if A is the majority there, else 0 (the node's share of the drying sum).
 template <typename T>
-__device__ __forceinline__ void density_node(const LBParams &p, const Deltas &d) {
+__device__ __forceinline__ float density_node(const LBParams &p, const Deltas &d) {
     float fa[Q], fb[Q];
     pull<T>(p, d, fa, fb);
     float ra = 0.f, rb = 0.f;
@@ -201,6 +202,45 @@ __device__ __forceinline__ void density_node(const LBParams &p, const Deltas &d)
     for (int i = 0; i < Q; ++i) { ra += fa[i]; rb += fb[i]; }
     p.rho[d.n] = make_float2(ra, rb);
     p.psi[d.n] = make_float2(psi_of(ra), psi_of(rb));
+    return ra > rb ? ra : 0.f;
+}
+
+// Drying: the sum of rho_A over the A-majority nodes.  Each block of the
+// density pass writes its partial sum; the last block to finish adds the
+// partials in index order (so the result does not depend on the order the
+// blocks ran in) and writes eps = dm / sum, at most 1, for the collide pass.
+__device__ __forceinline__ void dry_reduce(const LBParams &p, float s) {
+    __shared__ double part[BY];
+    __shared__ bool last;
+    double v = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) part[threadIdx.y] = v;  // a block row is one warp
+    __syncthreads();
+    const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        double b = 0.0;
+        for (int k = 0; k < BY; ++k) b += part[k];
+        p.dry_part[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = b;
+        __threadfence();
+        last = atomicAdd(p.dry_ctr, 1u) == nb - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double a = 0.0;
+    for (unsigned i = threadIdx.y * BX + threadIdx.x; i < nb; i += BX * BY) a += __ldcg(p.dry_part + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    __syncthreads();
+    if (threadIdx.x == 0) part[threadIdx.y] = a;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        double S = 0.0;
+        for (int k = 0; k < BY; ++k) S += part[k];
+        *p.dry_eps = S > 0.0 ? (float)fmin(1.0, p.dry_dm / S) : 0.f;
+        *p.dry_ctr = 0u;  // ready for the next step
+    }
 }
 
 // resident blocks per SM the density pass is compiled for: its 38 gathers are
@@ -209,18 +249,28 @@ __device__ __forceinline__ void density_node(const LBParams &p, const Deltas &d)
 #define CF_DENSITY_MINB 8
 #endif
 
-template <typename T>
+// DRY: also the drying sum (the whole block must reach the reduction)
+template <typename T, bool DRY = false>
 __global__ void __launch_bounds__(BX *BY, CF_DENSITY_MINB) k_density(const LBParams p) {
     if (Pop<T>::shifted && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 &&
         threadIdx.x == 0 && threadIdx.y == 0)
         atomicAdd(p.step_ctr, 1u);  // read by the collide pass that follows
     int x, y, z;
-    if (!node_of(p, x, y, z)) return;
-    for (; z < p.zhi; z += gridDim.z) density_node<T>(p, deltas(p, x, y, z));
+    if (!DRY) {
+        if (!node_of(p, x, y, z)) return;
+        for (; z < p.zhi; z += gridDim.z) density_node<T>(p, deltas(p, x, y, z));
+        return;
+    }
+    float s = 0.f;
+    if (node_of(p, x, y, z))
+        for (; z < p.zhi; z += gridDim.z) s += density_node<T>(p, deltas(p, x, y, z));
+    dry_reduce(p, s);
 }
 
-// Shan-Chen force with decoupling, velocity shift, BGK, store.
-template <typename T>
+// Shan-Chen force with decoupling, velocity shift, BGK, store.  With DRY, an
+// A-majority node then keeps 1 - eps of its post-collision A populations and
+// adds eps rho_A w_i to its B populations (drying by species conversion).
+template <typename T, bool DRY = false>
 __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d) {
     float fa[Q], fb[Q];
     const uint32_t m = pull<T>(p, d, fa, fb);
@@ -301,6 +351,12 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
         p.out[4 * p.N + n] = (ja[2] + jb[2] + 0.5f * (FA[2] + FB[2])) / rt;
     }
     if (!(ra + rb < 1e30f)) atomicOr(p.status, ST_NAN);
+    float ca = 1.f, cb = 0.f;  // drying: A kept, B gained per unit weight
+    if (DRY && ra > rb) {
+        const float e = __ldg(p.dry_eps);
+        ca = 1.f - e;
+        cb = e * ra;
+    }
     const float ka = 1.0f - 1.5f * (ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2]);
     const float kb = 1.0f - 1.5f * (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
     const int N = (int)p.N;
@@ -322,19 +378,34 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
             const float qb1 = sb_ + 3.0f * wb * eub, qb2 = sb_ - 3.0f * wb * eub;
             qa0 -= qa1 + qa2;
             qb0 -= qb1 + qb2;
-            Pop<T>::st(dA + i * N, fa[i] - (fa[i] - qa1) * ta, 0u);
-            Pop<T>::st(dA + (i + 1) * N, fa[i + 1] - (fa[i + 1] - qa2) * ta, 0u);
-            Pop<T>::st(dB + i * N, fb[i] - (fb[i] - qb1) * tb, 0u);
-            Pop<T>::st(dB + (i + 1) * N, fb[i + 1] - (fb[i + 1] - qb2) * tb, 0u);
+            float va1 = fa[i] - (fa[i] - qa1) * ta, va2 = fa[i + 1] - (fa[i + 1] - qa2) * ta;
+            float vb1 = fb[i] - (fb[i] - qb1) * tb, vb2 = fb[i + 1] - (fb[i + 1] - qb2) * tb;
+            if (DRY) {
+                va1 *= ca; va2 *= ca;
+                vb1 += wgt(i) * cb; vb2 += wgt(i) * cb;
+            }
+            Pop<T>::st(dA + i * N, va1, 0u);
+            Pop<T>::st(dA + (i + 1) * N, va2, 0u);
+            Pop<T>::st(dB + i * N, vb1, 0u);
+            Pop<T>::st(dB + (i + 1) * N, vb2, 0u);
         }
-        Pop<T>::st(dA, fa[0] - (fa[0] - qa0) * ta, 0u);
-        Pop<T>::st(dB, fb[0] - (fb[0] - qb0) * tb, 0u);
+        float va0 = fa[0] - (fa[0] - qa0) * ta, vb0 = fb[0] - (fb[0] - qb0) * tb;
+        if (DRY) {
+            va0 *= ca;
+            vb0 += wgt(0) * cb;
+        }
+        Pop<T>::st(dA, va0, 0u);
+        Pop<T>::st(dB, vb0, 0u);
         return;
     }
     // 16-bit offsets from w_i rho, stochastically rounded; the float rest
     // population takes what the rounded moving populations leave of the mass
     uint32_t rs = mix32((uint32_t)n * 0x9e3779b9u ^ mix32(*p.step_ctr));
     float ma = ra, mb = rb;  // mass left for the rest populations
+    if (DRY) {
+        ma = ca * ra;
+        mb = rb + cb;
+    }
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
         const float eua = ex(i) * ua[0] + ey(i) * ua[1] + ez(i) * ua[2];
@@ -343,32 +414,53 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
         const float sa_ = wa * (ka + 4.5f * eua * eua), sb_ = wb * (kb + 4.5f * eub * eub);
         const float qa1 = sa_ + 3.0f * wa * eua, qa2 = sa_ - 3.0f * wa * eua;
         const float qb1 = sb_ + 3.0f * wb * eub, qb2 = sb_ - 3.0f * wb * eub;
+        float va1 = fa[i] - (fa[i] - qa1) * ta, va2 = fa[i + 1] - (fa[i + 1] - qa2) * ta;
+        float vb1 = fb[i] - (fb[i] - qb1) * tb, vb2 = fb[i + 1] - (fb[i + 1] - qb2) * tb;
+        if (DRY) {
+            va1 *= ca; va2 *= ca;
+            vb1 += wgt(i) * cb; vb2 += wgt(i) * cb;
+        }
         // an LCG step per store draws its rounding bits
         rs = rs * 1664525u + 1013904223u;
-        ma -= Pop<T>::st(dA + i * N, fa[i] - (fa[i] - qa1) * ta - wa, rs >> 8) + wa;
+        ma -= Pop<T>::st(dA + i * N, va1 - wa, rs >> 8) + wa;
         rs = rs * 1664525u + 1013904223u;
-        ma -= Pop<T>::st(dA + (i + 1) * N, fa[i + 1] - (fa[i + 1] - qa2) * ta - wa, rs >> 8) + wa;
+        ma -= Pop<T>::st(dA + (i + 1) * N, va2 - wa, rs >> 8) + wa;
         rs = rs * 1664525u + 1013904223u;
-        mb -= Pop<T>::st(dB + i * N, fb[i] - (fb[i] - qb1) * tb - wb, rs >> 8) + wb;
+        mb -= Pop<T>::st(dB + i * N, vb1 - wb, rs >> 8) + wb;
         rs = rs * 1664525u + 1013904223u;
-        mb -= Pop<T>::st(dB + (i + 1) * N, fb[i + 1] - (fb[i + 1] - qb2) * tb - wb, rs >> 8) + wb;
+        mb -= Pop<T>::st(dB + (i + 1) * N, vb2 - wb, rs >> 8) + wb;
     }
     p.dst0[n] = ma;
     p.dst0[N + n] = mb;
 }
 
-template <typename T>
+template <typename T, bool DRY = false>
 __global__ void __launch_bounds__(BX *BY, CF_COLLIDE_MINB) k_collide(const LBParams p) {
     int x, y, z;
     if (!node_of<true>(p, x, y, z)) return;
-    for (; z < p.zhi; z += gridDim.z) collide_node<T>(p, deltas(p, x, y, z));
+    for (; z < p.zhi; z += gridDim.z) collide_node<T, DRY>(p, deltas(p, x, y, z));
+}
+
+size_t density_blocks_max(int nx, int ny, int nz) {
+    return (size_t)((nx + BX - 1) / BX) * ((ny + BY - 1) / BY) * nz;
 }
 
 cudaError_t launch_lb_step(const LBParams &p, int prec, cudaStream_t s) {
     const int nzf = p.zhi - p.zlo;
     const int gz = p.zchunk > 0 ? (nzf + p.zchunk - 1) / p.zchunk : nzf;
     dim3 grid((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, gz), block(BX, BY);
-    if (prec == P_F16) {
+    if (p.dry_dm > 0.0) {
+        if (prec == P_F16) {
+            k_density<__half, true><<<grid, block, 0, s>>>(p);
+            k_collide<__half, true><<<grid, block, 0, s>>>(p);
+        } else if (prec == P_BF16) {
+            k_density<__nv_bfloat16, true><<<grid, block, 0, s>>>(p);
+            k_collide<__nv_bfloat16, true><<<grid, block, 0, s>>>(p);
+        } else {
+            k_density<float, true><<<grid, block, 0, s>>>(p);
+            k_collide<float, true><<<grid, block, 0, s>>>(p);
+        }
+    } else if (prec == P_F16) {
         k_density<__half><<<grid, block, 0, s>>>(p);
         k_collide<__half><<<grid, block, 0, s>>>(p);
     } else if (prec == P_BF16) {

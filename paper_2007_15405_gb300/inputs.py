@@ -113,6 +113,7 @@ class Workload:
     jitter_amp: float = 1e-3
     seed: int = 1234
     rep_dz: float = REP_DZ
+    dry_dm: float = 0.0  # drying: A mass turned into B per step (0: off)
 
     @property
     def nodes(self) -> int:
@@ -212,6 +213,38 @@ def batched_sweep(n_dist: int = 16, moduli=SWEEP_MODULI, radius: float = 8.0, le
             out.append(sweep_point(d_over_R, kS, nx, ny, nz, radius=radius, level=level,
                                    steps=steps, seed=1234 + 97 * i + j))
     return out
+
+
+def drying_film(nx: int = 256, ny: int = 256, nz: int = 96, n_caps: int = 16, radius: float = 10.0,
+                level: int = 4, seed: int = 7, steps: int = 50000, h_from: float = 0.6,
+                h_to: float = 0.2) -> Workload:
+    """Drying film: n_caps capsules of radius R (level-4 icospheres, 2562
+    nodes each) at rest on the repulsive plane, on a seeded random layout
+    (centres uniform in xy, at least R + delta0 + 1 from the box sides, centre
+    distances at least 2R + 2 delta0; rejection sampling), in a film whose
+    height is lowered linearly from h_from R to h_to R above the repulsive
+    plane over `steps` steps.  The lowering is a steady conversion of A into B:
+    per step, the A excess (rho_maj - rho_min) of the lowered layer over the
+    whole nx x ny area, divided by the steps."""
+    rng = np.random.default_rng(seed)
+    lo = radius + DELTA0 + 1.0
+    dmin = 2.0 * radius + 2.0 * DELTA0
+    pts: List[Tuple[float, float]] = []
+    tries = 0
+    while len(pts) < n_caps:
+        tries += 1
+        if tries > 200000:
+            raise ValueError(f"{n_caps} capsules of radius {radius} do not fit in {nx}x{ny}")
+        p = (float(rng.uniform(lo, nx - lo)), float(rng.uniform(lo, ny - lo)))
+        if all(math.hypot(p[0] - q[0], p[1] - q[1]) >= dmin for q in pts):
+            pts.append(p)
+    zc = z_rest(radius) + _OFF[2]
+    caps = [CapsuleSpec(centre=(x + _OFF[0], y + _OFF[1], zc), radius=radius, level=level)
+            for x, y in pts]
+    h_top = 0.5 + REP_DZ + h_from * radius
+    dm = (h_from - h_to) * radius * nx * ny * (RHO_MAJ - RHO_MIN) / steps
+    return Workload(f"drying film {nx}x{ny}x{nz} {n_caps} capsules R={radius:g}", nx, ny, nz,
+                    h_top=h_top, capsules=caps, steps=steps, seed=seed, dry_dm=dm)
 
 
 def warm_dataset(n: int, seed: int = 0, nx: int = 48, ny: int = 32, nz: int = 32,
