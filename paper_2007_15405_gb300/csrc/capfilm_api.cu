@@ -86,6 +86,7 @@ struct cf_ctx {
     float *out = nullptr;
     float2 *rho[2] = {nullptr, nullptr};   // densities paired with each population buffer
     float2 *psi = nullptr;                 // pseudopotentials of the current step
+    float4 *J = nullptr;                   // total momentum of the current step (tau = 1)
     uint32_t *mask = nullptr;
     int *tri = nullptr;
     float2 *rec = nullptr;        // [N][18] bounce records (A, B) by arriving direction
@@ -196,6 +197,7 @@ LBParams lb_params(cf_ctx *c, bool with_out) {
     p.out = with_out ? c->out : nullptr;
     p.rho = c->rho[1 - c->fpar];
     p.psi = c->psi;
+    p.J = c->J;
     p.rec = c->rec;
     p.status = c->status;
     p.dry_dm = c->dry_dm;
@@ -581,6 +583,9 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     c->rho[0] = (float2 *)dalloc(c, sizeof(float2) * N);
     c->rho[1] = (float2 *)dalloc(c, sizeof(float2) * N);
     c->psi = (float2 *)dalloc(c, sizeof(float2) * N);
+    // tau = 1 for both components: the density pass also stores the momentum
+    const bool tau1 = (float)desc->tau[0] == 1.f && (float)desc->tau[1] == 1.f;
+    c->J = tau1 ? (float4 *)dalloc(c, sizeof(float4) * N) : nullptr;
     c->mask = (uint32_t *)dalloc(c, sizeof(uint32_t) * N);
     c->tri = (int *)dalloc(c, sizeof(int) * 18 * N);
     c->inside = (uint8_t *)dalloc(c, N);
@@ -588,7 +593,7 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     c->status = (unsigned *)dalloc(c, sizeof(unsigned));
     c->dscratch = (double *)dalloc(c, sizeof(double) * 8);
     c->hscratch = (float *)dalloc(c, sizeof(float) * desc->nx * desc->ny);
-    if (!c->f[0] || !c->f[1] || !c->f0[0] || !c->f0[1] || !c->step_ctr || !c->out || !c->rho[0] || !c->rho[1] || !c->psi || !c->mask || !c->tri || !c->inside ||
+    if (!c->f[0] || !c->f[1] || !c->f0[0] || !c->f0[1] || !c->step_ctr || !c->out || !c->rho[0] || !c->rho[1] || !c->psi || (tau1 && !c->J) || !c->mask || !c->tri || !c->inside ||
         !c->counts || !c->status || !c->dscratch || !c->hscratch) {
         cf_destroy(c);
         return fail(CF_ENOMEM, "device allocation failed");
@@ -1083,7 +1088,7 @@ cf_status batch_enqueue_step(cf_batch *b, bool with_out, int *nl) {
         tab.lat[i] = lb_params(b->ctx[i], with_out);
         tab.lat[i].zstride = b->zstride[i];
     }
-    CF_CUDA(launch_lb_batch(tab, b->work, b->nwork, b->prec, b->tile, b->stream));
+    CF_CUDA(launch_lb_batch(tab, (int)b->ctx.size(), b->work, b->nwork, b->prec, b->tile, b->stream));
     *nl += 2;
     CF_CUDA(cudaEventRecord(b->ev_lat, b->stream));
     for (cf_ctx *c : b->ctx) {

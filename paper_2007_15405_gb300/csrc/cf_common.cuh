@@ -80,6 +80,7 @@ struct LBParams {
     float *__restrict__ out;            // optional [5][N]: rhoA, rhoB, ux, uy, uz
     float2 *__restrict__ rho;           // [N] (rhoA, rhoB) of this step (written by the density pass)
     float2 *__restrict__ psi;           // [N] (psiA, psiB) of this step (written by the density pass)
+    float4 *__restrict__ J;             // [N] total momentum of this step (density pass, tau = 1 only)
     float4 *__restrict__ sdens;         // allocation-free step: (rho, psi) scratch of the library
     unsigned *__restrict__ status;      // device error flags
     // drying (A turned into B): the density pass sums rho_A over the
@@ -211,8 +212,9 @@ struct BatchTab {
 };
 constexpr int CF_NTILES = 6;  // tile shapes (x width, y depth) of the batched passes
 void lb_batch_tile(int tile, int *tx, int *ty);
-int lb_batch_resident(int tile, int prec);  // blocks of one pass resident on the device
-cudaError_t launch_lb_batch(const BatchTab &tab, const int4 *work, int nwork, int prec, int tile,
+int lb_batch_resident(int tile, int prec, bool eq);  // blocks of one pass resident on the device
+// nlat: lattices in tab
+cudaError_t launch_lb_batch(const BatchTab &tab, int nlat, const int4 *work, int nwork, int prec, int tile,
                             cudaStream_t s);
 cudaError_t launch_init_film(void *f, float *f0, int prec, float2 *rho, long long N, int nx, int ny,
                              int nz, int wall, float h_top, float rmaj, float rmin, float rmix,

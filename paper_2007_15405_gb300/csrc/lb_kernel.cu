@@ -33,6 +33,9 @@ constexpr int BX = 32, BY = 4;  // thread block: one row segment of 32 x 4 rows
 #ifndef CF_COLLIDE_MINB
 #define CF_COLLIDE_MINB 5
 #endif
+#ifndef CF_COLLIDE16_MINB  // the same for 16-bit storage
+#define CF_COLLIDE16_MINB 4
+#endif
 
 __device__ __forceinline__ float psi_of(float r) { return -expm1f(-r); }
 
@@ -71,6 +74,10 @@ __device__ __forceinline__ __half sr_f16(float v, uint32_t r) {
     if ((b & 0x7f800000u) != 0x7f800000u) b = (b + (r & 0x1fffu)) & ~0x1fffu;
     return __float2half_rz(__uint_as_float(b));
 }
+// Two offsets at once: cvt.rs rounds x into the high and y into the low
+// 16 bits of the result, stochastically, with the high and low 16 bits of r
+// as their random bits (unbiased: measured round-up frequencies equal the
+// fractional parts).  put2 stores the halves, val2 returns (x, y) as stored.
 template <> struct Pop<__half> {
     static constexpr bool shifted = true;
     __device__ static float ld(const __half *p) { return __half2float(__ldg(p)) * F16_INV_SCALE; }
@@ -78,6 +85,20 @@ template <> struct Pop<__half> {
         const __half h = sr_f16(v * F16_SCALE, r);
         *p = h;
         return __half2float(h) * F16_INV_SCALE;
+    }
+    __device__ static uint32_t cvt2(float x, float y, uint32_t r) {
+        uint32_t d;
+        asm("cvt.rs.satfinite.f16x2.f32 %0, %1, %2, %3;"
+            : "=r"(d) : "f"(x * F16_SCALE), "f"(y * F16_SCALE), "r"(r));
+        return d;
+    }
+    __device__ static float2 val2(uint32_t d) {
+        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&d));  // (low, high)
+        return make_float2(f.y * F16_INV_SCALE, f.x * F16_INV_SCALE);
+    }
+    __device__ static void put2(__half *px, __half *py, uint32_t d) {
+        *reinterpret_cast<unsigned short *>(px) = (unsigned short)(d >> 16);
+        *reinterpret_cast<unsigned short *>(py) = (unsigned short)(d & 0xffffu);
     }
 };
 template <> struct Pop<__nv_bfloat16> {
@@ -87,6 +108,18 @@ template <> struct Pop<__nv_bfloat16> {
         const __nv_bfloat16 h = sr_bf16(v, r);
         *p = h;
         return __bfloat162float(h);
+    }
+    __device__ static uint32_t cvt2(float x, float y, uint32_t r) {
+        uint32_t d;
+        asm("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(x), "f"(y), "r"(r));
+        return d;
+    }
+    __device__ static float2 val2(uint32_t d) {  // a bfloat16 is the high half of a float
+        return make_float2(__uint_as_float(d & 0xffff0000u), __uint_as_float(d << 16));
+    }
+    __device__ static void put2(__nv_bfloat16 *px, __nv_bfloat16 *py, uint32_t d) {
+        *reinterpret_cast<unsigned short *>(px) = (unsigned short)(d >> 16);
+        *reinterpret_cast<unsigned short *>(py) = (unsigned short)(d & 0xffffu);
     }
 };
 
@@ -191,9 +224,10 @@ __device__ __forceinline__ bool node_of(const LBParams &p, int &x, int &y, int &
     return x < p.nx && y < p.ny;
 }
 
-// Density pass of one node: streamed populations -> rho, psi.  Returns rho_A
-// if A is the majority there, else 0 (the node's share of the drying sum).
-template <typename T>
+// Density pass of one node: streamed populations -> rho, psi, and with MOM the
+// total momentum J = sum_c sum_i f_i^c e_i for the tau = 1 collision.  Returns
+// rho_A if A is the majority there, else 0 (the node's share of the drying sum).
+template <typename T, bool MOM = false>
 __device__ __forceinline__ float density_node(const LBParams &p, const Deltas &d) {
     float fa[Q], fb[Q];
     pull<T>(p, d, fa, fb);
@@ -202,6 +236,15 @@ __device__ __forceinline__ float density_node(const LBParams &p, const Deltas &d
     for (int i = 0; i < Q; ++i) { ra += fa[i]; rb += fb[i]; }
     p.rho[d.n] = make_float2(ra, rb);
     p.psi[d.n] = make_float2(psi_of(ra), psi_of(rb));
+    if (MOM) {
+        float j[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 1; i < Q; i += 2) {  // opposite pairs (i, i+1), both components
+            const float dj = (fa[i] - fa[i + 1]) + (fb[i] - fb[i + 1]);
+            j[0] += ex(i) * dj; j[1] += ey(i) * dj; j[2] += ez(i) * dj;
+        }
+        p.J[d.n] = make_float4(j[0], j[1], j[2], 0.f);
+    }
     return ra > rb ? ra : 0.f;
 }
 
@@ -248,35 +291,37 @@ __device__ __forceinline__ void dry_reduce(const LBParams &p, float s) {
 #ifndef CF_DENSITY_MINB
 #define CF_DENSITY_MINB 8
 #endif
+#ifndef CF_DENSITY_MOM_MINB  // the same when it also sums the momentum
+#define CF_DENSITY_MOM_MINB 6
+#endif
 
-// DRY: also the drying sum (the whole block must reach the reduction)
-template <typename T, bool DRY = false>
-__global__ void __launch_bounds__(BX *BY, CF_DENSITY_MINB) k_density(const LBParams p) {
+// DRY: also the drying sum (the whole block must reach the reduction);
+// MOM: also the total momentum (tau = 1 collision)
+template <typename T, bool DRY = false, bool MOM = false>
+__global__ void __launch_bounds__(BX *BY, MOM ? CF_DENSITY_MOM_MINB : CF_DENSITY_MINB) k_density(const LBParams p) {
     if (Pop<T>::shifted && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 &&
         threadIdx.x == 0 && threadIdx.y == 0)
         atomicAdd(p.step_ctr, 1u);  // read by the collide pass that follows
     int x, y, z;
     if (!DRY) {
         if (!node_of(p, x, y, z)) return;
-        for (; z < p.zhi; z += gridDim.z) density_node<T>(p, deltas(p, x, y, z));
+        for (; z < p.zhi; z += gridDim.z) density_node<T, MOM>(p, deltas(p, x, y, z));
         return;
     }
     float s = 0.f;
     if (node_of(p, x, y, z))
-        for (; z < p.zhi; z += gridDim.z) s += density_node<T>(p, deltas(p, x, y, z));
+        for (; z < p.zhi; z += gridDim.z) s += density_node<T, MOM>(p, deltas(p, x, y, z));
     dry_reduce(p, s);
 }
 
-// Shan-Chen force with decoupling, velocity shift, BGK, store.  With DRY, an
-// A-majority node then keeps 1 - eps of its post-collision A populations and
-// adds eps rho_A w_i to its B populations (drying by species conversion).
-template <typename T, bool DRY = false>
-__device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d) {
-    float fa[Q], fb[Q];
-    const uint32_t m = pull<T>(p, d, fa, fb);
+// Shan-Chen force on both components at a node (Eq. 10 with G^{AB} = G^{BA} = G,
+// G^{AA} = G^{BB} = 0), with the decoupling across cut and substrate links:
+// there the partner's pseudopotential comes from the mean density over this
+// node and its neighbours reached through uncut fluid links, and the reaction
+// goes to the crossed element.
+__device__ __forceinline__ void sc_force(const LBParams &p, const Deltas &d, uint32_t m, float ra, float rb,
+                                         float pa, float pb, float (&FA)[3], float (&FB)[3]) {
     const int n = d.n;
-    const float2 mr = __ldg(p.rho + n), mp = __ldg(p.psi + n);
-    const float ra = mr.x, rb = mr.y, pa = mp.x, pb = mp.y;
     float sa[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};  // sum_k w_k psi'(x+e_k) e_k
     if (!m && !d.wlo && !d.whi) {
 #pragma unroll
@@ -322,9 +367,119 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
             sb[0] += wgt(k) * ex(k) * qb; sb[1] += wgt(k) * ey(k) * qb; sb[2] += wgt(k) * ez(k) * qb;
         }
     }
-    // Eq. 10 with G^{AB} = G^{BA} = G, G^{AA} = G^{BB} = 0
-    const float FA[3] = {-p.G * pa * sb[0], -p.G * pa * sb[1], -p.G * pa * sb[2]};
-    const float FB[3] = {-p.G * pb * sa[0], -p.G * pb * sa[1], -p.G * pb * sa[2]};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        FA[a] = -p.G * pa * sb[a];
+        FB[a] = -p.G * pb * sa[a];
+    }
+}
+
+// Post-collision populations of node n from the equilibria at (rho, u^eq)
+// (Eq. 5): BGK relaxation of the pulled fa, fb, or with EQ (tau = 1 for both
+// components) the equilibria themselves.  Float storage: the rest population
+// takes the mass balance of the equilibria.  16-bit storage: offsets from w_i
+// rho, stochastically rounded, and the float rest population takes what the
+// rounded moving populations leave of the mass.  With DRY, an A-majority node
+// keeps 1 - eps of its A populations and adds eps rho_A w_i to its B ones.
+template <typename T, bool DRY, bool EQ>
+__device__ __forceinline__ void store_post(const LBParams &p, int n, float ra, float rb, const float (&ua)[3],
+                                           const float (&ub)[3], const float (&fa)[Q], const float (&fb)[Q]) {
+    float ca = 1.f, cb = 0.f;  // drying: A kept, B gained per unit weight
+    if (DRY && ra > rb) {
+        const float e = __ldg(p.dry_eps);
+        ca = 1.f - e;
+        cb = e * ra;
+    }
+    const float ka = 1.0f - 1.5f * (ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2]);
+    const float kb = 1.0f - 1.5f * (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
+    const int N = (int)p.N;
+    T *__restrict__ dA = static_cast<T *>(p.dst) + n;
+    T *__restrict__ dB = static_cast<T *>(p.dst) + (long long)Q * N + n;
+    const float ta = p.itau[0], tb = p.itau[1];
+    // Eq. 5 for opposite pairs: f^eq_{i,i+1} = w rho (ka + 4.5 eu^2 +- 3 eu); the
+    // rest population takes the mass balance (sum_i f^eq_i = rho) so that the
+    // float32 weights (which sum to 1 + 1.5e-8) create no mass
+    float qa0 = ra, qb0 = rb;
+    if constexpr (!Pop<T>::shifted) {
+#pragma unroll
+        for (int i = 1; i < Q; i += 2) {
+            const float eua = ex(i) * ua[0] + ey(i) * ua[1] + ez(i) * ua[2];
+            const float eub = ex(i) * ub[0] + ey(i) * ub[1] + ez(i) * ub[2];
+            const float wa = wgt(i) * ra, wb = wgt(i) * rb;
+            const float sa_ = wa * (ka + 4.5f * eua * eua), sb_ = wb * (kb + 4.5f * eub * eub);
+            const float qa1 = sa_ + 3.0f * wa * eua, qa2 = sa_ - 3.0f * wa * eua;
+            const float qb1 = sb_ + 3.0f * wb * eub, qb2 = sb_ - 3.0f * wb * eub;
+            qa0 -= qa1 + qa2;
+            qb0 -= qb1 + qb2;
+            float va1 = EQ ? qa1 : fa[i] - (fa[i] - qa1) * ta, va2 = EQ ? qa2 : fa[i + 1] - (fa[i + 1] - qa2) * ta;
+            float vb1 = EQ ? qb1 : fb[i] - (fb[i] - qb1) * tb, vb2 = EQ ? qb2 : fb[i + 1] - (fb[i + 1] - qb2) * tb;
+            if (DRY) {
+                va1 *= ca; va2 *= ca;
+                vb1 += wgt(i) * cb; vb2 += wgt(i) * cb;
+            }
+            Pop<T>::st(dA + i * N, va1, 0u);
+            Pop<T>::st(dA + (i + 1) * N, va2, 0u);
+            Pop<T>::st(dB + i * N, vb1, 0u);
+            Pop<T>::st(dB + (i + 1) * N, vb2, 0u);
+        }
+        float va0 = EQ ? qa0 : fa[0] - (fa[0] - qa0) * ta, vb0 = EQ ? qb0 : fb[0] - (fb[0] - qb0) * tb;
+        if (DRY) {
+            va0 *= ca;
+            vb0 += wgt(0) * cb;
+        }
+        Pop<T>::st(dA, va0, 0u);
+        Pop<T>::st(dB, vb0, 0u);
+    } else {
+        // 16-bit offsets from w_i rho, stochastically rounded; the float rest
+        // population takes what the rounded moving populations leave of the mass
+        uint32_t rs = mix32((uint32_t)n * 0x9e3779b9u ^ mix32(*p.step_ctr));
+        float ma = ra, mb = rb;  // mass left for the rest populations
+        if (DRY) {
+            ma = ca * ra;
+            mb = rb + cb;
+        }
+#pragma unroll
+        for (int i = 1; i < Q; i += 2) {
+            const float eua = ex(i) * ua[0] + ey(i) * ua[1] + ez(i) * ua[2];
+            const float eub = ex(i) * ub[0] + ey(i) * ub[1] + ez(i) * ub[2];
+            const float wa = wgt(i) * ra, wb = wgt(i) * rb;
+            const float sa_ = wa * (ka + 4.5f * eua * eua), sb_ = wb * (kb + 4.5f * eub * eub);
+            const float qa1 = sa_ + 3.0f * wa * eua, qa2 = sa_ - 3.0f * wa * eua;
+            const float qb1 = sb_ + 3.0f * wb * eub, qb2 = sb_ - 3.0f * wb * eub;
+            float va1 = EQ ? qa1 : fa[i] - (fa[i] - qa1) * ta, va2 = EQ ? qa2 : fa[i + 1] - (fa[i + 1] - qa2) * ta;
+            float vb1 = EQ ? qb1 : fb[i] - (fb[i] - qb1) * tb, vb2 = EQ ? qb2 : fb[i + 1] - (fb[i + 1] - qb2) * tb;
+            if (DRY) {
+                va1 *= ca; va2 *= ca;
+                vb1 += wgt(i) * cb; vb2 += wgt(i) * cb;
+            }
+            // an LCG step per pair draws its rounding bits; the xor-shift mixes
+            // the well-distributed high bits into the low half
+            rs = rs * 1664525u + 1013904223u;
+            const uint32_t hA = Pop<T>::cvt2(va1 - wa, va2 - wa, rs ^ (rs >> 16));
+            rs = rs * 1664525u + 1013904223u;
+            const uint32_t hB = Pop<T>::cvt2(vb1 - wb, vb2 - wb, rs ^ (rs >> 16));
+            Pop<T>::put2(dA + i * N, dA + (i + 1) * N, hA);
+            Pop<T>::put2(dB + i * N, dB + (i + 1) * N, hB);
+            const float2 sA = Pop<T>::val2(hA), sB = Pop<T>::val2(hB);
+            ma -= (sA.x + wa) + (sA.y + wa);
+            mb -= (sB.x + wb) + (sB.y + wb);
+        }
+        p.dst0[n] = ma;
+        p.dst0[N + n] = mb;
+    }
+}
+
+// Collision of one node for any tau: pull again, Shan-Chen force, velocity
+// shift, BGK (Eqs. 4-5), store.
+template <typename T, bool DRY = false>
+__device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d) {
+    float fa[Q], fb[Q];
+    const uint32_t m = pull<T>(p, d, fa, fb);
+    const int n = d.n;
+    const float2 mr = __ldg(p.rho + n), mp = __ldg(p.psi + n);
+    const float ra = mr.x, rb = mr.y, pa = mp.x, pb = mp.y;
+    float FA[3], FB[3];
+    sc_force(p, d, m, ra, rb, pa, pb, FA, FB);
     float ja[3] = {0.f, 0.f, 0.f}, jb[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {  // opposite pairs (i, i+1)
@@ -351,125 +506,96 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
         p.out[4 * p.N + n] = (ja[2] + jb[2] + 0.5f * (FA[2] + FB[2])) / rt;
     }
     if (!(ra + rb < 1e30f)) atomicOr(p.status, ST_NAN);
-    float ca = 1.f, cb = 0.f;  // drying: A kept, B gained per unit weight
-    if (DRY && ra > rb) {
-        const float e = __ldg(p.dry_eps);
-        ca = 1.f - e;
-        cb = e * ra;
-    }
-    const float ka = 1.0f - 1.5f * (ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2]);
-    const float kb = 1.0f - 1.5f * (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
-    const int N = (int)p.N;
-    T *__restrict__ dA = static_cast<T *>(p.dst) + n;
-    T *__restrict__ dB = static_cast<T *>(p.dst) + (long long)Q * N + n;
-    const float ta = p.itau[0], tb = p.itau[1];
-    // Eq. 5 for opposite pairs: f^eq_{i,i+1} = w rho (ka + 4.5 eu^2 +- 3 eu); the
-    // rest population takes the mass balance (sum_i f^eq_i = rho) so that the
-    // float32 weights (which sum to 1 + 1.5e-8) create no mass
-    float qa0 = ra, qb0 = rb;
-    if (!Pop<T>::shifted) {
+    store_post<T, DRY, false>(p, n, ra, rb, ua, ub, fa, fb);
+}
+
+// Collision of one node with tau = 1 for both components: BGK then stores the
+// equilibria themselves, which need only the moments.  The density pass has
+// stored the total momentum J = sum_c sum_i f_i^c e_i, so the populations are
+// not pulled a second time.  The common velocity is u' = J / (rho_A + rho_B)
+// and u^{c,eq} = u' + F^c / rho^c (the velocity shift with tau = 1).
+template <typename T, bool DRY = false>
+__device__ __forceinline__ void collide_eq_node(const LBParams &p, const Deltas &d) {
+    const int n = d.n;
+    const uint32_t m = __ldg(p.mask + n);
+    const float2 mr = __ldg(p.rho + n), mp = __ldg(p.psi + n);
+    const float ra = mr.x, rb = mr.y, pa = mp.x, pb = mp.y;
+    float FA[3], FB[3];
+    sc_force(p, d, m, ra, rb, pa, pb, FA, FB);
+    const float4 J4 = __ldg(p.J + n);
+    const float J[3] = {J4.x, J4.y, J4.z};
+    const float rt = ra + rb, iden = 1.0f / rt, ia = 1.0f / ra, ib = 1.0f / rb;
+    float ua[3], ub[3];
 #pragma unroll
-        for (int i = 1; i < Q; i += 2) {
-            const float eua = ex(i) * ua[0] + ey(i) * ua[1] + ez(i) * ua[2];
-            const float eub = ex(i) * ub[0] + ey(i) * ub[1] + ez(i) * ub[2];
-            const float wa = wgt(i) * ra, wb = wgt(i) * rb;
-            const float sa_ = wa * (ka + 4.5f * eua * eua), sb_ = wb * (kb + 4.5f * eub * eub);
-            const float qa1 = sa_ + 3.0f * wa * eua, qa2 = sa_ - 3.0f * wa * eua;
-            const float qb1 = sb_ + 3.0f * wb * eub, qb2 = sb_ - 3.0f * wb * eub;
-            qa0 -= qa1 + qa2;
-            qb0 -= qb1 + qb2;
-            float va1 = fa[i] - (fa[i] - qa1) * ta, va2 = fa[i + 1] - (fa[i + 1] - qa2) * ta;
-            float vb1 = fb[i] - (fb[i] - qb1) * tb, vb2 = fb[i + 1] - (fb[i + 1] - qb2) * tb;
-            if (DRY) {
-                va1 *= ca; va2 *= ca;
-                vb1 += wgt(i) * cb; vb2 += wgt(i) * cb;
-            }
-            Pop<T>::st(dA + i * N, va1, 0u);
-            Pop<T>::st(dA + (i + 1) * N, va2, 0u);
-            Pop<T>::st(dB + i * N, vb1, 0u);
-            Pop<T>::st(dB + (i + 1) * N, vb2, 0u);
-        }
-        float va0 = fa[0] - (fa[0] - qa0) * ta, vb0 = fb[0] - (fb[0] - qb0) * tb;
-        if (DRY) {
-            va0 *= ca;
-            vb0 += wgt(0) * cb;
-        }
-        Pop<T>::st(dA, va0, 0u);
-        Pop<T>::st(dB, vb0, 0u);
-        return;
+    for (int a = 0; a < 3; ++a) {
+        const float up = J[a] * iden;
+        ua[a] = up + ia * FA[a];
+        ub[a] = up + ib * FB[a];
     }
-    // 16-bit offsets from w_i rho, stochastically rounded; the float rest
-    // population takes what the rounded moving populations leave of the mass
-    uint32_t rs = mix32((uint32_t)n * 0x9e3779b9u ^ mix32(*p.step_ctr));
-    float ma = ra, mb = rb;  // mass left for the rest populations
-    if (DRY) {
-        ma = ca * ra;
-        mb = rb + cb;
+    if (p.out) {
+        p.out[n] = ra;
+        p.out[p.N + n] = rb;
+        p.out[2 * p.N + n] = (J[0] + 0.5f * (FA[0] + FB[0])) / rt;
+        p.out[3 * p.N + n] = (J[1] + 0.5f * (FA[1] + FB[1])) / rt;
+        p.out[4 * p.N + n] = (J[2] + 0.5f * (FA[2] + FB[2])) / rt;
     }
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-        const float eua = ex(i) * ua[0] + ey(i) * ua[1] + ez(i) * ua[2];
-        const float eub = ex(i) * ub[0] + ey(i) * ub[1] + ez(i) * ub[2];
-        const float wa = wgt(i) * ra, wb = wgt(i) * rb;
-        const float sa_ = wa * (ka + 4.5f * eua * eua), sb_ = wb * (kb + 4.5f * eub * eub);
-        const float qa1 = sa_ + 3.0f * wa * eua, qa2 = sa_ - 3.0f * wa * eua;
-        const float qb1 = sb_ + 3.0f * wb * eub, qb2 = sb_ - 3.0f * wb * eub;
-        float va1 = fa[i] - (fa[i] - qa1) * ta, va2 = fa[i + 1] - (fa[i + 1] - qa2) * ta;
-        float vb1 = fb[i] - (fb[i] - qb1) * tb, vb2 = fb[i + 1] - (fb[i + 1] - qb2) * tb;
-        if (DRY) {
-            va1 *= ca; va2 *= ca;
-            vb1 += wgt(i) * cb; vb2 += wgt(i) * cb;
-        }
-        // an LCG step per store draws its rounding bits
-        rs = rs * 1664525u + 1013904223u;
-        ma -= Pop<T>::st(dA + i * N, va1 - wa, rs >> 8) + wa;
-        rs = rs * 1664525u + 1013904223u;
-        ma -= Pop<T>::st(dA + (i + 1) * N, va2 - wa, rs >> 8) + wa;
-        rs = rs * 1664525u + 1013904223u;
-        mb -= Pop<T>::st(dB + i * N, vb1 - wb, rs >> 8) + wb;
-        rs = rs * 1664525u + 1013904223u;
-        mb -= Pop<T>::st(dB + (i + 1) * N, vb2 - wb, rs >> 8) + wb;
-    }
-    p.dst0[n] = ma;
-    p.dst0[N + n] = mb;
+    if (!(ra + rb < 1e30f)) atomicOr(p.status, ST_NAN);
+    float unused[Q];  // the equilibria need no pulled populations
+    store_post<T, DRY, true>(p, n, ra, rb, ua, ub, unused, unused);
 }
 
 template <typename T, bool DRY = false>
-__global__ void __launch_bounds__(BX *BY, CF_COLLIDE_MINB) k_collide(const LBParams p) {
+__global__ void __launch_bounds__(BX *BY, Pop<T>::shifted ? CF_COLLIDE16_MINB : CF_COLLIDE_MINB)
+    k_collide(const LBParams p) {
     int x, y, z;
     if (!node_of<true>(p, x, y, z)) return;
     for (; z < p.zhi; z += gridDim.z) collide_node<T, DRY>(p, deltas(p, x, y, z));
+}
+
+// resident blocks per SM of the tau = 1 collide pass (no second pull: few registers)
+#ifndef CF_COLLIDE_EQ_MINB
+#define CF_COLLIDE_EQ_MINB 8
+#endif
+
+template <typename T, bool DRY = false>
+__global__ void __launch_bounds__(BX *BY, CF_COLLIDE_EQ_MINB) k_collide_eq(const LBParams p) {
+    int x, y, z;
+    if (!node_of<true>(p, x, y, z)) return;
+    for (; z < p.zhi; z += gridDim.z) collide_eq_node<T, DRY>(p, deltas(p, x, y, z));
 }
 
 size_t density_blocks_max(int nx, int ny, int nz) {
     return (size_t)((nx + BX - 1) / BX) * ((ny + BY - 1) / BY) * nz;
 }
 
+namespace {
+template <typename T, bool DRY>
+void lb_passes(const LBParams &p, dim3 grid, dim3 block, cudaStream_t s, bool eq) {
+    if (eq) {
+        k_density<T, DRY, true><<<grid, block, 0, s>>>(p);
+        k_collide_eq<T, DRY><<<grid, block, 0, s>>>(p);
+    } else {
+        k_density<T, DRY><<<grid, block, 0, s>>>(p);
+        k_collide<T, DRY><<<grid, block, 0, s>>>(p);
+    }
+}
+template <typename T>
+void lb_passes(const LBParams &p, dim3 grid, dim3 block, cudaStream_t s, bool dry, bool eq) {
+    if (dry) lb_passes<T, true>(p, grid, block, s, eq);
+    else lb_passes<T, false>(p, grid, block, s, eq);
+}
+}  // namespace
+
 cudaError_t launch_lb_step(const LBParams &p, int prec, cudaStream_t s) {
     const int nzf = p.zhi - p.zlo;
     const int gz = p.zchunk > 0 ? (nzf + p.zchunk - 1) / p.zchunk : nzf;
     dim3 grid((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, gz), block(BX, BY);
-    if (p.dry_dm > 0.0) {
-        if (prec == P_F16) {
-            k_density<__half, true><<<grid, block, 0, s>>>(p);
-            k_collide<__half, true><<<grid, block, 0, s>>>(p);
-        } else if (prec == P_BF16) {
-            k_density<__nv_bfloat16, true><<<grid, block, 0, s>>>(p);
-            k_collide<__nv_bfloat16, true><<<grid, block, 0, s>>>(p);
-        } else {
-            k_density<float, true><<<grid, block, 0, s>>>(p);
-            k_collide<float, true><<<grid, block, 0, s>>>(p);
-        }
-    } else if (prec == P_F16) {
-        k_density<__half><<<grid, block, 0, s>>>(p);
-        k_collide<__half><<<grid, block, 0, s>>>(p);
-    } else if (prec == P_BF16) {
-        k_density<__nv_bfloat16><<<grid, block, 0, s>>>(p);
-        k_collide<__nv_bfloat16><<<grid, block, 0, s>>>(p);
-    } else {
-        k_density<float><<<grid, block, 0, s>>>(p);
-        k_collide<float><<<grid, block, 0, s>>>(p);
-    }
+    const bool dry = p.dry_dm > 0.0;
+    // tau = 1 for both components: the collide pass takes the density pass's momentum
+    const bool eq = p.J != nullptr && p.tau[0] == 1.f && p.tau[1] == 1.f;
+    if (prec == P_F16) lb_passes<__half>(p, grid, block, s, dry, eq);
+    else if (prec == P_BF16) lb_passes<__nv_bfloat16>(p, grid, block, s, dry, eq);
+    else lb_passes<float>(p, grid, block, s, dry, eq);
     return cudaGetLastError();
 }
 
@@ -481,8 +607,10 @@ cudaError_t launch_lb_step(const LBParams &p, int prec, cudaStream_t s) {
 // a lattice stepped in a batch follows the same trajectory as alone.  The
 // collide pass walks the list backwards (the tiles the density pass read last
 // are still in L2).  Tile shapes (x width x y depth, the block shape) are
-// compiled in and chosen by the autotuner of the batch.
-template <typename T, int TX, int TY>
+// compiled in and chosen by the autotuner of the batch.  EQ: every lattice has
+// tau = 1, and the passes are those of the tau = 1 collision (momentum from
+// the density pass, no second pull).
+template <typename T, int TX, int TY, bool EQ>
 __global__ void __launch_bounds__(TX *TY) k_density_batch(const __grid_constant__ BatchTab tab,
                                                           const int4 *__restrict__ work, int nwork) {
     for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
@@ -493,19 +621,22 @@ __global__ void __launch_bounds__(TX *TY) k_density_batch(const __grid_constant_
             atomicAdd(p.step_ctr, 1u);  // read by the collide pass that follows
         const int x = it.y * TX + (int)threadIdx.x, y = it.z * TY + (int)threadIdx.y;
         if (x >= p.nx || y >= p.ny) continue;
-        for (int z = p.zlo + it.w; z < p.zhi; z += p.zstride) density_node<T>(p, deltas(p, x, y, z));
+        for (int z = p.zlo + it.w; z < p.zhi; z += p.zstride) density_node<T, EQ>(p, deltas(p, x, y, z));
     }
 }
 
-template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, (TX * TY >= 256 ? 2 : 5)) k_collide_batch(
+template <typename T, int TX, int TY, bool EQ>
+__global__ void __launch_bounds__(TX *TY, (TX * TY >= 256 ? 2 : (EQ ? 8 : 5))) k_collide_batch(
     const __grid_constant__ BatchTab tab, const int4 *__restrict__ work, int nwork) {
     for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
         const int4 it = __ldg(work + (nwork - 1 - w));
         const LBParams &p = tab.lat[it.x];
         const int x = it.y * TX + (int)threadIdx.x, y = it.z * TY + (int)threadIdx.y;
         if (x >= p.nx || y >= p.ny) continue;
-        for (int z = p.zlo + it.w; z < p.zhi; z += p.zstride) collide_node<T>(p, deltas(p, x, y, z));
+        for (int z = p.zlo + it.w; z < p.zhi; z += p.zstride) {
+            if (EQ) collide_eq_node<T>(p, deltas(p, x, y, z));
+            else collide_node<T>(p, deltas(p, x, y, z));
+        }
     }
 }
 
@@ -514,27 +645,39 @@ constexpr int TILE_X[CF_NTILES] = {32, 32, 32, 64, 64, 128};
 constexpr int TILE_Y[CF_NTILES] = {2, 4, 8, 2, 4, 2};
 
 template <typename T, int TX, int TY>
-void batch_kernels(const void *&kd, const void *&kc) {
-    kd = reinterpret_cast<const void *>(&k_density_batch<T, TX, TY>);
-    kc = reinterpret_cast<const void *>(&k_collide_batch<T, TX, TY>);
-}
-
-template <typename T>
-void batch_kernels_t(int tile, const void *&kd, const void *&kc) {
-    switch (tile) {
-    case 0: batch_kernels<T, 32, 2>(kd, kc); break;
-    case 1: batch_kernels<T, 32, 4>(kd, kc); break;
-    case 2: batch_kernels<T, 32, 8>(kd, kc); break;
-    case 3: batch_kernels<T, 64, 2>(kd, kc); break;
-    case 4: batch_kernels<T, 64, 4>(kd, kc); break;
-    default: batch_kernels<T, 128, 2>(kd, kc); break;
+void batch_kernels(bool eq, const void *&kd, const void *&kc) {
+    if (eq) {
+        kd = reinterpret_cast<const void *>(&k_density_batch<T, TX, TY, true>);
+        kc = reinterpret_cast<const void *>(&k_collide_batch<T, TX, TY, true>);
+    } else {
+        kd = reinterpret_cast<const void *>(&k_density_batch<T, TX, TY, false>);
+        kc = reinterpret_cast<const void *>(&k_collide_batch<T, TX, TY, false>);
     }
 }
 
-void batch_kernel_ptrs(int tile, int prec, const void *&kd, const void *&kc) {
-    if (prec == P_F16) batch_kernels_t<__half>(tile, kd, kc);
-    else if (prec == P_BF16) batch_kernels_t<__nv_bfloat16>(tile, kd, kc);
-    else batch_kernels_t<float>(tile, kd, kc);
+template <typename T>
+void batch_kernels_t(int tile, bool eq, const void *&kd, const void *&kc) {
+    switch (tile) {
+    case 0: batch_kernels<T, 32, 2>(eq, kd, kc); break;
+    case 1: batch_kernels<T, 32, 4>(eq, kd, kc); break;
+    case 2: batch_kernels<T, 32, 8>(eq, kd, kc); break;
+    case 3: batch_kernels<T, 64, 2>(eq, kd, kc); break;
+    case 4: batch_kernels<T, 64, 4>(eq, kd, kc); break;
+    default: batch_kernels<T, 128, 2>(eq, kd, kc); break;
+    }
+}
+
+void batch_kernel_ptrs(int tile, int prec, bool eq, const void *&kd, const void *&kc) {
+    if (prec == P_F16) batch_kernels_t<__half>(tile, eq, kd, kc);
+    else if (prec == P_BF16) batch_kernels_t<__nv_bfloat16>(tile, eq, kd, kc);
+    else batch_kernels_t<float>(tile, eq, kd, kc);
+}
+
+// tau = 1 in every lattice of the table (the tau = 1 passes apply)
+bool batch_eq(const BatchTab &tab, int nlat) {
+    for (int i = 0; i < nlat; ++i)
+        if (!tab.lat[i].J || tab.lat[i].tau[0] != 1.f || tab.lat[i].tau[1] != 1.f) return false;
+    return nlat > 0;
 }
 }  // namespace
 
@@ -544,30 +687,32 @@ void lb_batch_tile(int tile, int *tx, int *ty) {
     *ty = TILE_Y[tile];
 }
 
-int lb_batch_resident(int tile, int prec) {
-    static int cache[3][CF_NTILES] = {};
+int lb_batch_resident(int tile, int prec, bool eq) {
+    static int cache[2][3][CF_NTILES] = {};
     tile = std::min(std::max(tile, 0), CF_NTILES - 1);
     prec = std::min(std::max(prec, 0), 2);
-    if (cache[prec][tile] == 0) {
+    int &c = cache[eq ? 1 : 0][prec][tile];
+    if (c == 0) {
         const void *kd, *kc;
-        batch_kernel_ptrs(tile, prec, kd, kc);
+        batch_kernel_ptrs(tile, prec, eq, kd, kc);
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kc, TILE_X[tile] * TILE_Y[tile], 0);
-        cache[prec][tile] = sms * std::max(per_sm, 1);
+        c = sms * std::max(per_sm, 1);
     }
-    return cache[prec][tile];
+    return c;
 }
 
-cudaError_t launch_lb_batch(const BatchTab &tab, const int4 *work, int nwork, int prec, int tile,
+cudaError_t launch_lb_batch(const BatchTab &tab, int nlat, const int4 *work, int nwork, int prec, int tile,
                             cudaStream_t s) {
     tile = std::min(std::max(tile, 0), CF_NTILES - 1);
+    const bool eq = batch_eq(tab, nlat);
     const void *kd, *kc;
-    batch_kernel_ptrs(tile, prec, kd, kc);
+    batch_kernel_ptrs(tile, prec, eq, kd, kc);
     const dim3 block(TILE_X[tile], TILE_Y[tile]);
     // enough blocks to cover the list, at most a few waves of resident blocks
-    const unsigned grid = (unsigned)std::max(1, std::min(nwork, 4 * lb_batch_resident(tile, prec)));
+    const unsigned grid = (unsigned)std::max(1, std::min(nwork, 4 * lb_batch_resident(tile, prec, eq)));
     void *args[] = {const_cast<BatchTab *>(&tab), &work, &nwork};
     cudaError_t e = cudaLaunchKernel(kd, dim3(grid), block, args, 0, s);
     if (e != cudaSuccess) return e;
