@@ -308,7 +308,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_of(wl, world, l2_note(alg_bytes * wl.nodes)),
-        "roofline": {"bound": "hbm", "kernel": "lattice update: k_density + k_collide",
+        "roofline": {"bound": "hbm", "kernel": "lattice update: k_density + k_collide_eq (tau = 1)",
                      "achieved": achieved, "peak": peak,
                      "peak_kind": f"{peak_kind} copy bandwidth (burst)", "unit": "GB/s",
                      "frac": achieved / peak,

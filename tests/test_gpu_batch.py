@@ -78,6 +78,22 @@ def test_batch_matches_lone_runs(cfm, config):
     b.close()
 
 
+@pytest.mark.parametrize("config", [None, (4, 1)])
+def test_batch_with_other_tau_matches_lone_runs(cfm, config):
+    """One lattice with tau != 1: the batch takes the general collision for
+    all of them, and every lattice still follows its lone run."""
+    wls = mixed_workloads()
+    wls[1].tau = (0.8, 0.9)
+    b, sims = run_batch(cfm, wls, 25, config=config)
+    alone = run_alone(cfm, wls, 25)
+    for s, a, w in zip(sims, alone, wls):
+        tol = TOL_SAME if w.tau != (1.0, 1.0) else 1e-5  # tau = 1 lattices: other summation order
+        assert rel(s.populations().astype(np.float64), a.populations().astype(np.float64)) < tol
+        rs, _ = s.fields(); ra, _ = a.fields()
+        assert rel(rs, ra) < tol
+    b.close()
+
+
 def test_batch_free_capsules_vs_oracle(cfm):
     """Free capsules in a batch: every lattice against the FP64 oracle."""
     wls = mixed_workloads(mode=I.MODE_FREE)

@@ -58,6 +58,20 @@ def test_tiny_film_16bit(cfm, prec, mode):
 
 
 @pytest.mark.parametrize("prec", [1, 2])
+def test_tiny_film_16bit_other_tau(cfm, prec):
+    """The general collision (tau != 1) with 16-bit storage."""
+    wl = I.tiny_film(mode=I.MODE_FREE, steps=40)
+    wl.tau = (0.8, 0.8)
+    sim = cfm.Simulation.from_workload(wl, precision=prec)
+    orc = O.Oracle.from_workload(wl)
+    sim.step(wl.steps); orc.step(wl.steps)
+    e = errors(sim, orc)
+    print(prec, e)
+    for k, v in e.items():
+        assert v < BOUNDS[prec][k], (k, v)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
 def test_mass_16bit_no_capsule(cfm, prec):
     """The float rest population takes each node's mass balance after the
     offsets are rounded, so 16-bit storage changes the mass of a component
