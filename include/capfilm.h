@@ -170,6 +170,30 @@ cf_status cf_meniscus_field(cf_ctx *ctx, double *h);
 cf_status cf_meniscus_profile(cf_ctx *ctx, int id, double *r, double *zeta, size_t *inout_n,
                               double *Z);
 
+/* Meniscus height Z of capsule id: the largest zeta of its profile (the
+ * capillary rise read out in Sec. 4), as cf_meniscus_profile computes it. */
+cf_status cf_meniscus_height(cf_ctx *ctx, int id, double *Z);
+
+/* Checkpoint and restart (no counterpart in the paper; the runs reach 2e4 to
+ * 5e4 steps).  cf_save writes the state between two steps to `path`: the
+ * populations (and 16-bit storage's float rest populations), the densities
+ * they were encoded with, the last step's fields, the stochastic-rounding
+ * step counter, and with capsules the node positions and velocities, both
+ * exchange accumulators (the two-step average), element velocities,
+ * per-capsule sums, bounding boxes and the cut-link structure; also the step
+ * count and the drying rate.  A versioned binary file (native byte order).
+ * cf_load restores it into a context created with the same lattice
+ * description and the same capsules added in the same order; the run then
+ * continues bit for bit as it would have without the restart (capsules whose
+ * motion feeds back through atomic float sums excepted: those runs are not
+ * bitwise reproducible even without a restart).  Synchronous.
+ * Errors: CF_EINVAL (file cannot be opened, written or read, wrong version,
+ * or a context that does not match: the context is then unchanged, except
+ * for a truncated file, after which cf_set_film must come again),
+ * CF_ESTATE (cf_save before cf_set_film), CF_ECUDA. */
+cf_status cf_save(cf_ctx *ctx, const char *path);
+cf_status cf_load(cf_ctx *ctx, const char *path);
+
 /* Cut-link structure for the current membrane positions (diagnostics):
  * mask[N] bit (k-1) set when link n -> n + e_k crosses a membrane an odd number
  * of times; tri[N*18] the crossed element (global index) or -1; inside[N]
@@ -269,6 +293,10 @@ cf_status cf_batch_autotune(cf_batch *batch, int steps, int *tile, int *zchunk, 
 
 /* Number of kernel launches issued by the last cf_batch_step / cf_batch_time. */
 cf_status cf_batch_launch_count(const cf_batch *batch, long long *n);
+
+/* Lateral force (as cf_lateral_force) between capsules a and b of every
+ * context of the batch: F[i] for context i (n values, the batch's order). */
+cf_status cf_batch_lateral_forces(cf_batch *batch, int a, int b, double *F);
 
 /* ------------------------------------------------------- learned warm start
  * Kernels of a small 3-D convolutional network that predicts an equilibrated

@@ -106,6 +106,10 @@ def load_library(path: Optional[str] = None):
                             C.POINTER(C.c_int)],
         "cf_batch_autotune": [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp],
         "cf_batch_launch_count": [C.c_void_p, C.POINTER(C.c_longlong)],
+        "cf_batch_lateral_forces": [C.c_void_p, C.c_int, C.c_int, _dp],
+        "cf_save": [C.c_void_p, C.c_char_p],
+        "cf_load": [C.c_void_p, C.c_char_p],
+        "cf_meniscus_height": [C.c_void_p, C.c_int, _dp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -122,7 +126,8 @@ def exported_symbols():
             "cf_meniscus_field", "cf_meniscus_profile", "cf_cuts", "cf_launch_count",
             "cf_time_phases", "cf_lattice_step_static", "cf_batch_create", "cf_batch_destroy",
             "cf_batch_step", "cf_batch_time", "cf_batch_set_config", "cf_batch_config",
-            "cf_batch_autotune", "cf_batch_launch_count", "cf_set_densities", "cf_remove_mass", "cf_conv3d_forward",
+            "cf_batch_autotune", "cf_batch_launch_count", "cf_set_densities", "cf_remove_mass", "cf_save", "cf_load", "cf_meniscus_height",
+            "cf_batch_lateral_forces", "cf_conv3d_forward",
             "cf_conv3d_backward", "cf_mse", "cf_adam", "cf_to_bf16", "cf_from_bf16"]
 
 
@@ -283,6 +288,47 @@ class Simulation:
         _check(_lib.cf_launch_count(self._h, C.byref(n)))
         return n.value
 
+    def save(self, path):
+        """Checkpoint the state between two steps to a file (cf_save)."""
+        _check(_lib.cf_save(self._h, os.fsencode(path)))
+
+    def load(self, path):
+        """Restore a checkpoint into this simulation, set up like the saved one (cf_load)."""
+        _check(_lib.cf_load(self._h, os.fsencode(path)))
+
+    def meniscus_height(self, cid):
+        """Largest rise zeta of capsule cid's meniscus profile (cf_meniscus_height)."""
+        z = C.c_double()
+        _check(_lib.cf_meniscus_height(self._h, int(cid), C.byref(z)))
+        return z.value
+
+    def run(self, steps, every, log=None):
+        """Step `steps` times and read out every `every` steps: one record per
+        readout (steps done in this call, MLUPS over the interval including the
+        readout's synchronisation, total masses, per-capsule coupling forces,
+        meniscus heights), appended as a JSON line to `log` (a path)
+        when given.  Returns the records."""
+        import json
+        import time
+        recs = []
+        done = 0
+        while done < steps:
+            k = min(every, steps - done)
+            t0 = time.perf_counter()
+            self.step(k)
+            self.sync()
+            dt = time.perf_counter() - t0
+            done += k
+            forces = [self.capsule_force(c)[0].tolist() for c in range(len(self.nv))]
+            zs = [self.meniscus_height(c) for c in range(len(self.nv))]
+            rec = dict(step=done, mlups=self.N * k / dt / 1e6,
+                       mass=self.total_mass().tolist(), force=forces, Z=zs)
+            recs.append(rec)
+            if log is not None:
+                with open(log, "a") as f:
+                    f.write(json.dumps(rec) + "\n")
+        return recs
+
     def capsule_force(self, cid):
         F = np.zeros(3); T = np.zeros(3)
         _check(_lib.cf_capsule_force(self._h, cid, _ptr(F), _ptr(T)))
@@ -385,6 +431,12 @@ class Batch:
         n = C.c_longlong()
         _check(_lib.cf_batch_launch_count(self._h, C.byref(n)))
         return n.value
+
+    def lateral_forces(self, a=0, b=1):
+        """Lateral force between capsules a and b of every simulation (cf_batch_lateral_forces)."""
+        F = np.zeros(len(self.sims))
+        _check(_lib.cf_batch_lateral_forces(self._h, int(a), int(b), _ptr(F)))
+        return F
 
     def close(self):
         if getattr(self, "_h", None):

@@ -1012,6 +1012,134 @@ cf_status cf_meniscus_profile(cf_ctx *c, int id, double *r, double *zeta, size_t
     return CF_OK;
 }
 
+// ------------------------------------------------------------ checkpoints
+namespace {
+struct CkptHeader {
+    char magic[8];  // "CFCKPT01"
+    uint32_t version;
+    int32_t nx, ny, nz, wall, precision;
+    int32_t ncaps, nnodes, nfaces, capacity;
+    int32_t fpar, xpar, lpar, ftpar;
+    int32_t count;  // entries of the current cut-link list
+    int64_t steps_done;
+    double dry_dm;
+};
+constexpr uint32_t CKPT_VERSION = 1;
+
+// the device arrays of the state between two steps, in file order
+struct CkptPart {
+    void *dev;
+    size_t bytes;
+};
+std::vector<CkptPart> ckpt_parts(cf_ctx *c, int count) {
+    const long long N = c->N;
+    std::vector<CkptPart> v;
+    v.push_back({c->f[c->fpar], pop_bytes(c->d.precision) * 38 * (size_t)N});
+    if (c->d.precision != CF_FP32) v.push_back({c->f0[c->fpar], sizeof(float) * 2 * (size_t)N});
+    v.push_back({c->rho[c->fpar], sizeof(float2) * (size_t)N});
+    v.push_back({c->out, sizeof(float) * 5 * (size_t)N});
+    v.push_back({c->step_ctr, sizeof(unsigned)});
+    if (c->nnodes > 0) {
+        const size_t nv = c->nnodes, nf = c->nfaces, nc = c->caps.size();
+        v.push_back({c->X[c->xpar], sizeof(float) * 6 * nv});
+        v.push_back({c->V, sizeof(float) * 3 * nv});
+        v.push_back({c->FT[0], sizeof(float) * 3 * nf});
+        v.push_back({c->FT[1], sizeof(float) * 3 * nf});
+        v.push_back({c->uT, sizeof(float4) * nf});
+        v.push_back({c->acc, sizeof(double) * A_NACC * nc});
+        v.push_back({c->bbox[0], sizeof(int) * 6 * nc});
+        v.push_back({c->bbox[1], sizeof(int) * 6 * nc});
+        v.push_back({c->mask, sizeof(uint32_t) * (size_t)N});
+        v.push_back({c->tri, sizeof(int) * 18 * (size_t)N});
+        v.push_back({c->list[c->lpar], sizeof(int2) * (size_t)count});
+    }
+    return v;
+}
+}  // namespace
+
+cf_status cf_save(cf_ctx *c, const char *path) {
+    if (!c || !path) return fail(CF_EINVAL, "null argument");
+    if (!c->film_set) return fail(CF_ESTATE, "nothing to save before cf_set_film");
+    cf_status s = sync_ok(c);
+    if (s != CF_OK) return s;
+    CkptHeader h{};
+    std::memcpy(h.magic, "CFCKPT01", 8);
+    h.version = CKPT_VERSION;
+    h.nx = c->d.nx; h.ny = c->d.ny; h.nz = c->d.nz; h.wall = c->d.wall; h.precision = c->d.precision;
+    h.ncaps = (int)c->caps.size(); h.nnodes = c->nnodes; h.nfaces = c->nfaces; h.capacity = c->capacity;
+    h.fpar = c->fpar; h.xpar = c->xpar; h.lpar = c->lpar; h.ftpar = c->ftpar;
+    h.steps_done = c->steps_done;
+    h.dry_dm = c->dry_dm;
+    int count = 0;
+    if (c->nnodes > 0) CF_CUDA(cudaMemcpy(&count, c->counts + c->lpar, sizeof(int), cudaMemcpyDeviceToHost));
+    h.count = count;
+    FILE *fp = std::fopen(path, "wb");
+    if (!fp) return fail(CF_EINVAL, std::string("cannot open for writing: ") + path);
+    bool ok = std::fwrite(&h, sizeof h, 1, fp) == 1;
+    std::vector<char> buf;
+    for (const CkptPart &part : ckpt_parts(c, count)) {
+        if (!ok) break;
+        buf.resize(part.bytes);
+        if (cudaMemcpy(buf.data(), part.dev, part.bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            std::fclose(fp);
+            return fail(CF_ECUDA, "device copy failed while saving");
+        }
+        ok = std::fwrite(buf.data(), 1, part.bytes, fp) == part.bytes;
+    }
+    ok = (std::fclose(fp) == 0) && ok;
+    if (!ok) return fail(CF_EINVAL, std::string("write failed: ") + path);
+    return CF_OK;
+}
+
+cf_status cf_load(cf_ctx *c, const char *path) {
+    if (!c || !path) return fail(CF_EINVAL, "null argument");
+    FILE *fp = std::fopen(path, "rb");
+    if (!fp) return fail(CF_EINVAL, std::string("cannot open: ") + path);
+    CkptHeader h{};
+    if (std::fread(&h, sizeof h, 1, fp) != 1 || std::memcmp(h.magic, "CFCKPT01", 8) != 0 ||
+        h.version != CKPT_VERSION) {
+        std::fclose(fp);
+        return fail(CF_EINVAL, "not a checkpoint of this version");
+    }
+    if (h.nx != c->d.nx || h.ny != c->d.ny || h.nz != c->d.nz || h.wall != c->d.wall ||
+        h.precision != c->d.precision || h.ncaps != (int)c->caps.size() || h.nnodes != c->nnodes ||
+        h.nfaces != c->nfaces || h.capacity != c->capacity || h.count < 0 || h.count > c->capacity ||
+        (h.fpar | h.xpar | h.lpar | h.ftpar) & ~1) {
+        std::fclose(fp);
+        return fail(CF_EINVAL, "checkpoint does not match this context (lattice, precision or capsules)");
+    }
+    cf_status s = sync_ok(c);
+    if (s != CF_OK) { std::fclose(fp); return s; }
+    c->fpar = h.fpar; c->xpar = h.xpar; c->lpar = h.lpar; c->ftpar = h.ftpar;
+    std::vector<char> buf;
+    for (const CkptPart &part : ckpt_parts(c, h.count)) {
+        buf.resize(part.bytes);
+        if (std::fread(buf.data(), 1, part.bytes, fp) != part.bytes) {
+            std::fclose(fp);
+            c->film_set = false;  // partly loaded: unusable until set up again
+            return fail(CF_EINVAL, "checkpoint is truncated");
+        }
+        if (cudaMemcpy(part.dev, buf.data(), part.bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+            std::fclose(fp);
+            c->film_set = false;
+            return fail(CF_ECUDA, "device copy failed while loading");
+        }
+    }
+    std::fclose(fp);
+    if (c->nnodes > 0) CF_CUDA(cudaMemcpy(c->counts + c->lpar, &h.count, sizeof(int), cudaMemcpyHostToDevice));
+    c->steps_done = h.steps_done;
+    c->film_set = true;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_key = -1; }
+    return cf_remove_mass(c, h.dry_dm);
+}
+
+cf_status cf_meniscus_height(cf_ctx *c, int id, double *Z) {
+    if (!c || !Z) return fail(CF_EINVAL, "null argument");
+    size_t n = (size_t)(std::min(c->d.nx, c->d.ny) / 2);
+    std::vector<double> r(std::max<size_t>(n, 1)), zeta(std::max<size_t>(n, 1));
+    return cf_meniscus_profile(c, id, r.data(), zeta.data(), &n, Z);
+}
+
 cf_status cf_cuts(cf_ctx *c, uint32_t *mask, int *tri, uint8_t *inside) {
     if (!c) return fail(CF_EINVAL, "null context");
     const long long N = c->N;
@@ -1304,6 +1432,15 @@ cf_status cf_batch_autotune(cf_batch *b, int steps, int *tile_out, int *zchunk_o
     if (tile_out) *tile_out = bt;
     if (zchunk_out) *zchunk_out = bz;
     if (ms_out) *ms_out = best / (2 * pairs);
+    return CF_OK;
+}
+
+cf_status cf_batch_lateral_forces(cf_batch *b, int a, int bb, double *F) {
+    if (!b || !F) return fail(CF_EINVAL, "null argument");
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        cf_status s = cf_lateral_force(b->ctx[i], a, bb, F + i);
+        if (s != CF_OK) return s;
+    }
     return CF_OK;
 }
 
