@@ -5,6 +5,32 @@
 
 namespace cf {
 
+// Programmatic dependent launch.  The kernels of the step's critical path are
+// launched with the programmatic-serialization attribute: the next kernel on
+// the stream may be scheduled while its predecessor's last blocks run.  Each
+// such kernel first lets its own successor be scheduled (pdl_trigger) and
+// then waits until its predecessor has completed with all writes visible
+// (pdl_wait), before it touches any memory.  For a normal launch both are
+// no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch a kernel whose first statements are pdl_trigger(); pdl_wait();
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // D3Q19 (Sec. 3.1): rest, six face neighbours (w = 1/18), twelve edge
 // neighbours (w = 1/36); opposite directions are adjacent pairs.
 __host__ __device__ constexpr int ex(int i) {

@@ -299,6 +299,8 @@ __device__ __forceinline__ void dry_reduce(const LBParams &p, float s) {
 // MOM: also the total momentum (tau = 1 collision)
 template <typename T, bool DRY = false, bool MOM = false>
 __global__ void __launch_bounds__(BX *BY, MOM ? CF_DENSITY_MOM_MINB : CF_DENSITY_MINB) k_density(const LBParams p) {
+    pdl_trigger();
+    pdl_wait();
     if (Pop<T>::shifted && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 &&
         threadIdx.x == 0 && threadIdx.y == 0)
         atomicAdd(p.step_ctr, 1u);  // read by the collide pass that follows
@@ -547,6 +549,8 @@ __device__ __forceinline__ void collide_eq_node(const LBParams &p, const Deltas 
 template <typename T, bool DRY = false>
 __global__ void __launch_bounds__(BX *BY, Pop<T>::shifted ? CF_COLLIDE16_MINB : CF_COLLIDE_MINB)
     k_collide(const LBParams p) {
+    pdl_trigger();
+    pdl_wait();
     int x, y, z;
     if (!node_of<true>(p, x, y, z)) return;
     for (; z < p.zhi; z += gridDim.z) collide_node<T, DRY>(p, deltas(p, x, y, z));
@@ -559,6 +563,8 @@ __global__ void __launch_bounds__(BX *BY, Pop<T>::shifted ? CF_COLLIDE16_MINB : 
 
 template <typename T, bool DRY = false>
 __global__ void __launch_bounds__(BX *BY, CF_COLLIDE_EQ_MINB) k_collide_eq(const LBParams p) {
+    pdl_trigger();
+    pdl_wait();
     int x, y, z;
     if (!node_of<true>(p, x, y, z)) return;
     for (; z < p.zhi; z += gridDim.z) collide_eq_node<T, DRY>(p, deltas(p, x, y, z));
@@ -572,11 +578,11 @@ namespace {
 template <typename T, bool DRY>
 void lb_passes(const LBParams &p, dim3 grid, dim3 block, cudaStream_t s, bool eq) {
     if (eq) {
-        k_density<T, DRY, true><<<grid, block, 0, s>>>(p);
-        k_collide_eq<T, DRY><<<grid, block, 0, s>>>(p);
+        launch_pdl(k_density<T, DRY, true>, grid, block, s, p);
+        launch_pdl(k_collide_eq<T, DRY>, grid, block, s, p);
     } else {
-        k_density<T, DRY><<<grid, block, 0, s>>>(p);
-        k_collide<T, DRY><<<grid, block, 0, s>>>(p);
+        launch_pdl(k_density<T, DRY>, grid, block, s, p);
+        launch_pdl(k_collide<T, DRY>, grid, block, s, p);
     }
 }
 template <typename T>

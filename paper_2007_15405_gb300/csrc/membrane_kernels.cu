@@ -370,6 +370,8 @@ __global__ void __launch_bounds__(MT) k_mem_bending(const MemParams p) {
 //    link: its mask word and crossed element are reset) before the cut links
 //    of the new positions are marked.
 __global__ void __launch_bounds__(MV) k_mem_update(const MemParams p, const ClearParams cl) {
+    pdl_trigger();
+    pdl_wait();
     const int node_blocks = (p.nnodes + MV - 1) / MV;
     if ((int)blockIdx.x >= node_blocks) {
         const int cnt = min(*cl.count, cl.capacity);
@@ -444,7 +446,7 @@ cudaError_t launch_membrane_forces(const MemParams &p, cudaStream_t s, int *nl) 
 cudaError_t launch_membrane_update(const MemParams &p, const ClearParams &cl, bool any_frozen,
                                    cudaStream_t s, int *nl) {
     const unsigned gv = (unsigned)((p.nnodes + MV - 1) / MV);
-    k_mem_update<<<gv + (unsigned)cl.blocks, MV, 0, s>>>(p, cl);
+    launch_pdl(k_mem_update, dim3(gv + (unsigned)cl.blocks), dim3(MV), s, p, cl);
     *nl += 1;
     if (any_frozen) {
         k_mem_frozen<<<gv, MV, 0, s>>>(p);
@@ -521,6 +523,8 @@ __device__ __forceinline__ bool plane_side(const f3 &nrm, const f3 &A, const f3 
 }
 
 __global__ void __launch_bounds__(32 * CUT_WPB, 4) k_cut_faces(const CutParams p) {
+    pdl_trigger();
+    pdl_wait();
     const unsigned full = 0xffffffffu;
     const int lane = (int)(threadIdx.x & 31);
     const int T = blockIdx.x * CUT_WPB + (int)(threadIdx.x >> 5);
@@ -633,7 +637,7 @@ __global__ void __launch_bounds__(32 * CUT_WPB, 4) k_cut_faces(const CutParams p
 }
 
 cudaError_t launch_cuts(const CutParams &p, cudaStream_t s, int *nl) {
-    k_cut_faces<<<(p.nfaces + CUT_WPB - 1) / CUT_WPB, 32 * CUT_WPB, 0, s>>>(p);
+    launch_pdl(k_cut_faces, dim3((p.nfaces + CUT_WPB - 1) / CUT_WPB), dim3(32 * CUT_WPB), s, p);
     *nl += 1;
     return cudaGetLastError();
 }
@@ -659,6 +663,8 @@ __device__ __forceinline__ float pop_at(const PrepParams &p, int c, int k, long 
 // smallest one (the element kept in tri) writes the record, and a link whose
 // crossings cancelled out (even count, cut bit clear) writes none.
 __global__ void k_cut_prep(const PrepParams p) {
+    pdl_trigger();
+    pdl_wait();
     const int cnt = min(*p.count, p.capacity);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
         const int2 e = __ldg(p.list + i);
@@ -685,7 +691,7 @@ __global__ void k_cut_prep(const PrepParams p) {
 }
 
 cudaError_t launch_prep(const PrepParams &p, cudaStream_t s, int *nl) {
-    k_cut_prep<<<2 * 152, 256, 0, s>>>(p);
+    launch_pdl(k_cut_prep, dim3(2 * 152), dim3(256), s, p);
     *nl += 1;
     return cudaGetLastError();
 }
