@@ -241,7 +241,8 @@ MemParams mem_params(cf_ctx *c) {
 }
 
 // Cut links for positions X (cur list lpar, clears the other list's nodes).
-cf_status enqueue_cuts(cf_ctx *c, const float *X, int *nl) {
+// zeroed: the node update has already zeroed the new list's entry counter
+cf_status enqueue_cuts(cf_ctx *c, const float *X, int *nl, bool zeroed = false) {
     if (c->nfaces == 0) return CF_OK;
     const int cur = 1 - c->lpar;
     CutParams q{};
@@ -258,7 +259,7 @@ cf_status enqueue_cuts(cf_ctx *c, const float *X, int *nl) {
     q.uT = c->uT;
     q.capacity = c->capacity;
     q.status = c->status;
-    CF_CUDA(cudaMemsetAsync(c->counts + cur, 0, sizeof(int), c->stream));
+    if (!zeroed) CF_CUDA(cudaMemsetAsync(c->counts + cur, 0, sizeof(int), c->stream));
     CF_CUDA(launch_cuts(q, c->stream, nl));
     c->lpar = cur;
     return CF_OK;
@@ -322,6 +323,7 @@ cf_status enqueue_post(cf_ctx *c, int *nl, cudaEvent_t ev2 = nullptr) {
             cl.mask = c->mask;
             cl.tri = c->tri;
             cl.blocks = 304;
+            cl.count_next = c->counts + (1 - c->lpar);  // the cut links' memset, done by the update
         }
         CF_CUDA(launch_membrane_update(mem_params(c), cl, c->any_frozen, c->stream, nl));
         c->xpar = 1 - c->xpar;
@@ -330,7 +332,7 @@ cf_status enqueue_post(cf_ctx *c, int *nl, cudaEvent_t ev2 = nullptr) {
     if (mem) {
         if (!c->all_fixed) {
             // also zeroes the exchange accumulator of the next step
-            cf_status s = enqueue_cuts(c, c->X[c->xpar], nl);
+            cf_status s = enqueue_cuts(c, c->X[c->xpar], nl, true);
             if (s != CF_OK) return s;
         } else {
             CF_CUDA(cudaMemsetAsync(c->FT[1 - c->ftpar], 0, sizeof(float) * 3 * (size_t)c->nfaces,

@@ -192,6 +192,7 @@ struct ClearParams {
     uint32_t *mask;
     int *tri;
     int blocks;              // blocks of the update kernel given to the reset (0: none)
+    int *count_next;         // entry counter of the list about to be built: zeroed (may be null)
 };
 
 // Bounce records of the cut links for the next streaming (built once per step).

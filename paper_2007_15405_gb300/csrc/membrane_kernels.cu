@@ -372,6 +372,7 @@ __global__ void __launch_bounds__(MT) k_mem_bending(const MemParams p) {
 __global__ void __launch_bounds__(MV) k_mem_update(const MemParams p, const ClearParams cl) {
     pdl_trigger();
     pdl_wait();
+    if (cl.count_next && blockIdx.x == 0 && threadIdx.x == 0) *cl.count_next = 0;
     const int node_blocks = (p.nnodes + MV - 1) / MV;
     if ((int)blockIdx.x >= node_blocks) {
         const int cnt = min(*cl.count, cl.capacity);
