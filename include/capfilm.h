@@ -106,8 +106,18 @@ typedef struct cf_ctx cf_ctx;
 const char *cf_last_error(void);
 
 /* Lattice and film set-up (Sec. 3.2).  Allocates the populations and the
- * coupling structures; populations start at zero until cf_set_film. */
+ * coupling structures; populations start at zero until cf_set_film.  With
+ * tau = 1 for both components the collision stores the equilibria computed
+ * from the moments of the density pass (no second pull of the populations);
+ * any other tau relaxes the pulled populations.
+ * Errors (checked before any CUDA call): CF_EINVAL for a null argument, a
+ * dimension below 3, a lattice with 38 * nx * ny * nz >= 2^31 (32-bit
+ * population offsets: at most 56.5 million nodes), tau <= 1/2 or not a
+ * number, an unknown precision; then CF_ECUDA (stream or event creation) and
+ * CF_ENOMEM (an allocation failed: all blocks obtained are given back). */
 cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out);
+/* Frees the context and everything it allocated; a null context is a no-op
+ * (CF_OK). */
 cf_status cf_destroy(cf_ctx *ctx);
 
 /* Capsule insertion with its elastic moduli (Sec. 3.1, Eqs. 6-8).  The given
