@@ -7,18 +7,24 @@
 // psi = 1 - exp(-rho), the Shan-Chen force (Eq. 10) with the interior/exterior
 // decoupling, and the BGK collision (Eqs. 4-5) with the velocity-shift forcing.
 //
-//   k_density   per node: sum the 38 streamed populations, write
-//               (rho_A, rho_B) and (psi_A, psi_B) as two float2
-//   k_collide   per node: gather the 38 streamed populations again, read the
-//               pseudopotentials of the 18 neighbours (float2, L1/L2 resident),
-//               Shan-Chen force, velocity shift, BGK, store
+//   k_density     per node: sum the 38 streamed populations, write
+//                 (rho_A, rho_B) and (psi_A, psi_B) as two float2, and for
+//                 tau = 1 the total momentum J as a float4
+//   k_collide_eq  tau = 1: read rho, psi, J of the node and the
+//                 pseudopotentials of the 18 neighbours (float2, L1/L2
+//                 resident), Shan-Chen force, velocity shift, store the
+//                 equilibria (BGK with tau = 1)
+//   k_collide     any tau: gather the 38 streamed populations again, then as
+//                 above with the BGK relaxation of the pulled populations
 //
-// Layout: populations f[c][i][z][y][x] (float), two buffers (src -> dst);
-// threads map to x so every gather is a coalesced row.  Both passes are
-// barrier-free and run at high occupancy; DRAM traffic per node update is
-// 2 x 152 B of population reads + 152 B of writes + 16 B of density writes.
-// Gather addresses are the node index plus per-direction offsets with the
-// periodic wrap folded into per-node deltas.
+// Layout: populations f[c][i][z][y][x] (float, or 16-bit offsets with float
+// rest populations), two buffers (src -> dst); threads map to x so every
+// gather is a coalesced row.  Both passes are barrier-free.  DRAM traffic per
+// node update with tau = 1: 152 B of population reads and 32 B of density,
+// pseudopotential and momentum writes in the density pass, 36 B of reads and
+// 152 B of population writes in the collide pass.  Gather addresses are the
+// node index plus per-direction offsets with the periodic wrap folded into
+// per-node deltas.
 #include "cf_common.cuh"
 #include "../../include/capfilm.h"
 
