@@ -671,16 +671,19 @@ __global__ void k_cut_prep(const PrepParams p) {
         const int2 e = __ldg(p.list + i);
         const long long n = (long long)((unsigned)e.x >> 5);
         const int k1 = e.x & 31, k = k1 + 1, T = e.y;
-        if (!((__ldg(p.mask + n) >> k1) & 1u)) continue;
-        if (__ldg(p.tri + n * 18 + k1) != T) continue;
+        // every load the entry needs is issued before its checks (the
+        // addresses are valid for any entry), so the loads overlap
+        const uint32_t m = __ldg(p.mask + n);
+        const int t = __ldg(p.tri + n * 18 + k1);
         // the node's density: the sum of its post-collision populations equals
         // the density of the step that produced them (BGK conserves mass)
         const float2 dn = __ldg(p.rho + n);
+        const float4 u = __ldg(p.uT + T);  // recorded by k_cut_faces
+        const float foa = pop_at(p, 0, k, n, dn.x), fob = pop_at(p, 1, k, n, dn.y);
+        if (!((m >> k1) & 1u) || t != T) continue;
         int kx, ky, kz;
         ek(k, kx, ky, kz);
-        const float4 u = __ldg(p.uT + T);  // recorded by k_cut_faces
         const float eu = kx * u.x + ky * u.y + kz * u.z;
-        const float foa = pop_at(p, 0, k, n, dn.x), fob = pop_at(p, 1, k, n, dn.y);
         const float w6 = 6.0f * wgt(k);
         const float ca = w6 * dn.x * eu, cb = w6 * dn.y * eu;
         p.rec[n * 18 + (opp(k) - 1)] = make_float2(foa - ca, fob - cb);
