@@ -346,6 +346,46 @@ cf_status cf_adam(float *w, void *w_bf16, const float *g, float *m1, float *m2, 
 cf_status cf_to_bf16(const float *x, void *y, long long n, void *stream);
 cf_status cf_from_bf16(const void *x, float *y, long long n, void *stream);
 
+/* Set-up of the warm start on a context (after its capsules are added; all
+ * arrays are device arrays of the caller, [c][nz][ny][nx] float32; the film
+ * is the one cf_set_film(h_top, rho_maj, rho_min, rho_mix) would make, and
+ * its mixed plane is floor(h_top + 1/2)).  Synchronous; CF_EINVAL for null
+ * arrays or bad parameters.
+ *
+ * cf_warm_features: the network inputs x [4][N] (capsule interior flag; the
+ * flat film's phi = +1 below the mixed plane, 0 in it and on the substrate,
+ * -1 above and inside capsules; z / nz; log10(kS) + 2) and, if mask is not
+ * NULL, the fluid mask [N] (1 outside the capsules and off the substrate). */
+cf_status cf_warm_features(cf_ctx *ctx, double h_top, double kS, float *x, float *mask);
+
+/* cf_warm_apply: the state predicted by the network from its corrections d
+ * [2][N] (in units of rho_maj - rho_min): the film's densities plus the
+ * corrections on the fluid outside the capsules (at least 1e-3), the film's
+ * inside them and on the substrate; each component is then scaled on that
+ * fluid to the flat film's mass (the run conserves mass, so a start with
+ * other masses would relax to another equilibrium).  Populations at rest
+ * (Eq. 5 with u = 0), as cf_set_densities.  The sums are reduced on the
+ * device in a fixed order. */
+cf_status cf_warm_apply(cf_ctx *ctx, double h_top, double rho_maj, double rho_min, double rho_mix,
+                        const float *d);
+
+/* cf_warm_target: the training target of the current state (the fields of
+ * the last step), t [2][N] = (rho_c - rho_c,film) / (rho_maj - rho_min) on the
+ * fluid outside the capsules, 0 elsewhere.  CF_ESTATE before the state is
+ * set (cf_set_film, cf_set_densities, cf_warm_apply or cf_load); step first,
+ * as the fields are recorded by the steps. */
+cf_status cf_warm_target(cf_ctx *ctx, double h_top, double rho_maj, double rho_min, double rho_mix,
+                         float *t);
+
+/* cf_field_check: residual statistics of the fields of the last step, for
+ * judging a warm start: out[0] = 1 if every density and velocity is finite
+ * (else 0), out[1] = smallest density, out[2] = largest |u| component,
+ * out[3] = mean |rho - rho_prev| over both components and all nodes, rho_prev
+ * being the densities of the previous cf_field_check call on this context
+ * (zero for the first).  CF_ESTATE before the state is set; step first, as
+ * the fields are recorded by the steps. */
+cf_status cf_field_check(cf_ctx *ctx, double out[4]);
+
 #ifdef __cplusplus
 }
 #endif

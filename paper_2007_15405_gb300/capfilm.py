@@ -53,6 +53,11 @@ _dp = C.POINTER(C.c_double)
 _fp = C.POINTER(C.c_float)
 
 
+def _dptr(t):
+    """Device pointer of a torch tensor (None stays NULL)."""
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
 def load_library(path: Optional[str] = None):
     """Load libcapfilm.so (raises if it has not been built)."""
     global _lib
@@ -110,6 +115,10 @@ def load_library(path: Optional[str] = None):
         "cf_save": [C.c_void_p, C.c_char_p],
         "cf_load": [C.c_void_p, C.c_char_p],
         "cf_meniscus_height": [C.c_void_p, C.c_int, _dp],
+        "cf_warm_features": [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p],
+        "cf_warm_apply": [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p],
+        "cf_warm_target": [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p],
+        "cf_field_check": [C.c_void_p, _dp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -127,7 +136,8 @@ def exported_symbols():
             "cf_time_phases", "cf_lattice_step_static", "cf_batch_create", "cf_batch_destroy",
             "cf_batch_step", "cf_batch_time", "cf_batch_set_config", "cf_batch_config",
             "cf_batch_autotune", "cf_batch_launch_count", "cf_set_densities", "cf_remove_mass", "cf_save", "cf_load", "cf_meniscus_height",
-            "cf_batch_lateral_forces", "cf_conv3d_forward",
+            "cf_batch_lateral_forces", "cf_warm_features", "cf_warm_apply", "cf_warm_target",
+            "cf_field_check", "cf_conv3d_forward",
             "cf_conv3d_backward", "cf_mse", "cf_adam", "cf_to_bf16", "cf_from_bf16"]
 
 
@@ -287,6 +297,25 @@ class Simulation:
         n = C.c_longlong()
         _check(_lib.cf_launch_count(self._h, C.byref(n)))
         return n.value
+
+    def warm_features(self, h_top, kS, x, mask=None):
+        """Network inputs into device tensor x [4][N] and the fluid mask [N] (cf_warm_features)."""
+        _check(_lib.cf_warm_features(self._h, float(h_top), float(kS), _dptr(x), _dptr(mask)))
+
+    def warm_apply(self, h_top, rho_maj, rho_min, rho_mix, d):
+        """State from predicted corrections d (device [2][N]) (cf_warm_apply)."""
+        _check(_lib.cf_warm_apply(self._h, float(h_top), rho_maj, rho_min, rho_mix, _dptr(d)))
+
+    def warm_target(self, h_top, rho_maj, rho_min, rho_mix, t):
+        """Training target of the current state into device tensor t [2][N] (cf_warm_target)."""
+        _check(_lib.cf_warm_target(self._h, float(h_top), rho_maj, rho_min, rho_mix, _dptr(t)))
+
+    def field_check(self):
+        """(all finite, smallest density, largest |u|, mean |rho - rho at the previous check|)
+        of the last step's fields (cf_field_check)."""
+        out = np.zeros(4)
+        _check(_lib.cf_field_check(self._h, _ptr(out)))
+        return out
 
     def save(self, path):
         """Checkpoint the state between two steps to a file (cf_save)."""

@@ -129,6 +129,11 @@ struct cf_ctx {
     int graph_key = -1;
     int graph_launches = 0;  // kernel launches of one graph replay (two steps)
 
+    // learned warm start: partial sums, density snapshot, check results
+    double *warm_part = nullptr;
+    float *snap = nullptr;
+    double *warm_res = nullptr;
+
     // drying: A mass turned into B per step, and the reduction scratch
     double dry_dm = 0.0;
     double *dry_part = nullptr;
@@ -737,6 +742,76 @@ cf_status cf_set_densities(cf_ctx *c, const double *rhoA, const double *rhoB) {
     CF_CUDA(launch_init_dens(c->f[c->fpar], c->f0[c->fpar], c->d.precision, c->rho[c->fpar], N, c->d.nx,
                              c->d.ny, c->d.wall, c->jit, c->stream));
     c->film_set = true;
+    return sync_ok(c);
+}
+
+// ------------------------------------------------ learned warm start set-up
+namespace {
+WarmGeom warm_geom(const cf_ctx *c, double h_top, double rmaj, double rmin, double rmix) {
+    WarmGeom g{};
+    g.nx = c->d.nx; g.ny = c->d.ny; g.nz = c->d.nz; g.wall = c->d.wall;
+    g.N = c->N;
+    g.zm = (int)std::floor(h_top + 0.5);
+    g.rmaj = rmaj; g.rmin = rmin; g.rmix = rmix; g.drho = rmaj - rmin;
+    return g;
+}
+cf_status warm_scratch(cf_ctx *c) {
+    if (!c->warm_part) {
+        c->warm_part = (double *)dalloc(c, sizeof(double) * 4 * (size_t)warm_parts());
+        c->warm_res = (double *)dalloc(c, sizeof(double) * 4);
+        c->snap = (float *)dalloc(c, sizeof(float) * 2 * (size_t)c->N);
+        if (!c->warm_part || !c->warm_res || !c->snap) return fail(CF_ENOMEM, "device allocation failed (warm start)");
+        CF_CUDA(cudaMemsetAsync(c->snap, 0, sizeof(float) * 2 * (size_t)c->N, c->stream));
+    }
+    if (!c->jit) {
+        c->jit = (double *)dalloc(c, sizeof(double) * 2 * c->N);
+        if (!c->jit) return fail(CF_ENOMEM, "device allocation failed (densities)");
+        c->allocations.pop_back();  // freed explicitly
+    }
+    return CF_OK;
+}
+}  // namespace
+
+cf_status cf_warm_features(cf_ctx *c, double h_top, double kS, float *x, float *mask) {
+    if (!c || !x) return fail(CF_EINVAL, "null argument");
+    if (!(kS > 0.0)) return fail(CF_EINVAL, "kS must be positive");
+    if (c->nfaces) CF_CUDA(launch_inside(c->mask, c->inside, c->d.nx, c->d.ny, c->d.nz, c->stream));
+    const WarmGeom g = warm_geom(c, h_top, 0.0, 0.0, 0.0);
+    CF_CUDA(launch_warm_features(g, c->inside, (float)(std::log10(kS) + 2.0), x, mask, c->stream));
+    return sync_ok(c);
+}
+
+cf_status cf_warm_apply(cf_ctx *c, double h_top, double rmaj, double rmin, double rmix, const float *d) {
+    if (!c || !d) return fail(CF_EINVAL, "null argument");
+    if (!(rmaj > rmin)) return fail(CF_EINVAL, "rho_maj must exceed rho_min");
+    cf_status s = warm_scratch(c);
+    if (s != CF_OK) return s;
+    if (c->nfaces) CF_CUDA(launch_inside(c->mask, c->inside, c->d.nx, c->d.ny, c->d.nz, c->stream));
+    const WarmGeom g = warm_geom(c, h_top, rmaj, rmin, rmix);
+    CF_CUDA(launch_warm_densities(g, c->inside, d, c->jit, c->warm_part, c->stream));
+    CF_CUDA(launch_init_dens(c->f[c->fpar], c->f0[c->fpar], c->d.precision, c->rho[c->fpar], c->N, c->d.nx,
+                             c->d.ny, c->d.wall, c->jit, c->stream));
+    c->film_set = true;
+    return sync_ok(c);
+}
+
+cf_status cf_warm_target(cf_ctx *c, double h_top, double rmaj, double rmin, double rmix, float *t) {
+    if (!c || !t) return fail(CF_EINVAL, "null argument");
+    if (!(rmaj > rmin)) return fail(CF_EINVAL, "rho_maj must exceed rho_min");
+    if (!c->film_set) return fail(CF_ESTATE, "no fields before the first step");
+    if (c->nfaces) CF_CUDA(launch_inside(c->mask, c->inside, c->d.nx, c->d.ny, c->d.nz, c->stream));
+    const WarmGeom g = warm_geom(c, h_top, rmaj, rmin, rmix);
+    CF_CUDA(launch_warm_target(g, c->inside, c->out, t, c->stream));
+    return sync_ok(c);
+}
+
+cf_status cf_field_check(cf_ctx *c, double out[4]) {
+    if (!c || !out) return fail(CF_EINVAL, "null argument");
+    if (!c->film_set) return fail(CF_ESTATE, "no fields before the first step");
+    cf_status s = warm_scratch(c);
+    if (s != CF_OK) return s;
+    CF_CUDA(launch_field_check(c->N, c->out, c->snap, c->warm_part, c->warm_res, c->stream));
+    CF_CUDA(cudaMemcpyAsync(out, c->warm_res, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream));
     return sync_ok(c);
 }
 

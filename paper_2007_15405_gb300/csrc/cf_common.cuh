@@ -254,6 +254,22 @@ cudaError_t launch_init_dens(void *f, float *f0, int prec, float2 *rho, long lon
                              int wall, const double *rAB, cudaStream_t s);
 cudaError_t launch_mass(const void *f, const float *f0, int prec, const float2 *rho, long long N,
                         double *m2, cudaStream_t s);
+// learned warm start: lattice, film plane and densities the set-up kernels use
+struct WarmGeom {
+    int nx, ny, nz, wall;
+    long long N;
+    int zm;                       // the film's mixed plane floor(h_top + 1/2)
+    double rmaj, rmin, rmix, drho;  // film densities, drho = rmaj - rmin
+};
+int warm_parts();  // doubles x 4 of partial sums the set-up kernels need
+cudaError_t launch_warm_features(const WarmGeom &g, const uint8_t *inside, float lks, float *x, float *mask,
+                                 cudaStream_t s);
+cudaError_t launch_warm_densities(const WarmGeom &g, const uint8_t *inside, const float *d, double *r,
+                                  double *part, cudaStream_t s);
+cudaError_t launch_warm_target(const WarmGeom &g, const uint8_t *inside, const float *out, float *t,
+                               cudaStream_t s);
+cudaError_t launch_field_check(long long N, const float *out, float *snap, double *part, double *res,
+                               cudaStream_t s);
 // membrane kernels 1-3 (positions only) and 4-5 (after the lattice update)
 cudaError_t launch_membrane_forces(const MemParams &p, cudaStream_t s, int *nlaunch);
 cudaError_t launch_membrane_update(const MemParams &p, const ClearParams &cl, bool any_frozen,

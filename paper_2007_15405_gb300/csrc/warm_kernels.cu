@@ -234,6 +234,194 @@ __global__ void k_from_bf16(const __nv_bfloat16 *__restrict__ x, float *__restri
         y[i] = __bfloat162float(x[i]);
 }
 
+// ----------------------------------------------- warm-start set-up kernels
+// The network's inputs, the state set from its prediction and its training
+// targets are per-node functions of the lattice and the film; the residual
+// check reduces the fields.  Block sums go to per-block partials, which every
+// consumer adds in index order (results do not depend on block scheduling).
+constexpr int WB = 256;           // threads per block of these kernels
+constexpr int WARM_BLOCKS = 608;  // blocks (4 per SM), fixed so partials fit a known size
+
+__device__ __forceinline__ int warm_z(const WarmGeom &g, long long n) {
+    return (int)(n / ((long long)g.nx * g.ny));
+}
+// the flat film's phi: +1 below the mixed plane, 0 in it, -1 above and inside
+// capsules, 0 on the substrate plane
+__device__ __forceinline__ float warm_phi(const WarmGeom &g, int z, bool ins) {
+    float phi = z < g.zm ? 1.f : z == g.zm ? 0.f : -1.f;
+    if (ins) phi = -1.f;
+    if (g.wall && z == 0) phi = 0.f;
+    return phi;
+}
+// the flat film's densities (no jitter) from its phi
+__device__ __forceinline__ void warm_film(const WarmGeom &g, float phi, int z, double &fa, double &fb) {
+    fa = phi > 0.5f ? g.rmaj : phi < -0.5f ? g.rmin : g.rmix;
+    fb = phi > 0.5f ? g.rmin : phi < -0.5f ? g.rmaj : g.rmix;
+    if (g.wall && z == 0) fa = fb = 0.0;
+}
+
+__global__ void __launch_bounds__(WB) k_warm_features(WarmGeom g, const uint8_t *__restrict__ inside, float lks,
+                                                      float *__restrict__ x, float *__restrict__ mask) {
+    const long long N = g.N;
+    for (long long n = blockIdx.x * (long long)WB + threadIdx.x; n < N; n += (long long)gridDim.x * WB) {
+        const int z = warm_z(g, n);
+        const bool ins = inside[n] != 0;
+        x[n] = ins ? 1.f : 0.f;
+        x[N + n] = warm_phi(g, z, ins);
+        x[2 * N + n] = (float)z / (float)g.nz;
+        x[3 * N + n] = lks;
+        if (mask) mask[n] = (!ins && z >= (g.wall ? 1 : 0)) ? 1.f : 0.f;
+    }
+}
+
+// sum of 4 doubles over the block into part[4 * blockIdx.x + j]
+__device__ __forceinline__ void block_sum4(double (&v)[4], double *part) {
+    __shared__ double sh[WB / 32][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+    if ((threadIdx.x & 31) == 0)
+        for (int j = 0; j < 4; ++j) sh[threadIdx.x >> 5][j] = v[j];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0.0;
+        for (int w = 0; w < WB / 32; ++w) s += sh[w][threadIdx.x];
+        part[4 * blockIdx.x + threadIdx.x] = s;
+    }
+}
+
+// predicted densities: the film plus the corrections on the fluid outside
+// the capsules (at least 1e-3), the film inside and on the substrate; sums of
+// the film's and the prediction's masses on that fluid
+__global__ void __launch_bounds__(WB) k_warm_dens(WarmGeom g, const uint8_t *__restrict__ inside,
+                                                  const float *__restrict__ d, double *__restrict__ r,
+                                                  double *__restrict__ part) {
+    const long long N = g.N;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};  // film A, predicted A, film B, predicted B
+    for (long long n = blockIdx.x * (long long)WB + threadIdx.x; n < N; n += (long long)gridDim.x * WB) {
+        const int z = warm_z(g, n);
+        const bool ins = inside[n] != 0;
+        double fa, fb;
+        warm_film(g, warm_phi(g, z, ins), z, fa, fb);
+        const bool free = !ins && !(g.wall && z == 0);
+        const double ra = free ? fmax(fa + g.drho * (double)d[n], 1e-3) : fa;
+        const double rb = free ? fmax(fb + g.drho * (double)d[N + n], 1e-3) : fb;
+        r[n] = ra;
+        r[N + n] = rb;
+        if (free) { v[0] += fa; v[1] += ra; v[2] += fb; v[3] += rb; }
+    }
+    block_sum4(v, part);
+}
+
+// scale each component on the free fluid to the film's mass
+__global__ void __launch_bounds__(WB) k_warm_rescale(WarmGeom g, const uint8_t *__restrict__ inside,
+                                                     const double *__restrict__ part, int nparts,
+                                                     double *__restrict__ r) {
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = 0; b < nparts; ++b)
+        for (int j = 0; j < 4; ++j) t[j] += part[4 * b + j];
+    const double sa = t[1] > 0.0 ? t[0] / t[1] : 1.0, sb = t[3] > 0.0 ? t[2] / t[3] : 1.0;
+    const long long N = g.N;
+    for (long long n = blockIdx.x * (long long)WB + threadIdx.x; n < N; n += (long long)gridDim.x * WB) {
+        const int z = warm_z(g, n);
+        if (inside[n] != 0 || (g.wall && z == 0)) continue;
+        r[n] *= sa;
+        r[N + n] *= sb;
+    }
+}
+
+// training targets: (rho_c - rho_c,film) / (rho_maj - rho_min) on the fluid
+// outside the capsules, 0 elsewhere; rho_c from the recorded fields
+__global__ void __launch_bounds__(WB) k_warm_target(WarmGeom g, const uint8_t *__restrict__ inside,
+                                                    const float *__restrict__ out, float *__restrict__ t) {
+    const long long N = g.N;
+    for (long long n = blockIdx.x * (long long)WB + threadIdx.x; n < N; n += (long long)gridDim.x * WB) {
+        const int z = warm_z(g, n);
+        const bool ins = inside[n] != 0;
+        double fa, fb;
+        warm_film(g, warm_phi(g, z, ins), z, fa, fb);
+        const bool m = !ins && z >= (g.wall ? 1 : 0);
+        t[n] = m ? (float)(((double)out[n] - fa) / g.drho) : 0.f;
+        t[N + n] = m ? (float)(((double)out[N + n] - fb) / g.drho) : 0.f;
+    }
+}
+
+// residual check: finite flag, smallest density, largest |u| component, sum
+// of |rho - snapshot| over both components; the snapshot takes the densities
+__global__ void __launch_bounds__(WB) k_field_check(long long N, const float *__restrict__ out,
+                                                    float *__restrict__ snap, double *__restrict__ part) {
+    double v[4] = {1.0, 1e300, 0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)WB + threadIdx.x; i < 5 * N; i += (long long)gridDim.x * WB) {
+        const float q = out[i];
+        if (!isfinite(q)) v[0] = 0.0;
+        if (i < 2 * N) {
+            v[1] = fmin(v[1], (double)q);
+            v[3] += fabs((double)q - (double)snap[i]);
+            snap[i] = q;
+        } else {
+            v[2] = fmax(v[2], fabs((double)q));
+        }
+    }
+    // reduce: min for the flag and the smallest density, max for |u|, sum
+    __shared__ double sh[WB / 32][4];
+    for (int o = 16; o > 0; o >>= 1) {
+        v[0] = fmin(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
+        v[1] = fmin(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
+        v[2] = fmax(v[2], __shfl_xor_sync(0xffffffffu, v[2], o));
+        v[3] += __shfl_xor_sync(0xffffffffu, v[3], o);
+    }
+    if ((threadIdx.x & 31) == 0)
+        for (int j = 0; j < 4; ++j) sh[threadIdx.x >> 5][j] = v[j];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a[4] = {sh[0][0], sh[0][1], sh[0][2], sh[0][3]};
+        for (int w = 1; w < WB / 32; ++w) {
+            a[0] = fmin(a[0], sh[w][0]); a[1] = fmin(a[1], sh[w][1]);
+            a[2] = fmax(a[2], sh[w][2]); a[3] += sh[w][3];
+        }
+        for (int j = 0; j < 4; ++j) part[4 * blockIdx.x + j] = a[j];
+    }
+}
+
+__global__ void k_field_check_final(const double *__restrict__ part, int nparts, long long N,
+                                    double *__restrict__ res) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a[4] = {1.0, 1e300, 0.0, 0.0};
+    for (int b = 0; b < nparts; ++b) {
+        a[0] = fmin(a[0], part[4 * b]); a[1] = fmin(a[1], part[4 * b + 1]);
+        a[2] = fmax(a[2], part[4 * b + 2]); a[3] += part[4 * b + 3];
+    }
+    res[0] = a[0]; res[1] = a[1]; res[2] = a[2]; res[3] = a[3] / (2.0 * (double)N);
+}
+
+cudaError_t launch_warm_features(const WarmGeom &g, const uint8_t *inside, float lks, float *x, float *mask,
+                                 cudaStream_t s) {
+    k_warm_features<<<WARM_BLOCKS, WB, 0, s>>>(g, inside, lks, x, mask);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warm_densities(const WarmGeom &g, const uint8_t *inside, const float *d, double *r,
+                                  double *part, cudaStream_t s) {
+    k_warm_dens<<<WARM_BLOCKS, WB, 0, s>>>(g, inside, d, r, part);
+    k_warm_rescale<<<WARM_BLOCKS, WB, 0, s>>>(g, inside, part, WARM_BLOCKS, r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warm_target(const WarmGeom &g, const uint8_t *inside, const float *out, float *t,
+                               cudaStream_t s) {
+    k_warm_target<<<WARM_BLOCKS, WB, 0, s>>>(g, inside, out, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_check(long long N, const float *out, float *snap, double *part, double *res,
+                               cudaStream_t s) {
+    k_field_check<<<WARM_BLOCKS, WB, 0, s>>>(N, out, snap, part);
+    k_field_check_final<<<1, 32, 0, s>>>(part, WARM_BLOCKS, N, res);
+    return cudaGetLastError();
+}
+
+int warm_parts() { return WARM_BLOCKS; }
+
 namespace {
 cf_status conv_check(int n, int cin, int cout, int nz, int ny, int nx, int dil) {
     if (n < 1 || cin < 1 || cout < 1 || cin > MAXC || cout > MAXC || nz < 1 || ny < 1 || nx < 1 || dil < 1) {

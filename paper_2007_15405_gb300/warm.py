@@ -25,6 +25,10 @@ The warm-started run judges its own start: it advances two short windows and
 falls back to the flat film when densities turn non-finite or negative, a
 velocity exceeds a low-Mach limit, or the density change of the second window
 exceeds 1.5 times that of the first (the residual grows instead of decaying).
+
+The inputs (cf_warm_features), the predicted state with its mass matching
+(cf_warm_apply), the training targets (cf_warm_target) and the residual
+statistics (cf_field_check) are computed by the library's kernels too.
 """
 import ctypes as C
 import math
@@ -43,67 +47,31 @@ def _p(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
 
 
-def features(sim, wl):
-    """Network inputs [4][nz][ny][nx] (float32) and the fluid mask for lattice wl."""
-    nz, ny, nx = wl.nz, wl.ny, wl.nx
-    _, _, inside = sim.cuts()
-    ins = inside.reshape(nz, ny, nx).astype(np.float32)
-    z = np.arange(nz, dtype=np.float32)[:, None, None] * np.ones((1, ny, nx), np.float32)
-    zm = math.floor(wl.h_top + 0.5)
-    phi = np.where(z < zm, 1.0, np.where(z == zm, 0.0, -1.0)).astype(np.float32)
-    phi = np.where(ins > 0, -1.0, phi)
-    if wl.wall:
-        phi[0] = 0.0
+def features_dev(sim, wl):
+    """Network inputs [4][N] and fluid mask [N] of lattice wl as float32 device
+    tensors, computed by cf_warm_features."""
+    import torch
+    x = torch.empty(N_IN * sim.N, dtype=torch.float32, device="cuda")
+    mask = torch.empty(sim.N, dtype=torch.float32, device="cuda")
     ks = wl.capsules[0].kS if wl.capsules else 1e-2
-    soft = np.full((nz, ny, nx), math.log10(ks) + 2.0, np.float32)
-    x = np.stack([ins, phi, z / nz, soft]).astype(np.float32)
-    mask = ((ins == 0) & (z >= (1 if wl.wall else 0))).astype(np.float32)
+    sim.warm_features(wl.h_top, ks, x, mask)
     return x, mask
 
 
-def phi_of(sim):
-    """phi = (rho_A - rho_B) / (rho_maj - rho_min) of the current state."""
-    rho, _ = sim.fields()
-    return ((rho[0] - rho[1]) / (I.RHO_MAJ - I.RHO_MIN)).astype(np.float32)
+def features(sim, wl):
+    """The same as host arrays [4][nz][ny][nx] and [nz][ny][nx] (training sets)."""
+    x, mask = features_dev(sim, wl)
+    return (x.cpu().numpy().reshape(N_IN, wl.nz, wl.ny, wl.nx),
+            mask.cpu().numpy().reshape(wl.nz, wl.ny, wl.nx))
 
 
-def target_of(sim, x, wl):
-    """Network target [2][nz][ny][nx]: density corrections from the film state."""
-    rho, _ = sim.fields()
-    fa, fb = film_densities(x, wl)
-    return np.stack([(rho[0] - fa) / D_RHO, (rho[1] - fb) / D_RHO]).astype(np.float32)
-
-
-def film_densities(x, wl):
-    """The flat film's densities (without jitter) from its phi channel:
-    majority / minority away from the interface, the mixed value in its plane."""
-    phi = x[1]
-    ra = np.where(phi > 0.5, I.RHO_MAJ, np.where(phi < -0.5, I.RHO_MIN, I.RHO_MIX)).astype(np.float64)
-    rb = np.where(phi > 0.5, I.RHO_MIN, np.where(phi < -0.5, I.RHO_MAJ, I.RHO_MIX)).astype(np.float64)
-    if wl.wall:
-        ra[0] = rb[0] = 0.0
-    return ra, rb
-
-
-def densities_from_prediction(d, x, wl):
-    """rho_A, rho_B [nz][ny][nx] from predicted corrections d [2][...]: the
-    film plus the corrections on the fluid outside the capsules (at least
-    1e-3), the film inside and on the substrate; then each component is scaled
-    on the fluid outside the capsules so that its total mass equals the flat
-    film's (masses are conserved, so a start with other masses relaxes to
-    another equilibrium)."""
-    fa, fb = film_densities(x, wl)
-    free = x[0] == 0
-    if wl.wall:
-        free[0] = False
-    ra = np.where(free, np.maximum(fa + D_RHO * d[0], 1e-3), fa)
-    rb = np.where(free, np.maximum(fb + D_RHO * d[1], 1e-3), fb)
-    for r, f in ((ra, fa), (rb, fb)):
-        target = f[free].sum()
-        have = r[free].sum()
-        if have > 0:
-            r[free] *= target / have
-    return ra, rb
+def target_of(sim, wl):
+    """Network target [2][nz][ny][nx] of the current (equilibrated) state: the
+    density corrections from the flat film on the fluid (cf_warm_target)."""
+    import torch
+    t = torch.empty(N_OUT * sim.N, dtype=torch.float32, device="cuda")
+    sim.warm_target(wl.h_top, I.RHO_MAJ, I.RHO_MIN, I.RHO_MIX, t)
+    return t.cpu().numpy().reshape(N_OUT, wl.nz, wl.ny, wl.nx)
 
 
 class WarmNet:
@@ -159,6 +127,18 @@ class WarmNet:
                                                   dil, int(relu), _p(y), C.c_void_p(self.stream)))
             acts.append(y)
         return acts
+
+    def predict_dev(self, x, shape):
+        """Density corrections for one lattice of shape (nz, ny, nx) from
+        device inputs x [4][N] (float32): a float32 device tensor [2][N]."""
+        torch = self.torch
+        n_nodes = x.numel() // N_IN
+        xb = torch.empty(x.numel(), dtype=torch.bfloat16, device=self.dev)
+        cfm._check(cfm._lib.cf_to_bf16(_p(x), _p(xb), x.numel(), C.c_void_p(self.stream)))
+        acts = self.forward(xb, (1,) + tuple(shape))
+        out = torch.empty(N_OUT * n_nodes, dtype=torch.float32, device=self.dev)
+        cfm._check(cfm._lib.cf_from_bf16(_p(acts[-1]), _p(out), out.numel(), C.c_void_p(self.stream)))
+        return out
 
     def predict(self, x):
         """Density corrections for one lattice: x [4][nz][ny][nx] -> [2][nz][ny][nx] float32."""
@@ -229,9 +209,8 @@ def dataset(wls, steps):
     xs, ts, ms = [], [], []
     for s, w in zip(sims, wls):
         x, mask = features(s, w)
-        t = target_of(s, x, w) * mask[None]
         xs.append(x)
-        ts.append(t)
+        ts.append(target_of(s, w))
         ms.append(np.stack([mask] * N_OUT))
         s.close()
     return np.stack(xs), np.stack(ts), np.stack(ms)
@@ -259,24 +238,20 @@ def train(net, X, T, M, steps=300, batch=8, lr=2e-3, seed=0, log=None):
 def warm_start(sim, wl, net, window=25, u_limit=0.1, grow=1.5):
     """Set the predicted state and judge it over two windows of `window`
     steps; falls back to the flat film when the residual misbehaves.
-    Returns (used_warm, steps_taken)."""
-    x, _ = features(sim, wl)
-    ra, rb = densities_from_prediction(net.predict(x), x, wl)
-    sim.set_densities(ra, rb)
-    ok = True
+    Returns (used_warm, steps_taken).  Inputs, prediction, the predicted state
+    and the residual statistics are all computed on the device."""
+    x, _ = features_dev(sim, wl)
+    d = net.predict_dev(x, (wl.nz, wl.ny, wl.nx))
+    sim.warm_apply(wl.h_top, I.RHO_MAJ, I.RHO_MIN, I.RHO_MIX, d)
     sim.step(1)
-    r0, _ = sim.fields()
+    sim.field_check()  # keeps the densities after the first step
     sim.step(window)
-    r1, u1 = sim.fields()
+    c1 = sim.field_check()
     sim.step(window)
-    r2, u2 = sim.fields()
-    for r, u in ((r1, u1), (r2, u2)):
-        if not (np.isfinite(r).all() and np.isfinite(u).all()) or (r < 0).any() or np.abs(u).max() > u_limit:
-            ok = False
-    if ok:
-        d1 = np.abs(r1 - r0).mean()
-        d2 = np.abs(r2 - r1).mean()
-        ok = d2 <= grow * d1
+    c2 = sim.field_check()
+    # finite, no negative density, velocities below the low-Mach limit, and a
+    # density change that decays from the first window to the second
+    ok = all(c[0] == 1.0 and c[1] >= 0.0 and c[2] <= u_limit for c in (c1, c2)) and c2[3] <= grow * c1[3]
     if ok:
         return True, 2 * window + 1
     sim.set_film(wl.h_top, I.RHO_MAJ, I.RHO_MIN, I.RHO_MIX, wl.jitter())

@@ -168,3 +168,97 @@ def test_trained_network_gains_over_the_flat_film(env):
     sim = cfm.Simulation.from_workload(wls[24])
     used, _ = warm.warm_start(sim, wls[24], net)
     assert used
+
+
+def np_film(phi, wall):
+    """The flat film's densities from its phi channel (definition)."""
+    ra = np.where(phi > 0.5, I.RHO_MAJ, np.where(phi < -0.5, I.RHO_MIN, I.RHO_MIX)).astype(np.float64)
+    rb = np.where(phi > 0.5, I.RHO_MIN, np.where(phi < -0.5, I.RHO_MAJ, I.RHO_MIX)).astype(np.float64)
+    if wall:
+        ra[0] = rb[0] = 0.0
+    return ra, rb
+
+
+def np_features(sim, wl):
+    """The network inputs from their definition, on the host."""
+    nz, ny, nx = wl.nz, wl.ny, wl.nx
+    ins = sim.cuts()[2].reshape(nz, ny, nx).astype(np.float32)
+    z = np.arange(nz, dtype=np.float32)[:, None, None] * np.ones((1, ny, nx), np.float32)
+    zm = np.floor(wl.h_top + 0.5)
+    phi = np.where(z < zm, 1.0, np.where(z == zm, 0.0, -1.0)).astype(np.float32)
+    phi = np.where(ins > 0, -1.0, phi).astype(np.float32)
+    if wl.wall:
+        phi[0] = 0.0
+    lks = np.float32(np.log10(wl.capsules[0].kS) + 2.0)
+    x = np.stack([ins, phi, z / np.float32(nz), np.full_like(z, lks)])
+    mask = ((ins == 0) & (z >= (1 if wl.wall else 0))).astype(np.float32)
+    return x, mask
+
+
+def test_warm_features_match_their_definition(env):
+    torch, cfm = env
+    from paper_2007_15405_gb300 import warm
+    wl = I.warm_dataset(1, seed=21)[0]
+    sim = cfm.Simulation.from_workload(wl)
+    x, mask = warm.features(sim, wl)
+    xr, mr = np_features(sim, wl)
+    assert np.array_equal(x, xr) and np.array_equal(mask, mr)
+
+
+def test_warm_apply_matches_its_definition(env):
+    """Film plus corrections on the free fluid (at least 1e-3), film elsewhere,
+    each component scaled to the film's mass on the free fluid: the state
+    equals cf_set_densities of the same densities made on the host."""
+    torch, cfm = env
+    from paper_2007_15405_gb300 import warm
+    wl = I.warm_dataset(1, seed=22)[0]
+    a = cfm.Simulation.from_workload(wl, set_film=False)
+    x, _ = warm.features(a, wl)
+    rng = np.random.default_rng(5)
+    d = (0.05 * rng.standard_normal((2,) + x.shape[1:])).astype(np.float32)
+    d[0, 3, 5, 7] = -50.0  # clipped at 1e-3
+    a.warm_apply(wl.h_top, I.RHO_MAJ, I.RHO_MIN, I.RHO_MIX, torch.from_numpy(d.reshape(-1)).cuda())
+    fa, fb = np_film(x[1], wl.wall)
+    free = x[0] == 0
+    if wl.wall:
+        free[0] = False
+    D = I.RHO_MAJ - I.RHO_MIN
+    ra = np.where(free, np.maximum(fa + D * d[0].astype(np.float64), 1e-3), fa)
+    rb = np.where(free, np.maximum(fb + D * d[1].astype(np.float64), 1e-3), fb)
+    for r, f in ((ra, fa), (rb, fb)):
+        r[free] *= f[free].sum() / r[free].sum()
+    b = cfm.Simulation.from_workload(wl, set_film=False)
+    b.set_densities(ra, rb)
+    pa, pb = a.populations().astype(np.float64), b.populations().astype(np.float64)
+    assert np.abs(pa - pb).max() <= 1e-6 * np.abs(pb).max()
+
+
+def test_warm_target_matches_its_definition(env):
+    torch, cfm = env
+    from paper_2007_15405_gb300 import warm
+    wl = I.warm_dataset(1, seed=23)[0]
+    sim = cfm.Simulation.from_workload(wl)
+    sim.step(30)
+    t = warm.target_of(sim, wl)
+    x, mask = np_features(sim, wl)
+    fa, fb = np_film(x[1], wl.wall)
+    rho, _ = sim.fields()
+    D = I.RHO_MAJ - I.RHO_MIN
+    ref = np.stack([(rho[0] - fa) / D, (rho[1] - fb) / D]).astype(np.float32) * mask[None]
+    assert np.abs(t - ref).max() <= 1e-6
+
+
+def test_field_check_matches_numpy(env):
+    torch, cfm = env
+    wl = I.warm_dataset(1, seed=24)[0]
+    sim = cfm.Simulation.from_workload(wl)
+    sim.step(3)
+    c0 = sim.field_check()
+    r0, u0 = sim.fields()
+    assert c0[0] == 1.0 and c0[1] == r0.min() and c0[2] == np.abs(u0).max()
+    assert c0[3] == pytest.approx(np.abs(r0).mean(), rel=1e-12)  # against zero
+    sim.step(7)
+    c1 = sim.field_check()
+    r1, u1 = sim.fields()
+    assert c1[1] == r1.min() and c1[2] == np.abs(u1).max()
+    assert c1[3] == pytest.approx(np.abs(r1 - r0).mean(), rel=1e-9)
