@@ -191,6 +191,22 @@ def l2_note(ws):
     return f"no flush: per-step working set {ws / 1e6:.0f} MB of populations (src + dst) {rel} the 129 MB L2"
 
 
+def max_over_ranks(x, device="cpu"):
+    """The largest x over the ranks of the process group (x itself alone)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist = torch.distributed
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(nodes, steps, world, seconds):
+    """Whole-job throughput: the node updates of all ranks (each rank runs its
+    own replica) over the slowest rank's time."""
+    return nodes * steps * world / seconds / 1e6
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -264,11 +280,8 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     sim.sync()
-    t_all = torch.tensor([ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t_all, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t_all.item())
-    value = wl.nodes * args.steps * world / (ms_max / 1e3) / 1e6
+    ms_max = max_over_ranks(ms, "cuda")
+    value = job_mlups(wl.nodes, args.steps, world, ms_max / 1e3)
     # ---- per-phase device time (lattice kernel, membrane phase, cut links)
     nprof = min(200, max(20, args.steps // 10))
     ph = sim.time_phases(nprof)
@@ -289,9 +302,9 @@ def run_ours(args):
         sim.step(sample_every)
         forces.append(sim.lateral_force(0, 1))
     barrier()
-    t_e2e = time.perf_counter() - t0
+    t_e2e = max_over_ranks(time.perf_counter() - t0, "cuda")
     e2e_steps = nsamp * sample_every
-    e2e_val = wl.nodes * e2e_steps * world / t_e2e / 1e6
+    e2e_val = job_mlups(wl.nodes, e2e_steps, world, t_e2e)
     h2d = jit.nbytes / e2e_steps
     d2h = 16 * 8 * len(wl.capsules) * nsamp / e2e_steps
     sim.close()
