@@ -176,3 +176,50 @@ def test_meniscus_field_recovers_linear_interface():
     rho = np.stack([0.5 + phi / 2, 0.5 - phi / 2])
     got = o.meniscus_field(rho)
     assert np.allclose(got, h, atol=1e-13)
+
+
+def sheet(nx, ny, zs, spacing=2.0, off=(0.3, 0.4)):
+    """A flat triangulated sheet at height zs tiling one x-y period of the
+    lattice (offset so that no link crosses it on an edge), counter-clockwise
+    seen from +z."""
+    xs = off[0] + spacing * np.arange(int(round(nx / spacing)) + 1)
+    ys = off[1] + spacing * np.arange(int(round(ny / spacing)) + 1)
+    X = np.array([[x, y, zs] for y in ys for x in xs])
+    F, n = [], len(xs)
+    for j in range(len(ys) - 1):
+        for i in range(n - 1):
+            a = j * n + i
+            F += [[a, a + 1, a + n + 1], [a, a + n + 1, a + n]]
+    return X, np.array(F)
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.8])
+def test_couette_between_substrate_and_moving_sheet(tau):
+    """A triangulated sheet at z = 6.5 moving with U along x between the
+    substrate (wall at z = 0.5) and its periodic image (z = nz - 1/2): at
+    steady state both gaps carry the linear Couette profile and the momentum
+    exchanged with the sheet is the closed-form shear force of both gaps,
+    -2 (rho_A + rho_B) nu U A / H with nu = c_s^2 (tau - 1/2) (Ladd's term
+    and the momentum exchange of Sec. 3.1; half-way bounce-back is exact for a
+    linear profile)."""
+    nx, ny, nz, zs, H, U = 4, 4, 13, 6.5, 6.0, 0.01
+    X, F = sheet(nx, ny, zs)
+    o = O.Oracle(nx, ny, nz, wall=1, tau=(tau, tau), G=0.0, rep_dz=2.0)
+    o.add_capsule(X, F, 0.0, 0.0, 0.0, 0.0, 25.0, I.MODE_FIXED)
+    rA, rB = 1.0, 0.1
+    f = rest(np.full((nz, ny, nx), rA), np.full((nz, ny, nx), rB))
+    f[:, :, 0] = 0.0
+    o.set_populations(f)
+    V = np.tile([U, 0.0, 0.0], (X.shape[0], 1))
+    for _ in range(3000):
+        o.set_capsule_velocity(0, V)  # a fixed capsule's node velocities are reset each step
+        o.step(1)
+    _, u = o.fields()
+    z = np.arange(1, nz)
+    exact = np.where(z <= zs, (z - 0.5) / H, (nz - 0.5 - z) / H)
+    assert np.abs(u[0, 1:] / U - exact[:, None, None]).max() < 1e-10
+    assert np.abs(u[1:, 1:]).max() < 1e-12
+    nu = (tau - 0.5) / 3.0
+    F_exp = -2.0 * (rA + rB) * nu * U * nx * ny / H
+    force = o.capsule_state(0)["force"]
+    assert abs(force[0] / F_exp - 1.0) < 1e-10 and np.abs(force[1:]).max() < 1e-12
