@@ -421,7 +421,7 @@ def run_warm(args):
         pred = net.predict(Xh[k])
         err_p.append(float(np.sqrt((Th[k] ** 2 * Mh[k]).sum() / Mh[k].sum())))
         err_w.append(float(np.sqrt(((pred - Th[k]) ** 2 * Mh[k]).sum() / Mh[k].sum())))
-    res = warm.convergence(net, test, total=total, every=every)
+    res, timing = warm.convergence(net, test, total=total, every=every)
     sp = [r[0] for r in res]
     sw = [r[1] for r in res]
     both = [(a, b) for a, b in zip(sp, sw) if a is not None and b is not None]
@@ -441,6 +441,13 @@ def run_warm(args):
                          "pairs": len(both), "flat_film_unsettled": sum(a is None for a in sp),
                          "warm_unsettled": sum(b is None for b in sw)},
         "fallbacks": sum(not r[2] for r in res),
+        "time_to_force_seconds": ({
+            "flat_film": float(np.mean([a for a, _ in both])) * timing["step_seconds"],
+            "warm": float(np.mean([b for _, b in both])) * timing["step_seconds"] + timing["warm_start_seconds"],
+            "step_seconds_per_lattice": timing["step_seconds"],
+            "warm_start_seconds": timing["warm_start_seconds"],
+            "note": f"per lattice within a batch of {n_test}; the warm start (inference, predicted state, "
+                    "51 judging steps run alone) is counted, the offline training is not"} if both else None),
         "value": float(np.mean([b for _, b in both])) if both else None,
     }
     print(json.dumps(line), flush=True)

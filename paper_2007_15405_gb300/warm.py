@@ -138,6 +138,8 @@ class WarmNet:
         acts = self.forward(xb, (1,) + tuple(shape))
         out = torch.empty(N_OUT * n_nodes, dtype=torch.float32, device=self.dev)
         cfm._check(cfm._lib.cf_from_bf16(_p(acts[-1]), _p(out), out.numel(), C.c_void_p(self.stream)))
+        # the simulation reads the prediction on its own stream
+        torch.cuda.synchronize()
         return out
 
     def predict(self, x):
@@ -283,15 +285,24 @@ def settle_step(trace, every, f_eq, tol=0.01):
 def convergence(net, wls, total=8000, every=50, tol=0.01):
     """Flat-film and warm-started runs of the set-ups wls: steps until the
     capsule force settles within tol of its equilibrium (the mean of the last
-    five samples of the flat-film run), and the warm starts that fell back."""
+    five samples of the flat-film run), and the warm starts that fell back.
+    Also the wall time of one warm start (inference, predicted state, judging
+    steps) and of one lattice step within the batch of force traces."""
+    import time
     plain = [cfm.Simulation.from_workload(w) for w in wls]
     warmed, used = [], []
+    t_warm = 0.0
     for w in wls:
         s = cfm.Simulation.from_workload(w)
+        t0 = time.perf_counter()
         u, _ = warm_start(s, w, net)
+        s.sync()
+        t_warm += time.perf_counter() - t0
         warmed.append(s)
         used.append(u)
+    t0 = time.perf_counter()
     fp = force_traces(plain, total, every)
+    t_plain = time.perf_counter() - t0
     fw = force_traces(warmed, total, every)
     res = []
     for k in range(len(wls)):
@@ -299,4 +310,5 @@ def convergence(net, wls, total=8000, every=50, tol=0.01):
         res.append((settle_step(fp[k], every, f_eq, tol), settle_step(fw[k], every, f_eq, tol), used[k]))
     for s in plain + warmed:
         s.close()
-    return res
+    timing = dict(warm_start_seconds=t_warm / len(wls), step_seconds=t_plain / (total * len(wls)))
+    return res, timing

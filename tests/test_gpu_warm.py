@@ -262,3 +262,32 @@ def test_field_check_matches_numpy(env):
     r1, u1 = sim.fields()
     assert c1[1] == r1.min() and c1[2] == np.abs(u1).max()
     assert c1[3] == pytest.approx(np.abs(r1 - r0).mean(), rel=1e-9)
+
+
+def test_device_warm_start_equals_the_host_construction(env):
+    """The prediction made on the device and applied with cf_warm_apply sets
+    the state the definition gives for the same network output (read back to
+    the host): the prediction is complete before the simulation's stream
+    reads it."""
+    torch, cfm = env
+    from paper_2007_15405_gb300 import warm
+    net = warm.WarmNet(seed=3)
+    D = I.RHO_MAJ - I.RHO_MIN
+    for wl in I.warm_dataset(3, seed=31):
+        a = cfm.Simulation.from_workload(wl)
+        x, _ = warm.features_dev(a, wl)
+        a.warm_apply(wl.h_top, I.RHO_MAJ, I.RHO_MIN, I.RHO_MIX, net.predict_dev(x, (wl.nz, wl.ny, wl.nx)))
+        b = cfm.Simulation.from_workload(wl)
+        xh, _ = warm.features(b, wl)
+        d = net.predict(xh).astype(np.float64)
+        fa, fb = np_film(xh[1], wl.wall)
+        free = xh[0] == 0
+        if wl.wall:
+            free[0] = False
+        ra = np.where(free, np.maximum(fa + D * d[0], 1e-3), fa)
+        rb = np.where(free, np.maximum(fb + D * d[1], 1e-3), fb)
+        for r, f in ((ra, fa), (rb, fb)):
+            r[free] *= f[free].sum() / r[free].sum()
+        b.set_densities(ra, rb)
+        pa, pb = a.populations().astype(np.float64), b.populations().astype(np.float64)
+        assert np.abs(pa - pb).max() <= 1e-6 * np.abs(pb).max()
