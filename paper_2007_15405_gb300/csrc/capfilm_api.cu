@@ -122,7 +122,6 @@ struct cf_ctx {
     bool film_set = false;
     long long steps_done = 0;
     long long launches_last = 0;
-    int lb_variant = 0;
     int zchunk = 0;
 
     cudaGraphExec_t graph = nullptr;
@@ -365,19 +364,21 @@ cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev = null
 
 void choose_launch(cf_ctx *c) {
     // blocks of 32 x 4 columns; each thread walks zchunk planes (strided), so
-    // the grid holds about 48 blocks per SM on 152 SMs (6 waves of the
-    // density pass, 6 of the collide pass at 8 resident blocks: measured best
-    // between 25 and 80 per SM on the 128x64x64 and 256x256x96 lattices)
+    // the grid holds about 48 blocks per SM (8 waves of the density pass at 6
+    // resident blocks, 6 of the collide pass at 8: measured best between 25
+    // and 80 blocks per SM on the 128x64x64 and 256x256x96 lattices)
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
     const int cols = ((c->d.nx + 31) / 32) * ((c->d.ny + 3) / 4);
     const int nzf = c->d.nz - (c->d.wall ? 1 : 0);
-    const int target = 152 * 48;
+    const int target = sms * 48;
     const int gz = std::max(1, std::min(nzf, (target + cols - 1) / cols));
     c->zchunk = std::max(1, (nzf + gz - 1) / gz);
     if (const char *e = std::getenv("CAPFILM_ZCHUNK")) {  // manual override for launch sweeps
         const int v = std::atoi(e);
         if (v > 0) c->zchunk = std::min(v, nzf);
     }
-    c->lb_variant = 0;
 }
 
 cf_status build_membrane(cf_ctx *c) {
