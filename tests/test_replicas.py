@@ -47,3 +47,16 @@ def test_single_process_keeps_its_own_time():
     import bench
     assert bench.max_over_ranks(12.5) == 12.5
     assert bench.job_mlups(524288, 2000, 1, 0.15) == pytest.approx(524288 * 2000 / 0.15 / 1e6)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    """Under torchrun the reference arm (the oracle on the host cores) runs on
+    rank 0 alone; the other ranks return at once and print nothing."""
+    import argparse
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+    args = argparse.Namespace(steps=1, warmup=3, cpu_sample_steps=None, drying=False)
+    assert bench.run_reference(args) is None
+    assert capsys.readouterr().out == ""
