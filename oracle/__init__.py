@@ -61,6 +61,19 @@ def lib():
         L.or_mesh_area.argtypes = [_dp, _ip, C.c_int]
         L.or_hertz.restype = C.c_double
         L.or_hertz.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.or_rho_interp.restype = C.c_double
+        L.or_rho_interp.argtypes = [C.c_void_p, _dp, C.c_int, C.c_int, C.c_int]
+        L.or_set_cuts.argtypes = [C.c_void_p, _up, _ip]
+        L.or_capsule_forces.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
+        L.or_meniscus_profile_of.restype = C.c_double
+        L.or_meniscus_profile_of.argtypes = [_dp, C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_int,
+                                             C.c_double, C.c_int, _dp, _dp, _dp]
+        L.or_meniscus_profile.restype = C.c_double
+        L.or_meniscus_profile.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, _dp, _dp, _dp]
+        L.or_lateral_force_of.restype = C.c_double
+        L.or_lateral_force_of.argtypes = [_dp, _dp, _dp, _dp, C.c_int, C.c_int]
+        L.or_lateral_force.restype = C.c_double
+        L.or_lateral_force.argtypes = [C.c_void_p, C.c_int, C.c_int]
         _lib = L
     return _lib
 
@@ -106,6 +119,31 @@ def mesh_area(X, F):
 
 def hertz(d, xi=1.5, delta0=1.5):
     return lib().or_hertz(xi, delta0, d)
+
+
+def profile_samples(nx, ny, dr=1.0):
+    """Samples of a meniscus profile: r_k = k dr for k < (min(nx, ny) // 2) / dr."""
+    return int(np.floor((min(nx, ny) // 2) / dr + 1e-9))
+
+
+def meniscus_profile_of(h, centres, cid, dr=1.0, nr=None):
+    """Profile (r, zeta), rise Z and far-field height h_inf of capsule cid from a
+    height field h [ny, nx] and the xy centroids [(cx, cy), ...] of all capsules."""
+    h = np.ascontiguousarray(h, np.float64)
+    ny, nx = h.shape
+    c = np.asarray(centres, np.float64).reshape(-1, 2)
+    cx = np.ascontiguousarray(c[:, 0]); cy = np.ascontiguousarray(c[:, 1])
+    nr = profile_samples(nx, ny, dr) if nr is None else nr
+    r = np.zeros(nr); z = np.zeros(nr); Z = np.zeros(1)
+    hinf = lib().or_meniscus_profile_of(_ptr(h), nx, ny, len(cx), _ptr(cx), _ptr(cy), int(cid),
+                                        float(dr), nr, _ptr(r), _ptr(z), _ptr(Z))
+    return r, z, float(Z[0]), hinf
+
+
+def lateral_force_of(Fa, Fb, ca, cb, nx, ny):
+    """1/2 (F_b - F_a) . e_ab with e_ab the unit xy vector from centroid a to b."""
+    a = [np.ascontiguousarray(v, np.float64) for v in (Fa, Fb, ca, cb)]
+    return lib().or_lateral_force_of(_ptr(a[0]), _ptr(a[1]), _ptr(a[2]), _ptr(a[3]), int(nx), int(ny))
 
 
 class Oracle:
@@ -221,6 +259,36 @@ class Oracle:
     def set_capsule_velocity(self, cid, V):
         V = np.ascontiguousarray(V, np.float64)
         lib().or_set_capsule_velocity(self._h, cid, _ptr(V))
+
+    def rho_interp(self, rho, x, y, z):
+        """Partner density across a cut or substrate link at node (x, y, z) for
+        the density field rho [nz, ny, nx] of one component."""
+        r = np.ascontiguousarray(rho, np.float64)
+        assert r.size == self.N
+        return lib().or_rho_interp(self._h, _ptr(r), int(x), int(y), int(z))
+
+    def set_cuts(self, mask, tri):
+        """Replace the cut structure (mask [nz, ny, nx], elements [nz, ny, nx, 18])."""
+        m = np.ascontiguousarray(mask, np.uint32)
+        t = np.ascontiguousarray(tri, np.int32)
+        lib().or_set_cuts(self._h, _ptr(m, _up), _ptr(t, _ip))
+
+    def capsule_forces(self, cid):
+        """(elastic, interaction) node forces [nv, 3] of the last step."""
+        nv = self.nv[cid]
+        Fe = np.zeros((nv, 3)); Fi = np.zeros((nv, 3))
+        lib().or_capsule_forces(self._h, cid, _ptr(Fe), _ptr(Fi))
+        return Fe, Fi
+
+    def meniscus_profile(self, cid, dr=1.0):
+        """(r, zeta, Z, h_inf) of capsule cid on the last step's densities."""
+        nr = profile_samples(self.nx, self.ny, dr)
+        r = np.zeros(nr); z = np.zeros(nr); Z = np.zeros(1)
+        hinf = lib().or_meniscus_profile(self._h, int(cid), float(dr), nr, _ptr(r), _ptr(z), _ptr(Z))
+        return r, z, float(Z[0]), hinf
+
+    def lateral_force(self, a, b):
+        return lib().or_lateral_force(self._h, int(a), int(b))
 
     def sc_forces(self):
         F = np.zeros((2, 3, self.nz, self.ny, self.nx))

@@ -1014,3 +1014,138 @@ void or_cuts_bruteforce(const or_ctx *c, uint32_t *mask, int *tri) {
                     }
                 }
 }
+
+/* ------------------------------------------- hooks for the oracle's pins */
+/* Partner density across a cut or substrate link (reading c10) of component
+ * `comp` at node (x, y, z), evaluated on the density field rho [N] given by
+ * the caller and the context's current cut structure and substrate. */
+double or_rho_interp(const or_ctx *c, const double *rho, int x, int y, int z) {
+    init_weights();
+    return rho_interp(c, rho, x, y, z, nidx(c, x, y, z));
+}
+
+/* Replace the context's cut structure (mask [N], elements [N*18]) and
+ * recompute the interior flags from it. */
+void or_set_cuts(or_ctx *c, const uint32_t *mask, const int *tri) {
+    memcpy(c->mask, mask, sizeof(uint32_t) * c->N);
+    memcpy(c->tri, tri, sizeof(int) * 18 * c->N);
+    compute_inside(c);
+}
+
+/* Elastic (Eqs. 6-8) and interaction (Eq. 11) node forces [nv*3] of capsule
+ * id from the last step (either may be NULL). */
+void or_capsule_forces(const or_ctx *c, int id, double *Fel, double *Fint) {
+    const or_capsule *p = &c->caps[id];
+    if (Fel) memcpy(Fel, p->Fel, sizeof(double) * 3 * p->nv);
+    if (Fint) memcpy(Fint, p->Fint, sizeof(double) * 3 * p->nv);
+}
+
+/* ------------------------------------------ meniscus profile and rise Z */
+/* Meniscus profile around capsule id (Sec. 4.1 and reading c21) from a
+ * column height field h [ny][nx] (NaN = no valid interface) and the xy
+ * centroids cx, cy of all ncaps capsules:
+ *  - h_inf: mean of the valid columns whose periodic distance to the nearest
+ *    centroid is at least 0.9 times the largest such distance over the valid
+ *    columns (the film far from every capsule);
+ *  - rays: from the column nearest to capsule id's centroid along +x, -x, +y
+ *    and -y; at distance r_k = k dr (k = 0 .. nr-1) the height is read by
+ *    linear interpolation between the two columns that bracket r_k on the ray
+ *    (periodic), a sample being invalid when either column is NaN;
+ *  - zeta_k = (mean of the valid ray samples) - h_inf, NaN if none is valid;
+ *  - Z = the largest valid zeta_k (the capillary rise), NaN if none.
+ * r, zeta: [nr].  Returns h_inf. */
+double or_meniscus_profile_of(const double *h, int nx, int ny, int ncaps, const double *cx,
+                              const double *cy, int id, double dr, int nr, double *r,
+                              double *zeta, double *Z) {
+    double dmax = 0.0;
+    double *dmin = (double *)malloc(sizeof(double) * (size_t)nx * ny);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double best = INFINITY;
+            for (int k = 0; k < ncaps; ++k) {
+                double dx = x - cx[k], dy = y - cy[k];
+                dx -= nx * floor(dx / nx + 0.5);
+                dy -= ny * floor(dy / ny + 0.5);
+                double d = sqrt(dx * dx + dy * dy);
+                if (d < best) best = d;
+            }
+            dmin[(long)y * nx + x] = best;
+            if (!isnan(h[(long)y * nx + x]) && best > dmax) dmax = best;
+        }
+    double hs = 0.0;
+    long hc = 0;
+    for (long i = 0; i < (long)nx * ny; ++i)
+        if (!isnan(h[i]) && dmin[i] >= 0.9 * dmax) { hs += h[i]; ++hc; }
+    free(dmin);
+    double hinf = hc ? hs / hc : NAN;
+    int x0 = (int)lround(cx[id]), y0 = (int)lround(cy[id]);
+    const int rx[4] = {1, -1, 0, 0}, ry[4] = {0, 0, 1, -1};
+    double zmax = NAN;
+    for (int k = 0; k < nr; ++k) {
+        double rk = k * dr, s = 0.0;
+        int cnt = 0;
+        int j0 = (int)floor(rk);
+        double t = rk - j0;
+        for (int q = 0; q < 4; ++q) {
+            int xa = wrap(x0 + rx[q] * j0, nx), ya = wrap(y0 + ry[q] * j0, ny);
+            int xb = wrap(x0 + rx[q] * (j0 + 1), nx), yb = wrap(y0 + ry[q] * (j0 + 1), ny);
+            double ha = h[(long)ya * nx + xa], hb = h[(long)yb * nx + xb];
+            double v = (t == 0.0) ? ha : (1.0 - t) * ha + t * hb;
+            if (!isnan(v)) { s += v; ++cnt; }
+        }
+        r[k] = rk;
+        zeta[k] = cnt ? s / cnt - hinf : NAN;
+        if (cnt && (isnan(zmax) || zeta[k] > zmax)) zmax = zeta[k];
+    }
+    if (Z) *Z = zmax;
+    return hinf;
+}
+
+/* xy centroid of every capsule (mean of its node positions). */
+static void centroids_xy(const or_ctx *c, double *cx, double *cy) {
+    for (int k = 0; k < c->ncaps; ++k) {
+        const or_capsule *p = &c->caps[k];
+        double sx = 0.0, sy = 0.0;
+        for (int v = 0; v < p->nv; ++v) { sx += p->X[3 * v]; sy += p->X[3 * v + 1]; }
+        cx[k] = sx / p->nv;
+        cy[k] = sy / p->nv;
+    }
+}
+
+/* The profile of capsule id on the context's own height field (the
+ * densities of the last step).  Returns h_inf. */
+double or_meniscus_profile(const or_ctx *c, int id, double dr, int nr, double *r, double *zeta,
+                           double *Z) {
+    double *h = (double *)malloc(sizeof(double) * (size_t)c->nx * c->ny);
+    double cx[MAXCAPS], cy[MAXCAPS];
+    or_meniscus_field(c, NULL, h);
+    centroids_xy(c, cx, cy);
+    double hinf = or_meniscus_profile_of(h, c->nx, c->ny, c->ncaps, cx, cy, id, dr, nr, r, zeta, Z);
+    free(h);
+    return hinf;
+}
+
+/* ------------------------------------------------------- lateral force */
+/* Lateral capillary force between capsules a and b (Eq. 3 sign convention,
+ * reading c22): with e the unit xy vector from centroid a to centroid b
+ * (nearest periodic image in x and y), F = 1/2 (F_b - F_a) . e, F_a and F_b
+ * the fluid coupling forces on the capsules.  Negative = attraction.
+ * Returns NaN when the centroids coincide in the xy plane. */
+double or_lateral_force_of(const double *Fa, const double *Fb, const double *ca, const double *cb,
+                           int nx, int ny) {
+    double dx = cb[0] - ca[0], dy = cb[1] - ca[1];
+    dx -= nx * floor(dx / nx + 0.5);
+    dy -= ny * floor(dy / ny + 0.5);
+    double L = sqrt(dx * dx + dy * dy);
+    if (!(L > 0.0)) return NAN;
+    return 0.5 * ((Fb[0] - Fa[0]) * dx + (Fb[1] - Fa[1]) * dy) / L;
+}
+
+/* The same for two capsules of the context (coupling forces of the last
+ * step, centroids of the current node positions). */
+double or_lateral_force(const or_ctx *c, int a, int b) {
+    double cx[MAXCAPS], cy[MAXCAPS];
+    centroids_xy(c, cx, cy);
+    double ca[2] = {cx[a], cy[a]}, cb[2] = {cx[b], cy[b]};
+    return or_lateral_force_of(c->caps[a].force, c->caps[b].force, ca, cb, c->nx, c->ny);
+}
