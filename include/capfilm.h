@@ -44,9 +44,8 @@ typedef enum {
     CF_ESTATE = 4,     /* call not valid in the current state                */
     CF_ENOTFOUND = 5,  /* unknown capsule id                                 */
     CF_EDIVERGED = 6,  /* non-finite density detected                        */
-    CF_EOVERFLOW = 7,  /* the cut-link list exceeded its capacity, or an element
+    CF_EOVERFLOW = 7   /* the cut-link list exceeded its capacity, or an element
                           spans more than 16 lattice units */
-    CF_ETIMEOUT = 8    /* a bounded device-side wait gave up (kernel returned early) */
 } cf_status;
 
 /* Storage of the populations (arithmetic is float32 in every case):
@@ -98,6 +97,13 @@ typedef struct {
     double kV;               /* volume penalty kappa_V (Eq. 8)                */
     double mass;             /* mass per node m_i (Sec. 3.2: 25)              */
     int mode;                /* cf_mode                                       */
+    double wet;              /* wetting offset (Sec. 3.1, last paragraph): on
+                                every link this membrane cuts, the partner
+                                densities interpolated for the Shan-Chen force
+                                are rho_A + wet and rho_B - wet (the reaction
+                                on the element uses the same); 0 = neutral
+                                wetting, the paper's choice; > 0 draws the
+                                film fluid A onto the surface.  Finite. */
 } cf_capsule_desc;
 
 typedef struct cf_ctx cf_ctx;
@@ -158,8 +164,10 @@ cf_status cf_lateral_force(cf_ctx *ctx, int a, int b, double *F);
 cf_status cf_capsule_state(cf_ctx *ctx, int id, double *nodes, double *area, double *volume);
 
 /* Densities [2][N] and barycentric velocity u = (j_A + j_B + F/2)/rho [3][N]
- * of the last step (N = nx*ny*nz; solid nodes read 0).  Either may be NULL. */
-cf_status cf_fields(cf_ctx *ctx, double *rho, double *u);
+ * of the last step (N = nx*ny*nz; solid nodes read 0).  Either may be NULL.
+ * *inout_n: the capacity of the buffers in nodes (in) and N (out); a
+ * capacity below N returns CF_EINVAL with *inout_n = N and writes nothing. */
+cf_status cf_fields(cf_ctx *ctx, double *rho, double *u, size_t *inout_n);
 
 /* Post-collision populations [2][19][N] as float (16-bit storage decoded). */
 cf_status cf_populations(cf_ctx *ctx, float *f);
@@ -171,18 +179,44 @@ cf_status cf_total_mass(cf_ctx *ctx, double m[2]);
  * substrate, linearly interpolated; NaN where it touches a capsule interior. */
 cf_status cf_meniscus_field(cf_ctx *ctx, double *h);
 
-/* Meniscus profile around capsule id (Sec. 4.1): zeta(r) = h - h_inf along the
- * four principal directions from the capsule centroid column, averaged; h_inf
- * is the mean height of the valid columns farthest from every capsule.
+/* Meniscus profile around capsule id (Sec. 4.1, the slice through the
+ * particle centre averaged over the four sides), computed on the device in
+ * FP64 from the column heights of cf_meniscus_field:
+ *  - h_inf, the far-field film height: the mean height of the valid columns
+ *    whose (periodic) distance to the nearest capsule centroid is at least
+ *    0.9 times the largest such distance;
+ *  - from the column nearest to the capsule's xy centroid, the rays +x, -x,
+ *    +y and -y are sampled at r_k = k dr, k = 0 .. floor((min(nx,ny)/2)/dr)-1,
+ *    by linear interpolation between the two columns that bracket r_k (a
+ *    sample touching a NaN column is skipped); zeta_k = mean of the valid
+ *    samples - h_inf (NaN when none is valid);
+ *  - Z receives the largest valid zeta (the capillary rise; may be NULL).
  * r and zeta have capacity *inout_n (in) and receive *inout_n entries (out);
- * too small returns CF_EINVAL with the needed size.  Z receives the largest
- * zeta (the capillary rise) and may be NULL. */
-cf_status cf_meniscus_profile(cf_ctx *ctx, int id, double *r, double *zeta, size_t *inout_n,
-                              double *Z);
+ * too small returns CF_EINVAL with the needed size.  dr must be positive and
+ * at most min(nx, ny)/2 (else CF_EINVAL). */
+cf_status cf_meniscus_profile(cf_ctx *ctx, int id, double dr, double *r, double *zeta,
+                              size_t *inout_n, double *Z);
 
-/* Meniscus height Z of capsule id: the largest zeta of its profile (the
- * capillary rise read out in Sec. 4), as cf_meniscus_profile computes it. */
+/* Meniscus height Z of capsule id: the largest zeta of its profile with
+ * dr = 1 (the capillary rise read out in Sec. 4). */
 cf_status cf_meniscus_height(cf_ctx *ctx, int id, double *Z);
+
+/* Fit of the meniscus model of Sec. 2 (Eq. 12: zeta(r) = Q K_0(q r), Q the
+ * capillary charge, q the inverse capillary length), as done for the
+ * equilibrated profile of Sec. 4.1: least squares over the samples (host
+ * arrays r[n], zeta[n], e.g. from cf_meniscus_profile) with r > 0,
+ * rmin <= r <= rmax and a finite zeta.  For a given q the best Q is linear;
+ * q is scanned on 400 logarithmic steps over [1e-3, 3] and refined by
+ * golden-section search.  out[0] = Q, out[1] = q, out[2] = rms residual,
+ * out[3] = samples used.  K_0 from std::cyl_bessel_k.  Host only, no
+ * context.  CF_EINVAL for null arrays or fewer than two samples. */
+cf_status cf_meniscus_fit(const double *r, const double *zeta, size_t n, double rmin, double rmax,
+                          double out[4]);
+
+/* The lateral capillary force of the theory (Eq. 13) between particles of
+ * capillary charges Q1, Q2 at centre distance L: *F = -2 pi q gamma Q1 Q2
+ * K_1(q L), negative = attraction.  Host only.  CF_EINVAL unless q, L > 0. */
+cf_status cf_capillary_force(double q, double gamma, double Q1, double Q2, double L, double *F);
 
 /* Checkpoint and restart (no counterpart in the paper; the runs reach 2e4 to
  * 5e4 steps).  cf_save writes the state between two steps to `path`: the
@@ -224,14 +258,16 @@ cf_status cf_time_phases(cf_ctx *ctx, long long n, double ms[4]);
  * the same streaming, substrate bounce-back, Shan-Chen force and BGK collision
  * as cf_step does for a lattice without capsules.
  *   src, dst  device pointers, caller-owned, [2][19][nz][ny][nx] float
- *             populations (post-collision) in and out; must not overlap; with
- *             a substrate (wall != 0) the plane z = 0 of dst is not written
+ *             populations (post-collision) in and out; overlapping ranges
+ *             return CF_EINVAL; with a substrate (wall != 0) the plane z = 0
+ *             of dst is not written
  *   nx..G     as in cf_lattice_desc; stream: cudaStream_t or NULL
  * The per-node density scratch is a fixed array inside the library, sized for
  * at most 1048576 nodes (16 MiB, held by every GPU that loads the library until
- * the process exits); larger lattices return CF_EINVAL.  The first call on a
- * device looks up the array's device address with that device current; make
- * that first call before any stream capture.  All calls share the array, so
+ * the process exits); larger lattices return CF_EINVAL.  Every call looks up
+ * the array's device address in the calling thread's current context (the
+ * array's host-side name is not a device address); make the first call on a
+ * device before any stream capture.  All calls share the array, so
  * calls that overlap on the GPU (other streams, other threads) race; each
  * call overwrites the scratch completely before reading it.  Asynchronous on
  * `stream`. */
@@ -273,7 +309,7 @@ cf_status cf_remove_mass(cf_ctx *ctx, double dmA);
 typedef struct cf_batch cf_batch;
 
 /* n (1..128) distinct contexts, all after cf_set_film and with the same
- * precision.  Starts with tile shape 1 (32 x 4) and 2 planes per thread.
+ * precision.  Starts with tile shape 1 (32 x 4) and 4 planes per work item.
  * Errors: CF_EINVAL (bad or repeated context, mixed precision), CF_ESTATE. */
 cf_status cf_batch_create(cf_ctx *const *ctxs, int n, cf_batch **batch);
 cf_status cf_batch_destroy(cf_batch *batch);
@@ -286,20 +322,40 @@ cf_status cf_batch_step(cf_batch *batch, long long n);
  * the batch's own stream). */
 cf_status cf_batch_time(cf_batch *batch, long long n, double *ms);
 
+/* As cf_batch_step without graph replay, timing each phase of every step
+ * with CUDA events on the batch's stream: ms[0] the two batched lattice
+ * passes, ms[1] the phase before them (every context's membrane forces and
+ * bounce records), ms[2] the phase after them (node updates and cut links),
+ * as mean milliseconds per step.  For measurement; the contexts advance
+ * exactly as with cf_batch_step.  Synchronous. */
+cf_status cf_batch_time_phases(cf_batch *batch, long long n, double ms[3]);
+
 /* Launch shape of the batched lattice passes: tile in 0..5 selects the block
  * (x width, y depth) = (32,2), (32,4), (32,8), (64,2), (64,4), (128,2);
- * zchunk >= 1 is the number of planes each thread walks.  Results do not
- * depend on the shape. */
+ * zchunk >= 1 is the number of contiguous planes of a work item (a block
+ * walks them; with tau = 1 through its shared-memory ring of
+ * pseudopotentials).  Results do not depend on the shape. */
 cf_status cf_batch_set_config(cf_batch *batch, int tile, int zchunk);
-cf_status cf_batch_config(const cf_batch *batch, int *tile, int *tile_x, int *tile_y, int *zchunk);
+/* Pipeline groups (1..8): the contexts are split, in order, into this many
+ * groups of about equal node count; each group's lattice passes are launches
+ * of their own on a stream branch of their own, so the membrane and cut-link
+ * phases of one group overlap the lattice passes of another.  Results do not
+ * depend on it.  cf_batch_config reports the groups in use (at most the
+ * number of contexts). */
+cf_status cf_batch_set_groups(cf_batch *batch, int groups);
+cf_status cf_batch_config(const cf_batch *batch, int *tile, int *tile_x, int *tile_y, int *zchunk,
+                          int *groups);
 
-/* Autotuner: for every tile shape and zchunk in {1, 2, 4} it replays the
- * captured two-step graph once untimed and then ceil(steps/2) times timed
- * (steps >= 2), keeps the fastest shape and returns it with its time per step.
- * The trials are real steps: every context advances by
- * 18 * (2 + 2 * ceil(steps / 2)) steps; the fields readout (cf_fields) is
- * refreshed only by the next cf_batch_step. */
-cf_status cf_batch_autotune(cf_batch *batch, int steps, int *tile, int *zchunk, double *ms_per_step);
+/* Autotuner: for every tile shape and zchunk in {2, 4, 8} (one group) it
+ * replays the captured two-step graph once untimed and then ceil(steps/2)
+ * times timed (steps >= 2), keeps the fastest shape, then times the groups
+ * 2, 4 and 8 with that shape, and returns the chosen configuration with its
+ * time per step (any output may be NULL).  The trials are real steps: every
+ * context advances by 2 + 2 ceil(steps/2) steps per configuration tried;
+ * the fields readout (cf_fields) is refreshed only by the next
+ * cf_batch_step. */
+cf_status cf_batch_autotune(cf_batch *batch, int steps, int *tile, int *zchunk, int *groups,
+                            double *ms_per_step);
 
 /* Number of kernel launches issued by the last cf_batch_step / cf_batch_time. */
 cf_status cf_batch_launch_count(const cf_batch *batch, long long *n);

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libcapfilm.so")
 
 CF_OK = 0
 STATUS_NAMES = {0: "CF_OK", 1: "CF_EINVAL", 2: "CF_ENOMEM", 3: "CF_ECUDA", 4: "CF_ESTATE",
-                5: "CF_ENOTFOUND", 6: "CF_EDIVERGED", 7: "CF_EOVERFLOW", 8: "CF_ETIMEOUT"}
+                5: "CF_ENOTFOUND", 6: "CF_EDIVERGED", 7: "CF_EOVERFLOW"}
 
 FREE, FROZEN, FIXED = 0, 1, 2
 FP32, FP16_SHIFT, BF16_SHIFT = 0, 1, 2
@@ -41,7 +41,8 @@ class LatticeDesc(C.Structure):
 class CapsuleDesc(C.Structure):
     _fields_ = [("nv", C.c_int), ("nf", C.c_int), ("nodes", C.POINTER(C.c_double)),
                 ("faces", C.POINTER(C.c_int)), ("kS", C.c_double), ("C", C.c_double),
-                ("kB", C.c_double), ("kV", C.c_double), ("mass", C.c_double), ("mode", C.c_int)]
+                ("kB", C.c_double), ("kV", C.c_double), ("mass", C.c_double), ("mode", C.c_int),
+                ("wet", C.c_double)]
 
 
 class CapfilmError(RuntimeError):
@@ -79,11 +80,12 @@ def load_library(path: Optional[str] = None):
         "cf_capsule_force": [C.c_void_p, C.c_int, _dp, _dp],
         "cf_lateral_force": [C.c_void_p, C.c_int, C.c_int, _dp],
         "cf_capsule_state": [C.c_void_p, C.c_int, _dp, _dp, _dp],
-        "cf_fields": [C.c_void_p, _dp, _dp],
+        "cf_fields": [C.c_void_p, _dp, _dp, C.POINTER(C.c_size_t)],
         "cf_populations": [C.c_void_p, _fp],
         "cf_total_mass": [C.c_void_p, _dp],
         "cf_meniscus_field": [C.c_void_p, _dp],
-        "cf_meniscus_profile": [C.c_void_p, C.c_int, _dp, _dp, C.POINTER(C.c_size_t), _dp],
+        "cf_meniscus_profile": [C.c_void_p, C.c_int, C.c_double, _dp, _dp, C.POINTER(C.c_size_t),
+                                _dp],
         "cf_cuts": [C.c_void_p, C.POINTER(C.c_uint32), C.POINTER(C.c_int), C.POINTER(C.c_uint8)],
         "cf_launch_count": [C.c_void_p, C.POINTER(C.c_longlong)],
         "cf_time_phases": [C.c_void_p, C.c_longlong, _dp],
@@ -106,10 +108,13 @@ def load_library(path: Optional[str] = None):
         "cf_batch_destroy": [C.c_void_p],
         "cf_batch_step": [C.c_void_p, C.c_longlong],
         "cf_batch_time": [C.c_void_p, C.c_longlong, _dp],
+        "cf_batch_time_phases": [C.c_void_p, C.c_longlong, _dp],
         "cf_batch_set_config": [C.c_void_p, C.c_int, C.c_int],
+        "cf_batch_set_groups": [C.c_void_p, C.c_int],
         "cf_batch_config": [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
-                            C.POINTER(C.c_int)],
-        "cf_batch_autotune": [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp],
+                            C.POINTER(C.c_int), C.POINTER(C.c_int)],
+        "cf_batch_autotune": [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                              C.POINTER(C.c_int), _dp],
         "cf_batch_launch_count": [C.c_void_p, C.POINTER(C.c_longlong)],
         "cf_batch_lateral_forces": [C.c_void_p, C.c_int, C.c_int, _dp],
         "cf_save": [C.c_void_p, C.c_char_p],
@@ -119,6 +124,8 @@ def load_library(path: Optional[str] = None):
         "cf_warm_apply": [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p],
         "cf_warm_target": [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p],
         "cf_field_check": [C.c_void_p, _dp],
+        "cf_meniscus_fit": [_dp, _dp, C.c_size_t, C.c_double, C.c_double, _dp],
+        "cf_capillary_force": [C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _dp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -134,11 +141,12 @@ def exported_symbols():
             "cf_capsule_state", "cf_fields", "cf_populations", "cf_total_mass",
             "cf_meniscus_field", "cf_meniscus_profile", "cf_cuts", "cf_launch_count",
             "cf_time_phases", "cf_lattice_step_static", "cf_batch_create", "cf_batch_destroy",
-            "cf_batch_step", "cf_batch_time", "cf_batch_set_config", "cf_batch_config",
+            "cf_batch_step", "cf_batch_time", "cf_batch_time_phases", "cf_batch_set_config", "cf_batch_set_groups", "cf_batch_config",
             "cf_batch_autotune", "cf_batch_launch_count", "cf_set_densities", "cf_remove_mass", "cf_save", "cf_load", "cf_meniscus_height",
             "cf_batch_lateral_forces", "cf_warm_features", "cf_warm_apply", "cf_warm_target",
             "cf_field_check", "cf_conv3d_forward",
-            "cf_conv3d_backward", "cf_mse", "cf_adam", "cf_to_bf16", "cf_from_bf16"]
+            "cf_conv3d_backward", "cf_mse", "cf_adam", "cf_to_bf16", "cf_from_bf16",
+            "cf_meniscus_fit", "cf_capillary_force"]
 
 
 def _check(rc):
@@ -159,6 +167,25 @@ def lattice_step_static(src_ptr, dst_ptr, nx, ny, nz, wall=1, tau=(1.0, 1.0), G=
     t = np.ascontiguousarray(tau, np.float64)
     _check(L.cf_lattice_step_static(C.c_void_p(src_ptr), C.c_void_p(dst_ptr), nx, ny, nz, wall,
                                     _ptr(t), G, C.c_void_p(stream_ptr) if stream_ptr else None))
+
+
+def meniscus_fit(r, zeta, rmin=0.0, rmax=np.inf):
+    """(Q, q, rms, samples) of zeta = Q K_0(q r) fitted over rmin <= r <= rmax
+    (cf_meniscus_fit)."""
+    L = load_library()
+    r = np.ascontiguousarray(r, np.float64)
+    z = np.ascontiguousarray(zeta, np.float64)
+    out = np.zeros(4)
+    _check(L.cf_meniscus_fit(_ptr(r), _ptr(z), len(r), float(rmin), float(min(rmax, 1e300)), _ptr(out)))
+    return float(out[0]), float(out[1]), float(out[2]), int(out[3])
+
+
+def capillary_force(q, gamma, Q1, Q2, L_):
+    """-2 pi q gamma Q1 Q2 K_1(q L) (cf_capillary_force)."""
+    L = load_library()
+    F = np.zeros(1)
+    _check(L.cf_capillary_force(float(q), float(gamma), float(Q1), float(Q2), float(L_), _ptr(F)))
+    return float(F[0])
 
 
 class _TorchAllocator:
@@ -226,7 +253,8 @@ class Simulation:
         s = cls(wl.nx, wl.ny, wl.nz, wall=wl.wall, tau=wl.tau, G=wl.G, rep_dz=wl.rep_dz, **kw)
         for cap in wl.capsules:
             X, F = cap.mesh()
-            s.add_capsule(X, F, cap.kS, cap.C, cap.kB, cap.kV, cap.mass, cap.mode)
+            s.add_capsule(X, F, cap.kS, cap.C, cap.kB, cap.kV, cap.mass, cap.mode,
+                          wet=getattr(cap, "wet", 0.0))
         if set_film:
             from .inputs import RHO_MAJ, RHO_MIN, RHO_MIX
             s.set_film(wl.h_top, RHO_MAJ, RHO_MIN, RHO_MIX, wl.jitter())
@@ -245,11 +273,11 @@ class Simulation:
         except Exception:
             pass
 
-    def add_capsule(self, X, F, kS, C_, kB, kV, mass, mode):
+    def add_capsule(self, X, F, kS, C_, kB, kV, mass, mode, wet=0.0):
         X = np.ascontiguousarray(X, np.float64)
         F = np.ascontiguousarray(F, np.int32)
         d = CapsuleDesc(X.shape[0], F.shape[0], _ptr(X), F.ctypes.data_as(C.POINTER(C.c_int)),
-                        kS, C_, kB, kV, mass, mode)
+                        kS, C_, kB, kV, mass, mode, float(wet))
         cid = C.c_int()
         _check(_lib.cf_add_capsule(self._h, C.byref(d), C.byref(cid)))
         self.nv.append(X.shape[0])
@@ -376,7 +404,8 @@ class Simulation:
     def fields(self):
         rho = np.zeros((2, self.nz, self.ny, self.nx))
         u = np.zeros((3, self.nz, self.ny, self.nx))
-        _check(_lib.cf_fields(self._h, _ptr(rho), _ptr(u)))
+        n = C.c_size_t(self.N)
+        _check(_lib.cf_fields(self._h, _ptr(rho), _ptr(u), C.byref(n)))
         return rho, u
 
     def populations(self):
@@ -394,11 +423,12 @@ class Simulation:
         _check(_lib.cf_meniscus_field(self._h, _ptr(h)))
         return h
 
-    def meniscus_profile(self, cid):
+    def meniscus_profile(self, cid, dr=1.0):
+        """(r, zeta, Z) of capsule cid's meniscus, sampled every dr (cf_meniscus_profile)."""
         n = C.c_size_t(0)
-        rc = _lib.cf_meniscus_profile(self._h, cid, None, None, C.byref(n), None)
+        _lib.cf_meniscus_profile(self._h, cid, float(dr), None, None, C.byref(n), None)
         r = np.zeros(n.value); z = np.zeros(n.value); Z = np.zeros(1)
-        _check(_lib.cf_meniscus_profile(self._h, cid, _ptr(r), _ptr(z), C.byref(n), _ptr(Z)))
+        _check(_lib.cf_meniscus_profile(self._h, cid, float(dr), _ptr(r), _ptr(z), C.byref(n), _ptr(Z)))
         return r, z, float(Z[0])
 
     def cuts(self):
@@ -439,19 +469,31 @@ class Batch:
         _check(_lib.cf_batch_time(self._h, int(n), C.byref(ms)))
         return ms.value
 
+    def time_phases(self, n):
+        """Mean device ms per step of (lattice passes, phase before them, phase
+        after them) over n steps (cf_batch_time_phases)."""
+        ms = np.zeros(3)
+        _check(_lib.cf_batch_time_phases(self._h, int(n), _ptr(ms)))
+        return ms
+
     def set_config(self, tile, zchunk):
         _check(_lib.cf_batch_set_config(self._h, int(tile), int(zchunk)))
 
+    def set_groups(self, groups):
+        """Pipeline groups of the batch (cf_batch_set_groups)."""
+        _check(_lib.cf_batch_set_groups(self._h, int(groups)))
+
     def config(self):
-        t, tx, ty, zc = C.c_int(), C.c_int(), C.c_int(), C.c_int()
-        _check(_lib.cf_batch_config(self._h, C.byref(t), C.byref(tx), C.byref(ty), C.byref(zc)))
-        return dict(tile=t.value, tile_x=tx.value, tile_y=ty.value, zchunk=zc.value)
+        t, tx, ty, zc, g = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(_lib.cf_batch_config(self._h, C.byref(t), C.byref(tx), C.byref(ty), C.byref(zc), C.byref(g)))
+        return dict(tile=t.value, tile_x=tx.value, tile_y=ty.value, zchunk=zc.value, groups=g.value)
 
     def autotune(self, steps=6):
-        """Time every launch shape for `steps` steps (real steps) and keep the
-        fastest; returns the chosen shape and its ms per step."""
-        t, zc, ms = C.c_int(), C.c_int(), C.c_double()
-        _check(_lib.cf_batch_autotune(self._h, int(steps), C.byref(t), C.byref(zc), C.byref(ms)))
+        """Time the launch shapes and pipeline groups for `steps` steps each
+        (real steps) and keep the fastest; returns the chosen configuration
+        and its ms per step."""
+        t, zc, g, ms = C.c_int(), C.c_int(), C.c_int(), C.c_double()
+        _check(_lib.cf_batch_autotune(self._h, int(steps), C.byref(t), C.byref(zc), C.byref(g), C.byref(ms)))
         d = self.config()
         d["ms_per_step"] = ms.value
         return d

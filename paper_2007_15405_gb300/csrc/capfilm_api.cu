@@ -36,7 +36,7 @@ cf_status fail(cf_status s, const std::string &msg) {
 
 struct HostCapsule {
     int nv, nf, mode;
-    double kS, C, kB, kV, mass;
+    double kS, C, kB, kV, mass, wet;
     std::vector<float> X;      // reference positions (float)
     std::vector<int> F;        // local faces
 };
@@ -97,6 +97,8 @@ struct cf_ctx {
     int capacity = 0;
     unsigned *status = nullptr;
     double *dscratch = nullptr;  // small FP64 scratch (mass)
+    double *pscratch = nullptr;  // meniscus profile readout [pcap]
+    size_t pcap = 0;
     float *hscratch = nullptr;   // meniscus field [nx*ny]
     double *jit = nullptr;
 
@@ -111,6 +113,7 @@ struct cf_ctx {
     float *FT[2] = {nullptr, nullptr};
     int ftpar = 0;
     float4 *uT = nullptr;  // element velocities, recorded with the cut links
+    float *wet_el = nullptr;  // [nfaces] wetting offset per element (null when every capsule is neutral)
     float *V = nullptr, *fscr = nullptr, *vscr = nullptr,
           *Fcpl = nullptr, *refM = nullptr, *refA = nullptr, *refDet = nullptr;
     int *faces = nullptr, *face_cap = nullptr, *node_cap = nullptr, *vf_off = nullptr,
@@ -123,6 +126,7 @@ struct cf_ctx {
     long long steps_done = 0;
     long long launches_last = 0;
     int zchunk = 0;
+    int zring = 1;
 
     cudaGraphExec_t graph = nullptr;
     int graph_key = -1;
@@ -170,7 +174,6 @@ cf_status check_status(cf_ctx *c) {
         if (st & ST_OVERFLOW)
             return fail(CF_EOVERFLOW, "cut-link list exceeded its capacity, or an element spans more "
                                       "than 16 lattice units (or has a non-finite position)");
-        if (st & ST_TIMEOUT) return fail(CF_ETIMEOUT, "a bounded device-side wait timed out");
     }
     return CF_OK;
 }
@@ -182,6 +185,7 @@ LBParams lb_params(cf_ctx *c, bool with_out) {
     p.zlo = c->d.wall ? 1 : 0;
     p.zhi = c->d.nz;
     p.zchunk = c->zchunk;
+    p.zring = c->zring;
     for (int k = 0; k < 2; ++k) {
         p.tau[k] = (float)c->d.tau[k];
         p.itau[k] = (float)(1.0 / c->d.tau[k]);
@@ -203,6 +207,7 @@ LBParams lb_params(cf_ctx *c, bool with_out) {
     p.psi = c->psi;
     p.J = c->J;
     p.rec = c->rec;
+    p.wet_el = c->wet_el;
     p.status = c->status;
     p.dry_dm = c->dry_dm;
     p.dry_part = c->dry_part;
@@ -379,6 +384,15 @@ void choose_launch(cf_ctx *c) {
         const int v = std::atoi(e);
         if (v > 0) c->zchunk = std::min(v, nzf);
     }
+    // tau = 1 collide pass: each block walks zring contiguous planes through its
+    // pseudopotential ring (halo loads amortised over the planes); as many as
+    // keep about two waves of resident blocks (8 per SM), at most 16
+    const int waves2 = 2 * 8 * sms;
+    c->zring = std::max(1, std::min(16, (int)((long long)cols * nzf / waves2)));
+    if (const char *e = std::getenv("CAPFILM_ZRING")) {
+        const int v = std::atoi(e);
+        if (v > 0) c->zring = std::min(v, nzf);
+    }
 }
 
 cf_status build_membrane(cf_ctx *c) {
@@ -477,6 +491,15 @@ cf_status build_membrane(cf_ctx *c) {
     MALLOC_M(c->bbox[1], int, 6 * nc);
     MALLOC_M(c->capdev, CapDev, nc);
     MALLOC_M(c->acc, double, A_NACC * nc);
+    c->wet_el = nullptr;
+    bool any_wet = false;
+    for (auto &h : c->caps) any_wet |= h.wet != 0.0;
+    if (any_wet) {
+        MALLOC_M(c->wet_el, float, nf);
+        std::vector<float> we(nf);
+        for (int f = 0; f < nf; ++f) we[f] = (float)c->caps[face_cap[f]].wet;
+        CF_CUDA(up(c->wet_el, we.data(), sizeof(float) * we.size()));
+    }
 #undef MALLOC_M
     c->xpar = 0;
     {   // bounding boxes of the initial shapes (read as the previous step's)
@@ -639,6 +662,7 @@ cf_status cf_destroy(cf_ctx *c) {
     for (void *p : c->mem_allocs) dfree(c, p);
     for (void *p : c->allocations) dfree(c, p);
     if (c->jit) dfree(c, c->jit);
+    if (c->pscratch) dfree(c, c->pscratch);
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->stream2) { cudaStreamSynchronize(c->stream2); cudaStreamDestroy(c->stream2); }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -654,10 +678,11 @@ cf_status cf_add_capsule(cf_ctx *c, const cf_capsule_desc *d, int *id) {
     if (d->nv < 4 || d->nf < 4) return fail(CF_EINVAL, "capsule mesh too small");
     if (d->mode < 0 || d->mode > 2) return fail(CF_EINVAL, "bad capsule mode");
     if (!(d->mass > 0)) return fail(CF_EINVAL, "node mass must be positive");
+    if (!std::isfinite(d->wet)) return fail(CF_EINVAL, "wetting offset must be finite");
     if (c->film_set) return fail(CF_ESTATE, "capsules must be added before cf_set_film");
     HostCapsule h;
     h.nv = d->nv; h.nf = d->nf; h.mode = d->mode;
-    h.kS = d->kS; h.C = d->C; h.kB = d->kB; h.kV = d->kV; h.mass = d->mass;
+    h.kS = d->kS; h.C = d->C; h.kB = d->kB; h.kV = d->kV; h.mass = d->mass; h.wet = d->wet;
     h.X.resize(3 * (size_t)d->nv);
     for (size_t i = 0; i < h.X.size(); ++i) h.X[i] = (float)d->nodes[i];
     h.F.assign(d->faces, d->faces + 3 * (size_t)d->nf);
@@ -823,8 +848,16 @@ cf_status cf_step(cf_ctx *c, long long n) {
     if (n == 0) return CF_OK;
     int nl = 0;
     long long left = n - 1;  // the last step records the fields
+    auto key_of = [](const cf_ctx *x) { return x->fpar | (x->xpar << 1) | (x->lpar << 2) | (x->ftpar << 3); };
+    if (left >= 3 && c->graph && c->graph_key != key_of(c)) {
+        // every double buffer flips each step, so one plain step brings the
+        // context to the parity of the captured graph (no capture here)
+        cf_status s = enqueue_step(c, false, &nl);
+        if (s != CF_OK) return s;
+        --left;
+    }
     if (left >= 2) {
-        const int key = c->fpar | (c->xpar << 1) | (c->lpar << 2) | (c->ftpar << 3);
+        const int key = key_of(c);
         if (!c->graph || c->graph_key != key) {
             if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
             cudaGraph_t g;
@@ -962,9 +995,14 @@ cf_status cf_capsule_state(cf_ctx *c, int id, double *nodes, double *area, doubl
     return CF_OK;
 }
 
-cf_status cf_fields(cf_ctx *c, double *rho, double *u) {
-    if (!c) return fail(CF_EINVAL, "null context");
+cf_status cf_fields(cf_ctx *c, double *rho, double *u, size_t *inout_n) {
+    if (!c || !inout_n) return fail(CF_EINVAL, "null argument");
     const long long N = c->N;
+    if (*inout_n < (size_t)N) {
+        *inout_n = (size_t)N;
+        return fail(CF_EINVAL, "field buffers too small (need " + std::to_string(N) + " nodes)");
+    }
+    *inout_n = (size_t)N;
     std::vector<float> h(5 * (size_t)N);
     CF_CUDA(cudaMemcpyAsync(h.data(), c->out, sizeof(float) * h.size(), cudaMemcpyDeviceToHost, c->stream));
     cf_status s = sync_ok(c);
@@ -1031,62 +1069,113 @@ cf_status cf_meniscus_field(cf_ctx *c, double *h) {
     return CF_OK;
 }
 
-cf_status cf_meniscus_profile(cf_ctx *c, int id, double *r, double *zeta, size_t *inout_n, double *Z) {
+static size_t profile_samples(const cf_ctx *c, double dr) {
+    return (size_t)std::floor((double)(std::min(c->d.nx, c->d.ny) / 2) / dr + 1e-9);
+}
+
+cf_status cf_meniscus_profile(cf_ctx *c, int id, double dr, double *r, double *zeta, size_t *inout_n,
+                              double *Z) {
     if (!c || !inout_n) return fail(CF_EINVAL, "null argument");
     const int nc = (int)c->caps.size();
     if (id < 0 || id >= nc) return fail(CF_ENOTFOUND, "unknown capsule");
-    const int nx = c->d.nx, ny = c->d.ny;
-    const size_t nr = (size_t)(std::min(nx, ny) / 2);
+    if (!(dr > 0.0) || !std::isfinite(dr) || dr > std::min(c->d.nx, c->d.ny) / 2)
+        return fail(CF_EINVAL, "dr must be positive and at most half the smaller lateral size");
+    const size_t nr = profile_samples(c, dr);
     if (*inout_n < nr || !r || !zeta) { *inout_n = nr; return fail(CF_EINVAL, "profile buffer too small"); }
-    std::vector<double> h((size_t)nx * ny), acc;
-    cf_status s = cf_meniscus_field(c, h.data());
-    if (s != CF_OK) return s;
-    s = read_acc(c, acc);
-    if (s != CF_OK) return s;
-    std::vector<double> cx(nc), cy(nc);
-    for (int k = 0; k < nc; ++k) {
-        cx[k] = acc[(size_t)k * A_NACC + A_OX] + acc[(size_t)k * A_NACC + A_CX] / c->caps[k].nv;
-        cy[k] = acc[(size_t)k * A_NACC + A_OY] + acc[(size_t)k * A_NACC + A_CY] / c->caps[k].nv;
+    if (c->pcap < nr + 2) {
+        if (c->pscratch) dfree(c, c->pscratch);
+        c->pscratch = (double *)dalloc(c, sizeof(double) * (nr + 2));
+        if (!c->pscratch) { c->pcap = 0; return fail(CF_ENOMEM, "device allocation failed (profile)"); }
+        c->allocations.pop_back();  // freed explicitly
+        c->pcap = nr + 2;
     }
-    // far-field height: valid columns whose distance to the nearest capsule
-    // is at least 90 % of the largest such distance
-    std::vector<double> dmin((size_t)nx * ny);
-    double dmax = 0.0;
-    for (int y = 0; y < ny; ++y)
-        for (int x = 0; x < nx; ++x) {
-            double best = 1e300;
-            for (int k = 0; k < nc; ++k) {
-                double dx = x - cx[k], dy = y - cy[k];
-                dx -= nx * std::floor(dx / nx + 0.5);
-                dy -= ny * std::floor(dy / ny + 0.5);
-                best = std::min(best, std::sqrt(dx * dx + dy * dy));
-            }
-            dmin[(size_t)y * nx + x] = best;
-            if (!std::isnan(h[(size_t)y * nx + x])) dmax = std::max(dmax, best);
-        }
-    double hs = 0.0;
-    int hc = 0;
-    for (size_t i = 0; i < h.size(); ++i)
-        if (!std::isnan(h[i]) && dmin[i] >= 0.9 * dmax) { hs += h[i]; ++hc; }
-    const double hinf = hc ? hs / hc : NAN;
-    const int x0 = (int)std::lround(cx[id]), y0 = (int)std::lround(cy[id]);
-    double zmax = -1e300;
+    CF_CUDA(launch_inside(c->mask, c->inside, c->d.nx, c->d.ny, c->d.nz, c->stream));
+    CF_CUDA(launch_meniscus(c->out, c->inside, c->hscratch, c->d.nx, c->d.ny, c->d.nz, c->d.wall, c->stream));
+    CF_CUDA(launch_meniscus_profile(c->hscratch, c->d.nx, c->d.ny, c->acc, c->capdev, nc, id, dr, (int)nr,
+                                    c->pscratch, c->stream));
+    std::vector<double> out(nr + 2);
+    CF_CUDA(cudaMemcpyAsync(out.data(), c->pscratch, sizeof(double) * out.size(), cudaMemcpyDeviceToHost,
+                            c->stream));
+    cf_status s = sync_ok(c);
+    if (s != CF_OK) return s;
     for (size_t k = 0; k < nr; ++k) {
-        double s2 = 0.0;
-        int cnt = 0;
-        const int dxs[4] = {1, -1, 0, 0}, dys[4] = {0, 0, 1, -1};
-        for (int q = 0; q < 4; ++q) {
-            const int x = ((x0 + dxs[q] * (int)k) % nx + nx) % nx;
-            const int y = ((y0 + dys[q] * (int)k) % ny + ny) % ny;
-            const double v = h[(size_t)y * nx + x];
-            if (!std::isnan(v)) { s2 += v; ++cnt; }
-        }
-        r[k] = (double)k;
-        zeta[k] = cnt ? s2 / cnt - hinf : NAN;
-        if (cnt && zeta[k] > zmax) zmax = zeta[k];
+        r[k] = (double)k * dr;
+        zeta[k] = out[k];
     }
     *inout_n = nr;
-    if (Z) *Z = zmax;
+    if (Z) *Z = out[nr];
+    return CF_OK;
+}
+
+// ------------------------------------------- theory of the capillary force
+namespace {
+// sum of squared residuals of zeta ~ Q K0(q r) at the best Q for this q
+double fit_residual(const std::vector<double> &r, const std::vector<double> &z, double q, double *Qbest) {
+    double zk = 0.0, kk = 0.0;
+    std::vector<double> k0(r.size());
+    for (size_t i = 0; i < r.size(); ++i) {
+        k0[i] = std::cyl_bessel_k(0.0, q * r[i]);
+        zk += z[i] * k0[i];
+        kk += k0[i] * k0[i];
+    }
+    const double Q = kk > 0.0 ? zk / kk : 0.0;
+    double S = 0.0;
+    for (size_t i = 0; i < r.size(); ++i) S += (z[i] - Q * k0[i]) * (z[i] - Q * k0[i]);
+    if (Qbest) *Qbest = Q;
+    return S;
+}
+}  // namespace
+
+extern "C" cf_status cf_meniscus_fit(const double *r, const double *zeta, size_t n, double rmin, double rmax,
+                                     double out[4]) {
+    if (!r || !zeta || !out) return fail(CF_EINVAL, "null argument");
+    std::vector<double> rr, zz;
+    for (size_t i = 0; i < n; ++i)
+        if (r[i] > 0.0 && r[i] >= rmin && r[i] <= rmax && std::isfinite(zeta[i])) {
+            rr.push_back(r[i]);
+            zz.push_back(zeta[i]);
+        }
+    if (rr.size() < 2) return fail(CF_EINVAL, "fewer than two finite profile samples in [rmin, rmax]");
+    // coarse scan of ln q over [ln 1e-3, ln 3], then golden-section refinement
+    const int NS = 400;
+    const double a0 = std::log(1e-3), a1 = std::log(3.0);
+    int best = 0;
+    double bestS = HUGE_VAL;
+    for (int i = 0; i < NS; ++i) {
+        const double S = fit_residual(rr, zz, std::exp(a0 + (a1 - a0) * i / (NS - 1)), nullptr);
+        if (S < bestS) { bestS = S; best = i; }
+    }
+    double lo = a0 + (a1 - a0) * std::max(best - 1, 0) / (NS - 1);
+    double hi = a0 + (a1 - a0) * std::min(best + 1, NS - 1) / (NS - 1);
+    const double phi = 0.5 * (std::sqrt(5.0) - 1.0);
+    double x1 = hi - phi * (hi - lo), x2 = lo + phi * (hi - lo);
+    double f1 = fit_residual(rr, zz, std::exp(x1), nullptr), f2 = fit_residual(rr, zz, std::exp(x2), nullptr);
+    for (int it = 0; it < 200 && hi - lo > 1e-15; ++it) {
+        if (f1 < f2) {
+            hi = x2; x2 = x1; f2 = f1;
+            x1 = hi - phi * (hi - lo);
+            f1 = fit_residual(rr, zz, std::exp(x1), nullptr);
+        } else {
+            lo = x1; x1 = x2; f1 = f2;
+            x2 = lo + phi * (hi - lo);
+            f2 = fit_residual(rr, zz, std::exp(x2), nullptr);
+        }
+    }
+    const double q = std::exp(0.5 * (lo + hi));
+    double Q = 0.0;
+    const double S = fit_residual(rr, zz, q, &Q);
+    out[0] = Q;
+    out[1] = q;
+    out[2] = std::sqrt(S / rr.size());
+    out[3] = (double)rr.size();
+    return CF_OK;
+}
+
+extern "C" cf_status cf_capillary_force(double q, double gamma, double Q1, double Q2, double L, double *F) {
+    if (!F) return fail(CF_EINVAL, "null argument");
+    if (!(q > 0.0) || !(L > 0.0)) return fail(CF_EINVAL, "q and L must be positive");
+    const double pi = 3.14159265358979323846;
+    *F = -2.0 * pi * q * gamma * Q1 * Q2 * std::cyl_bessel_k(1.0, q * L);
     return CF_OK;
 }
 
@@ -1213,9 +1302,9 @@ cf_status cf_load(cf_ctx *c, const char *path) {
 
 cf_status cf_meniscus_height(cf_ctx *c, int id, double *Z) {
     if (!c || !Z) return fail(CF_EINVAL, "null argument");
-    size_t n = (size_t)(std::min(c->d.nx, c->d.ny) / 2);
+    size_t n = profile_samples(c, 1.0);
     std::vector<double> r(std::max<size_t>(n, 1)), zeta(std::max<size_t>(n, 1));
-    return cf_meniscus_profile(c, id, r.data(), zeta.data(), &n, Z);
+    return cf_meniscus_profile(c, id, 1.0, r.data(), zeta.data(), &n, Z);
 }
 
 cf_status cf_cuts(cf_ctx *c, uint32_t *mask, int *tri, uint8_t *inside) {
@@ -1240,15 +1329,26 @@ cf_status cf_cuts(cf_ctx *c, uint32_t *mask, int *tri, uint8_t *inside) {
 // ----------------------------------------------------------------- batches
 // A batch steps many contexts together: their membrane halves run as
 // parallel branches, their lattice passes as one persistent launch per pass.
+// With groups > 1 the contexts are split into groups of about equal node
+// count, each with its own lattice launches on a stream branch of its own,
+// so that the membrane phases of one group overlap the lattice passes of
+// another.
+constexpr int CF_MAX_GROUPS = 8;
 struct cf_batch {
     std::vector<cf_ctx *> ctx;
     int prec = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_lat = nullptr;
-    int tile = 1, zchunk = 2;     // tile shape index and planes per thread
-    int4 *work = nullptr;          // device work list
+    int tile = 1, zchunk = 4;     // tile shape index and contiguous planes per work item
+    int groups = 1;               // pipeline groups
+    int4 *work = nullptr;          // device work list of all lattices (one launch)
     int nwork = 0;
     std::vector<int> zstride;      // per lattice
+    std::vector<int> gbeg;                 // [groups + 1] context ranges of the groups
+    std::vector<cudaStream_t> gstream;     // [CF_MAX_GROUPS] stream branch per group
+    std::vector<cudaEvent_t> gev;          // [CF_MAX_GROUPS] after the group's lattice passes
+    std::vector<int4 *> gwork;             // per group: work list (lattice index within the group)
+    std::vector<int> gnwork;
     cudaGraphExec_t graph = nullptr;
     std::vector<int> graph_key;    // parities of all contexts at capture
     int graph_launches = 0;
@@ -1257,32 +1357,115 @@ struct cf_batch {
 
 namespace {
 
-cf_status batch_build_work(cf_batch *b) {
+// work items (lattice index - base, x tile, y tile, z slice) of contexts [i0, i1)
+void batch_items(cf_batch *b, size_t i0, size_t i1, int base, std::vector<int4> &w) {
     int tx, ty;
     lb_batch_tile(b->tile, &tx, &ty);
-    std::vector<int4> w;
-    b->zstride.assign(b->ctx.size(), 1);
-    for (size_t i = 0; i < b->ctx.size(); ++i) {
+    for (size_t i = i0; i < i1; ++i) {
         const cf_ctx *c = b->ctx[i];
-        const int nzf = c->d.nz - (c->d.wall ? 1 : 0);
-        const int gz = std::max(1, (nzf + b->zchunk - 1) / b->zchunk);
-        b->zstride[i] = gz;
-        for (int zs = 0; zs < gz; ++zs)
+        for (int zs = 0; zs < b->zstride[i]; ++zs)
             for (int ty_ = 0; ty_ < (c->d.ny + ty - 1) / ty; ++ty_)
                 for (int tx_ = 0; tx_ < (c->d.nx + tx - 1) / tx; ++tx_)
-                    w.push_back(make_int4((int)i, tx_, ty_, zs));
+                    w.push_back(make_int4((int)i - base, tx_, ty_, zs));
     }
-    if (b->work) cudaFree(b->work);
-    b->work = nullptr;
-    CF_CUDA(cudaMalloc(&b->work, sizeof(int4) * w.size()));
-    CF_CUDA(cudaMemcpy(b->work, w.data(), sizeof(int4) * w.size(), cudaMemcpyHostToDevice));
+}
+
+cf_status upload_work(const std::vector<int4> &w, int4 **dev) {
+    if (*dev) cudaFree(*dev);
+    *dev = nullptr;
+    CF_CUDA(cudaMalloc(dev, sizeof(int4) * std::max<size_t>(w.size(), 1)));
+    CF_CUDA(cudaMemcpy(*dev, w.data(), sizeof(int4) * w.size(), cudaMemcpyHostToDevice));
+    return CF_OK;
+}
+
+cf_status batch_build_work(cf_batch *b) {
+    const size_t n = b->ctx.size();
+    b->zstride.assign(n, 1);
+    for (size_t i = 0; i < n; ++i) {
+        const cf_ctx *c = b->ctx[i];
+        const int nzf = c->d.nz - (c->d.wall ? 1 : 0);
+        b->zstride[i] = std::max(1, (nzf + b->zchunk - 1) / b->zchunk);
+    }
+    std::vector<int4> w;
+    batch_items(b, 0, n, 0, w);
+    cf_status s = upload_work(w, &b->work);
+    if (s != CF_OK) return s;
     b->nwork = (int)w.size();
+    // groups: G contiguous context ranges, each non-empty, boundary k placed
+    // where the node count before it is nearest to k / G of the total
+    const int G = std::max(1, std::min(b->groups, (int)n));
+    std::vector<long long> cum(n + 1, 0);
+    for (size_t i = 0; i < n; ++i) cum[i + 1] = cum[i] + b->ctx[i]->N;
+    b->gbeg.assign(1, 0);
+    for (int k = 1; k < G; ++k) {
+        const int lo = b->gbeg.back() + 1, hi = (int)n - (G - k);
+        int bi = lo;
+        for (int i = lo; i <= hi; ++i)
+            if (std::llabs(cum[i] * G - cum[n] * k) < std::llabs(cum[bi] * G - cum[n] * k)) bi = i;
+        b->gbeg.push_back(bi);
+    }
+    b->gbeg.push_back((int)n);
+    const int ng = (int)b->gbeg.size() - 1;
+    b->gnwork.assign(ng, 0);
+    if (b->gwork.size() < (size_t)ng) b->gwork.resize(ng, nullptr);
+    for (int g = 0; g < ng; ++g) {
+        std::vector<int4> wg;
+        batch_items(b, b->gbeg[g], b->gbeg[g + 1], b->gbeg[g], wg);
+        s = upload_work(wg, &b->gwork[g]);
+        if (s != CF_OK) return s;
+        b->gnwork[g] = (int)wg.size();
+    }
     if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
     return CF_OK;
 }
 
-// one step of every context of the batch, enqueued on the batch stream
-cf_status batch_enqueue_step(cf_batch *b, bool with_out, int *nl) {
+// one step with the contexts in pipeline groups (see cf_batch)
+cf_status batch_enqueue_groups(cf_batch *b, bool with_out, int *nl) {
+    CF_CUDA(cudaEventRecord(b->ev_fork, b->stream));
+    const int ng = (int)b->gbeg.size() - 1;
+    static BatchTab tab;  // copied into each launch
+    for (int g = 0; g < ng; ++g) {
+        cudaStream_t gs = b->gstream[g];
+        CF_CUDA(cudaStreamWaitEvent(gs, b->ev_fork, 0));
+        for (int i = b->gbeg[g]; i < b->gbeg[g + 1]; ++i) {
+            cf_ctx *c = b->ctx[i];
+            CF_CUDA(cudaStreamWaitEvent(c->stream, b->ev_fork, 0));
+            cf_status s = enqueue_pre(c, nl);
+            if (s != CF_OK) return s;
+            CF_CUDA(cudaEventRecord(c->ev_batch, c->stream));
+            CF_CUDA(cudaStreamWaitEvent(gs, c->ev_batch, 0));
+        }
+        for (int i = b->gbeg[g]; i < b->gbeg[g + 1]; ++i) {
+            LBParams &l = tab.lat[i - b->gbeg[g]];
+            l = lb_params(b->ctx[i], with_out);
+            l.zstride = b->zstride[i];
+            l.zchunk = b->zchunk;
+        }
+        CF_CUDA(launch_lb_batch(tab, b->gbeg[g + 1] - b->gbeg[g], b->gwork[g], b->gnwork[g], b->prec, b->tile, gs));
+        *nl += 2;
+        CF_CUDA(cudaEventRecord(b->gev[g], gs));
+        CF_CUDA(cudaStreamWaitEvent(b->stream, b->gev[g], 0));
+        for (int i = b->gbeg[g]; i < b->gbeg[g + 1]; ++i) {
+            cf_ctx *c = b->ctx[i];
+            c->fpar = 1 - c->fpar;
+            CF_CUDA(cudaStreamWaitEvent(c->stream, b->gev[g], 0));
+            cf_status s = enqueue_post(c, nl);
+            if (s != CF_OK) return s;
+            CF_CUDA(cudaEventRecord(c->ev_batch, c->stream));
+            CF_CUDA(cudaStreamWaitEvent(b->stream, c->ev_batch, 0));
+        }
+    }
+    return CF_OK;
+}
+
+// one step of every context of the batch, enqueued on the batch stream; ev,
+// when given, receives four events on the batch stream: ev[0] step start,
+// ev[1] before and ev[2] after the lattice passes, ev[3] step end (the
+// lattice passes of all contexts then run as one launch per pass, whatever
+// the group setting)
+cf_status batch_enqueue_step(cf_batch *b, bool with_out, int *nl, cudaEvent_t *ev = nullptr) {
+    if (!ev && b->gbeg.size() > 2) return batch_enqueue_groups(b, with_out, nl);
+    if (ev) CF_CUDA(cudaEventRecord(ev[0], b->stream));
     CF_CUDA(cudaEventRecord(b->ev_fork, b->stream));
     for (cf_ctx *c : b->ctx) {
         CF_CUDA(cudaStreamWaitEvent(c->stream, b->ev_fork, 0));
@@ -1295,9 +1478,12 @@ cf_status batch_enqueue_step(cf_batch *b, bool with_out, int *nl) {
     for (size_t i = 0; i < b->ctx.size(); ++i) {
         tab.lat[i] = lb_params(b->ctx[i], with_out);
         tab.lat[i].zstride = b->zstride[i];
+        tab.lat[i].zchunk = b->zchunk;  // contiguous planes per work item
     }
+    if (ev) CF_CUDA(cudaEventRecord(ev[1], b->stream));
     CF_CUDA(launch_lb_batch(tab, (int)b->ctx.size(), b->work, b->nwork, b->prec, b->tile, b->stream));
     *nl += 2;
+    if (ev) CF_CUDA(cudaEventRecord(ev[2], b->stream));
     CF_CUDA(cudaEventRecord(b->ev_lat, b->stream));
     for (cf_ctx *c : b->ctx) {
         c->fpar = 1 - c->fpar;
@@ -1307,6 +1493,7 @@ cf_status batch_enqueue_step(cf_batch *b, bool with_out, int *nl) {
         CF_CUDA(cudaEventRecord(c->ev_batch, c->stream));
         CF_CUDA(cudaStreamWaitEvent(b->stream, c->ev_batch, 0));
     }
+    if (ev) CF_CUDA(cudaEventRecord(ev[3], b->stream));
     return CF_OK;
 }
 
@@ -1353,6 +1540,12 @@ cf_status batch_run(cf_batch *b, long long n) {
         if (c->dry_dm > 0.0) return fail(CF_ESTATE, "drying (cf_remove_mass) is not available in a batch");
     int nl = 0;
     long long left = n - 1;  // the last step records the fields
+    if (left >= 3 && b->graph && b->graph_key != batch_key(b)) {
+        // one plain step brings every context to the captured graph's parity
+        cf_status s = batch_enqueue_step(b, false, &nl);
+        if (s != CF_OK) return s;
+        --left;
+    }
     if (left >= 2) {
         cf_status s = batch_graph(b);
         if (s != CF_OK) return s;
@@ -1402,9 +1595,15 @@ cf_status cf_batch_create(cf_ctx *const *ctxs, int n, cf_batch **out) {
     cf_batch *b = new cf_batch();
     b->ctx.assign(ctxs, ctxs + n);
     b->prec = ctxs[0]->d.precision;
-    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->ev_lat, cudaEventDisableTiming) != cudaSuccess) {
+    b->gstream.assign(CF_MAX_GROUPS, nullptr);
+    b->gev.assign(CF_MAX_GROUPS, nullptr);
+    bool ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_lat, cudaEventDisableTiming) == cudaSuccess;
+    for (int g = 0; ok && g < CF_MAX_GROUPS; ++g)
+        ok = cudaStreamCreateWithFlags(&b->gstream[g], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->gev[g], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
         cf_batch_destroy(b);
         return fail(CF_ECUDA, "stream / event creation failed");
     }
@@ -1424,6 +1623,12 @@ cf_status cf_batch_destroy(cf_batch *b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->work) cudaFree(b->work);
+    for (int4 *w : b->gwork)
+        if (w) cudaFree(w);
+    for (cudaStream_t gs : b->gstream)
+        if (gs) cudaStreamDestroy(gs);
+    for (cudaEvent_t e : b->gev)
+        if (e) cudaEventDestroy(e);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->ev_lat) cudaEventDestroy(b->ev_lat);
     if (b->stream) cudaStreamDestroy(b->stream);
@@ -1439,7 +1644,14 @@ cf_status cf_batch_set_config(cf_batch *b, int tile, int zchunk) {
     return batch_build_work(b);
 }
 
-cf_status cf_batch_config(const cf_batch *b, int *tile, int *tile_x, int *tile_y, int *zchunk) {
+cf_status cf_batch_set_groups(cf_batch *b, int groups) {
+    if (!b || groups < 1 || groups > CF_MAX_GROUPS) return fail(CF_EINVAL, "bad argument");
+    CF_CUDA(cudaStreamSynchronize(b->stream));
+    b->groups = groups;
+    return batch_build_work(b);
+}
+
+cf_status cf_batch_config(const cf_batch *b, int *tile, int *tile_x, int *tile_y, int *zchunk, int *groups) {
     if (!b) return fail(CF_EINVAL, "null batch");
     int tx, ty;
     lb_batch_tile(b->tile, &tx, &ty);
@@ -1447,6 +1659,7 @@ cf_status cf_batch_config(const cf_batch *b, int *tile, int *tile_x, int *tile_y
     if (tile_x) *tile_x = tx;
     if (tile_y) *tile_y = ty;
     if (zchunk) *zchunk = b->zchunk;
+    if (groups) *groups = (int)b->gbeg.size() - 1;
     return CF_OK;
 }
 
@@ -1477,38 +1690,83 @@ cf_status cf_batch_time(cf_batch *b, long long n, double *ms) {
     return batch_sync(b);
 }
 
-cf_status cf_batch_autotune(cf_batch *b, int steps, int *tile_out, int *zchunk_out, double *ms_out) {
+cf_status cf_batch_time_phases(cf_batch *b, long long n, double ms[3]) {
+    if (!b || !ms || n <= 0) return fail(CF_EINVAL, "bad argument");
+    for (cf_ctx *c : b->ctx)
+        if (c->dry_dm > 0.0) return fail(CF_ESTATE, "drying (cf_remove_mass) is not available in a batch");
+    std::vector<cudaEvent_t> ev(4 * (size_t)n);
+    for (auto &e : ev) CF_CUDA(cudaEventCreate(&e));
+    int nl = 0;
+    cf_status st = CF_OK;
+    for (long long k = 0; k < n && st == CF_OK; ++k) st = batch_enqueue_step(b, k == n - 1, &nl, &ev[4 * k]);
+    CF_CUDA(cudaStreamSynchronize(b->stream));
+    ms[0] = ms[1] = ms[2] = 0.0;
+    for (long long k = 0; k < n && st == CF_OK; ++k) {
+        float t = 0.f;
+        CF_CUDA(cudaEventElapsedTime(&t, ev[4 * k + 1], ev[4 * k + 2]));
+        ms[0] += t / n;
+        CF_CUDA(cudaEventElapsedTime(&t, ev[4 * k], ev[4 * k + 1]));
+        ms[1] += t / n;
+        CF_CUDA(cudaEventElapsedTime(&t, ev[4 * k + 2], ev[4 * k + 3]));
+        ms[2] += t / n;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (st != CF_OK) return st;
+    for (cf_ctx *c : b->ctx) c->steps_done += n;
+    b->launches_last = nl;
+    return batch_sync(b);
+}
+
+cf_status cf_batch_autotune(cf_batch *b, int steps, int *tile_out, int *zchunk_out, int *groups_out,
+                            double *ms_out) {
     if (!b || steps < 2) return fail(CF_EINVAL, "bad argument");
-    const int zcs[3] = {1, 2, 4};
+    const int zcs[3] = {2, 4, 8};
+    const int gs[4] = {1, 2, 4, 8};
     const int pairs = (steps + 1) / 2;
     double best = 1e300;
-    int bt = b->tile, bz = b->zchunk;
+    int bt = b->tile, bz = b->zchunk, bg = b->groups;
     cudaEvent_t e0, e1;
     CF_CUDA(cudaEventCreate(&e0));
     CF_CUDA(cudaEventCreate(&e1));
+    // one configuration: capture and one untimed replay, then `pairs` timed replays
+    auto trial = [&](int t, int zc, int g, float *ms) -> cf_status {
+        b->groups = g;
+        cf_status st = cf_batch_set_config(b, t, zc);
+        if (st == CF_OK) st = batch_replay(b, 1);
+        if (st != CF_OK) return st;
+        CF_CUDA(cudaEventRecord(e0, b->stream));
+        st = batch_replay(b, pairs);
+        if (st != CF_OK) return st;
+        CF_CUDA(cudaEventRecord(e1, b->stream));
+        CF_CUDA(cudaEventSynchronize(e1));
+        CF_CUDA(cudaEventElapsedTime(ms, e0, e1));
+        return CF_OK;
+    };
     cf_status s = CF_OK;
+    // the launch shape of the lattice passes with one group, then the groups
     for (int t = 0; t < CF_NTILES && s == CF_OK; ++t)
         for (int zc : zcs) {
-            s = cf_batch_set_config(b, t, zc);
-            if (s == CF_OK) s = batch_replay(b, 1);  // capture and one untimed replay
-            if (s != CF_OK) break;
-            CF_CUDA(cudaEventRecord(e0, b->stream));
-            s = batch_replay(b, pairs);
-            if (s != CF_OK) break;
-            CF_CUDA(cudaEventRecord(e1, b->stream));
-            CF_CUDA(cudaEventSynchronize(e1));
             float ms = 0.f;
-            CF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) { best = ms; bt = t; bz = zc; }
+            s = trial(t, zc, 1, &ms);
+            if (s != CF_OK) break;
+            if (ms < best) { best = ms; bt = t; bz = zc; bg = 1; }
         }
+    for (int g : gs) {
+        if (s != CF_OK || g == 1 || g > (int)b->ctx.size()) continue;
+        float ms = 0.f;
+        s = trial(bt, bz, g, &ms);
+        if (s == CF_OK && ms < best) { best = ms; bg = g; }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (s == CF_OK) s = batch_sync(b);
     if (s != CF_OK) return s;
+    b->groups = bg;
     s = cf_batch_set_config(b, bt, bz);
     if (s != CF_OK) return s;
     if (tile_out) *tile_out = bt;
     if (zchunk_out) *zchunk_out = bz;
+    if (groups_out) *groups_out = (int)b->gbeg.size() - 1;
     if (ms_out) *ms_out = best / (2 * pairs);
     return CF_OK;
 }

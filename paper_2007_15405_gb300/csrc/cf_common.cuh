@@ -87,8 +87,10 @@ struct LBParams {
     int nx, ny, nz, wall;
     long long N;            // nodes
     int zlo, zhi;           // fluid planes [zlo, zhi)
-    int zchunk;             // planes walked per thread (grid.z = fluid planes / zchunk)
-    int zstride;            // batched passes: z slices of this lattice (a thread's plane stride)
+    int zchunk;             // density pass: planes walked per thread (grid.z = fluid planes /
+                            // zchunk, strided); batched passes: contiguous planes of a work item
+    int zring;              // tau = 1 collide pass: contiguous planes per block (its psi ring)
+    int zstride;            // batched passes: z slices of this lattice
     float itau[2], tau[2];  // 1/tau and tau per component
     float G;
     const void *__restrict__ src;    // post-collision populations of the last step
@@ -103,6 +105,7 @@ struct LBParams {
     const float *__restrict__ V;        // node velocities [3*nnodes]
     float *__restrict__ FT;             // element momentum exchange accumulators [3*nfaces]
     const float2 *__restrict__ rec;     // [N][18] bounced (A, B) populations by arriving direction - 1
+    const float *__restrict__ wet_el;   // [nfaces] wetting offset of each element's capsule (null: all 0)
     float *__restrict__ out;            // optional [5][N]: rhoA, rhoB, ux, uy, uz
     float2 *__restrict__ rho;           // [N] (rhoA, rhoB) of this step (written by the density pass)
     float2 *__restrict__ psi;           // [N] (psiA, psiB) of this step (written by the density pass)
@@ -118,7 +121,7 @@ struct LBParams {
     float *__restrict__ dry_eps;        // fraction of this step
 };
 
-enum StatusBits : unsigned { ST_OVERFLOW = 1u, ST_NAN = 2u, ST_TIMEOUT = 4u };
+enum StatusBits : unsigned { ST_OVERFLOW = 1u, ST_NAN = 2u };
 
 // Capsule description on the device.
 struct CapDev {
@@ -250,6 +253,10 @@ cudaError_t launch_inside(const uint32_t *mask, uint8_t *inside, int nx, int ny,
                           cudaStream_t s);
 cudaError_t launch_meniscus(const float *out, const uint8_t *inside, float *h, int nx, int ny,
                             int nz, int wall, cudaStream_t s);
+// meniscus profile of capsule id from the column heights (one block, FP64):
+// out[0..nr) = zeta at r_k = k dr, out[nr] = Z, out[nr+1] = h_inf
+cudaError_t launch_meniscus_profile(const float *h, int nx, int ny, const double *acc, const CapDev *caps,
+                                    int ncaps, int id, double dr, int nr, double *out, cudaStream_t s);
 cudaError_t launch_init_dens(void *f, float *f0, int prec, float2 *rho, long long N, int nx, int ny,
                              int wall, const double *rAB, cudaStream_t s);
 cudaError_t launch_mass(const void *f, const float *f0, int prec, const float2 *rho, long long N,

@@ -30,7 +30,9 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
-#include <mutex>
+#include <math_constants.h>
+#include <algorithm>
+#include <cstdint>
 
 namespace cf {
 
@@ -325,18 +327,25 @@ __global__ void __launch_bounds__(BX *BY, MOM ? CF_DENSITY_MOM_MINB : CF_DENSITY
 // Shan-Chen force on both components at a node (Eq. 10 with G^{AB} = G^{BA} = G,
 // G^{AA} = G^{BB} = 0), with the decoupling across cut and substrate links:
 // there the partner's pseudopotential comes from the mean density over this
-// node and its neighbours reached through uncut fluid links, and the reaction
-// goes to the crossed element.
+// node and its neighbours reached through uncut fluid links (on a membrane
+// link plus the capsule's wetting offset, +wet for A and -wet for B), and
+// the reaction goes to the crossed element.
 __device__ __forceinline__ void sc_force(const LBParams &p, const Deltas &d, uint32_t m, float ra, float rb,
                                          float pa, float pb, float (&FA)[3], float (&FB)[3]) {
     const int n = d.n;
-    float sa[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};  // sum_k w_k psi'(x+e_k) e_k
+    // sum_k w_k psi'(x+e_k) e_k, summed over opposite pairs (k, k+1) as
+    // w_k e_k (psi'(x+e_k) - psi'(x-e_k)): the difference of two nearby
+    // pseudopotentials is exact in float, so the rounding error of the sum
+    // scales with the (small) gradient instead of the pseudopotentials
+    float sa[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};
     if (!m && !d.wlo && !d.whi) {
 #pragma unroll
-        for (int k = 1; k < Q; ++k) {
-            const float2 q = __ldg(p.psi + n + nb_off(d, ex(k), ey(k), ez(k)));
-            sa[0] += wgt(k) * ex(k) * q.x; sa[1] += wgt(k) * ey(k) * q.x; sa[2] += wgt(k) * ez(k) * q.x;
-            sb[0] += wgt(k) * ex(k) * q.y; sb[1] += wgt(k) * ey(k) * q.y; sb[2] += wgt(k) * ez(k) * q.y;
+        for (int k = 1; k < Q; k += 2) {
+            const float2 q1 = __ldg(p.psi + n + nb_off(d, ex(k), ey(k), ez(k)));
+            const float2 q2 = __ldg(p.psi + n + nb_off(d, -ex(k), -ey(k), -ez(k)));
+            const float da = q1.x - q2.x, db = q1.y - q2.y;
+            sa[0] += wgt(k) * ex(k) * da; sa[1] += wgt(k) * ey(k) * da; sa[2] += wgt(k) * ez(k) * da;
+            sb[0] += wgt(k) * ex(k) * db; sb[1] += wgt(k) * ey(k) * db; sb[2] += wgt(k) * ez(k) * db;
         }
     } else {
         // partner densities across a cut or substrate link: mean over this
@@ -351,7 +360,9 @@ __device__ __forceinline__ void sc_force(const LBParams &p, const Deltas &d, uin
                 ia += q.x; ib += q.y; cnt += 1.f;
             }
         }
-        const float qa_eff = psi_of(ia / cnt), qb_eff = psi_of(ib / cnt);
+        const float ma = ia / cnt, mb = ib / cnt;
+        const float qa_eff = psi_of(ma), qb_eff = psi_of(mb);
+        float qA[Q], qB[Q];  // partner pseudopotentials per direction
 #pragma unroll
         for (int k = 1; k < Q; ++k) {
             const bool solid = (ez(k) == 1 && d.whi) || (ez(k) == -1 && d.wlo);
@@ -360,9 +371,15 @@ __device__ __forceinline__ void sc_force(const LBParams &p, const Deltas &d, uin
             if (solid || cut) {
                 qa = qa_eff; qb = qb_eff;
                 if (cut && !solid) {
-                    // reaction of the decoupled interaction on the crossed element
                     const int el = __ldg(p.tri + (long long)n * 18 + (k - 1));
-                    const float r = p.G * wgt(k) * (pa * qb_eff + pb * qa_eff);
+                    if (p.wet_el) {
+                        // wetting of the crossed element's capsule: offset of the
+                        // interpolated densities, +wet for A and -wet for B
+                        const float w = __ldg(p.wet_el + el);
+                        if (w != 0.f) { qa = psi_of(ma + w); qb = psi_of(mb - w); }
+                    }
+                    // reaction of the decoupled interaction on the crossed element
+                    const float r = p.G * wgt(k) * (pa * qb + pb * qa);
                     if (ex(k)) atomicAdd(p.FT + 3 * el + 0, ex(k) * r);
                     if (ey(k)) atomicAdd(p.FT + 3 * el + 1, ey(k) * r);
                     if (ez(k)) atomicAdd(p.FT + 3 * el + 2, ez(k) * r);
@@ -371,8 +388,13 @@ __device__ __forceinline__ void sc_force(const LBParams &p, const Deltas &d, uin
                 const float2 q = __ldg(p.psi + n + nb_off(d, ex(k), ey(k), ez(k)));
                 qa = q.x; qb = q.y;
             }
-            sa[0] += wgt(k) * ex(k) * qa; sa[1] += wgt(k) * ey(k) * qa; sa[2] += wgt(k) * ez(k) * qa;
-            sb[0] += wgt(k) * ex(k) * qb; sb[1] += wgt(k) * ey(k) * qb; sb[2] += wgt(k) * ez(k) * qb;
+            qA[k] = qa; qB[k] = qb;
+        }
+#pragma unroll
+        for (int k = 1; k < Q; k += 2) {
+            const float da = qA[k] - qA[k + 1], db = qB[k] - qB[k + 1];
+            sa[0] += wgt(k) * ex(k) * da; sa[1] += wgt(k) * ey(k) * da; sa[2] += wgt(k) * ez(k) * da;
+            sb[0] += wgt(k) * ex(k) * db; sb[1] += wgt(k) * ey(k) * db; sb[2] += wgt(k) * ez(k) * db;
         }
     }
 #pragma unroll
@@ -522,15 +544,9 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
 // stored the total momentum J = sum_c sum_i f_i^c e_i, so the populations are
 // not pulled a second time.  The common velocity is u' = J / (rho_A + rho_B)
 // and u^{c,eq} = u' + F^c / rho^c (the velocity shift with tau = 1).
-template <typename T, bool DRY = false>
-__device__ __forceinline__ void collide_eq_node(const LBParams &p, const Deltas &d) {
-    const int n = d.n;
-    const uint32_t m = __ldg(p.mask + n);
-    const float2 mr = __ldg(p.rho + n), mp = __ldg(p.psi + n);
-    const float ra = mr.x, rb = mr.y, pa = mp.x, pb = mp.y;
-    float FA[3], FB[3];
-    sc_force(p, d, m, ra, rb, pa, pb, FA, FB);
-    const float4 J4 = __ldg(p.J + n);
+template <typename T, bool DRY>
+__device__ __forceinline__ void collide_eq_finish(const LBParams &p, int n, float ra, float rb, const float4 J4,
+                                                  const float (&FA)[3], const float (&FB)[3]) {
     const float J[3] = {J4.x, J4.y, J4.z};
     const float rt = ra + rb, iden = 1.0f / rt, ia = 1.0f / ra, ib = 1.0f / rb;
     float ua[3], ub[3];
@@ -553,6 +569,107 @@ __device__ __forceinline__ void collide_eq_node(const LBParams &p, const Deltas 
 }
 
 template <typename T, bool DRY = false>
+__device__ __forceinline__ void collide_eq_node(const LBParams &p, const Deltas &d) {
+    const int n = d.n;
+    const uint32_t m = __ldg(p.mask + n);
+    const float2 mr = __ldg(p.rho + n), mp = __ldg(p.psi + n);
+    float FA[3], FB[3];
+    sc_force(p, d, m, mr.x, mr.y, mp.x, mp.y, FA, FB);
+    collide_eq_finish<T, DRY>(p, n, mr.x, mr.y, __ldg(p.J + n), FA, FB);
+}
+
+// ---------------------------------------------------------------------------
+// tau = 1 collide pass with the pseudopotentials staged in shared memory.
+// A block owns a TX x TY column tile and walks a contiguous run of planes; a
+// ring of four planes of psi (the tile plus a one-node halo, periodic wrap)
+// holds the planes z-1, z, z+1 the Shan-Chen stencil of plane z reads, while
+// cp.async fills the fourth with plane z+2.  The 18 neighbour pseudopotentials
+// of a node then come from shared memory at fixed offsets instead of 18 global
+// gathers.  Nodes next to a cut or substrate link take the general stencil
+// (sc_force, global loads), which also forms the partner densities.
+template <int TX, int TY> struct PsiRing {
+    float2 v[4][TY + 2][TX + 2];
+};
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// plane z (any integer; the data wraps periodically) of the tile at (x0, y0)
+// into ring slot z & 3
+template <int TX, int TY>
+__device__ __forceinline__ void ring_load(const LBParams &p, PsiRing<TX, TY> &R, int z, int x0, int y0) {
+    const int nx = p.nx, ny = p.ny;
+    const int gz = ((unsigned)z < (unsigned)p.nz) ? z : wrapi(z, p.nz);
+    const float2 *plane = p.psi + (long long)gz * nx * ny;
+    float2(*dst)[TX + 2] = R.v[z & 3];
+    for (int e = threadIdx.y * TX + threadIdx.x; e < (TY + 2) * (TX + 2); e += TX * TY) {
+        const int ly = e / (TX + 2), lx = e - ly * (TX + 2);
+        int gx = x0 + lx - 1, gy = y0 + ly - 1;
+        if ((unsigned)gx >= (unsigned)nx) gx = wrapi(gx, nx);
+        if ((unsigned)gy >= (unsigned)ny) gy = wrapi(gy, ny);
+        cp_async8(&dst[ly][lx], plane + (long long)gy * nx + gx);
+    }
+}
+
+template <typename T, bool DRY, int TX, int TY>
+__device__ __forceinline__ void collide_eq_node_ring(const LBParams &p, const Deltas &d,
+                                                     const PsiRing<TX, TY> &R, int z) {
+    const int n = d.n;
+    const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
+    const uint32_t m = __ldg(p.mask + n);
+    const float2 mr = __ldg(p.rho + n), mp = R.v[z & 3][ty][tx];
+    const float ra = mr.x, rb = mr.y, pa = mp.x, pb = mp.y;
+    float FA[3], FB[3];
+    if (!m && !d.wlo && !d.whi) {
+        // the stencil of sc_force over opposite pairs, neighbours from the ring
+        float sa[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 1; k < Q; k += 2) {
+            const float2 q1 = R.v[(z + ez(k)) & 3][ty + ey(k)][tx + ex(k)];
+            const float2 q2 = R.v[(z - ez(k)) & 3][ty - ey(k)][tx - ex(k)];
+            const float da = q1.x - q2.x, db = q1.y - q2.y;
+            sa[0] += wgt(k) * ex(k) * da; sa[1] += wgt(k) * ey(k) * da; sa[2] += wgt(k) * ez(k) * da;
+            sb[0] += wgt(k) * ex(k) * db; sb[1] += wgt(k) * ey(k) * db; sb[2] += wgt(k) * ez(k) * db;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            FA[a] = -p.G * pa * sb[a];
+            FB[a] = -p.G * pb * sa[a];
+        }
+    } else {
+        sc_force(p, d, m, ra, rb, pa, pb, FA, FB);
+    }
+    collide_eq_finish<T, DRY>(p, n, ra, rb, __ldg(p.J + n), FA, FB);
+}
+
+// planes [zb, ze) of the tile at (x0, y0); every thread of the block calls it
+// with the same arguments (the ring loads and barriers are block-wide)
+template <typename T, bool DRY, int TX, int TY>
+__device__ __forceinline__ void collide_eq_ring(const LBParams &p, PsiRing<TX, TY> &R, int x0, int y0, int zb,
+                                                int ze) {
+    if (zb >= ze) return;
+    const int x = x0 + (int)threadIdx.x, y = y0 + (int)threadIdx.y;
+    const bool in = x < p.nx && y < p.ny;
+    ring_load<TX, TY>(p, R, zb - 1, x0, y0);
+    ring_load<TX, TY>(p, R, zb, x0, y0);
+    ring_load<TX, TY>(p, R, zb + 1, x0, y0);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    for (int z = zb; z < ze; ++z) {
+        if (z + 1 < ze) ring_load<TX, TY>(p, R, z + 2, x0, y0);  // for the next plane
+        cp_async_commit();
+        if (in) collide_eq_node_ring<T, DRY, TX, TY>(p, deltas(p, x, y, z), R, z);
+        cp_async_wait_all();
+        __syncthreads();
+    }
+}
+
+template <typename T, bool DRY = false>
 __global__ void __launch_bounds__(BX *BY, Pop<T>::shifted ? CF_COLLIDE16_MINB : CF_COLLIDE_MINB)
     k_collide(const LBParams p) {
     pdl_trigger();
@@ -567,13 +684,30 @@ __global__ void __launch_bounds__(BX *BY, Pop<T>::shifted ? CF_COLLIDE16_MINB : 
 #define CF_COLLIDE_EQ_MINB 8
 #endif
 
+// Blocks in reverse order (the tiles the density pass read last first).
+// With CF_PSI_RING set, each block walks zring contiguous planes through its
+// pseudopotential ring; by default the neighbour pseudopotentials are global
+// gathers (L1/L2 hits) and threads walk planes strided by grid.z like the
+// density pass (measured faster on the GB300: the ring's loads and barriers
+// cost more than the gathers they replace).
+#ifndef CF_PSI_RING
+#define CF_PSI_RING 0
+#endif
 template <typename T, bool DRY = false>
 __global__ void __launch_bounds__(BX *BY, CF_COLLIDE_EQ_MINB) k_collide_eq(const LBParams p) {
     pdl_trigger();
     pdl_wait();
+#if CF_PSI_RING
+    __shared__ PsiRing<BX, BY> R;
+    const int bx = (int)(gridDim.x - 1 - blockIdx.x), by = (int)(gridDim.y - 1 - blockIdx.y);
+    const int bz = (int)(gridDim.z - 1 - blockIdx.z);
+    const int zb = p.zlo + bz * p.zring, ze = min(p.zhi, zb + p.zring);
+    collide_eq_ring<T, DRY, BX, BY>(p, R, bx * BX, by * BY, zb, ze);
+#else
     int x, y, z;
     if (!node_of<true>(p, x, y, z)) return;
     for (; z < p.zhi; z += gridDim.z) collide_eq_node<T, DRY>(p, deltas(p, x, y, z));
+#endif
 }
 
 size_t density_blocks_max(int nx, int ny, int nz) {
@@ -585,7 +719,13 @@ template <typename T, bool DRY>
 void lb_passes(const LBParams &p, dim3 grid, dim3 block, cudaStream_t s, bool eq) {
     if (eq) {
         launch_pdl(k_density<T, DRY, true>, grid, block, s, p);
+#if CF_PSI_RING
+        const int zr = std::max(1, p.zring);
+        const dim3 gc(grid.x, grid.y, (unsigned)((p.zhi - p.zlo + zr - 1) / zr));
+        launch_pdl(k_collide_eq<T, DRY>, gc, block, s, p);
+#else
         launch_pdl(k_collide_eq<T, DRY>, grid, block, s, p);
+#endif
     } else {
         launch_pdl(k_density<T, DRY>, grid, block, s, p);
         launch_pdl(k_collide<T, DRY>, grid, block, s, p);
@@ -622,6 +762,8 @@ cudaError_t launch_lb_step(const LBParams &p, int prec, cudaStream_t s) {
 // compiled in and chosen by the autotuner of the batch.  EQ: every lattice has
 // tau = 1, and the passes are those of the tau = 1 collision (momentum from
 // the density pass, no second pull).
+// work item (lattice, x tile, y tile, z slice): slice s covers the planes
+// [zlo + s zchunk, zlo + (s + 1) zchunk) of its lattice
 template <typename T, int TX, int TY, bool EQ>
 __global__ void __launch_bounds__(TX *TY) k_density_batch(const __grid_constant__ BatchTab tab,
                                                           const int4 *__restrict__ work, int nwork) {
@@ -633,21 +775,34 @@ __global__ void __launch_bounds__(TX *TY) k_density_batch(const __grid_constant_
             atomicAdd(p.step_ctr, 1u);  // read by the collide pass that follows
         const int x = it.y * TX + (int)threadIdx.x, y = it.z * TY + (int)threadIdx.y;
         if (x >= p.nx || y >= p.ny) continue;
-        for (int z = p.zlo + it.w; z < p.zhi; z += p.zstride) density_node<T, EQ>(p, deltas(p, x, y, z));
+        const int zb = p.zlo + it.w * p.zchunk, ze = min(p.zhi, zb + p.zchunk);
+        for (int z = zb; z < ze; ++z) density_node<T, EQ>(p, deltas(p, x, y, z));
     }
 }
 
+// the collide pass walks the work list backwards; with EQ (tau = 1) through
+// the pseudopotential ring (block-wide: every thread takes part in each item)
+#ifndef CF_COLLIDE_BATCH_EQ_MINB  // resident blocks per SM of the tau = 1 batched collide (128 threads)
+#define CF_COLLIDE_BATCH_EQ_MINB 8
+#endif
 template <typename T, int TX, int TY, bool EQ>
-__global__ void __launch_bounds__(TX *TY, (TX * TY >= 256 ? 2 : (EQ ? 8 : 5))) k_collide_batch(
+__global__ void __launch_bounds__(TX *TY, (TX * TY >= 256 ? 2 : (EQ ? CF_COLLIDE_BATCH_EQ_MINB : 5))) k_collide_batch(
     const __grid_constant__ BatchTab tab, const int4 *__restrict__ work, int nwork) {
+    __shared__ PsiRing<TX, (EQ && CF_PSI_RING != 0) ? TY : 1> R;
     for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
         const int4 it = __ldg(work + (nwork - 1 - w));
         const LBParams &p = tab.lat[it.x];
-        const int x = it.y * TX + (int)threadIdx.x, y = it.z * TY + (int)threadIdx.y;
-        if (x >= p.nx || y >= p.ny) continue;
-        for (int z = p.zlo + it.w; z < p.zhi; z += p.zstride) {
-            if (EQ) collide_eq_node<T>(p, deltas(p, x, y, z));
-            else collide_node<T>(p, deltas(p, x, y, z));
+        const int zb = p.zlo + it.w * p.zchunk, ze = min(p.zhi, zb + p.zchunk);
+        if constexpr (EQ && CF_PSI_RING != 0) {
+            collide_eq_ring<T, false, TX, TY>(p, R, it.y * TX, it.z * TY, zb, ze);
+        } else if constexpr (EQ) {
+            const int x = it.y * TX + (int)threadIdx.x, y = it.z * TY + (int)threadIdx.y;
+            if (x >= p.nx || y >= p.ny) continue;
+            for (int z = zb; z < ze; ++z) collide_eq_node<T>(p, deltas(p, x, y, z));
+        } else {
+            const int x = it.y * TX + (int)threadIdx.x, y = it.z * TY + (int)threadIdx.y;
+            if (x >= p.nx || y >= p.ny) continue;
+            for (int z = zb; z < ze; ++z) collide_node<T>(p, deltas(p, x, y, z));
         }
     }
 }
@@ -871,6 +1026,109 @@ cudaError_t launch_meniscus(const float *out, const uint8_t *inside, float *h, i
     return cudaGetLastError();
 }
 
+// Meniscus profile of capsule `id` (Sec. 4.1) from the column heights h
+// [ny][nx] (NaN where no valid interface): one block, FP64.
+//  - centroids: the FP64 node sums of the last step (per-capsule accumulators)
+//  - h_inf: mean of the valid columns whose periodic distance to the nearest
+//    capsule centroid is at least 0.9 of the largest such distance
+//  - rays from the column nearest to the centroid along +x, -x, +y, -y,
+//    sampled at r_k = k dr with linear interpolation between the bracketing
+//    columns (invalid where either is NaN); zeta_k = ray mean - h_inf
+//  - out[0..nr) = zeta, out[nr] = Z (largest valid zeta), out[nr+1] = h_inf
+constexpr int PROF_THREADS = 256;
+
+__device__ __forceinline__ double block_sum(double v, double *red) {
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = PROF_THREADS / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+__device__ __forceinline__ double block_max(double v, double *red) {
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = PROF_THREADS / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(PROF_THREADS) k_meniscus_profile(
+    const float *__restrict__ h, int nx, int ny, const double *__restrict__ acc, const CapDev *__restrict__ caps,
+    int ncaps, int id, double dr, int nr, double *__restrict__ out) {
+    __shared__ double red[PROF_THREADS];
+    auto centre = [&](int k, double &cx, double &cy) {
+        const double *a = acc + (size_t)k * A_NACC;
+        const double nv = (double)caps[k].nv;
+        cx = a[A_OX] + a[A_CX] / nv;
+        cy = a[A_OY] + a[A_CY] / nv;
+    };
+    auto nearest = [&](int x, int y) {
+        double best = CUDART_INF;
+        for (int k = 0; k < ncaps; ++k) {
+            double cx, cy;
+            centre(k, cx, cy);
+            double dx = x - cx, dy = y - cy;
+            dx -= nx * floor(dx / nx + 0.5);
+            dy -= ny * floor(dy / ny + 0.5);
+            best = fmin(best, sqrt(dx * dx + dy * dy));
+        }
+        return best;
+    };
+    const int ncol = nx * ny;
+    double m = 0.0;
+    for (int c = threadIdx.x; c < ncol; c += PROF_THREADS)
+        if (!isnan(h[c])) m = fmax(m, nearest(c % nx, c / nx));
+    const double dmax = block_max(m, red);
+    double hs = 0.0, hc = 0.0;
+    for (int c = threadIdx.x; c < ncol; c += PROF_THREADS) {
+        const float v = h[c];
+        if (!isnan(v) && nearest(c % nx, c / nx) >= 0.9 * dmax) { hs += v; hc += 1.0; }
+    }
+    const double S = block_sum(hs, red), Cn = block_sum(hc, red);
+    const double hinf = Cn > 0.0 ? S / Cn : CUDART_NAN;
+    double cx, cy;
+    centre(id, cx, cy);
+    const int x0 = (int)lround(cx), y0 = (int)lround(cy);
+    for (int k = threadIdx.x; k < nr; k += PROF_THREADS) {
+        const double rk = k * dr;
+        const int j0 = (int)floor(rk);
+        const double t = rk - j0;
+        double s = 0.0;
+        int cnt = 0;
+        for (int q = 0; q < 4; ++q) {
+            const int sx = q == 0 ? 1 : q == 1 ? -1 : 0, sy = q == 2 ? 1 : q == 3 ? -1 : 0;
+            const int xa = wrapi(x0 + sx * j0, nx), ya = wrapi(y0 + sy * j0, ny);
+            const int xb = wrapi(x0 + sx * (j0 + 1), nx), yb = wrapi(y0 + sy * (j0 + 1), ny);
+            const double ha = h[ya * nx + xa], hb = h[yb * nx + xb];
+            const double v = t == 0.0 ? ha : (1.0 - t) * ha + t * hb;
+            if (!isnan(v)) { s += v; ++cnt; }
+        }
+        out[k] = cnt ? s / cnt - hinf : CUDART_NAN;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double Z = CUDART_NAN;
+        for (int k = 0; k < nr; ++k)
+            if (!isnan(out[k]) && (isnan(Z) || out[k] > Z)) Z = out[k];
+        out[nr] = Z;
+        out[nr + 1] = hinf;
+    }
+}
+
+cudaError_t launch_meniscus_profile(const float *h, int nx, int ny, const double *acc, const CapDev *caps,
+                                    int ncaps, int id, double dr, int nr, double *out, cudaStream_t s) {
+    k_meniscus_profile<<<1, PROF_THREADS, 0, s>>>(h, nx, ny, acc, caps, ncaps, id, dr, nr, out);
+    return cudaGetLastError();
+}
+
 // FP64 mass of each component (decoded populations)
 template <typename T>
 __global__ void k_mass(const T *f, const float *f0, const float2 *rho, long long N, double *m2) {
@@ -964,13 +1222,15 @@ __device__ __forceinline__ void collide_node_static(const LBParams &p, const Del
     }
     const float4 me = p.sdens[n];
     const float ra = me.x, rb = me.y, pa = me.z, pb = me.w;
-    float sa[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};
+    float sa[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};  // summed over opposite pairs
     if (!d.wlo && !d.whi) {
 #pragma unroll
-        for (int k = 1; k < Q; ++k) {
-            const float4 q = p.sdens[n + nb_off(d, ex(k), ey(k), ez(k))];
-            sa[0] += wgt(k) * ex(k) * q.z; sa[1] += wgt(k) * ey(k) * q.z; sa[2] += wgt(k) * ez(k) * q.z;
-            sb[0] += wgt(k) * ex(k) * q.w; sb[1] += wgt(k) * ey(k) * q.w; sb[2] += wgt(k) * ez(k) * q.w;
+        for (int k = 1; k < Q; k += 2) {
+            const float4 q1 = p.sdens[n + nb_off(d, ex(k), ey(k), ez(k))];
+            const float4 q2 = p.sdens[n + nb_off(d, -ex(k), -ey(k), -ez(k))];
+            const float da = q1.z - q2.z, db = q1.w - q2.w;
+            sa[0] += wgt(k) * ex(k) * da; sa[1] += wgt(k) * ey(k) * da; sa[2] += wgt(k) * ez(k) * da;
+            sb[0] += wgt(k) * ex(k) * db; sb[1] += wgt(k) * ey(k) * db; sb[2] += wgt(k) * ez(k) * db;
         }
     } else {
         float ia = ra, ib = rb, cnt = 1.f;
@@ -983,17 +1243,21 @@ __device__ __forceinline__ void collide_node_static(const LBParams &p, const Del
             }
         }
         const float qa_eff = psi_of(ia / cnt), qb_eff = psi_of(ib / cnt);
+        float qA[Q], qB[Q];
 #pragma unroll
         for (int k = 1; k < Q; ++k) {
             const bool solid = (ez(k) == 1 && d.whi) || (ez(k) == -1 && d.wlo);
-            float qa, qb;
-            if (solid) { qa = qa_eff; qb = qb_eff; }
+            if (solid) { qA[k] = qa_eff; qB[k] = qb_eff; }
             else {
                 const float4 q = p.sdens[n + nb_off(d, ex(k), ey(k), ez(k))];
-                qa = q.z; qb = q.w;
+                qA[k] = q.z; qB[k] = q.w;
             }
-            sa[0] += wgt(k) * ex(k) * qa; sa[1] += wgt(k) * ey(k) * qa; sa[2] += wgt(k) * ez(k) * qa;
-            sb[0] += wgt(k) * ex(k) * qb; sb[1] += wgt(k) * ey(k) * qb; sb[2] += wgt(k) * ez(k) * qb;
+        }
+#pragma unroll
+        for (int k = 1; k < Q; k += 2) {
+            const float da = qA[k] - qA[k + 1], db = qB[k] - qB[k + 1];
+            sa[0] += wgt(k) * ex(k) * da; sa[1] += wgt(k) * ey(k) * da; sa[2] += wgt(k) * ez(k) * da;
+            sb[0] += wgt(k) * ex(k) * db; sb[1] += wgt(k) * ey(k) * db; sb[2] += wgt(k) * ez(k) * db;
         }
     }
     const float FA[3] = {-p.G * pa * sb[0], -p.G * pa * sb[1], -p.G * pa * sb[2]};
@@ -1044,22 +1308,14 @@ __global__ void __launch_bounds__(BX *BY) k_collide_static(const LBParams p) {
     for (; z < p.zhi; z += gridDim.z) collide_node_static(p, deltas(p, x, y, z));
 }
 
-// Device address of the static scratch, looked up once per device with that
-// device current (the array's name is only a host-side stand-in).
-static float4 *static_dens_address(int dev, cudaError_t *err) {
-    constexpr int MAXDEV = 64;
-    static float4 *addr[MAXDEV] = {};
-    static std::mutex mu;
-    *err = cudaSuccess;
-    if (dev < 0 || dev >= MAXDEV) { *err = cudaErrorInvalidDevice; return nullptr; }
-    std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        void *ptr = nullptr;
-        *err = cudaGetSymbolAddress(&ptr, g_static_dens);
-        if (*err != cudaSuccess) return nullptr;
-        addr[dev] = static_cast<float4 *>(ptr);
-    }
-    return addr[dev];
+// Device address of the static scratch in the current context (the array's
+// name is only a host-side stand-in).  Looked up on every call: the lookup is
+// a cheap host call, and a cached address could belong to a context that has
+// since been destroyed (cudaDeviceReset) or to another context on the device.
+static float4 *static_dens_address(cudaError_t *err) {
+    void *ptr = nullptr;
+    *err = cudaGetSymbolAddress(&ptr, g_static_dens);
+    return *err == cudaSuccess ? static_cast<float4 *>(ptr) : nullptr;
 }
 
 }  // namespace cf
@@ -1076,9 +1332,16 @@ extern "C" cf_status cf_lattice_step_static(const float *src, float *dst, int nx
         return CF_EINVAL;
     }
     if (!(tau[0] > 0.5) || !(tau[1] > 0.5)) { set_last_error("tau must exceed 1/2"); return CF_EINVAL; }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    float4 *dens = e == cudaSuccess ? static_dens_address(dev, &e) : nullptr;
+    {   // the collide pass reads src around every node while it writes dst
+        const uintptr_t a0 = (uintptr_t)src, b0 = (uintptr_t)dst;
+        const uintptr_t bytes = (uintptr_t)(2 * Q * N) * sizeof(float);
+        if (a0 < b0 + bytes && b0 < a0 + bytes) {
+            set_last_error("cf_lattice_step_static: src and dst overlap");
+            return CF_EINVAL;
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    float4 *dens = static_dens_address(&e);
     if (!dens) {
         set_last_error(cudaGetErrorString(e));
         return CF_ECUDA;
@@ -1095,7 +1358,9 @@ extern "C" cf_status cf_lattice_step_static(const float *src, float *dst, int nx
     p.dst = dst;
     p.sdens = dens;
     const cudaStream_t s = (cudaStream_t)stream;
-    dim3 grid((nx + BX - 1) / BX, (ny + BY - 1) / BY, p.zhi - p.zlo), block(BX, BY);
+    // both kernels stride over the planes by gridDim.z, so grid.z stays
+    // within the 65535 launch limit for any accepted lattice
+    dim3 grid((nx + BX - 1) / BX, (ny + BY - 1) / BY, std::min(p.zhi - p.zlo, 65535)), block(BX, BY);
     k_density_static<<<grid, block, 0, s>>>(p);
     k_collide_static<<<grid, block, 0, s>>>(p);
     e = cudaGetLastError();
