@@ -64,6 +64,15 @@ def lib():
         L.or_rho_interp.restype = C.c_double
         L.or_rho_interp.argtypes = [C.c_void_p, _dp, C.c_int, C.c_int, C.c_int]
         L.or_set_cuts.argtypes = [C.c_void_p, _up, _ip]
+        L.or_set_capsule_wetting.argtypes = [C.c_void_p, C.c_int, C.c_double]
+        L.or_bessel_k.restype = C.c_double
+        L.or_bessel_k.argtypes = [C.c_int, C.c_double]
+        L.or_meniscus_fit.restype = C.c_int
+        L.or_meniscus_fit.argtypes = [_dp, _dp, C.c_int, C.c_double, C.c_double, _dp, _dp, _dp]
+        L.or_capillary_force.restype = C.c_double
+        L.or_capillary_force.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]
+        L.or_override_cuts.restype = C.c_long
+        L.or_override_cuts.argtypes = [C.c_void_p, _up, _ip, C.c_double]
         L.or_capsule_forces.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
         L.or_meniscus_profile_of.restype = C.c_double
         L.or_meniscus_profile_of.argtypes = [_dp, C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_int,
@@ -146,6 +155,27 @@ def lateral_force_of(Fa, Fb, ca, cb, nx, ny):
     return lib().or_lateral_force_of(_ptr(a[0]), _ptr(a[1]), _ptr(a[2]), _ptr(a[3]), int(nx), int(ny))
 
 
+def bessel_k(nu, x):
+    """K_nu(x) from its integral representation (nu = 0, 1, ...)."""
+    return lib().or_bessel_k(int(nu), float(x))
+
+
+def meniscus_fit(r, zeta, rmin=0.0, rmax=np.inf):
+    """(Q, q, rms, samples) of the least-squares fit zeta = Q K_0(q r) over
+    rmin <= r <= rmax (finite samples only)."""
+    r = np.ascontiguousarray(r, np.float64)
+    z = np.ascontiguousarray(zeta, np.float64)
+    Q, q, rms = np.zeros(1), np.zeros(1), np.zeros(1)
+    m = lib().or_meniscus_fit(_ptr(r), _ptr(z), len(r), float(rmin), float(min(rmax, 1e300)),
+                              _ptr(Q), _ptr(q), _ptr(rms))
+    return float(Q[0]), float(q[0]), float(rms[0]), m
+
+
+def capillary_force(q, gamma, Q1, Q2, L):
+    """-2 pi q gamma Q1 Q2 K_1(q L) (Eq. 13)."""
+    return lib().or_capillary_force(float(q), float(gamma), float(Q1), float(Q2), float(L))
+
+
 class Oracle:
     """One lattice with its capsules, stepped by the FP64 oracle."""
 
@@ -171,7 +201,8 @@ class Oracle:
         o = cls(wl.nx, wl.ny, wl.nz, wall=wl.wall, tau=wl.tau, G=wl.G, rep_dz=wl.rep_dz)
         for cap in wl.capsules:
             X, F = cap.mesh()
-            o.add_capsule(X, F, cap.kS, cap.C, cap.kB, cap.kV, cap.mass, cap.mode)
+            o.add_capsule(X, F, cap.kS, cap.C, cap.kB, cap.kV, cap.mass, cap.mode,
+                          wet=getattr(cap, "wet", 0.0))
         if set_film:
             from paper_2007_15405_gb300.inputs import RHO_MAJ, RHO_MIN, RHO_MIX
             o.set_film(wl.h_top, RHO_MAJ, RHO_MIN, RHO_MIX, wl.jitter())
@@ -179,11 +210,13 @@ class Oracle:
             o.remove_mass(wl.dry_dm)
         return o
 
-    def add_capsule(self, X, F, kS, C, kB, kV, mass, mode):
+    def add_capsule(self, X, F, kS, C, kB, kV, mass, mode, wet=0.0):
         X = np.ascontiguousarray(X, np.float64)
         F = np.ascontiguousarray(F, np.int32)
         cid = lib().or_add_capsule(self._h, X.shape[0], _ptr(X), F.shape[0], _ptr(F, _ip), kS, C,
                                    kB, kV, mass, mode)
+        if wet:
+            lib().or_set_capsule_wetting(self._h, cid, float(wet))
         self.nv.append(X.shape[0])
         return cid
 
@@ -272,6 +305,15 @@ class Oracle:
         m = np.ascontiguousarray(mask, np.uint32)
         t = np.ascontiguousarray(tri, np.int32)
         lib().or_set_cuts(self._h, _ptr(m, _up), _ptr(t, _ip))
+
+    def override_cuts(self, mask, tri, margin=1e-4):
+        """Adopt a cut structure computed elsewhere where every difference is a
+        near tie of the oracle's decision (returns the number of differing link
+        ends), else keep the oracle's (returns minus the number of differences
+        that are not near ties)."""
+        m = np.ascontiguousarray(mask, np.uint32)
+        t = np.ascontiguousarray(tri, np.int32)
+        return lib().or_override_cuts(self._h, _ptr(m, _up), _ptr(t, _ip), float(margin))
 
     def capsule_forces(self, cid):
         """(elastic, interaction) node forces [nv, 3] of the last step."""

@@ -79,6 +79,7 @@ typedef struct {
     double force[3];            /* sum of coupling forces (last step)     */
     double torque[3];
     double area, volume;
+    double wet;                 /* wetting offset of the interpolated densities */
     int tri_base;               /* global index of face 0                 */
 } or_capsule;
 
@@ -667,7 +668,7 @@ static void collide(or_ctx *c, double *Fsc_out) {
                 if (is_solid(c, z)) continue;
                 long n = nidx(c, x, y, z);
                 double Fc[2][3] = {{0, 0, 0}, {0, 0, 0}};
-                double psi_eff_far[2] = {-1.0, -1.0};
+                double rho_far[2] = {-1.0, -1.0};
                 for (int cc = 0; cc < 2; ++cc) {
                     int cb = 1 - cc;
                     double G = c->G;  /* G^{AB} = G^{BA} = G, G^{cc} = 0 */
@@ -677,9 +678,16 @@ static void collide(or_ctx *c, double *Fsc_out) {
                         int cutk = c->mask[n] & (1u << (k - 1));
                         double pf;
                         if (wallk || cutk) {
-                            if (psi_eff_far[cb] < 0.0)
-                                psi_eff_far[cb] = psi_of(rho_interp(c, &rho[cb * N], x, y, z, n));
-                            pf = psi_eff_far[cb];
+                            if (rho_far[cb] < 0.0) rho_far[cb] = rho_interp(c, &rho[cb * N], x, y, z, n);
+                            double r = rho_far[cb];
+                            if (cutk && !wallk) {
+                                /* wetting: the crossed element's capsule offsets the
+                                 * interpolated densities, +wet for A and -wet for B */
+                                int f;
+                                const or_capsule *q = capsule_of(c, c->tri[18 * n + k - 1], &f);
+                                r += cb == 0 ? q->wet : -q->wet;
+                            }
+                            pf = psi_of(r);
                             if (cutk && !wallk)  /* reaction on the crossed element */
                                 c->slink[18 * n + k - 1] += psi[cc * N + n] * G * WV[k] * pf;
                         } else {
@@ -1024,6 +1032,14 @@ double or_rho_interp(const or_ctx *c, const double *rho, int x, int y, int z) {
     return rho_interp(c, rho, x, y, z, nidx(c, x, y, z));
 }
 
+/* Wetting of capsule id (Sec. 3.1, last paragraph: an offset added to the
+ * interpolated densities tunes the contact angle; 0 is the neutral wetting
+ * the paper uses).  Reading: on every link the capsule's membrane cuts, the
+ * partner density interpolated for the Shan-Chen force is rho_interp + wet
+ * for component A and rho_interp - wet for component B (the reaction on the
+ * element uses the same values); substrate links stay neutral. */
+void or_set_capsule_wetting(or_ctx *c, int id, double wet) { c->caps[id].wet = wet; }
+
 /* Replace the context's cut structure (mask [N], elements [N*18]) and
  * recompute the interior flags from it. */
 void or_set_cuts(or_ctx *c, const uint32_t *mask, const int *tri) {
@@ -1148,4 +1164,179 @@ double or_lateral_force(const or_ctx *c, int a, int b) {
     centroids_xy(c, cx, cy);
     double ca[2] = {cx[a], cy[a]}, cb[2] = {cx[b], cy[b]};
     return or_lateral_force_of(c->caps[a].force, c->caps[b].force, ca, cb, c->nx, c->ny);
+}
+
+/* ------------------------------------------------- cut-structure override */
+/* A crossing decision of link P->Q against element (A, B, C) is a near tie
+ * when some perturbation of the inputs by at most `margin` lattice units can
+ * flip it: each of the five orientation tests of seg_tri (the link ends
+ * against the element plane, the link line against the three edges) is
+ * classed +, - or undecided (|normalised value| < margin), and the decision
+ * is ambiguous when an assignment of the undecided tests makes it a
+ * crossing and another makes it none.  Plane tests are normalised to
+ * distances by |n|, edge tests by |edge| |Q - P|. */
+static int near_tie(const double *P, const double *Q, const double *A, const double *B,
+                    const double *C, double margin) {
+    double u[3], w[3], n[3], pq[3];
+    sub3(B, A, u); sub3(C, A, w); cross3(u, w, n);
+    sub3(Q, P, pq);
+    double nn = norm3(n), lpq = norm3(pq);
+    if (!(nn > 0.0)) return 1;
+    double e1[3], e2[3], e3[3];
+    sub3(B, A, e1); sub3(C, B, e2); sub3(A, C, e3);
+    double v[5] = {orient3(A, B, C, P) / nn, orient3(A, B, C, Q) / nn,
+                   orient3(P, Q, A, B) / (norm3(e1) * lpq), orient3(P, Q, B, C) / (norm3(e2) * lpq),
+                   orient3(P, Q, C, A) / (norm3(e3) * lpq)};
+    int cls[5];
+    for (int k = 0; k < 5; ++k) cls[k] = fabs(v[k]) < margin ? 0 : (v[k] > 0.0 ? 1 : -1);
+    /* can the two ends lie on different sides / on the same side? */
+    int can_differ = cls[0] == 0 || cls[1] == 0 || cls[0] != cls[1];
+    int can_same = cls[0] == 0 || cls[1] == 0 || cls[0] == cls[1];
+    /* can the three edge tests agree / disagree? */
+    int has_p = 0, has_m = 0, n_u = 0;
+    for (int k = 2; k < 5; ++k) { has_p |= cls[k] == 1; has_m |= cls[k] == -1; n_u += cls[k] == 0; }
+    int can_agree = !(has_p && has_m);
+    int can_disagree = (has_p && has_m) || (n_u >= 1 && (has_p || has_m)) || n_u >= 2;
+    int possible_true = can_differ && can_agree;
+    int possible_false = can_same || can_disagree;
+    return possible_true && possible_false;
+}
+
+/* Is any element's crossing decision for the link from node (x, y, z) along
+ * e_k a near tie?  (Brute force over all elements, nearest periodic image of
+ * the link to each element, single-precision node positions as in
+ * compute_cuts.) */
+static int link_near_tie(const or_ctx *c, int x, int y, int z, int k, double margin) {
+    for (int ci = 0; ci < c->ncaps; ++ci) {
+        const or_capsule *p = &c->caps[ci];
+        for (int f = 0; f < p->nf; ++f) {
+            double A[3], B[3], C[3];
+            tri_vertices_f(p, f, A, B, C);
+            double cx = (A[0] + B[0] + C[0]) / 3.0, cy = (A[1] + B[1] + C[1]) / 3.0;
+            double cz = (A[2] + B[2] + C[2]) / 3.0;
+            double px = x + c->nx * floor((cx - x) / c->nx + 0.5);
+            double py = y + c->ny * floor((cy - y) / c->ny + 0.5);
+            double pz = z + c->nz * floor((cz - z) / c->nz + 0.5);
+            if (fabs(px - cx) > 18.0 || fabs(py - cy) > 18.0 || fabs(pz - cz) > 18.0) continue;
+            double P[3] = {px, py, pz};
+            double Q[3] = {px + EV[k][0], py + EV[k][1], pz + EV[k][2]};
+            if (near_tie(P, Q, A, B, C, margin)) return 1;
+        }
+    }
+    return 0;
+}
+
+/* Cut-list override (a diagnostic for free-membrane parity runs): compare a
+ * cut structure computed elsewhere (mask [N], elements [N*18], e.g. by the
+ * single-precision GPU path on its own node positions) with the oracle's.
+ * Every link end where they differ (in the cut bit, or in the element of a
+ * link both cut) must be a near tie of the oracle's own decision within
+ * `margin`; then the given structure replaces the oracle's (interior flags
+ * recomputed) and the number of differing link ends is returned (0: nothing
+ * to do).  Otherwise nothing changes and the return value is minus the
+ * number of differing link ends that are not near ties. */
+long or_override_cuts(or_ctx *c, const uint32_t *mask, const int *tri, double margin) {
+    long ndiff = 0, bad = 0;
+    for (int z = 0; z < c->nz; ++z)
+        for (int y = 0; y < c->ny; ++y)
+            for (int x = 0; x < c->nx; ++x) {
+                long n = nidx(c, x, y, z);
+                uint32_t d = c->mask[n] ^ mask[n];
+                for (int k = 1; k < NQ; ++k) {
+                    uint32_t bit = 1u << (k - 1);
+                    int differs = (d & bit) != 0;
+                    if (!differs && (mask[n] & bit) && tri[18 * n + k - 1] != c->tri[18 * n + k - 1])
+                        differs = 1;
+                    if (!differs) continue;
+                    ++ndiff;
+                    if (!link_near_tie(c, x, y, z, k, margin)) ++bad;
+                }
+            }
+    if (bad) return -bad;
+    if (ndiff) or_set_cuts(c, mask, tri);
+    return ndiff;
+}
+
+/* ------------------------------------------- theory of Sec. 2 (the check) */
+/* Modified Bessel function of the second kind K_nu(x), x > 0, from the
+ * integral representation K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt
+ * (a standard identity; the paper prints K_0 as a cosine integral and K_1 in
+ * a garbled form, reading c5).  The integrand is analytic and decays
+ * doubly exponentially, so the trapezoid rule with step 1/64 is exact to
+ * rounding; the sum stops once a term falls below 1e-18 of the total. */
+double or_bessel_k(int nu, double x) {
+    if (!(x > 0.0)) return NAN;
+    const double h = 1.0 / 64.0;
+    double sum = 0.5 * exp(-x);  /* t = 0: cosh(0) = 1, halved (trapezoid end point) */
+    for (int k = 1; k < 1000000; ++k) {
+        double t = k * h;
+        double term = exp(-x * cosh(t)) * cosh(nu * t);
+        sum += term;
+        if (term < 1e-18 * sum) break;
+    }
+    return sum * h;
+}
+
+/* Least-squares fit of the meniscus model zeta(r) = Q K_0(q r) (Eq. 12 with
+ * Q = Gamma sin psi, Sec. 4.1) to the samples (r_k, zeta_k) with
+ * rmin <= r_k <= rmax and a finite zeta_k: minimises
+ * S(Q, q) = sum_k (zeta_k - Q K_0(q r_k))^2.  For a given q the best Q is
+ * linear, Q(q) = sum zeta K_0 / sum K_0^2; S(Q(q), q) is scanned on 400
+ * logarithmically spaced q in [1e-3, 3] and the best bracket refined by
+ * golden-section search.  Returns the number of samples used (0: no fit);
+ * rms = sqrt(S / samples). */
+static double fit_S(const double *r, const double *z, int m, double q, double *Qout) {
+    double zk = 0.0, kk = 0.0;
+    for (int i = 0; i < m; ++i) {
+        double k0 = or_bessel_k(0, q * r[i]);
+        zk += z[i] * k0;
+        kk += k0 * k0;
+    }
+    double Q = kk > 0.0 ? zk / kk : 0.0, S = 0.0;
+    for (int i = 0; i < m; ++i) {
+        double d = z[i] - Q * or_bessel_k(0, q * r[i]);
+        S += d * d;
+    }
+    if (Qout) *Qout = Q;
+    return S;
+}
+
+int or_meniscus_fit(const double *r, const double *zeta, int n, double rmin, double rmax, double *Q,
+                    double *q, double *rms) {
+    double *rr = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    double *zz = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    int m = 0;
+    for (int i = 0; i < n; ++i)
+        if (r[i] >= rmin && r[i] <= rmax && isfinite(zeta[i]) && r[i] > 0.0) { rr[m] = r[i]; zz[m] = zeta[i]; ++m; }
+    if (m < 2) { free(rr); free(zz); *Q = *q = *rms = NAN; return 0; }
+    const int NS = 400;
+    const double lq0 = log(1e-3), lq1 = log(3.0);
+    int best = 0;
+    double bestS = INFINITY;
+    for (int i = 0; i < NS; ++i) {
+        double S = fit_S(rr, zz, m, exp(lq0 + (lq1 - lq0) * i / (NS - 1)), NULL);
+        if (S < bestS) { bestS = S; best = i; }
+    }
+    double a = lq0 + (lq1 - lq0) * (best > 0 ? best - 1 : 0) / (NS - 1);
+    double b = lq0 + (lq1 - lq0) * (best < NS - 1 ? best + 1 : NS - 1) / (NS - 1);
+    const double g = (sqrt(5.0) - 1.0) / 2.0;
+    double c = b - g * (b - a), d = a + g * (b - a);
+    double Sc = fit_S(rr, zz, m, exp(c), NULL), Sd = fit_S(rr, zz, m, exp(d), NULL);
+    for (int it = 0; it < 200 && b - a > 1e-15; ++it) {
+        if (Sc < Sd) { b = d; d = c; Sd = Sc; c = b - g * (b - a); Sc = fit_S(rr, zz, m, exp(c), NULL); }
+        else { a = c; c = d; Sc = Sd; d = a + g * (b - a); Sd = fit_S(rr, zz, m, exp(d), NULL); }
+    }
+    *q = exp(0.5 * (a + b));
+    double S = fit_S(rr, zz, m, *q, Q);
+    *rms = sqrt(S / m);
+    free(rr); free(zz);
+    return m;
+}
+
+/* Lateral capillary force between two particles of capillary charges Q1, Q2
+ * at centre distance L (Eq. 13): F = -2 pi q gamma Q1 Q2 K_1(q L); negative is
+ * attraction. */
+double or_capillary_force(double q, double gamma, double Q1, double Q2, double L) {
+    const double pi = 3.14159265358979323846;
+    return -2.0 * pi * q * gamma * Q1 * Q2 * or_bessel_k(1, q * L);
 }

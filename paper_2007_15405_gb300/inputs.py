@@ -93,6 +93,7 @@ class CapsuleSpec:
     kV: float = 1.0
     mass: float = NODE_MASS
     mode: int = MODE_FREE
+    wet: float = 0.0  # wetting offset of the interpolated densities (0: neutral)
 
     def mesh(self):
         return icosphere(self.level, self.radius, self.centre)
@@ -175,32 +176,68 @@ def tiny_film(nx=16, ny=12, nz=20, radius=4.0, level=2, mode=MODE_FREE, steps=20
 
 
 def sweep_point(d_over_R: float, kS: Optional[float], nx: int, ny: int, nz: int,
-                radius: float = 8.0, level: int = 3, steps: int = 20000, seed: int = 1234) -> Workload:
+                radius: float = 10.0, level: int = 4, steps: int = 20000, seed: int = 1234,
+                h_frac: float = 0.4, mode: Optional[int] = None) -> Workload:
     """One lattice of a distance x softness sweep: two capsules of radius R at
-    centre distance d = d_over_R * R along x, film 0.6R above the repulsive
-    plane; kS None is the rigid limit (frozen shape)."""
+    centre distance d = d_over_R * R along x, film h_frac R above the
+    repulsive plane; kS None is the rigid limit (frozen shape).  mode, when
+    given, overrides the capsules' mode (e.g. fixed capsules for force runs)."""
     d = d_over_R * radius
     zc = z_rest(radius) + _OFF[2]
     cx, cy = nx / 2 + _OFF[0], ny / 2 + _OFF[1]
-    mode = MODE_FROZEN if kS is None else MODE_FREE
+    if mode is None:
+        mode = MODE_FROZEN if kS is None else MODE_FREE
     k = 5e-3 if kS is None else kS
     caps = [CapsuleSpec(centre=(cx - d / 2, cy, zc), radius=radius, level=level, kS=k, mode=mode),
             CapsuleSpec(centre=(cx + d / 2, cy, zc), radius=radius, level=level, kS=k, mode=mode)]
-    h_top = 0.5 + REP_DZ + 0.6 * radius
+    h_top = 0.5 + REP_DZ + h_frac * radius
     soft = "rigid" if kS is None else f"kS={kS:g}"
     return Workload(f"sweep {nx}x{ny}x{nz} d={d_over_R:.2f}R {soft}", nx, ny, nz, h_top=h_top,
                     capsules=caps, steps=steps, seed=seed)
 
 
+def rigid_particle(h_frac: float, radius: float = 10.0, level: int = 4, nx: int = 128, ny: int = 128,
+                   nz: int = 40, steps: int = 40000, seed: int = 4321) -> Workload:
+    """One fixed rigid particle (Sec. 4.1: a level-4 icosphere of radius R,
+    its bottom where the substrate repulsion starts) at the lattice centre,
+    film h_frac R above the repulsive plane: the meniscus of one particle,
+    for the fit of Eq. 12 and the film-height series of Q and Z."""
+    cap = CapsuleSpec(centre=(nx / 2 + _OFF[0], ny / 2 + _OFF[1], z_rest(radius) + _OFF[2]), radius=radius,
+                      level=level, mode=MODE_FIXED)
+    return Workload(f"rigid particle {nx}x{ny}x{nz} h0={h_frac:g}R", nx, ny, nz,
+                    h_top=0.5 + REP_DZ + h_frac * radius, capsules=[cap], steps=steps, seed=seed)
+
+
+def rigid_pair(gap_over_R: float, h_frac: float = 0.16, radius: float = 10.0, level: int = 4,
+               nx: Optional[int] = None, ny: int = 96, nz: int = 40, steps: int = 40000,
+               seed: int = 4322) -> Workload:
+    """Two fixed rigid particles (Sec. 4.1 force validation) with surface gap
+    gap_over_R * R (centre distance L = gap + 2R) along x, film h_frac R
+    above the repulsive plane (0.16R in the paper).  The box is 2L + 64 long
+    (a multiple of 8) unless given, so the pair's periodic images stay
+    farther than L + 64."""
+    L = gap_over_R * radius + 2.0 * radius
+    if nx is None:
+        nx = 8 * int(math.ceil((2.0 * L + 64.0) / 8.0))
+    zc = z_rest(radius) + _OFF[2]
+    cx, cy = nx / 2 + _OFF[0], ny / 2 + _OFF[1]
+    caps = [CapsuleSpec(centre=(cx - L / 2, cy, zc), radius=radius, level=level, mode=MODE_FIXED),
+            CapsuleSpec(centre=(cx + L / 2, cy, zc), radius=radius, level=level, mode=MODE_FIXED)]
+    return Workload(f"rigid pair {nx}x{ny}x{nz} gap={gap_over_R:g}R", nx, ny, nz,
+                    h_top=0.5 + REP_DZ + h_frac * radius, capsules=caps, steps=steps, seed=seed)
+
+
 SWEEP_MODULI = (1e-3, 1e-2, 1e-1, None)  # shear moduli and the rigid limit
 
 
-def batched_sweep(n_dist: int = 16, moduli=SWEEP_MODULI, radius: float = 8.0, level: int = 3,
-                  steps: int = 20000) -> List[Workload]:
+def batched_sweep(n_dist: int = 16, moduli=SWEEP_MODULI, radius: float = 10.0, level: int = 4,
+                  steps: int = 20000, h_frac: float = 0.4, mode: Optional[int] = None) -> List[Workload]:
     """Distance x softness sweep of independent lattices of uneven size: n_dist
-    distances in [2.2R, 6R] times the moduli (64 lattices by default).  The
-    lattice grows with the distance (x: 64..160) and with the modulus index
-    (y: 48..80, z: 48..64), from 147k to 819k nodes."""
+    distances in [2.2R, 6R] times the moduli (64 lattices by default), two
+    R = 10 level-4 capsules (2562 nodes each) per lattice, film 0.4R above the
+    repulsive plane.  The lattice grows with the distance (x: 64..160) and
+    with the modulus index (y: 48..80, z: 48..64), from 147k to 819k nodes
+    (26.1M in all)."""
     out = []
     for i in range(n_dist):
         f = i / max(1, n_dist - 1)
@@ -211,7 +248,7 @@ def batched_sweep(n_dist: int = 16, moduli=SWEEP_MODULI, radius: float = 8.0, le
             ny = 48 + 8 * int(round(g * 4))
             nz = 48 + 8 * int(round(g * 2))
             out.append(sweep_point(d_over_R, kS, nx, ny, nz, radius=radius, level=level,
-                                   steps=steps, seed=1234 + 97 * i + j))
+                                   steps=steps, seed=1234 + 97 * i + j, h_frac=h_frac, mode=mode))
     return out
 
 

@@ -56,6 +56,9 @@ def test_batched_sweep_sizes_and_moduli():
         d = abs(b.centre[0] - a.centre[0]) / a.radius
         assert 2.2 - 1e-9 <= d <= 6.0 + 1e-9
         assert b.centre[0] + b.radius < w.nx and a.centre[0] - a.radius > 0
+        assert a.radius == 10.0 and a.level == 4
+        assert math.isclose(w.h_top, 0.5 + I.REP_DZ + 0.4 * a.radius)
+    assert sum(nodes) == 26148864
 
 
 def test_warm_dataset_ranges():

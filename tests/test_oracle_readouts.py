@@ -265,3 +265,92 @@ def test_lateral_force_of_mirror_pair_is_antisymmetric():
     assert L == pytest.approx(0.5 * (Fb[0] - Fa[0]), rel=1e-12)
     assert L == pytest.approx(Fb[0], rel=1e-4)
     assert o.lateral_force(1, 0) == pytest.approx(L, rel=1e-12)
+
+
+# ---------------------------------------------------- cut-structure override
+def sheet_oracle(zs, G=0.0, wet=0.0):
+    """A flat triangulated sheet at height zs over a 6 x 6 periodic box (the
+    vertices offset by (0.3, 0.4), so no link passes near an element edge)."""
+    nx, ny, nz = 6, 6, 12
+    xs = 0.3 + 2.0 * np.arange(4)
+    ys = 0.4 + 2.0 * np.arange(4)
+    X = np.array([[x, y, zs] for y in ys for x in xs])
+    F = []
+    for j in range(3):
+        for i in range(3):
+            a = j * 4 + i
+            F += [[a, a + 1, a + 5], [a, a + 5, a + 4]]
+    o = O.Oracle(nx, ny, nz, wall=0, G=G)
+    o.add_capsule(X, np.array(F, np.int32), 0.0, 0.0, 0.0, 0.0, 25.0, I.MODE_FIXED, wet=wet)
+    return o
+
+
+def flip_link(mask, tri, x, y, z, k, nx, ny, nz, T=0):
+    e, _, op = O.tables()
+    m = mask.copy(); t = tri.copy()
+    x2, y2, z2 = (x + e[k, 0]) % nx, (y + e[k, 1]) % ny, (z + e[k, 2]) % nz
+    m[z, y, x] ^= np.uint32(1 << (k - 1))
+    m[z2, y2, x2] ^= np.uint32(1 << (op[k] - 1))
+    t[z, y, x, k - 1] = T
+    t[z2, y2, x2, op[k] - 1] = T
+    return m, t
+
+
+def test_override_rejects_a_flip_far_from_a_tie():
+    """The sheet at z = 6.5 crosses every link from z = 6 to 7 half-way,
+    far from its edges: a structure that disagrees there is refused and the
+    oracle's stays."""
+    o = sheet_oracle(6.5)
+    m, t, _ = o.cuts()
+    assert m[6, 2, 2] >> 4 & 1                       # +z link of (2, 2, 6) cut
+    assert o.override_cuts(m, t) == 0                # identical: nothing to do
+    m2, t2 = flip_link(m, t, 2, 2, 6, 5, 6, 6, 12)
+    assert o.override_cuts(m2, t2, 1e-4) == -2       # both link ends differ, no tie
+    assert np.array_equal(o.cuts()[0], m)
+
+
+def test_override_adopts_a_flip_at_a_tie():
+    """The sheet 3e-5 above the plane z = 6: the link (2, 2, 5) -> +z ends
+    within the margin of the element plane, so either decision is a tie: the
+    oracle adopts the given structure (and its interior flags).  With a
+    margin below the distance it does not."""
+    o = sheet_oracle(6.00003)
+    m, t, _ = o.cuts()
+    assert not (m[5, 2, 2] >> 4 & 1) and (m[6, 2, 2] >> 4 & 1)
+    m2, t2 = flip_link(m, t, 2, 2, 5, 5, 6, 6, 12)
+    assert o.override_cuts(m2, t2, 1e-6) == -2
+    assert o.override_cuts(m2, t2, 1e-4) == 2
+    assert np.array_equal(o.cuts()[0], m2)
+
+
+# ------------------------------------------------------------------ wetting
+@pytest.mark.parametrize("wet", [0.0, 0.05, -0.05])
+def test_wetting_offset_on_a_flat_sheet(wet):
+    """A uniform state (rho_A = 0.5, rho_B = 0.3) around a flat sheet at
+    z = 6.5: the partner densities across the sheet's cut links are the
+    uniform ones plus the offset (A: +wet, B: -wet), every other neighbour
+    term cancels, and the five cut links of a node below the sheet carry
+    sum w e_z = 1/18 + 4/36 = 1/6.  So F^A_z = -G psi_A/6 (psi(rho_B - wet)
+    - psi(rho_B)) and F^B_z = -G psi_B/6 (psi(rho_A + wet) - psi(rho_A)),
+    with the opposite sign above the sheet and no lateral force: a positive
+    offset draws A towards the sheet (A-philic), a negative one B, zero is
+    neutral."""
+    o = sheet_oracle(6.5, G=3.6, wet=wet)
+    _, w, _ = O.tables()
+    f = np.zeros((2, 19, o.nz, o.ny, o.nx))
+    f[0] = w[:, None, None, None] * 0.5
+    f[1] = w[:, None, None, None] * 0.3
+    o.set_populations(f)
+    F = o.sc_forces()
+    psi = lambda r: 1.0 - math.exp(-r)
+    fa = -3.6 * psi(0.5) / 6.0 * (psi(0.3 - wet) - psi(0.3))
+    fb = -3.6 * psi(0.3) / 6.0 * (psi(0.5 + wet) - psi(0.5))
+    assert np.allclose(F[0, 2, 6], fa, atol=1e-15) and np.allclose(F[1, 2, 6], fb, atol=1e-15)
+    assert np.allclose(F[0, 2, 7], -fa, atol=1e-15) and np.allclose(F[1, 2, 7], -fb, atol=1e-15)
+    assert np.abs(F[:, :2]).max() < 1e-15
+    far = [z for z in range(o.nz) if z not in (6, 7)]
+    assert np.abs(F[:, :, far]).max() < 1e-15
+    if wet > 0:
+        assert fa > 0 and fb < 0
+    elif wet < 0:
+        assert fa < 0 and fb > 0
