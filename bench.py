@@ -1,24 +1,23 @@
 """Benchmark of the coupled LB-FEM step on GB300.
 
-Workload: two R=12 level-4 capsules (2562 nodes each) at centre distance 3R in
-a 128x64x64 lattice with a substrate, film height 0.6R, FP32 populations.  One
-bench step = one coupled time step (streaming with bounce-back and Ladd
-exchange, Shan-Chen forces with decoupling, BGK, membrane forces, node
-update, cut-link rebuild).  Metric: coupled MLUPS = nodes x steps / s / 1e6.
+Default workload: the distance x softness sweep of the paper's force study
+(Sec. 4.1-4.3) as one batch: 64 independent lattices of uneven size
+(64x48x48 .. 160x80x64, 26.1M nodes), each with two R=10 level-4 capsules
+(2562 nodes / 5120 elements each) at a centre distance d in [2.2R, 6R],
+shear modulus 1e-3, 1e-2, 1e-1 or rigid, film 0.4R above the repulsive
+plane, float32 populations.  One bench step = one coupled time step of all 64
+lattices (streaming with bounce-back and Ladd exchange, Shan-Chen forces with
+decoupling, BGK, membrane forces, node update, cut-link rebuild), the lattice
+passes of all lattices in one persistent launch per pass, the steps replayed
+from a captured CUDA graph.  Metric: coupled MLUPS = nodes x steps / s / 1e6.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-  python bench.py --sweep [--steps K]      # batched distance x softness sweep
-  python bench.py --warm                   # learned warm start vs flat film
+  python bench.py --pair                     # one capsule pair, 128x64x64
   python bench.py --drying --precision fp16  # drying film, 16 capsules, 256x256x96
+  python bench.py --warm                     # learned warm start vs flat film
 
---drying measures the mixed-precision drying film instead: a 256x256x96
-lattice with 16 R=10 capsules on a seeded random layout, the film lowered by a
-steady conversion of A into B (0.6R to 0.2R over 50k steps).
-
---sweep measures the batched step instead: 64 independent lattices of uneven
-size (147k-819k nodes, two capsules each, 16 distances x 4 moduli) stepped
-together after the autotuner has picked the launch shape, against the same
-lattices stepped one by one.
+Extra keys of the default line: the same sweep with half and bfloat16 offset
+storage (mixed precision), and the single capsule pair.
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload
 (weak scaling: no data-path collective); time = max over ranks.
@@ -41,27 +40,33 @@ ALG_BYTES_PER_LU = 2 * 19 * 2 * 4  # two components x 19 populations x (read + w
 ALG_BYTES_PER_LU_16 = 2 * (18 * 2 + 4) * 2
 PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2}
 METRIC = "coupled LB+IBM MLUPS (% HBM roofline)"
+SAMPLE_EVERY = 10  # e2e: lateral forces read back every this many steps
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default line only (no 16-bit sweep, no capsule pair)")
     ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS),
                     help="population storage (arithmetic is float32 in every mode)")
-    ap.add_argument("--sweep", action="store_true",
-                    help="batched 64-lattice sweep instead of the capsule pair")
+    ap.add_argument("--sweep", action="store_true", help="the batched sweep (the default)")
+    ap.add_argument("--pair", action="store_true", help="one capsule pair (128x64x64) instead of the sweep")
     ap.add_argument("--tune-steps", type=int, default=8)
     ap.add_argument("--warm", action="store_true",
                     help="train the warm-start network and measure its gain on held-out set-ups")
     ap.add_argument("--sweep-n", type=int, default=16,
                     help="distances of the sweep (x 4 moduli lattices)")
+    ap.add_argument("--theory", action="store_true",
+                    help="theory check: meniscus fits over film heights and rigid-pair forces vs Eq. 13")
+    ap.add_argument("--theory-steps", type=int, default=40000)
     ap.add_argument("--drying", action="store_true",
-                    help="drying film with 16 capsules (256x256x96) instead of the capsule pair")
+                    help="drying film with 16 capsules (256x256x96) instead of the sweep")
     return ap.parse_args()
 
 
@@ -122,26 +127,8 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def profiled_traffic():
-    """DRAM bytes per step of the two lattice passes from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
-    import hashlib
-    try:
-        txt = open(os.path.join(ROOT, "profiles", "lattice_passes_capsule_pair.md")).read()
-        src = open(os.path.join(ROOT, "paper_2007_15405_gb300", "csrc", "lb_kernel.cu"), "rb").read()
-    except OSError:
-        return None
-    sha = hashlib.sha256(src).hexdigest()[:16]
-    t = h = None
-    for line in txt.splitlines():
-        if line.startswith("traffic_bytes_per_step:"):
-            t = int(line.split(":")[1])
-        if line.startswith("lb_kernel.cu sha256[:16]:"):
-            h = line.rsplit(":", 1)[1].strip()
-    return t if (t is not None and h == sha) else None
-
-
 def measured_peak():
+    """The HBM copy bandwidth measured on the GB300s (burst)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return float(json.load(f)["hbm_gbs"]), "measured"
@@ -149,41 +136,35 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def cpu_baseline(wl, steps):
+def host_cores():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def cpu_baseline(wl, steps, what):
     """The FP64 oracle as it stands, on the host cores, on a bounded sample:
-    `steps` time steps of the full workload."""
+    `steps` coupled time steps of lattice `wl`."""
     import oracle as O
     o = O.Oracle.from_workload(wl)
     o.step(1)  # warm-up (first-touch of the arrays)
     t = time.perf_counter()
     o.step(steps)
     dt = time.perf_counter() - t
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": wl.nodes * steps / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{steps} coupled steps of the full {wl.nx}x{wl.ny}x{wl.nz} workload "
-                      f"({dt:.1f} s, FP64, OpenMP over lattice planes)"}
+    o.close()
+    return {"value": wl.nodes * steps / dt / 1e6, "unit": "MLUPS", "cores": host_cores(), "kind": "oracle",
+            "sample": f"{steps} coupled steps of {what} ({wl.nx}x{wl.ny}x{wl.nz}, {dt:.1f} s, FP64, "
+                      f"OpenMP over lattice planes)"}
 
 
-def workload(args=None):
+def sweep_workloads(args):
     from paper_2007_15405_gb300 import inputs as I
-    if args is not None and args.drying:
-        return I.drying_film()
-    return I.capsule_pair(steps=20000)
+    return I.batched_sweep(n_dist=args.sweep_n)
 
 
-def config_of(wl, world, l2note):
-    if wl.dry_dm > 0.0:
-        desc = (f"drying film: {wl.nx}x{wl.ny}x{wl.nz} lattice, substrate, {len(wl.capsules)} R=10 "
-                f"level-4 capsules (2562 nodes / 5120 elements each) on a seeded random layout, "
-                f"film lowered from 0.6R to 0.2R over 50k steps by converting {wl.dry_dm:.4f} of A "
-                f"into B per step, free capsules")
-    else:
-        desc = ("capsule pair: 128x64x64 lattice, substrate, two R=12 level-4 capsules "
-                "(2562 nodes / 5120 elements each) at d=3R, film 0.6R, free capsules")
-    return {"workload": desc,
-            "lattice": [wl.nx, wl.ny, wl.nz], "capsules": len(wl.capsules), "nodes": wl.nodes,
-            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-            "l2": l2note}
+SWEEP_DESC = ("batched distance x softness sweep: 64 independent lattices 64x48x48..160x80x64 "
+              "(26.1M nodes) with a substrate, each with two R=10 level-4 capsules (2562 nodes / "
+              "5120 elements each) at d in [2.2R, 6R] (16 distances) x kS in {1e-3, 1e-2, 1e-1, rigid}, "
+              "film 0.4R above the repulsive plane; one persistent launch per lattice pass, "
+              "steps replayed from a captured CUDA graph")
 
 
 def l2_note(ws):
@@ -207,35 +188,87 @@ def job_mlups(nodes, steps, world, seconds):
     return nodes * steps * world / seconds / 1e6
 
 
-def run_reference(args):
-    rank, world, _ = dist_env()
-    if rank != 0:
-        return
-    wl = workload(args)
-    steps_per = args.cpu_sample_steps or 2
-    import oracle as O
-    o = O.Oracle.from_workload(wl)
-    for _ in range(args.warmup):
-        o.step(steps_per)
-    t = time.perf_counter()
-    for _ in range(args.steps):
-        o.step(steps_per)
-    dt = time.perf_counter() - t
-    val = wl.nodes * steps_per * args.steps / dt / 1e6
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": dt / (args.steps * steps_per) * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(wl, 1, "host CPU"),
-            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                             "sample": f"each bench step = {steps_per} oracle time steps of the "
-                                       f"full workload"},
-            "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+def roofline(alg_bytes, nodes, kernel_ms, kernel, peak, peak_kind, traffic=None):
+    achieved = alg_bytes * nodes / (kernel_ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak,
+            "peak_kind": f"{peak_kind} copy bandwidth (burst)", "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes * nodes,
+            "algorithmic_bytes_per_lu": alg_bytes, "kernel_ms": kernel_ms}
 
 
-def run_ours(args):
+def build_batch(cfm, wls, prec, tune_steps):
+    sims = [cfm.Simulation.from_workload(w, precision=prec) for w in wls]
+    batch = cfm.Batch(sims)
+    t0 = time.perf_counter()
+    cfg = batch.autotune(steps=tune_steps)
+    cfg["seconds"] = time.perf_counter() - t0
+    return sims, batch, cfg
+
+
+def time_batch(batch, warmup, steps, barrier, sampler=None):
+    """W untimed steps (they capture the step graph), then exactly K steps timed
+    with CUDA events on the batch's stream; returns ms."""
+    batch.step(max(3, warmup))
+    if sampler is not None:
+        sampler.start()
+        time.sleep(0.3)
+    barrier()
+    ms = batch.time(steps)
+    barrier()
+    return ms
+
+
+def run_sweep_precision(cfm, wls, prec, args, peak, peak_kind, barrier):
+    """The sweep with another population storage: value and lattice-pass roofline."""
+    nodes = sum(w.nodes for w in wls)
+    sims, batch, cfg = build_batch(cfm, wls, prec, args.tune_steps)
+    ms = time_batch(batch, args.warmup, args.steps, barrier)
+    ph = batch.time_phases(10)
+    alg = ALG_BYTES_PER_LU if prec == 0 else ALG_BYTES_PER_LU_16
+    out = {"value": nodes * args.steps / (ms / 1e3) / 1e6, "unit": "MLUPS", "steps": args.steps,
+           "ms_per_step": ms / args.steps, "autotune": cfg,
+           "roofline": roofline(alg, nodes, ph[0], "batched lattice passes: k_density_batch + "
+                                "k_collide_batch (tau = 1)", peak, peak_kind),
+           "phases_ms": {"lattice": ph[0], "before_lattice": ph[1], "after_lattice": ph[2]}}
+    batch.close()
+    for s in sims:
+        s.close()
+    return out
+
+
+def run_pair(cfm, args, peak, peak_kind, barrier, world=1, precision=0):
+    """One capsule pair (128x64x64, two R=12 level-4 capsules at d = 3R, film
+    0.6R) stepped alone through cf_step."""
+    import torch
+    from paper_2007_15405_gb300 import inputs as I
+    wl = I.capsule_pair(steps=20000)
+    sim = cfm.Simulation.from_workload(wl, precision=precision)
+    stream = sim.stream
+    sim.step(max(3, args.warmup))
+    sim.sync()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1), "cuda")
+    launches = sim.launches()
+    ph = sim.time_phases(min(200, max(20, args.steps // 10)))
+    alg = ALG_BYTES_PER_LU if precision == 0 else ALG_BYTES_PER_LU_16
+    out = {"workload": "capsule pair: 128x64x64 lattice, substrate, two R=12 level-4 capsules "
+                       "(2562 nodes / 5120 elements each) at d=3R, film 0.6R, free capsules",
+           "value": job_mlups(wl.nodes, args.steps, world, ms / 1e3), "unit": "MLUPS",
+           "ms_per_step": ms / args.steps, "nodes": wl.nodes, "gpu_launches": launches,
+           "roofline": roofline(alg, wl.nodes, ph[0], "lattice update: k_density + k_collide_eq (tau = 1)",
+                                peak, peak_kind),
+           "phases_ms": {"lattice": ph[0], "membrane": ph[1], "cut_links": ph[2], "bounce_prep": ph[3]}}
+    return sim, wl, out
+
+
+def setup(args):
     import torch
     rank, world, local = dist_env()
     if world > 1:
@@ -256,143 +289,186 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    wl = workload(args)
-    prec = PRECISIONS[args.precision]
-    alg_bytes = ALG_BYTES_PER_LU if prec == 0 else ALG_BYTES_PER_LU_16
-    sim = cfm.Simulation.from_workload(wl, precision=prec)
-    stream = sim.stream  # the events must be recorded on the stream the steps run on
-    # warm-up
-    sim.step(args.warmup)
-    sim.sync()
-    # ---- device-resident throughput: K steps through cf_step (graph replay)
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    sim.step(args.steps)
-    e1.record(stream)
-    e1.synchronize()
-    launches = sim.launches()
-    barrier()
-    ms = e0.elapsed_time(e1)
-    clk = clocks.stop()
-    sim.sync()
-    ms_max = max_over_ranks(ms, "cuda")
-    value = job_mlups(wl.nodes, args.steps, world, ms_max / 1e3)
-    # ---- per-phase device time (lattice kernel, membrane phase, cut links)
-    nprof = min(200, max(20, args.steps // 10))
-    ph = sim.time_phases(nprof)
-    lb_ms = ph[0]
-    peak, peak_kind = measured_peak()
-    achieved = alg_bytes * wl.nodes / (lb_ms / 1e3) / 1e9
-    # ---- end to end through the public API with host buffers
-    from paper_2007_15405_gb300.inputs import RHO_MAJ, RHO_MIN, RHO_MIX
-    jit = wl.jitter()
-    jit_pinned = torch.from_numpy(jit.reshape(-1)).pin_memory().numpy()
-    sample_every = 100
-    nsamp = max(1, args.steps // sample_every)
-    barrier()
-    t0 = time.perf_counter()
-    sim.set_film(wl.h_top, RHO_MAJ, RHO_MIN, RHO_MIX, jit_pinned)
-    forces = []
-    for _ in range(nsamp):
-        sim.step(sample_every)
-        forces.append(sim.lateral_force(0, 1))
-    barrier()
-    t_e2e = max_over_ranks(time.perf_counter() - t0, "cuda")
-    e2e_steps = nsamp * sample_every
-    e2e_val = job_mlups(wl.nodes, e2e_steps, world, t_e2e)
-    h2d = jit.nbytes / e2e_steps
-    d2h = 16 * 8 * len(wl.capsules) * nsamp / e2e_steps
-    sim.close()
+    return rank, world, local, cfm, barrier
+
+
+def teardown(world):
+    import torch
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_ours(args):
+    """Default line: the batched sweep."""
+    import torch
+    rank, world, local, cfm, barrier = setup(args)
+    from paper_2007_15405_gb300.inputs import RHO_MAJ, RHO_MIN, RHO_MIX
+    prec = PRECISIONS[args.precision]
+    alg = ALG_BYTES_PER_LU if prec == 0 else ALG_BYTES_PER_LU_16
+    peak, peak_kind = measured_peak()
+    wls = sweep_workloads(args)
+    nodes = sum(w.nodes for w in wls)
+    sims, batch, tune = build_batch(cfm, wls, prec, args.tune_steps)
+    # ---- device-resident throughput: W untimed steps, then K steps timed
+    clocks = ClockSampler(local)
+    ms = time_batch(batch, args.warmup, args.steps, barrier, clocks)
+    clk = clocks.stop()
+    launches = batch.launches()
+    ms_max = max_over_ranks(ms, "cuda")
+    value = job_mlups(nodes, args.steps, world, ms_max / 1e3)
+    # ---- per-phase device time (CUDA events on the batch's stream)
+    ph = batch.time_phases(10)
+    # ---- end to end through the public API with host buffers: every lattice
+    # set up from its pinned host jitter (H2D), exactly K steps, the lateral
+    # forces of all lattices read back every SAMPLE_EVERY steps and at the end
+    jits = [torch.from_numpy(w.jitter().reshape(-1)).pin_memory() for w in wls]
+    h2d = sum(j.numel() * j.element_size() for j in jits)
+    barrier()
+    t0 = time.perf_counter()
+    for s, w, j in zip(sims, wls, jits):
+        s.set_film(w.h_top, RHO_MAJ, RHO_MIN, RHO_MIX, j.numpy())
+    done, nread = 0, 0
+    while done < args.steps:
+        k = min(SAMPLE_EVERY, args.steps - done)
+        batch.step(k)
+        batch.lateral_forces(0, 1)
+        nread += 1
+        done += k
+    barrier()
+    t_e2e = max_over_ranks(time.perf_counter() - t0, "cuda")
+    e2e_val = job_mlups(nodes, args.steps, world, t_e2e)
+    d2h = 8 * len(wls) * nread
+    batch.close()
+    for s in sims:
+        s.close()
+    extras = {}
+    if not args.no_extras:
+        for name, pr in (("sweep_fp16_storage", 1), ("sweep_bf16_storage", 2)):
+            if pr != prec:
+                extras[name] = run_sweep_precision(cfm, wls, pr, args, peak, peak_kind, barrier)
+        sim, _, pair = run_pair(cfm, args, peak, peak_kind, barrier, world)
+        sim.close()
+        extras["capsule_pair"] = pair
+    teardown(world)
     if rank != 0:
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        # about 10-20 s of oracle work on 16 host cores
-        cpu = cpu_baseline(wl, args.cpu_sample_steps or max(2, int(5.2e7 // wl.nodes)))
+        w0 = wls[0]  # the smallest lattice of the sweep: about 10-20 s of oracle work
+        cpu = cpu_baseline(w0, args.cpu_sample_steps or max(2, int(4e7 // w0.nodes)),
+                           "the sweep's smallest lattice (d = 2.2R, kS = 1e-3)")
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_of(wl, world, l2_note(alg_bytes * wl.nodes)),
-        "roofline": {"bound": "hbm", "kernel": "lattice update: k_density + k_collide_eq (tau = 1)",
-                     "achieved": achieved, "peak": peak,
-                     "peak_kind": f"{peak_kind} copy bandwidth (burst)", "unit": "GB/s",
-                     "frac": achieved / peak,
-                     "traffic": profiled_traffic() if prec == 0 else None,
-                     "algorithmic_bytes_per_launch": alg_bytes * wl.nodes,
-                     "kernel_ms": lb_ms},
-        "phases_ms": {"lattice": ph[0], "membrane": ph[1], "cut_links": ph[2], "bounce_prep": ph[3]},
+        "config": {"workload": SWEEP_DESC, "lattices": len(wls), "nodes": nodes,
+                   "capsules": 2 * len(wls), "population_storage": args.precision,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": l2_note(alg * nodes)},
+        "roofline": roofline(alg, nodes, ph[0], "batched lattice passes: k_density_batch + k_collide_batch "
+                             "(tau = 1), one persistent launch each over all 64 lattices", peak, peak_kind),
+        "phases_ms": {"lattice": ph[0], "before_lattice": ph[1], "after_lattice": ph[2]},
+        "autotune": tune,
         "clocks": clk,
-        "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h,
-                "note": f"film set-up from pinned host jitter, {e2e_steps} steps, lateral force "
-                        f"read back every {sample_every} steps"},
+        "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
+                "d2h_bytes_per_step": d2h / args.steps,
+                "note": f"every lattice set up from pinned host jitter (H2D), {args.steps} steps through "
+                        f"cf_batch_step, lateral forces of all lattices read back every {SAMPLE_EVERY} "
+                        f"steps ({nread} reads)"},
         "gpu_launches": launches,
         "cpu_baseline": cpu,
     }
-    line["config"]["population_storage"] = args.precision
+    line.update(extras)
     print(json.dumps(line), flush=True)
 
 
-def run_sweep(args):
+def run_single(args):
+    """--pair / --drying: one lattice stepped alone through cf_step."""
     import torch
-    from paper_2007_15405_gb300 import build as B
-    B.build()
-    from paper_2007_15405_gb300 import capfilm as cfm
+    rank, world, local, cfm, barrier = setup(args)
     from paper_2007_15405_gb300 import inputs as I
-    torch.cuda.set_device(0)
     prec = PRECISIONS[args.precision]
-    wls = I.batched_sweep(n_dist=args.sweep_n)
-    nodes = sum(w.nodes for w in wls)
-    sims = [cfm.Simulation.from_workload(w, precision=prec) for w in wls]
-    batch = cfm.Batch(sims)
-    t0 = time.perf_counter()
-    cfg = batch.autotune(steps=args.tune_steps)
-    t_tune = time.perf_counter() - t0
-    batch.step(max(3, args.warmup))
-    clocks = ClockSampler(0)
-    clocks.start()
-    time.sleep(0.3)
-    ms = batch.time(args.steps)
-    launches = batch.launches()
-    clk = clocks.stop()
-    value = nodes * args.steps / (ms / 1e3) / 1e6
-    # the same lattices stepped one after the other (each replaying its own graph)
-    k = max(4, min(args.steps, 40))
-    seq_ms = 0.0
-    for s in sims:
-        s.step(3)
-        s.sync()
+    alg = ALG_BYTES_PER_LU if prec == 0 else ALG_BYTES_PER_LU_16
+    peak, peak_kind = measured_peak()
+    clocks = ClockSampler(local)
+    if args.drying:
+        wl = I.drying_film()
+        sim = cfm.Simulation.from_workload(wl, precision=prec)
+        sim.step(max(3, args.warmup))
+        sim.sync()
+        clocks.start()
+        time.sleep(0.3)
+        barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(s.stream)
-        s.step(k)
-        e1.record(s.stream)
+        e0.record(sim.stream)
+        sim.step(args.steps)
+        e1.record(sim.stream)
         e1.synchronize()
-        seq_ms += e0.elapsed_time(e1)
-    seq_value = nodes * k / (seq_ms / 1e3) / 1e6
-    batch.close()
-    line = {
-        "metric": "batched sweep coupled MLUPS", "value": value, "unit": "MLUPS", "n_gpus": 1,
-        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{len(wls)} lattices 64x48x48..160x80x64 ({nodes} nodes), two R=8 "
-                               "level-3 capsules each, d in [2.2R, 6R] x kS in {1e-3, 1e-2, 1e-1, rigid}",
-                   "population_storage": args.precision,
-                   "l2": f"no flush: per-step working set {nodes * 304 / 1e9:.1f} GB of populations "
-                         "exceeds the 129 MB L2"},
-        "autotune": dict(cfg, seconds=t_tune),
-        "one_by_one": {"value": seq_value, "unit": "MLUPS", "steps": k},
-        "speedup_vs_one_by_one": value / seq_value,
-        "clocks": clk, "gpu_launches": launches,
-    }
+        barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1), "cuda")
+        ph = sim.time_phases(min(200, max(20, args.steps // 10)))
+        out = {"workload": f"drying film: {wl.nx}x{wl.ny}x{wl.nz} lattice, substrate, {len(wl.capsules)} R=10 "
+                           f"level-4 capsules (2562 nodes / 5120 elements each) on a seeded random layout, "
+                           f"film lowered from 0.6R to 0.2R over 50k steps by converting {wl.dry_dm:.4f} "
+                           f"of A into B per step, free capsules",
+               "value": job_mlups(wl.nodes, args.steps, world, ms / 1e3), "ms_per_step": ms / args.steps,
+               "gpu_launches": sim.launches(),
+               "roofline": roofline(alg, wl.nodes, ph[0], "lattice update: k_density + k_collide_eq (tau = 1)",
+                                    peak, peak_kind),
+               "phases_ms": {"lattice": ph[0], "membrane": ph[1], "cut_links": ph[2], "bounce_prep": ph[3]}}
+    else:
+        clocks.start()
+        sim, wl, out = run_pair(cfm, args, peak, peak_kind, barrier, world, prec)
+    clk = clocks.stop()
+    sim.close()
+    teardown(world)
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(wl, args.cpu_sample_steps or max(2, int(5.2e7 // wl.nodes)), "the full workload")
+    line = {"metric": METRIC, "value": out.pop("value"), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": out.pop("ms_per_step"),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": out.pop("workload"), "lattice": [wl.nx, wl.ny, wl.nz],
+                       "capsules": len(wl.capsules), "nodes": wl.nodes, "population_storage": args.precision,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": l2_note(alg * wl.nodes)},
+            "clocks": clk, "cpu_baseline": cpu}
+    line.update(out)
+    print(json.dumps(line), flush=True)
+
+
+def run_reference(args):
+    """The oracle arm: each bench step is one coupled time step of one lattice
+    of the sweep (the smallest), on the host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    wl = sweep_workloads(args)[0]
+    steps_per = args.cpu_sample_steps or 1
+    import oracle as O
+    o = O.Oracle.from_workload(wl)
+    for _ in range(args.warmup):
+        o.step(steps_per)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(steps_per)
+    dt = time.perf_counter() - t
+    o.close()
+    val = wl.nodes * steps_per * args.steps / dt / 1e6
+    cores = host_cores()
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / (args.steps * steps_per) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": SWEEP_DESC, "sample": f"{wl.nx}x{wl.ny}x{wl.nz} (the smallest lattice)"},
+            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": f"each bench step = {steps_per} oracle time step(s) of the sweep's "
+                                       f"smallest lattice ({wl.nx}x{wl.ny}x{wl.nz}, two capsules)"},
+            "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -453,16 +529,87 @@ def run_warm(args):
     print(json.dumps(line), flush=True)
 
 
+def gamma_g36():
+    """Surface tension at G = 3.6 from the oracle's Laplace test (the value
+    tests/golden/make_gamma.py wrote)."""
+    with open(os.path.join(ROOT, "tests", "golden", "gamma_G3.6.txt")) as f:
+        return float([l for l in f.read().split("\n") if l and not l.startswith("#")][0])
+
+
+def run_theory(args):
+    """Theory check (Sec. 2, Eqs. 12-13; Sec. 4.1) and the film-height series
+    of the capillary charge and rise: single fixed particles at several film
+    heights and fixed pairs at h0 = 0.16R with surface gaps 3..7 R, all in one
+    batch, stepped to (near) equilibrium.  Each single particle's profile is
+    fitted with zeta = Q K_0(q r); the pair forces are compared with
+    F = -2 pi q gamma Q^2 K_1(q L) using q and Q of the single particle at the
+    same film height and gamma from the Laplace test."""
+    import torch
+    from paper_2007_15405_gb300 import build as B
+    B.build()
+    from paper_2007_15405_gb300 import capfilm as cfm
+    from paper_2007_15405_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    R = 10.0
+    hs = [0.16, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9]
+    gaps = [3.0, 4.0, 5.0, 6.0, 7.0]
+    singles = [I.rigid_particle(h, R) for h in hs]
+    pairs = [I.rigid_pair(g, 0.16, R) for g in gaps]
+    wls = singles + pairs
+    sims = [cfm.Simulation.from_workload(w) for w in wls]
+    batch = cfm.Batch(sims)
+    batch.autotune(steps=2)
+    every = max(1, args.theory_steps // 10)
+    hist_F, hist_Z = [], []
+    t0 = time.perf_counter()
+    done = 0
+    while done < args.theory_steps:
+        batch.step(every)
+        done += every
+        hist_F.append([sims[len(singles) + k].lateral_force(0, 1) for k in range(len(pairs))])
+        hist_Z.append([s.meniscus_height(0) for s in sims[:len(singles)]])
+    wall = time.perf_counter() - t0
+    gamma = gamma_g36()
+    fits = []
+    for h, s, w in zip(hs, sims, singles):
+        r, z, Z = s.meniscus_profile(0, 1.0)
+        Q, q, rms, m = cfm.meniscus_fit(r, z, rmin=R + 4.0, rmax=0.5 * w.nx - 4.0)
+        fits.append({"h0_over_R": h, "Q": Q, "q": q, "Z": Z, "fit_rms": rms, "samples": m,
+                     "Z_drift_last_interval": (hist_Z[-1][hs.index(h)] - hist_Z[-2][hs.index(h)])
+                     if len(hist_Z) > 1 else None})
+    f0 = fits[0]
+    force = []
+    for k, (g, w) in enumerate(zip(gaps, pairs)):
+        L = g * R + 2 * R
+        Fs = float(np.mean([hf[k] for hf in hist_F[-3:]]))
+        Ft = cfm.capillary_force(f0["q"], gamma, f0["Q"], f0["Q"], L)
+        force.append({"gap_over_R": g, "L": L, "F_sim": Fs, "F_theory": Ft, "ratio": Fs / Ft,
+                      "F_history": [hf[k] for hf in hist_F]})
+    batch.close()
+    line = {"metric": "lateral capillary force of fixed rigid pairs against Eq. 13, and Q, Z against h0",
+            "unit": "ratio F_sim / F_theory", "data": "synthetic", "dtype": "f32",
+            "config": {"workload": f"batch of {len(singles)} single fixed R=10 level-4 particles (128x128x40, "
+                                   f"h0/R in {hs}) and {len(pairs)} fixed pairs ((2L + 64)x96x40, h0 = 0.16R, "
+                                   f"surface gaps {gaps} R)", "steps": done,
+                       "gamma": gamma, "gamma_source": "Laplace test of the oracle at G = 3.6"},
+            "film_height_series": fits, "pair_force": force,
+            "value": float(np.mean([abs(f["ratio"] - 1.0) for f in force])),
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.theory:
+        run_theory(args)
+        return
     if args.warm:
         run_warm(args)
         return
-    if args.sweep:
-        run_sweep(args)
-        return
     if args.impl == "reference":
         run_reference(args)
+    elif args.pair or args.drying:
+        run_single(args)
     else:
         run_ours(args)
 

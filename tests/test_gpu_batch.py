@@ -78,6 +78,25 @@ def test_batch_matches_lone_runs(cfm, config):
     b.close()
 
 
+@pytest.mark.parametrize("groups", [2, 3])
+def test_batch_groups_match_lone_runs(cfm, groups):
+    """Pipeline groups (each group's lattice passes on a stream branch of its
+    own): every lattice still equals its lone run, over an odd step count
+    (graph replays and plain steps)."""
+    wls = mixed_workloads()
+    sims = [cfm.Simulation.from_workload(w) for w in wls]
+    b = cfm.Batch(sims)
+    b.set_groups(groups)
+    assert b.config()["groups"] == groups
+    b.step(25)
+    alone = run_alone(cfm, wls, 25)
+    for s, a in zip(sims, alone):
+        assert rel(s.populations().astype(np.float64), a.populations().astype(np.float64)) < TOL_SAME
+        rs, _ = s.fields(); ra, _ = a.fields()
+        assert rel(rs, ra) < TOL_SAME
+    b.close()
+
+
 @pytest.mark.parametrize("config", [None, (4, 1)])
 def test_batch_with_other_tau_matches_lone_runs(cfm, config):
     """One lattice with tau != 1: the batch takes the general collision for
@@ -131,9 +150,11 @@ def test_batch_autotune(cfm):
     sims = [cfm.Simulation.from_workload(w) for w in wls]
     b = cfm.Batch(sims)
     cfg = b.autotune(steps=2)
-    assert 0 <= cfg["tile"] < 6 and cfg["zchunk"] in (1, 2, 4) and cfg["ms_per_step"] > 0
+    assert 0 <= cfg["tile"] < 6 and cfg["zchunk"] in (2, 4, 8) and cfg["ms_per_step"] > 0
     assert cfg["tile_x"] in (32, 64, 128) and cfg["tile_y"] in (2, 4, 8)
-    done = 18 * (2 + 2)
+    assert cfg["groups"] in (1, 2)
+    # 18 launch shapes with one group, then 2 groups (4 and 8 exceed the 3 lattices)
+    done = (18 + 1) * (2 + 2)
     ref = run_alone(cfm, wls, done)
     for s, a in zip(sims, ref):
         assert rel(s.populations().astype(np.float64), a.populations().astype(np.float64)) < TOL_SAME
