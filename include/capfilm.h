@@ -402,6 +402,74 @@ cf_status cf_adam(float *w, void *w_bf16, const float *g, float *m1, float *m2, 
 cf_status cf_to_bf16(const float *x, void *y, long long n, void *stream);
 cf_status cf_from_bf16(const void *x, float *y, long long n, void *stream);
 
+/* ------------------------------------------------ U-net layers (tensor cores)
+ * Layers of the warm start's 3-D U-net (the paper has no counterpart; see the
+ * warm start above).  Activations are channels-last bfloat16
+ * [n][nz][ny][nx][c]; weights bfloat16 [27][cout][cin] (tap = (dz+1)*9 +
+ * (dy+1)*3 + (dx+1)); biases and gradients float32.  Every pointer is a
+ * device pointer owned by the caller; calls are asynchronous on `stream`;
+ * bad shapes return CF_EINVAL (text in cf_last_error).
+ *
+ * cf_unet_conv: 3x3x3 convolution, zero padding, y = act(b + conv(w, x)),
+ * act = ReLU when relu != 0; contracted on the tensor cores (mma.sync
+ * m16n8k16, bf16 products, fp32 accumulation).  cin a multiple of 16, cout
+ * of 8; b may be NULL; y is float32 when out_f32 != 0, else bfloat16. */
+cf_status cf_unet_conv(const void *x, int n, int nz, int ny, int nx, int cin, const void *w, const float *b,
+                       int cout, int relu, int out_f32, void *y, void *stream);
+/* wt[26 - t][ci][co] = w[t][co][ci]: with wt as weights, cf_unet_conv of an
+ * output gradient (cout channels) gives the input gradient (cin channels). */
+cf_status cf_unet_flip(const void *w, int cin, int cout, void *wt, void *stream);
+/* Weight and bias gradients for the output gradient gy (bfloat16, cout
+ * channels, already masked by the ReLU) and the layer input x: ADDS
+ * sum_v gy[v][co] x[v + off(t)][ci] to gw [27][cout][cin] and sum_v gy[v][co]
+ * to gb [cout] (gb may be NULL).  The voxels are split into `chunks` ranges;
+ * part (at least chunks * 27 * cout * cin floats) receives each range's sums,
+ * which are then added in a fixed order: the result is bitwise reproducible.
+ * cin a multiple of 16, cout of 8. */
+cf_status cf_unet_wgrad(const void *x, const void *gy, int n, int nz, int ny, int nx, int cin, int cout,
+                        int chunks, float *part, float *gw, float *gb, void *stream);
+/* out[i] = bf16((g[i] + g2[i]) * (y[i] > 0)) (ReLU mask of the layer's
+ * output y, bfloat16; no mask when y is NULL; g2 NULL counts as zero), m
+ * elements: the gradient of an activation that feeds two layers is the sum. */
+cf_status cf_unet_relu_grad(const float *g, const float *g2, const void *y, long long m, void *out,
+                            void *stream);
+/* Training loss of the U-net's head out (float [n][nz][ny][nx][ch], ch >= 5:
+ * channels 0, 1 the density corrections of A and B, channels 2..4 a
+ * displacement field) and its gradient g (same shape; channels beyond 4
+ * zero).  ADDS to *loss (device double):
+ *   wd * sum_{s,c,v} mask[s][v] (out[s][v][c] - t[s][c][v])^2   (t [n][2][V],
+ *   mask [n][V]; pass wd = weight / mask sum), plus, when nodes > 0 and
+ *   wx > 0, wx / (n nodes) * sum_{s,i} |D_s(X[s][i]) - d[s][i]|^2, D_s the
+ *   displacement channels interpolated trilinearly at the node's reference
+ *   position X[s][i] (lattice units, float [n][nodes][3], clamped into the
+ *   grid) and d the target displacement (float [n][nodes][3]).
+ * part: device scratch of at least 304 + n doubles.  Sums are taken in a
+ * fixed order (the node gradient by one thread per sample walking its nodes),
+ * so the result is bitwise reproducible. */
+cf_status cf_unet_loss(const float *out, int n, int nz, int ny, int nx, int ch, const float *t,
+                       const float *mask, double wd, const float *X, const float *d, int nodes, double wx,
+                       double *part, float *g, double *loss, void *stream);
+/* 2x2x2 average pooling of x (bfloat16, fine grid nz x ny x nx, each even)
+ * into y, and its gradient (float: gx from the coarse gradient gy). */
+cf_status cf_unet_pool(const void *x, int n, int nz, int ny, int nx, int c, void *y, void *stream);
+cf_status cf_unet_pool_bwd(const float *gy, int n, int nz, int ny, int nx, int c, float *gx, void *stream);
+/* Nearest-neighbour upsampling by 2 of x (bfloat16, coarse grid) to the fine
+ * grid nz x ny x nx (each even), and its gradient (float). */
+cf_status cf_unet_upsample(const void *x, int n, int nz, int ny, int nx, int c, void *y, void *stream);
+cf_status cf_unet_upsample_bwd(const float *gy, int n, int nz, int ny, int nx, int c, float *gx,
+                               void *stream);
+/* Channel concatenation y[v] = (a[v][0..ca), b[v][0..cb)) of nv voxels
+ * (bfloat16), and the split of a float gradient (a or b may be NULL). */
+cf_status cf_unet_concat(long long nv, const void *a, int ca, const void *b, int cb, void *y, void *stream);
+cf_status cf_unet_split(long long nv, const float *y, int ca, int cb, float *a, float *b, void *stream);
+/* Layout changes for one sample: pack channel-first float [c][N] into
+ * channels-last bfloat16 [N][cpad] (zero channels beyond c); unpack channels
+ * [c0, c0 + c) of channels-last [N][cpad] (bfloat16, or float when x_f32)
+ * into channel-first float [c][N]. */
+cf_status cf_unet_pack(const float *x, int c, long long N, int cpad, void *y, void *stream);
+cf_status cf_unet_unpack(const void *x, int x_f32, int cpad, long long N, int c0, int c, float *y,
+                         void *stream);
+
 /* Set-up of the warm start on a context (after its capsules are added; all
  * arrays are device arrays of the caller, [c][nz][ny][nx] float32; the film
  * is the one cf_set_film(h_top, rho_maj, rho_min, rho_mix) would make, and

@@ -5,9 +5,12 @@ runs the CUDA kernels.  Each function is the plain definition of the
 operation, written with numpy:
 
   conv3d   y[n, co, v] = b[co] + sum_ci sum_t w[co, ci, t] x[n, ci, v + dil * off(t)]
+           (conv3d_cl: the same in the channels-last layout of the U-net)
            (zero outside the grid; off(t) = (t//9 - 1, (t//3)%3 - 1, t%3 - 1) in
            (z, y, x)), then max(0, .) when relu
   backward gx = dL/dx, gw = dL/dw, gb = dL/db for dL/dy = gy (ReLU mask from y)
+  pool     mean over 2 x 2 x 2 blocks; upsample: nearest neighbour by 2; and
+           their adjoints (the gradients)
   mse      L = sum_i m_i (p_i - t_i)^2 / msum,  dL/dp_i = 2 m_i (p_i - t_i) / msum
   adam     Kingma & Ba (2015), bias-corrected moments
 
@@ -64,6 +67,51 @@ def conv3d_backward(x, w, dil, y, relu, gy):
         gx += np.einsum("oc,nozyx->nczyx", w[:, :, t], _shifted(g, -dz, -dy, -dx))
     gb = g.sum(axis=(0, 2, 3, 4))
     return gx, gw, gb
+
+
+def conv3d_cl(x, w, b, relu):
+    """Channels-last layer of the U-net: x [n][nz][ny][nx][cin], w [27][cout][cin]
+    (tap-major), b [cout] -> y [n][nz][ny][nx][cout]; the same operation as
+    conv3d (dilation 1) in another memory layout."""
+    xc = np.moveaxis(np.asarray(x, np.float64), -1, 1)
+    wc = np.transpose(np.asarray(w, np.float64), (1, 2, 0))
+    return np.moveaxis(conv3d(xc, wc, b, 1, relu), 1, -1)
+
+
+def conv3d_cl_backward(x, w, y, relu, gy):
+    """Gradients (gx, gw [27][cout][cin], gb) of conv3d_cl for dL/dy = gy."""
+    xc = np.moveaxis(np.asarray(x, np.float64), -1, 1)
+    wc = np.transpose(np.asarray(w, np.float64), (1, 2, 0))
+    yc = np.moveaxis(np.asarray(y, np.float64), -1, 1)
+    gc = np.moveaxis(np.asarray(gy, np.float64), -1, 1)
+    gx, gw, gb = conv3d_backward(xc, wc, 1, yc, relu, gc)
+    return np.moveaxis(gx, 1, -1), np.transpose(gw, (2, 0, 1)), gb
+
+
+def avg_pool2(x):
+    """Mean over 2 x 2 x 2 blocks of a channels-last [n][nz][ny][nx][c] field."""
+    x = np.asarray(x, np.float64)
+    n, nz, ny, nx, c = x.shape
+    return x.reshape(n, nz // 2, 2, ny // 2, 2, nx // 2, 2, c).mean(axis=(2, 4, 6))
+
+
+def avg_pool2_backward(gy):
+    """Adjoint of avg_pool2: each fine voxel gets 1/8 of its block's gradient."""
+    g = np.asarray(gy, np.float64)
+    return np.repeat(np.repeat(np.repeat(g, 2, axis=1), 2, axis=2), 2, axis=3) / 8.0
+
+
+def upsample2(x):
+    """Nearest-neighbour upsampling by 2 in z, y and x (channels-last)."""
+    x = np.asarray(x, np.float64)
+    return np.repeat(np.repeat(np.repeat(x, 2, axis=1), 2, axis=2), 2, axis=3)
+
+
+def upsample2_backward(gy):
+    """Adjoint of upsample2: each coarse voxel sums its eight fine ones."""
+    g = np.asarray(gy, np.float64)
+    n, nz, ny, nx, c = g.shape
+    return g.reshape(n, nz // 2, 2, ny // 2, 2, nx // 2, 2, c).sum(axis=(2, 4, 6))
 
 
 def mse(pred, target, mask=None):

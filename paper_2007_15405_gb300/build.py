@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcapfilm.so")
-SOURCES = ["lb_kernel.cu", "membrane_kernels.cu", "capfilm_api.cu", "warm_kernels.cu"]
+SOURCES = ["lb_kernel.cu", "membrane_kernels.cu", "capfilm_api.cu", "warm_kernels.cu", "unet_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 # extra nvcc flags for tuning builds (e.g. "-DCF_COLLIDE_MINB=6"); a change of

@@ -124,6 +124,27 @@ def load_library(path: Optional[str] = None):
         "cf_warm_apply": [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p],
         "cf_warm_target": [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p],
         "cf_field_check": [C.c_void_p, _dp],
+        "cf_unet_conv": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                         C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+        "cf_unet_flip": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+        "cf_unet_wgrad": [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                          C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+        "cf_unet_relu_grad": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p],
+        "cf_unet_loss": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                         C.c_double, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p,
+                         C.c_void_p, C.c_void_p],
+        "cf_unet_pool": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+        "cf_unet_pool_bwd": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                             C.c_void_p],
+        "cf_unet_upsample": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                             C.c_void_p],
+        "cf_unet_upsample_bwd": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                 C.c_void_p],
+        "cf_unet_concat": [C.c_longlong, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+        "cf_unet_split": [C.c_longlong, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p],
+        "cf_unet_pack": [C.c_void_p, C.c_int, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p],
+        "cf_unet_unpack": [C.c_void_p, C.c_int, C.c_int, C.c_longlong, C.c_int, C.c_int, C.c_void_p,
+                           C.c_void_p],
         "cf_meniscus_fit": [_dp, _dp, C.c_size_t, C.c_double, C.c_double, _dp],
         "cf_capillary_force": [C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _dp],
     }
@@ -146,7 +167,9 @@ def exported_symbols():
             "cf_batch_lateral_forces", "cf_warm_features", "cf_warm_apply", "cf_warm_target",
             "cf_field_check", "cf_conv3d_forward",
             "cf_conv3d_backward", "cf_mse", "cf_adam", "cf_to_bf16", "cf_from_bf16",
-            "cf_meniscus_fit", "cf_capillary_force"]
+            "cf_meniscus_fit", "cf_capillary_force", "cf_unet_conv", "cf_unet_flip", "cf_unet_wgrad",
+            "cf_unet_relu_grad", "cf_unet_loss", "cf_unet_pool", "cf_unet_pool_bwd", "cf_unet_upsample",
+            "cf_unet_upsample_bwd", "cf_unet_concat", "cf_unet_split", "cf_unet_pack", "cf_unet_unpack"]
 
 
 def _check(rc):

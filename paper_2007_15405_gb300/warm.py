@@ -312,3 +312,132 @@ def convergence(net, wls, total=8000, every=50, tol=0.01):
         s.close()
     timing = dict(warm_start_seconds=t_warm / len(wls), step_seconds=t_plain / (total * len(wls)))
     return res, timing
+
+
+# ----------------------------------------------------------- the U-net path
+# The 3-D U-net (unet.py) trained on the sweep's generator: capsule pairs at
+# distances 2.2R..6R with moduli 1e-3..1e-1 or rigid and films 0.2R..0.6R.
+# Its density head gives the warm start of the coupled run (set up and judged
+# as above); its displacement head the deformation of free capsules.
+
+def pair_dataset(wls_fixed, wls_free, eq_steps, def_steps):
+    """Training data of the U-net generated by the method.  Per set-up: the
+    network inputs [4][V], density targets [2][V] and fluid mask [V] of the
+    fixed-capsule run after eq_steps; the capsules' reference node positions
+    [nodes][3] (lattice units) and their deformation after def_steps of the
+    free run (each node's displacement minus its capsule's mean displacement)
+    [nodes][3]."""
+    sims = equilibrate(wls_fixed, eq_steps)
+    X, T, M = [], [], []
+    for s, w in zip(sims, wls_fixed):
+        x, mask = features(s, w)
+        X.append(x.reshape(N_IN, -1))
+        T.append(target_of(s, w).reshape(N_OUT, -1))
+        M.append(mask.reshape(-1))
+        s.close()
+    free = equilibrate(wls_free, def_steps)
+    Xn, D = [], []
+    for s, w in zip(free, wls_free):
+        ref, dis = [], []
+        for k, cap in enumerate(w.capsules):
+            X0, _ = cap.mesh()
+            X1 = s.capsule_state(k)["X"]
+            ref.append(X0)
+            dis.append((X1 - X1.mean(0)) - (X0 - X0.mean(0)))
+        Xn.append(np.concatenate(ref))
+        D.append(np.concatenate(dis))
+        s.close()
+    f32 = lambda a: np.ascontiguousarray(np.stack(a), np.float32)  # noqa: E731
+    return dict(X=f32(X), T=f32(T), M=f32(M), Xn=f32(Xn), D=f32(D),
+                shape=(wls_fixed[0].nz, wls_fixed[0].ny, wls_fixed[0].nx))
+
+
+def train_unet(net, data, steps, batch=4, lr=1e-3, wx=1.0, seed=0, log=None):
+    """Adam on mini-batches of the U-net data; returns the losses."""
+    torch = net.torch
+    from . import unet as U
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = data["shape"]
+    V = nz * ny * nx
+    n, nodes = data["X"].shape[0], data["Xn"].shape[1]
+    dev = net.dev
+    losses = []
+    for it in range(steps):
+        idx = np.sort(rng.choice(n, size=min(batch, n), replace=False))
+        b = len(idx)
+        xf = torch.from_numpy(data["X"][idx]).to(dev)
+        x = torch.empty(b * V * U.CIN, dtype=torch.bfloat16, device=dev)
+        for k in range(b):
+            cfm._check(cfm._lib.cf_unet_pack(_p(xf[k]), U.N_FEAT, V, U.CIN, _p(x[k * V * U.CIN:]),
+                                             C.c_void_p(net.stream)))
+        t = torch.from_numpy(data["T"][idx]).to(dev)
+        m = torch.from_numpy(data["M"][idx]).to(dev)
+        Xn = torch.from_numpy(data["Xn"][idx]).to(dev)
+        D = torch.from_numpy(data["D"][idx]).to(dev)
+        loss = net.train_step(x, (b, nz, ny, nx), t, m, float(data["M"][idx].sum()), Xn, D, nodes, lr=lr,
+                              wd=1.0, wx=wx)
+        losses.append(loss)
+        if log and it % 50 == 0:
+            log(f"step {it}: loss {loss:.4e}")
+    return losses
+
+
+def sample_field(field, X):
+    """Trilinear samples of a vector field [3][nz][ny][nx] at positions X
+    [k][3] (lattice units, clamped into the grid) -> [k][3] (host)."""
+    c, nz, ny, nx = field.shape
+    p = np.clip(X, 0, [nx - 1.001, ny - 1.001, nz - 1.001])
+    i0 = np.floor(p).astype(int)
+    f = p - i0
+    out = np.zeros((X.shape[0], c))
+    for k in range(8):
+        dx, dy, dz = k & 1, (k >> 1) & 1, k >> 2
+        wgt = (f[:, 0] if dx else 1 - f[:, 0]) * (f[:, 1] if dy else 1 - f[:, 1]) * (f[:, 2] if dz else 1 - f[:, 2])
+        out += wgt[:, None] * field[:, i0[:, 2] + dz, i0[:, 1] + dy, i0[:, 0] + dx].T
+    return out
+
+
+def lateral_traces(sims, total, every):
+    """Lateral force between capsules 0 and 1 of every simulation every
+    `every` steps (one batch); returns ([len(sims)][total // every], seconds
+    per lattice step)."""
+    import time
+    batch = cfm.Batch(sims)
+    out = []
+    t0 = time.perf_counter()
+    for _ in range(total // every):
+        batch.step(every)
+        out.append(batch.lateral_forces(0, 1))
+    dt = time.perf_counter() - t0
+    batch.close()
+    return np.array(out).T, dt / (total * len(sims))
+
+
+def time_to_force(net, wls, total, every, tol=0.01):
+    """Plain (flat film) and warm-started runs of the pair set-ups wls in
+    batches: the steps after which the lateral force stays within tol of its
+    converged value (the mean of the plain run's last five samples), whether
+    each warm start was kept, and the wall times (one warm start; one
+    lattice step within the batch)."""
+    import time
+    plain = [cfm.Simulation.from_workload(w) for w in wls]
+    warmed, used = [], []
+    t_warm = 0.0
+    for w in wls:
+        s = cfm.Simulation.from_workload(w)
+        t0 = time.perf_counter()
+        u, _ = warm_start(s, w, net)
+        s.sync()
+        t_warm += time.perf_counter() - t0
+        warmed.append(s)
+        used.append(u)
+    fp, step_plain = lateral_traces(plain, total, every)
+    fw, step_warm = lateral_traces(warmed, total, every)
+    res = []
+    for k in range(len(wls)):
+        f_eq = fp[k, -5:].mean()
+        res.append(dict(plain=settle_step(fp[k], every, f_eq, tol), warm=settle_step(fw[k], every, f_eq, tol),
+                        kept=bool(used[k]), f_eq=float(f_eq), f_warm_end=float(fw[k, -1])))
+    for s in plain + warmed:
+        s.close()
+    return res, dict(warm_start_seconds=t_warm / len(wls), step_seconds=step_plain, step_seconds_warm=step_warm)

@@ -103,3 +103,57 @@ def test_bf16_rounding():
     assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0 + 2 ** -6
     assert r[3] == -2.5
     assert abs(r[4] - 1e-30) / 1e-30 < 2 ** -8
+
+
+# ---------------------------------------------------- U-net layers (channels-last)
+def test_pool_and_upsample_identities():
+    """Pooling an upsampled field returns it exactly; upsampling a constant
+    gives the constant; pooling a field linear in z gives the mean of each
+    block's two planes."""
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((2, 3, 4, 5, 6))
+    assert np.allclose(W.avg_pool2(W.upsample2(x)), x, atol=1e-15)
+    c = np.full((1, 2, 2, 2, 3), 2.5)
+    assert np.array_equal(W.upsample2(c), np.full((1, 4, 4, 4, 3), 2.5))
+    z = np.arange(8.0)[None, :, None, None, None] * np.ones((1, 8, 4, 4, 2))
+    assert np.allclose(W.avg_pool2(z)[0, :, 0, 0, 0], [0.5, 2.5, 4.5, 6.5])
+
+
+def test_pool_upsample_backward_are_adjoints():
+    """<op(x), g> = <x, op_backward(g)> for both operators (pins the gradients
+    to the forward definitions)."""
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal((2, 4, 6, 8, 3))
+    g = rng.standard_normal((2, 2, 3, 4, 3))
+    assert np.isclose(np.sum(W.avg_pool2(x) * g), np.sum(x * W.avg_pool2_backward(g)), rtol=1e-13)
+    xc = rng.standard_normal((2, 2, 3, 4, 3))
+    gf = rng.standard_normal((2, 4, 6, 8, 3))
+    assert np.isclose(np.sum(W.upsample2(xc) * gf), np.sum(xc * W.upsample2_backward(gf)), rtol=1e-13)
+
+
+def test_channels_last_conv_matches_definition_by_finite_differences():
+    """conv3d_cl_backward against central differences of a loss through one
+    channels-last layer (ReLU on), for an input, a weight and a bias entry."""
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal((1, 3, 4, 5, 2))
+    w = rng.standard_normal((27, 3, 2)) * 0.3
+    b = rng.standard_normal(3) * 0.1
+    gy = rng.standard_normal((1, 3, 4, 5, 3))
+
+    def L(x_, w_, b_):
+        return float(np.sum(W.conv3d_cl(x_, w_, b_, True) * gy))
+
+    y = W.conv3d_cl(x, w, b, True)
+    gx, gw, gb = W.conv3d_cl_backward(x, w, y, True, gy)
+    h = 1e-6
+    for idx in [(0, 1, 2, 3, 1), (0, 0, 0, 0, 0)]:
+        xp = x.copy(); xp[idx] += h
+        xm = x.copy(); xm[idx] -= h
+        assert np.isclose((L(xp, w, b) - L(xm, w, b)) / (2 * h), gx[idx], rtol=1e-5, atol=1e-8)
+    for idx in [(13, 2, 1), (0, 0, 0)]:
+        wp = w.copy(); wp[idx] += h
+        wm = w.copy(); wm[idx] -= h
+        assert np.isclose((L(x, wp, b) - L(x, wm, b)) / (2 * h), gw[idx], rtol=1e-5, atol=1e-8)
+    bp = b.copy(); bp[1] += h
+    bm = b.copy(); bm[1] -= h
+    assert np.isclose((L(x, w, bp) - L(x, w, bm)) / (2 * h), gb[1], rtol=1e-5, atol=1e-8)
