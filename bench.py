@@ -65,6 +65,17 @@ def parse():
     ap.add_argument("--theory", action="store_true",
                     help="theory check: meniscus fits over film heights and rigid-pair forces vs Eq. 13")
     ap.add_argument("--theory-steps", type=int, default=40000)
+    ap.add_argument("--theory-box", type=int, default=128,
+                    help="lateral size of the single-particle boxes and y size of the pair boxes")
+    ap.add_argument("--approach", action="store_true",
+                    help="approach dynamics of two free soft particles (gap against time)")
+    ap.add_argument("--approach-steps", type=int, default=40000)
+    ap.add_argument("--warm-train", type=int, default=96, help="training set-ups of the warm start")
+    ap.add_argument("--warm-eq", type=int, default=4000, help="equilibration steps of the training data")
+    ap.add_argument("--warm-def", type=int, default=1000, help="free steps of the deformation data")
+    ap.add_argument("--warm-steps", type=int, default=300, help="Adam steps")
+    ap.add_argument("--warm-total", type=int, default=20000, help="steps of the time-to-force runs")
+    ap.add_argument("--warm-every", type=int, default=200, help="lateral-force sampling interval")
     ap.add_argument("--drying", action="store_true",
                     help="drying film with 16 capsules (256x256x96) instead of the sweep")
     return ap.parse_args()
@@ -473,60 +484,85 @@ def run_reference(args):
 
 
 def run_warm(args):
+    """Learned warm start (the U-net) and the time to an equilibrated lateral
+    force with warm start plus batching against the plain batched FP32 run."""
     import torch
     from paper_2007_15405_gb300 import build as B
     B.build()
     from paper_2007_15405_gb300 import inputs as I
+    from paper_2007_15405_gb300 import unet as U
     from paper_2007_15405_gb300 import warm
     torch.cuda.set_device(0)
-    # fixed capsules: their capillary force settles when the film does, so
-    # the time to 1% of the equilibrium force is well defined
-    n_train, n_test, eq_steps, total, every = 48, 32, 3000, 8000, 50
+    out = warm_measure(args, I, U, warm)
+    print(json.dumps(out), flush=True)
+
+
+def warm_measure(args, I, U, warm):
+    """Data from the method, training, held-out errors and the time-to-force
+    comparison (see run_warm); returns the result dict."""
+    import torch
+    n_train, eq, dfs = args.warm_train, args.warm_eq, args.warm_def
     t0 = time.perf_counter()
-    X, T, M = warm.dataset(I.warm_dataset(n_train, seed=11, mode=I.MODE_FIXED), eq_steps)
+    data = warm.pair_dataset(I.warm_pair_dataset(n_train, seed=11, mode=I.MODE_FIXED),
+                             I.warm_pair_dataset(n_train, seed=11, mode=I.MODE_FREE), eq, dfs)
     t_data = time.perf_counter() - t0
-    net = warm.WarmNet(seed=0)
+    net = U.UNet(seed=0)
     t0 = time.perf_counter()
-    losses = warm.train(net, X, T, M, steps=400, batch=8, lr=2e-3)
+    losses = warm.train_unet(net, data, steps=args.warm_steps, batch=4, lr=1e-3, wx=1.0)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    test = I.warm_dataset(n_test, seed=99, mode=I.MODE_FIXED)
-    err_p, err_w = [], []
-    Xh, Th, Mh = warm.dataset(test, eq_steps)
-    for k in range(n_test):
-        pred = net.predict(Xh[k])
-        err_p.append(float(np.sqrt((Th[k] ** 2 * Mh[k]).sum() / Mh[k].sum())))
-        err_w.append(float(np.sqrt(((pred - Th[k]) ** 2 * Mh[k]).sum() / Mh[k].sum())))
-    res, timing = warm.convergence(net, test, total=total, every=every)
-    sp = [r[0] for r in res]
-    sw = [r[1] for r in res]
-    both = [(a, b) for a, b in zip(sp, sw) if a is not None and b is not None]
-    line = {
-        "metric": "steps to capsule force within 1% of equilibrium, learned warm start vs flat film",
-        "unit": "steps", "higher_is_better": False, "data": "synthetic", "dtype": "bf16 network / f32 lattice",
-        "config": {"workload": f"{n_test} held-out lattices 48x32x32, one fixed capsule R in [5, 7] "
-                               "(level 3), film 0.3R..0.9R above the repulsive plane; network trained on "
-                               f"{n_train} equilibria of {eq_steps} steps; settling judged over {total} "
-                               f"steps sampled every {every}"},
-        "network": {"params": net.n_params, "train_steps": len(losses), "loss_first": losses[0],
+    # held-out set-ups of the same generator
+    hold = warm.pair_dataset(I.warm_pair_dataset(16, seed=99, mode=I.MODE_FIXED),
+                             I.warm_pair_dataset(16, seed=99, mode=I.MODE_FREE), eq, dfs)
+    nz, ny, nx = hold["shape"]
+    e_flat, e_warm, d_rms, d_err = [], [], [], []
+    for k in range(hold["X"].shape[0]):
+        dens, disp = net.predict_both(torch.from_numpy(hold["X"][k]).cuda(), hold["shape"])
+        pr = dens.cpu().numpy().reshape(2, -1)
+        T, M = hold["T"][k], hold["M"][k]
+        e_flat.append(float(np.sqrt((T ** 2 * M).sum() / (2 * M.sum()))))
+        e_warm.append(float(np.sqrt(((pr - T) ** 2 * M).sum() / (2 * M.sum()))))
+        D = warm.sample_field(disp.cpu().numpy().reshape(3, nz, ny, nx), hold["Xn"][k].astype(np.float64))
+        d_rms.append(float(np.sqrt((hold["D"][k] ** 2).sum(1).mean())))
+        d_err.append(float(np.sqrt(((D - hold["D"][k]) ** 2).sum(1).mean())))
+    # time to force on the sweep's lattices (one per distance), fixed capsules
+    wls = [w for i, w in enumerate(I.batched_sweep(mode=I.MODE_FIXED)) if i % 4 == 0]
+    res, timing = warm.time_to_force(net, wls, total=args.warm_total, every=args.warm_every)
+    both = [r for r in res if r["plain"] is not None and r["warm"] is not None]
+    sp = float(np.mean([r["plain"] for r in both])) if both else None
+    sw = float(np.mean([r["warm"] for r in both])) if both else None
+    judge = 51  # the warm start's judging steps (two windows of 25 after one step)
+    return {
+        "metric": "time to the lateral capillary force within 1% of the converged plain-FP32 value, "
+                  "learned warm start + batching vs plain (flat film) + batching",
+        "unit": "s per lattice", "higher_is_better": False, "data": "synthetic",
+        "dtype": "bf16 network (fp32 accumulation on the tensor cores) / f32 lattice",
+        "config": {"workload": f"{len(wls)} lattices of the batched sweep (one per capsule distance 2.2R..6R, "
+                               "64..160 x 48 x 48, two fixed R=10 level-4 capsules, film 0.4R), stepped as "
+                               f"one batch for {args.warm_total} steps, lateral force sampled every "
+                               f"{args.warm_every}",
+                   "training": f"{n_train} pair set-ups of the sweep's generator (128x64x48, d in [2.2R, 6R], "
+                               f"kS in [1e-3, 1e-1] or rigid, film 0.2R..0.6R), densities after {eq} steps "
+                               f"with fixed capsules, deformations after {dfs} steps with free ones; "
+                               f"{args.warm_steps} Adam steps of 4 set-ups"},
+        "network": {"params": net.n_params, "widths": list(net.widths), "loss_first": losses[0],
                     "loss_last": losses[-1], "train_seconds": t_train, "data_seconds": t_data},
-        "density_rms_error": {"flat_film": float(np.mean(err_p)), "warm": float(np.mean(err_w)),
-                              "unit": "(rho_maj - rho_min), against the equilibria"},
-        "settle_steps": {"flat_film_mean": float(np.mean([a for a, _ in both])) if both else None,
-                         "warm_mean": float(np.mean([b for _, b in both])) if both else None,
-                         "pairs": len(both), "flat_film_unsettled": sum(a is None for a in sp),
-                         "warm_unsettled": sum(b is None for b in sw)},
-        "fallbacks": sum(not r[2] for r in res),
+        "held_out": {"set_ups": len(e_flat), "density_rms_flat_film": float(np.mean(e_flat)),
+                     "density_rms_warm": float(np.mean(e_warm)),
+                     "deformation_rms": float(np.mean(d_rms)), "deformation_rms_error": float(np.mean(d_err)),
+                     "unit": "densities in rho_maj - rho_min, deformations in lattice units"},
+        "settle_steps": {"plain_mean": sp, "warm_mean": (sw + judge) if sw is not None else None,
+                         "pairs": len(both), "plain_unsettled": sum(r["plain"] is None for r in res),
+                         "warm_unsettled": sum(r["warm"] is None for r in res),
+                         "fallbacks": sum(not r["kept"] for r in res), "per_lattice": res},
         "time_to_force_seconds": ({
-            "flat_film": float(np.mean([a for a, _ in both])) * timing["step_seconds"],
-            "warm": float(np.mean([b for _, b in both])) * timing["step_seconds"] + timing["warm_start_seconds"],
-            "step_seconds_per_lattice": timing["step_seconds"],
-            "warm_start_seconds": timing["warm_start_seconds"],
-            "note": f"per lattice within a batch of {n_test}; the warm start (inference, predicted state, "
-                    "51 judging steps run alone) is counted, the offline training is not"} if both else None),
-        "value": float(np.mean([b for _, b in both])) if both else None,
+            "plain": sp * timing["step_seconds"],
+            "warm": (sw + judge) * timing["step_seconds_warm"] + timing["warm_start_seconds"],
+            **timing,
+            "note": "per lattice within the batch; the warm start (inference, predicted state, judging "
+                    "steps run alone) is counted, the offline training is not"} if both else None),
+        "value": ((sw + judge) * timing["step_seconds_warm"] + timing["warm_start_seconds"]) if both else None,
     }
-    print(json.dumps(line), flush=True)
 
 
 def gamma_g36():
@@ -553,8 +589,8 @@ def run_theory(args):
     R = 10.0
     hs = [0.16, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9]
     gaps = [3.0, 4.0, 5.0, 6.0, 7.0]
-    singles = [I.rigid_particle(h, R) for h in hs]
-    pairs = [I.rigid_pair(g, 0.16, R) for g in gaps]
+    singles = [I.rigid_particle(h, R, nx=args.theory_box, ny=args.theory_box) for h in hs]
+    pairs = [I.rigid_pair(g, 0.16, R, ny=args.theory_box) for g in gaps]
     wls = singles + pairs
     sims = [cfm.Simulation.from_workload(w) for w in wls]
     batch = cfm.Batch(sims)
@@ -588,8 +624,9 @@ def run_theory(args):
     batch.close()
     line = {"metric": "lateral capillary force of fixed rigid pairs against Eq. 13, and Q, Z against h0",
             "unit": "ratio F_sim / F_theory", "data": "synthetic", "dtype": "f32",
-            "config": {"workload": f"batch of {len(singles)} single fixed R=10 level-4 particles (128x128x40, "
-                                   f"h0/R in {hs}) and {len(pairs)} fixed pairs ((2L + 64)x96x40, h0 = 0.16R, "
+            "config": {"workload": f"batch of {len(singles)} single fixed R=10 level-4 particles "
+                                   f"({args.theory_box}x{args.theory_box}x40, h0/R in {hs}) and {len(pairs)} fixed "
+                                   f"pairs ((2L + 64)x{args.theory_box}x40, h0 = 0.16R, "
                                    f"surface gaps {gaps} R)", "steps": done,
                        "gamma": gamma, "gamma_source": "Laplace test of the oracle at G = 3.6"},
             "film_height_series": fits, "pair_force": force,
@@ -598,8 +635,51 @@ def run_theory(args):
     print(json.dumps(line), flush=True)
 
 
+def surface_gap(Xa, Xb):
+    """Smallest distance between the nodes of two meshes (the surface gap)."""
+    d2 = ((Xa[:, None, :] - Xb[None, :, :]) ** 2).sum(-1)
+    return float(np.sqrt(d2.min()))
+
+
+def run_approach(args):
+    """Approach dynamics of two free soft particles (Sec. 4.6): the surface
+    gap against time for softness beta = 10, 25, 50, starting at 2R in a film
+    0.4R above the repulsive plane (one batch)."""
+    import torch
+    from paper_2007_15405_gb300 import build as B
+    B.build()
+    from paper_2007_15405_gb300 import capfilm as cfm
+    from paper_2007_15405_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    betas = (10.0, 25.0, 50.0)
+    wls = [I.approach_pair(b) for b in betas]
+    sims = [cfm.Simulation.from_workload(w) for w in wls]
+    batch = cfm.Batch(sims)
+    every = max(1, args.approach_steps // 40)
+    hist = [[surface_gap(s.capsule_state(0)["X"], s.capsule_state(1)["X"]) for s in sims]]
+    t0 = time.perf_counter()
+    for _ in range(args.approach_steps // every):
+        batch.step(every)
+        hist.append([surface_gap(s.capsule_state(0)["X"], s.capsule_state(1)["X"]) for s in sims])
+    wall = time.perf_counter() - t0
+    batch.close()
+    hist = np.array(hist)
+    line = {"metric": "surface gap of two free soft particles against time", "unit": "lattice units",
+            "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "two free R=10 level-4 capsules, initial gap 2R, film 0.4R, 128x64x48, "
+                                   "nu_s = 0.9 (C = 9), kS = 5e-3, kB = R^2 gamma / beta",
+                       "steps": args.approach_steps, "every": every},
+            "gap": {f"beta={b:g}": hist[:, k].tolist() for k, b in enumerate(betas)},
+            "final_gap": {f"beta={b:g}": float(hist[-1, k]) for k, b in enumerate(betas)},
+            "wall_s": wall, "value": float(hist[-1, 0])}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.approach:
+        run_approach(args)
+        return
     if args.theory:
         run_theory(args)
         return

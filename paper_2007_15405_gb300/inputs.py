@@ -303,3 +303,48 @@ def warm_dataset(n: int, seed: int = 0, nx: int = 48, ny: int = 32, nz: int = 32
         out.append(Workload(f"warm {i} R={R:.2f} kS={kS:.1e} h={h_top:.2f}", nx, ny, nz, h_top=h_top,
                             capsules=[cap], steps=1, seed=5000 + i))
     return out
+
+
+def warm_pair_dataset(n: int, seed: int = 0, nx: int = 128, ny: int = 64, nz: int = 48, radius: float = 10.0,
+                      level: int = 4, mode: int = MODE_FIXED) -> List[Workload]:
+    """Set-ups of the sweep's generator for training the warm start: a
+    capsule pair (R = 10 level-4 icospheres) at a centre distance uniform in
+    [2.2R, 6R], a shear modulus log-uniform in [1e-3, 1e-1] or rigid (one
+    set-up in four), a film uniform in [0.2R, 0.6R] above the repulsive plane,
+    on one lattice shape (128 x 64 x 48: every lattice of a training batch has
+    the same shape).  A rigid pair is given kS = 1 (far stiffer than the soft
+    range, so its shape does not change and its modulus feature is distinct).
+    mode: the capsules' mode (fixed for the equilibrated densities, free for
+    the deformation)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        d_over_R = float(rng.uniform(2.2, 6.0))
+        rigid = rng.random() < 0.25
+        kS = 1.0 if rigid else float(10 ** rng.uniform(-3.0, -1.0))
+        h = float(rng.uniform(0.2, 0.6))
+        w = sweep_point(d_over_R, kS, nx, ny, nz, radius=radius, level=level, seed=7000 + 31 * seed + i,
+                        h_frac=h, mode=mode)
+        w.name = f"warm pair {i} d={d_over_R:.2f}R kS={'rigid' if rigid else f'{kS:.1e}'} h0={h:.2f}R"
+        out.append(w)
+    return out
+
+
+GAMMA_G36 = 0.048812802376  # surface tension at G = 3.6 (oracle Laplace test, tests/golden)
+
+
+def approach_pair(beta: float, gap_over_R: float = 2.0, h_frac: float = 0.4, radius: float = 10.0,
+                  level: int = 4, nx: int = 128, ny: int = 64, nz: int = 48, steps: int = 40000,
+                  kS: float = 5e-3, seed: int = 4323) -> Workload:
+    """Two free soft particles (Sec. 4.6, approach dynamics): spheres of
+    radius R at surface gap gap_over_R * R along x in a film h_frac R above
+    the repulsive plane, softness beta = R^2 gamma / kB (kB from beta and the
+    surface tension at G = 3.6), Poisson ratio 0.9 (C = 9), shear modulus kS."""
+    kB = radius * radius * GAMMA_G36 / beta
+    L = gap_over_R * radius + 2.0 * radius
+    zc = z_rest(radius) + _OFF[2]
+    cx, cy = nx / 2 + _OFF[0], ny / 2 + _OFF[1]
+    caps = [CapsuleSpec(centre=(cx - L / 2, cy, zc), radius=radius, level=level, kS=kS, C=9.0, kB=kB),
+            CapsuleSpec(centre=(cx + L / 2, cy, zc), radius=radius, level=level, kS=kS, C=9.0, kB=kB)]
+    return Workload(f"approach beta={beta:g} {nx}x{ny}x{nz}", nx, ny, nz, h_top=0.5 + REP_DZ + h_frac * radius,
+                    capsules=caps, steps=steps, seed=seed)
