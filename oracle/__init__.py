@@ -65,6 +65,7 @@ def lib():
         L.or_rho_interp.argtypes = [C.c_void_p, _dp, C.c_int, C.c_int, C.c_int]
         L.or_set_cuts.argtypes = [C.c_void_p, _up, _ip]
         L.or_set_capsule_wetting.argtypes = [C.c_void_p, C.c_int, C.c_double]
+        L.or_set_flags.argtypes = [C.c_void_p, C.c_int]
         L.or_bessel_k.restype = C.c_double
         L.or_bessel_k.argtypes = [C.c_int, C.c_double]
         L.or_meniscus_fit.restype = C.c_int
@@ -179,10 +180,15 @@ def capillary_force(q, gamma, Q1, Q2, L):
 class Oracle:
     """One lattice with its capsules, stepped by the FP64 oracle."""
 
-    def __init__(self, nx, ny, nz, wall=1, tau=(1.0, 1.0), G=3.6, rep_dz=10.0):
+    # alternative readings of paper-silent points (or_set_flags)
+    INERTIAL, REF_RHO, MIRROR, REMOVE = 1, 2, 4, 8
+
+    def __init__(self, nx, ny, nz, wall=1, tau=(1.0, 1.0), G=3.6, rep_dz=10.0, flags=0):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.N = nx * ny * nz
         self._h = lib().or_create(nx, ny, nz, wall, tau[0], tau[1], G, rep_dz)
+        if flags:
+            lib().or_set_flags(self._h, int(flags))
         self.nv = []
 
     def close(self):
@@ -198,7 +204,8 @@ class Oracle:
 
     @classmethod
     def from_workload(cls, wl, set_film=True):
-        o = cls(wl.nx, wl.ny, wl.nz, wall=wl.wall, tau=wl.tau, G=wl.G, rep_dz=wl.rep_dz)
+        o = cls(wl.nx, wl.ny, wl.nz, wall=wl.wall, tau=wl.tau, G=wl.G, rep_dz=wl.rep_dz,
+                flags=getattr(wl, "flags", 0))
         for cap in wl.capsules:
             X, F = cap.mesh()
             o.add_capsule(X, F, cap.kS, cap.C, cap.kB, cap.kV, cap.mass, cap.mode,

@@ -97,9 +97,20 @@ typedef struct or_ctx {
     or_capsule caps[MAXCAPS];
     long step;
     double dmA;                 /* drying: A mass turned into B per step (0: off) */
+    int flags;                  /* alternative readings (OR_* below)       */
     double mom_to_membrane[3];  /* cumulative momentum given to membranes  */
     double mom_to_wall[3];      /* cumulative momentum given to substrate  */
 } or_ctx;
+
+/* Alternative readings of points where the paper is silent (the defaults
+ * are the readings c6, c8, c10, c23 of the design notes):
+ *   OR_INERTIAL  node update v += F/m, x += v instead of x += F/m (c6)
+ *   OR_REF_RHO   Ladd's term with the reference density rho_0 = 1 instead
+ *                of the node's density (c8)
+ *   OR_MIRROR    partner density across a cut or substrate link = the node's
+ *                own density instead of the mean over its side (c10)
+ *   OR_REMOVE    drying removes the A mass instead of turning it into B (c23) */
+enum { OR_INERTIAL = 1, OR_REF_RHO = 2, OR_MIRROR = 4, OR_REMOVE = 8 };
 
 static long nidx(const or_ctx *c, int x, int y, int z) {
     return ((long)z * c->ny + y) * c->nx + x;
@@ -596,7 +607,8 @@ static void stream(or_ctx *c) {
                             double uT[3];
                             uT_of(c, c->tri[18 * n + ib - 1], uT);
                             double eu = EV[ib][0] * uT[0] + EV[ib][1] * uT[1] + EV[ib][2] * uT[2];
-                            double corr = 2.0 * WV[ib] * rw[cc] * eu / CS2;  /* Ladd term */
+                            double rl = (c->flags & OR_REF_RHO) ? 1.0 : rw[cc];
+                            double corr = 2.0 * WV[ib] * rl * eu / CS2;  /* Ladd term */
                             double fout = *F_(c, c->fpost, cc, ib, n);
                             *dst = fout - corr;
                             c->slink[18 * n + ib - 1] += 2.0 * fout - corr;
@@ -628,6 +640,7 @@ static void stream(or_ctx *c) {
 /* density interpolated for the far side of a cut (or wall) link: mean of the
  * node's own value and those of its neighbours reached through uncut fluid links */
 static double rho_interp(const or_ctx *c, const double *rho, int x, int y, int z, long n) {
+    if (c->flags & OR_MIRROR) return rho[n];
     double s = rho[n];
     int cnt = 1;
     for (int k = 1; k < NQ; ++k) {
@@ -807,16 +820,20 @@ static void membrane_update(or_ctx *c) {
         /* area and volume of the mesh this step's forces were computed on */
         p->area = mesh_area(p->X, p->F, p->nf);
         p->volume = mesh_volume(p->X, p->F, p->nf);
+        const int inertial = (c->flags & OR_INERTIAL) != 0;
         if (p->mode == 0) {          /* free: x += F/m, v = F/m (Eq. 9, dt = 1) */
             for (int k = 0; k < 3 * p->nv; ++k) {
-                p->V[k] = p->Ftot[k] / p->mass;
+                p->V[k] = (inertial ? p->V[k] : 0.0) + p->Ftot[k] / p->mass;
                 p->X[k] += p->V[k];
             }
         } else if (p->mode == 1) {   /* frozen shape: rigid translation */
             double vr[3];
             for (int a = 0; a < 3; ++a) vr[a] = sFt[a] / (p->mass * p->nv);
             for (int v = 0; v < p->nv; ++v)
-                for (int a = 0; a < 3; ++a) { p->V[3 * v + a] = vr[a]; p->X[3 * v + a] += vr[a]; }
+                for (int a = 0; a < 3; ++a) {
+                    p->V[3 * v + a] = (inertial ? p->V[3 * v + a] : 0.0) + vr[a];
+                    p->X[3 * v + a] += p->V[3 * v + a];
+                }
         } else {                     /* fixed */
             memset(p->V, 0, sizeof(double) * 3 * p->nv);
         }
@@ -846,12 +863,15 @@ static void remove_mass(or_ctx *c) {
         const double dm = eps * c->rho[n];
         for (int i = 0; i < NQ; ++i) {
             *F_(c, c->fpost, 0, i, n) *= 1.0 - eps;
-            *F_(c, c->fpost, 1, i, n) += WV[i] * dm;
+            if (!(c->flags & OR_REMOVE)) *F_(c, c->fpost, 1, i, n) += WV[i] * dm;
         }
     }
 }
 
 void or_remove_mass(or_ctx *c, double dmA) { c->dmA = dmA; }
+
+/* Alternative readings (OR_* flags above), 0 for the defaults. */
+void or_set_flags(or_ctx *c, int flags) { c->flags = flags; }
 
 int or_step(or_ctx *c, int nsteps) {
     for (int s = 0; s < nsteps; ++s) {
