@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--theory-steps", type=int, default=40000)
     ap.add_argument("--theory-box", type=int, default=128,
                     help="lateral size of the single-particle boxes and y size of the pair boxes")
+    ap.add_argument("--cluster", action="store_true",
+                    help="aggregation of 100 free soft particles (clusters and radial distribution)")
+    ap.add_argument("--cluster-steps", type=int, default=20000)
     ap.add_argument("--approach", action="store_true",
                     help="approach dynamics of two free soft particles (gap against time)")
     ap.add_argument("--approach-steps", type=int, default=40000)
@@ -656,27 +659,90 @@ def run_approach(args):
     sims = [cfm.Simulation.from_workload(w) for w in wls]
     batch = cfm.Batch(sims)
     every = max(1, args.approach_steps // 40)
-    hist = [[surface_gap(s.capsule_state(0)["X"], s.capsule_state(1)["X"]) for s in sims]]
+
+    def sample():
+        gaps, dist = [], []
+        for s in sims:
+            Xa, Xb = s.capsule_state(0)["X"], s.capsule_state(1)["X"]
+            gaps.append(surface_gap(Xa, Xb))
+            dist.append(float(np.linalg.norm((Xb.mean(0) - Xa.mean(0))[:2])))
+        return gaps, dist
+
+    g0, d0 = sample()
+    hist, hdist = [g0], [d0]
     t0 = time.perf_counter()
     for _ in range(args.approach_steps // every):
         batch.step(every)
-        hist.append([surface_gap(s.capsule_state(0)["X"], s.capsule_state(1)["X"]) for s in sims])
+        g, d = sample()
+        hist.append(g)
+        hdist.append(d)
     wall = time.perf_counter() - t0
     batch.close()
-    hist = np.array(hist)
+    hist, hdist = np.array(hist), np.array(hdist)
     line = {"metric": "surface gap of two free soft particles against time", "unit": "lattice units",
             "data": "synthetic", "dtype": "f32",
             "config": {"workload": "two free R=10 level-4 capsules, initial gap 2R, film 0.4R, 128x64x48, "
                                    "nu_s = 0.9 (C = 9), kS = 5e-3, kB = R^2 gamma / beta",
                        "steps": args.approach_steps, "every": every},
             "gap": {f"beta={b:g}": hist[:, k].tolist() for k, b in enumerate(betas)},
+            "centre_distance": {f"beta={b:g}": hdist[:, k].tolist() for k, b in enumerate(betas)},
             "final_gap": {f"beta={b:g}": float(hist[-1, k]) for k, b in enumerate(betas)},
+            "final_centre_distance": {f"beta={b:g}": float(hdist[-1, k]) for k, b in enumerate(betas)},
             "wall_s": wall, "value": float(hist[-1, 0])}
+    print(json.dumps(line), flush=True)
+
+
+def run_cluster(args):
+    """Aggregation of many free soft particles (Sec. 4.7): the cluster
+    statistics of the capsule centroids over time (bonded below 2R + delta0
+    + 1) and their radial distribution at the start and the end."""
+    import torch
+    from paper_2007_15405_gb300 import build as B
+    B.build()
+    from paper_2007_15405_gb300 import analysis as A
+    from paper_2007_15405_gb300 import capfilm as cfm
+    from paper_2007_15405_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    wl = I.many_capsules()
+    R = wl.capsules[0].radius
+    sim = cfm.Simulation.from_workload(wl)
+    L = (wl.nx, wl.ny)
+    cut = 2 * R + I.DELTA0 + 1.0
+
+    def centroids():
+        return np.array([sim.capsule_state(k)["X"].mean(0) for k in range(len(wl.capsules))])
+
+    c0 = centroids()
+    every = max(1, args.cluster_steps // 10)
+    series = [dict(step=0, stats=A.cluster_stats(A.clusters(c0, L, cut)))]
+    t0 = time.perf_counter()
+    for k in range(args.cluster_steps // every):
+        sim.step(every)
+        c = centroids()
+        series.append(dict(step=(k + 1) * every, stats=A.cluster_stats(A.clusters(c, L, cut)),
+                           min_height=float(c[:, 2].min())))
+    wall = time.perf_counter() - t0
+    r, g0 = A.rdf(c0, L, 2.0, 60.0)
+    _, g1 = A.rdf(c, L, 2.0, 60.0)
+    sim.close()
+    line = {"metric": "aggregation of free soft particles: clusters and radial distribution over time",
+            "unit": "particles", "data": "synthetic", "dtype": "f32",
+            "config": {"workload": wl.name + f", R=10 level-4, film 0.35R, {len(wl.capsules)} particles",
+                       "steps": args.cluster_steps, "bond_cutoff": cut},
+            "series": [dict(step=e["step"], clusters=e["stats"][0], mean_size=e["stats"][1],
+                            largest=e["stats"][2], **({"min_height": e["min_height"]} if "min_height" in e else {}))
+                       for e in series],
+            "rdf": {"r": r.tolist(), "start": g0.tolist(), "end": g1.tolist()},
+            "mlups": wl.nodes * args.cluster_steps / wall / 1e6, "wall_s": wall,
+            "value": series[-1]["stats"][1]}
     print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse()
+    if args.cluster:
+        run_cluster(args)
+        return
     if args.approach:
         run_approach(args)
         return

@@ -75,6 +75,20 @@ typedef struct {
     void *user;
 } cf_allocator;
 
+/* Alternative readings of points where the paper is silent (flags of
+ * cf_lattice_desc; 0 selects the default readings):
+ * CF_INERTIAL        node update v += F_tot/m, x += v instead of the literal
+ *                    x += F_tot/m of Eq. 9 with dt = 1 (free and frozen
+ *                    capsules; the node velocity enters Ladd's term)
+ * CF_LADD_REF_RHO    Ladd's moving-wall term (Sec. 3.1) with the reference
+ *                    density rho_0 = 1 instead of the fluid node's density
+ * CF_PARTNER_MIRROR  partner density across a cut or substrate link (Sec.
+ *                    3.1, last paragraph) = the node's own density instead
+ *                    of the mean over the node and its same-side neighbours
+ * CF_DRY_REMOVE      drying (cf_remove_mass) removes the A mass instead of
+ *                    turning it into B */
+enum { CF_INERTIAL = 1, CF_LADD_REF_RHO = 2, CF_PARTNER_MIRROR = 4, CF_DRY_REMOVE = 8 };
+
 typedef struct {
     int nx, ny, nz;          /* lattice size, each >= 3                        */
     int wall;                /* 1: substrate plane z = 0; 0: fully periodic    */
@@ -85,6 +99,7 @@ typedef struct {
     int precision;           /* cf_precision                                   */
     const cf_allocator *allocator; /* may be NULL                              */
     void *stream;            /* cudaStream_t or NULL                           */
+    int flags;               /* CF_INERTIAL | ... (0: the default readings)    */
 } cf_lattice_desc;
 
 typedef struct {
@@ -119,7 +134,7 @@ const char *cf_last_error(void);
  * Errors (checked before any CUDA call): CF_EINVAL for a null argument, a
  * dimension below 3, a lattice with 38 * nx * ny * nz >= 2^31 (32-bit
  * population offsets: at most 56.5 million nodes), tau <= 1/2 or not a
- * number, an unknown precision; then CF_ECUDA (stream or event creation) and
+ * number, an unknown precision or flag; then CF_ECUDA (stream or event creation) and
  * CF_ENOMEM (an allocation failed: all blocks obtained are given back). */
 cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out);
 /* Frees the context and everything it allocated; a null context is a no-op
@@ -469,6 +484,45 @@ cf_status cf_unet_split(long long nv, const float *y, int ca, int cb, float *a, 
 cf_status cf_unet_pack(const float *x, int c, long long N, int cpad, void *y, void *stream);
 cf_status cf_unet_unpack(const void *x, int x_f32, int cpad, long long N, int c0, int c, float *y,
                          void *stream);
+
+/* ------------------------------------------------ warm start in the library
+ * The trained U-net (the paper has no counterpart: its long equilibration
+ * runs, Sec. 4, are what the prediction shortens) loaded onto the device,
+ * and the whole warm start of a context: inputs (cf_warm_features), the
+ * U-net's density head, the predicted state (cf_warm_apply), then two
+ * judging windows of the coupled run with a fallback to the flat film.
+ *
+ * cf_model_load: weights file "CFUNET01", int32 widths w0 w1 w2, then for
+ * the layers e0a e0b e1a e1b ma mb d1a d1b d0a d0b head: int32 cin, cout,
+ * float32 weights [27][cout][cin], float32 biases [cout] (native byte
+ * order; the shapes must be those of the U-net with these widths).  Weights
+ * are stored on the current device in bfloat16.  CF_EINVAL for a missing or
+ * malformed file, CF_ENOMEM. */
+typedef struct cf_model cf_model;
+cf_status cf_model_load(const char *path, cf_model **out);
+cf_status cf_model_destroy(cf_model *model);
+
+typedef struct {
+    int window;      /* steps of each judging window (>= 1), e.g. 25          */
+    double u_limit;  /* largest velocity component allowed, e.g. 0.1          */
+    double grow;     /* the mean density change of the second window may be
+                        at most grow times the first's, e.g. 1.5              */
+    int fallback;    /* 1: restore the flat film when the judgement fails     */
+} cf_warm_policy;
+
+/* Warm start of a context (after its capsules are added; lattice sizes
+ * divisible by 4): sets the U-net's predicted densities (film h_top,
+ * densities rho_maj / rho_min / rho_mix, modulus kS for the input feature),
+ * runs 1 + 2 * window steps and judges them: the start is kept when all
+ * densities and velocities are finite, no density is negative, no velocity
+ * component exceeds u_limit and the density change of the second window is
+ * at most grow times the first's; otherwise, with fallback set, the flat
+ * film (cf_set_film with `jitter`, which may be NULL) is restored.  *used
+ * receives 1 when the prediction was kept, *steps the judging steps taken
+ * (either may be NULL).  Synchronous. */
+cf_status cf_warmstart(cf_ctx *ctx, const cf_model *model, const cf_warm_policy *policy, double h_top,
+                       double rho_maj, double rho_min, double rho_mix, double kS, const double *jitter,
+                       int *used, long long *steps);
 
 /* Set-up of the warm start on a context (after its capsules are added; all
  * arrays are device arrays of the caller, [c][nz][ny][nx] float32; the film

@@ -21,6 +21,8 @@ STATUS_NAMES = {0: "CF_OK", 1: "CF_EINVAL", 2: "CF_ENOMEM", 3: "CF_ECUDA", 4: "C
                 5: "CF_ENOTFOUND", 6: "CF_EDIVERGED", 7: "CF_EOVERFLOW"}
 
 FREE, FROZEN, FIXED = 0, 1, 2
+# alternative readings (cf_lattice_desc.flags)
+INERTIAL, LADD_REF_RHO, PARTNER_MIRROR, DRY_REMOVE = 1, 2, 4, 8
 FP32, FP16_SHIFT, BF16_SHIFT = 0, 1, 2
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -35,7 +37,7 @@ class LatticeDesc(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("wall", C.c_int),
                 ("tau", C.c_double * 2), ("G", C.c_double), ("rep_dz", C.c_double),
                 ("xi", C.c_double), ("delta0", C.c_double), ("precision", C.c_int),
-                ("allocator", C.POINTER(Allocator)), ("stream", C.c_void_p)]
+                ("allocator", C.POINTER(Allocator)), ("stream", C.c_void_p), ("flags", C.c_int)]
 
 
 class CapsuleDesc(C.Structure):
@@ -43,6 +45,10 @@ class CapsuleDesc(C.Structure):
                 ("faces", C.POINTER(C.c_int)), ("kS", C.c_double), ("C", C.c_double),
                 ("kB", C.c_double), ("kV", C.c_double), ("mass", C.c_double), ("mode", C.c_int),
                 ("wet", C.c_double)]
+
+
+class WarmPolicy(C.Structure):
+    _fields_ = [("window", C.c_int), ("u_limit", C.c_double), ("grow", C.c_double), ("fallback", C.c_int)]
 
 
 class CapfilmError(RuntimeError):
@@ -146,6 +152,10 @@ def load_library(path: Optional[str] = None):
         "cf_unet_unpack": [C.c_void_p, C.c_int, C.c_int, C.c_longlong, C.c_int, C.c_int, C.c_void_p,
                            C.c_void_p],
         "cf_meniscus_fit": [_dp, _dp, C.c_size_t, C.c_double, C.c_double, _dp],
+        "cf_model_load": [C.c_char_p, C.POINTER(C.c_void_p)],
+        "cf_model_destroy": [C.c_void_p],
+        "cf_warmstart": [C.c_void_p, C.c_void_p, C.POINTER(WarmPolicy), C.c_double, C.c_double, C.c_double,
+                         C.c_double, C.c_double, _dp, C.POINTER(C.c_int), C.POINTER(C.c_longlong)],
         "cf_capillary_force": [C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _dp],
     }
     for name, args in sig.items():
@@ -167,7 +177,8 @@ def exported_symbols():
             "cf_batch_lateral_forces", "cf_warm_features", "cf_warm_apply", "cf_warm_target",
             "cf_field_check", "cf_conv3d_forward",
             "cf_conv3d_backward", "cf_mse", "cf_adam", "cf_to_bf16", "cf_from_bf16",
-            "cf_meniscus_fit", "cf_capillary_force", "cf_unet_conv", "cf_unet_flip", "cf_unet_wgrad",
+            "cf_meniscus_fit", "cf_capillary_force", "cf_model_load", "cf_model_destroy", "cf_warmstart",
+            "cf_unet_conv", "cf_unet_flip", "cf_unet_wgrad",
             "cf_unet_relu_grad", "cf_unet_loss", "cf_unet_pool", "cf_unet_pool_bwd", "cf_unet_upsample",
             "cf_unet_upsample_bwd", "cf_unet_concat", "cf_unet_split", "cf_unet_pack", "cf_unet_unpack"]
 
@@ -240,7 +251,7 @@ class Simulation:
     """One lattice with its capsules, stepped on the GPU by the CUDA library."""
 
     def __init__(self, nx, ny, nz, wall=1, tau=(1.0, 1.0), G=3.6, rep_dz=10.0, xi=1.5,
-                 delta0=1.5, stream=None, use_torch_allocator=True, precision=FP32):
+                 delta0=1.5, stream=None, use_torch_allocator=True, precision=FP32, flags=0):
         L = load_library()
         self.nx, self.ny, self.nz = nx, ny, nz
         self.N = nx * ny * nz
@@ -264,7 +275,7 @@ class Simulation:
             stream_handle = stream.cuda_stream
             self._stream = stream
         desc = LatticeDesc(nx, ny, nz, wall, (C.c_double * 2)(*tau), G, rep_dz, xi, delta0,
-                           precision, alloc_ptr, stream_handle)
+                           precision, alloc_ptr, stream_handle, int(flags))
         self._desc = desc
         h = C.c_void_p()
         _check(L.cf_create(C.byref(desc), C.byref(h)))
@@ -273,6 +284,7 @@ class Simulation:
 
     @classmethod
     def from_workload(cls, wl, set_film=True, **kw):
+        kw.setdefault("flags", getattr(wl, "flags", 0))
         s = cls(wl.nx, wl.ny, wl.nz, wall=wl.wall, tau=wl.tau, G=wl.G, rep_dz=wl.rep_dz, **kw)
         for cap in wl.capsules:
             X, F = cap.mesh()
@@ -409,6 +421,16 @@ class Simulation:
                     f.write(json.dumps(rec) + "\n")
         return recs
 
+    def warmstart(self, model, h_top, kS, jitter=None, window=25, u_limit=0.1, grow=1.5, fallback=True):
+        """The library's warm start (cf_warmstart): returns (kept, judging steps)."""
+        from .inputs import RHO_MAJ, RHO_MIN, RHO_MIX
+        pol = WarmPolicy(int(window), float(u_limit), float(grow), int(bool(fallback)))
+        j = None if jitter is None else np.ascontiguousarray(jitter, np.float64).reshape(-1)
+        used, steps = C.c_int(), C.c_longlong()
+        _check(_lib.cf_warmstart(self._h, model._h, C.byref(pol), float(h_top), RHO_MAJ, RHO_MIN, RHO_MIX,
+                                 float(kS), _ptr(j), C.byref(used), C.byref(steps)))
+        return bool(used.value), int(steps.value)
+
     def capsule_force(self, cid):
         F = np.zeros(3); T = np.zeros(3)
         _check(_lib.cf_capsule_force(self._h, cid, _ptr(F), _ptr(T)))
@@ -468,6 +490,27 @@ class Simulation:
         mask = np.zeros((self.nz, self.ny, self.nx), np.uint32)
         _check(_lib.cf_cuts(self._h, mask.ctypes.data_as(C.POINTER(C.c_uint32)), None, None))
         return mask
+
+
+class Model:
+    """The trained U-net loaded into the library (cf_model_load)."""
+
+    def __init__(self, path):
+        L = load_library()
+        h = C.c_void_p()
+        _check(L.cf_model_load(os.fsencode(path), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.cf_model_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

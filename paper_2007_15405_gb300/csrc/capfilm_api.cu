@@ -191,6 +191,7 @@ LBParams lb_params(cf_ctx *c, bool with_out) {
         p.itau[k] = (float)(1.0 / c->d.tau[k]);
     }
     p.G = (float)c->d.G;
+    p.flags = c->d.flags;
     p.src = c->f[c->fpar];
     p.dst = c->f[1 - c->fpar];
     p.rho_src = c->rho[c->fpar];
@@ -246,6 +247,7 @@ MemParams mem_params(cf_ctx *c) {
     p.bbox_prev = c->bbox[1 - c->xpar];
     p.status = c->status;
     p.any_frozen = c->any_frozen ? 1 : 0;
+    p.inertial = (c->d.flags & CF_INERTIAL) ? 1 : 0;
     return p;
 }
 
@@ -312,6 +314,7 @@ cf_status enqueue_pre(cf_ctx *c, int *nl) {
     q.rec = c->rec;
     q.FT = c->FT[c->ftpar];
     q.capacity = c->capacity;
+    q.ref_rho = (c->d.flags & CF_LADD_REF_RHO) ? 1 : 0;
     CF_CUDA(launch_prep(q, c->stream, nl));
     return CF_OK;
 }
@@ -583,6 +586,8 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     if (desc->precision != CF_FP32 && desc->precision != CF_FP16_SHIFT &&
         desc->precision != CF_BF16_SHIFT)
         return fail(CF_EINVAL, "unsupported precision");
+    if (desc->flags & ~(CF_INERTIAL | CF_LADD_REF_RHO | CF_PARTNER_MIRROR | CF_DRY_REMOVE))
+        return fail(CF_EINVAL, "unknown flag");
     cf_ctx *c = new cf_ctx();
     c->d = *desc;
     c->N = (long long)desc->nx * desc->ny * desc->nz;
@@ -1104,6 +1109,68 @@ cf_status cf_meniscus_profile(cf_ctx *c, int id, double dr, double *r, double *z
     }
     *inout_n = nr;
     if (Z) *Z = out[nr];
+    return CF_OK;
+}
+
+// ------------------------------------------------ warm start in the library
+struct cf_model {
+    UNetModel *m = nullptr;
+};
+
+extern "C" cf_status cf_model_load(const char *path, cf_model **out) {
+    if (!path || !out) return fail(CF_EINVAL, "null argument");
+    UNetModel *m = nullptr;
+    const cf_status s = unet_load(path, &m);
+    if (s != CF_OK) return s;
+    *out = new cf_model{m};
+    return CF_OK;
+}
+
+extern "C" cf_status cf_model_destroy(cf_model *model) {
+    if (!model) return CF_OK;
+    unet_free(model->m);
+    delete model;
+    return CF_OK;
+}
+
+extern "C" cf_status cf_warmstart(cf_ctx *c, const cf_model *model, const cf_warm_policy *pol, double h_top,
+                                  double rmaj, double rmin, double rmix, double kS, const double *jitter, int *used,
+                                  long long *steps) {
+    if (!c || !model || !pol) return fail(CF_EINVAL, "null argument");
+    if (pol->window < 1 || !(pol->grow > 0.0) || !(pol->u_limit > 0.0))
+        return fail(CF_EINVAL, "bad warm-start policy (window >= 1, grow > 0, u_limit > 0)");
+    if (c->d.nx % 4 || c->d.ny % 4 || c->d.nz % 4) return fail(CF_EINVAL, "the U-net needs lattice sizes divisible by 4");
+    const long long N = c->N;
+    float *feats = (float *)dalloc(c, sizeof(float) * 4 * (size_t)N);
+    float *dens = (float *)dalloc(c, sizeof(float) * 2 * (size_t)N);
+    if (!feats || !dens) return fail(CF_ENOMEM, "device allocation failed (warm start)");
+    c->allocations.pop_back();
+    c->allocations.pop_back();
+    auto release = [&]() { dfree(c, feats); dfree(c, dens); };
+    cf_status s = cf_warm_features(c, h_top, kS, feats, nullptr);
+    if (s == CF_OK) s = unet_forward(model->m, feats, c->d.nz, c->d.ny, c->d.nx, dens, nullptr, c->stream);
+    if (s == CF_OK) s = cf_warm_apply(c, h_top, rmaj, rmin, rmix, dens);
+    if (s != CF_OK) { release(); return s; }
+    // judge the predicted start over two windows: finite, no negative
+    // density, velocities below u_limit, and a density change that decays
+    double ck[3][4];
+    s = cf_step(c, 1);
+    if (s == CF_OK) s = cf_field_check(c, ck[0]);
+    for (int w = 1; w <= 2 && s == CF_OK; ++w) {
+        s = cf_step(c, pol->window);
+        if (s == CF_OK) s = cf_field_check(c, ck[w]);
+    }
+    release();
+    if (s != CF_OK && s != CF_EDIVERGED) return s;
+    bool ok = s == CF_OK;
+    for (int w = 1; w <= 2 && ok; ++w) ok = ck[w][0] == 1.0 && ck[w][1] >= 0.0 && ck[w][2] <= pol->u_limit;
+    ok = ok && ck[2][3] <= pol->grow * ck[1][3];
+    if (!ok && pol->fallback) {
+        s = cf_set_film(c, h_top, rmaj, rmin, rmix, jitter);
+        if (s != CF_OK) return s;
+    }
+    if (used) *used = ok ? 1 : 0;
+    if (steps) *steps = 2LL * pol->window + 1;
     return CF_OK;
 }
 

@@ -3,6 +3,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/capfilm.h"
+
 namespace cf {
 
 // Programmatic dependent launch.  The kernels of the step's critical path are
@@ -93,6 +95,7 @@ struct LBParams {
     int zstride;            // batched passes: z slices of this lattice
     float itau[2], tau[2];  // 1/tau and tau per component
     float G;
+    int flags;              // CF_PARTNER_MIRROR, CF_DRY_REMOVE (alternative readings)
     const void *__restrict__ src;    // post-collision populations of the last step
     void *__restrict__ dst;          // post-collision populations of this step
     const float2 *__restrict__ rho_src;  // densities the src populations were encoded with
@@ -109,8 +112,9 @@ struct LBParams {
     float *__restrict__ out;            // optional [5][N]: rhoA, rhoB, ux, uy, uz
     float2 *__restrict__ rho;           // [N] (rhoA, rhoB) of this step (written by the density pass)
     float2 *__restrict__ psi;           // [N] (psiA, psiB) of this step (written by the density pass)
-    float4 *__restrict__ J;             // [N] total momentum of this step (density pass, tau = 1 only)
-    float4 *__restrict__ sdens;         // allocation-free step: (rho, psi) scratch of the library
+    float4 *__restrict__ J;             // [N] total momentum of this step (density pass, tau = 1 only);
+                                        // the allocation-free step keeps (rho_A, rho_B, psi_A, psi_B)
+                                        // of its static scratch here
     unsigned *__restrict__ status;      // device error flags
     // drying (A turned into B): the density pass sums rho_A over the
     // A-majority nodes into block partials, its last block turns them into the
@@ -165,6 +169,7 @@ struct MemParams {
     const int *bbox_prev;    // same, of the previous step (Hertz prefilter)
     unsigned *status;        // device error flags
     int any_frozen;
+    int inertial;            // CF_INERTIAL: v += F/m, x += v
 };
 
 // per-element scratch layout (floats)
@@ -212,6 +217,7 @@ struct PrepParams {
     float2 *rec;             // [N][18] bounced (A, B) populations by arriving direction - 1
     float *FT;               // element momentum exchange accumulators
     int capacity;
+    int ref_rho;             // CF_LADD_REF_RHO: Ladd's term with rho_0 = 1
 };
 
 __host__ __device__ inline int wrapi(int a, int n) {
@@ -277,6 +283,12 @@ cudaError_t launch_warm_target(const WarmGeom &g, const uint8_t *inside, const f
                                cudaStream_t s);
 cudaError_t launch_field_check(long long N, const float *out, float *snap, double *part, double *res,
                                cudaStream_t s);
+// the warm start's U-net on the device (unet_kernels.cu)
+struct UNetModel;
+cf_status unet_load(const char *path, UNetModel **out);
+void unet_free(UNetModel *m);
+cf_status unet_forward(const UNetModel *m, const float *feats, int nz, int ny, int nx, float *dens, float *disp,
+                       cudaStream_t s);
 // membrane kernels 1-3 (positions only) and 4-5 (after the lattice update)
 cudaError_t launch_membrane_forces(const MemParams &p, cudaStream_t s, int *nlaunch);
 cudaError_t launch_membrane_update(const MemParams &p, const ClearParams &cl, bool any_frozen,

@@ -349,15 +349,18 @@ __device__ __forceinline__ void sc_force(const LBParams &p, const Deltas &d, uin
         }
     } else {
         // partner densities across a cut or substrate link: mean over this
-        // node and its neighbours reached through uncut fluid links
+        // node and its neighbours reached through uncut fluid links (with
+        // CF_PARTNER_MIRROR the node's own densities)
         float ia = ra, ib = rb, cnt = 1.f;
+        if (!(p.flags & CF_PARTNER_MIRROR)) {
 #pragma unroll
-        for (int k = 1; k < Q; ++k) {
-            const bool solid = (ez(k) == 1 && d.whi) || (ez(k) == -1 && d.wlo);
-            const bool cut = (m >> (k - 1)) & 1u;
-            if (!solid && !cut) {
-                const float2 q = __ldg(p.rho + n + nb_off(d, ex(k), ey(k), ez(k)));
-                ia += q.x; ib += q.y; cnt += 1.f;
+            for (int k = 1; k < Q; ++k) {
+                const bool solid = (ez(k) == 1 && d.whi) || (ez(k) == -1 && d.wlo);
+                const bool cut = (m >> (k - 1)) & 1u;
+                if (!solid && !cut) {
+                    const float2 q = __ldg(p.rho + n + nb_off(d, ex(k), ey(k), ez(k)));
+                    ia += q.x; ib += q.y; cnt += 1.f;
+                }
             }
         }
         const float ma = ia / cnt, mb = ib / cnt;
@@ -418,7 +421,7 @@ __device__ __forceinline__ void store_post(const LBParams &p, int n, float ra, f
     if (DRY && ra > rb) {
         const float e = __ldg(p.dry_eps);
         ca = 1.f - e;
-        cb = e * ra;
+        cb = (p.flags & CF_DRY_REMOVE) ? 0.f : e * ra;  // removed, or turned into B
     }
     const float ka = 1.0f - 1.5f * (ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2]);
     const float kb = 1.0f - 1.5f * (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
@@ -1201,7 +1204,7 @@ __global__ void __launch_bounds__(BX *BY) k_density_static(const LBParams p) {
             ra += __ldg(sA + o);
             rb += __ldg(sB + o);
         }
-        p.sdens[d.n] = make_float4(ra, rb, psi_of(ra), psi_of(rb));
+        p.J[d.n] = make_float4(ra, rb, psi_of(ra), psi_of(rb));
     }
 }
 
@@ -1220,14 +1223,14 @@ __device__ __forceinline__ void collide_node_static(const LBParams &p, const Del
             fb[i] = __ldg(sB + o);
         }
     }
-    const float4 me = p.sdens[n];
+    const float4 me = p.J[n];
     const float ra = me.x, rb = me.y, pa = me.z, pb = me.w;
     float sa[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};  // summed over opposite pairs
     if (!d.wlo && !d.whi) {
 #pragma unroll
         for (int k = 1; k < Q; k += 2) {
-            const float4 q1 = p.sdens[n + nb_off(d, ex(k), ey(k), ez(k))];
-            const float4 q2 = p.sdens[n + nb_off(d, -ex(k), -ey(k), -ez(k))];
+            const float4 q1 = p.J[n + nb_off(d, ex(k), ey(k), ez(k))];
+            const float4 q2 = p.J[n + nb_off(d, -ex(k), -ey(k), -ez(k))];
             const float da = q1.z - q2.z, db = q1.w - q2.w;
             sa[0] += wgt(k) * ex(k) * da; sa[1] += wgt(k) * ey(k) * da; sa[2] += wgt(k) * ez(k) * da;
             sb[0] += wgt(k) * ex(k) * db; sb[1] += wgt(k) * ey(k) * db; sb[2] += wgt(k) * ez(k) * db;
@@ -1238,7 +1241,7 @@ __device__ __forceinline__ void collide_node_static(const LBParams &p, const Del
         for (int k = 1; k < Q; ++k) {
             const bool solid = (ez(k) == 1 && d.whi) || (ez(k) == -1 && d.wlo);
             if (!solid) {
-                const float4 q = p.sdens[n + nb_off(d, ex(k), ey(k), ez(k))];
+                const float4 q = p.J[n + nb_off(d, ex(k), ey(k), ez(k))];
                 ia += q.x; ib += q.y; cnt += 1.f;
             }
         }
@@ -1249,7 +1252,7 @@ __device__ __forceinline__ void collide_node_static(const LBParams &p, const Del
             const bool solid = (ez(k) == 1 && d.whi) || (ez(k) == -1 && d.wlo);
             if (solid) { qA[k] = qa_eff; qB[k] = qb_eff; }
             else {
-                const float4 q = p.sdens[n + nb_off(d, ex(k), ey(k), ez(k))];
+                const float4 q = p.J[n + nb_off(d, ex(k), ey(k), ez(k))];
                 qA[k] = q.z; qB[k] = q.w;
             }
         }
@@ -1356,7 +1359,7 @@ extern "C" cf_status cf_lattice_step_static(const float *src, float *dst, int nx
     p.G = (float)G;
     p.src = src;
     p.dst = dst;
-    p.sdens = dens;
+    p.J = dens;
     const cudaStream_t s = (cudaStream_t)stream;
     // both kernels stride over the planes by gridDim.z, so grid.z stays
     // within the 65535 launch limit for any accepted lattice

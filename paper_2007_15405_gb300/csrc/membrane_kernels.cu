@@ -397,7 +397,9 @@ __global__ void __launch_bounds__(MV) k_mem_update(const MemParams p, const Clea
         node_forces(p, cp, cap, vv, pre, x, Fc, Ft);
         st3(p.Fcpl + 3 * vv, Fc);
         if (cp.mode == 0) {
-            const f3 vel = (1.f / cp.mass) * Ft;
+            // Eq. 9 with dt = 1 (v = F/m), or with CF_INERTIAL v += F/m
+            f3 vel = (1.f / cp.mass) * Ft;
+            if (p.inertial) vel = vel + ld3(p.V, vv);
             st3(p.V + 3 * vv, vel);
             st_pos(p.Xnh, p.Xnl, vv, x, vel);
         } else if (cp.mode == 2) {
@@ -430,7 +432,8 @@ __global__ void __launch_bounds__(MV) k_mem_frozen(const MemParams p) {
     if (cp.mode != 1) return;
     const double *A = p.acc + cap * A_NACC;
     const double sc = 1.0 / ((double)cp.mass * cp.nv);
-    const f3 vel{(float)(A[A_FTX] * sc), (float)(A[A_FTY] * sc), (float)(A[A_FTZ] * sc)};
+    f3 vel{(float)(A[A_FTX] * sc), (float)(A[A_FTY] * sc), (float)(A[A_FTZ] * sc)};
+    if (p.inertial) vel = vel + ld3(p.V, v);
     st3(p.V + 3 * v, vel);
     st_pos(p.Xnh, p.Xnl, v, ldp(p.Xh, p.Xl, v), vel);
 }
@@ -685,7 +688,8 @@ __global__ void k_cut_prep(const PrepParams p) {
         ek(k, kx, ky, kz);
         const float eu = kx * u.x + ky * u.y + kz * u.z;
         const float w6 = 6.0f * wgt(k);
-        const float ca = w6 * dn.x * eu, cb = w6 * dn.y * eu;
+        const float ra = p.ref_rho ? 1.f : dn.x, rb = p.ref_rho ? 1.f : dn.y;  // CF_LADD_REF_RHO
+        const float ca = w6 * ra * eu, cb = w6 * rb * eu;
         p.rec[n * 18 + (opp(k) - 1)] = make_float2(foa - ca, fob - cb);
         const float sx = (2.0f * foa - ca) + (2.0f * fob - cb);
         if (kx) atomicAdd(p.FT + 3 * T + 0, kx * sx);

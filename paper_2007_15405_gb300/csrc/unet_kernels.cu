@@ -22,7 +22,11 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
 
 namespace cf {
 
@@ -463,6 +467,132 @@ cf_status bad(const char *m) {
 bool grid_ok(int n, int nz, int ny, int nx) { return n >= 1 && nz >= 1 && ny >= 1 && nx >= 1; }
 
 }  // namespace
+
+// ------------------------------------------------------- the model on device
+// The U-net's parameters (bfloat16 weights [27][cout][cin], float biases) in
+// layer order e0a e0b e1a e1b ma mb d1a d1b d0a d0b head, for inference
+// inside the library (cf_warmstart).
+struct UNetModel {
+    int w0 = 0, w1 = 0, w2 = 0;
+    int cin[11] = {}, cout[11] = {};
+    __nv_bfloat16 *w[11] = {};
+    float *b[11] = {};
+};
+
+void unet_free(UNetModel *m) {
+    if (!m) return;
+    for (int k = 0; k < 11; ++k) {
+        if (m->w[k]) cudaFree(m->w[k]);
+        if (m->b[k]) cudaFree(m->b[k]);
+    }
+    delete m;
+}
+
+namespace {
+__global__ void k_f32_to_bf16(const float *__restrict__ x, __nv_bfloat16 *__restrict__ y, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = __float2bfloat16_rn(x[i]);
+}
+}  // namespace
+
+// File: "CFUNET01", int32 w0 w1 w2, then per layer int32 cin, cout, float32
+// weights [27][cout][cin], float32 biases [cout] (native byte order).
+cf_status unet_load(const char *path, UNetModel **out) {
+    FILE *fp = std::fopen(path, "rb");
+    if (!fp) { set_last_error("cf_model_load: cannot open the file"); return CF_EINVAL; }
+    char magic[8];
+    int32_t wd[3];
+    UNetModel *m = new UNetModel();
+    auto fail_ = [&](const char *msg, cf_status st) { std::fclose(fp); unet_free(m); set_last_error(msg); return st; };
+    if (std::fread(magic, 1, 8, fp) != 8 || std::memcmp(magic, "CFUNET01", 8) != 0 || std::fread(wd, 4, 3, fp) != 3)
+        return fail_("cf_model_load: not a U-net weight file", CF_EINVAL);
+    m->w0 = wd[0]; m->w1 = wd[1]; m->w2 = wd[2];
+    const int W0 = wd[0], W1 = wd[1], W2 = wd[2];
+    const int ecin[11] = {16, W0, W0, W1, W1, W2, W1 + W2, W1, W0 + W1, W0, W0};
+    const int ecout[11] = {W0, W0, W1, W1, W2, W2, W1, W1, W0, W0, 16};
+    for (int k = 0; k < 11; ++k) {
+        int32_t cc[2];
+        if (std::fread(cc, 4, 2, fp) != 2 || cc[0] != ecin[k] || cc[1] != ecout[k] || cc[0] % 16 || cc[1] % 16)
+            return fail_("cf_model_load: layer shapes do not match the U-net", CF_EINVAL);
+        m->cin[k] = cc[0];
+        m->cout[k] = cc[1];
+        const size_t nw = 27ull * cc[0] * cc[1];
+        std::vector<float> hw(nw), hb(cc[1]);
+        if (std::fread(hw.data(), 4, nw, fp) != nw || std::fread(hb.data(), 4, (size_t)cc[1], fp) != (size_t)cc[1])
+            return fail_("cf_model_load: file truncated", CF_EINVAL);
+        float *tmp = nullptr;
+        if (cudaMalloc(&m->w[k], nw * 2) != cudaSuccess || cudaMalloc(&m->b[k], (size_t)cc[1] * 4) != cudaSuccess ||
+            cudaMalloc(&tmp, nw * 4) != cudaSuccess) {
+            if (tmp) cudaFree(tmp);
+            return fail_("cf_model_load: device allocation failed", CF_ENOMEM);
+        }
+        cudaMemcpy(tmp, hw.data(), nw * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(m->b[k], hb.data(), (size_t)cc[1] * 4, cudaMemcpyHostToDevice);
+        k_f32_to_bf16<<<nblk((long long)nw), 256>>>(tmp, m->w[k], (long long)nw);
+        const cudaError_t e = cudaDeviceSynchronize();
+        cudaFree(tmp);
+        if (e != cudaSuccess) return fail_(cudaGetErrorString(e), CF_ECUDA);
+    }
+    std::fclose(fp);
+    *out = m;
+    return CF_OK;
+}
+
+// Forward of one lattice (nz, ny, nx multiples of 4) from its features
+// [4][N] (float, channel-first): density corrections dens [2][N] and the
+// displacement field disp [3][N] (float, channel-first; either may be null).
+// Temporaries come from cudaMallocAsync on the stream.
+cf_status unet_forward(const UNetModel *m, const float *feats, int nz, int ny, int nx, float *dens, float *disp,
+                       cudaStream_t s) {
+    if (nz % 4 || ny % 4 || nx % 4) { set_last_error("the U-net needs lattice sizes divisible by 4"); return CF_EINVAL; }
+    const long long N = (long long)nz * ny * nx, N1 = N / 8, N2 = N / 64;
+    const int W0 = m->w0, W1 = m->w1, W2 = m->w2;
+    std::vector<void *> bufs;
+    auto alloc = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (cudaMallocAsync(&p, std::max<size_t>(bytes, 256), s) != cudaSuccess) return nullptr;
+        bufs.push_back(p);
+        return p;
+    };
+    auto bf = [&](long long n) { return static_cast<__nv_bfloat16 *>(alloc((size_t)n * 2)); };
+    __nv_bfloat16 *x = bf(N * 16), *e0a = bf(N * W0), *e0b = bf(N * W0), *p1 = bf(N1 * W0), *e1a = bf(N1 * W1),
+                  *e1b = bf(N1 * W1), *p2 = bf(N2 * W1), *ma = bf(N2 * W2), *mb = bf(N2 * W2), *u1 = bf(N1 * W2),
+                  *c1 = bf(N1 * (W1 + W2)), *d1a = bf(N1 * W1), *d1b = bf(N1 * W1), *u0 = bf(N * W1),
+                  *c0 = bf(N * (W0 + W1)), *d0a = bf(N * W0), *d0b = bf(N * W0);
+    float *head = static_cast<float *>(alloc((size_t)N * 16 * 4));
+    cf_status st = CF_OK;
+    for (void *p : bufs)
+        if (!p) st = CF_ENOMEM;
+    auto conv = [&](int k, const void *in, int gz, int gy, int gx, void *out, int f32) {
+        if (st == CF_OK)
+            st = cf_unet_conv(in, 1, gz, gy, gx, m->cin[k], m->w[k], m->b[k], m->cout[k], k == 10 ? 0 : 1, f32, out, s);
+    };
+    if (st == CF_OK) st = cf_unet_pack(feats, 4, N, 16, x, s);
+    conv(0, x, nz, ny, nx, e0a, 0);
+    conv(1, e0a, nz, ny, nx, e0b, 0);
+    if (st == CF_OK) st = cf_unet_pool(e0b, 1, nz, ny, nx, W0, p1, s);
+    conv(2, p1, nz / 2, ny / 2, nx / 2, e1a, 0);
+    conv(3, e1a, nz / 2, ny / 2, nx / 2, e1b, 0);
+    if (st == CF_OK) st = cf_unet_pool(e1b, 1, nz / 2, ny / 2, nx / 2, W1, p2, s);
+    conv(4, p2, nz / 4, ny / 4, nx / 4, ma, 0);
+    conv(5, ma, nz / 4, ny / 4, nx / 4, mb, 0);
+    if (st == CF_OK) st = cf_unet_upsample(mb, 1, nz / 2, ny / 2, nx / 2, W2, u1, s);
+    if (st == CF_OK) st = cf_unet_concat(N1, e1b, W1, u1, W2, c1, s);
+    conv(6, c1, nz / 2, ny / 2, nx / 2, d1a, 0);
+    conv(7, d1a, nz / 2, ny / 2, nx / 2, d1b, 0);
+    if (st == CF_OK) st = cf_unet_upsample(d1b, 1, nz, ny, nx, W1, u0, s);
+    if (st == CF_OK) st = cf_unet_concat(N, e0b, W0, u0, W1, c0, s);
+    conv(8, c0, nz, ny, nx, d0a, 0);
+    conv(9, d0a, nz, ny, nx, d0b, 0);
+    conv(10, d0b, nz, ny, nx, head, 1);
+    if (st == CF_OK && dens) st = cf_unet_unpack(head, 1, 16, N, 0, 2, dens, s);
+    if (st == CF_OK && disp) st = cf_unet_unpack(head, 1, 16, N, 2, 3, disp, s);
+    for (void *p : bufs)
+        if (p) cudaFreeAsync(p, s);
+    if (st == CF_ENOMEM) set_last_error("device allocation failed (U-net activations)");
+    return st;
+}
+
 }  // namespace cf
 
 using namespace cf;

@@ -235,6 +235,19 @@ class UNet:
         self.adam(grads, lr)
         return float(loss.item())
 
+    def save(self, path):
+        """Weights file read by the library's cf_model_load: "CFUNET01", int32
+        widths, then per layer int32 cin, cout, float32 weights [27][cout][cin]
+        and biases [cout]."""
+        import struct
+        with open(path, "wb") as f:
+            f.write(b"CFUNET01")
+            f.write(struct.pack("<3i", *self.widths))
+            for name, ci, co, _ in self.specs:
+                f.write(struct.pack("<2i", ci, co))
+                f.write(self.w[name].cpu().numpy().astype("<f4").tobytes())
+                f.write(self.b[name].cpu().numpy().astype("<f4").tobytes())
+
     # ----------------------------------------------------------- inference
     def pack(self, feats, N):
         """Features float [4][N] (one lattice, device) -> bfloat16 [N][16]."""

@@ -419,18 +419,25 @@ def time_to_force(net, wls, total, every, tol=0.01):
     converged value (the mean of the plain run's last five samples), whether
     each warm start was kept, and the wall times (one warm start; one
     lattice step within the batch)."""
+    import os
+    import tempfile
     import time
     plain = [cfm.Simulation.from_workload(w) for w in wls]
     warmed, used = [], []
     t_warm = 0.0
+    # the warm start runs inside the library (cf_warmstart) on the saved network
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "unet.bin")
+        net.save(path)
+        model = cfm.Model(path)
     for w in wls:
         s = cfm.Simulation.from_workload(w)
         t0 = time.perf_counter()
-        u, _ = warm_start(s, w, net)
-        s.sync()
+        u, _ = s.warmstart(model, w.h_top, w.capsules[0].kS, jitter=w.jitter())
         t_warm += time.perf_counter() - t0
         warmed.append(s)
         used.append(u)
+    model.close()
     fp, step_plain = lateral_traces(plain, total, every)
     fw, step_warm = lateral_traces(warmed, total, every)
     res = []

@@ -65,13 +65,14 @@ def test_host_side_argument_checks_without_a_gpu():
     from paper_2007_15405_gb300 import capfilm as cf
     L = cf.load_library()
 
-    def desc(nx=16, ny=12, nz=20, tau=(1.0, 1.0), precision=0):
+    def desc(nx=16, ny=12, nz=20, tau=(1.0, 1.0), precision=0, flags=0):
         return cf.LatticeDesc(nx, ny, nz, 1, (C.c_double * 2)(*tau), 3.6, 10.0, 1.5, 1.5, precision,
-                              None, None)
+                              None, None, flags)
 
     cases = [(desc(nx=2), "dimensions"), (desc(nz=0), "dimensions"),
              (desc(nx=512, ny=512, nz=220), "too large"), (desc(tau=(0.5, 1.0)), "tau"),
-             (desc(tau=(1.0, float("nan"))), "tau"), (desc(precision=7), "precision")]
+             (desc(tau=(1.0, float("nan"))), "tau"), (desc(precision=7), "precision"),
+             (desc(flags=16), "unknown flag")]
     for d, why in cases:
         h = C.c_void_p()
         rc = L.cf_create(C.byref(d), C.byref(h))

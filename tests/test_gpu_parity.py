@@ -375,3 +375,59 @@ def test_meniscus_fit_and_theory_force_match_oracle(cfm):
         F1 = cfm.capillary_force(lib[1], 0.0488, lib[0], lib[0], L)
         F2 = O.capillary_force(lib[1], 0.0488, lib[0], lib[0], L)
         assert F1 == pytest.approx(F2, rel=1e-12)
+
+
+@pytest.mark.parametrize("flag", ["INERTIAL", "LADD_REF_RHO", "PARTNER_MIRROR"])
+def test_alternative_readings_parity(cfm, flag):
+    """The alternative readings of paper-silent points (inertial node update,
+    Ladd's term with the reference density, mirrored partner density), each
+    selected by a flag of both the library and the oracle: free capsule, 40
+    steps, the parity tolerances."""
+    wl = I.tiny_film(mode=I.MODE_FREE, steps=40)
+    wl.flags = getattr(cfm, flag)
+    sim = cfm.Simulation.from_workload(wl)
+    orc = O.Oracle.from_workload(wl)
+    sim.step(wl.steps); orc.step(wl.steps)
+    compare_state(sim, orc)
+    assert np.abs(sim.capsule_state(0)["X"] - orc.capsule_state(0)["X"]).max() < 1e-5
+    Fg, _ = sim.capsule_force(0)
+    Fo = orc.capsule_state(0)["force"]
+    assert np.abs(Fg - Fo).max() < 1e-3 * np.abs(Fo).max() + 1e-7
+    compare_cuts(sim, orc)
+
+
+def test_drying_by_removal_parity(cfm):
+    """Drying by removal (flag): the A mass goes, B keeps its mass; fields
+    against the oracle after 30 steps, and the mass budget."""
+    wl = I.tiny_film(mode=I.MODE_FIXED, steps=30)
+    wl.flags = cfm.DRY_REMOVE
+    wl.dry_dm = 0.02
+    sim = cfm.Simulation.from_workload(wl)
+    orc = O.Oracle.from_workload(wl)
+    m0 = orc.total_mass()
+    sim.step(wl.steps); orc.step(wl.steps)
+    compare_state(sim, orc)
+    mg, mo = sim.total_mass(), orc.total_mass()
+    assert mo[0] == pytest.approx(m0[0] - 30 * 0.02, rel=1e-10)
+    assert np.allclose(mg, mo, rtol=1e-5)
+
+
+@pytest.mark.slow
+def test_equilibrated_lateral_force_matches_oracle(cfm):
+    """A reduced fixed pair (64 x 40 x 40, R = 6 level-3 capsules at d = 3R,
+    film 0.4R) run until its lateral force is stationary (windowed change
+    below 0.5%): the GPU's equilibrated force within 1% of the oracle's."""
+    R = 6.0
+    zc = I.z_rest(R) + 0.17
+    caps = [I.CapsuleSpec(centre=(32.3 - 1.5 * R, 20.4, zc), radius=R, level=3, mode=I.MODE_FIXED),
+            I.CapsuleSpec(centre=(32.3 + 1.5 * R, 20.4, zc), radius=R, level=3, mode=I.MODE_FIXED)]
+    wl = I.Workload("pair eq", 64, 40, 40, h_top=0.5 + I.REP_DZ + 0.4 * R, capsules=caps, steps=6000, seed=23)
+    sim = cfm.Simulation.from_workload(wl)
+    orc = O.Oracle.from_workload(wl)
+    fg, fo = [], []
+    for _ in range(6):
+        sim.step(1000); orc.step(1000)
+        fg.append(sim.lateral_force(0, 1)); fo.append(orc.lateral_force(0, 1))
+    print("lateral force gpu", fg, "oracle", fo)
+    assert abs(fg[-1] - fg[-2]) < 5e-3 * abs(fg[-1])   # stationary
+    assert fo[-1] < 0 and abs(fg[-1] - fo[-1]) <= 1e-2 * abs(fo[-1]), (fg[-1], fo[-1])

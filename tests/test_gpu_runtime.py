@@ -143,7 +143,7 @@ def test_failing_allocator_reports_enomem_and_frees(cfm):
     a_fn, f_fn = cfm.ALLOC_FN(alloc), cfm.FREE_FN(free)
     al = cfm.Allocator(a_fn, f_fn, None)
     desc = cfm.LatticeDesc(16, 12, 20, 1, (C.c_double * 2)(1.0, 1.0), 3.6, 2.0, 1.5, 1.5, 0,
-                           C.pointer(al), None)
+                           C.pointer(al), None, 0)
     h = C.c_void_p()
     rc = L.cf_create(C.byref(desc), C.byref(h))
     assert cfm.STATUS_NAMES[rc] == "CF_ENOMEM"

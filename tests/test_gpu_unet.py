@@ -274,12 +274,15 @@ def test_unet_forward_backward_match_fp64_composition(env):
     gp1 = back("e1a", ge1a)
     ge0a = back("e0b", ge0b_skip, W.avg_pool2_backward(gp1))
     back("e0a", ge0a)
+    # the reference carries the input gradients in FP64, the GPU in float32:
+    # where a masked gradient sits at a bfloat16 rounding boundary the two
+    # round it one ulp (2^-8) apart, so the bound is on the bfloat16 scale
     for name in net.w:
         gw, gb = grads[name]
         rw, rb = ref_gw[name]
         rw = rw.reshape(-1)
-        assert np.abs(host(gw) - rw).max() <= 1e-3 * np.abs(rw).max() + 1e-9, name
-        assert np.abs(host(gb) - rb).max() <= 1e-3 * np.abs(rb).max() + 1e-9, name
+        assert np.abs(host(gw) - rw).max() <= 1e-2 * np.abs(rw).max() + 1e-9, name
+        assert np.abs(host(gb) - rb).max() <= 1e-2 * np.abs(rb).max() + 1e-9, name
 
 
 def test_unet_training_is_reproducible_and_learns(env):
@@ -304,3 +307,34 @@ def test_unet_training_is_reproducible_and_learns(env):
     assert out[0][0] == out[1][0]
     assert all(torch.equal(out[0][1][k], out[1][1][k]) for k in out[0][1])
     assert out[0][0][-1] < 0.5 * out[0][0][0]
+
+
+# ---------------------------------------------------- the library's warm start
+def test_library_warm_start_equals_python_path_and_falls_back(env, tmp_path):
+    """cf_model_load + cf_warmstart (inference, predicted state and judging
+    inside the library) give bitwise the state of the Python orchestration of
+    the same kernels (features, U-net, cf_warm_apply, the same judging
+    steps); a policy that cannot be met restores the flat film."""
+    torch, cfm = env
+    from paper_2007_15405_gb300 import inputs as I, unet as U, warm
+    wl = I.warm_pair_dataset(1, seed=3, nx=48, ny=32, nz=32, radius=5.0, level=2)[0]
+    net = U.UNet(widths=(16, 32, 32), seed=5)
+    path = str(tmp_path / "unet.bin")
+    net.save(path)
+    model = cfm.Model(path)
+    a = cfm.Simulation.from_workload(wl, set_film=False)
+    used, steps = a.warmstart(model, wl.h_top, wl.capsules[0].kS, window=10, u_limit=1.0, grow=1e9)
+    assert used and steps == 21
+    b = cfm.Simulation.from_workload(wl, set_film=False)
+    x, _ = warm.features_dev(b, wl)
+    d = net.predict_dev(x, (wl.nz, wl.ny, wl.nx))
+    b.warm_apply(wl.h_top, I.RHO_MAJ, I.RHO_MIN, I.RHO_MIX, d)
+    b.step(1); b.field_check(); b.step(10); b.field_check(); b.step(10); b.field_check()
+    assert np.array_equal(a.populations(), b.populations())
+    # a velocity limit nothing meets: back to the flat film
+    c = cfm.Simulation.from_workload(wl, set_film=False)
+    used, _ = c.warmstart(model, wl.h_top, wl.capsules[0].kS, jitter=wl.jitter(), window=5, u_limit=1e-30)
+    assert not used
+    f = cfm.Simulation.from_workload(wl)
+    assert np.array_equal(c.populations(), f.populations())
+    model.close()
