@@ -118,6 +118,9 @@ struct cf_ctx {
           *Fcpl = nullptr, *refM = nullptr, *refA = nullptr, *refDet = nullptr;
     int *faces = nullptr, *face_cap = nullptr, *node_cap = nullptr, *vf_off = nullptr,
         *vf_ent = nullptr, *bbox[2] = {nullptr, nullptr};
+    int *perm = nullptr;      // node of each patch slot (-1: padding), see MemParams
+    float *pbox = nullptr;    // patch boxes of this step
+    int nslots = 0;
     CapDev *capdev = nullptr;
     double *acc = nullptr;
     std::vector<void *> mem_allocs;
@@ -248,13 +251,14 @@ MemParams mem_params(cf_ctx *c) {
     p.status = c->status;
     p.any_frozen = c->any_frozen ? 1 : 0;
     p.inertial = (c->d.flags & CF_INERTIAL) ? 1 : 0;
+    p.perm = c->perm;
+    p.nslots = c->nslots;
+    p.pbox = c->pbox;
     return p;
 }
 
-// Cut links for positions X (cur list lpar, clears the other list's nodes).
-// zeroed: the node update has already zeroed the new list's entry counter
-cf_status enqueue_cuts(cf_ctx *c, const float *X, int *nl, bool zeroed = false) {
-    if (c->nfaces == 0) return CF_OK;
+// Cut links of positions X into the list other than lpar (the caller flips lpar)
+CutParams cut_params(cf_ctx *c, const float *X) {
     const int cur = 1 - c->lpar;
     CutParams q{};
     q.nx = c->d.nx; q.ny = c->d.ny; q.nz = c->d.nz; q.wall = c->d.wall;
@@ -270,10 +274,55 @@ cf_status enqueue_cuts(cf_ctx *c, const float *X, int *nl, bool zeroed = false) 
     q.uT = c->uT;
     q.capacity = c->capacity;
     q.status = c->status;
+    return q;
+}
+
+// Cut links for positions X (cur list lpar, clears the other list's nodes).
+// zeroed: the node update has already zeroed the new list's entry counter
+cf_status enqueue_cuts(cf_ctx *c, const float *X, int *nl, bool zeroed = false) {
+    if (c->nfaces == 0) return CF_OK;
+    const int cur = 1 - c->lpar;
+    const CutParams q = cut_params(c, X);
     if (!zeroed) CF_CUDA(cudaMemsetAsync(c->counts + cur, 0, sizeof(int), c->stream));
     CF_CUDA(launch_cuts(q, c->stream, nl));
     c->lpar = cur;
     return CF_OK;
+}
+
+// bounce records of the cut links for this step's streaming
+PrepParams prep_params(cf_ctx *c, int blocks) {
+    PrepParams q{};
+    q.N = c->N;
+    q.prec = c->d.precision;
+    q.src = c->f[c->fpar];
+    q.rho = c->rho[c->fpar];
+    q.mask = c->mask;
+    q.tri = c->tri;
+    q.uT = c->uT;
+    q.list = c->list[c->lpar];
+    q.count = c->counts + c->lpar;
+    q.rec = c->rec;
+    q.FT = c->FT[c->ftpar];
+    q.capacity = c->capacity;
+    q.ref_rho = (c->d.flags & CF_LADD_REF_RHO) ? 1 : 0;
+    q.blocks = blocks;
+    return q;
+}
+
+// reset of the cut structure about to be rebuilt, by `blocks` extra blocks of
+// the node update (none for fixed capsules, whose cut links never move)
+ClearParams clear_params(cf_ctx *c, int blocks) {
+    ClearParams cl{};
+    if (!c->all_fixed) {
+        cl.list = c->list[c->lpar];
+        cl.count = c->counts + c->lpar;
+        cl.capacity = c->capacity;
+        cl.mask = c->mask;
+        cl.tri = c->tri;
+        cl.blocks = blocks;
+        cl.count_next = c->counts + (1 - c->lpar);  // the cut links' memset, done by the update
+    }
+    return cl;
 }
 
 // One coupled step on the stream (also used under graph capture).  ev, when
@@ -301,21 +350,7 @@ cf_status enqueue_pre(cf_ctx *c, int *nl) {
     CF_CUDA(launch_membrane_forces(mem_params(c), c->stream2, nl));
     CF_CUDA(cudaEventRecord(c->ev_join, c->stream2));
     // bounce records of the cut links for this step's streaming
-    PrepParams q{};
-    q.N = c->N;
-    q.prec = c->d.precision;
-    q.src = c->f[c->fpar];
-    q.rho = c->rho[c->fpar];
-    q.mask = c->mask;
-    q.tri = c->tri;
-    q.uT = c->uT;
-    q.list = c->list[c->lpar];
-    q.count = c->counts + c->lpar;
-    q.rec = c->rec;
-    q.FT = c->FT[c->ftpar];
-    q.capacity = c->capacity;
-    q.ref_rho = (c->d.flags & CF_LADD_REF_RHO) ? 1 : 0;
-    CF_CUDA(launch_prep(q, c->stream, nl));
+    CF_CUDA(launch_prep(prep_params(c, 2 * 152), c->stream, nl));
     return CF_OK;
 }
 
@@ -327,17 +362,7 @@ cf_status enqueue_post(cf_ctx *c, int *nl, cudaEvent_t ev2 = nullptr) {
     if (mem) {
         CF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
         // extra blocks of the update reset the cut structure about to be rebuilt
-        ClearParams cl{};
-        if (!c->all_fixed) {
-            cl.list = c->list[c->lpar];
-            cl.count = c->counts + c->lpar;
-            cl.capacity = c->capacity;
-            cl.mask = c->mask;
-            cl.tri = c->tri;
-            cl.blocks = 304;
-            cl.count_next = c->counts + (1 - c->lpar);  // the cut links' memset, done by the update
-        }
-        CF_CUDA(launch_membrane_update(mem_params(c), cl, c->any_frozen, c->stream, nl));
+        CF_CUDA(launch_membrane_update(mem_params(c), clear_params(c, 304), c->any_frozen, c->stream, nl));
         c->xpar = 1 - c->xpar;
     }
     if (ev2) CF_CUDA(cudaEventRecord(ev2, c->stream));
@@ -465,6 +490,34 @@ cf_status build_membrane(cf_ctx *c) {
         vf_off[v + 1] = vf_off[v] + (int)vf[v].size();
         for (int e : vf[v]) vf_ent.push_back(e);
     }
+    // contact patches: each capsule's nodes in Morton order of their positions
+    // (10 bits per axis over the capsule's box), 32 slots per patch
+    std::vector<int> perm;
+    for (int k = 0; k < nc; ++k) {
+        CapDev &d = cd[k];
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int i = d.v0; i < d.v0 + d.nv; ++i)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = std::min(lo[a], X[3 * (size_t)i + a]);
+                hi[a] = std::max(hi[a], X[3 * (size_t)i + a]);
+            }
+        std::vector<std::pair<unsigned long long, int>> key(d.nv);
+        for (int i = 0; i < d.nv; ++i) {
+            unsigned long long m = 0;
+            for (int a = 0; a < 3; ++a) {
+                const double span = hi[a] - lo[a];
+                const double t = span > 0.0 ? (X[3 * (size_t)(d.v0 + i) + a] - lo[a]) / span : 0.0;
+                const unsigned q = (unsigned)std::min(1023.0, std::max(0.0, std::floor(t * 1024.0)));
+                for (int bit = 0; bit < 10; ++bit) m |= (unsigned long long)((q >> bit) & 1u) << (3 * bit + a);
+            }
+            key[i] = {m, d.v0 + i};
+        }
+        std::sort(key.begin(), key.end());
+        d.s0 = (int)perm.size();
+        d.ns = 32 * ((d.nv + 31) / 32);
+        for (int i = 0; i < d.ns; ++i) perm.push_back(i < d.nv ? key[i].second : -1);
+    }
+    c->nslots = (int)perm.size();
     auto up = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
         return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream);
     };
@@ -493,6 +546,8 @@ cf_status build_membrane(cf_ctx *c) {
     MALLOC_M(c->bbox[0], int, 6 * nc);
     MALLOC_M(c->bbox[1], int, 6 * nc);
     MALLOC_M(c->capdev, CapDev, nc);
+    MALLOC_M(c->perm, int, c->nslots);
+    MALLOC_M(c->pbox, float, 6 * (c->nslots / 32));
     MALLOC_M(c->acc, double, A_NACC * nc);
     c->wet_el = nullptr;
     bool any_wet = false;
@@ -542,6 +597,7 @@ cf_status build_membrane(cf_ctx *c) {
     CF_CUDA(up(c->vf_off, vf_off.data(), sizeof(int) * vf_off.size()));
     CF_CUDA(up(c->vf_ent, vf_ent.data(), sizeof(int) * vf_ent.size()));
     CF_CUDA(up(c->capdev, cd.data(), sizeof(CapDev) * cd.size()));
+    CF_CUDA(up(c->perm, perm.data(), sizeof(int) * perm.size()));
     // cut-link lists: one entry per end node of each crossing (link, element);
     // an element of edge < 1 crosses a few links, 24 entries per element is a
     // wide bound (overflow raises CF_EOVERFLOW)
@@ -1405,7 +1461,7 @@ struct cf_batch {
     std::vector<cf_ctx *> ctx;
     int prec = 0;
     cudaStream_t stream = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_lat = nullptr;
+    cudaEvent_t ev_fork = nullptr;
     int tile = 1, zchunk = 4;     // tile shape index and contiguous planes per work item
     int groups = 1;               // pipeline groups
     int4 *work = nullptr;          // device work list of all lattices (one launch)
@@ -1414,6 +1470,8 @@ struct cf_batch {
     std::vector<int> gbeg;                 // [groups + 1] context ranges of the groups
     std::vector<cudaStream_t> gstream;     // [CF_MAX_GROUPS] stream branch per group
     std::vector<cudaEvent_t> gev;          // [CF_MAX_GROUPS] after the group's lattice passes
+    std::vector<cudaStream_t> gmem;        // [CF_MAX_GROUPS] the group's position-only membrane kernels
+    std::vector<cudaEvent_t> gfork, gjoin; // [CF_MAX_GROUPS] around them
     std::vector<int4 *> gwork;             // per group: work list (lattice index within the group)
     std::vector<int> gnwork;
     cudaGraphExec_t graph = nullptr;
@@ -1486,6 +1544,95 @@ cf_status batch_build_work(cf_batch *b) {
     return CF_OK;
 }
 
+// The membrane and cut-link kernels of contexts [i0, i1) as one launch per
+// kernel (per 64 contexts).  Before the lattice passes: the position-only
+// membrane kernels fork onto the group's membrane stream `sm` (joined by the
+// node update), the bounce records go on the lattice stream `s`.
+cf_status batch_pre(cf_batch *b, int g, int i0, int i1, cudaStream_t s, int *nl) {
+    static SparseTab<MemParams> tv, tf;  // copied into each launch
+    static SparseTab<PrepParams> tp;
+    std::vector<cf_ctx *> mem;
+    for (int i = i0; i < i1; ++i)
+        if (b->ctx[i]->nnodes > 0) mem.push_back(b->ctx[i]);
+    CF_CUDA(cudaEventRecord(b->gfork[g], s));
+    CF_CUDA(cudaStreamWaitEvent(b->gmem[g], b->gfork[g], 0));
+    // bounce-record blocks per context: about four per SM over the group
+    const int pb = std::max(4, std::min(304, (int)((4 * 152 + mem.size() - 1) / std::max<size_t>(mem.size(), 1))));
+    for (size_t j0 = 0; j0 < mem.size(); j0 += CF_SPARSE_CAP) {
+        const int n = (int)std::min<size_t>(CF_SPARSE_CAP, mem.size() - j0);
+        tv.n = tf.n = tp.n = n;
+        tv.boff[0] = tf.boff[0] = tp.boff[0] = 0;
+        for (int j = 0; j < n; ++j) {
+            cf_ctx *c = mem[j0 + j];
+            tv.p[j] = tf.p[j] = mem_params(c);
+            tv.boff[j + 1] = tv.boff[j] + c->nslots / CF_MEM_NODE_BLOCK;  // one warp per patch
+            tf.boff[j + 1] = tf.boff[j] + (c->nfaces + CF_MEM_FACE_BLOCK - 1) / CF_MEM_FACE_BLOCK;
+            tp.p[j] = prep_params(c, pb);
+            tp.boff[j + 1] = tp.boff[j] + pb;
+        }
+        CF_CUDA(launch_membrane_forces_batch(tv, tf, b->gmem[g], nl));
+        CF_CUDA(launch_prep_batch(tp, s, nl));
+    }
+    CF_CUDA(cudaEventRecord(b->gjoin[g], b->gmem[g]));
+    return CF_OK;
+}
+
+// After the lattice passes of contexts [i0, i1) (whose populations are now in
+// f[fpar]): node update with the reset of the old cut structure, then the cut
+// links of the new positions (fixed capsules: only the next step's exchange
+// accumulator is zeroed).
+cf_status batch_post(cf_batch *b, int g, int i0, int i1, cudaStream_t s, int *nl) {
+    static SparseTab<UpdateParams> tu;
+    static SparseTab<MemParams> tz;
+    static SparseTab<CutParams> tc;
+    std::vector<cf_ctx *> mem;
+    for (int i = i0; i < i1; ++i)
+        if (b->ctx[i]->nnodes > 0) mem.push_back(b->ctx[i]);
+    CF_CUDA(cudaStreamWaitEvent(s, b->gjoin[g], 0));
+    const int cb = 32;  // reset blocks per context
+    for (size_t j0 = 0; j0 < mem.size(); j0 += CF_SPARSE_CAP) {
+        const int n = (int)std::min<size_t>(CF_SPARSE_CAP, mem.size() - j0);
+        tu.n = n;
+        tz.n = 0;
+        tu.boff[0] = tz.boff[0] = 0;
+        for (int j = 0; j < n; ++j) {
+            cf_ctx *c = mem[j0 + j];
+            tu.p[j].m = mem_params(c);
+            tu.p[j].c = clear_params(c, cb);
+            const int nb = (c->nnodes + CF_MEM_NODE_BLOCK - 1) / CF_MEM_NODE_BLOCK;
+            tu.boff[j + 1] = tu.boff[j] + nb + tu.p[j].c.blocks;
+            if (c->any_frozen) {
+                tz.p[tz.n] = tu.p[j].m;
+                tz.boff[tz.n + 1] = tz.boff[tz.n] + nb;
+                ++tz.n;
+            }
+        }
+        CF_CUDA(launch_membrane_update_batch(tu, tz.n ? &tz : nullptr, s, nl));
+    }
+    for (cf_ctx *c : mem) c->xpar = 1 - c->xpar;
+    for (size_t j0 = 0; j0 < mem.size(); j0 += CF_SPARSE_CAP) {
+        const int n = (int)std::min<size_t>(CF_SPARSE_CAP, mem.size() - j0);
+        tc.n = n;
+        tc.boff[0] = 0;
+        for (int j = 0; j < n; ++j) {
+            cf_ctx *c = mem[j0 + j];
+            if (!c->all_fixed) {
+                tc.p[j] = cut_params(c, c->X[c->xpar]);  // entry counter zeroed by the update
+                c->lpar = 1 - c->lpar;
+            } else {
+                tc.p[j] = CutParams{};
+                tc.p[j].nfaces = c->nfaces;
+                tc.p[j].FTnext = c->FT[1 - c->ftpar];
+                tc.p[j].zero_only = 1;
+            }
+            tc.boff[j + 1] = tc.boff[j] + cut_blocks(c->nfaces);
+        }
+        CF_CUDA(launch_cuts_batch(tc, s, nl));
+    }
+    for (cf_ctx *c : mem) c->ftpar = 1 - c->ftpar;
+    return CF_OK;
+}
+
 // one step with the contexts in pipeline groups (see cf_batch)
 cf_status batch_enqueue_groups(cf_batch *b, bool with_out, int *nl) {
     CF_CUDA(cudaEventRecord(b->ev_fork, b->stream));
@@ -1494,14 +1641,8 @@ cf_status batch_enqueue_groups(cf_batch *b, bool with_out, int *nl) {
     for (int g = 0; g < ng; ++g) {
         cudaStream_t gs = b->gstream[g];
         CF_CUDA(cudaStreamWaitEvent(gs, b->ev_fork, 0));
-        for (int i = b->gbeg[g]; i < b->gbeg[g + 1]; ++i) {
-            cf_ctx *c = b->ctx[i];
-            CF_CUDA(cudaStreamWaitEvent(c->stream, b->ev_fork, 0));
-            cf_status s = enqueue_pre(c, nl);
-            if (s != CF_OK) return s;
-            CF_CUDA(cudaEventRecord(c->ev_batch, c->stream));
-            CF_CUDA(cudaStreamWaitEvent(gs, c->ev_batch, 0));
-        }
+        cf_status s = batch_pre(b, g, b->gbeg[g], b->gbeg[g + 1], gs, nl);
+        if (s != CF_OK) return s;
         for (int i = b->gbeg[g]; i < b->gbeg[g + 1]; ++i) {
             LBParams &l = tab.lat[i - b->gbeg[g]];
             l = lb_params(b->ctx[i], with_out);
@@ -1510,17 +1651,11 @@ cf_status batch_enqueue_groups(cf_batch *b, bool with_out, int *nl) {
         }
         CF_CUDA(launch_lb_batch(tab, b->gbeg[g + 1] - b->gbeg[g], b->gwork[g], b->gnwork[g], b->prec, b->tile, gs));
         *nl += 2;
+        for (int i = b->gbeg[g]; i < b->gbeg[g + 1]; ++i) b->ctx[i]->fpar = 1 - b->ctx[i]->fpar;
+        s = batch_post(b, g, b->gbeg[g], b->gbeg[g + 1], gs, nl);
+        if (s != CF_OK) return s;
         CF_CUDA(cudaEventRecord(b->gev[g], gs));
         CF_CUDA(cudaStreamWaitEvent(b->stream, b->gev[g], 0));
-        for (int i = b->gbeg[g]; i < b->gbeg[g + 1]; ++i) {
-            cf_ctx *c = b->ctx[i];
-            c->fpar = 1 - c->fpar;
-            CF_CUDA(cudaStreamWaitEvent(c->stream, b->gev[g], 0));
-            cf_status s = enqueue_post(c, nl);
-            if (s != CF_OK) return s;
-            CF_CUDA(cudaEventRecord(c->ev_batch, c->stream));
-            CF_CUDA(cudaStreamWaitEvent(b->stream, c->ev_batch, 0));
-        }
     }
     return CF_OK;
 }
@@ -1533,14 +1668,9 @@ cf_status batch_enqueue_groups(cf_batch *b, bool with_out, int *nl) {
 cf_status batch_enqueue_step(cf_batch *b, bool with_out, int *nl, cudaEvent_t *ev = nullptr) {
     if (!ev && b->gbeg.size() > 2) return batch_enqueue_groups(b, with_out, nl);
     if (ev) CF_CUDA(cudaEventRecord(ev[0], b->stream));
-    CF_CUDA(cudaEventRecord(b->ev_fork, b->stream));
-    for (cf_ctx *c : b->ctx) {
-        CF_CUDA(cudaStreamWaitEvent(c->stream, b->ev_fork, 0));
-        cf_status s = enqueue_pre(c, nl);
-        if (s != CF_OK) return s;
-        CF_CUDA(cudaEventRecord(c->ev_batch, c->stream));
-        CF_CUDA(cudaStreamWaitEvent(b->stream, c->ev_batch, 0));
-    }
+    const int n = (int)b->ctx.size();
+    cf_status s = batch_pre(b, 0, 0, n, b->stream, nl);
+    if (s != CF_OK) return s;
     static BatchTab tab;  // copied into the launch
     for (size_t i = 0; i < b->ctx.size(); ++i) {
         tab.lat[i] = lb_params(b->ctx[i], with_out);
@@ -1551,15 +1681,9 @@ cf_status batch_enqueue_step(cf_batch *b, bool with_out, int *nl, cudaEvent_t *e
     CF_CUDA(launch_lb_batch(tab, (int)b->ctx.size(), b->work, b->nwork, b->prec, b->tile, b->stream));
     *nl += 2;
     if (ev) CF_CUDA(cudaEventRecord(ev[2], b->stream));
-    CF_CUDA(cudaEventRecord(b->ev_lat, b->stream));
-    for (cf_ctx *c : b->ctx) {
-        c->fpar = 1 - c->fpar;
-        CF_CUDA(cudaStreamWaitEvent(c->stream, b->ev_lat, 0));
-        cf_status s = enqueue_post(c, nl);
-        if (s != CF_OK) return s;
-        CF_CUDA(cudaEventRecord(c->ev_batch, c->stream));
-        CF_CUDA(cudaStreamWaitEvent(b->stream, c->ev_batch, 0));
-    }
+    for (cf_ctx *c : b->ctx) c->fpar = 1 - c->fpar;
+    s = batch_post(b, 0, 0, n, b->stream, nl);
+    if (s != CF_OK) return s;
     if (ev) CF_CUDA(cudaEventRecord(ev[3], b->stream));
     return CF_OK;
 }
@@ -1592,9 +1716,21 @@ cf_status batch_graph(cf_batch *b) {
     return CF_OK;
 }
 
+// work a context still has in flight on its own stream comes first (the batch
+// step runs all of its kernels on the batch's streams)
+cf_status batch_join_contexts(cf_batch *b) {
+    for (cf_ctx *c : b->ctx) {
+        CF_CUDA(cudaEventRecord(c->ev_batch, c->stream));
+        CF_CUDA(cudaStreamWaitEvent(b->stream, c->ev_batch, 0));
+    }
+    return CF_OK;
+}
+
 // pairs graph replays (2 * pairs steps; the fields readout is not refreshed)
 cf_status batch_replay(cf_batch *b, int pairs) {
-    cf_status s = batch_graph(b);
+    cf_status s = batch_join_contexts(b);
+    if (s != CF_OK) return s;
+    s = batch_graph(b);
     if (s != CF_OK) return s;
     for (int k = 0; k < pairs; ++k) CF_CUDA(cudaGraphLaunch(b->graph, b->stream));
     for (cf_ctx *c : b->ctx) c->steps_done += 2 * pairs;
@@ -1606,6 +1742,8 @@ cf_status batch_run(cf_batch *b, long long n) {
     for (cf_ctx *c : b->ctx)
         if (c->dry_dm > 0.0) return fail(CF_ESTATE, "drying (cf_remove_mass) is not available in a batch");
     int nl = 0;
+    cf_status sj = batch_join_contexts(b);
+    if (sj != CF_OK) return sj;
     long long left = n - 1;  // the last step records the fields
     if (left >= 3 && b->graph && b->graph_key != batch_key(b)) {
         // one plain step brings every context to the captured graph's parity
@@ -1664,12 +1802,17 @@ cf_status cf_batch_create(cf_ctx *const *ctxs, int n, cf_batch **out) {
     b->prec = ctxs[0]->d.precision;
     b->gstream.assign(CF_MAX_GROUPS, nullptr);
     b->gev.assign(CF_MAX_GROUPS, nullptr);
+    b->gmem.assign(CF_MAX_GROUPS, nullptr);
+    b->gfork.assign(CF_MAX_GROUPS, nullptr);
+    b->gjoin.assign(CF_MAX_GROUPS, nullptr);
     bool ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
-              cudaEventCreateWithFlags(&b->ev_lat, cudaEventDisableTiming) == cudaSuccess;
+              cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
     for (int g = 0; ok && g < CF_MAX_GROUPS; ++g)
         ok = cudaStreamCreateWithFlags(&b->gstream[g], cudaStreamNonBlocking) == cudaSuccess &&
-             cudaEventCreateWithFlags(&b->gev[g], cudaEventDisableTiming) == cudaSuccess;
+             cudaEventCreateWithFlags(&b->gev[g], cudaEventDisableTiming) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&b->gmem[g], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->gfork[g], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->gjoin[g], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         cf_batch_destroy(b);
         return fail(CF_ECUDA, "stream / event creation failed");
@@ -1694,10 +1837,15 @@ cf_status cf_batch_destroy(cf_batch *b) {
         if (w) cudaFree(w);
     for (cudaStream_t gs : b->gstream)
         if (gs) cudaStreamDestroy(gs);
+    for (cudaStream_t gs : b->gmem)
+        if (gs) cudaStreamDestroy(gs);
     for (cudaEvent_t e : b->gev)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->gfork)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->gjoin)
+        if (e) cudaEventDestroy(e);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
-    if (b->ev_lat) cudaEventDestroy(b->ev_lat);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
     return CF_OK;
@@ -1764,7 +1912,7 @@ cf_status cf_batch_time_phases(cf_batch *b, long long n, double ms[3]) {
     std::vector<cudaEvent_t> ev(4 * (size_t)n);
     for (auto &e : ev) CF_CUDA(cudaEventCreate(&e));
     int nl = 0;
-    cf_status st = CF_OK;
+    cf_status st = batch_join_contexts(b);
     for (long long k = 0; k < n && st == CF_OK; ++k) st = batch_enqueue_step(b, k == n - 1, &nl, &ev[4 * k]);
     CF_CUDA(cudaStreamSynchronize(b->stream));
     ms[0] = ms[1] = ms[2] = 0.0;

@@ -132,6 +132,7 @@ struct CapDev {
     float kS, C, kB, kV, mass;
     int mode;               // 0 free, 1 frozen, 2 fixed
     int v0, nv, f0, nf;     // global offsets and counts
+    int s0, ns;             // node slots [s0, s0 + ns) of the capsule's patches (ns: multiple of 32)
     double V0;              // reference volume
 };
 
@@ -170,6 +171,13 @@ struct MemParams {
     unsigned *status;        // device error flags
     int any_frozen;
     int inertial;            // CF_INERTIAL: v += F/m, x += v
+    // Contact prefilter: each capsule's nodes in patches of 32 neighbouring
+    // nodes (Morton order of the shape the capsule was added with); slot s of
+    // patch s / 32 holds node perm[s] (-1: padding at a capsule's last patch).
+    // The node kernel runs one warp per patch and writes its box.
+    const int *perm;         // [nslots]
+    int nslots;
+    float *pbox;             // [nslots / 32][6]: float min x, y, z, max x, y, z of this step
 };
 
 // per-element scratch layout (floats)
@@ -189,6 +197,7 @@ struct CutParams {
     float4 *uT;              // [nfaces] element velocities (written here)
     int capacity;
     unsigned *status;
+    int zero_only;           // fixed capsules: only zero FTnext (the cut links never move)
 };
 
 // Reset of the previous cut structure, run by extra blocks of the node-update
@@ -218,6 +227,23 @@ struct PrepParams {
     float *FT;               // element momentum exchange accumulators
     int capacity;
     int ref_rho;             // CF_LADD_REF_RHO: Ladd's term with rho_0 = 1
+    int blocks;              // blocks striding over the list
+};
+
+// The membrane and cut-link kernels of many lattices in one launch: entry i
+// holds lattice i's parameters, its blocks are [boff[i], boff[i+1]) of the
+// grid.  Travels by value in the launch (64 x 272 B stays under the 32 KB
+// launch-parameter limit); larger batches take one launch per 64 lattices.
+constexpr int CF_SPARSE_CAP = 64;
+template <class P>
+struct SparseTab {
+    int n;
+    int boff[CF_SPARSE_CAP + 1];
+    P p[CF_SPARSE_CAP];
+};
+struct UpdateParams {
+    MemParams m;
+    ClearParams c;
 };
 
 __host__ __device__ inline int wrapi(int a, int n) {
@@ -295,4 +321,15 @@ cudaError_t launch_membrane_update(const MemParams &p, const ClearParams &cl, bo
                                    cudaStream_t s, int *nlaunch);
 cudaError_t launch_cuts(const CutParams &p, cudaStream_t s, int *nlaunch);
 cudaError_t launch_prep(const PrepParams &p, cudaStream_t s, int *nlaunch);
+// batched forms (one launch per kernel for all lattices of the tables); tv:
+// node-kernel blocks (32 nodes), tf: element-kernel blocks (64 elements), cut
+// links: cut_blocks(nfaces) blocks, prep: PrepParams.blocks blocks of 256
+constexpr int CF_MEM_NODE_BLOCK = 32, CF_MEM_FACE_BLOCK = 64;
+int cut_blocks(int nfaces);
+cudaError_t launch_membrane_forces_batch(const SparseTab<MemParams> &tv, const SparseTab<MemParams> &tf,
+                                         cudaStream_t s, int *nlaunch);
+cudaError_t launch_membrane_update_batch(const SparseTab<UpdateParams> &tu, const SparseTab<MemParams> *tfrozen,
+                                         cudaStream_t s, int *nlaunch);
+cudaError_t launch_cuts_batch(const SparseTab<CutParams> &t, cudaStream_t s, int *nlaunch);
+cudaError_t launch_prep_batch(const SparseTab<PrepParams> &t, cudaStream_t s, int *nlaunch);
 }  // namespace cf

@@ -290,9 +290,15 @@ __device__ __forceinline__ void node_forces(const MemParams &p, const CapDev &cp
         const float d = (x.h.z - p.zrep) + x.l.z;
         if (d < p.delta0) Fi.z += hertz(p.xi, p.delta0, d);
     }
-    // Hertz: nodes of other capsules, prefiltered by their bounding boxes of
-    // the previous step widened by one lattice unit (nodes move far less per step)
-    const float pad = p.delta0 + 1.0f;
+    // Hertz: nodes of other capsules, in three filters: the other capsule's
+    // bounding box of the previous step widened by one lattice unit (nodes
+    // move far less per step), per periodic image of this node; then the
+    // boxes of that capsule's 32-node patches at this step's positions
+    // (written by the node kernel) widened by delta0; then the distance of
+    // each node of an overlapping patch.  With the image shift applied to
+    // this node, each pair closer than delta0 is met in exactly one image
+    // (the lattice spans more than 2 delta0 in x and y).
+    const float pad = p.delta0 + 1.0f, ppad = p.delta0 + 1e-3f;
     for (int c2 = 0; c2 < p.ncaps; ++c2) {
         if (c2 == cap) continue;
         const int *lo = p.bbox_prev + 3 * c2, *hi = p.bbox_prev + 3 * p.ncaps + 3 * c2;
@@ -300,15 +306,24 @@ __device__ __forceinline__ void node_forces(const MemParams &p, const CapDev &cp
         for (int sy = -1; sy <= 1; ++sy)
             for (int sx = -1; sx <= 1; ++sx) {
                 const float ox = (float)(sx * p.nx), oy = (float)(sy * p.ny);
-                if (x.h.x + ox < lo[0] - pad || x.h.x + ox > hi[0] + pad) continue;
-                if (x.h.y + oy < lo[1] - pad || x.h.y + oy > hi[1] + pad) continue;
+                const float qx = x.h.x + ox, qy = x.h.y + oy;
+                if (qx < lo[0] - pad || qx > hi[0] + pad) continue;
+                if (qy < lo[1] - pad || qy > hi[1] + pad) continue;
                 const CapDev c2d = p.caps[c2];
-                for (int w = c2d.v0; w < c2d.v0 + c2d.nv; ++w) {
-                    f3 dd = pdiff(x, ldp(p.Xh, p.Xl, w));
-                    dd.x -= p.nx * floorf(dd.x / p.nx + 0.5f);
-                    dd.y -= p.ny * floorf(dd.y / p.ny + 0.5f);
-                    const float d = sqrtf(dot(dd, dd));
-                    if (d < p.delta0 && d > 0.f) Fi = Fi + (hertz(p.xi, p.delta0, d) / d) * dd;
+                for (int q = c2d.s0 >> 5; q < (c2d.s0 + c2d.ns) >> 5; ++q) {
+                    const float *B = p.pbox + 6 * q;
+                    if (qx < B[0] - ppad || qx > B[3] + ppad || qy < B[1] - ppad || qy > B[4] + ppad ||
+                        x.h.z < B[2] - ppad || x.h.z > B[5] + ppad)
+                        continue;
+                    for (int j = 0; j < 32; ++j) {
+                        const int w = __ldg(p.perm + 32 * q + j);
+                        if (w < 0) break;  // padding ends the capsule's last patch
+                        f3 dd = pdiff(x, ldp(p.Xh, p.Xl, w));
+                        dd.x += ox;
+                        dd.y += oy;
+                        const float d = sqrtf(dot(dd, dd));
+                        if (d < p.delta0 && d > 0.f) Fi = Fi + (hertz(p.xi, p.delta0, d) / d) * dd;
+                    }
                 }
             }
     }
@@ -317,12 +332,40 @@ __device__ __forceinline__ void node_forces(const MemParams &p, const CapDev &cp
 
 // Threads per block of the membrane kernels: small blocks spread the few
 // thousand latency-bound threads over all SMs.
-constexpr int MT = 64;   // element kernels
-constexpr int MV = 32;   // node kernels
+constexpr int MT = CF_MEM_FACE_BLOCK;  // element kernels
+constexpr int MV = CF_MEM_NODE_BLOCK;  // node kernels
+
+// Each kernel body takes its block index within its own capsule set (bid), so
+// that one launch can serve the capsule sets of many lattices: the batched
+// form of a kernel finds its lattice from the table's block offsets.
+__device__ __forceinline__ int tab_find(const int *boff, int n, int b) {
+    int lo = 0, hi = n - 1;  // the last table entry whose blocks start at or before b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (boff[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+#define CF_BATCHED(name, body, P, bound)                                              \
+    __global__ void __launch_bounds__(bound) name(const __grid_constant__ SparseTab<P> t) { \
+        const int i = tab_find(t.boff, t.n, (int)blockIdx.x);                        \
+        body(t.p[i], (int)blockIdx.x - t.boff[i]);                                   \
+    }
+
+// 0. per-capsule accumulators and bounding boxes of this step: zero and empty
+//    (one block per capsule set)
+__device__ __forceinline__ void mem_reset_body(const MemParams &p, int) {
+    for (int i = threadIdx.x; i < p.ncaps * A_NACC; i += blockDim.x) p.acc[i] = 0.0;
+    for (int i = threadIdx.x; i < 3 * p.ncaps; i += blockDim.x) {
+        p.bbox[i] = 0x7f7f7f7f;                  // the byte patterns of the single-lattice
+        p.bbox[3 * p.ncaps + i] = (int)0x80808080u;  // step's memsets
+    }
+}
 
 // 1. elements: Skalak, volume and first bending terms, FP64 area and volume
-__global__ void __launch_bounds__(MT) k_mem_elements(const MemParams p) {
-    const int f = blockIdx.x * MT + threadIdx.x;
+__device__ __forceinline__ void mem_elements_body(const MemParams &p, int bid) {
+    const int f = bid * MT + threadIdx.x;
     const bool valid = f < p.nfaces;
     const int cap = p.face_cap[valid ? f : 0];
     float area = 0.f, vol = 0.f;
@@ -331,12 +374,14 @@ __global__ void __launch_bounds__(MT) k_mem_elements(const MemParams p) {
     acc_add(p.acc, cap, A_VOL, vol, valid);
 }
 
-// 2. nodes: bending gradients, centroid (relative to the capsule's first
-//    node), bounding box
-__global__ void __launch_bounds__(MV) k_mem_nodes(const MemParams p) {
-    const int v = blockIdx.x * MV + threadIdx.x;
-    const bool valid = v < p.nnodes;
-    const int vv = valid ? v : 0;
+// 2. nodes, one warp per 32-node patch: bending gradients, centroid
+//    (relative to the capsule's first node), bounding boxes of the capsule
+//    and of the patch.  Lane 0 of a patch always holds a node, so padding
+//    lanes take its capsule and every warp sums for one capsule.
+__device__ __forceinline__ void mem_nodes_body(const MemParams &p, int bid) {
+    const int v = p.perm[bid * MV + threadIdx.x];
+    const bool valid = v >= 0;
+    const int vv = valid ? v : p.perm[bid * MV];
     const int cap = p.node_cap[vv];
     const CapDev cp = p.caps[cap];
     if (valid && cp.mode == 0) node_bending_grad(p, cp, vv);
@@ -356,11 +401,26 @@ __global__ void __launch_bounds__(MV) k_mem_nodes(const MemParams p) {
     acc_add(p.acc, cap, A_CY, r.y, valid);
     acc_add(p.acc, cap, A_CZ, r.z, valid);
     acc_minmax(p.bbox, p.ncaps, cap, x.h, valid);
+    // the patch's box (the padding lanes repeat lane 0's node)
+    float b[6] = {x.h.x, x.h.y, x.h.z, x.h.x, x.h.y, x.h.z};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            b[a] = fminf(b[a], __shfl_xor_sync(0xffffffffu, b[a], o));
+            b[3 + a] = fmaxf(b[3 + a], __shfl_xor_sync(0xffffffffu, b[3 + a], o));
+        }
+    if (threadIdx.x < 6) {
+        float vb = b[0];
+#pragma unroll
+        for (int a = 1; a < 6; ++a) vb = threadIdx.x == a ? b[a] : vb;
+        p.pbox[6 * bid + threadIdx.x] = vb;
+    }
 }
 
 // 3. elements: bending back-propagation
-__global__ void __launch_bounds__(MT) k_mem_bending(const MemParams p) {
-    const int f = blockIdx.x * MT + threadIdx.x;
+__device__ __forceinline__ void mem_bending_body(const MemParams &p, int bid) {
+    const int f = bid * MT + threadIdx.x;
     if (f < p.nfaces && p.caps[p.face_cap[f]].mode == 0) face_bending(p, f);
 }
 
@@ -369,14 +429,12 @@ __global__ void __launch_bounds__(MT) k_mem_bending(const MemParams p) {
 //    previous cut structure (each entry of the previous list names one marked
 //    link: its mask word and crossed element are reset) before the cut links
 //    of the new positions are marked.
-__global__ void __launch_bounds__(MV) k_mem_update(const MemParams p, const ClearParams cl) {
-    pdl_trigger();
-    pdl_wait();
-    if (cl.count_next && blockIdx.x == 0 && threadIdx.x == 0) *cl.count_next = 0;
+__device__ __forceinline__ void mem_update_body(const MemParams &p, const ClearParams &cl, int bid) {
+    if (cl.count_next && bid == 0 && threadIdx.x == 0) *cl.count_next = 0;
     const int node_blocks = (p.nnodes + MV - 1) / MV;
-    if ((int)blockIdx.x >= node_blocks) {
+    if (bid >= node_blocks) {
         const int cnt = min(*cl.count, cl.capacity);
-        for (int i = ((int)blockIdx.x - node_blocks) * MV + threadIdx.x; i < cnt; i += cl.blocks * MV) {
+        for (int i = (bid - node_blocks) * MV + threadIdx.x; i < cnt; i += cl.blocks * MV) {
             const int2 e = cl.list[i];
             const long long n = (long long)((unsigned)e.x >> 5);
             cl.mask[n] = 0u;
@@ -384,7 +442,7 @@ __global__ void __launch_bounds__(MV) k_mem_update(const MemParams p, const Clea
         }
         return;
     }
-    const int v = blockIdx.x * MV + threadIdx.x;
+    const int v = bid * MV + threadIdx.x;
     const bool valid = v < p.nnodes;
     const int vv = valid ? v : 0;
     const int cap = p.node_cap[vv];
@@ -422,10 +480,11 @@ __global__ void __launch_bounds__(MV) k_mem_update(const MemParams p, const Clea
     acc_add(Aw, cap, A_FTY, Ft.y, valid);
     acc_add(Aw, cap, A_FTZ, Ft.z, valid);
 }
+__device__ __forceinline__ void mem_update_body(const UpdateParams &u, int bid) { mem_update_body(u.m, u.c, bid); }
 
 // 5. frozen shapes: rigid translation with the summed force
-__global__ void __launch_bounds__(MV) k_mem_frozen(const MemParams p) {
-    const int v = blockIdx.x * MV + threadIdx.x;
+__device__ __forceinline__ void mem_frozen_body(const MemParams &p, int bid) {
+    const int v = bid * MV + threadIdx.x;
     if (v >= p.nnodes) return;
     const int cap = p.node_cap[v];
     const CapDev cp = p.caps[cap];
@@ -438,10 +497,34 @@ __global__ void __launch_bounds__(MV) k_mem_frozen(const MemParams p) {
     st_pos(p.Xnh, p.Xnl, v, ldp(p.Xh, p.Xl, v), vel);
 }
 
+__global__ void __launch_bounds__(MT) k_mem_elements(const MemParams p) { mem_elements_body(p, blockIdx.x); }
+__global__ void __launch_bounds__(MV) k_mem_nodes(const MemParams p) { mem_nodes_body(p, blockIdx.x); }
+__global__ void __launch_bounds__(MT) k_mem_bending(const MemParams p) { mem_bending_body(p, blockIdx.x); }
+__global__ void __launch_bounds__(MV) k_mem_update(const MemParams p, const ClearParams cl) {
+    pdl_trigger();
+    pdl_wait();
+    mem_update_body(p, cl, blockIdx.x);
+}
+__global__ void __launch_bounds__(MV) k_mem_frozen(const MemParams p) { mem_frozen_body(p, blockIdx.x); }
+
+__global__ void __launch_bounds__(MT) k_mem_reset_b(const __grid_constant__ SparseTab<MemParams> t) {
+    mem_reset_body(t.p[blockIdx.x], 0);
+}
+CF_BATCHED(k_mem_elements_b, mem_elements_body, MemParams, MT)
+CF_BATCHED(k_mem_nodes_b, mem_nodes_body, MemParams, MV)
+CF_BATCHED(k_mem_bending_b, mem_bending_body, MemParams, MT)
+CF_BATCHED(k_mem_frozen_b, mem_frozen_body, MemParams, MV)
+__global__ void __launch_bounds__(MV) k_mem_update_b(const __grid_constant__ SparseTab<UpdateParams> t) {
+    pdl_trigger();
+    pdl_wait();
+    const int i = tab_find(t.boff, t.n, (int)blockIdx.x);
+    mem_update_body(t.p[i], (int)blockIdx.x - t.boff[i]);
+}
+
 cudaError_t launch_membrane_forces(const MemParams &p, cudaStream_t s, int *nl) {
-    const unsigned gf = (unsigned)((p.nfaces + MT - 1) / MT), gv = (unsigned)((p.nnodes + MV - 1) / MV);
+    const unsigned gf = (unsigned)((p.nfaces + MT - 1) / MT), gs = (unsigned)(p.nslots / MV);
     k_mem_elements<<<gf, MT, 0, s>>>(p);
-    k_mem_nodes<<<gv, MV, 0, s>>>(p);
+    k_mem_nodes<<<gs, MV, 0, s>>>(p);
     k_mem_bending<<<gf, MT, 0, s>>>(p);
     *nl += 3;
     return cudaGetLastError();
@@ -454,6 +537,30 @@ cudaError_t launch_membrane_update(const MemParams &p, const ClearParams &cl, bo
     *nl += 1;
     if (any_frozen) {
         k_mem_frozen<<<gv, MV, 0, s>>>(p);
+        *nl += 1;
+    }
+    return cudaGetLastError();
+}
+
+// Batched forms: tv holds node-kernel block offsets, tf element-kernel ones
+cudaError_t launch_membrane_forces_batch(const SparseTab<MemParams> &tv, const SparseTab<MemParams> &tf,
+                                         cudaStream_t s, int *nl) {
+    if (tv.n == 0) return cudaSuccess;
+    k_mem_reset_b<<<tv.n, MT, 0, s>>>(tv);
+    if (tf.boff[tf.n] > 0) k_mem_elements_b<<<tf.boff[tf.n], MT, 0, s>>>(tf);
+    k_mem_nodes_b<<<tv.boff[tv.n], MV, 0, s>>>(tv);
+    if (tf.boff[tf.n] > 0) k_mem_bending_b<<<tf.boff[tf.n], MT, 0, s>>>(tf);
+    *nl += 4;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_membrane_update_batch(const SparseTab<UpdateParams> &tu, const SparseTab<MemParams> *tfz,
+                                         cudaStream_t s, int *nl) {
+    if (tu.n == 0) return cudaSuccess;
+    launch_pdl(k_mem_update_b, dim3((unsigned)tu.boff[tu.n]), dim3(MV), s, tu);
+    *nl += 1;
+    if (tfz && tfz->n > 0) {
+        k_mem_frozen_b<<<tfz->boff[tfz->n], MV, 0, s>>>(*tfz);
         *nl += 1;
     }
     return cudaGetLastError();
@@ -526,13 +633,15 @@ __device__ __forceinline__ bool plane_side(const f3 &nrm, const f3 &A, const f3 
     return fabsf(d) > OEPS ? d >= 0.f : side_of_d(A, B, C, P);
 }
 
-__global__ void __launch_bounds__(32 * CUT_WPB, 4) k_cut_faces(const CutParams p) {
-    pdl_trigger();
-    pdl_wait();
+__device__ __forceinline__ void cut_faces_body(const CutParams &p, int bid) {
     const unsigned full = 0xffffffffu;
     const int lane = (int)(threadIdx.x & 31);
-    const int T = blockIdx.x * CUT_WPB + (int)(threadIdx.x >> 5);
+    const int T = bid * CUT_WPB + (int)(threadIdx.x >> 5);
     if (T >= p.nfaces) return;  // the whole warp
+    if (p.zero_only) {  // fixed capsules: the cut links stay, the accumulator is zeroed
+        if (lane < 3) p.FTnext[3 * T + lane] = 0.f;
+        return;
+    }
     const int ia = p.faces[3 * T], ib = p.faces[3 * T + 1], ic = p.faces[3 * T + 2];
     if (lane == 0) {
         const float ux = (p.V[3 * ia] + p.V[3 * ib] + p.V[3 * ic]) * (1.0f / 3.0f);
@@ -640,8 +749,29 @@ __global__ void __launch_bounds__(32 * CUT_WPB, 4) k_cut_faces(const CutParams p
     }
 }
 
+__global__ void __launch_bounds__(32 * CUT_WPB, 4) k_cut_faces(const CutParams p) {
+    pdl_trigger();
+    pdl_wait();
+    cut_faces_body(p, blockIdx.x);
+}
+__global__ void __launch_bounds__(32 * CUT_WPB, 4) k_cut_faces_b(const __grid_constant__ SparseTab<CutParams> t) {
+    pdl_trigger();
+    pdl_wait();
+    const int i = tab_find(t.boff, t.n, (int)blockIdx.x);
+    cut_faces_body(t.p[i], (int)blockIdx.x - t.boff[i]);
+}
+
+int cut_blocks(int nfaces) { return (nfaces + CUT_WPB - 1) / CUT_WPB; }
+
 cudaError_t launch_cuts(const CutParams &p, cudaStream_t s, int *nl) {
-    launch_pdl(k_cut_faces, dim3((p.nfaces + CUT_WPB - 1) / CUT_WPB), dim3(32 * CUT_WPB), s, p);
+    launch_pdl(k_cut_faces, dim3(cut_blocks(p.nfaces)), dim3(32 * CUT_WPB), s, p);
+    *nl += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cuts_batch(const SparseTab<CutParams> &t, cudaStream_t s, int *nl) {
+    if (t.n == 0 || t.boff[t.n] == 0) return cudaSuccess;
+    launch_pdl(k_cut_faces_b, dim3((unsigned)t.boff[t.n]), dim3(32 * CUT_WPB), s, t);
     *nl += 1;
     return cudaGetLastError();
 }
@@ -666,11 +796,9 @@ __device__ __forceinline__ float pop_at(const PrepParams &p, int c, int k, long 
 // crossed by several elements has one entry per element: the entry of the
 // smallest one (the element kept in tri) writes the record, and a link whose
 // crossings cancelled out (even count, cut bit clear) writes none.
-__global__ void k_cut_prep(const PrepParams p) {
-    pdl_trigger();
-    pdl_wait();
+__device__ __forceinline__ void cut_prep_body(const PrepParams &p, int bid) {
     const int cnt = min(*p.count, p.capacity);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    for (int i = bid * (int)blockDim.x + (int)threadIdx.x; i < cnt; i += p.blocks * (int)blockDim.x) {
         const int2 e = __ldg(p.list + i);
         const long long n = (long long)((unsigned)e.x >> 5);
         const int k1 = e.x & 31, k = k1 + 1, T = e.y;
@@ -698,8 +826,27 @@ __global__ void k_cut_prep(const PrepParams p) {
     }
 }
 
+__global__ void __launch_bounds__(256) k_cut_prep(const PrepParams p) {
+    pdl_trigger();
+    pdl_wait();
+    cut_prep_body(p, blockIdx.x);
+}
+__global__ void __launch_bounds__(256) k_cut_prep_b(const __grid_constant__ SparseTab<PrepParams> t) {
+    pdl_trigger();
+    pdl_wait();
+    const int i = tab_find(t.boff, t.n, (int)blockIdx.x);
+    cut_prep_body(t.p[i], (int)blockIdx.x - t.boff[i]);
+}
+
 cudaError_t launch_prep(const PrepParams &p, cudaStream_t s, int *nl) {
-    launch_pdl(k_cut_prep, dim3(2 * 152), dim3(256), s, p);
+    launch_pdl(k_cut_prep, dim3((unsigned)p.blocks), dim3(256), s, p);
+    *nl += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_batch(const SparseTab<PrepParams> &t, cudaStream_t s, int *nl) {
+    if (t.n == 0 || t.boff[t.n] == 0) return cudaSuccess;
+    launch_pdl(k_cut_prep_b, dim3((unsigned)t.boff[t.n]), dim3(256), s, t);
     *nl += 1;
     return cudaGetLastError();
 }

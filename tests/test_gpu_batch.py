@@ -127,6 +127,33 @@ def test_batch_free_capsules_vs_oracle(cfm):
     b.close()
 
 
+def test_batch_mixed_modes_and_many_lattices(cfm):
+    """70 small lattices (more than one launch table of 64 lattices), with
+    free, frozen and fixed capsules and capsule-free films mixed: the
+    membrane and cut-link kernels of all lattices run batched, and every
+    lattice follows its lone run (populations, cut links, node positions)."""
+    modes = (I.MODE_FREE, I.MODE_FROZEN, I.MODE_FIXED)
+    wls = []
+    for i in range(70):
+        if i % 7 == 3:
+            wls.append(I.Workload("film", 14 + i % 3, 12, 12, h_top=5.5, capsules=[], steps=1, seed=i))
+        else:
+            wls.append(I.tiny_film(nx=16 + 2 * (i % 3), mode=modes[i % 3], seed=100 + i))
+    sims = [cfm.Simulation.from_workload(w) for w in wls]
+    b = cfm.Batch(sims)
+    b.step(9)
+    alone = run_alone(cfm, wls, 9)
+    for s, a, w in zip(sims, alone, wls):
+        assert rel(s.populations().astype(np.float64), a.populations().astype(np.float64)) < 1e-5, w.name
+        ms, ts, _ = s.cuts(); ma, ta, _ = a.cuts()
+        assert (ms == ma).all() and (ts == ta).all(), w.name
+        if w.capsules:
+            assert np.abs(s.capsule_state(0)["X"] - a.capsule_state(0)["X"]).max() < 1e-5
+            Fs, _ = s.capsule_force(0); Fa, _ = a.capsule_force(0)
+            assert np.abs(Fs - Fa).max() <= 1e-4 * np.abs(Fa).max() + 1e-8
+    b.close()
+
+
 def test_batch_then_alone_then_batch(cfm):
     """Contexts stay consistent when batch steps and lone steps alternate
     (odd step counts change every double-buffer parity)."""
