@@ -599,23 +599,22 @@ __device__ __forceinline__ bool edges_pass(f3 P, f3 Qp, f3 A, f3 B, f3 C) {
     return edges_pass_d(P, Qp, A, B, C);
 }
 
-// One warp per element.  A link (P, P+e_k), k in the nine positive directions,
-// can cross the element only where its crossing point lies in the element's
-// bounding box: along an axis a with e_a = 0 the start node lies in the box,
-// along an axis with e_a = +1 (-1) in the box widened by one unit below
-// (above).  Lanes 0-8 take one direction each and compute that range of
-// start nodes (widened by 1e-3, so the candidates cover every crossing the
-// exact tests can find); a warp prefix sum then hands every lane one
-// (direction, start node) candidate, 32 per pass.  Each candidate gets the
-// exact tests: plane sides of both end points (orientation against the
-// element, sign(0) = +, FP32 with a margin and FP64 otherwise) and, where they
-// differ, the three edge orientations.  A crossing toggles the cut bit of the
-// link at both of its end nodes, keeps the smallest crossing element there,
-// and appends one list entry per end node (one counter update per warp and
-// pass).  The warp also records the element's velocity (the mean of its
-// nodes', for Ladd's term of the next streaming) and zeroes the element's
+// One thread per element.  A link (P, P+e_k), k in the nine positive
+// directions, can cross the element only where its crossing point lies in the
+// element's bounding box: along an axis a with e_a = 0 the start node lies in
+// the box, along an axis with e_a = +1 (-1) in the box widened by one unit
+// below (above).  The thread walks that range of start nodes for each
+// direction (widened by 1e-3, so the candidates cover every crossing the
+// exact tests can find; an element of the usual size has about twenty) and
+// gives each candidate the exact tests: plane sides of both end points
+// (orientation against the element, sign(0) = +, FP32 with a margin and FP64
+// otherwise) and, where they differ, the three edge orientations.  A crossing
+// toggles the cut bit of the link at both of its end nodes, keeps the
+// smallest crossing element there, and appends one list entry per end node.
+// The thread also records the element's velocity (the mean of its nodes',
+// for Ladd's term of the next streaming) and zeroes the element's
 // momentum-exchange accumulator of the next step.
-constexpr int CUT_WPB = 8;  // elements (warps) per block
+constexpr int CUT_TPB = 128;  // elements (threads) per block
 
 // periodic index, with the common in-range case first
 __device__ __forceinline__ int wrap_fast(int a, int n) { return (unsigned)a < (unsigned)n ? a : wrapi(a, n); }
@@ -634,22 +633,18 @@ __device__ __forceinline__ bool plane_side(const f3 &nrm, const f3 &A, const f3 
 }
 
 __device__ __forceinline__ void cut_faces_body(const CutParams &p, int bid) {
-    const unsigned full = 0xffffffffu;
-    const int lane = (int)(threadIdx.x & 31);
-    const int T = bid * CUT_WPB + (int)(threadIdx.x >> 5);
-    if (T >= p.nfaces) return;  // the whole warp
-    if (p.zero_only) {  // fixed capsules: the cut links stay, the accumulator is zeroed
-        if (lane < 3) p.FTnext[3 * T + lane] = 0.f;
-        return;
-    }
+    const int T = bid * CUT_TPB + (int)threadIdx.x;
+    if (T >= p.nfaces) return;
+    p.FTnext[3 * T] = 0.f;
+    p.FTnext[3 * T + 1] = 0.f;
+    p.FTnext[3 * T + 2] = 0.f;
+    if (p.zero_only) return;  // fixed capsules: the cut links stay, the accumulator is zeroed
     const int ia = p.faces[3 * T], ib = p.faces[3 * T + 1], ic = p.faces[3 * T + 2];
-    if (lane == 0) {
+    {
         const float ux = (p.V[3 * ia] + p.V[3 * ib] + p.V[3 * ic]) * (1.0f / 3.0f);
         const float uy = (p.V[3 * ia + 1] + p.V[3 * ib + 1] + p.V[3 * ic + 1]) * (1.0f / 3.0f);
         const float uz = (p.V[3 * ia + 2] + p.V[3 * ib + 2] + p.V[3 * ic + 2]) * (1.0f / 3.0f);
         p.uT[T] = make_float4(ux, uy, uz, 0.f);
-    } else if (lane < 4) {
-        p.FTnext[3 * T + lane - 1] = 0.f;
     }
     // the decision is taken on the float (hi) positions
     const f3 A = ld3(p.X, ia), B = ld3(p.X, ib), C = ld3(p.X, ic);
@@ -658,120 +653,75 @@ __device__ __forceinline__ void cut_faces_body(const CutParams &p, int bid) {
     const float emax[3] = {fmaxf(A.x, fmaxf(B.x, C.x)), fmaxf(A.y, fmaxf(B.y, C.y)),
                            fmaxf(A.z, fmaxf(B.z, C.z))};
     // an element spanning more than 16 units (or with a non-finite position)
-    // is an error, not a workload: it would hand the warp unbounded candidates
+    // is an error, not a workload: it would hand the thread unbounded candidates
     if (!(emax[0] - emin[0] <= 16.f && emax[1] - emin[1] <= 16.f && emax[2] - emin[2] <= 16.f)) {
-        if (lane == 0) atomicOr(p.status, ST_OVERFLOW);
+        atomicOr(p.status, ST_OVERFLOW);
         return;
     }
-    // lane d < 9: start-node range of direction k = 2d + 1
     const float pad = 1e-3f;
-    int rlo[3] = {0, 0, 0}, rn[3] = {0, 0, 0};
-    int cnt = 0;
-    if (lane < 9) {
+    const f3 nrm = cross(B - A, C - A);
+    for (int d = 0; d < 9; ++d) {
+        const int k = 2 * d + 1;
         int e[3];
-        ek(2 * lane + 1, e[0], e[1], e[2]);
+        ek(k, e[0], e[1], e[2]);
+        int rlo[3], rhi[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const float lo = (e[a] > 0 ? emin[a] - 1.f : emin[a]) - pad;
             const float hi = (e[a] < 0 ? emax[a] + 1.f : emax[a]) + pad;
             rlo[a] = (int)ceilf(lo);
-            rn[a] = max(0, (int)floorf(hi) - rlo[a] + 1);
+            rhi[a] = (int)floorf(hi);
         }
-        cnt = rn[0] * rn[1] * rn[2];
-    }
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 16; o <<= 1) {
-        const int t = __shfl_up_sync(full, incl, o);
-        if (lane >= o) incl += t;
-    }
-    const int total = __shfl_sync(full, incl, 8);
-    const f3 nrm = cross(B - A, C - A);
-    for (int j0 = 0; j0 < total; j0 += 32) {
-        const int j = j0 + lane;
-        // direction of candidate j: the number of directions whose inclusive
-        // prefix is at most j
-        int dsel = 0;
-#pragma unroll
-        for (int d = 0; d < 9; ++d) dsel += __shfl_sync(full, incl, d) <= j ? 1 : 0;
-        const int src = min(dsel, 8);
-        const int base = __shfl_sync(full, incl - cnt, src);
-        const int lx = __shfl_sync(full, rlo[0], src), ly = __shfl_sync(full, rlo[1], src),
-                  lz = __shfl_sync(full, rlo[2], src);
-        const int nx_ = __shfl_sync(full, rn[0], src), ny_ = __shfl_sync(full, rn[1], src);
-        bool hit = false;
-        long long n0 = 0, n1 = 0;
-        const int k = 2 * src + 1;
-        if (j < total) {
-            // start node idx of the direction's range, x fastest
-            const int idx = j - base;
-            const int nxy = nx_ * ny_;
-            // (idx + 1/2) / nxy lies at least 1/(2 nxy) from an integer, far
-            // above the error of the fast quotient, so truncation is exact
-            const int iz = (int)__fdividef((float)idx + 0.5f, (float)nxy);
-            const int r = idx - iz * nxy;
-            const int iy = (int)__fdividef((float)r + 0.5f, (float)nx_);
-            const int x = lx + r - iy * nx_, y = ly + iy, z = lz + iz;
-            int kx, ky, kz;
-            ek(k, kx, ky, kz);
+        for (int z = rlo[2]; z <= rhi[2]; ++z) {
             // links touching the substrate plane z = 0 are not fluid links
-            if (!(p.wall && (wrap_fast(z, p.nz) == 0 || wrap_fast(z + kz, p.nz) == 0))) {
-                const f3 P{(float)x, (float)y, (float)z};
-                const f3 Qp{(float)(x + kx), (float)(y + ky), (float)(z + kz)};
-                hit = plane_side(nrm, A, B, C, P) != plane_side(nrm, A, B, C, Qp) &&
-                      edges_pass(P, Qp, A, B, C);
-            }
-            if (hit) {
-                n0 = node_at(p, x, y, z);
-                n1 = node_at(p, x + kx, y + ky, z + kz);
-            }
-        }
-        const unsigned hits = __ballot_sync(full, hit);
-        if (!hits) continue;
-        const int leader = __ffs(hits) - 1;
-        int at = 0;
-        if (lane == leader) at = atomicAdd(p.count, 2 * __popc(hits));
-        at = __shfl_sync(full, at, leader);
-        if (hit) {
-            const int k2 = opp(k);
-            atomicXor(p.mask + n0, 1u << (k - 1));
-            atomicMin(p.tri + n0 * 18 + (k - 1), T);
-            atomicXor(p.mask + n1, 1u << (k2 - 1));
-            atomicMin(p.tri + n1 * 18 + (k2 - 1), T);
-            const int idx = at + 2 * __popc(hits & ((1u << lane) - 1u));
-            if (idx + 1 < p.capacity) {
-                p.list[idx] = make_int2(cut_code(n0, k), T);
-                p.list[idx + 1] = make_int2(cut_code(n1, k2), T);
-            } else {
-                atomicOr(p.status, ST_OVERFLOW);
-            }
+            if (p.wall && (wrap_fast(z, p.nz) == 0 || wrap_fast(z + e[2], p.nz) == 0)) continue;
+            for (int y = rlo[1]; y <= rhi[1]; ++y)
+                for (int x = rlo[0]; x <= rhi[0]; ++x) {
+                    const f3 P{(float)x, (float)y, (float)z};
+                    const f3 Qp{(float)(x + e[0]), (float)(y + e[1]), (float)(z + e[2])};
+                    if (plane_side(nrm, A, B, C, P) == plane_side(nrm, A, B, C, Qp) || !edges_pass(P, Qp, A, B, C))
+                        continue;
+                    const long long n0 = node_at(p, x, y, z), n1 = node_at(p, x + e[0], y + e[1], z + e[2]);
+                    const int k2 = opp(k);
+                    atomicXor(p.mask + n0, 1u << (k - 1));
+                    atomicMin(p.tri + n0 * 18 + (k - 1), T);
+                    atomicXor(p.mask + n1, 1u << (k2 - 1));
+                    atomicMin(p.tri + n1 * 18 + (k2 - 1), T);
+                    const int idx = atomicAdd(p.count, 2);
+                    if (idx + 1 < p.capacity) {
+                        p.list[idx] = make_int2(cut_code(n0, k), T);
+                        p.list[idx + 1] = make_int2(cut_code(n1, k2), T);
+                    } else {
+                        atomicOr(p.status, ST_OVERFLOW);
+                    }
+                }
         }
     }
 }
 
-__global__ void __launch_bounds__(32 * CUT_WPB, 4) k_cut_faces(const CutParams p) {
+__global__ void __launch_bounds__(CUT_TPB) k_cut_faces(const CutParams p) {
     pdl_trigger();
     pdl_wait();
     cut_faces_body(p, blockIdx.x);
 }
-__global__ void __launch_bounds__(32 * CUT_WPB, 4) k_cut_faces_b(const __grid_constant__ SparseTab<CutParams> t) {
+__global__ void __launch_bounds__(CUT_TPB) k_cut_faces_b(const __grid_constant__ SparseTab<CutParams> t) {
     pdl_trigger();
     pdl_wait();
     const int i = tab_find(t.boff, t.n, (int)blockIdx.x);
     cut_faces_body(t.p[i], (int)blockIdx.x - t.boff[i]);
 }
 
-int cut_blocks(int nfaces) { return (nfaces + CUT_WPB - 1) / CUT_WPB; }
+int cut_blocks(int nfaces) { return (nfaces + CUT_TPB - 1) / CUT_TPB; }
 
 cudaError_t launch_cuts(const CutParams &p, cudaStream_t s, int *nl) {
-    launch_pdl(k_cut_faces, dim3(cut_blocks(p.nfaces)), dim3(32 * CUT_WPB), s, p);
+    launch_pdl(k_cut_faces, dim3(cut_blocks(p.nfaces)), dim3(CUT_TPB), s, p);
     *nl += 1;
     return cudaGetLastError();
 }
 
 cudaError_t launch_cuts_batch(const SparseTab<CutParams> &t, cudaStream_t s, int *nl) {
     if (t.n == 0 || t.boff[t.n] == 0) return cudaSuccess;
-    launch_pdl(k_cut_faces_b, dim3((unsigned)t.boff[t.n]), dim3(32 * CUT_WPB), s, t);
+    launch_pdl(k_cut_faces_b, dim3((unsigned)t.boff[t.n]), dim3(CUT_TPB), s, t);
     *nl += 1;
     return cudaGetLastError();
 }
