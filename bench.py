@@ -57,7 +57,11 @@ def parse():
                     help="population storage (arithmetic is float32 in every mode)")
     ap.add_argument("--sweep", action="store_true", help="the batched sweep (the default)")
     ap.add_argument("--pair", action="store_true", help="one capsule pair (128x64x64) instead of the sweep")
-    ap.add_argument("--tune-steps", type=int, default=8)
+    ap.add_argument("--tune-steps", type=int, default=8,
+                    help="autotuner steps per trial (0: skip it, take the usual pick)")
+    ap.add_argument("--groups", type=int, default=None,
+                    help="with --tune-steps 0: pipeline groups (default 8; 1 puts every lattice in each "
+                         "launch, as a profile of the batched passes wants)")
     ap.add_argument("--warm", action="store_true",
                     help="train the warm-start network and measure its gain on held-out set-ups")
     ap.add_argument("--sweep-n", type=int, default=16,
@@ -67,6 +71,9 @@ def parse():
     ap.add_argument("--theory-steps", type=int, default=40000)
     ap.add_argument("--theory-box", type=int, default=128,
                     help="lateral size of the single-particle boxes and y size of the pair boxes")
+    ap.add_argument("--unet", action="store_true",
+                    help="warm-start U-net forward pass on the sweep's largest lattice: time and the "
+                         "convolutions' tensor-core roofline")
     ap.add_argument("--cluster", action="store_true",
                     help="aggregation of 100 free soft particles (clusters and radial distribution)")
     ap.add_argument("--cluster-steps", type=int, default=20000)
@@ -79,6 +86,9 @@ def parse():
     ap.add_argument("--warm-steps", type=int, default=300, help="Adam steps")
     ap.add_argument("--warm-total", type=int, default=20000, help="steps of the time-to-force runs")
     ap.add_argument("--warm-every", type=int, default=200, help="lateral-force sampling interval")
+    ap.add_argument("--warm-save", default=None,
+                    help="with --warm: also save the trained network there (the default line's warm start "
+                         "reads paper_2007_15405_gb300/warm_unet.cfm)")
     ap.add_argument("--drying", action="store_true",
                     help="drying film with 16 capsules (256x256x96) instead of the sweep")
     return ap.parse_args()
@@ -210,11 +220,22 @@ def roofline(alg_bytes, nodes, kernel_ms, kernel, peak, peak_kind, traffic=None)
             "algorithmic_bytes_per_lu": alg_bytes, "kernel_ms": kernel_ms}
 
 
-def build_batch(cfm, wls, prec, tune_steps):
+DEFAULT_BATCH = (1, 2, 8)  # tile 32 x 4, 2 planes per work item, 8 groups: the autotuner's usual pick
+
+
+def build_batch(cfm, wls, prec, tune_steps, groups=None):
+    """The batch of all lattices, autotuned over tune_steps steps per trial
+    (0: the usual pick, or `groups` pipeline groups with its launch shape, as
+    profiling commands use it)."""
     sims = [cfm.Simulation.from_workload(w, precision=prec) for w in wls]
     batch = cfm.Batch(sims)
     t0 = time.perf_counter()
-    cfg = batch.autotune(steps=tune_steps)
+    if tune_steps > 0:
+        cfg = batch.autotune(steps=tune_steps)
+    else:
+        batch.set_config(*DEFAULT_BATCH[:2])
+        batch.set_groups(groups or DEFAULT_BATCH[2])
+        cfg = dict(batch.config(), note="autotuner skipped")
     cfg["seconds"] = time.perf_counter() - t0
     return sims, batch, cfg
 
@@ -322,7 +343,7 @@ def run_ours(args):
     peak, peak_kind = measured_peak()
     wls = sweep_workloads(args)
     nodes = sum(w.nodes for w in wls)
-    sims, batch, tune = build_batch(cfm, wls, prec, args.tune_steps)
+    sims, batch, tune = build_batch(cfm, wls, prec, args.tune_steps, args.groups)
     # ---- device-resident throughput: W untimed steps, then K steps timed
     clocks = ClockSampler(local)
     ms = time_batch(batch, args.warmup, args.steps, barrier, clocks)
@@ -366,6 +387,9 @@ def run_ours(args):
     teardown(world)
     if rank != 0:
         return
+    model = os.path.join(ROOT, "paper_2007_15405_gb300", "warm_unet.cfm")
+    if not args.no_extras and os.path.exists(model):
+        extras["time_to_force"] = warm_row(args, model)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         w0 = wls[0]  # the smallest lattice of the sweep: about 10-20 s of oracle work
@@ -529,8 +553,12 @@ def warm_measure(args, I, U, warm):
         d_rms.append(float(np.sqrt((hold["D"][k] ** 2).sum(1).mean())))
         d_err.append(float(np.sqrt(((D - hold["D"][k]) ** 2).sum(1).mean())))
     # time to force on the sweep's lattices (one per distance), fixed capsules
-    wls = [w for i, w in enumerate(I.batched_sweep(mode=I.MODE_FIXED)) if i % 4 == 0]
-    res, timing = warm.time_to_force(net, wls, total=args.warm_total, every=args.warm_every)
+    import tempfile
+    wls = warm_lattices(I)
+    with tempfile.TemporaryDirectory() as tmp:
+        path = args.warm_save or os.path.join(tmp, "unet.cfm")
+        net.save(path)
+        res, timing = warm.time_to_force(path, wls, total=args.warm_total, every=args.warm_every)
     both = [r for r in res if r["plain"] is not None and r["warm"] is not None]
     sp = float(np.mean([r["plain"] for r in both])) if both else None
     sw = float(np.mean([r["warm"] for r in both])) if both else None
@@ -566,6 +594,85 @@ def warm_measure(args, I, U, warm):
                     "steps run alone) is counted, the offline training is not"} if both else None),
         "value": ((sw + judge) * timing["step_seconds_warm"] + timing["warm_start_seconds"]) if both else None,
     }
+
+
+def warm_lattices(I):
+    """The time-to-force lattices: one per capsule distance of the batched
+    sweep (kS = 1e-3 column), capsules fixed."""
+    return [w for i, w in enumerate(I.batched_sweep(mode=I.MODE_FIXED)) if i % 4 == 0]
+
+
+def warm_row(args, model_path):
+    """The default line's time-to-force key: the committed network (trained by
+    `bench.py --warm --warm-save`), the sweep's 16 distances, plain batched
+    FP32 from the flat film against warm start plus batching."""
+    from paper_2007_15405_gb300 import inputs as I
+    from paper_2007_15405_gb300 import warm
+    wls = warm_lattices(I)
+    res, timing = warm.time_to_force(model_path, wls, total=args.warm_total, every=args.warm_every)
+    both = [r for r in res if r["plain"] is not None and r["warm"] is not None]
+    judge = 51  # the warm start's judging steps (two windows of 25 after one step)
+    out = {"metric": "time to the lateral capillary force within 1% of the converged plain-FP32 value",
+           "unit": "s per lattice", "higher_is_better": False,
+           "workload": f"{len(wls)} lattices of the sweep (one per distance 2.2R..6R, fixed capsules), "
+                       f"one batch, {args.warm_total} steps, lateral force every {args.warm_every}",
+           "model": os.path.relpath(model_path, ROOT),
+           "lattices_settled_both": len(both), "fallbacks": sum(not r["kept"] for r in res)}
+    if both:
+        sp = float(np.mean([r["plain"] for r in both]))
+        sw = float(np.mean([r["warm"] for r in both])) + judge
+        tp = sp * timing["step_seconds"]
+        tw = sw * timing["step_seconds_warm"] + timing["warm_start_seconds"]
+        out.update({"plain": {"steps": sp, "seconds": tp}, "warm": {"steps": sw, "seconds": tw},
+                    "value": tw, "speedup": tp / tw, "warm_start_seconds": timing["warm_start_seconds"],
+                    "step_seconds": timing["step_seconds"]})
+    return out
+
+
+def run_unet(args):
+    """The learned warm start's network (forward pass, the inference the warm
+    start runs): the 3-D U-net on a 160 x 80 x 64 lattice (the sweep's
+    largest), bfloat16 activations, fp32 accumulation on the tensor cores.
+    Roofline of the 3x3x3 convolutions: 2 x voxels x 27 x cin x cout flops
+    per layer over their device time, against the measured dense bf16 peak."""
+    import torch
+    from paper_2007_15405_gb300 import build as B
+    B.build()
+    from paper_2007_15405_gb300 import unet as U
+    torch.cuda.set_device(0)
+    nz, ny, nx = 64, 80, 160
+    net = U.UNet(seed=0)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.rand(nz * ny * nx * U.CIN, device="cuda", generator=g).to(torch.bfloat16)
+    grid = (1, nz, ny, nx)
+    V = nz * ny * nx
+    flops = 0  # levels: full grid, 1/8 of the voxels (e1, d1), 1/64 (m)
+    for name, ci, co, _ in net.specs:
+        vox = V // 8 if name[:2] in ("e1", "d1") else V // 64 if name[0] == "m" else V
+        flops += 2 * vox * 27 * ci * co
+    for _ in range(max(3, args.warmup)):
+        net.forward(x, grid)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        net.forward(x, grid)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
+    tf = flops / (ms / 1e3) / 1e12
+    print(json.dumps({
+        "metric": "U-net forward pass (warm-start inference)", "value": ms, "unit": "ms",
+        "higher_is_better": False, "steps": args.steps, "warmup": max(3, args.warmup), "dtype": "bf16",
+        "data": "synthetic", "config": {"workload": f"3-D U-net, {net.n_params} parameters, one "
+                                                    f"{nx}x{ny}x{nz} lattice, widths {list(net.widths)}"},
+        "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                     "traffic": None, "flops_per_forward": flops,
+                     "kernel": "all layers of one forward (11 convolutions plus pooling, upsampling and "
+                               "concatenation); flops counted for the convolutions only"},
+    }), flush=True)
 
 
 def gamma_g36():
@@ -740,6 +847,8 @@ def run_cluster(args):
 
 def main():
     args = parse()
+    if args.unet:
+        return run_unet(args)
     if args.cluster:
         run_cluster(args)
         return

@@ -110,7 +110,7 @@ struct cf_ctx {
     int xpar = 0;
     // momentum exchanged with each element: FT[ftpar] accumulates this step's,
     // FT[1 - ftpar] holds the previous step's (two-step average)
-    float *FT[2] = {nullptr, nullptr};
+    long long *FT[2] = {nullptr, nullptr};  // fixed point (ft_add)
     int ftpar = 0;
     float4 *uT = nullptr;  // element velocities, recorded with the cut links
     float *wet_el = nullptr;  // [nfaces] wetting offset per element (null when every capsule is neutral)
@@ -372,7 +372,7 @@ cf_status enqueue_post(cf_ctx *c, int *nl, cudaEvent_t ev2 = nullptr) {
             cf_status s = enqueue_cuts(c, c->X[c->xpar], nl, true);
             if (s != CF_OK) return s;
         } else {
-            CF_CUDA(cudaMemsetAsync(c->FT[1 - c->ftpar], 0, sizeof(float) * 3 * (size_t)c->nfaces,
+            CF_CUDA(cudaMemsetAsync(c->FT[1 - c->ftpar], 0, sizeof(long long) * 3 * (size_t)c->nfaces,
                                     c->stream));
         }
         c->ftpar = 1 - c->ftpar;
@@ -531,8 +531,8 @@ cf_status build_membrane(cf_ctx *c) {
     MALLOC_M(c->V, float, 3 * nv);
     MALLOC_M(c->Fcpl, float, 3 * nv);
     MALLOC_M(c->vscr, float, 4 * nv);
-    MALLOC_M(c->FT[0], float, 3 * nf);
-    MALLOC_M(c->FT[1], float, 3 * nf);
+    MALLOC_M(c->FT[0], long long, 3 * nf);
+    MALLOC_M(c->FT[1], long long, 3 * nf);
     MALLOC_M(c->uT, float4, nf);
     MALLOC_M(c->fscr, float, (size_t)FS_N * nf);
     MALLOC_M(c->refM, float, 3 * nf);
@@ -584,8 +584,8 @@ cf_status build_membrane(cf_ctx *c) {
     }
     CF_CUDA(cudaMemsetAsync(c->V, 0, sizeof(float) * 3 * nv, c->stream));
     CF_CUDA(cudaMemsetAsync(c->Fcpl, 0, sizeof(float) * 3 * nv, c->stream));
-    CF_CUDA(cudaMemsetAsync(c->FT[0], 0, sizeof(float) * 3 * nf, c->stream));
-    CF_CUDA(cudaMemsetAsync(c->FT[1], 0, sizeof(float) * 3 * nf, c->stream));
+    CF_CUDA(cudaMemsetAsync(c->FT[0], 0, sizeof(long long) * 3 * nf, c->stream));
+    CF_CUDA(cudaMemsetAsync(c->FT[1], 0, sizeof(long long) * 3 * nf, c->stream));
     c->ftpar = 0;
     CF_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(double) * A_NACC * nc, c->stream));
     CF_CUDA(up(c->refM, refM.data(), sizeof(float) * refM.size()));
@@ -1314,7 +1314,7 @@ struct CkptHeader {
     int64_t steps_done;
     double dry_dm;
 };
-constexpr uint32_t CKPT_VERSION = 1;
+constexpr uint32_t CKPT_VERSION = 2;  // 2: element momentum exchange in fixed point
 
 // the device arrays of the state between two steps, in file order
 struct CkptPart {
@@ -1333,8 +1333,8 @@ std::vector<CkptPart> ckpt_parts(cf_ctx *c, int count) {
         const size_t nv = c->nnodes, nf = c->nfaces, nc = c->caps.size();
         v.push_back({c->X[c->xpar], sizeof(float) * 6 * nv});
         v.push_back({c->V, sizeof(float) * 3 * nv});
-        v.push_back({c->FT[0], sizeof(float) * 3 * nf});
-        v.push_back({c->FT[1], sizeof(float) * 3 * nf});
+        v.push_back({c->FT[0], sizeof(long long) * 3 * nf});
+        v.push_back({c->FT[1], sizeof(long long) * 3 * nf});
         v.push_back({c->uT, sizeof(float4) * nf});
         v.push_back({c->acc, sizeof(double) * A_NACC * nc});
         v.push_back({c->bbox[0], sizeof(int) * 6 * nc});
@@ -1612,6 +1612,9 @@ cf_status batch_post(cf_batch *b, int g, int i0, int i1, cudaStream_t s, int *nl
     for (cf_ctx *c : mem) c->xpar = 1 - c->xpar;
     for (size_t j0 = 0; j0 < mem.size(); j0 += CF_SPARSE_CAP) {
         const int n = (int)std::min<size_t>(CF_SPARSE_CAP, mem.size() - j0);
+        long long faces = 0;
+        for (int j = 0; j < n; ++j) faces += mem[j0 + j]->nfaces;
+        const int lanes = cut_lanes(faces);
         tc.n = n;
         tc.boff[0] = 0;
         for (int j = 0; j < n; ++j) {
@@ -1625,9 +1628,9 @@ cf_status batch_post(cf_batch *b, int g, int i0, int i1, cudaStream_t s, int *nl
                 tc.p[j].FTnext = c->FT[1 - c->ftpar];
                 tc.p[j].zero_only = 1;
             }
-            tc.boff[j + 1] = tc.boff[j] + cut_blocks(c->nfaces);
+            tc.boff[j + 1] = tc.boff[j] + cut_blocks(c->nfaces, lanes);
         }
-        CF_CUDA(launch_cuts_batch(tc, s, nl));
+        CF_CUDA(launch_cuts_batch(tc, lanes, s, nl));
     }
     for (cf_ctx *c : mem) c->ftpar = 1 - c->ftpar;
     return CF_OK;

@@ -84,6 +84,19 @@ enum Prec { P_F32 = 0, P_F16 = 1, P_BF16 = 2 };
 constexpr float F16_SCALE = 32768.0f, F16_INV_SCALE = 1.0f / 32768.0f;
 inline size_t pop_bytes(int prec) { return prec == P_F32 ? 4 : 2; }
 
+// Momentum exchanged with each membrane element (Sec. 3.1, coupling): summed
+// in 64-bit fixed point (units of 2^-40) by integer atomics, which are exact
+// and do not depend on the order the contributions arrive in, so runs with
+// moving capsules and their restarts repeat bit for bit.  A contribution is
+// a float below ~10 in magnitude, so its rounding to 2^-40 lies far below
+// its own float precision, and a sum stays far from the 2^63 range.
+constexpr float FT_SCALE = 1099511627776.0f;  // 2^40
+constexpr double FT_UNIT = 1.0 / 1099511627776.0;
+__device__ __forceinline__ void ft_add(long long *a, float v) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(a), (unsigned long long)__float2ll_rn(v * FT_SCALE));
+}
+__device__ __forceinline__ float ft_val(long long v) { return (float)((double)v * FT_UNIT); }
+
 // Parameters of the lattice passes.
 struct LBParams {
     int nx, ny, nz, wall;
@@ -106,7 +119,7 @@ struct LBParams {
     const int *__restrict__ tri;        // crossed element per node and link [N*18]
     const int *__restrict__ faces;      // element nodes [3*nfaces]
     const float *__restrict__ V;        // node velocities [3*nnodes]
-    float *__restrict__ FT;             // element momentum exchange accumulators [3*nfaces]
+    long long *__restrict__ FT;         // element momentum exchange accumulators [3*nfaces] (ft_add)
     const float2 *__restrict__ rec;     // [N][18] bounced (A, B) populations by arriving direction - 1
     const float *__restrict__ wet_el;   // [nfaces] wetting offset of each element's capsule (null: all 0)
     float *__restrict__ out;            // optional [5][N]: rhoA, rhoB, ux, uy, uz
@@ -160,8 +173,8 @@ struct MemParams {
                              // (per-step displacements are below a float ulp at x ~ 100)
     float *Xnh, *Xnl;        // [3*nv] positions of the next step
     float *V;                // [3*nv] node velocities (written)
-    const float *FT;         // [3*nf] momentum exchanged with the fluid in this step
-    const float *FTprev;     // [3*nf] the same, of the previous step
+    const long long *FT;     // [3*nf] momentum exchanged with the fluid in this step (ft_add)
+    const long long *FTprev; // [3*nf] the same, of the previous step
     float *fscr;             // [nf*FS_N] per-element scratch
     float *vscr;             // [nv*4] per-node scratch (gL, gA)
     float *Fcpl;             // [3*nv] coupling force on nodes (readout)
@@ -192,7 +205,7 @@ struct CutParams {
     int *tri;
     int2 *list;              // one entry per marked link: (cut_code(n, k), T)
     int *count;              // entries appended to `list` (zeroed before)
-    float *FTnext;           // [3*nfaces] exchange accumulator of the next step (zeroed here)
+    long long *FTnext;       // [3*nfaces] exchange accumulator of the next step (zeroed here)
     const float *V;          // [3*nnodes] node velocities
     float4 *uT;              // [nfaces] element velocities (written here)
     int capacity;
@@ -224,7 +237,7 @@ struct PrepParams {
     const int2 *list;        // cut-link entries (cut_code(n, k), T), with repetitions
     const int *count;
     float2 *rec;             // [N][18] bounced (A, B) populations by arriving direction - 1
-    float *FT;               // element momentum exchange accumulators
+    long long *FT;           // element momentum exchange accumulators (ft_add)
     int capacity;
     int ref_rho;             // CF_LADD_REF_RHO: Ladd's term with rho_0 = 1
     int blocks;              // blocks striding over the list
@@ -323,13 +336,15 @@ cudaError_t launch_cuts(const CutParams &p, cudaStream_t s, int *nlaunch);
 cudaError_t launch_prep(const PrepParams &p, cudaStream_t s, int *nlaunch);
 // batched forms (one launch per kernel for all lattices of the tables); tv:
 // node-kernel blocks (32 nodes), tf: element-kernel blocks (64 elements), cut
-// links: cut_blocks(nfaces) blocks, prep: PrepParams.blocks blocks of 256
+// links: cut_blocks(nfaces, lanes) blocks with lanes = cut_lanes(the launch's
+// elements), prep: PrepParams.blocks blocks of 256
 constexpr int CF_MEM_NODE_BLOCK = 32, CF_MEM_FACE_BLOCK = 64;
-int cut_blocks(int nfaces);
+int cut_lanes(long long nfaces);
+int cut_blocks(int nfaces, int lanes);
 cudaError_t launch_membrane_forces_batch(const SparseTab<MemParams> &tv, const SparseTab<MemParams> &tf,
                                          cudaStream_t s, int *nlaunch);
 cudaError_t launch_membrane_update_batch(const SparseTab<UpdateParams> &tu, const SparseTab<MemParams> *tfrozen,
                                          cudaStream_t s, int *nlaunch);
-cudaError_t launch_cuts_batch(const SparseTab<CutParams> &t, cudaStream_t s, int *nlaunch);
+cudaError_t launch_cuts_batch(const SparseTab<CutParams> &t, int lanes, cudaStream_t s, int *nlaunch);
 cudaError_t launch_prep_batch(const SparseTab<PrepParams> &t, cudaStream_t s, int *nlaunch);
 }  // namespace cf

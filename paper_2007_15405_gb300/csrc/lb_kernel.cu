@@ -383,9 +383,9 @@ __device__ __forceinline__ void sc_force(const LBParams &p, const Deltas &d, uin
                     }
                     // reaction of the decoupled interaction on the crossed element
                     const float r = p.G * wgt(k) * (pa * qb + pb * qa);
-                    if (ex(k)) atomicAdd(p.FT + 3 * el + 0, ex(k) * r);
-                    if (ey(k)) atomicAdd(p.FT + 3 * el + 1, ey(k) * r);
-                    if (ez(k)) atomicAdd(p.FT + 3 * el + 2, ez(k) * r);
+                    if (ex(k)) ft_add(p.FT + 3 * el + 0, ex(k) * r);
+                    if (ey(k)) ft_add(p.FT + 3 * el + 1, ey(k) * r);
+                    if (ez(k)) ft_add(p.FT + 3 * el + 2, ez(k) * r);
                 }
             } else {
                 const float2 q = __ldg(p.psi + n + nb_off(d, ex(k), ey(k), ez(k)));

@@ -413,23 +413,18 @@ def lateral_traces(sims, total, every):
     return np.array(out).T, dt / (total * len(sims))
 
 
-def time_to_force(net, wls, total, every, tol=0.01):
+def time_to_force(model_path, wls, total, every, tol=0.01):
     """Plain (flat film) and warm-started runs of the pair set-ups wls in
     batches: the steps after which the lateral force stays within tol of its
     converged value (the mean of the plain run's last five samples), whether
     each warm start was kept, and the wall times (one warm start; one
-    lattice step within the batch)."""
-    import os
-    import tempfile
+    lattice step within the batch).  The warm start runs inside the library
+    (cf_warmstart) on the network saved at model_path (UNet.save)."""
     import time
     plain = [cfm.Simulation.from_workload(w) for w in wls]
     warmed, used = [], []
     t_warm = 0.0
-    # the warm start runs inside the library (cf_warmstart) on the saved network
-    with tempfile.TemporaryDirectory() as tmp:
-        path = os.path.join(tmp, "unet.bin")
-        net.save(path)
-        model = cfm.Model(path)
+    model = cfm.Model(model_path)
     for w in wls:
         s = cfm.Simulation.from_workload(w)
         t0 = time.perf_counter()

@@ -60,8 +60,9 @@ def test_restart_is_bit_identical(cfm, tmp_path, prec, mode):
 
 
 def test_restart_free_capsule_continues(cfm, tmp_path):
-    """Free capsule: the restarted run follows the original to float rounding
-    of the atomic force sums."""
+    """Free capsule: the restarted run repeats the original bit for bit (the
+    momentum exchanged with each element is summed in fixed point, so no sum
+    depends on the order its atomic contributions arrive in)."""
     wl = I.tiny_film(mode=I.MODE_FREE)
     a = cfm.Simulation.from_workload(wl)
     a.step(20)
@@ -73,9 +74,24 @@ def test_restart_free_capsule_continues(cfm, tmp_path):
     b.step(20)
     sa, sb = state(a), state(b)
     for k in ("f", "rho", "X0"):
-        assert np.abs(sa[k].astype(np.float64) - sb[k]).max() <= 1e-6 * np.abs(sa[k]).max(), k
+        assert np.array_equal(sa[k], sb[k]), k
     ma, mb = a.cuts()[0], b.cuts()[0]
     assert (ma == mb).all()
+
+
+def test_free_runs_repeat_bit_for_bit(cfm):
+    """Two runs of the same free two-capsule set-up (contact, moving cut
+    links, momentum exchange) end in identical states."""
+    caps = [I.CapsuleSpec(centre=(10.3, 8.4, 10.17), radius=4.0, level=2, C=1.0, mode=I.MODE_FREE),
+            I.CapsuleSpec(centre=(19.1, 8.4, 10.17), radius=4.0, level=2, C=1.0, mode=I.MODE_FREE)]
+    wl = I.Workload("contact", 32, 16, 20, h_top=8.5, capsules=caps, steps=60, rep_dz=2.0)
+    runs = []
+    for _ in range(2):
+        s = cfm.Simulation.from_workload(wl)
+        s.step(wl.steps)
+        runs.append((s.populations(), s.capsule_state(0)["X"], s.capsule_state(1)["X"], s.capsule_force(0)[0]))
+    for x, y in zip(*runs):
+        assert np.array_equal(x, y)
 
 
 def test_load_rejects_what_does_not_match(cfm, tmp_path):
