@@ -864,12 +864,12 @@ __global__ void __launch_bounds__(CUT_TPB) k_cut_faces_b(const __grid_constant__
     cut_faces_any<L>(t.p[i], (int)blockIdx.x - t.boff[i]);
 }
 
-// lanes per element: one thread per element once the launch has elements
-// enough for about a wave of full blocks (measured: 0.32 ms for the 655k
-// elements of the 64-lattice sweep against 0.64 ms with warps), else a warp
-// per element (16 us for the 10k elements of one capsule pair against 44 us
-// with threads)
-int cut_lanes(long long nfaces) { return nfaces >= 152LL * 1024 ? 1 : 32; }
+// lanes per element: one thread per element once the launch has some 40k
+// elements, else a warp per element (measured: 10k elements of one capsule
+// pair 16 us with warps against 44 us with threads; 82k elements of eight
+// sweep lattices 56 us with threads against 79 us with warps; 655k elements
+// of the 64-lattice sweep 0.32 ms against 0.64 ms)
+int cut_lanes(long long nfaces) { return nfaces >= 40960 ? 1 : 32; }
 int cut_blocks(int nfaces, int lanes) { return (int)(((long long)nfaces * lanes + CUT_TPB - 1) / CUT_TPB); }
 
 cudaError_t launch_cuts(const CutParams &p, cudaStream_t s, int *nl) {
