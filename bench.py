@@ -77,6 +77,10 @@ def parse():
     ap.add_argument("--cluster", action="store_true",
                     help="aggregation of 100 free soft particles (clusters and radial distribution)")
     ap.add_argument("--cluster-steps", type=int, default=20000)
+    ap.add_argument("--cluster-n", type=int, default=100, help="particles of --cluster")
+    ap.add_argument("--cluster-box", type=int, nargs=2, default=(320, 320), metavar=("NX", "NY"),
+                    help="lattice of --cluster (the paper's 1730 particles: 1200 1176, the largest "
+                         "1200 x ny x 40 lattice the library takes)")
     ap.add_argument("--approach", action="store_true",
                     help="approach dynamics of two free soft particles (gap against time)")
     ap.add_argument("--approach-steps", type=int, default=40000)
@@ -810,7 +814,10 @@ def run_cluster(args):
     from paper_2007_15405_gb300 import capfilm as cfm
     from paper_2007_15405_gb300 import inputs as I
     torch.cuda.set_device(0)
-    wl = I.many_capsules()
+    nx, ny = args.cluster_box
+    # 2R + 2 delta0 apart at the start: denser packings than the default gap reach the
+    # paper's area fraction (random sequential addition jams near 0.55 of excluded area)
+    wl = I.many_capsules(args.cluster_n, nx, ny, dmin=None if args.cluster_n <= 100 else 23.0)
     R = wl.capsules[0].radius
     sim = cfm.Simulation.from_workload(wl)
     L = (wl.nx, wl.ny)
@@ -835,6 +842,8 @@ def run_cluster(args):
     line = {"metric": "aggregation of free soft particles: clusters and radial distribution over time",
             "unit": "particles", "data": "synthetic", "dtype": "f32",
             "config": {"workload": wl.name + f", R=10 level-4, film 0.35R, {len(wl.capsules)} particles",
+                       "nodes": wl.nodes, "membrane_nodes": 2562 * len(wl.capsules),
+                       "area_fraction": len(wl.capsules) * np.pi * R * R / (nx * ny),
                        "steps": args.cluster_steps, "bond_cutoff": cut},
             "series": [dict(step=e["step"], clusters=e["stats"][0], mean_size=e["stats"][1],
                             largest=e["stats"][2], **({"min_height": e["min_height"]} if "min_height" in e else {}))

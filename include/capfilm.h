@@ -146,6 +146,12 @@ cf_status cf_destroy(cf_ctx *ctx);
  * (0, 1, ... in insertion order).  Capsules must be added before cf_set_film,
  * which fills their interior with the B-majority fluid. */
 cf_status cf_add_capsule(cf_ctx *ctx, const cf_capsule_desc *desc, int *id);
+/* The same for n capsules desc[0..n) at once (ids[k] receives the index of
+ * desc[k]; ids may be null): the device structures of the membrane are
+ * rebuilt once instead of after each capsule, for lattices with many
+ * capsules.  Errors as cf_add_capsule, checked for every descriptor before
+ * any is added (none is added then). */
+cf_status cf_add_capsules(cf_ctx *ctx, const cf_capsule_desc *desc, int n, int *ids);
 cf_status cf_set_capsule_mode(cf_ctx *ctx, int id, int mode);
 
 /* Film initialisation (Sec. 3.2): A-majority (rho_maj / rho_min) below the

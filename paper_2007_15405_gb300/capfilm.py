@@ -79,6 +79,7 @@ def load_library(path: Optional[str] = None):
         "cf_create": [C.POINTER(LatticeDesc), C.POINTER(C.c_void_p)],
         "cf_destroy": [C.c_void_p],
         "cf_add_capsule": [C.c_void_p, C.POINTER(CapsuleDesc), C.POINTER(C.c_int)],
+        "cf_add_capsules": [C.c_void_p, C.POINTER(CapsuleDesc), C.c_int, C.POINTER(C.c_int)],
         "cf_set_capsule_mode": [C.c_void_p, C.c_int, C.c_int],
         "cf_set_film": [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, _dp],
         "cf_step": [C.c_void_p, C.c_longlong],
@@ -167,7 +168,7 @@ def load_library(path: Optional[str] = None):
 
 
 def exported_symbols():
-    return ["cf_last_error", "cf_create", "cf_destroy", "cf_add_capsule", "cf_set_capsule_mode",
+    return ["cf_last_error", "cf_create", "cf_destroy", "cf_add_capsule", "cf_add_capsules", "cf_set_capsule_mode",
             "cf_set_film", "cf_step", "cf_sync", "cf_capsule_force", "cf_lateral_force",
             "cf_capsule_state", "cf_fields", "cf_populations", "cf_total_mass",
             "cf_meniscus_field", "cf_meniscus_profile", "cf_cuts", "cf_launch_count",
@@ -286,10 +287,10 @@ class Simulation:
     def from_workload(cls, wl, set_film=True, **kw):
         kw.setdefault("flags", getattr(wl, "flags", 0))
         s = cls(wl.nx, wl.ny, wl.nz, wall=wl.wall, tau=wl.tau, G=wl.G, rep_dz=wl.rep_dz, **kw)
-        for cap in wl.capsules:
-            X, F = cap.mesh()
-            s.add_capsule(X, F, cap.kS, cap.C, cap.kB, cap.kV, cap.mass, cap.mode,
-                          wet=getattr(cap, "wet", 0.0))
+        if wl.capsules:
+            meshes = [cap.mesh() for cap in wl.capsules]
+            s.add_capsules([(X, F, cap.kS, cap.C, cap.kB, cap.kV, cap.mass, cap.mode, getattr(cap, "wet", 0.0))
+                            for (X, F), cap in zip(meshes, wl.capsules)])
         if set_film:
             from .inputs import RHO_MAJ, RHO_MIN, RHO_MIX
             s.set_film(wl.h_top, RHO_MAJ, RHO_MIN, RHO_MIX, wl.jitter())
@@ -307,6 +308,22 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+    def add_capsules(self, specs):
+        """Many capsules at once (cf_add_capsules): specs of (X, F, kS, C,
+        kB, kV, mass, mode, wet); returns their ids."""
+        keep, descs = [], (CapsuleDesc * len(specs))()
+        for k, (X, F, kS, C_, kB, kV, mass, mode, wet) in enumerate(specs):
+            X = np.ascontiguousarray(X, np.float64)
+            F = np.ascontiguousarray(F, np.int32)
+            keep.append((X, F))  # alive until the call returns
+            descs[k] = CapsuleDesc(X.shape[0], F.shape[0], _ptr(X), F.ctypes.data_as(C.POINTER(C.c_int)),
+                                   kS, C_, kB, kV, mass, mode, float(wet))
+        ids = (C.c_int * len(specs))()
+        _check(_lib.cf_add_capsules(self._h, descs, len(specs), ids))
+        for X, _ in keep:
+            self.nv.append(X.shape[0])
+        return list(ids)
 
     def add_capsule(self, X, F, kS, C_, kB, kV, mass, mode, wet=0.0):
         X = np.ascontiguousarray(X, np.float64)

@@ -119,6 +119,7 @@ struct cf_ctx {
     int *faces = nullptr, *face_cap = nullptr, *node_cap = nullptr, *vf_off = nullptr,
         *vf_ent = nullptr, *bbox[2] = {nullptr, nullptr};
     int *perm = nullptr;      // node of each patch slot (-1: padding), see MemParams
+    int *nbr = nullptr, *nbr_cnt = nullptr;  // contact partners (CF_NBR_MIN_CAPS capsules or more)
     float *pbox = nullptr;    // patch boxes of this step
     int nslots = 0;
     CapDev *capdev = nullptr;
@@ -254,6 +255,8 @@ MemParams mem_params(cf_ctx *c) {
     p.perm = c->perm;
     p.nslots = c->nslots;
     p.pbox = c->pbox;
+    p.nbr = c->nbr;
+    p.nbr_cnt = c->nbr_cnt;
     return p;
 }
 
@@ -347,6 +350,11 @@ cf_status enqueue_pre(cf_ctx *c, int *nl) {
     CF_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(double) * A_NACC * nc, c->stream2));
     CF_CUDA(cudaMemsetAsync(bb, 0x7f, sizeof(int) * 3 * nc, c->stream2));
     CF_CUDA(cudaMemsetAsync(bb + 3 * nc, 0x80, sizeof(int) * 3 * nc, c->stream2));
+    if (c->nbr) {  // partners from the previous step's boxes, read by the node update
+        MemParams q = mem_params(c);
+        q.nbr = nullptr;
+        CF_CUDA(launch_contact_partners(q, c->nbr, c->nbr_cnt, c->stream2, nl));
+    }
     CF_CUDA(launch_membrane_forces(mem_params(c), c->stream2, nl));
     CF_CUDA(cudaEventRecord(c->ev_join, c->stream2));
     // bounce records of the cut links for this step's streaming
@@ -548,6 +556,11 @@ cf_status build_membrane(cf_ctx *c) {
     MALLOC_M(c->capdev, CapDev, nc);
     MALLOC_M(c->perm, int, c->nslots);
     MALLOC_M(c->pbox, float, 6 * (c->nslots / 32));
+    c->nbr = c->nbr_cnt = nullptr;
+    if (nc >= CF_NBR_MIN_CAPS) {
+        MALLOC_M(c->nbr, int, (size_t)CF_NBR_MAX * nc);
+        MALLOC_M(c->nbr_cnt, int, nc);
+    }
     MALLOC_M(c->acc, double, A_NACC * nc);
     c->wet_el = nullptr;
     bool any_wet = false;
@@ -734,14 +747,13 @@ cf_status cf_destroy(cf_ctx *c) {
     return CF_OK;
 }
 
-cf_status cf_add_capsule(cf_ctx *c, const cf_capsule_desc *d, int *id) {
-    if (!c || !d || !d->nodes || !d->faces) return fail(CF_EINVAL, "null argument");
+// one capsule descriptor as host data (validated)
+static cf_status host_capsule(const cf_capsule_desc *d, HostCapsule &h) {
+    if (!d->nodes || !d->faces) return fail(CF_EINVAL, "null argument");
     if (d->nv < 4 || d->nf < 4) return fail(CF_EINVAL, "capsule mesh too small");
     if (d->mode < 0 || d->mode > 2) return fail(CF_EINVAL, "bad capsule mode");
     if (!(d->mass > 0)) return fail(CF_EINVAL, "node mass must be positive");
     if (!std::isfinite(d->wet)) return fail(CF_EINVAL, "wetting offset must be finite");
-    if (c->film_set) return fail(CF_ESTATE, "capsules must be added before cf_set_film");
-    HostCapsule h;
     h.nv = d->nv; h.nf = d->nf; h.mode = d->mode;
     h.kS = d->kS; h.C = d->C; h.kB = d->kB; h.kV = d->kV; h.mass = d->mass; h.wet = d->wet;
     h.X.resize(3 * (size_t)d->nv);
@@ -749,11 +761,29 @@ cf_status cf_add_capsule(cf_ctx *c, const cf_capsule_desc *d, int *id) {
     h.F.assign(d->faces, d->faces + 3 * (size_t)d->nf);
     for (int v : h.F)
         if (v < 0 || v >= d->nv) return fail(CF_EINVAL, "face index out of range");
-    c->caps.push_back(h);
+    return CF_OK;
+}
+
+cf_status cf_add_capsules(cf_ctx *c, const cf_capsule_desc *d, int n, int *ids) {
+    if (!c || !d || n < 1) return fail(CF_EINVAL, "null argument");
+    if (c->film_set) return fail(CF_ESTATE, "capsules must be added before cf_set_film");
+    std::vector<HostCapsule> hs(n);
+    for (int k = 0; k < n; ++k) {
+        cf_status s = host_capsule(d + k, hs[k]);
+        if (s != CF_OK) return s;
+    }
+    const size_t n0 = c->caps.size();
+    for (auto &h : hs) c->caps.push_back(std::move(h));
     cf_status s = build_membrane(c);
-    if (s != CF_OK) { c->caps.pop_back(); return s; }
-    if (id) *id = (int)c->caps.size() - 1;
+    if (s != CF_OK) { c->caps.resize(n0); return s; }
+    if (ids)
+        for (int k = 0; k < n; ++k) ids[k] = (int)(n0 + k);
     return sync_ok(c);
+}
+
+cf_status cf_add_capsule(cf_ctx *c, const cf_capsule_desc *d, int *id) {
+    if (!c || !d) return fail(CF_EINVAL, "null argument");
+    return cf_add_capsules(c, d, 1, id);
 }
 
 cf_status cf_set_capsule_mode(cf_ctx *c, int id, int mode) {
@@ -1569,6 +1599,13 @@ cf_status batch_pre(cf_batch *b, int g, int i0, int i1, cudaStream_t s, int *nl)
             tf.boff[j + 1] = tf.boff[j] + (c->nfaces + CF_MEM_FACE_BLOCK - 1) / CF_MEM_FACE_BLOCK;
             tp.p[j] = prep_params(c, pb);
             tp.boff[j + 1] = tp.boff[j] + pb;
+        }
+        for (int j = 0; j < n; ++j) {  // lattices with many capsules: their contact partners first
+            cf_ctx *c = mem[j0 + j];
+            if (!c->nbr) continue;
+            MemParams q = mem_params(c);
+            q.nbr = nullptr;
+            CF_CUDA(launch_contact_partners(q, c->nbr, c->nbr_cnt, b->gmem[g], nl));
         }
         CF_CUDA(launch_membrane_forces_batch(tv, tf, b->gmem[g], nl));
         CF_CUDA(launch_prep_batch(tp, s, nl));

@@ -191,7 +191,15 @@ struct MemParams {
     const int *perm;         // [nslots]
     int nslots;
     float *pbox;             // [nslots / 32][6]: float min x, y, z, max x, y, z of this step
+    // Contact partners of each capsule (lattices with many capsules): nbr[c *
+    // CF_NBR_MAX + j], j < nbr_cnt[c], the capsules whose boxes of the previous
+    // step come within the contact range, in ascending order; a count above
+    // CF_NBR_MAX means "all capsules".  Null: every capsule is checked.
+    const int *nbr;
+    const int *nbr_cnt;
 };
+constexpr int CF_NBR_MAX = 48;
+constexpr int CF_NBR_MIN_CAPS = 16;  // fewer capsules: no lists, the loop checks them all
 
 // per-element scratch layout (floats)
 enum FaceScr { FS_SK = 0, FS_DV = 9, FS_L = 18, FS_AF3 = 27, FS_BEND = 28, FS_N = 37 };
@@ -332,6 +340,9 @@ cf_status unet_forward(const UNetModel *m, const float *feats, int nz, int ny, i
 cudaError_t launch_membrane_forces(const MemParams &p, cudaStream_t s, int *nlaunch);
 cudaError_t launch_membrane_update(const MemParams &p, const ClearParams &cl, bool any_frozen,
                                    cudaStream_t s, int *nlaunch);
+// contact partners of every capsule from the boxes of the previous step
+// (writes nbr and nbr_cnt of p; one warp per capsule)
+cudaError_t launch_contact_partners(const MemParams &p, int *nbr, int *nbr_cnt, cudaStream_t s, int *nlaunch);
 cudaError_t launch_cuts(const CutParams &p, cudaStream_t s, int *nlaunch);
 cudaError_t launch_prep(const PrepParams &p, cudaStream_t s, int *nlaunch);
 // batched forms (one launch per kernel for all lattices of the tables); tv:

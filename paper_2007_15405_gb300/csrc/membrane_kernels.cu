@@ -303,7 +303,14 @@ __device__ __forceinline__ void node_forces(const MemParams &p, const CapDev &cp
     // this node, each pair closer than delta0 is met in exactly one image
     // (the lattice spans more than 2 delta0 in x and y).
     const float pad = p.delta0 + 1.0f, ppad = p.delta0 + 1e-3f;
-    for (int c2 = 0; c2 < p.ncaps; ++c2) {
+    // the partner list (if any) holds, in ascending order, every capsule whose
+    // box test below can pass, so the sum runs over the same capsules in the
+    // same order as a loop over all of them
+    const int nlist = p.nbr ? __ldg(p.nbr_cnt + cap) : 0;
+    const bool all = !p.nbr || nlist > CF_NBR_MAX;
+    const int ncand = all ? p.ncaps : nlist;
+    for (int j = 0; j < ncand; ++j) {
+        const int c2 = all ? j : __ldg(p.nbr + cap * CF_NBR_MAX + j);
         if (c2 == cap) continue;
         const int *lo = p.bbox_prev + 3 * c2, *hi = p.bbox_prev + 3 * p.ncaps + 3 * c2;
         if (x.h.z < lo[2] - pad || x.h.z > hi[2] + pad) continue;
@@ -523,6 +530,48 @@ __global__ void __launch_bounds__(MV) k_mem_update_b(const __grid_constant__ Spa
     pdl_wait();
     const int i = tab_find(t.boff, t.n, (int)blockIdx.x);
     mem_update_body(t.p[i], (int)blockIdx.x - t.boff[i]);
+}
+
+// One warp per capsule c: the capsules c2 != c (ascending) whose box of the
+// previous step, widened by the contact range plus one unit, overlaps c's box
+// widened by one unit (nodes move far less than a unit per step) in some
+// periodic image along x and y: a superset of the capsules the node loop's
+// box test can accept for a node of c.
+__global__ void __launch_bounds__(32) k_contact_partners(const MemParams p, int *nbr, int *nbr_cnt) {
+    const int c = blockIdx.x;
+    const int lane = threadIdx.x;
+    const int *lo = p.bbox_prev, *hi = p.bbox_prev + 3 * p.ncaps;
+    const float pad = p.delta0 + 2.0f;
+    const float cl[3] = {(float)lo[3 * c], (float)lo[3 * c + 1], (float)lo[3 * c + 2]};
+    const float ch[3] = {(float)hi[3 * c], (float)hi[3 * c + 1], (float)hi[3 * c + 2]};
+    int count = 0;
+    for (int b = 0; b < p.ncaps; b += 32) {
+        const int c2 = b + lane;
+        bool ok = false;
+        if (c2 < p.ncaps && c2 != c) {
+            const float l2[3] = {(float)lo[3 * c2], (float)lo[3 * c2 + 1], (float)lo[3 * c2 + 2]};
+            const float h2[3] = {(float)hi[3 * c2], (float)hi[3 * c2 + 1], (float)hi[3 * c2 + 2]};
+            if (ch[2] >= l2[2] - pad && cl[2] <= h2[2] + pad) {
+                for (int sy = -1; sy <= 1 && !ok; ++sy)
+                    for (int sx = -1; sx <= 1 && !ok; ++sx) {
+                        const float ox = (float)(sx * p.nx), oy = (float)(sy * p.ny);
+                        ok = ch[0] + ox >= l2[0] - pad && cl[0] + ox <= h2[0] + pad &&
+                             ch[1] + oy >= l2[1] - pad && cl[1] + oy <= h2[1] + pad;
+                    }
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        const int at = count + __popc(m & ((1u << lane) - 1u));
+        if (ok && at < CF_NBR_MAX) nbr[c * CF_NBR_MAX + at] = c2;
+        count += __popc(m);
+    }
+    if (lane == 0) nbr_cnt[c] = count;  // above CF_NBR_MAX: the node loop checks every capsule
+}
+
+cudaError_t launch_contact_partners(const MemParams &p, int *nbr, int *nbr_cnt, cudaStream_t s, int *nl) {
+    k_contact_partners<<<p.ncaps, 32, 0, s>>>(p, nbr, nbr_cnt);
+    *nl += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_membrane_forces(const MemParams &p, cudaStream_t s, int *nl) {

@@ -353,33 +353,31 @@ def approach_pair(beta: float, gap_over_R: float = 2.0, h_frac: float = 0.4, rad
 
 def many_capsules(n_caps: int = 100, nx: int = 320, ny: int = 320, nz: int = 40, radius: float = 10.0,
                   level: int = 4, h_frac: float = 0.35, beta: float = 25.0, seed: int = 12,
-                  steps: int = 20000) -> Workload:
+                  steps: int = 20000, dmin: Optional[float] = None) -> Workload:
     """Many free soft particles in a film (Sec. 4.7, aggregation; the paper's
     run has 1730 particles of R = 10 on 1200 x 1200 x 40 at h0 = 0.35R, an
     area fraction of 0.38; 100 particles on 320 x 320 give 0.31): centres
-    uniform in xy with centre distances at least 2R + 2 delta0 + 1 (rejection
-    sampling, periodic), bottoms where the substrate repulsion starts,
-    softness beta = R^2 gamma / kB with Poisson ratio 0.9."""
+    uniform in xy with centre distances at least dmin (default 2R + 2 delta0
+    + 1; random sequential addition, periodic), bottoms where the substrate
+    repulsion starts, softness beta = R^2 gamma / kB with Poisson ratio 0.9."""
     rng = np.random.default_rng(seed)
-    dmin = 2.0 * radius + 2.0 * DELTA0 + 1.0
-    pts: List[Tuple[float, float]] = []
+    if dmin is None:
+        dmin = 2.0 * radius + 2.0 * DELTA0 + 1.0
+    box = np.array([nx, ny], dtype=np.float64)
+    pts = np.zeros((0, 2))
     tries = 0
     while len(pts) < n_caps:
         tries += 1
-        if tries > 500000:
+        if tries > 2000000:
             raise ValueError(f"{n_caps} capsules of radius {radius} do not fit in {nx}x{ny}")
-        p = (float(rng.uniform(0, nx)), float(rng.uniform(0, ny)))
-        ok = True
-        for q in pts:
-            dx = (p[0] - q[0] + nx / 2) % nx - nx / 2
-            dy = (p[1] - q[1] + ny / 2) % ny - ny / 2
-            if math.hypot(dx, dy) < dmin:
-                ok = False
-                break
-        if ok:
-            pts.append(p)
+        p = rng.uniform(0.0, 1.0, 2) * box
+        d = pts - p
+        d -= np.floor(d / box + 0.5) * box  # nearest periodic image
+        if len(pts) == 0 or np.hypot(d[:, 0], d[:, 1]).min() >= dmin:
+            pts = np.vstack([pts, p])
     kB = radius * radius * GAMMA_G36 / beta
     zc = z_rest(radius) + _OFF[2]
-    caps = [CapsuleSpec(centre=(x, y, zc), radius=radius, level=level, kS=5e-3, C=9.0, kB=kB) for x, y in pts]
+    caps = [CapsuleSpec(centre=(float(x), float(y), zc), radius=radius, level=level, kS=5e-3, C=9.0, kB=kB)
+            for x, y in pts]
     return Workload(f"{n_caps} capsules {nx}x{ny}x{nz} beta={beta:g}", nx, ny, nz,
                     h_top=0.5 + REP_DZ + h_frac * radius, capsules=caps, steps=steps, seed=seed)

@@ -198,3 +198,28 @@ def test_run_writes_one_json_line_per_readout(cfm, tmp_path):
     assert [r["step"] for r in lines] == [10, 20, 25] and lines == json.loads(json.dumps(recs))
     assert set(lines[0]) == {"step", "mlups", "mass", "force", "Z"}
     assert len(lines[-1]["force"]) == 1 and lines[-1]["mlups"] > 0
+
+
+def test_add_capsules_at_once_equals_one_by_one(cfm):
+    """cf_add_capsules builds the membrane once for many capsules; the state
+    equals the one built capsule by capsule, and a bad descriptor adds none."""
+    from paper_2007_15405_gb300.inputs import RHO_MAJ, RHO_MIN, RHO_MIX
+    wl = I.many_capsules(n_caps=20, nx=120, ny=120, nz=40, radius=6.0, level=2, seed=3)
+    specs = [(*c.mesh(), c.kS, c.C, c.kB, c.kV, c.mass, c.mode, 0.0) for c in wl.capsules]
+    a = cfm.Simulation(wl.nx, wl.ny, wl.nz, wall=wl.wall, tau=wl.tau, G=wl.G, rep_dz=wl.rep_dz)
+    assert a.add_capsules(specs) == list(range(20))
+    b = cfm.Simulation(wl.nx, wl.ny, wl.nz, wall=wl.wall, tau=wl.tau, G=wl.G, rep_dz=wl.rep_dz)
+    for sp in specs:
+        b.add_capsule(*sp[:8], wet=sp[8])
+    for s in (a, b):
+        s.set_film(wl.h_top, RHO_MAJ, RHO_MIN, RHO_MIX, wl.jitter())
+        s.step(12)
+    assert np.array_equal(a.populations(), b.populations())
+    for k in (0, 7, 19):
+        assert np.array_equal(a.capsule_state(k)["X"], b.capsule_state(k)["X"])
+    c = cfm.Simulation(wl.nx, wl.ny, wl.nz, wall=wl.wall, tau=wl.tau, G=wl.G, rep_dz=wl.rep_dz)
+    bad = list(specs[:3])
+    bad[1] = (*specs[1][:6], -1.0, *specs[1][7:])  # node mass must be positive
+    with pytest.raises(cfm.CapfilmError, match="mass"):
+        c.add_capsules(bad)
+    assert c.add_capsules(specs[:2]) == [0, 1]
