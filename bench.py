@@ -79,8 +79,7 @@ def parse():
     ap.add_argument("--cluster-steps", type=int, default=20000)
     ap.add_argument("--cluster-n", type=int, default=100, help="particles of --cluster")
     ap.add_argument("--cluster-box", type=int, nargs=2, default=(320, 320), metavar=("NX", "NY"),
-                    help="lattice of --cluster (the paper's 1730 particles: 1200 1176, the largest "
-                         "1200 x ny x 40 lattice the library takes)")
+                    help="lattice of --cluster (the paper's 1730 particles: 1200 1200)")
     ap.add_argument("--approach", action="store_true",
                     help="approach dynamics of two free soft particles (gap against time)")
     ap.add_argument("--approach-steps", type=int, default=40000)

@@ -132,8 +132,8 @@ const char *cf_last_error(void);
  * from the moments of the density pass (no second pull of the populations);
  * any other tau relaxes the pulled populations.
  * Errors (checked before any CUDA call): CF_EINVAL for a null argument, a
- * dimension below 3, a lattice with 38 * nx * ny * nz >= 2^31 (32-bit
- * population offsets: at most 56.5 million nodes), tau <= 1/2 or not a
+ * dimension below 3, a lattice of 2^26 nodes or more (a cut-list entry holds
+ * the node index in 26 bits: at most 67.1 million nodes), tau <= 1/2 or not a
  * number, an unknown precision or flag; then CF_ECUDA (stream or event creation) and
  * CF_ENOMEM (an allocation failed: all blocks obtained are given back). */
 cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out);

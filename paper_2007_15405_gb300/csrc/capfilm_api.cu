@@ -649,8 +649,10 @@ const char *cf_last_error(void) { return g_err.c_str(); }
 cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     if (!desc || !out) return fail(CF_EINVAL, "null argument");
     if (desc->nx < 3 || desc->ny < 3 || desc->nz < 3) return fail(CF_EINVAL, "lattice dimensions must be >= 3");
-    // population offsets are 32-bit: 38 * N must stay below 2^31
-    if (38LL * desc->nx * desc->ny * desc->nz >= (1LL << 31)) return fail(CF_EINVAL, "lattice too large (38*N >= 2^31)");
+    // a cut-list entry holds the node index in 26 bits (cut_code); population
+    // offsets within one component (at most 18 N) then stay 32-bit
+    if ((long long)desc->nx * desc->ny * desc->nz >= (1LL << 26))
+        return fail(CF_EINVAL, "lattice too large (N >= 2^26 nodes)");
     if (!(desc->tau[0] > 0.5) || !(desc->tau[1] > 0.5)) return fail(CF_EINVAL, "tau must exceed 1/2");
     if (desc->precision != CF_FP32 && desc->precision != CF_FP16_SHIFT &&
         desc->precision != CF_BF16_SHIFT)
