@@ -84,6 +84,7 @@ def parse():
                     help="approach dynamics of two free soft particles (gap against time)")
     ap.add_argument("--approach-steps", type=int, default=40000)
     ap.add_argument("--warm-train", type=int, default=96, help="training set-ups of the warm start")
+    ap.add_argument("--warm-hold", type=int, default=16, help="held-out set-ups of the warm start")
     ap.add_argument("--warm-eq", type=int, default=4000, help="equilibration steps of the training data")
     ap.add_argument("--warm-def", type=int, default=1000, help="free steps of the deformation data")
     ap.add_argument("--warm-steps", type=int, default=300, help="Adam steps")
@@ -542,8 +543,8 @@ def warm_measure(args, I, U, warm):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     # held-out set-ups of the same generator
-    hold = warm.pair_dataset(I.warm_pair_dataset(16, seed=99, mode=I.MODE_FIXED),
-                             I.warm_pair_dataset(16, seed=99, mode=I.MODE_FREE), eq, dfs)
+    hold = warm.pair_dataset(I.warm_pair_dataset(args.warm_hold, seed=99, mode=I.MODE_FIXED),
+                             I.warm_pair_dataset(args.warm_hold, seed=99, mode=I.MODE_FREE), eq, dfs)
     nz, ny, nx = hold["shape"]
     e_flat, e_warm, d_rms, d_err = [], [], [], []
     for k in range(hold["X"].shape[0]):
@@ -653,16 +654,21 @@ def run_unet(args):
     for name, ci, co, _ in net.specs:
         vox = V // 8 if name[:2] in ("e1", "d1") else V // 64 if name[0] == "m" else V
         flops += 2 * vox * 27 * ci * co
-    for _ in range(max(3, args.warmup)):
-        net.forward(x, grid)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        net.forward(x, grid)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    def timed(tensor_memory):
+        net.tensor_memory = tensor_memory
+        for _ in range(max(3, args.warmup)):
+            net.forward(x, grid)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            net.forward(x, grid)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    ms_mma = timed(False)
+    ms = timed(True)
     peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
     tf = flops / (ms / 1e3) / 1e12
@@ -673,8 +679,10 @@ def run_unet(args):
                                                     f"{nx}x{ny}x{nz} lattice, widths {list(net.widths)}"},
         "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
                      "traffic": None, "flops_per_forward": flops,
-                     "kernel": "all layers of one forward (11 convolutions plus pooling, upsampling and "
-                               "concatenation); flops counted for the convolutions only"},
+                     "kernel": "all layers of one forward on the tcgen05 convolution (11 convolutions plus "
+                               "pooling, upsampling and concatenation); flops counted for the convolutions only"},
+        "mma_sync": {"ms": ms_mma, "tflops": flops / (ms_mma / 1e3) / 1e12,
+                     "note": "the same forward with the mma.sync convolution"},
     }), flush=True)
 
 

@@ -437,6 +437,17 @@ cf_status cf_from_bf16(const void *x, float *y, long long n, void *stream);
  * of 8; b may be NULL; y is float32 when out_f32 != 0, else bfloat16. */
 cf_status cf_unet_conv(const void *x, int n, int nz, int ny, int nx, int cin, const void *w, const float *b,
                        int cout, int relu, int out_f32, void *y, void *stream);
+/* The same convolution on the 5th-generation tensor cores (tcgen05.mma, M =
+ * 128 voxels, N = cout, bf16 operands staged in shared memory, fp32
+ * accumulators in tensor memory).  cin a multiple of 16 up to 256, cout a
+ * multiple of 16 up to 256 (CF_EINVAL otherwise).  Its waits are bounded:
+ * cf_unet_tc_error reports whether one ran out. */
+cf_status cf_unet_conv_tc(const void *x, int n, int nz, int ny, int nx, int cin, const void *w, const float *b,
+                          int cout, int relu, int out_f32, void *y, void *stream);
+/* *err = 1 when a tensor-core convolution launched since the last call gave
+ * up a wait (its output is then incomplete), else 0; synchronises the device
+ * and clears the flag. */
+cf_status cf_unet_tc_error(unsigned *err);
 /* wt[26 - t][ci][co] = w[t][co][ci]: with wt as weights, cf_unet_conv of an
  * output gradient (cout channels) gives the input gradient (cin channels). */
 cf_status cf_unet_flip(const void *w, int cin, int cout, void *wt, void *stream);

@@ -133,6 +133,9 @@ def load_library(path: Optional[str] = None):
         "cf_field_check": [C.c_void_p, _dp],
         "cf_unet_conv": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                          C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+        "cf_unet_conv_tc": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                            C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+        "cf_unet_tc_error": [C.POINTER(C.c_uint)],
         "cf_unet_flip": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
         "cf_unet_wgrad": [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                           C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
@@ -179,7 +182,7 @@ def exported_symbols():
             "cf_field_check", "cf_conv3d_forward",
             "cf_conv3d_backward", "cf_mse", "cf_adam", "cf_to_bf16", "cf_from_bf16",
             "cf_meniscus_fit", "cf_capillary_force", "cf_model_load", "cf_model_destroy", "cf_warmstart",
-            "cf_unet_conv", "cf_unet_flip", "cf_unet_wgrad",
+            "cf_unet_conv", "cf_unet_conv_tc", "cf_unet_tc_error", "cf_unet_flip", "cf_unet_wgrad",
             "cf_unet_relu_grad", "cf_unet_loss", "cf_unet_pool", "cf_unet_pool_bwd", "cf_unet_upsample",
             "cf_unet_upsample_bwd", "cf_unet_concat", "cf_unet_split", "cf_unet_pack", "cf_unet_unpack"]
 

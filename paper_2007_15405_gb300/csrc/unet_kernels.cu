@@ -135,6 +135,187 @@ __global__ void __launch_bounds__(32 * CW) k_conv_mma(Grid3 g, const __nv_bfloat
     }
 }
 
+// ------------------------------------------------------------------------
+// The same convolution on the 5th-generation tensor cores (tcgen05).  A block
+// owns 128 consecutive voxels (the MMA's M) and all cout output channels (N).
+// For each of the 27 taps the block stages the shifted input rows A_t
+// [128][cin] (zero rows outside the grid) and the tap's weights B_t
+// [cout][cin] in shared memory, as K-major operands without swizzle: 8-row x
+// 16-byte core matrices, K blocks adjacent (128 B apart), row blocks
+// cin * 16 B apart.  One thread issues the tap's cin / 16 MMAs (M = 128,
+// N = cout, K = 16, bf16 inputs, fp32 accumulation in tensor memory) and
+// commits them to the stage's mbarrier; two stages let the loads of one tap
+// overlap the MMAs of the previous one.  The epilogue reads the accumulators
+// from tensor memory (each warp its 32 rows), adds the bias, applies the ReLU
+// and stores bfloat16 (or float) rows.  Waits are bounded: a wait that runs
+// out sets *err and the block frees its tensor memory and returns.
+__device__ unsigned g_tc_err;  // a tensor-core convolution gave up a wait
+
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory operand descriptor: start >> 4 (bits 0-13), leading byte
+// offset >> 4 (16-29), stride byte offset >> 4 (32-45), descriptor version 1
+// (46-47), no swizzle (61-63 = 0)
+__device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3fffu) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
+}
+// instruction descriptor of kind::f16: fp32 accumulator (bits 4-5 = 1), bf16 A
+// and B (7-9 = 1, 10-12 = 1), both K-major, N >> 3 (17-22), M >> 4 (24-28)
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// bounded wait for the phase of parity `phase`; false when the limit ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase) {
+    const uint32_t a = smem_u32(bar);
+    for (int it = 0; it < (1 << 20); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <bool OUTF>
+__global__ void __launch_bounds__(128, 1) k_conv_tc(Grid3 g, const __nv_bfloat16 *__restrict__ x, int cin,
+                                                    const __nv_bfloat16 *__restrict__ w,
+                                                    const float *__restrict__ b, int cout, int relu,
+                                                    void *__restrict__ yout, unsigned *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t bar[2];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long total = (long long)g.n * g.V;
+    const long long v0 = (long long)blockIdx.x * 128;
+    const int kb = cin / 8;                       // 16-byte chunks per row
+    const uint32_t a_bytes = 128u * cin * 2u, b_bytes = (uint32_t)cout * cin * 2u;
+    const uint32_t stage_bytes = a_bytes + b_bytes;
+    const int ncols = cout <= 32 ? 32 : (cout <= 64 ? 64 : (cout <= 128 ? 128 : 256));
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = idesc_bf16(128, cout);
+    // this thread's row of A: voxel v0 + tid, its coordinates decoded once
+    const long long vr = v0 + tid;
+    const bool vin = vr < total;
+    int rz = 0, ry = 0, rx = 0;
+    long long sbase = 0;
+    if (vin) {
+        const long long sm = vr / g.V, l = vr - sm * g.V;
+        sbase = sm * g.V;
+        rz = (int)(l / ((long long)g.ny * g.nx));
+        const int rem = (int)(l - (long long)rz * g.ny * g.nx);
+        ry = rem / g.nx;
+        rx = rem - ry * g.nx;
+    }
+    unsigned char *const arow = smem + ((tid >> 3) * kb) * 128 + (tid & 7) * 16;  // chunk q at + q * 128
+    bool ok = true;
+    for (int t = 0; t < 27 && ok; ++t) {
+        const int st = t & 1;
+        unsigned char *sa = smem + st * stage_bytes, *sb = sa + a_bytes;
+        if (t >= 2) ok = mbar_wait(&bar[st], ((t - 2) >> 1) & 1);  // the MMAs of tap t - 2 read this stage
+        if (__syncthreads_and(ok) == 0) { ok = false; break; }
+        // A_t: the thread's row shifted by tap t (zero outside the grid), all cin channels
+        {
+            const int zz = rz + t / 9 - 1, yy = ry + (t / 3) % 3 - 1, xx = rx + t % 3 - 1;
+            const bool in = vin && (unsigned)zz < (unsigned)g.nz && (unsigned)yy < (unsigned)g.ny &&
+                            (unsigned)xx < (unsigned)g.nx;
+            const uint4 *src =
+                reinterpret_cast<const uint4 *>(x + (sbase + ((long long)zz * g.ny + yy) * g.nx + xx) * cin);
+            unsigned char *dst = arow + st * stage_bytes;
+            for (int q = 0; q < kb; ++q)
+                *reinterpret_cast<uint4 *>(dst + q * 128) = in ? __ldg(src + q) : make_uint4(0u, 0u, 0u, 0u);
+        }
+        // B_t: weights w[t][co][ci], row co
+        const __nv_bfloat16 *wt = w + (size_t)t * cout * cin;
+        for (int i = tid; i < cout * kb; i += 128) {
+            const int r = i / kb, q = i - r * kb;
+            const uint4 val = __ldg(reinterpret_cast<const uint4 *>(wt + (size_t)r * cin) + q);
+            *reinterpret_cast<uint4 *>(sb + ((r >> 3) * kb + q) * 128 + (r & 7) * 16) = val;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb), sbo = (uint32_t)cin * 16u;
+            for (int ks = 0; ks < cin / 16; ++ks) {
+                const uint64_t ad = desc(a0 + ks * 256u, 128u, sbo), bd = desc(b0 + ks * 256u, 128u, sbo);
+                const uint32_t acc = (t > 0 || ks > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bar[st]))
+                         : "memory");
+        }
+    }
+    // the last commit covers every MMA issued before it (taps 25 and 26 both)
+    if (ok) ok = mbar_wait(&bar[0], 1) && mbar_wait(&bar[1], 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (__syncthreads_and(ok)) {
+        const long long v = v0 + warp * 32 + lane;
+        for (int c = 0; c < cout; c += 8) {
+            uint32_t r[8];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (v >= total) continue;
+            float o[8];
+            for (int j = 0; j < 8; ++j) {
+                o[j] = __uint_as_float(r[j]) + (b ? b[c + j] : 0.f);
+                if (relu) o[j] = fmaxf(o[j], 0.f);
+            }
+            if (OUTF) {
+                float4 *yo = reinterpret_cast<float4 *>(static_cast<float *>(yout) + v * cout + c);
+                yo[0] = make_float4(o[0], o[1], o[2], o[3]);
+                yo[1] = make_float4(o[4], o[5], o[6], o[7]);
+            } else {
+                uint4 pk;
+                pk.x = pack2(__float2bfloat16_rn(o[0]), __float2bfloat16_rn(o[1]));
+                pk.y = pack2(__float2bfloat16_rn(o[2]), __float2bfloat16_rn(o[3]));
+                pk.z = pack2(__float2bfloat16_rn(o[4]), __float2bfloat16_rn(o[5]));
+                pk.w = pack2(__float2bfloat16_rn(o[6]), __float2bfloat16_rn(o[7]));
+                *reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(yout) + v * cout + c) = pk;
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(err, 1u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+}  // namespace tc
+
 // wt[26 - t][ci][co] = w[t][co][ci]: the input gradient is the convolution of
 // the output gradient with the weights mirrored in space, channels transposed
 __global__ void k_flip(const __nv_bfloat16 *__restrict__ w, int cin, int cout, __nv_bfloat16 *__restrict__ wt) {
@@ -563,9 +744,14 @@ cf_status unet_forward(const UNetModel *m, const float *feats, int nz, int ny, i
     cf_status st = CF_OK;
     for (void *p : bufs)
         if (!p) st = CF_ENOMEM;
+    // every layer on the tcgen05 convolution where its channel counts allow (all of the default widths)
     auto conv = [&](int k, const void *in, int gz, int gy, int gx, void *out, int f32) {
-        if (st == CF_OK)
-            st = cf_unet_conv(in, 1, gz, gy, gx, m->cin[k], m->w[k], m->b[k], m->cout[k], k == 10 ? 0 : 1, f32, out, s);
+        if (st != CF_OK) return;
+        const int ci = m->cin[k], co = m->cout[k], relu = k == 10 ? 0 : 1;
+        if (ci % 16 == 0 && ci <= 256 && co % 16 == 0 && co <= 256)
+            st = cf_unet_conv_tc(in, 1, gz, gy, gx, ci, m->w[k], m->b[k], co, relu, f32, out, s);
+        else
+            st = cf_unet_conv(in, 1, gz, gy, gx, ci, m->w[k], m->b[k], co, relu, f32, out, s);
     };
     if (st == CF_OK) st = cf_unet_pack(feats, 4, N, 16, x, s);
     conv(0, x, nz, ny, nx, e0a, 0);
@@ -613,6 +799,45 @@ cf_status cf_unet_conv(const void *x, int n, int nz, int ny, int nx, int cin, co
     if (out_f32) k_conv_mma<true><<<grid, 32 * CW, 0, s>>>(g, xb, cin, wb, b, cout, relu, y);
     else k_conv_mma<false><<<grid, 32 * CW, 0, s>>>(g, xb, cin, wb, b, cout, relu, y);
     return ucheck(cudaGetLastError());
+}
+
+cf_status cf_unet_conv_tc(const void *x, int n, int nz, int ny, int nx, int cin, const void *w, const float *b,
+                          int cout, int relu, int out_f32, void *y, void *stream) {
+    if (!x || !w || !y) return bad("null argument");
+    if (!grid_ok(n, nz, ny, nx) || cin < 16 || cin % 16 || cin > 256 || cout < 16 || cout % 16 || cout > 256)
+        return bad("cf_unet_conv_tc: bad shape (cin and cout multiples of 16 up to 256)");
+    const Grid3 g{n, nz, ny, nx, (long long)nz * ny * nx};
+    const long long rows = (long long)n * g.V;
+    // the two operand stages; at least 228 KB * ncols / 512 so that the blocks
+    // resident on an SM never ask for more than its 512 tensor-memory columns
+    const int ncols = cout <= 32 ? 32 : (cout <= 64 ? 64 : (cout <= 128 ? 128 : 256));
+    const size_t smem = std::max(2 * ((size_t)128 * cin * 2 + (size_t)cout * cin * 2),
+                                 (size_t)228 * 1024 * ncols / 512 + 1024);
+    const cudaStream_t s = (cudaStream_t)stream;
+    const auto *xb = static_cast<const __nv_bfloat16 *>(x);
+    const auto *wb = static_cast<const __nv_bfloat16 *>(w);
+    unsigned *err = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void **>(&err), g_tc_err);
+    if (e != cudaSuccess) return ucheck(e);
+    const unsigned blocks = (unsigned)((rows + 127) / 128);
+    if (out_f32) {
+        e = cudaFuncSetAttribute(tc::k_conv_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) tc::k_conv_tc<true><<<blocks, 128, smem, s>>>(g, xb, cin, wb, b, cout, relu, y, err);
+    } else {
+        e = cudaFuncSetAttribute(tc::k_conv_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) tc::k_conv_tc<false><<<blocks, 128, smem, s>>>(g, xb, cin, wb, b, cout, relu, y, err);
+    }
+    if (e != cudaSuccess) return ucheck(e);
+    return ucheck(cudaGetLastError());
+}
+
+cf_status cf_unet_tc_error(unsigned *err) {
+    if (!err) return bad("null argument");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(err, g_tc_err, sizeof(unsigned));
+    const unsigned zero = 0;
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tc_err, &zero, sizeof(unsigned));
+    return ucheck(e);
 }
 
 cf_status cf_unet_flip(const void *w, int cin, int cout, void *wt, void *stream) {

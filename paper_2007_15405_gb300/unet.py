@@ -1,7 +1,8 @@
 """3-D U-net of the learned warm start, on the library's tensor-core layers.
 
 Every layer, gradient, loss and optimiser step runs in the CUDA library
-(cf_unet_conv / cf_unet_flip / cf_unet_wgrad / cf_unet_relu_grad /
+(cf_unet_conv_tc on the tcgen05 tensor cores, or cf_unet_conv on mma.sync /
+cf_unet_flip / cf_unet_wgrad / cf_unet_relu_grad /
 cf_unet_pool / cf_unet_upsample / cf_unet_concat / cf_unet_split /
 cf_unet_loss / cf_adam: bfloat16 activations and weights, fp32 accumulation
 on the tensor cores, fp32 gradients and master weights, sums in fixed order);
@@ -42,10 +43,11 @@ def _p(t):
 
 
 class UNet:
-    def __init__(self, widths=(32, 64, 128), seed=0, device="cuda"):
+    def __init__(self, widths=(32, 64, 128), seed=0, device="cuda", tensor_memory=True):
         import torch
         self.torch = torch
         self.dev = device
+        self.tensor_memory = tensor_memory  # tcgen05 convolutions (else mma.sync)
         w0, w1, w2 = widths
         self.widths = widths
         self.specs = [("e0a", CIN, w0, True), ("e0b", w0, w0, True), ("e1a", w0, w1, True),
@@ -87,14 +89,20 @@ class UNet:
         return next(s for s in self.specs if s[0] == name)
 
     # ------------------------------------------------------------- forward
+    def _conv_call(self, x, n, nz, ny, nx, ci, w, b, co, relu, out_f32, y):
+        """One convolution: on the tcgen05 path (cf_unet_conv_tc) where the
+        channel counts allow and self.tensor_memory is set, else mma.sync."""
+        fn = cfm._lib.cf_unet_conv_tc if (self.tensor_memory and ci % 16 == 0 and co % 16 == 0
+                                          and ci <= 256 and co <= 256) else cfm._lib.cf_unet_conv
+        cfm._check(fn(_p(x), n, nz, ny, nx, ci, _p(w), _p(b), co, int(relu), int(out_f32), _p(y), self._s()))
+
     def _conv(self, name, x, grid, out_f32=False):
         torch = self.torch
         _, ci, co, relu = self._spec(name)
         n, nz, ny, nx = grid
         y = torch.empty(n * nz * ny * nx * co, device=self.dev,
                         dtype=torch.float32 if out_f32 else torch.bfloat16)
-        cfm._check(cfm._lib.cf_unet_conv(_p(x), n, nz, ny, nx, ci, _p(self.wb[name]), _p(self.b[name]), co,
-                                         int(relu), int(out_f32), _p(y), self._s()))
+        self._conv_call(x, n, nz, ny, nx, ci, self.wb[name], self.b[name], co, relu, out_f32, y)
         return y
 
     def _pool(self, x, grid, c):
@@ -163,7 +171,7 @@ class UNet:
         wt = torch.empty_like(self.wb[name])
         cfm._check(L.cf_unet_flip(_p(self.wb[name]), ci, co, _p(wt), self._s()))
         gx = torch.empty(n * nz * ny * nx * ci, device=self.dev, dtype=torch.float32)
-        cfm._check(L.cf_unet_conv(_p(gm), n, nz, ny, nx, co, _p(wt), None, ci, 0, 1, _p(gx), self._s()))
+        self._conv_call(gm, n, nz, ny, nx, co, wt, None, ci, 0, 1, gx)
         return gx
 
     def backward(self, a, g_head, grid):

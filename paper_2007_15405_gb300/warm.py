@@ -1,25 +1,28 @@
-"""Learned warm start: a small 3-D convolutional network that predicts the
-equilibrated density field of a film with capsules from its set-up, so that
-the coupled run starts near equilibrium instead of from the flat film.
+"""Learned warm start: a network predicts the equilibrated state of a film
+with capsules from its set-up, so that the coupled run starts near
+equilibrium instead of from the flat film.
 
-Every layer, gradient and optimiser step runs in the library's CUDA kernels
-(cf_conv3d_forward / cf_conv3d_backward / cf_mse / cf_adam, bfloat16
-activations and weights, float32 accumulation and master weights); this
-module only holds the device buffers (torch tensors) and orders the calls.
+Two networks run on the library's CUDA kernels:
+- the 3-D U-net of unet.py (1.44M parameters, tensor-core convolutions) that
+  the library's cf_warmstart runs: density corrections and node
+  displacements, trained on capsule pairs of the sweep's generator
+  (pair_dataset, train_unet) and measured by the time to a 1% lateral force
+  (time_to_force);
+- WarmNet below, the first, smaller form (five dilated 3x3x3 convolutions
+  4 -> 16 -> 16 -> 16 -> 16 -> 2, dilations 1, 2, 4, 8, 1, on the FP32
+  layer kernels cf_conv3d_forward / cf_conv3d_backward / cf_mse / cf_adam),
+  kept with its set-up path (warm_start) and its convergence study.
 
-Network: five 3x3x3 convolutions 4 -> 16 -> 16 -> 16 -> 16 -> 2 with
-dilations 1, 2, 4, 8, 1 (receptive field 33 nodes), ReLU between them.
 Inputs per lattice node:
   0  capsule interior (1 inside a membrane, from the cut links)
   1  phi of the flat initial film, phi = (rho_A - rho_B) / (rho_maj - rho_min)
   2  z / nz
   3  log10(kS) + 2 (shear modulus of the capsule)
-Outputs: the equilibrium corrections of both densities on fluid nodes,
-(rho_c,eq - rho_c,film) / (rho_maj - rho_min) for c = A, B (the bulk
-composition relaxes too, not only the interface).  The predicted state is the
-film plus these corrections outside the capsules (at least 1e-3), the film
-values inside; each component is then scaled on the fluid outside the
-capsules to the flat film's mass, which the run conserves.
+Density outputs: the equilibrium corrections of both densities on fluid
+nodes, (rho_c,eq - rho_c,film) / (rho_maj - rho_min) for c = A, B.  The
+predicted state is the film plus these corrections outside the capsules (at
+least 1e-3), the film values inside; each component is then scaled on the
+fluid outside the capsules to the flat film's mass, which the run conserves.
 
 The warm-started run judges its own start: it advances two short windows and
 falls back to the flat film when densities turn non-finite or negative, a
@@ -320,33 +323,36 @@ def convergence(net, wls, total=8000, every=50, tol=0.01):
 # Its density head gives the warm start of the coupled run (set up and judged
 # as above); its displacement head the deformation of free capsules.
 
-def pair_dataset(wls_fixed, wls_free, eq_steps, def_steps):
+def pair_dataset(wls_fixed, wls_free, eq_steps, def_steps, chunk=64):
     """Training data of the U-net generated by the method.  Per set-up: the
     network inputs [4][V], density targets [2][V] and fluid mask [V] of the
     fixed-capsule run after eq_steps; the capsules' reference node positions
     [nodes][3] (lattice units) and their deformation after def_steps of the
     free run (each node's displacement minus its capsule's mean displacement)
-    [nodes][3]."""
-    sims = equilibrate(wls_fixed, eq_steps)
+    [nodes][3].  The runs go in batches of `chunk` lattices, each freed once
+    its data is read."""
     X, T, M = [], [], []
-    for s, w in zip(sims, wls_fixed):
-        x, mask = features(s, w)
-        X.append(x.reshape(N_IN, -1))
-        T.append(target_of(s, w).reshape(N_OUT, -1))
-        M.append(mask.reshape(-1))
-        s.close()
-    free = equilibrate(wls_free, def_steps)
+    for i0 in range(0, len(wls_fixed), chunk):
+        part = wls_fixed[i0:i0 + chunk]
+        for s, w in zip(equilibrate(part, eq_steps), part):
+            x, mask = features(s, w)
+            X.append(x.reshape(N_IN, -1))
+            T.append(target_of(s, w).reshape(N_OUT, -1))
+            M.append(mask.reshape(-1))
+            s.close()
     Xn, D = [], []
-    for s, w in zip(free, wls_free):
-        ref, dis = [], []
-        for k, cap in enumerate(w.capsules):
-            X0, _ = cap.mesh()
-            X1 = s.capsule_state(k)["X"]
-            ref.append(X0)
-            dis.append((X1 - X1.mean(0)) - (X0 - X0.mean(0)))
-        Xn.append(np.concatenate(ref))
-        D.append(np.concatenate(dis))
-        s.close()
+    for i0 in range(0, len(wls_free), chunk):
+        part = wls_free[i0:i0 + chunk]
+        for s, w in zip(equilibrate(part, def_steps), part):
+            ref, dis = [], []
+            for k, cap in enumerate(w.capsules):
+                X0, _ = cap.mesh()
+                X1 = s.capsule_state(k)["X"]
+                ref.append(X0)
+                dis.append((X1 - X1.mean(0)) - (X0 - X0.mean(0)))
+            Xn.append(np.concatenate(ref))
+            D.append(np.concatenate(dis))
+            s.close()
     f32 = lambda a: np.ascontiguousarray(np.stack(a), np.float32)  # noqa: E731
     return dict(X=f32(X), T=f32(T), M=f32(M), Xn=f32(Xn), D=f32(D),
                 shape=(wls_fixed[0].nz, wls_fixed[0].ny, wls_fixed[0].nx))

@@ -67,6 +67,48 @@ def test_conv_forward(env, n, nz, ny, nx, cin, cout):
     assert np.abs(gotb - np.maximum(ref, 0)).max() <= 2 ** -8 * np.abs(ref).max() + 1e-7
 
 
+TC_SHAPES = [(1, 4, 6, 8, 16, 16), (2, 5, 3, 7, 32, 48), (1, 6, 6, 6, 48, 16), (3, 4, 4, 8, 32, 32),
+             (1, 8, 10, 12, 192, 64), (1, 4, 8, 16, 128, 128), (1, 8, 8, 8, 32, 16)]
+
+
+@pytest.mark.parametrize("n,nz,ny,nx,cin,cout", TC_SHAPES)
+def test_conv_tensor_memory_path(env, n, nz, ny, nx, cin, cout):
+    """cf_unet_conv_tc (tcgen05 MMAs, accumulators in tensor memory) against
+    the FP64 definition, over tiles of 128 voxels with ragged tails, across
+    samples of a batch, and for every channel count the network uses."""
+    torch, cfm = env
+    L = cfm.load_library()
+    rng = np.random.default_rng(7 * cin + cout + n)
+    x = W.bf16_round(rng.standard_normal((n, nz, ny, nx, cin)))
+    w = W.bf16_round(rng.standard_normal((27, cout, cin)) / np.sqrt(27 * cin))
+    b = rng.standard_normal(cout).astype(np.float32)
+    ref = W.conv3d_cl(x, w, b.astype(np.float64), False)
+    xd, wd = bf16_dev(torch, x), bf16_dev(torch, w)
+    bd = torch.from_numpy(b).cuda()
+    yf = torch.empty(n * nz * ny * nx * cout, device="cuda")
+    cfm._check(L.cf_unet_conv_tc(p(xd), n, nz, ny, nx, cin, p(wd), p(bd), cout, 0, 1, p(yf), None))
+    yb = torch.empty(n * nz * ny * nx * cout, device="cuda", dtype=torch.bfloat16)
+    cfm._check(L.cf_unet_conv_tc(p(xd), n, nz, ny, nx, cin, p(wd), p(bd), cout, 1, 0, p(yb), None))
+    import ctypes
+    err = ctypes.c_uint(7)
+    cfm._check(L.cf_unet_tc_error(ctypes.byref(err)))
+    assert err.value == 0
+    got = host(yf).reshape(ref.shape)
+    assert rel(got, ref) < 5e-6, rel(got, ref)
+    gotb = host(yb).reshape(ref.shape)
+    assert np.abs(gotb - np.maximum(ref, 0)).max() <= 2 ** -8 * np.abs(ref).max() + 1e-7
+
+
+def test_conv_tensor_memory_path_rejects_bad_shapes(env):
+    torch, cfm = env
+    L = cfm.load_library()
+    x = torch.zeros(4 * 4 * 4 * 16, device="cuda", dtype=torch.bfloat16)
+    w = torch.zeros(27 * 8 * 16, device="cuda", dtype=torch.bfloat16)
+    y = torch.zeros(4 * 4 * 4 * 8, device="cuda", dtype=torch.bfloat16)
+    with pytest.raises(cfm.CapfilmError, match="multiples of 16"):
+        cfm._check(L.cf_unet_conv_tc(p(x), 1, 4, 4, 4, 16, p(w), None, 8, 0, 0, p(y), None))
+
+
 @pytest.mark.parametrize("n,nz,ny,nx,cin,cout", [(1, 4, 6, 8, 16, 16), (2, 5, 3, 7, 32, 48), (1, 6, 6, 6, 48, 16)])
 def test_conv_backward(env, n, nz, ny, nx, cin, cout):
     """Input gradient (mirrored, transposed weights through the forward
