@@ -84,8 +84,17 @@ def lib():
         L.or_lateral_force_of.argtypes = [_dp, _dp, _dp, _dp, C.c_int, C.c_int]
         L.or_lateral_force.restype = C.c_double
         L.or_lateral_force.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.or_peskin.restype = C.c_double
+        L.or_peskin.argtypes = [C.c_double]
+        L.or_ibm_spread_point.argtypes = [C.c_void_p, _dp, _dp, _dp]
+        L.or_ibm_interp_point.argtypes = [C.c_void_p, _dp, _dp, _dp]
         _lib = L
     return _lib
+
+
+def peskin(r):
+    """Peskin's 4-point kernel at offset r."""
+    return lib().or_peskin(float(r))
 
 
 def tables():
@@ -181,7 +190,7 @@ class Oracle:
     """One lattice with its capsules, stepped by the FP64 oracle."""
 
     # alternative readings of paper-silent points (or_set_flags)
-    INERTIAL, REF_RHO, MIRROR, REMOVE = 1, 2, 4, 8
+    INERTIAL, REF_RHO, MIRROR, REMOVE, IBM = 1, 2, 4, 8, 16
 
     def __init__(self, nx, ny, nz, wall=1, tau=(1.0, 1.0), G=3.6, rep_dz=10.0, flags=0):
         self.nx, self.ny, self.nz = nx, ny, nz
@@ -335,6 +344,24 @@ class Oracle:
         r = np.zeros(nr); z = np.zeros(nr); Z = np.zeros(1)
         hinf = lib().or_meniscus_profile(self._h, int(cid), float(dr), nr, _ptr(r), _ptr(z), _ptr(Z))
         return r, z, float(Z[0]), hinf
+
+    def ibm_spread_point(self, X, F, f=None):
+        """f [3][N] (float64) += the force F at X spread with Peskin's
+        4-point kernel (diffuse-interface coupling)."""
+        N = self.nx * self.ny * self.nz
+        f = np.zeros(3 * N) if f is None else f
+        X = np.ascontiguousarray(X, np.float64)
+        F = np.ascontiguousarray(F, np.float64)
+        lib().or_ibm_spread_point(self._h, _ptr(X), _ptr(F), _ptr(f))
+        return f
+
+    def ibm_interp_point(self, u, X):
+        """The field u [3][N] interpolated at X with the same kernel."""
+        u = np.ascontiguousarray(u, np.float64).reshape(-1)
+        X = np.ascontiguousarray(X, np.float64)
+        out = np.zeros(3)
+        lib().or_ibm_interp_point(self._h, _ptr(u), _ptr(X), _ptr(out))
+        return out
 
     def lateral_force(self, a, b):
         return lib().or_lateral_force(self._h, int(a), int(b))

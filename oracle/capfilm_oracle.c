@@ -28,6 +28,10 @@
  *   7. new cut links for the moved membrane.
  * An optional drying step (a reading: the paper fixes each film height per
  * run and lowers none) follows the collision, see remove_mass below.
+ * The flag OR_IBM replaces steps 1, 5 and 6's node update with the diffuse-
+ * interface coupling that the conclusions name for many-particle films: the
+ * membrane forces are spread with Peskin's 4-point kernel, act on the fluid
+ * in the collision, and the nodes move with the interpolated fluid velocity.
  * Points where the paper is silent are resolved the same way as in the CUDA
  * library and are listed as readings c1..c25 in the design notes.
  *
@@ -98,6 +102,7 @@ typedef struct or_ctx {
     long step;
     double dmA;                 /* drying: A mass turned into B per step (0: off) */
     int flags;                  /* alternative readings (OR_* below)       */
+    double *fibm;               /* [3][N] spread membrane force (OR_IBM)   */
     double mom_to_membrane[3];  /* cumulative momentum given to membranes  */
     double mom_to_wall[3];      /* cumulative momentum given to substrate  */
 } or_ctx;
@@ -110,7 +115,17 @@ typedef struct or_ctx {
  *   OR_MIRROR    partner density across a cut or substrate link = the node's
  *                own density instead of the mean over its side (c10)
  *   OR_REMOVE    drying removes the A mass instead of turning it into B (c23) */
-enum { OR_INERTIAL = 1, OR_REF_RHO = 2, OR_MIRROR = 4, OR_REMOVE = 8 };
+enum { OR_INERTIAL = 1, OR_REF_RHO = 2, OR_MIRROR = 4, OR_REMOVE = 8, OR_IBM = 16 };
+/*   OR_IBM      diffuse-interface (immersed-boundary) coupling instead of the
+ *               cut-link bounce-back: the membrane forces are spread to the
+ *               lattice with Peskin's 4-point kernel and enter the collision
+ *               as a body force shared by the components in proportion to
+ *               their densities; the nodes move with the fluid velocity
+ *               interpolated with the same kernel; no link is cut for the
+ *               fluid (the cut structure is kept for the interior flags). */
+
+/* cut bits the lattice sees: none with the diffuse-interface coupling */
+static uint32_t lmask(const or_ctx *c, long n) { return (c->flags & OR_IBM) ? 0u : c->mask[n]; }
 
 static long nidx(const or_ctx *c, int x, int y, int z) {
     return ((long)z * c->ny + y) * c->nx + x;
@@ -162,7 +177,7 @@ void or_destroy(or_ctx *c) {
         free(p->Fint); free(p->Ftot);
     }
     free(c->fpost); free(c->fpre); free(c->rho); free(c->u); free(c->mask); free(c->tri);
-    free(c->slink); free(c->inside);
+    free(c->slink); free(c->inside); free(c->fibm);
     free(c);
 }
 
@@ -598,7 +613,7 @@ static void stream(or_ctx *c) {
                     int sx = x - EV[i][0], sy = y - EV[i][1], sz = z - EV[i][2];
                     int ib = opp(i);  /* x + e_ib is the source node */
                     int solid = c->wall && wrap(sz, c->nz) == 0;
-                    int cut = (i != 0) && (c->mask[n] & (1u << (ib - 1)));
+                    int cut = (i != 0) && (lmask(c, n) & (1u << (ib - 1)));
                     for (int cc = 0; cc < 2; ++cc) {
                         double *dst = F_(c, c->fpre, cc, i, n);
                         if (i != 0 && solid) {
@@ -646,7 +661,7 @@ static double rho_interp(const or_ctx *c, const double *rho, int x, int y, int z
     for (int k = 1; k < NQ; ++k) {
         int z2 = z + EV[k][2];
         if (c->wall && wrap(z2, c->nz) == 0) continue;
-        if (c->mask[n] & (1u << (k - 1))) continue;
+        if (lmask(c, n) & (1u << (k - 1))) continue;
         long m = nidx(c, wrap(x + EV[k][0], c->nx), wrap(y + EV[k][1], c->ny), wrap(z2, c->nz));
         s += rho[m];
         ++cnt;
@@ -688,7 +703,7 @@ static void collide(or_ctx *c, double *Fsc_out) {
                     for (int k = 1; k < NQ; ++k) {
                         int z2 = z + EV[k][2];
                         int wallk = c->wall && wrap(z2, c->nz) == 0;
-                        int cutk = c->mask[n] & (1u << (k - 1));
+                        int cutk = lmask(c, n) & (1u << (k - 1));
                         double pf;
                         if (wallk || cutk) {
                             if (rho_far[cb] < 0.0) rho_far[cb] = rho_interp(c, &rho[cb * N], x, y, z, n);
@@ -713,6 +728,11 @@ static void collide(or_ctx *c, double *Fsc_out) {
                 if (Fsc_out)
                     for (int cc = 0; cc < 2; ++cc)
                         for (int a = 0; a < 3; ++a) Fsc_out[(cc * 3 + a) * N + n] = Fc[cc][a];
+                if (c->flags & OR_IBM) {  /* spread membrane force, shared by density */
+                    double rt = rho[n] + rho[N + n];
+                    for (int cc = 0; cc < 2; ++cc)
+                        for (int a = 0; a < 3; ++a) Fc[cc][a] += c->fibm[a * N + n] * rho[cc * N + n] / rt;
+                }
                 /* velocity shift (Shan & Chen): common velocity weighted by 1/tau */
                 double num[3] = {0, 0, 0}, den = 0.0;
                 for (int cc = 0; cc < 2; ++cc) {
@@ -747,6 +767,9 @@ static void elastic_forces(const or_capsule *p, double *Fel, double *E3) {
     if (E3) { E3[0] = es; E3[1] = eb; E3[2] = ev; }
 }
 
+static void membrane_forces(or_ctx *c);
+static void integrate(or_ctx *c);
+
 static void membrane_update(or_ctx *c) {
     /* element momentum exchange of this step (links were recorded per node) */
     for (int ci = 0; ci < c->ncaps; ++ci) memset(c->caps[ci].FT_cur, 0, sizeof(double) * 3 * c->caps[ci].nf);
@@ -773,6 +796,16 @@ static void membrane_update(or_ctx *c) {
             }
         }
         memcpy(p->FT_prev, p->FT_cur, sizeof(double) * 3 * p->nf);
+    }
+    membrane_forces(c);
+    integrate(c);
+}
+
+/* elastic (Fel) and Hertz (Fint) node forces of every capsule at the current
+ * positions */
+static void membrane_forces(or_ctx *c) {
+    for (int ci = 0; ci < c->ncaps; ++ci) {
+        or_capsule *p = &c->caps[ci];
         if (p->mode == 0) elastic_forces(p, p->Fel, NULL);
         else memset(p->Fel, 0, sizeof(double) * 3 * p->nv);
         memset(p->Fint, 0, sizeof(double) * 3 * p->nv);
@@ -798,7 +831,10 @@ static void membrane_update(or_ctx *c) {
                     }
                 }
         }
-    /* integrate and reduce */
+}
+
+/* node update (Eq. 9) and the per-capsule sums */
+static void integrate(or_ctx *c) {
     for (int ci = 0; ci < c->ncaps; ++ci) {
         or_capsule *p = &c->caps[ci];
         double sF[3] = {0, 0, 0}, sT[3] = {0, 0, 0}, com[3] = {0, 0, 0}, sFt[3] = {0, 0, 0};
@@ -868,13 +904,124 @@ static void remove_mass(or_ctx *c) {
     }
 }
 
+/* ------------------------------------------- diffuse-interface coupling */
+/* Peskin's 4-point kernel: phi(r) = (3 - 2|r| + sqrt(1 + 4|r| - 4r^2)) / 8
+ * for |r| <= 1, (5 - 2|r| - sqrt(-7 + 12|r| - 4r^2)) / 8 for 1 <= |r| <= 2,
+ * 0 beyond; its shifts sum to 1 and have zero first moment at every offset */
+static double peskin(double r) {
+    r = fabs(r);
+    if (r <= 1.0) return (3.0 - 2.0 * r + sqrt(1.0 + 4.0 * r - 4.0 * r * r)) / 8.0;
+    if (r <= 2.0) return (5.0 - 2.0 * r - sqrt(-7.0 + 12.0 * r - 4.0 * r * r)) / 8.0;
+    return 0.0;
+}
+
+/* the 64 lattice nodes around X (periodic) with their weights; solid
+ * (substrate) nodes get index -1 */
+static void ibm_stencil(const or_ctx *c, const double *X, long idx[64], double w[64]) {
+    int b[3];
+    double wa[3][4];
+    for (int a = 0; a < 3; ++a) {
+        b[a] = (int)floor(X[a]) - 1;
+        for (int k = 0; k < 4; ++k) wa[a][k] = peskin(X[a] - (double)(b[a] + k));
+    }
+    int m = 0;
+    for (int kz = 0; kz < 4; ++kz)
+        for (int ky = 0; ky < 4; ++ky)
+            for (int kx = 0; kx < 4; ++kx, ++m) {
+                const int z = wrap(b[2] + kz, c->nz);
+                w[m] = wa[0][kx] * wa[1][ky] * wa[2][kz];
+                idx[m] = is_solid(c, z) ? -1 : nidx(c, wrap(b[0] + kx, c->nx), wrap(b[1] + ky, c->ny), z);
+            }
+}
+
+/* f[3][N] += the force F at X spread with the kernel (nothing on solid nodes) */
+static void ibm_spread_point(const or_ctx *c, const double *X, const double *F, double *f) {
+    long idx[64];
+    double w[64];
+    ibm_stencil(c, X, idx, w);
+    for (int m = 0; m < 64; ++m)
+        if (idx[m] >= 0)
+            for (int a = 0; a < 3; ++a) f[a * c->N + idx[m]] += F[a] * w[m];
+}
+
+/* the field u[3][N] interpolated at X (solid nodes carry zero velocity) */
+static void ibm_interp_point(const or_ctx *c, const double *u, const double *X, double out[3]) {
+    long idx[64];
+    double w[64];
+    ibm_stencil(c, X, idx, w);
+    out[0] = out[1] = out[2] = 0.0;
+    for (int m = 0; m < 64; ++m)
+        if (idx[m] >= 0)
+            for (int a = 0; a < 3; ++a) out[a] += u[a * c->N + idx[m]] * w[m];
+}
+
+/* membrane forces at the current positions, spread to the lattice */
+static void ibm_spread(or_ctx *c) {
+    memset(c->fibm, 0, sizeof(double) * 3 * c->N);
+    for (int ci = 0; ci < c->ncaps; ++ci) memset(c->caps[ci].Fcpl, 0, sizeof(double) * 3 * c->caps[ci].nv);
+    membrane_forces(c);
+    for (int ci = 0; ci < c->ncaps; ++ci) {
+        or_capsule *p = &c->caps[ci];
+        for (int v = 0; v < p->nv; ++v) {
+            double F[3];
+            for (int a = 0; a < 3; ++a) F[a] = p->Fel[3 * v + a] + p->Fint[3 * v + a];
+            ibm_spread_point(c, &p->X[3 * v], F, c->fibm);
+        }
+    }
+}
+
+/* nodes moved with the interpolated physical fluid velocity of this step;
+ * force sums (the coupling force is zero: no link is cut), area, volume */
+static void ibm_move(or_ctx *c) {
+    for (int ci = 0; ci < c->ncaps; ++ci) {
+        or_capsule *p = &c->caps[ci];
+        for (int v = 0; v < p->nv; ++v)
+            for (int a = 0; a < 3; ++a) p->Ftot[3 * v + a] = p->Fel[3 * v + a] + p->Fint[3 * v + a];
+        memset(p->force, 0, sizeof(p->force));
+        memset(p->torque, 0, sizeof(p->torque));
+        p->area = mesh_area(p->X, p->F, p->nf);
+        p->volume = mesh_volume(p->X, p->F, p->nf);
+        if (p->mode != 0) { memset(p->V, 0, sizeof(double) * 3 * p->nv); continue; }
+        for (int v = 0; v < p->nv; ++v) {
+            double u[3];
+            ibm_interp_point(c, c->u, &p->X[3 * v], u);
+            for (int a = 0; a < 3; ++a) {
+                p->V[3 * v + a] = u[a];
+                p->X[3 * v + a] += u[a];
+            }
+        }
+    }
+}
+
+double or_peskin(double r) { return peskin(r); }
+void or_ibm_spread_point(const or_ctx *c, const double *X, const double *F, double *f) {
+    ibm_spread_point(c, X, F, f);
+}
+void or_ibm_interp_point(const or_ctx *c, const double *u, const double *X, double *out) {
+    ibm_interp_point(c, u, X, out);
+}
+
 void or_remove_mass(or_ctx *c, double dmA) { c->dmA = dmA; }
 
 /* Alternative readings (OR_* flags above), 0 for the defaults. */
-void or_set_flags(or_ctx *c, int flags) { c->flags = flags; }
+void or_set_flags(or_ctx *c, int flags) {
+    c->flags = flags;
+    if ((flags & OR_IBM) && !c->fibm) c->fibm = (double *)calloc(3 * (size_t)c->N, sizeof(double));
+}
 
 int or_step(or_ctx *c, int nsteps) {
     for (int s = 0; s < nsteps; ++s) {
+        if (c->flags & OR_IBM) {
+            stream(c);
+            ibm_spread(c);
+            collide(c, NULL);
+            if (c->dmA > 0.0) remove_mass(c);
+            ibm_move(c);
+            compute_cuts(c);   /* the interior flags of the readouts follow the membrane */
+            compute_inside(c);
+            c->step++;
+            continue;
+        }
         stream(c);
         collide(c, NULL);
         if (c->dmA > 0.0) remove_mass(c);
