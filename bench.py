@@ -80,6 +80,9 @@ def parse():
     ap.add_argument("--cluster-n", type=int, default=100, help="particles of --cluster")
     ap.add_argument("--cluster-box", type=int, nargs=2, default=(320, 320), metavar=("NX", "NY"),
                     help="lattice of --cluster (the paper's 1730 particles: 1200 1200)")
+    ap.add_argument("--coupling", action="store_true",
+                    help="the cut-link coupling against the diffuse-interface (Peskin-kernel) variant on the "
+                         "many-particle film of --cluster (--cluster-n, --cluster-box)")
     ap.add_argument("--approach", action="store_true",
                     help="approach dynamics of two free soft particles (gap against time)")
     ap.add_argument("--approach-steps", type=int, default=40000)
@@ -861,8 +864,68 @@ def run_cluster(args):
     print(json.dumps(line), flush=True)
 
 
+IBM_BYTES_PER_LU = 304 + 24 + 24 + 16  # + spread force read and cleared, fluid velocity written
+
+
+def run_coupling(args):
+    """The paper's cut-link coupling (Sec. 3.1) and the diffuse-interface
+    variant (CF_IBM) on the same many-particle film: time per step through
+    cf_step (CUDA events, W warm-up steps, K timed steps) and its phases."""
+    import torch
+    from paper_2007_15405_gb300 import build as B
+    B.build()
+    from paper_2007_15405_gb300 import capfilm as cfm
+    from paper_2007_15405_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    peak, peak_kind = measured_peak()
+    nx, ny = args.cluster_box
+    wl = I.many_capsules(args.cluster_n, nx, ny, dmin=None if args.cluster_n <= 100 else 23.0)
+    nmem = sum(cap.mesh()[0].shape[0] for cap in wl.capsules)
+    clocks = ClockSampler(0)
+    res = {}
+    for name, flags in (("cut_link", 0), ("ibm", cfm.IBM)):
+        wl.flags = flags
+        sim = cfm.Simulation.from_workload(wl)
+        sim.step(max(3, args.warmup))
+        sim.sync()
+        if name == "cut_link":
+            clocks.start()
+            time.sleep(0.3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(sim.stream)
+        sim.step(args.steps)
+        e1.record(sim.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        launches = sim.launches()
+        ph = sim.time_phases(min(100, max(10, args.steps // 5)))
+        sim.close()
+        alg = ALG_BYTES_PER_LU if name == "cut_link" else IBM_BYTES_PER_LU
+        r = {"mlups": wl.nodes / ms / 1e3, "ms_per_step": ms, "gpu_launches": launches,
+             "lattice_roofline": roofline(alg, wl.nodes, ph[0], "lattice update: k_density + k_collide_eq "
+                                          "(tau = 1)", peak, peak_kind)}
+        if name == "cut_link":
+            r["phases_ms"] = {"lattice": ph[0], "membrane": ph[1], "cut_links": ph[2], "bounce_prep": ph[3]}
+        else:
+            r["phases_ms"] = {"lattice": ph[0], "interpolate_and_move": ph[1], "cut_links": ph[2],
+                              "forces_and_spread": ph[3]}
+            r["spread_atomics_per_step"] = 192 * nmem
+        res[name] = r
+    clk = clocks.stop()
+    line = {"metric": "coupled step time: cut-link bounce-back against the diffuse-interface variant",
+            "unit": "MLUPS", "value": res["ibm"]["mlups"], "higher_is_better": True,
+            "steps": args.steps, "warmup": max(3, args.warmup), "data": "synthetic", "dtype": "f32",
+            "config": {"workload": wl.name + f", {len(wl.capsules)} free R=10 level-4 particles, film 0.35R",
+                       "nodes": wl.nodes, "membrane_nodes": nmem, "l2": l2_note(ALG_BYTES_PER_LU * wl.nodes)},
+            "clocks": clk, **res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.coupling:
+        return run_coupling(args)
     if args.unet:
         return run_unet(args)
     if args.cluster:

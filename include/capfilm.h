@@ -86,8 +86,24 @@ typedef struct {
  *                    3.1, last paragraph) = the node's own density instead
  *                    of the mean over the node and its same-side neighbours
  * CF_DRY_REMOVE      drying (cf_remove_mass) removes the A mass instead of
- *                    turning it into B */
-enum { CF_INERTIAL = 1, CF_LADD_REF_RHO = 2, CF_PARTNER_MIRROR = 4, CF_DRY_REMOVE = 8 };
+ *                    turning it into B
+ * CF_IBM             diffuse-interface (immersed-boundary) coupling instead
+ *                    of the paper's cut-link coupling (Sec. 3.1); not part
+ *                    of the paper, a variant for comparison: each step the membrane forces (Eqs. 6-8, 11) of every
+ *                    node are spread to the 4x4x4 lattice nodes around it
+ *                    with Peskin's 4-point kernel, act in the collision as a
+ *                    body force shared by the components in proportion to
+ *                    their densities, and the nodes then move with the fluid
+ *                    velocity (with the half-force shift) interpolated with
+ *                    the same kernel.  No lattice link is cut: no bounce-back,
+ *                    momentum exchange, Shan-Chen decoupling or wetting offset
+ *                    at the membrane, so cf_capsule_force and the lateral
+ *                    force read zero; the cut links of the moved membrane
+ *                    still give the interior flags of the meniscus readouts.
+ *                    Free and fixed capsules only (CF_EINVAL for frozen ones,
+ *                    for CF_INERTIAL, and for a batch).  Costs 44 more bytes
+ *                    per lattice node. */
+enum { CF_INERTIAL = 1, CF_LADD_REF_RHO = 2, CF_PARTNER_MIRROR = 4, CF_DRY_REMOVE = 8, CF_IBM = 16 };
 
 typedef struct {
     int nx, ny, nz;          /* lattice size, each >= 3                        */
@@ -268,8 +284,10 @@ cf_status cf_cuts(cf_ctx *ctx, uint32_t *mask, int *tri, uint8_t *inside);
 /* Advance n steps like cf_step, without graph replay, timing each phase with
  * CUDA events on the context stream; ms[0..3] receive the mean device time per
  * step of the two lattice passes, of the membrane phase, of the cut-link
- * rebuild and of the bounce-record preparation (milliseconds).  Synchronises.
- * For measurement; the populations advance exactly as with cf_step. */
+ * rebuild and of the bounce-record preparation (milliseconds).  With CF_IBM,
+ * ms[1] is the interpolation and move of the nodes and ms[3] the membrane
+ * forces with their spreading.  Synchronises.  For measurement; the
+ * populations advance exactly as with cf_step. */
 cf_status cf_time_phases(cf_ctx *ctx, long long n, double ms[4]);
 
 /* One lattice time step without capsules that allocates no device memory.

@@ -28,10 +28,11 @@
  *   7. new cut links for the moved membrane.
  * An optional drying step (a reading: the paper fixes each film height per
  * run and lowers none) follows the collision, see remove_mass below.
- * The flag OR_IBM replaces steps 1, 5 and 6's node update with the diffuse-
- * interface coupling that the conclusions name for many-particle films: the
- * membrane forces are spread with Peskin's 4-point kernel, act on the fluid
- * in the collision, and the nodes move with the interpolated fluid velocity.
+ * The flag OR_IBM replaces the cut-link parts of steps 1, 3 and 5 and the node
+ * update of step 6 with a diffuse-interface (immersed-boundary) coupling, a
+ * variant that is not part of the paper: the membrane forces are spread with
+ * Peskin's 4-point kernel, act on the fluid in the collision, and the nodes
+ * move with the interpolated fluid velocity.
  * Points where the paper is silent are resolved the same way as in the CUDA
  * library and are listed as readings c1..c25 in the design notes.
  *

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "CF_OK", 1: "CF_EINVAL", 2: "CF_ENOMEM", 3: "CF_ECUDA", 4: "C
 
 FREE, FROZEN, FIXED = 0, 1, 2
 # alternative readings (cf_lattice_desc.flags)
-INERTIAL, LADD_REF_RHO, PARTNER_MIRROR, DRY_REMOVE = 1, 2, 4, 8
+INERTIAL, LADD_REF_RHO, PARTNER_MIRROR, DRY_REMOVE, IBM = 1, 2, 4, 8, 16
 FP32, FP16_SHIFT, BF16_SHIFT = 0, 1, 2
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

@@ -88,6 +88,11 @@ struct cf_ctx {
     float2 *psi = nullptr;                 // pseudopotentials of the current step
     float4 *J = nullptr;                   // total momentum of the current step (tau = 1)
     uint32_t *mask = nullptr;
+    // diffuse-interface coupling (CF_IBM): spread membrane force [3][N] (fixed
+    // point), fluid velocity [N], and the all-zero cut bits the lattice reads
+    long long *fibm = nullptr;
+    float4 *uphys = nullptr;
+    uint32_t *mask0 = nullptr;
     int *tri = nullptr;
     float2 *rec = nullptr;        // [N][18] bounce records (A, B) by arriving direction
     uint8_t *inside = nullptr;
@@ -202,10 +207,11 @@ LBParams lb_params(cf_ctx *c, bool with_out) {
     p.src0 = c->f0[c->fpar];
     p.dst0 = c->f0[1 - c->fpar];
     p.step_ctr = c->step_ctr;
-    p.mask = c->mask;
+    // with the diffuse-interface coupling no link is cut for the fluid
+    p.mask = c->mask0 ? c->mask0 : c->mask;
     p.tri = c->tri;
-    p.faces = c->faces;
-    p.V = c->V;
+    p.fibm = c->fibm;
+    p.uphys = c->uphys;
     p.FT = c->FT[c->ftpar];
     p.out = with_out ? c->out : nullptr;
     p.rho = c->rho[1 - c->fpar];
@@ -257,6 +263,9 @@ MemParams mem_params(cf_ctx *c) {
     p.pbox = c->pbox;
     p.nbr = c->nbr;
     p.nbr_cnt = c->nbr_cnt;
+    p.fibm = c->fibm;
+    p.uphys = c->uphys;
+    p.N = c->N;
     return p;
 }
 
@@ -388,7 +397,59 @@ cf_status enqueue_post(cf_ctx *c, int *nl, cudaEvent_t ev2 = nullptr) {
     return CF_OK;
 }
 
+// One step with the diffuse-interface coupling (CF_IBM):
+//
+//   stream   ------------------join-> update: spread (+ cut reset) -> density -> collide -> move -> cut links
+//   stream2  \-> memsets -> elements -> nodes -> bending -/
+//
+// The membrane forces of the current positions are spread before the
+// collision that applies them; the nodes then move with this step's fluid
+// velocity.  The lattice sees no cut link; the cut links of the new positions
+// only give the interior flags of the readouts.
+cf_status enqueue_step_ibm(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev) {
+    if (ev) CF_CUDA(cudaEventRecord(ev[4], c->stream));
+    const bool mem = c->nnodes > 0;
+    if (mem) {
+        CF_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+        CF_CUDA(cudaStreamWaitEvent(c->stream2, c->ev_fork, 0));
+        const int nc = (int)c->caps.size();
+        int *bb = c->bbox[c->xpar];
+        CF_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(double) * A_NACC * nc, c->stream2));
+        CF_CUDA(cudaMemsetAsync(bb, 0x7f, sizeof(int) * 3 * nc, c->stream2));
+        CF_CUDA(cudaMemsetAsync(bb + 3 * nc, 0x80, sizeof(int) * 3 * nc, c->stream2));
+        if (c->nbr) {
+            MemParams q = mem_params(c);
+            q.nbr = nullptr;
+            CF_CUDA(launch_contact_partners(q, c->nbr, c->nbr_cnt, c->stream2, nl));
+        }
+        CF_CUDA(launch_membrane_forces(mem_params(c), c->stream2, nl));
+        CF_CUDA(cudaEventRecord(c->ev_join, c->stream2));
+        CF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+        CF_CUDA(launch_membrane_update(mem_params(c), clear_params(c, 304), false, c->stream, nl));
+    }
+    if (ev) CF_CUDA(cudaEventRecord(ev[0], c->stream));
+    CF_CUDA(launch_lb_step(lb_params(c, with_out), c->d.precision, c->stream));
+    *nl += 2;
+    c->fpar = 1 - c->fpar;
+    if (ev) CF_CUDA(cudaEventRecord(ev[1], c->stream));
+    if (mem) {
+        CF_CUDA(launch_ibm_move(mem_params(c), c->stream, nl));
+        c->xpar = 1 - c->xpar;
+    }
+    if (ev) CF_CUDA(cudaEventRecord(ev[2], c->stream));
+    if (mem) {
+        if (!c->all_fixed) {
+            cf_status s = enqueue_cuts(c, c->X[c->xpar], nl, true);
+            if (s != CF_OK) return s;
+        }
+        c->ftpar = 1 - c->ftpar;  // the exchange accumulators stay zero: no link is cut for the fluid
+    }
+    if (ev) CF_CUDA(cudaEventRecord(ev[3], c->stream));
+    return CF_OK;
+}
+
 cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev = nullptr) {
+    if (c->fibm) return enqueue_step_ibm(c, with_out, nl, ev);
     if (ev) CF_CUDA(cudaEventRecord(ev[4], c->stream));
     cf_status s = enqueue_pre(c, nl);
     if (s != CF_OK) return s;
@@ -657,8 +718,10 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     if (desc->precision != CF_FP32 && desc->precision != CF_FP16_SHIFT &&
         desc->precision != CF_BF16_SHIFT)
         return fail(CF_EINVAL, "unsupported precision");
-    if (desc->flags & ~(CF_INERTIAL | CF_LADD_REF_RHO | CF_PARTNER_MIRROR | CF_DRY_REMOVE))
+    if (desc->flags & ~(CF_INERTIAL | CF_LADD_REF_RHO | CF_PARTNER_MIRROR | CF_DRY_REMOVE | CF_IBM))
         return fail(CF_EINVAL, "unknown flag");
+    if ((desc->flags & CF_IBM) && (desc->flags & CF_INERTIAL))
+        return fail(CF_EINVAL, "CF_INERTIAL does not apply to the diffuse-interface coupling (CF_IBM)");
     cf_ctx *c = new cf_ctx();
     c->d = *desc;
     c->N = (long long)desc->nx * desc->ny * desc->nz;
@@ -702,7 +765,13 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     c->status = (unsigned *)dalloc(c, sizeof(unsigned));
     c->dscratch = (double *)dalloc(c, sizeof(double) * 8);
     c->hscratch = (float *)dalloc(c, sizeof(float) * desc->nx * desc->ny);
-    if (!c->f[0] || !c->f[1] || !c->f0[0] || !c->f0[1] || !c->step_ctr || !c->out || !c->rho[0] || !c->rho[1] || !c->psi || (tau1 && !c->J) || !c->mask || !c->tri || !c->inside ||
+    const bool ibm = (desc->flags & CF_IBM) != 0;
+    if (ibm) {
+        c->fibm = (long long *)dalloc(c, sizeof(long long) * 3 * N);
+        c->uphys = (float4 *)dalloc(c, sizeof(float4) * N);
+        c->mask0 = (uint32_t *)dalloc(c, sizeof(uint32_t) * N);
+    }
+    if ((ibm && (!c->fibm || !c->uphys || !c->mask0)) || !c->f[0] || !c->f[1] || !c->f0[0] || !c->f0[1] || !c->step_ctr || !c->out || !c->rho[0] || !c->rho[1] || !c->psi || (tau1 && !c->J) || !c->mask || !c->tri || !c->inside ||
         !c->counts || !c->status || !c->dscratch || !c->hscratch) {
         cf_destroy(c);
         return fail(CF_ENOMEM, "device allocation failed");
@@ -721,6 +790,11 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     cudaMemsetAsync(c->inside, 0, N, c->stream);
     cudaMemsetAsync(c->counts, 0, sizeof(int) * 2, c->stream);
     cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream);
+    if (ibm) {
+        cudaMemsetAsync(c->fibm, 0, sizeof(long long) * 3 * N, c->stream);
+        cudaMemsetAsync(c->uphys, 0, sizeof(float4) * N, c->stream);
+        cudaMemsetAsync(c->mask0, 0, sizeof(uint32_t) * N, c->stream);
+    }
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         cf_destroy(c);
@@ -773,6 +847,8 @@ cf_status cf_add_capsules(cf_ctx *c, const cf_capsule_desc *d, int n, int *ids) 
     for (int k = 0; k < n; ++k) {
         cf_status s = host_capsule(d + k, hs[k]);
         if (s != CF_OK) return s;
+        if (c->fibm && hs[k].mode == CF_FROZEN)
+            return fail(CF_EINVAL, "frozen capsules need the cut-link coupling (not CF_IBM)");
     }
     const size_t n0 = c->caps.size();
     for (auto &h : hs) c->caps.push_back(std::move(h));
@@ -792,6 +868,8 @@ cf_status cf_set_capsule_mode(cf_ctx *c, int id, int mode) {
     if (!c) return fail(CF_EINVAL, "null context");
     if (id < 0 || id >= (int)c->caps.size()) return fail(CF_ENOTFOUND, "unknown capsule");
     if (mode < 0 || mode > 2) return fail(CF_EINVAL, "bad capsule mode");
+    if (c->fibm && mode == CF_FROZEN)
+        return fail(CF_EINVAL, "frozen capsules need the cut-link coupling (not CF_IBM)");
     CF_CUDA(cudaStreamSynchronize(c->stream));
     c->caps[id].mode = mode;
     CapDev d;
@@ -1834,6 +1912,7 @@ cf_status cf_batch_create(cf_ctx *const *ctxs, int n, cf_batch **out) {
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i]) return fail(CF_EINVAL, "null context in batch");
         if (!ctxs[i]->film_set) return fail(CF_ESTATE, "cf_set_film must come before cf_batch_create");
+        if (ctxs[i]->fibm) return fail(CF_EINVAL, "the diffuse-interface coupling (CF_IBM) is not available in a batch");
         if (ctxs[i]->d.precision != ctxs[0]->d.precision)
             return fail(CF_EINVAL, "all contexts of a batch need the same precision");
         for (int j = 0; j < i; ++j)

@@ -117,8 +117,11 @@ struct LBParams {
     unsigned *__restrict__ step_ctr; // step counter (stochastic-rounding stream)
     const uint32_t *__restrict__ mask;  // cut bits per node
     const int *__restrict__ tri;        // crossed element per node and link [N*18]
-    const int *__restrict__ faces;      // element nodes [3*nfaces]
-    const float *__restrict__ V;        // node velocities [3*nnodes]
+    // diffuse-interface coupling (CF_IBM; null otherwise): the membrane force
+    // spread to the lattice (ft_add), read and cleared by the collide pass,
+    // which also writes the fluid velocity the nodes move with
+    long long *__restrict__ fibm;       // [3][N]
+    float4 *__restrict__ uphys;         // [N] (ux, uy, uz, 0)
     long long *__restrict__ FT;         // element momentum exchange accumulators [3*nfaces] (ft_add)
     const float2 *__restrict__ rec;     // [N][18] bounced (A, B) populations by arriving direction - 1
     const float *__restrict__ wet_el;   // [nfaces] wetting offset of each element's capsule (null: all 0)
@@ -197,6 +200,12 @@ struct MemParams {
     // CF_NBR_MAX means "all capsules".  Null: every capsule is checked.
     const int *nbr;
     const int *nbr_cnt;
+    // diffuse-interface coupling (CF_IBM; null otherwise): the node update
+    // spreads each node's force into fibm [3][N] instead of moving it, and the
+    // move kernel steps the nodes with uphys [N] interpolated at their positions
+    long long *fibm;
+    const float4 *uphys;
+    long long N;
 };
 constexpr int CF_NBR_MAX = 48;
 constexpr int CF_NBR_MIN_CAPS = 16;  // fewer capsules: no lists, the loop checks them all
@@ -285,7 +294,7 @@ cudaError_t launch_lb_step(const LBParams &p, int prec, cudaStream_t s);
 // per pass.  The per-lattice parameters travel by value in the launch (one
 // table per step parity of a captured step pair); the work list holds
 // (lattice, x tile, y tile, z slice) items of the chosen tile shape.
-// (128 x 200 B fits the 32 KB launch-parameter limit; a build with a table of
+// (128 x 248 B fits the 32 KB launch-parameter limit; a build with a table of
 // at most 16 lattices keeps the launch parameters under 4 KB)
 #ifndef CF_BATCH_MAX
 #define CF_BATCH_MAX 128
@@ -345,6 +354,8 @@ cudaError_t launch_membrane_update(const MemParams &p, const ClearParams &cl, bo
 cudaError_t launch_contact_partners(const MemParams &p, int *nbr, int *nbr_cnt, cudaStream_t s, int *nlaunch);
 cudaError_t launch_cuts(const CutParams &p, cudaStream_t s, int *nlaunch);
 cudaError_t launch_prep(const PrepParams &p, cudaStream_t s, int *nlaunch);
+// diffuse-interface coupling: nodes moved with the interpolated fluid velocity
+cudaError_t launch_ibm_move(const MemParams &p, cudaStream_t s, int *nl);
 // batched forms (one launch per kernel for all lattices of the tables); tv:
 // node-kernel blocks (32 nodes), tf: element-kernel blocks (64 elements), cut
 // links: cut_blocks(nfaces, lanes) blocks with lanes = cut_lanes(the launch's

@@ -407,6 +407,22 @@ __device__ __forceinline__ void sc_force(const LBParams &p, const Deltas &d, uin
     }
 }
 
+// Diffuse-interface coupling (CF_IBM): the membrane force spread to node n
+// acts on the fluid as a body force, shared by the components in proportion
+// to their densities.  The accumulator is cleared for the next spreading.
+__device__ __forceinline__ void ibm_force(const LBParams &p, int n, float ra, float rb, float (&FA)[3],
+                                          float (&FB)[3]) {
+    long long *f = p.fibm + n;
+    const float F[3] = {ft_val(f[0]), ft_val(f[p.N]), ft_val(f[2 * p.N])};
+    f[0] = 0; f[p.N] = 0; f[2 * p.N] = 0;
+    const float sa = ra / (ra + rb), sb = rb / (ra + rb);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        FA[a] += sa * F[a];
+        FB[a] += sb * F[a];
+    }
+}
+
 // Post-collision populations of node n from the equilibria at (rho, u^eq)
 // (Eq. 5): BGK relaxation of the pulled fa, fb, or with EQ (tau = 1 for both
 // components) the equilibria themselves.  Float storage: the rest population
@@ -513,6 +529,7 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
     const float ra = mr.x, rb = mr.y, pa = mp.x, pb = mp.y;
     float FA[3], FB[3];
     sc_force(p, d, m, ra, rb, pa, pb, FA, FB);
+    if (p.fibm) ibm_force(p, n, ra, rb, FA, FB);
     float ja[3] = {0.f, 0.f, 0.f}, jb[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {  // opposite pairs (i, i+1)
@@ -530,13 +547,19 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
         ua[a] = up + sfa * FA[a];
         ub[a] = up + sfb * FB[a];
     }
-    if (p.out) {
+    if (p.out || p.uphys) {
         const float rt = ra + rb;
-        p.out[n] = ra;
-        p.out[p.N + n] = rb;
-        p.out[2 * p.N + n] = (ja[0] + jb[0] + 0.5f * (FA[0] + FB[0])) / rt;
-        p.out[3 * p.N + n] = (ja[1] + jb[1] + 0.5f * (FA[1] + FB[1])) / rt;
-        p.out[4 * p.N + n] = (ja[2] + jb[2] + 0.5f * (FA[2] + FB[2])) / rt;
+        const float u[3] = {(ja[0] + jb[0] + 0.5f * (FA[0] + FB[0])) / rt,
+                            (ja[1] + jb[1] + 0.5f * (FA[1] + FB[1])) / rt,
+                            (ja[2] + jb[2] + 0.5f * (FA[2] + FB[2])) / rt};
+        if (p.out) {
+            p.out[n] = ra;
+            p.out[p.N + n] = rb;
+            p.out[2 * p.N + n] = u[0];
+            p.out[3 * p.N + n] = u[1];
+            p.out[4 * p.N + n] = u[2];
+        }
+        if (p.uphys) p.uphys[n] = make_float4(u[0], u[1], u[2], 0.f);
     }
     if (!(ra + rb < 1e30f)) atomicOr(p.status, ST_NAN);
     store_post<T, DRY, false>(p, n, ra, rb, ua, ub, fa, fb);
@@ -549,7 +572,8 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
 // and u^{c,eq} = u' + F^c / rho^c (the velocity shift with tau = 1).
 template <typename T, bool DRY>
 __device__ __forceinline__ void collide_eq_finish(const LBParams &p, int n, float ra, float rb, const float4 J4,
-                                                  const float (&FA)[3], const float (&FB)[3]) {
+                                                  float (&FA)[3], float (&FB)[3]) {
+    if (p.fibm) ibm_force(p, n, ra, rb, FA, FB);
     const float J[3] = {J4.x, J4.y, J4.z};
     const float rt = ra + rb, iden = 1.0f / rt, ia = 1.0f / ra, ib = 1.0f / rb;
     float ua[3], ub[3];
@@ -559,12 +583,17 @@ __device__ __forceinline__ void collide_eq_finish(const LBParams &p, int n, floa
         ua[a] = up + ia * FA[a];
         ub[a] = up + ib * FB[a];
     }
-    if (p.out) {
-        p.out[n] = ra;
-        p.out[p.N + n] = rb;
-        p.out[2 * p.N + n] = (J[0] + 0.5f * (FA[0] + FB[0])) / rt;
-        p.out[3 * p.N + n] = (J[1] + 0.5f * (FA[1] + FB[1])) / rt;
-        p.out[4 * p.N + n] = (J[2] + 0.5f * (FA[2] + FB[2])) / rt;
+    if (p.out || p.uphys) {
+        const float u[3] = {(J[0] + 0.5f * (FA[0] + FB[0])) / rt, (J[1] + 0.5f * (FA[1] + FB[1])) / rt,
+                            (J[2] + 0.5f * (FA[2] + FB[2])) / rt};
+        if (p.out) {
+            p.out[n] = ra;
+            p.out[p.N + n] = rb;
+            p.out[2 * p.N + n] = u[0];
+            p.out[3 * p.N + n] = u[1];
+            p.out[4 * p.N + n] = u[2];
+        }
+        if (p.uphys) p.uphys[n] = make_float4(u[0], u[1], u[2], 0.f);
     }
     if (!(ra + rb < 1e30f)) atomicOr(p.status, ST_NAN);
     float unused[Q];  // the equilibria need no pulled populations

@@ -440,6 +440,62 @@ __device__ __forceinline__ void mem_bending_body(const MemParams &p, int bid) {
 //    previous cut structure (each entry of the previous list names one marked
 //    link: its mask word and crossed element are reset) before the cut links
 //    of the new positions are marked.
+// ------------------------------------------------ diffuse-interface coupling
+// Peskin's 4-point kernel (Peskin, "The immersed boundary method", Acta
+// Numerica 2002): phi(r) = (3 - 2r + sqrt(1 + 4r - 4r^2)) / 8 on [0, 1] and
+// (5 - 2r - sqrt(-7 + 12r - 4r^2)) / 8 on [1, 2], which equals 1/2 - phi(2 - r)
+// there.  A coordinate with integer part f and fraction t in [0, 1] reaches
+// the nodes f-1 .. f+2 at distances 1+t, t, 1-t, 2-t, so its four weights are
+// 1/2 - phi(1-t), phi(t), phi(1-t), 1/2 - phi(t): two square roots, and the
+// weights sum to one.
+__device__ __forceinline__ float peskin_inner(float r) {
+    return 0.125f * (3.f - 2.f * r + sqrtf(1.f + 4.f * r * (1.f - r)));
+}
+// first node b (= floor(x) - 1) and weights of one coordinate x = h + l
+__device__ __forceinline__ void ibm_axis(float h, float l, int &b, float (&w)[4]) {
+    float fl = floorf(h);
+    float t = (h - fl) + l;  // h - fl is exact; |l| <= ulp(h) / 2
+    if (t < 0.f) { t += 1.f; fl -= 1.f; }
+    else if (t >= 1.f) { t -= 1.f; fl += 1.f; }
+    // a non-finite position (reported by the cut-link kernel) still gives
+    // in-range nodes: fmaxf drops a NaN, the clamp keeps the int conversion defined
+    b = (int)fminf(fmaxf(fl, -1e8f), 1e8f) - 1;
+    const float p0 = peskin_inner(t), p1 = peskin_inner(1.f - t);
+    w[0] = 0.5f - p1; w[1] = p0; w[2] = p1; w[3] = 0.5f - p0;
+}
+// The 4 x 4 x 4 nodes around x (periodic; substrate nodes skipped) with their
+// weights: f(lattice index, weight) for each
+template <class Fn>
+__device__ __forceinline__ void ibm_stencil(const MemParams &p, const pf &x, Fn f) {
+    int b[3];
+    float w[3][4];
+    ibm_axis(x.h.x, x.l.x, b[0], w[0]);
+    ibm_axis(x.h.y, x.l.y, b[1], w[1]);
+    ibm_axis(x.h.z, x.l.z, b[2], w[2]);
+#pragma unroll
+    for (int kz = 0; kz < 4; ++kz) {
+        const int z = wrapi(b[2] + kz, p.nz);
+        if (p.wall && z == 0) continue;
+#pragma unroll
+        for (int ky = 0; ky < 4; ++ky) {
+            const long long row = ((long long)z * p.ny + wrapi(b[1] + ky, p.ny)) * p.nx;
+#pragma unroll
+            for (int kx = 0; kx < 4; ++kx) f(row + wrapi(b[0] + kx, p.nx), (w[0][kx] * w[1][ky]) * w[2][kz]);
+        }
+    }
+}
+// the force F of a node at x spread to the lattice (fixed point, so that the
+// sums do not depend on the order of the atomics)
+__device__ __forceinline__ void ibm_spread_node(const MemParams &p, const pf &x, f3 F) {
+    long long *fb = p.fibm;
+    const long long N = p.N;
+    ibm_stencil(p, x, [&](long long n, float w) {
+        ft_add(fb + n, F.x * w);
+        ft_add(fb + N + n, F.y * w);
+        ft_add(fb + 2 * N + n, F.z * w);
+    });
+}
+
 __device__ __forceinline__ void mem_update_body(const MemParams &p, const ClearParams &cl, int bid) {
     if (cl.count_next && bid == 0 && threadIdx.x == 0) *cl.count_next = 0;
     const int node_blocks = (p.nnodes + MV - 1) / MV;
@@ -465,7 +521,9 @@ __device__ __forceinline__ void mem_update_body(const MemParams &p, const ClearP
         const float pre = (float)A[A_PRE];
         node_forces(p, cp, cap, vv, pre, x, Fc, Ft);
         st3(p.Fcpl + 3 * vv, Fc);
-        if (cp.mode == 0) {
+        if (p.fibm) {
+            ibm_spread_node(p, x, Ft);  // the node moves after the lattice update (k_ibm_move)
+        } else if (cp.mode == 0) {
             // Eq. 9 with dt = 1 (v = F/m), or with CF_INERTIAL v += F/m
             f3 vel = (1.f / cp.mass) * Ft;
             if (p.inertial) vel = vel + ld3(p.V, vv);
@@ -517,6 +575,31 @@ __global__ void __launch_bounds__(MV) k_mem_update(const MemParams p, const Clea
     mem_update_body(p, cl, blockIdx.x);
 }
 __global__ void __launch_bounds__(MV) k_mem_frozen(const MemParams p) { mem_frozen_body(p, blockIdx.x); }
+
+// Diffuse-interface coupling: each free node moves with the fluid velocity of
+// this step interpolated at its position with the spreading kernel (substrate
+// nodes carry zero velocity); fixed nodes stay.
+__global__ void __launch_bounds__(MV) k_ibm_move(const MemParams p) {
+    const int v = blockIdx.x * MV + threadIdx.x;
+    if (v >= p.nnodes) return;
+    const pf x = ldp(p.Xh, p.Xl, v);
+    f3 u{0.f, 0.f, 0.f};
+    if (p.caps[p.node_cap[v]].mode == 0) {
+        const float4 *up = p.uphys;
+        ibm_stencil(p, x, [&](long long n, float w) {
+            const float4 q = __ldg(up + n);
+            u = u + w * f3{q.x, q.y, q.z};
+        });
+    }
+    st3(p.V + 3 * v, u);
+    st_pos(p.Xnh, p.Xnl, v, x, u);
+}
+
+cudaError_t launch_ibm_move(const MemParams &p, cudaStream_t s, int *nl) {
+    k_ibm_move<<<(unsigned)((p.nnodes + MV - 1) / MV), MV, 0, s>>>(p);
+    *nl += 1;
+    return cudaGetLastError();
+}
 
 __global__ void __launch_bounds__(MT) k_mem_reset_b(const __grid_constant__ SparseTab<MemParams> t) {
     mem_reset_body(t.p[blockIdx.x], 0);

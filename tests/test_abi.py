@@ -72,7 +72,7 @@ def test_host_side_argument_checks_without_a_gpu():
     cases = [(desc(nx=2), "dimensions"), (desc(nz=0), "dimensions"),
              (desc(nx=512, ny=512, nz=256), "too large"), (desc(tau=(0.5, 1.0)), "tau"),
              (desc(tau=(1.0, float("nan"))), "tau"), (desc(precision=7), "precision"),
-             (desc(flags=16), "unknown flag")]
+             (desc(flags=32), "unknown flag"), (desc(flags=16 | 1), "CF_INERTIAL")]
     for d, why in cases:
         h = C.c_void_p()
         rc = L.cf_create(C.byref(d), C.byref(h))

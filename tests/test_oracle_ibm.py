@@ -1,8 +1,7 @@
-"""Pins of the oracle's diffuse-interface (immersed-boundary) coupling
-variant (the alternative to the cut-link bounce-back named for the
-many-capsule studies): Peskin's 4-point kernel, spreading and interpolation,
-and one coupled step against fields derived by hand from the pinned membrane
-forces."""
+"""Pins of the oracle's diffuse-interface (immersed-boundary) coupling, a
+variant of the cut-link bounce-back coupling that is not part of the paper:
+Peskin's 4-point kernel, spreading and interpolation, and one coupled step
+against fields derived by hand from the pinned membrane forces."""
 import numpy as np
 import pytest
 
