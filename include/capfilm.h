@@ -285,8 +285,9 @@ cf_status cf_cuts(cf_ctx *ctx, uint32_t *mask, int *tri, uint8_t *inside);
  * CUDA events on the context stream; ms[0..3] receive the mean device time per
  * step of the two lattice passes, of the membrane phase, of the cut-link
  * rebuild and of the bounce-record preparation (milliseconds).  With CF_IBM,
- * ms[1] is the interpolation and move of the nodes and ms[3] the membrane
- * forces with their spreading.  Synchronises.  For measurement; the
+ * ms[0] covers the lattice passes together with the membrane forces and their
+ * spreading (which run beside the density pass), ms[1] the interpolation and
+ * move of the nodes, and ms[2] = ms[3] = 0.  Synchronises.  For measurement; the
  * populations advance exactly as with cf_step. */
 cf_status cf_time_phases(cf_ctx *ctx, long long n, double ms[4]);
 

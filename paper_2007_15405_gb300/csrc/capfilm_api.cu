@@ -89,10 +89,12 @@ struct cf_ctx {
     float4 *J = nullptr;                   // total momentum of the current step (tau = 1)
     uint32_t *mask = nullptr;
     // diffuse-interface coupling (CF_IBM): spread membrane force [3][N] (fixed
-    // point), fluid velocity [N], and the all-zero cut bits the lattice reads
+    // point), fluid velocity [N] followed by the block flags (ibm_flags), and
+    // the all-zero cut bits the lattice reads
     long long *fibm = nullptr;
     float4 *uphys = nullptr;
     uint32_t *mask0 = nullptr;
+    bool cuts_stale = false;  // CF_IBM: the cut links lag the positions until a readout needs them
     int *tri = nullptr;
     float2 *rec = nullptr;        // [N][18] bounce records (A, B) by arriving direction
     uint8_t *inside = nullptr;
@@ -154,6 +156,9 @@ struct cf_ctx {
 };
 
 namespace {
+
+// bytes of the block flags of the diffuse-interface coupling (one per 32 nodes)
+size_t ibm_flag_bytes(long long N) { return (size_t)((N + 31) / 32 + 15) / 16 * 16; }
 
 void *dalloc(cf_ctx *c, size_t bytes, bool membrane = false) {
     void *p = nullptr;
@@ -399,13 +404,14 @@ cf_status enqueue_post(cf_ctx *c, int *nl, cudaEvent_t ev2 = nullptr) {
 
 // One step with the diffuse-interface coupling (CF_IBM):
 //
-//   stream   ------------------join-> update: spread (+ cut reset) -> density -> collide -> move -> cut links
-//   stream2  \-> memsets -> elements -> nodes -> bending -/
+//   stream   -------------------------------------> density --join-> collide -> move
+//   stream2  \-> memsets -> elements -> nodes -> bending -> update: spread -/
 //
-// The membrane forces of the current positions are spread before the
-// collision that applies them; the nodes then move with this step's fluid
-// velocity.  The lattice sees no cut link; the cut links of the new positions
-// only give the interior flags of the readouts.
+// The membrane forces of the current positions are spread, beside the
+// density pass, before the collision that applies them; the nodes then move
+// with this step's fluid velocity.  The lattice sees no cut link: the cut
+// links only give the interior flags of the readouts, which rebuild them
+// (refresh_cuts) for the positions of the moment.
 cf_status enqueue_step_ibm(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev) {
     if (ev) CF_CUDA(cudaEventRecord(ev[4], c->stream));
     const bool mem = c->nnodes > 0;
@@ -417,18 +423,18 @@ cf_status enqueue_step_ibm(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev) {
         CF_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(double) * A_NACC * nc, c->stream2));
         CF_CUDA(cudaMemsetAsync(bb, 0x7f, sizeof(int) * 3 * nc, c->stream2));
         CF_CUDA(cudaMemsetAsync(bb + 3 * nc, 0x80, sizeof(int) * 3 * nc, c->stream2));
+        CF_CUDA(cudaMemsetAsync(ibm_flags(c->uphys, c->N), 0, ibm_flag_bytes(c->N), c->stream2));
         if (c->nbr) {
             MemParams q = mem_params(c);
             q.nbr = nullptr;
             CF_CUDA(launch_contact_partners(q, c->nbr, c->nbr_cnt, c->stream2, nl));
         }
         CF_CUDA(launch_membrane_forces(mem_params(c), c->stream2, nl));
+        CF_CUDA(launch_membrane_update(mem_params(c), ClearParams{}, false, c->stream2, nl));
         CF_CUDA(cudaEventRecord(c->ev_join, c->stream2));
-        CF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
-        CF_CUDA(launch_membrane_update(mem_params(c), clear_params(c, 304), false, c->stream, nl));
     }
     if (ev) CF_CUDA(cudaEventRecord(ev[0], c->stream));
-    CF_CUDA(launch_lb_step(lb_params(c, with_out), c->d.precision, c->stream));
+    CF_CUDA(launch_lb_step(lb_params(c, with_out), c->d.precision, c->stream, mem ? c->ev_join : nullptr));
     *nl += 2;
     c->fpar = 1 - c->fpar;
     if (ev) CF_CUDA(cudaEventRecord(ev[1], c->stream));
@@ -437,14 +443,27 @@ cf_status enqueue_step_ibm(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev) {
         c->xpar = 1 - c->xpar;
     }
     if (ev) CF_CUDA(cudaEventRecord(ev[2], c->stream));
-    if (mem) {
-        if (!c->all_fixed) {
-            cf_status s = enqueue_cuts(c, c->X[c->xpar], nl, true);
-            if (s != CF_OK) return s;
-        }
-        c->ftpar = 1 - c->ftpar;  // the exchange accumulators stay zero: no link is cut for the fluid
-    }
+    if (mem && !c->all_fixed) c->cuts_stale = true;
     if (ev) CF_CUDA(cudaEventRecord(ev[3], c->stream));
+    return CF_OK;
+}
+
+// Cut links of the current positions, where the steps have left them behind
+// (CF_IBM): reset of the old structure, then the cut-link kernel.
+cf_status refresh_cuts(cf_ctx *c) {
+    if (!c->cuts_stale) return CF_OK;
+    c->cuts_stale = false;
+    int nl = 0;
+    CF_CUDA(launch_cut_clear(clear_params(c, 304), c->stream, &nl));
+    return enqueue_cuts(c, c->X[c->xpar], &nl, true);
+}
+
+// interior flags of the current positions (readouts)
+cf_status inside_flags(cf_ctx *c) {
+    if (!c->nfaces) return CF_OK;
+    cf_status s = refresh_cuts(c);
+    if (s != CF_OK) return s;
+    CF_CUDA(launch_inside(c->mask, c->inside, c->d.nx, c->d.ny, c->d.nz, c->stream));
     return CF_OK;
 }
 
@@ -768,7 +787,7 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     const bool ibm = (desc->flags & CF_IBM) != 0;
     if (ibm) {
         c->fibm = (long long *)dalloc(c, sizeof(long long) * 3 * N);
-        c->uphys = (float4 *)dalloc(c, sizeof(float4) * N);
+        c->uphys = (float4 *)dalloc(c, sizeof(float4) * N + ibm_flag_bytes(N));
         c->mask0 = (uint32_t *)dalloc(c, sizeof(uint32_t) * N);
     }
     if ((ibm && (!c->fibm || !c->uphys || !c->mask0)) || !c->f[0] || !c->f[1] || !c->f0[0] || !c->f0[1] || !c->step_ctr || !c->out || !c->rho[0] || !c->rho[1] || !c->psi || (tau1 && !c->J) || !c->mask || !c->tri || !c->inside ||
@@ -792,7 +811,7 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
     cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream);
     if (ibm) {
         cudaMemsetAsync(c->fibm, 0, sizeof(long long) * 3 * N, c->stream);
-        cudaMemsetAsync(c->uphys, 0, sizeof(float4) * N, c->stream);
+        cudaMemsetAsync(c->uphys, 0, sizeof(float4) * N + ibm_flag_bytes(N), c->stream);
         cudaMemsetAsync(c->mask0, 0, sizeof(uint32_t) * N, c->stream);
     }
     cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -919,7 +938,7 @@ cf_status cf_set_film(cf_ctx *c, double h_top, double rmaj, double rmin, double 
         CF_CUDA(cudaMemcpyAsync(c->jit, jitter, sizeof(double) * 2 * N, cudaMemcpyHostToDevice, c->stream));
         djit = c->jit;
     }
-    if (c->nfaces) CF_CUDA(launch_inside(c->mask, c->inside, c->d.nx, c->d.ny, c->d.nz, c->stream));
+    if (cf_status si = inside_flags(c); si != CF_OK) return si;
     CF_CUDA(launch_init_film(c->f[c->fpar], c->f0[c->fpar], c->d.precision, c->rho[c->fpar], N, c->d.nx, c->d.ny, c->d.nz, c->d.wall, (float)h_top,
                              (float)rmaj, (float)rmin, (float)rmix, djit, c->inside, c->stream));
     c->film_set = true;
@@ -972,7 +991,7 @@ cf_status warm_scratch(cf_ctx *c) {
 cf_status cf_warm_features(cf_ctx *c, double h_top, double kS, float *x, float *mask) {
     if (!c || !x) return fail(CF_EINVAL, "null argument");
     if (!(kS > 0.0)) return fail(CF_EINVAL, "kS must be positive");
-    if (c->nfaces) CF_CUDA(launch_inside(c->mask, c->inside, c->d.nx, c->d.ny, c->d.nz, c->stream));
+    if (cf_status si = inside_flags(c); si != CF_OK) return si;
     const WarmGeom g = warm_geom(c, h_top, 0.0, 0.0, 0.0);
     CF_CUDA(launch_warm_features(g, c->inside, (float)(std::log10(kS) + 2.0), x, mask, c->stream));
     return sync_ok(c);
@@ -983,7 +1002,7 @@ cf_status cf_warm_apply(cf_ctx *c, double h_top, double rmaj, double rmin, doubl
     if (!(rmaj > rmin)) return fail(CF_EINVAL, "rho_maj must exceed rho_min");
     cf_status s = warm_scratch(c);
     if (s != CF_OK) return s;
-    if (c->nfaces) CF_CUDA(launch_inside(c->mask, c->inside, c->d.nx, c->d.ny, c->d.nz, c->stream));
+    if (cf_status si = inside_flags(c); si != CF_OK) return si;
     const WarmGeom g = warm_geom(c, h_top, rmaj, rmin, rmix);
     CF_CUDA(launch_warm_densities(g, c->inside, d, c->jit, c->warm_part, c->stream));
     CF_CUDA(launch_init_dens(c->f[c->fpar], c->f0[c->fpar], c->d.precision, c->rho[c->fpar], c->N, c->d.nx,
@@ -996,7 +1015,7 @@ cf_status cf_warm_target(cf_ctx *c, double h_top, double rmaj, double rmin, doub
     if (!c || !t) return fail(CF_EINVAL, "null argument");
     if (!(rmaj > rmin)) return fail(CF_EINVAL, "rho_maj must exceed rho_min");
     if (!c->film_set) return fail(CF_ESTATE, "no fields before the first step");
-    if (c->nfaces) CF_CUDA(launch_inside(c->mask, c->inside, c->d.nx, c->d.ny, c->d.nz, c->stream));
+    if (cf_status si = inside_flags(c); si != CF_OK) return si;
     const WarmGeom g = warm_geom(c, h_top, rmaj, rmin, rmix);
     CF_CUDA(launch_warm_target(g, c->inside, c->out, t, c->stream));
     return sync_ok(c);
@@ -1230,7 +1249,7 @@ cf_status cf_total_mass(cf_ctx *c, double m[2]) {
 cf_status cf_meniscus_field(cf_ctx *c, double *h) {
     if (!c || !h) return fail(CF_EINVAL, "null argument");
     const int nxy = c->d.nx * c->d.ny;
-    CF_CUDA(launch_inside(c->mask, c->inside, c->d.nx, c->d.ny, c->d.nz, c->stream));
+    if (cf_status si = inside_flags(c); si != CF_OK) return si;
     CF_CUDA(launch_meniscus(c->out, c->inside, c->hscratch, c->d.nx, c->d.ny, c->d.nz, c->d.wall, c->stream));
     std::vector<float> hf(nxy);
     CF_CUDA(cudaMemcpyAsync(hf.data(), c->hscratch, sizeof(float) * nxy, cudaMemcpyDeviceToHost, c->stream));
@@ -1260,7 +1279,7 @@ cf_status cf_meniscus_profile(cf_ctx *c, int id, double dr, double *r, double *z
         c->allocations.pop_back();  // freed explicitly
         c->pcap = nr + 2;
     }
-    CF_CUDA(launch_inside(c->mask, c->inside, c->d.nx, c->d.ny, c->d.nz, c->stream));
+    if (cf_status si = inside_flags(c); si != CF_OK) return si;
     CF_CUDA(launch_meniscus(c->out, c->inside, c->hscratch, c->d.nx, c->d.ny, c->d.nz, c->d.wall, c->stream));
     CF_CUDA(launch_meniscus_profile(c->hscratch, c->d.nx, c->d.ny, c->acc, c->capdev, nc, id, dr, (int)nr,
                                     c->pscratch, c->stream));
@@ -1460,7 +1479,8 @@ std::vector<CkptPart> ckpt_parts(cf_ctx *c, int count) {
 cf_status cf_save(cf_ctx *c, const char *path) {
     if (!c || !path) return fail(CF_EINVAL, "null argument");
     if (!c->film_set) return fail(CF_ESTATE, "nothing to save before cf_set_film");
-    cf_status s = sync_ok(c);
+    cf_status s = refresh_cuts(c);  // the checkpoint holds the cut links of its positions
+    if (s == CF_OK) s = sync_ok(c);
     if (s != CF_OK) return s;
     CkptHeader h{};
     std::memcpy(h.magic, "CFCKPT01", 8);
@@ -1542,6 +1562,7 @@ cf_status cf_meniscus_height(cf_ctx *c, int id, double *Z) {
 
 cf_status cf_cuts(cf_ctx *c, uint32_t *mask, int *tri, uint8_t *inside) {
     if (!c) return fail(CF_EINVAL, "null context");
+    if (cf_status si = refresh_cuts(c); si != CF_OK) return si;
     const long long N = c->N;
     if (mask) CF_CUDA(cudaMemcpyAsync(mask, c->mask, sizeof(uint32_t) * N, cudaMemcpyDeviceToHost, c->stream));
     if (tri) CF_CUDA(cudaMemcpyAsync(tri, c->tri, sizeof(int) * 18 * N, cudaMemcpyDeviceToHost, c->stream));

@@ -119,9 +119,10 @@ struct LBParams {
     const int *__restrict__ tri;        // crossed element per node and link [N*18]
     // diffuse-interface coupling (CF_IBM; null otherwise): the membrane force
     // spread to the lattice (ft_add), read and cleared by the collide pass,
-    // which also writes the fluid velocity the nodes move with
+    // which also writes the fluid velocity the nodes move with; both only in
+    // the blocks of 32 nodes (n / 32) that the spreading flagged
     long long *__restrict__ fibm;       // [3][N]
-    float4 *__restrict__ uphys;         // [N] (ux, uy, uz, 0)
+    float4 *__restrict__ uphys;         // [N] (ux, uy, uz, 0), then the flags: ibm_flags(uphys, N)
     long long *__restrict__ FT;         // element momentum exchange accumulators [3*nfaces] (ft_add)
     const float2 *__restrict__ rec;     // [N][18] bounced (A, B) populations by arriving direction - 1
     const float *__restrict__ wet_el;   // [nfaces] wetting offset of each element's capsule (null: all 0)
@@ -204,9 +205,14 @@ struct MemParams {
     // spreads each node's force into fibm [3][N] instead of moving it, and the
     // move kernel steps the nodes with uphys [N] interpolated at their positions
     long long *fibm;
-    const float4 *uphys;
+    float4 *uphys;
     long long N;
 };
+// block flags of the diffuse-interface coupling: byte n / 32 is set when the
+// spreading reached node n in this step; they follow the [N] velocities
+__host__ __device__ inline uint8_t *ibm_flags(float4 *uphys, long long N) {
+    return reinterpret_cast<uint8_t *>(uphys + N);
+}
 constexpr int CF_NBR_MAX = 48;
 constexpr int CF_NBR_MIN_CAPS = 16;  // fewer capsules: no lists, the loop checks them all
 
@@ -288,7 +294,8 @@ namespace cf {
 void set_last_error(const char *msg);  // text returned by cf_last_error() on this thread
 // most blocks a density pass of an nx x ny x nz lattice launches
 size_t density_blocks_max(int nx, int ny, int nz);
-cudaError_t launch_lb_step(const LBParams &p, int prec, cudaStream_t s);
+// before_collide (optional): an event the collide pass waits for as well
+cudaError_t launch_lb_step(const LBParams &p, int prec, cudaStream_t s, cudaEvent_t before_collide = nullptr);
 
 // Batched lattice passes: many independent lattices in one persistent launch
 // per pass.  The per-lattice parameters travel by value in the launch (one
@@ -356,6 +363,8 @@ cudaError_t launch_cuts(const CutParams &p, cudaStream_t s, int *nlaunch);
 cudaError_t launch_prep(const PrepParams &p, cudaStream_t s, int *nlaunch);
 // diffuse-interface coupling: nodes moved with the interpolated fluid velocity
 cudaError_t launch_ibm_move(const MemParams &p, cudaStream_t s, int *nl);
+// reset of a cut structure (as the node update's extra blocks do)
+cudaError_t launch_cut_clear(const ClearParams &cl, cudaStream_t s, int *nl);
 // batched forms (one launch per kernel for all lattices of the tables); tv:
 // node-kernel blocks (32 nodes), tf: element-kernel blocks (64 elements), cut
 // links: cut_blocks(nfaces, lanes) blocks with lanes = cut_lanes(the launch's

@@ -410,6 +410,10 @@ __device__ __forceinline__ void sc_force(const LBParams &p, const Deltas &d, uin
 // Diffuse-interface coupling (CF_IBM): the membrane force spread to node n
 // acts on the fluid as a body force, shared by the components in proportion
 // to their densities.  The accumulator is cleared for the next spreading.
+// Only in blocks the spreading reached (elsewhere the accumulator is zero).
+__device__ __forceinline__ bool ibm_reached(const LBParams &p, int n) {
+    return p.fibm && __ldg(ibm_flags(p.uphys, p.N) + (n >> 5));
+}
 __device__ __forceinline__ void ibm_force(const LBParams &p, int n, float ra, float rb, float (&FA)[3],
                                           float (&FB)[3]) {
     long long *f = p.fibm + n;
@@ -529,7 +533,8 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
     const float ra = mr.x, rb = mr.y, pa = mp.x, pb = mp.y;
     float FA[3], FB[3];
     sc_force(p, d, m, ra, rb, pa, pb, FA, FB);
-    if (p.fibm) ibm_force(p, n, ra, rb, FA, FB);
+    const bool ibm = ibm_reached(p, n);
+    if (ibm) ibm_force(p, n, ra, rb, FA, FB);
     float ja[3] = {0.f, 0.f, 0.f}, jb[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {  // opposite pairs (i, i+1)
@@ -547,7 +552,7 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
         ua[a] = up + sfa * FA[a];
         ub[a] = up + sfb * FB[a];
     }
-    if (p.out || p.uphys) {
+    if (p.out || ibm) {
         const float rt = ra + rb;
         const float u[3] = {(ja[0] + jb[0] + 0.5f * (FA[0] + FB[0])) / rt,
                             (ja[1] + jb[1] + 0.5f * (FA[1] + FB[1])) / rt,
@@ -559,7 +564,7 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
             p.out[3 * p.N + n] = u[1];
             p.out[4 * p.N + n] = u[2];
         }
-        if (p.uphys) p.uphys[n] = make_float4(u[0], u[1], u[2], 0.f);
+        if (ibm) p.uphys[n] = make_float4(u[0], u[1], u[2], 0.f);
     }
     if (!(ra + rb < 1e30f)) atomicOr(p.status, ST_NAN);
     store_post<T, DRY, false>(p, n, ra, rb, ua, ub, fa, fb);
@@ -573,7 +578,8 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
 template <typename T, bool DRY>
 __device__ __forceinline__ void collide_eq_finish(const LBParams &p, int n, float ra, float rb, const float4 J4,
                                                   float (&FA)[3], float (&FB)[3]) {
-    if (p.fibm) ibm_force(p, n, ra, rb, FA, FB);
+    const bool ibm = ibm_reached(p, n);
+    if (ibm) ibm_force(p, n, ra, rb, FA, FB);
     const float J[3] = {J4.x, J4.y, J4.z};
     const float rt = ra + rb, iden = 1.0f / rt, ia = 1.0f / ra, ib = 1.0f / rb;
     float ua[3], ub[3];
@@ -583,7 +589,7 @@ __device__ __forceinline__ void collide_eq_finish(const LBParams &p, int n, floa
         ua[a] = up + ia * FA[a];
         ub[a] = up + ib * FB[a];
     }
-    if (p.out || p.uphys) {
+    if (p.out || ibm) {
         const float u[3] = {(J[0] + 0.5f * (FA[0] + FB[0])) / rt, (J[1] + 0.5f * (FA[1] + FB[1])) / rt,
                             (J[2] + 0.5f * (FA[2] + FB[2])) / rt};
         if (p.out) {
@@ -593,7 +599,7 @@ __device__ __forceinline__ void collide_eq_finish(const LBParams &p, int n, floa
             p.out[3 * p.N + n] = u[1];
             p.out[4 * p.N + n] = u[2];
         }
-        if (p.uphys) p.uphys[n] = make_float4(u[0], u[1], u[2], 0.f);
+        if (ibm) p.uphys[n] = make_float4(u[0], u[1], u[2], 0.f);
     }
     if (!(ra + rb < 1e30f)) atomicOr(p.status, ST_NAN);
     float unused[Q];  // the equilibria need no pulled populations
@@ -747,39 +753,51 @@ size_t density_blocks_max(int nx, int ny, int nz) {
 }
 
 namespace {
+// before_collide (optional): the collide pass also waits for this event (a
+// plain launch then, the density pass stays programmatic)
 template <typename T, bool DRY>
-void lb_passes(const LBParams &p, dim3 grid, dim3 block, cudaStream_t s, bool eq) {
+void lb_passes(const LBParams &p, dim3 grid, dim3 block, cudaStream_t s, bool eq, cudaEvent_t before_collide) {
     if (eq) {
         launch_pdl(k_density<T, DRY, true>, grid, block, s, p);
 #if CF_PSI_RING
         const int zr = std::max(1, p.zring);
         const dim3 gc(grid.x, grid.y, (unsigned)((p.zhi - p.zlo + zr - 1) / zr));
-        launch_pdl(k_collide_eq<T, DRY>, gc, block, s, p);
 #else
-        launch_pdl(k_collide_eq<T, DRY>, grid, block, s, p);
+        const dim3 gc = grid;
 #endif
+        if (before_collide) {
+            cudaStreamWaitEvent(s, before_collide, 0);
+            k_collide_eq<T, DRY><<<gc, block, 0, s>>>(p);
+        } else {
+            launch_pdl(k_collide_eq<T, DRY>, gc, block, s, p);
+        }
     } else {
         launch_pdl(k_density<T, DRY>, grid, block, s, p);
-        launch_pdl(k_collide<T, DRY>, grid, block, s, p);
+        if (before_collide) {
+            cudaStreamWaitEvent(s, before_collide, 0);
+            k_collide<T, DRY><<<grid, block, 0, s>>>(p);
+        } else {
+            launch_pdl(k_collide<T, DRY>, grid, block, s, p);
+        }
     }
 }
 template <typename T>
-void lb_passes(const LBParams &p, dim3 grid, dim3 block, cudaStream_t s, bool dry, bool eq) {
-    if (dry) lb_passes<T, true>(p, grid, block, s, eq);
-    else lb_passes<T, false>(p, grid, block, s, eq);
+void lb_passes(const LBParams &p, dim3 grid, dim3 block, cudaStream_t s, bool dry, bool eq, cudaEvent_t ev) {
+    if (dry) lb_passes<T, true>(p, grid, block, s, eq, ev);
+    else lb_passes<T, false>(p, grid, block, s, eq, ev);
 }
 }  // namespace
 
-cudaError_t launch_lb_step(const LBParams &p, int prec, cudaStream_t s) {
+cudaError_t launch_lb_step(const LBParams &p, int prec, cudaStream_t s, cudaEvent_t before_collide) {
     const int nzf = p.zhi - p.zlo;
     const int gz = p.zchunk > 0 ? (nzf + p.zchunk - 1) / p.zchunk : nzf;
     dim3 grid((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, gz), block(BX, BY);
     const bool dry = p.dry_dm > 0.0;
     // tau = 1 for both components: the collide pass takes the density pass's momentum
     const bool eq = p.J != nullptr && p.tau[0] == 1.f && p.tau[1] == 1.f;
-    if (prec == P_F16) lb_passes<__half>(p, grid, block, s, dry, eq);
-    else if (prec == P_BF16) lb_passes<__nv_bfloat16>(p, grid, block, s, dry, eq);
-    else lb_passes<float>(p, grid, block, s, dry, eq);
+    if (prec == P_F16) lb_passes<__half>(p, grid, block, s, dry, eq, before_collide);
+    else if (prec == P_BF16) lb_passes<__nv_bfloat16>(p, grid, block, s, dry, eq, before_collide);
+    else lb_passes<float>(p, grid, block, s, dry, eq, before_collide);
     return cudaGetLastError();
 }
 

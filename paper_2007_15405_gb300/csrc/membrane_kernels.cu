@@ -440,6 +440,17 @@ __device__ __forceinline__ void mem_bending_body(const MemParams &p, int bid) {
 //    previous cut structure (each entry of the previous list names one marked
 //    link: its mask word and crossed element are reset) before the cut links
 //    of the new positions are marked.
+// reset of the cut structure of list cl.list: block bid of cl.blocks
+__device__ __forceinline__ void cut_clear_body(const ClearParams &cl, int bid) {
+    const int cnt = min(*cl.count, cl.capacity);
+    for (int i = bid * MV + threadIdx.x; i < cnt; i += cl.blocks * MV) {
+        const int2 e = cl.list[i];
+        const long long n = (long long)((unsigned)e.x >> 5);
+        cl.mask[n] = 0u;
+        cl.tri[n * 18 + (e.x & 31)] = 0x7fffffff;
+    }
+}
+
 // ------------------------------------------------ diffuse-interface coupling
 // Peskin's 4-point kernel (Peskin, "The immersed boundary method", Acta
 // Numerica 2002): phi(r) = (3 - 2r + sqrt(1 + 4r - 4r^2)) / 8 on [0, 1] and
@@ -484,15 +495,18 @@ __device__ __forceinline__ void ibm_stencil(const MemParams &p, const pf &x, Fn 
         }
     }
 }
+
 // the force F of a node at x spread to the lattice (fixed point, so that the
-// sums do not depend on the order of the atomics)
+// sums do not depend on the order of the atomics), its nodes flagged
 __device__ __forceinline__ void ibm_spread_node(const MemParams &p, const pf &x, f3 F) {
     long long *fb = p.fibm;
     const long long N = p.N;
+    uint8_t *flag = ibm_flags(p.uphys, N);
     ibm_stencil(p, x, [&](long long n, float w) {
         ft_add(fb + n, F.x * w);
         ft_add(fb + N + n, F.y * w);
         ft_add(fb + 2 * N + n, F.z * w);
+        flag[n >> 5] = 1;
     });
 }
 
@@ -500,13 +514,7 @@ __device__ __forceinline__ void mem_update_body(const MemParams &p, const ClearP
     if (cl.count_next && bid == 0 && threadIdx.x == 0) *cl.count_next = 0;
     const int node_blocks = (p.nnodes + MV - 1) / MV;
     if (bid >= node_blocks) {
-        const int cnt = min(*cl.count, cl.capacity);
-        for (int i = (bid - node_blocks) * MV + threadIdx.x; i < cnt; i += cl.blocks * MV) {
-            const int2 e = cl.list[i];
-            const long long n = (long long)((unsigned)e.x >> 5);
-            cl.mask[n] = 0u;
-            cl.tri[n * 18 + (e.x & 31)] = 0x7fffffff;
-        }
+        cut_clear_body(cl, bid - node_blocks);
         return;
     }
     const int v = bid * MV + threadIdx.x;
@@ -593,6 +601,18 @@ __global__ void __launch_bounds__(MV) k_ibm_move(const MemParams p) {
     }
     st3(p.V + 3 * v, u);
     st_pos(p.Xnh, p.Xnl, v, x, u);
+}
+
+__global__ void __launch_bounds__(MV) k_cut_clear(const ClearParams cl) {
+    if (cl.count_next && blockIdx.x == 0 && threadIdx.x == 0) *cl.count_next = 0;
+    cut_clear_body(cl, blockIdx.x);
+}
+
+cudaError_t launch_cut_clear(const ClearParams &cl, cudaStream_t s, int *nl) {
+    if (cl.blocks <= 0) return cudaSuccess;
+    k_cut_clear<<<(unsigned)cl.blocks, MV, 0, s>>>(cl);
+    *nl += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ibm_move(const MemParams &p, cudaStream_t s, int *nl) {
