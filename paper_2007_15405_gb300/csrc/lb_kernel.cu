@@ -524,7 +524,9 @@ __device__ __forceinline__ void store_post(const LBParams &p, int n, float ra, f
 
 // Collision of one node for any tau: pull again, Shan-Chen force, velocity
 // shift, BGK (Eqs. 4-5), store.
-template <typename T, bool DRY = false>
+// IBM: the diffuse-interface body force may be present (single-lattice passes;
+// the batched passes compile it out)
+template <typename T, bool DRY = false, bool IBM = false>
 __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d) {
     float fa[Q], fb[Q];
     const uint32_t m = pull<T>(p, d, fa, fb);
@@ -533,7 +535,7 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
     const float ra = mr.x, rb = mr.y, pa = mp.x, pb = mp.y;
     float FA[3], FB[3];
     sc_force(p, d, m, ra, rb, pa, pb, FA, FB);
-    const bool ibm = ibm_reached(p, n);
+    const bool ibm = IBM && ibm_reached(p, n);
     if (ibm) ibm_force(p, n, ra, rb, FA, FB);
     float ja[3] = {0.f, 0.f, 0.f}, jb[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -575,10 +577,10 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
 // stored the total momentum J = sum_c sum_i f_i^c e_i, so the populations are
 // not pulled a second time.  The common velocity is u' = J / (rho_A + rho_B)
 // and u^{c,eq} = u' + F^c / rho^c (the velocity shift with tau = 1).
-template <typename T, bool DRY>
+template <typename T, bool DRY, bool IBM>
 __device__ __forceinline__ void collide_eq_finish(const LBParams &p, int n, float ra, float rb, const float4 J4,
                                                   float (&FA)[3], float (&FB)[3]) {
-    const bool ibm = ibm_reached(p, n);
+    const bool ibm = IBM && ibm_reached(p, n);
     if (ibm) ibm_force(p, n, ra, rb, FA, FB);
     const float J[3] = {J4.x, J4.y, J4.z};
     const float rt = ra + rb, iden = 1.0f / rt, ia = 1.0f / ra, ib = 1.0f / rb;
@@ -606,14 +608,14 @@ __device__ __forceinline__ void collide_eq_finish(const LBParams &p, int n, floa
     store_post<T, DRY, true>(p, n, ra, rb, ua, ub, unused, unused);
 }
 
-template <typename T, bool DRY = false>
+template <typename T, bool DRY = false, bool IBM = false>
 __device__ __forceinline__ void collide_eq_node(const LBParams &p, const Deltas &d) {
     const int n = d.n;
     const uint32_t m = __ldg(p.mask + n);
     const float2 mr = __ldg(p.rho + n), mp = __ldg(p.psi + n);
     float FA[3], FB[3];
     sc_force(p, d, m, mr.x, mr.y, mp.x, mp.y, FA, FB);
-    collide_eq_finish<T, DRY>(p, n, mr.x, mr.y, __ldg(p.J + n), FA, FB);
+    collide_eq_finish<T, DRY, IBM>(p, n, mr.x, mr.y, __ldg(p.J + n), FA, FB);
 }
 
 // ---------------------------------------------------------------------------
@@ -653,7 +655,7 @@ __device__ __forceinline__ void ring_load(const LBParams &p, PsiRing<TX, TY> &R,
     }
 }
 
-template <typename T, bool DRY, int TX, int TY>
+template <typename T, bool DRY, int TX, int TY, bool IBM = false>
 __device__ __forceinline__ void collide_eq_node_ring(const LBParams &p, const Deltas &d,
                                                      const PsiRing<TX, TY> &R, int z) {
     const int n = d.n;
@@ -681,12 +683,12 @@ __device__ __forceinline__ void collide_eq_node_ring(const LBParams &p, const De
     } else {
         sc_force(p, d, m, ra, rb, pa, pb, FA, FB);
     }
-    collide_eq_finish<T, DRY>(p, n, ra, rb, __ldg(p.J + n), FA, FB);
+    collide_eq_finish<T, DRY, IBM>(p, n, ra, rb, __ldg(p.J + n), FA, FB);
 }
 
 // planes [zb, ze) of the tile at (x0, y0); every thread of the block calls it
 // with the same arguments (the ring loads and barriers are block-wide)
-template <typename T, bool DRY, int TX, int TY>
+template <typename T, bool DRY, int TX, int TY, bool IBM = false>
 __device__ __forceinline__ void collide_eq_ring(const LBParams &p, PsiRing<TX, TY> &R, int x0, int y0, int zb,
                                                 int ze) {
     if (zb >= ze) return;
@@ -701,7 +703,7 @@ __device__ __forceinline__ void collide_eq_ring(const LBParams &p, PsiRing<TX, T
     for (int z = zb; z < ze; ++z) {
         if (z + 1 < ze) ring_load<TX, TY>(p, R, z + 2, x0, y0);  // for the next plane
         cp_async_commit();
-        if (in) collide_eq_node_ring<T, DRY, TX, TY>(p, deltas(p, x, y, z), R, z);
+        if (in) collide_eq_node_ring<T, DRY, TX, TY, IBM>(p, deltas(p, x, y, z), R, z);
         cp_async_wait_all();
         __syncthreads();
     }
@@ -714,7 +716,7 @@ __global__ void __launch_bounds__(BX *BY, Pop<T>::shifted ? CF_COLLIDE16_MINB : 
     pdl_wait();
     int x, y, z;
     if (!node_of<true>(p, x, y, z)) return;
-    for (; z < p.zhi; z += gridDim.z) collide_node<T, DRY>(p, deltas(p, x, y, z));
+    for (; z < p.zhi; z += gridDim.z) collide_node<T, DRY, true>(p, deltas(p, x, y, z));
 }
 
 // resident blocks per SM of the tau = 1 collide pass (no second pull: few registers)
@@ -740,11 +742,11 @@ __global__ void __launch_bounds__(BX *BY, CF_COLLIDE_EQ_MINB) k_collide_eq(const
     const int bx = (int)(gridDim.x - 1 - blockIdx.x), by = (int)(gridDim.y - 1 - blockIdx.y);
     const int bz = (int)(gridDim.z - 1 - blockIdx.z);
     const int zb = p.zlo + bz * p.zring, ze = min(p.zhi, zb + p.zring);
-    collide_eq_ring<T, DRY, BX, BY>(p, R, bx * BX, by * BY, zb, ze);
+    collide_eq_ring<T, DRY, BX, BY, true>(p, R, bx * BX, by * BY, zb, ze);
 #else
     int x, y, z;
     if (!node_of<true>(p, x, y, z)) return;
-    for (; z < p.zhi; z += gridDim.z) collide_eq_node<T, DRY>(p, deltas(p, x, y, z));
+    for (; z < p.zhi; z += gridDim.z) collide_eq_node<T, DRY, true>(p, deltas(p, x, y, z));
 #endif
 }
 
