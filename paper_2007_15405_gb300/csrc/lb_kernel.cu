@@ -414,16 +414,23 @@ __device__ __forceinline__ void sc_force(const LBParams &p, const Deltas &d, uin
 __device__ __forceinline__ bool ibm_reached(const LBParams &p, int n) {
     return p.fibm && __ldg(ibm_flags(p.uphys, p.N) + (n >> 5));
 }
-__device__ __forceinline__ void ibm_force(const LBParams &p, int n, float ra, float rb, float (&FA)[3],
-                                          float (&FB)[3]) {
+// The loads are issued with the node's own loads, ahead of the Shan-Chen
+// stencil's gathers (ibm_load); the force is added after it (ibm_apply).
+struct IbmForce { long long f[3]; };
+__device__ __forceinline__ IbmForce ibm_load(const LBParams &p, int n) {
+    const long long *f = p.fibm + n;
+    return {{f[0], f[p.N], f[2 * p.N]}};
+}
+__device__ __forceinline__ void ibm_apply(const LBParams &p, int n, float ra, float rb, const IbmForce &q,
+                                          float (&FA)[3], float (&FB)[3]) {
     long long *f = p.fibm + n;
-    const float F[3] = {ft_val(f[0]), ft_val(f[p.N]), ft_val(f[2 * p.N])};
     f[0] = 0; f[p.N] = 0; f[2 * p.N] = 0;
     const float sa = ra / (ra + rb), sb = rb / (ra + rb);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        FA[a] += sa * F[a];
-        FB[a] += sb * F[a];
+        const float F = ft_val(q.f[a]);
+        FA[a] += sa * F;
+        FB[a] += sb * F;
     }
 }
 
@@ -533,10 +540,12 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
     const int n = d.n;
     const float2 mr = __ldg(p.rho + n), mp = __ldg(p.psi + n);
     const float ra = mr.x, rb = mr.y, pa = mp.x, pb = mp.y;
+    const bool ibm = IBM && ibm_reached(p, n);
+    IbmForce fi{};
+    if (ibm) fi = ibm_load(p, n);
     float FA[3], FB[3];
     sc_force(p, d, m, ra, rb, pa, pb, FA, FB);
-    const bool ibm = IBM && ibm_reached(p, n);
-    if (ibm) ibm_force(p, n, ra, rb, FA, FB);
+    if (ibm) ibm_apply(p, n, ra, rb, fi, FA, FB);
     float ja[3] = {0.f, 0.f, 0.f}, jb[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {  // opposite pairs (i, i+1)
@@ -577,11 +586,10 @@ __device__ __forceinline__ void collide_node(const LBParams &p, const Deltas &d)
 // stored the total momentum J = sum_c sum_i f_i^c e_i, so the populations are
 // not pulled a second time.  The common velocity is u' = J / (rho_A + rho_B)
 // and u^{c,eq} = u' + F^c / rho^c (the velocity shift with tau = 1).
-template <typename T, bool DRY, bool IBM>
+// ibm: the node's spread force is in FA, FB (its velocity goes to uphys)
+template <typename T, bool DRY>
 __device__ __forceinline__ void collide_eq_finish(const LBParams &p, int n, float ra, float rb, const float4 J4,
-                                                  float (&FA)[3], float (&FB)[3]) {
-    const bool ibm = IBM && ibm_reached(p, n);
-    if (ibm) ibm_force(p, n, ra, rb, FA, FB);
+                                                  const float (&FA)[3], const float (&FB)[3], bool ibm) {
     const float J[3] = {J4.x, J4.y, J4.z};
     const float rt = ra + rb, iden = 1.0f / rt, ia = 1.0f / ra, ib = 1.0f / rb;
     float ua[3], ub[3];
@@ -613,9 +621,13 @@ __device__ __forceinline__ void collide_eq_node(const LBParams &p, const Deltas 
     const int n = d.n;
     const uint32_t m = __ldg(p.mask + n);
     const float2 mr = __ldg(p.rho + n), mp = __ldg(p.psi + n);
+    const bool ibm = IBM && ibm_reached(p, n);
+    IbmForce fi{};
+    if (ibm) fi = ibm_load(p, n);
     float FA[3], FB[3];
     sc_force(p, d, m, mr.x, mr.y, mp.x, mp.y, FA, FB);
-    collide_eq_finish<T, DRY, IBM>(p, n, mr.x, mr.y, __ldg(p.J + n), FA, FB);
+    if (ibm) ibm_apply(p, n, mr.x, mr.y, fi, FA, FB);
+    collide_eq_finish<T, DRY>(p, n, mr.x, mr.y, __ldg(p.J + n), FA, FB, ibm);
 }
 
 // ---------------------------------------------------------------------------
@@ -663,6 +675,9 @@ __device__ __forceinline__ void collide_eq_node_ring(const LBParams &p, const De
     const uint32_t m = __ldg(p.mask + n);
     const float2 mr = __ldg(p.rho + n), mp = R.v[z & 3][ty][tx];
     const float ra = mr.x, rb = mr.y, pa = mp.x, pb = mp.y;
+    const bool ibm = IBM && ibm_reached(p, n);
+    IbmForce fi{};
+    if (ibm) fi = ibm_load(p, n);
     float FA[3], FB[3];
     if (!m && !d.wlo && !d.whi) {
         // the stencil of sc_force over opposite pairs, neighbours from the ring
@@ -683,7 +698,8 @@ __device__ __forceinline__ void collide_eq_node_ring(const LBParams &p, const De
     } else {
         sc_force(p, d, m, ra, rb, pa, pb, FA, FB);
     }
-    collide_eq_finish<T, DRY, IBM>(p, n, ra, rb, __ldg(p.J + n), FA, FB);
+    if (ibm) ibm_apply(p, n, ra, rb, fi, FA, FB);
+    collide_eq_finish<T, DRY>(p, n, ra, rb, __ldg(p.J + n), FA, FB, ibm);
 }
 
 // planes [zb, ze) of the tile at (x0, y0); every thread of the block calls it
@@ -709,14 +725,16 @@ __device__ __forceinline__ void collide_eq_ring(const LBParams &p, PsiRing<TX, T
     }
 }
 
-template <typename T, bool DRY = false>
+// IBM: with the diffuse-interface body force (its own instantiation, so that
+// the lattices without it keep their registers)
+template <typename T, bool DRY = false, bool IBM = false>
 __global__ void __launch_bounds__(BX *BY, Pop<T>::shifted ? CF_COLLIDE16_MINB : CF_COLLIDE_MINB)
     k_collide(const LBParams p) {
     pdl_trigger();
     pdl_wait();
     int x, y, z;
     if (!node_of<true>(p, x, y, z)) return;
-    for (; z < p.zhi; z += gridDim.z) collide_node<T, DRY, true>(p, deltas(p, x, y, z));
+    for (; z < p.zhi; z += gridDim.z) collide_node<T, DRY, IBM>(p, deltas(p, x, y, z));
 }
 
 // resident blocks per SM of the tau = 1 collide pass (no second pull: few registers)
@@ -733,7 +751,7 @@ __global__ void __launch_bounds__(BX *BY, Pop<T>::shifted ? CF_COLLIDE16_MINB : 
 #ifndef CF_PSI_RING
 #define CF_PSI_RING 0
 #endif
-template <typename T, bool DRY = false>
+template <typename T, bool DRY = false, bool IBM = false>
 __global__ void __launch_bounds__(BX *BY, CF_COLLIDE_EQ_MINB) k_collide_eq(const LBParams p) {
     pdl_trigger();
     pdl_wait();
@@ -742,11 +760,11 @@ __global__ void __launch_bounds__(BX *BY, CF_COLLIDE_EQ_MINB) k_collide_eq(const
     const int bx = (int)(gridDim.x - 1 - blockIdx.x), by = (int)(gridDim.y - 1 - blockIdx.y);
     const int bz = (int)(gridDim.z - 1 - blockIdx.z);
     const int zb = p.zlo + bz * p.zring, ze = min(p.zhi, zb + p.zring);
-    collide_eq_ring<T, DRY, BX, BY, true>(p, R, bx * BX, by * BY, zb, ze);
+    collide_eq_ring<T, DRY, BX, BY, IBM>(p, R, bx * BX, by * BY, zb, ze);
 #else
     int x, y, z;
     if (!node_of<true>(p, x, y, z)) return;
-    for (; z < p.zhi; z += gridDim.z) collide_eq_node<T, DRY, true>(p, deltas(p, x, y, z));
+    for (; z < p.zhi; z += gridDim.z) collide_eq_node<T, DRY, IBM>(p, deltas(p, x, y, z));
 #endif
 }
 
@@ -757,7 +775,7 @@ size_t density_blocks_max(int nx, int ny, int nz) {
 namespace {
 // before_collide (optional): the collide pass also waits for this event (a
 // plain launch then, the density pass stays programmatic)
-template <typename T, bool DRY>
+template <typename T, bool DRY, bool IBM>
 void lb_passes(const LBParams &p, dim3 grid, dim3 block, cudaStream_t s, bool eq, cudaEvent_t before_collide) {
     if (eq) {
         launch_pdl(k_density<T, DRY, true>, grid, block, s, p);
@@ -769,24 +787,30 @@ void lb_passes(const LBParams &p, dim3 grid, dim3 block, cudaStream_t s, bool eq
 #endif
         if (before_collide) {
             cudaStreamWaitEvent(s, before_collide, 0);
-            k_collide_eq<T, DRY><<<gc, block, 0, s>>>(p);
+            k_collide_eq<T, DRY, IBM><<<gc, block, 0, s>>>(p);
         } else {
-            launch_pdl(k_collide_eq<T, DRY>, gc, block, s, p);
+            launch_pdl(k_collide_eq<T, DRY, IBM>, gc, block, s, p);
         }
     } else {
         launch_pdl(k_density<T, DRY>, grid, block, s, p);
         if (before_collide) {
             cudaStreamWaitEvent(s, before_collide, 0);
-            k_collide<T, DRY><<<grid, block, 0, s>>>(p);
+            k_collide<T, DRY, IBM><<<grid, block, 0, s>>>(p);
         } else {
-            launch_pdl(k_collide<T, DRY>, grid, block, s, p);
+            launch_pdl(k_collide<T, DRY, IBM>, grid, block, s, p);
         }
     }
 }
 template <typename T>
 void lb_passes(const LBParams &p, dim3 grid, dim3 block, cudaStream_t s, bool dry, bool eq, cudaEvent_t ev) {
-    if (dry) lb_passes<T, true>(p, grid, block, s, eq, ev);
-    else lb_passes<T, false>(p, grid, block, s, eq, ev);
+    const bool ibm = p.fibm != nullptr;
+    if (dry) {
+        if (ibm) lb_passes<T, true, true>(p, grid, block, s, eq, ev);
+        else lb_passes<T, true, false>(p, grid, block, s, eq, ev);
+    } else {
+        if (ibm) lb_passes<T, false, true>(p, grid, block, s, eq, ev);
+        else lb_passes<T, false, false>(p, grid, block, s, eq, ev);
+    }
 }
 }  // namespace
 
