@@ -496,20 +496,56 @@ __device__ __forceinline__ void ibm_stencil(const MemParams &p, const pf &x, Fn 
     }
 }
 
-// the force F of a node at x spread to the lattice (fixed point, so that the
-// sums do not depend on the order of the atomics), its nodes flagged
-__device__ __forceinline__ void ibm_spread_node(const MemParams &p, const pf &x, f3 F) {
+// The forces F of the warp's nodes at x spread to the lattice, their stencil
+// nodes flagged.  Each contribution F_a w is rounded to fixed point (ft_add),
+// so the sums do not depend on the order of the atomics.  The warp takes its
+// nodes one after another; lane l adds stencil column kx = l % 4 of the rows
+// (kz, ky) in group g = l / 4, so that an atomic instruction writes 8 runs of
+// 4 consecutive lattice nodes instead of 32 scattered ones.  Per node the six
+// passes cover the component a = pass / 2 and the rows ky = g % 4,
+// kz = g / 4 + 2 (pass % 2).  Called by the whole (32-thread) warp.
+struct IbmNode { int b[3]; float w[3][4]; float F[3]; };
+__device__ __forceinline__ void ibm_spread_warp(const MemParams &p, bool valid, const pf &x, f3 F) {
+    __shared__ IbmNode sn[32];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    if (valid) {
+        IbmNode &m = sn[lane];
+        ibm_axis(x.h.x, x.l.x, m.b[0], m.w[0]);
+        ibm_axis(x.h.y, x.l.y, m.b[1], m.w[1]);
+        ibm_axis(x.h.z, x.l.z, m.b[2], m.w[2]);
+        m.F[0] = F.x; m.F[1] = F.y; m.F[2] = F.z;
+    }
+    __syncwarp();
     long long *fb = p.fibm;
     const long long N = p.N;
     uint8_t *flag = ibm_flags(p.uphys, N);
-    ibm_stencil(p, x, [&](long long n, float w) {
-        ft_add(fb + n, F.x * w);
-        ft_add(fb + N + n, F.y * w);
-        ft_add(fb + 2 * N + n, F.z * w);
-        flag[n >> 5] = 1;
-    });
+    const int kx = lane & 3, g = lane >> 2, ky = g & 3, kz0 = g >> 2;
+    unsigned todo = __ballot_sync(full, valid);
+    while (todo) {
+        const int j = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const IbmNode &m = sn[j];
+        const long long xn = wrapi(m.b[0] + kx, p.nx);
+        const long long yrow = wrapi(m.b[1] + ky, p.ny);
+        const float wxy = m.w[0][kx] * m.w[1][ky];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // rows kz = kz0 and kz0 + 2
+            const int kz = kz0 + 2 * h;
+            const int z = wrapi(m.b[2] + kz, p.nz);
+            if (p.wall && z == 0) continue;  // substrate nodes take no force
+            const long long n = ((long long)z * p.ny + yrow) * p.nx + xn;
+            const float wt = wxy * m.w[2][kz];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) ft_add(fb + a * N + n, m.F[a] * wt);
+            flag[n >> 5] = 1;
+        }
+    }
+    __syncwarp();
 }
 
+// IBM: the diffuse-interface spreading may be on (single-lattice kernel only)
+template <bool IBM = false>
 __device__ __forceinline__ void mem_update_body(const MemParams &p, const ClearParams &cl, int bid) {
     if (cl.count_next && bid == 0 && threadIdx.x == 0) *cl.count_next = 0;
     const int node_blocks = (p.nnodes + MV - 1) / MV;
@@ -524,13 +560,13 @@ __device__ __forceinline__ void mem_update_body(const MemParams &p, const ClearP
     const CapDev cp = p.caps[cap];
     const double *A = p.acc + cap * A_NACC;
     f3 Fc{0.f, 0.f, 0.f}, Ft{0.f, 0.f, 0.f}, r{0.f, 0.f, 0.f};
+    const pf x = ldp(p.Xh, p.Xl, vv);
     if (valid) {
-        const pf x = ldp(p.Xh, p.Xl, vv);
         const float pre = (float)A[A_PRE];
         node_forces(p, cp, cap, vv, pre, x, Fc, Ft);
         st3(p.Fcpl + 3 * vv, Fc);
         if (p.fibm) {
-            ibm_spread_node(p, x, Ft);  // the node moves after the lattice update (k_ibm_move)
+            // spread below by the whole warp; the node moves after the lattice update (k_ibm_move)
         } else if (cp.mode == 0) {
             // Eq. 9 with dt = 1 (v = F/m), or with CF_INERTIAL v += F/m
             f3 vel = (1.f / cp.mass) * Ft;
@@ -556,6 +592,7 @@ __device__ __forceinline__ void mem_update_body(const MemParams &p, const ClearP
     acc_add(Aw, cap, A_FTX, Ft.x, valid);
     acc_add(Aw, cap, A_FTY, Ft.y, valid);
     acc_add(Aw, cap, A_FTZ, Ft.z, valid);
+    if (IBM && p.fibm) ibm_spread_warp(p, valid, x, Ft);
 }
 __device__ __forceinline__ void mem_update_body(const UpdateParams &u, int bid) { mem_update_body(u.m, u.c, bid); }
 
@@ -580,7 +617,7 @@ __global__ void __launch_bounds__(MT) k_mem_bending(const MemParams p) { mem_ben
 __global__ void __launch_bounds__(MV) k_mem_update(const MemParams p, const ClearParams cl) {
     pdl_trigger();
     pdl_wait();
-    mem_update_body(p, cl, blockIdx.x);
+    mem_update_body<true>(p, cl, blockIdx.x);
 }
 __global__ void __launch_bounds__(MV) k_mem_frozen(const MemParams p) { mem_frozen_body(p, blockIdx.x); }
 
