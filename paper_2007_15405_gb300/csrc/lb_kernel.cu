@@ -619,15 +619,17 @@ __device__ __forceinline__ void collide_eq_finish(const LBParams &p, int n, floa
 template <typename T, bool DRY = false, bool IBM = false>
 __device__ __forceinline__ void collide_eq_node(const LBParams &p, const Deltas &d) {
     const int n = d.n;
+    // the node's own loads first, so that they overlap the stencil's gathers
     const uint32_t m = __ldg(p.mask + n);
     const float2 mr = __ldg(p.rho + n), mp = __ldg(p.psi + n);
+    const float4 J4 = __ldg(p.J + n);
     const bool ibm = IBM && ibm_reached(p, n);
     IbmForce fi{};
     if (ibm) fi = ibm_load(p, n);
     float FA[3], FB[3];
     sc_force(p, d, m, mr.x, mr.y, mp.x, mp.y, FA, FB);
     if (ibm) ibm_apply(p, n, mr.x, mr.y, fi, FA, FB);
-    collide_eq_finish<T, DRY>(p, n, mr.x, mr.y, __ldg(p.J + n), FA, FB, ibm);
+    collide_eq_finish<T, DRY>(p, n, mr.x, mr.y, J4, FA, FB, ibm);
 }
 
 // ---------------------------------------------------------------------------

@@ -614,10 +614,12 @@ __device__ __forceinline__ void mem_frozen_body(const MemParams &p, int bid) {
 __global__ void __launch_bounds__(MT) k_mem_elements(const MemParams p) { mem_elements_body(p, blockIdx.x); }
 __global__ void __launch_bounds__(MV) k_mem_nodes(const MemParams p) { mem_nodes_body(p, blockIdx.x); }
 __global__ void __launch_bounds__(MT) k_mem_bending(const MemParams p) { mem_bending_body(p, blockIdx.x); }
+// IBM: spreading for the diffuse-interface coupling (its own instantiation)
+template <bool IBM>
 __global__ void __launch_bounds__(MV) k_mem_update(const MemParams p, const ClearParams cl) {
     pdl_trigger();
     pdl_wait();
-    mem_update_body<true>(p, cl, blockIdx.x);
+    mem_update_body<IBM>(p, cl, blockIdx.x);
 }
 __global__ void __launch_bounds__(MV) k_mem_frozen(const MemParams p) { mem_frozen_body(p, blockIdx.x); }
 
@@ -726,7 +728,8 @@ cudaError_t launch_membrane_forces(const MemParams &p, cudaStream_t s, int *nl) 
 cudaError_t launch_membrane_update(const MemParams &p, const ClearParams &cl, bool any_frozen,
                                    cudaStream_t s, int *nl) {
     const unsigned gv = (unsigned)((p.nnodes + MV - 1) / MV);
-    launch_pdl(k_mem_update, dim3(gv + (unsigned)cl.blocks), dim3(MV), s, p, cl);
+    if (p.fibm) launch_pdl(k_mem_update<true>, dim3(gv + (unsigned)cl.blocks), dim3(MV), s, p, cl);
+    else launch_pdl(k_mem_update<false>, dim3(gv + (unsigned)cl.blocks), dim3(MV), s, p, cl);
     *nl += 1;
     if (any_frozen) {
         k_mem_frozen<<<gv, MV, 0, s>>>(p);

@@ -173,6 +173,78 @@ def test_ibm_hundred_capsules_in_contact(cfm):
         assert np.abs(sim.capsule_state(k)["X"] - orc.capsule_state(k)["X"]).max() < TOL_X, k
 
 
+def test_ibm_drying(cfm):
+    """Drying (A turned into B at A-majority nodes, Sec. 3.2 reading) with the
+    diffuse-interface coupling, against the oracle."""
+    wl = I.tiny_film(mode=I.MODE_FREE, steps=30)
+    wl.dry_dm = 0.05
+    sim, orc = run_pair(cfm, wl)
+    compare(sim, orc, 1)
+    mg, mo = sim.total_mass(), orc.total_mass()
+    assert np.abs(mg - mo).max() < 1e-6 * mo.sum()
+
+
+# 16-bit storage against the FP64 oracle: 3x the measured maxima of the
+# cut-link coupling's 16-bit parity (tests/test_gpu_precision.py)
+BOUNDS_16 = {1: dict(rho=2e-4, u=8e-3, X=1.2e-4), 2: dict(rho=1.2e-3, u=6e-2, X=5e-4)}
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_ibm_16bit_storage(cfm, prec):
+    """FP16 / BF16 population storage with the diffuse-interface coupling."""
+    wl = I.tiny_film(mode=I.MODE_FREE, steps=40)
+    wl.flags = O.Oracle.IBM
+    sim = cfm.Simulation.from_workload(wl, precision=prec)
+    orc = O.Oracle.from_workload(wl)
+    sim.step(wl.steps)
+    orc.step(wl.steps)
+    rg, ug = sim.fields()
+    ro, uo = orc.fields()
+    e = dict(rho=rel(rg, ro), u=rel(ug, uo),
+             X=np.abs(sim.capsule_state(0)["X"] - orc.capsule_state(0)["X"]).max())
+    for k, v in e.items():
+        assert v < BOUNDS_16[prec][k], (k, v)
+
+
+def test_ibm_restart_is_bit_identical(cfm, tmp_path):
+    """A checkpoint of a diffuse-interface run (its cut links rebuilt for the
+    saved positions) restarts into the same bits."""
+    wl = I.tiny_film(mode=I.MODE_FREE, steps=1)
+    wl.flags = O.Oracle.IBM
+    a = cfm.Simulation.from_workload(wl)
+    a.step(17)
+    path = str(tmp_path / "ibm.bin")
+    a.save(path)
+    a.step(20)
+    b = cfm.Simulation.from_workload(wl, set_film=False)
+    b.load(path)
+    b.step(20)
+    assert np.array_equal(a.populations(), b.populations())
+    assert np.array_equal(a.capsule_state(0)["X"], b.capsule_state(0)["X"])
+    assert (a.cuts()[0] == b.cuts()[0]).all()
+
+
+def test_ibm_meniscus_readouts_between_steps(cfm):
+    """Readouts rebuild the cut links for the positions of the moment; taken
+    between steps they change nothing of the run, and the meniscus field
+    equals the oracle's."""
+    wl = I.tiny_film(mode=I.MODE_FREE, steps=30)
+    wl.flags = O.Oracle.IBM
+    a = cfm.Simulation.from_workload(wl)
+    b = cfm.Simulation.from_workload(wl)
+    orc = O.Oracle.from_workload(wl)
+    for _ in range(3):
+        a.step(10)
+        a.meniscus_field()
+    b.step(30)
+    orc.step(30)
+    assert np.array_equal(a.populations(), b.populations())
+    hg, ho = a.meniscus_field(), orc.meniscus_field()
+    assert (np.isnan(hg) == np.isnan(ho)).all()
+    ok = ~np.isnan(ho)
+    assert np.abs(hg[ok] - ho[ok]).max() < 1e-3
+
+
 def test_ibm_rejections(cfm):
     """Frozen capsules, the inertial reading and batches need the cut-link
     coupling."""
