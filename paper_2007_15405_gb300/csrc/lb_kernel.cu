@@ -616,13 +616,23 @@ __device__ __forceinline__ void collide_eq_finish(const LBParams &p, int n, floa
     store_post<T, DRY, true>(p, n, ra, rb, ua, ub, unused, unused);
 }
 
+// the node's own inputs of the tau = 1 collision, loaded together ahead of
+// the Shan-Chen stencil's gathers
+struct NodeOwn {
+    uint32_t m;
+    float2 r, q;
+    float4 J;
+};
+__device__ __forceinline__ NodeOwn node_own(const LBParams &p, long long n) {
+    return {__ldg(p.mask + n), __ldg(p.rho + n), __ldg(p.psi + n), __ldg(p.J + n)};
+}
+
 template <typename T, bool DRY = false, bool IBM = false>
-__device__ __forceinline__ void collide_eq_node(const LBParams &p, const Deltas &d) {
+__device__ __forceinline__ void collide_eq_node(const LBParams &p, const Deltas &d, const NodeOwn &o) {
     const int n = d.n;
-    // the node's own loads first, so that they overlap the stencil's gathers
-    const uint32_t m = __ldg(p.mask + n);
-    const float2 mr = __ldg(p.rho + n), mp = __ldg(p.psi + n);
-    const float4 J4 = __ldg(p.J + n);
+    const uint32_t m = o.m;
+    const float2 mr = o.r, mp = o.q;
+    const float4 J4 = o.J;
     const bool ibm = IBM && ibm_reached(p, n);
     IbmForce fi{};
     if (ibm) fi = ibm_load(p, n);
@@ -630,6 +640,15 @@ __device__ __forceinline__ void collide_eq_node(const LBParams &p, const Deltas 
     sc_force(p, d, m, mr.x, mr.y, mp.x, mp.y, FA, FB);
     if (ibm) ibm_apply(p, n, mr.x, mr.y, fi, FA, FB);
     collide_eq_finish<T, DRY>(p, n, mr.x, mr.y, J4, FA, FB, ibm);
+}
+
+// the planes zb, zb + zs, ... below ze of column (x, y)
+template <typename T, bool DRY = false, bool IBM = false>
+__device__ __forceinline__ void collide_eq_column(const LBParams &p, int x, int y, int zb, int ze, int zs) {
+    for (int z = zb; z < ze; z += zs) {
+        const Deltas d = deltas(p, x, y, z);
+        collide_eq_node<T, DRY, IBM>(p, d, node_own(p, d.n));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -766,7 +785,7 @@ __global__ void __launch_bounds__(BX *BY, CF_COLLIDE_EQ_MINB) k_collide_eq(const
 #else
     int x, y, z;
     if (!node_of<true>(p, x, y, z)) return;
-    for (; z < p.zhi; z += gridDim.z) collide_eq_node<T, DRY, IBM>(p, deltas(p, x, y, z));
+    collide_eq_column<T, DRY, IBM>(p, x, y, z, p.zhi, (int)gridDim.z);
 #endif
 }
 
@@ -876,7 +895,7 @@ __global__ void __launch_bounds__(TX *TY, (TX * TY >= 256 ? 2 : (EQ ? CF_COLLIDE
         } else if constexpr (EQ) {
             const int x = it.y * TX + (int)threadIdx.x, y = it.z * TY + (int)threadIdx.y;
             if (x >= p.nx || y >= p.ny) continue;
-            for (int z = zb; z < ze; ++z) collide_eq_node<T>(p, deltas(p, x, y, z));
+            collide_eq_column<T>(p, x, y, zb, ze, 1);
         } else {
             const int x = it.y * TX + (int)threadIdx.x, y = it.z * TY + (int)threadIdx.y;
             if (x >= p.nx || y >= p.ny) continue;
