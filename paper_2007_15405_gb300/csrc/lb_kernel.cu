@@ -88,6 +88,7 @@ __device__ __forceinline__ __half sr_f16(float v, uint32_t r) {
 // fractional parts).  put2 stores the halves, val2 returns (x, y) as stored.
 template <> struct Pop<__half> {
     static constexpr bool shifted = true;
+    static constexpr float scale = F16_SCALE, inv_scale = F16_INV_SCALE;  // stored = offset x scale
     __device__ static float ld(const __half *p) { return __half2float(__ldg(p)) * F16_INV_SCALE; }
     __device__ static float st(__half *p, float v, uint32_t r) {
         const __half h = sr_f16(v * F16_SCALE, r);
@@ -104,6 +105,16 @@ template <> struct Pop<__half> {
         const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&d));  // (low, high)
         return make_float2(f.y * F16_INV_SCALE, f.x * F16_INV_SCALE);
     }
+    // the same with x and y already scaled, and the stored values in scaled units
+    __device__ static uint32_t cvt2s(float xs, float ys, uint32_t r) {
+        uint32_t d;
+        asm("cvt.rs.satfinite.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(xs), "f"(ys), "r"(r));
+        return d;
+    }
+    __device__ static float2 raw2(uint32_t d) {
+        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&d));
+        return make_float2(f.y, f.x);
+    }
     __device__ static void put2(__half *px, __half *py, uint32_t d) {
         *reinterpret_cast<unsigned short *>(px) = (unsigned short)(d >> 16);
         *reinterpret_cast<unsigned short *>(py) = (unsigned short)(d & 0xffffu);
@@ -111,6 +122,7 @@ template <> struct Pop<__half> {
 };
 template <> struct Pop<__nv_bfloat16> {
     static constexpr bool shifted = true;
+    static constexpr float scale = 1.0f, inv_scale = 1.0f;
     __device__ static float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
     __device__ static float st(__nv_bfloat16 *p, float v, uint32_t r) {
         const __nv_bfloat16 h = sr_bf16(v, r);
@@ -125,6 +137,8 @@ template <> struct Pop<__nv_bfloat16> {
     __device__ static float2 val2(uint32_t d) {  // a bfloat16 is the high half of a float
         return make_float2(__uint_as_float(d & 0xffff0000u), __uint_as_float(d << 16));
     }
+    __device__ static uint32_t cvt2s(float x, float y, uint32_t r) { return cvt2(x, y, r); }
+    __device__ static float2 raw2(uint32_t d) { return val2(d); }
     __device__ static void put2(__nv_bfloat16 *px, __nv_bfloat16 *py, uint32_t d) {
         *reinterpret_cast<unsigned short *>(px) = (unsigned short)(d >> 16);
         *reinterpret_cast<unsigned short *>(py) = (unsigned short)(d & 0xffffu);
@@ -489,6 +503,40 @@ __device__ __forceinline__ void store_post(const LBParams &p, int n, float ra, f
         }
         Pop<T>::st(dA, va0, 0u);
         Pop<T>::st(dB, vb0, 0u);
+    } else if constexpr (EQ && !DRY) {
+        // tau = 1, no drying: the offsets f^eq_i - w_i rho = w_i rho (kappa +
+        // 4.5 eu^2 +- 3 eu), kappa = -1.5 u^2, computed directly (no
+        // cancellation against w_i rho) with the storage scale folded into
+        // w_i rho; stochastically rounded as below.  The rest population takes
+        // the mass balance rho - sum_i w_i rho - sum_i stored offsets, the
+        // weight sum being 12 w_1 (the float weights: w_1 = 1/18, w_7 = w_1 / 2
+        // exactly), so the rounding of w_1 rho is unbiased.
+        uint32_t rs = mix32((uint32_t)n * 0x9e3779b9u ^ mix32(*p.step_ctr));
+        const float S = Pop<T>::scale;
+        const float kA = -1.5f * (ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2]);
+        const float kB = -1.5f * (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
+        const float raS = ra * S, rbS = rb * S;
+        float sumA = 0.f, sumB = 0.f;  // stored offsets, scaled
+#pragma unroll
+        for (int i = 1; i < Q; i += 2) {
+            const float eua = ex(i) * ua[0] + ey(i) * ua[1] + ez(i) * ua[2];
+            const float eub = ex(i) * ub[0] + ey(i) * ub[1] + ez(i) * ub[2];
+            const float waS = wgt(i) * raS, wbS = wgt(i) * rbS;
+            const float ca = kA + 4.5f * eua * eua, cb = kB + 4.5f * eub * eub;
+            const float ta = 3.0f * eua, tb = 3.0f * eub;
+            rs = rs * 1664525u + 1013904223u;
+            const uint32_t hA = Pop<T>::cvt2s(waS * (ca + ta), waS * (ca - ta), rs ^ (rs >> 16));
+            rs = rs * 1664525u + 1013904223u;
+            const uint32_t hB = Pop<T>::cvt2s(wbS * (cb + tb), wbS * (cb - tb), rs ^ (rs >> 16));
+            Pop<T>::put2(dA + i * N, dA + (i + 1) * N, hA);
+            Pop<T>::put2(dB + i * N, dB + (i + 1) * N, hB);
+            const float2 sA = Pop<T>::raw2(hA), sB = Pop<T>::raw2(hB);
+            sumA += sA.x + sA.y;
+            sumB += sB.x + sB.y;
+        }
+        const float w1 = wgt(1);
+        p.dst0[n] = (ra - 12.0f * (w1 * ra)) - sumA * Pop<T>::inv_scale;
+        p.dst0[N + n] = (rb - 12.0f * (w1 * rb)) - sumB * Pop<T>::inv_scale;
     } else {
         // 16-bit offsets from w_i rho, stochastically rounded; the float rest
         // population takes what the rounded moving populations leave of the mass
