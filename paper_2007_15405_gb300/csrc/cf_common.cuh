@@ -268,8 +268,9 @@ struct PrepParams {
 
 // The membrane and cut-link kernels of many lattices in one launch: entry i
 // holds lattice i's parameters, its blocks are [boff[i], boff[i+1]) of the
-// grid.  Travels by value in the launch (64 x 272 B stays under the 32 KB
-// launch-parameter limit); larger batches take one launch per 64 lattices.
+// grid.  Travels by value in the launch (64 entries of at most 352 B, the node
+// update's, stay under the 32,764-byte launch-parameter limit); larger batches
+// take one launch per 64 lattices.
 constexpr int CF_SPARSE_CAP = 64;
 template <class P>
 struct SparseTab {
@@ -281,6 +282,8 @@ struct UpdateParams {
     MemParams m;
     ClearParams c;
 };
+constexpr size_t CF_MAX_LAUNCH_PARAMS = 32764;  // bytes of kernel parameters a launch may carry
+static_assert(sizeof(SparseTab<UpdateParams>) <= CF_MAX_LAUNCH_PARAMS, "node-update table too large");
 
 __host__ __device__ inline int wrapi(int a, int n) {
     a %= n;
@@ -301,14 +304,17 @@ cudaError_t launch_lb_step(const LBParams &p, int prec, cudaStream_t s, cudaEven
 // per pass.  The per-lattice parameters travel by value in the launch (one
 // table per step parity of a captured step pair); the work list holds
 // (lattice, x tile, y tile, z slice) items of the chosen tile shape.
-// (128 x 248 B fits the 32 KB launch-parameter limit; a build with a table of
-// at most 16 lattices keeps the launch parameters under 4 KB)
+// (128 x 248 B fits the 32,764-byte launch-parameter limit with the work-list
+// pointer and count; a build with a table of at most 16 lattices keeps the
+// launch parameters under 4 KB)
 #ifndef CF_BATCH_MAX
 #define CF_BATCH_MAX 128
 #endif
 struct BatchTab {
     LBParams lat[CF_BATCH_MAX];
 };
+static_assert(sizeof(BatchTab) + sizeof(void *) + sizeof(int) <= CF_MAX_LAUNCH_PARAMS,
+              "lattice table too large for one launch");
 constexpr int CF_NTILES = 6;  // tile shapes (x width, y depth) of the batched passes
 void lb_batch_tile(int tile, int *tx, int *ty);
 int lb_batch_resident(int tile, int prec, bool eq);  // blocks of one pass resident on the device

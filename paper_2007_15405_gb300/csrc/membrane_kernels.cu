@@ -21,6 +21,10 @@
 // cut links of the moved membrane are rebuilt by k_cut_faces after
 // k_mem_update has reset the previous ones; the density pass of the next step
 // prepares the bounce records of the cut links.
+// With the diffuse-interface coupling (CF_IBM) kernel 4 runs before the
+// collide pass and spreads each node's force to the lattice with Peskin's
+// 4-point kernel instead of moving it; k_ibm_move then moves the nodes with
+// the fluid velocity of the step, interpolated with the same kernel.
 #include "cf_common.cuh"
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
