@@ -25,6 +25,12 @@
 // 152 B of population writes in the collide pass.  Gather addresses are the
 // node index plus per-direction offsets with the periodic wrap folded into
 // per-node deltas.
+//
+// With the diffuse-interface coupling (CF_IBM, own instantiations of the
+// single-lattice collide passes) the collide pass also adds the membrane
+// force spread to the node, shared by the components in proportion to their
+// densities, and writes the fluid velocity the membrane nodes move with; the
+// lattice then sees no cut link.
 #include "cf_common.cuh"
 #include "../../include/capfilm.h"
 
