@@ -139,7 +139,8 @@ struct cf_ctx {
     int zchunk = 0;
     int zring = 1;
 
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;      // a captured step pair
+    cudaGraphExec_t graph_out = nullptr;  // the same, its second step also recording the fields
     int graph_key = -1;
     int graph_launches = 0;  // kernel launches of one graph replay (two steps)
 
@@ -159,6 +160,14 @@ namespace {
 
 // bytes of the block flags of the diffuse-interface coupling (one per 32 nodes)
 size_t ibm_flag_bytes(long long N) { return (size_t)((N + 31) / 32 + 15) / 16 * 16; }
+
+// the captured step pairs are stale (the layout or the parities changed)
+void drop_graphs(cf_ctx *c) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->graph_out) cudaGraphExecDestroy(c->graph_out);
+    c->graph = c->graph_out = nullptr;
+    c->graph_key = -1;
+}
 
 void *dalloc(cf_ctx *c, size_t bytes, bool membrane = false) {
     void *p = nullptr;
@@ -483,6 +492,32 @@ cf_status enqueue_step(cf_ctx *c, bool with_out, int *nl, cudaEvent_t *ev = null
     return CF_OK;
 }
 
+// The captured step pair of the context's current parities (out: its second
+// step also records the fields); captured on first use, both dropped when the
+// parities or the layout change.
+cf_status step_graph(cf_ctx *c, bool out, cudaGraphExec_t *ge) {
+    const int key = c->fpar | (c->xpar << 1) | (c->lpar << 2) | (c->ftpar << 3);
+    if (c->graph_key != key) drop_graphs(c);
+    cudaGraphExec_t &slot = out ? c->graph_out : c->graph;
+    if (!slot) {
+        cudaGraph_t g;
+        CF_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        int nlg = 0;
+        cf_status s1 = enqueue_step(c, false, &nlg);
+        cf_status s2 = s1 == CF_OK ? enqueue_step(c, out, &nlg) : s1;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (s2 != CF_OK) return s2;
+        if (e != cudaSuccess) return fail(CF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&slot, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(CF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        c->graph_key = key;
+        c->graph_launches = nlg;
+    }
+    *ge = slot;
+    return CF_OK;
+}
+
 void choose_launch(cf_ctx *c) {
     // blocks of 32 x 4 columns; each thread walks zchunk planes (strided), so
     // the grid holds about 48 blocks per SM (8 waves of the density pass at 6
@@ -711,7 +746,7 @@ cf_status build_membrane(cf_ctx *c) {
     cf_status s = enqueue_cuts(c, c->X[c->xpar], &nl);
     if (s != CF_OK) return s;
     CF_CUDA(launch_inside(c->mask, c->inside, c->d.nx, c->d.ny, c->d.nz, c->stream));
-    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_key = -1; }
+    drop_graphs(c);
     return CF_OK;
 }
 
@@ -827,7 +862,7 @@ cf_status cf_create(const cf_lattice_desc *desc, cf_ctx **out) {
 cf_status cf_destroy(cf_ctx *c) {
     if (!c) return CF_OK;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    if (c->graph) cudaGraphExecDestroy(c->graph);
+    drop_graphs(c);
     for (void *p : c->mem_allocs) dfree(c, p);
     for (void *p : c->allocations) dfree(c, p);
     if (c->jit) dfree(c, c->jit);
@@ -901,7 +936,7 @@ cf_status cf_set_capsule_mode(cf_ctx *c, int id, int mode) {
         c->any_frozen |= h.mode == CF_FROZEN;
         c->all_fixed &= h.mode == CF_FIXED;
     }
-    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_key = -1; }
+    drop_graphs(c);
     return CF_OK;
 }
 
@@ -920,7 +955,7 @@ cf_status cf_remove_mass(cf_ctx *c, double dm) {
     }
     CF_CUDA(cudaStreamSynchronize(c->stream));
     c->dry_dm = dm;
-    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_key = -1; }
+    drop_graphs(c);
     return CF_OK;
 }
 
@@ -1036,47 +1071,38 @@ cf_status cf_step(cf_ctx *c, long long n) {
     if (!c->film_set) return fail(CF_ESTATE, "cf_set_film must come before cf_step");
     if (n < 0) return fail(CF_EINVAL, "negative step count");
     if (n == 0) return CF_OK;
+    // Steps come from captured step pairs (each returns every double buffer
+    // to its parity), the last step recording the fields: an even count ends
+    // with the pair whose second step records them, an odd count with one
+    // plain recording step.
     int nl = 0;
-    long long left = n - 1;  // the last step records the fields
+    long long left = n;
     auto key_of = [](const cf_ctx *x) { return x->fpar | (x->xpar << 1) | (x->lpar << 2) | (x->ftpar << 3); };
-    if (left >= 3 && c->graph && c->graph_key != key_of(c)) {
+    if (left >= 4 && c->graph && c->graph_key != key_of(c)) {
         // every double buffer flips each step, so one plain step brings the
-        // context to the parity of the captured graph (no capture here)
+        // context to the parity of the captured graphs (no capture here)
         cf_status s = enqueue_step(c, false, &nl);
         if (s != CF_OK) return s;
         --left;
     }
-    if (left >= 2) {
-        const int key = key_of(c);
-        if (!c->graph || c->graph_key != key) {
-            if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
-            cudaGraph_t g;
-            CF_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-            int nlg = 0;
-            cf_status s1 = enqueue_step(c, false, &nlg);
-            cf_status s2 = s1 == CF_OK ? enqueue_step(c, false, &nlg) : s1;
-            cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-            if (s2 != CF_OK) return s2;
-            if (e != cudaSuccess) return fail(CF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-            e = cudaGraphInstantiate(&c->graph, g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) return fail(CF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-            c->graph_key = key;
-            c->graph_launches = nlg;
-        }
-        while (left >= 2) {
-            CF_CUDA(cudaGraphLaunch(c->graph, c->stream));
-            left -= 2;
+    if (left >= 3) {
+        const bool odd = (left & 1) != 0;
+        const long long pairs = left / 2;
+        for (long long k = 0; k < pairs; ++k) {
+            const bool out = !odd && k == pairs - 1;
+            cudaGraphExec_t ge = nullptr;
+            cf_status s = step_graph(c, out, &ge);
+            if (s != CF_OK) return s;
+            CF_CUDA(cudaGraphLaunch(ge, c->stream));
             nl += c->graph_launches;
         }
+        left -= 2 * pairs;
     }
     while (left > 0) {
-        cf_status s = enqueue_step(c, false, &nl);
+        cf_status s = enqueue_step(c, left == 1, &nl);
         if (s != CF_OK) return s;
         --left;
     }
-    cf_status s = enqueue_step(c, true, &nl);
-    if (s != CF_OK) return s;
     c->steps_done += n;
     c->launches_last = nl;
     return CF_OK;
@@ -1549,7 +1575,7 @@ cf_status cf_load(cf_ctx *c, const char *path) {
     if (c->nnodes > 0) CF_CUDA(cudaMemcpy(c->counts + c->lpar, &h.count, sizeof(int), cudaMemcpyHostToDevice));
     c->steps_done = h.steps_done;
     c->film_set = true;
-    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_key = -1; }
+    drop_graphs(c);
     return cf_remove_mass(c, h.dry_dm);
 }
 
@@ -1605,13 +1631,22 @@ struct cf_batch {
     std::vector<cudaEvent_t> gfork, gjoin; // [CF_MAX_GROUPS] around them
     std::vector<int4 *> gwork;             // per group: work list (lattice index within the group)
     std::vector<int> gnwork;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;      // a captured step pair of all groups
+    cudaGraphExec_t graph_out = nullptr;  // the same, its second step also recording the fields
     std::vector<int> graph_key;    // parities of all contexts at capture
     int graph_launches = 0;
     long long launches_last = 0;
 };
 
 namespace {
+
+// the captured step pairs are stale (the layout or the parities changed)
+void batch_drop_graphs(cf_batch *b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->graph_out) cudaGraphExecDestroy(b->graph_out);
+    b->graph = b->graph_out = nullptr;
+    b->graph_key.clear();
+}
 
 // work items (lattice index - base, x tile, y tile, z slice) of contexts [i0, i1)
 void batch_items(cf_batch *b, size_t i0, size_t i1, int base, std::vector<int4> &w) {
@@ -1671,7 +1706,7 @@ cf_status batch_build_work(cf_batch *b) {
         if (s != CF_OK) return s;
         b->gnwork[g] = (int)wg.size();
     }
-    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    batch_drop_graphs(b);
     return CF_OK;
 }
 
@@ -1836,19 +1871,23 @@ std::vector<int> batch_key(const cf_batch *b) {
 }
 
 // the captured two-step graph for the contexts' current parities
-cf_status batch_graph(cf_batch *b) {
+// The captured step pair of the contexts' current parities (out: its second
+// step also records the fields); captured on first use, both dropped when the
+// parities or the layout change.
+cf_status batch_graph(cf_batch *b, bool out = false) {
     const std::vector<int> key = batch_key(b);
-    if (!b->graph || b->graph_key != key) {
-        if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    if (b->graph_key != key) batch_drop_graphs(b);
+    cudaGraphExec_t &slot = out ? b->graph_out : b->graph;
+    if (!slot) {
         cudaGraph_t g;
         CF_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
         int nlg = 0;
         cf_status s1 = batch_enqueue_step(b, false, &nlg);
-        cf_status s2 = s1 == CF_OK ? batch_enqueue_step(b, false, &nlg) : s1;
+        cf_status s2 = s1 == CF_OK ? batch_enqueue_step(b, out, &nlg) : s1;
         cudaError_t e = cudaStreamEndCapture(b->stream, &g);
         if (s2 != CF_OK) return s2;
         if (e != cudaSuccess) return fail(CF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&b->graph, g, 0);
+        e = cudaGraphInstantiate(&slot, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return fail(CF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
         b->graph_key = key;
@@ -1882,32 +1921,34 @@ cf_status batch_replay(cf_batch *b, int pairs) {
 cf_status batch_run(cf_batch *b, long long n) {
     for (cf_ctx *c : b->ctx)
         if (c->dry_dm > 0.0) return fail(CF_ESTATE, "drying (cf_remove_mass) is not available in a batch");
+    // as cf_step: captured step pairs, the last step recording the fields
     int nl = 0;
     cf_status sj = batch_join_contexts(b);
     if (sj != CF_OK) return sj;
-    long long left = n - 1;  // the last step records the fields
-    if (left >= 3 && b->graph && b->graph_key != batch_key(b)) {
-        // one plain step brings every context to the captured graph's parity
+    long long left = n;
+    if (left >= 4 && b->graph && b->graph_key != batch_key(b)) {
+        // one plain step brings every context to the captured graphs' parity
         cf_status s = batch_enqueue_step(b, false, &nl);
         if (s != CF_OK) return s;
         --left;
     }
-    if (left >= 2) {
-        cf_status s = batch_graph(b);
-        if (s != CF_OK) return s;
-        while (left >= 2) {
-            CF_CUDA(cudaGraphLaunch(b->graph, b->stream));
-            left -= 2;
+    if (left >= 3) {
+        const bool odd = (left & 1) != 0;
+        const long long pairs = left / 2;
+        for (long long k = 0; k < pairs; ++k) {
+            const bool out = !odd && k == pairs - 1;
+            cf_status s = batch_graph(b, out);
+            if (s != CF_OK) return s;
+            CF_CUDA(cudaGraphLaunch(out ? b->graph_out : b->graph, b->stream));
             nl += b->graph_launches;
         }
+        left -= 2 * pairs;
     }
     while (left > 0) {
-        cf_status s = batch_enqueue_step(b, false, &nl);
+        cf_status s = batch_enqueue_step(b, left == 1, &nl);
         if (s != CF_OK) return s;
         --left;
     }
-    cf_status s = batch_enqueue_step(b, true, &nl);
-    if (s != CF_OK) return s;
     for (cf_ctx *c : b->ctx) c->steps_done += n;
     b->launches_last = nl;
     return CF_OK;
@@ -1973,7 +2014,7 @@ cf_status cf_batch_create(cf_ctx *const *ctxs, int n, cf_batch **out) {
 cf_status cf_batch_destroy(cf_batch *b) {
     if (!b) return CF_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
-    if (b->graph) cudaGraphExecDestroy(b->graph);
+    batch_drop_graphs(b);
     if (b->work) cudaFree(b->work);
     for (int4 *w : b->gwork)
         if (w) cudaFree(w);
