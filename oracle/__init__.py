@@ -231,6 +231,9 @@ class Oracle:
         F = np.ascontiguousarray(F, np.int32)
         cid = lib().or_add_capsule(self._h, X.shape[0], _ptr(X), F.shape[0], _ptr(F, _ip), kS, C,
                                    kB, kV, mass, mode)
+        if cid < 0:
+            raise RuntimeError("oracle: capsule rejected (too many capsules, or an element spans more than "
+                               "16 lattice units)")
         if wet:
             lib().or_set_capsule_wetting(self._h, cid, float(wet))
         self.nv.append(X.shape[0])
@@ -251,7 +254,9 @@ class Oracle:
         return f
 
     def step(self, n=1):
-        lib().or_step(self._h, int(n))
+        if lib().or_step(self._h, int(n)) != 0:
+            raise RuntimeError("oracle: a membrane element spans more than 16 lattice units or has a "
+                               "non-finite vertex (diverged run)")
 
     def remove_mass(self, dmA):
         """Drying: turn dmA of component A into B each step (0 turns it off)."""

@@ -469,7 +469,10 @@ static int link_fluid(const or_ctx *c, int z, int k) {
  * bounding box (a link touching the element must start within one lattice
  * unit of the box).  A link is cut when the number of elements it crosses is
  * odd; its element is the smallest global index among those it crosses. */
-static void compute_cuts(or_ctx *c) {
+/* Returns -1 (the cut structure left partial) when an element spans more than
+ * 16 lattice units along an axis or has a non-finite vertex: a diverged
+ * membrane, which the search below would otherwise walk without end. */
+static int compute_cuts(or_ctx *c) {
     clear_cuts(c);
     for (int ci = 0; ci < c->ncaps; ++ci) {
         or_capsule *p = &c->caps[ci];
@@ -479,6 +482,7 @@ static void compute_cuts(or_ctx *c) {
             int lo[3], hi[3];
             for (int k = 0; k < 3; ++k) {
                 double mn = fmin(A[k], fmin(B[k], C[k])), mx = fmax(A[k], fmax(B[k], C[k]));
+                if (!(mx - mn <= 16.0) || !isfinite(mn) || !isfinite(mx)) return -1;
                 lo[k] = (int)ceil(mn - 1.0);
                 hi[k] = (int)floor(mx + 1.0);
             }
@@ -494,6 +498,7 @@ static void compute_cuts(or_ctx *c) {
                         }
         }
     }
+    return 0;
 }
 
 /* Interior flags by parity of cut +z links walked up each column. */
@@ -540,7 +545,7 @@ int or_add_capsule(or_ctx *c, int nv, const double *X, int nf, const int *F, dou
     p->area = mesh_area(p->X, p->F, nf);
     p->volume = p->V0;
     c->ncaps++;
-    compute_cuts(c);
+    if (compute_cuts(c) != 0) return -1;
     compute_inside(c);
     return c->ncaps - 1;
 }
@@ -1018,7 +1023,8 @@ int or_step(or_ctx *c, int nsteps) {
             collide(c, NULL);
             if (c->dmA > 0.0) remove_mass(c);
             ibm_move(c);
-            compute_cuts(c);   /* the interior flags of the readouts follow the membrane */
+            /* the interior flags of the readouts follow the membrane */
+            if (compute_cuts(c) != 0) return -1;
             compute_inside(c);
             c->step++;
             continue;
@@ -1029,7 +1035,10 @@ int or_step(or_ctx *c, int nsteps) {
         membrane_update(c);
         int moving = 0;
         for (int ci = 0; ci < c->ncaps; ++ci) moving |= c->caps[ci].mode != 2;
-        if (moving) { compute_cuts(c); compute_inside(c); }
+        if (moving) {
+            if (compute_cuts(c) != 0) return -1;
+            compute_inside(c);
+        }
         c->step++;
     }
     return 0;

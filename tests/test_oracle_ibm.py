@@ -112,3 +112,45 @@ def test_first_step_against_hand_fields():
     moved = np.array([o.ibm_interp_point(u, X0[v]) for v in range(X0.shape[0])])
     assert np.allclose(X1 - X0, moved, atol=1e-15)
     assert np.abs(moved).max() > 1e-7  # the capsule does move
+
+
+def test_drying_with_the_diffuse_interface():
+    """Drying composes with the diffuse-interface step: with a capsule in the
+    film the A inventory still falls by exactly dm per step and the total mass
+    stays (the spread force moves momentum, no mass)."""
+    o = O.Oracle(14, 12, 18, wall=1, rep_dz=2.0, flags=O.Oracle.IBM)
+    X, F = I.icosphere(2, 4.0, (7.3, 5.9, 9.17))
+    o.add_capsule(X, F, 5e-3, 1.0, 1e-3, 1.0, 25.0, I.MODE_FREE)
+    o.set_film(8.0, I.RHO_MAJ, I.RHO_MIN, I.RHO_MIX, I.jitter((18, 12, 14), 1e-3, seed=2))
+    m0 = o.total_mass()
+    dm = 0.04
+    o.remove_mass(dm)
+    o.step(6)
+    m = o.total_mass()
+    assert abs((m0[0] - m[0]) - 6 * dm) < 1e-10
+    assert abs(m.sum() - m0.sum()) < 1e-10
+
+
+def test_flag_value_agrees_with_the_library_header_and_binding():
+    """The diffuse-interface flag has one value in the C header, the Python
+    binding and the oracle."""
+    import os
+    import re
+    from paper_2007_15405_gb300 import capfilm as cfm
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                            "capfilm.h")).read()
+    m = re.search(r"CF_IBM\s*=\s*(\d+)", hdr)
+    assert m and int(m.group(1)) == cfm.IBM == O.Oracle.IBM
+
+
+def test_diverged_membrane_is_reported():
+    """A capsule placed below the repulsive plane (z = 10.5) meets Hertz forces
+    of order Xi (delta0 - d)^1.5 with d ~ -5 and is thrown apart in one step;
+    the oracle reports the diverged membrane instead of searching the
+    exploded elements for cut links."""
+    o = O.Oracle(14, 12, 18, wall=1, rep_dz=10.0, flags=O.Oracle.IBM)
+    X, F = I.icosphere(2, 4.0, (7.3, 5.9, 9.17))
+    o.add_capsule(X, F, 5e-3, 1.0, 1e-3, 1.0, 25.0, I.MODE_FREE)
+    o.set_film(8.0, I.RHO_MAJ, I.RHO_MIN, I.RHO_MIX, None)
+    with pytest.raises(RuntimeError, match="16 lattice units"):
+        o.step(4)
