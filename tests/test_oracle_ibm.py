@@ -154,3 +154,38 @@ def test_diverged_membrane_is_reported():
     o.set_film(8.0, I.RHO_MAJ, I.RHO_MIN, I.RHO_MIX, None)
     with pytest.raises(RuntimeError, match="16 lattice units"):
         o.step(4)
+
+
+def _random_point_cases():
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+    return hyp, st
+
+
+def test_spreading_and_interpolation_at_random_positions():
+    """At any position, also across the periodic boundaries and next to the
+    substrate: interpolation is the adjoint of spreading, spreading keeps the
+    force where no stencil node is solid, and the weights of a point sum to
+    one there (a constant field is interpolated exactly)."""
+    hyp, st = _random_point_cases()
+    o_per = ibm_box(9, 8, 7, wall=0)
+    o_sub = ibm_box(9, 8, 7, wall=1)
+    rng = np.random.default_rng(11)
+    fields = {id(o): rng.standard_normal(3 * o.N) for o in (o_per, o_sub)}
+
+    @hyp.settings(max_examples=60, deadline=None)
+    @hyp.given(st.floats(-3.0, 12.0), st.floats(-3.0, 11.0), st.floats(0.0, 7.0), st.booleans())
+    def check(x, y, z, wall):
+        o = o_sub if wall else o_per
+        X = np.array([x, y, z])
+        F = np.array([0.7, -1.3, 0.4])
+        f = o.ibm_spread_point(X, F)
+        u = fields[id(o)]
+        assert abs(o.ibm_interp_point(u, X) @ F - u @ f) < 1e-11
+        zs = [int(np.floor(z)) - 1 + k for k in range(4)]
+        if not wall or all(zz % o.nz != 0 for zz in zs):
+            assert np.allclose(f.reshape(3, -1).sum(axis=1), F, atol=1e-13)
+            const = np.concatenate([np.full(o.N, c) for c in (0.3, -0.2, 0.1)])
+            assert np.allclose(o.ibm_interp_point(const, X), [0.3, -0.2, 0.1], atol=1e-14)
+
+    check()
