@@ -70,3 +70,25 @@ def test_warm_dataset_ranges():
         assert 0.3 <= h <= 0.9
         assert cap.radius + 4 <= cap.centre[0] - 0.3 <= w.nx - cap.radius - 4
     assert [w.capsules[0].centre for w in I.warm_dataset(40, seed=5)] == [w.capsules[0].centre for w in wls]
+
+
+def test_many_capsules_layout():
+    """The many-particle film: seeded random sequential addition with every
+    periodic centre distance at least 2R + 2 delta0 + 1, bottoms where the
+    substrate repulsion starts, bending modulus from beta = R^2 gamma / kB."""
+    wl = I.many_capsules(100, 320, 320)
+    again = I.many_capsules(100, 320, 320)
+    other = I.many_capsules(100, 320, 320, seed=13)
+    c = np.array([cap.centre for cap in wl.capsules])
+    assert len(wl.capsules) == 100
+    assert np.array_equal(c, np.array([cap.centre for cap in again.capsules]))
+    assert not np.array_equal(c, np.array([cap.centre for cap in other.capsules]))
+    R = wl.capsules[0].radius
+    d = c[:, None, :2] - c[None, :, :2]
+    d -= np.round(d / 320.0) * 320.0
+    r = np.hypot(d[..., 0], d[..., 1]) + np.eye(len(c)) * 1e9
+    assert r.min() >= 2 * R + 2 * I.DELTA0 + 1.0
+    assert np.allclose(c[:, 2], I.z_rest(R) + c[0, 2] - I.z_rest(R))
+    assert abs(c[0, 2] - R - I.DELTA0 - (0.5 + I.REP_DZ)) < 1.0  # bottom at the repulsion's reach
+    assert all(abs(R * R * I.GAMMA_G36 / cap.kB - 25.0) < 1e-9 for cap in wl.capsules)
+    assert abs(100 * np.pi * R * R / (320 * 320) - 0.307) < 1e-3
