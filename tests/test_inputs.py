@@ -92,3 +92,31 @@ def test_many_capsules_layout():
     assert abs(c[0, 2] - R - I.DELTA0 - (0.5 + I.REP_DZ)) < 1.0  # bottom at the repulsion's reach
     assert all(abs(R * R * I.GAMMA_G36 / cap.kB - 25.0) < 1e-9 for cap in wl.capsules)
     assert abs(100 * np.pi * R * R / (320 * 320) - 0.307) < 1e-3
+
+
+def test_pair_and_single_particle_workloads():
+    """The two-particle and single-particle set-ups: centre distances, film
+    heights above the repulsive plane, boxes and moduli as their recipes state."""
+    rest = 0.5 + I.REP_DZ
+    pair = I.capsule_pair()
+    (a, b) = [np.array(c.centre) for c in pair.capsules]
+    assert (pair.nx, pair.ny, pair.nz) == (128, 64, 64)
+    assert abs(np.linalg.norm(b - a) - 3 * 12.0) < 1e-12 and a[2] == b[2]
+    assert abs(pair.h_top - (rest + 0.6 * 12.0)) < 1e-12
+    for gap in (3.0, 5.0, 7.0):
+        rp = I.rigid_pair(gap)
+        (a, b) = [np.array(c.centre) for c in rp.capsules]
+        L = gap * 10.0 + 20.0
+        assert abs(b[0] - a[0] - L) < 1e-12
+        assert rp.nx % 8 == 0 and rp.nx >= 2 * L + 64
+        assert all(c.mode == I.MODE_FIXED for c in rp.capsules)
+        assert abs(rp.h_top - (rest + 0.16 * 10.0)) < 1e-12
+    one = I.rigid_particle(0.4)
+    assert len(one.capsules) == 1 and one.capsules[0].mode == I.MODE_FIXED
+    assert abs(one.h_top - (rest + 4.0)) < 1e-12
+    for beta in (10.0, 25.0, 50.0):
+        ap = I.approach_pair(beta)
+        (a, b) = [np.array(c.centre) for c in ap.capsules]
+        assert abs(b[0] - a[0] - 40.0) < 1e-12  # surface gap 2R
+        for c in ap.capsules:
+            assert c.C == 9.0 and abs(100.0 * I.GAMMA_G36 / c.kB - beta) < 1e-9
